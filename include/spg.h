@@ -1,0 +1,176 @@
+/*
+ * spg.h -- C ABI of libspg: low-energy states of clustered Ising / Potts
+ * models on quasi-2D grids by boundary-MPS contraction of the PEPS of their
+ * Boltzmann distribution and a merging branch-and-bound (beam) search,
+ * following arXiv:2502.02317 (SpinGlassPEPS.jl).
+ *
+ * Conventions (all entry points):
+ *   - return 0 (SPG_OK) on success, a negative SPG_E* code on failure; the
+ *     message of the last failure on a context is spg_last_error(ctx);
+ *   - every input array is a HOST pointer and is copied during the call;
+ *     the caller keeps ownership;
+ *   - handles (spg_ctx, spg_problem, spg_result) are owned by the library and
+ *     released with the matching *_destroy, which accept NULL;
+ *   - energies are exact int64 integers in units of 2^-energy_shift;
+ *   - no C++ exception crosses this boundary.
+ *
+ * The library runs on one CUDA device, on the stream given to spg_create
+ * (or a stream it creates).  Solves are enqueued on that stream: spg_solve
+ * returns once the work is enqueued; spg_result_get / spg_result_info wait
+ * for it.
+ */
+#ifndef SPG_H
+#define SPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPG_OK 0
+#define SPG_EINVAL (-1)       /* bad argument, size or structure           */
+#define SPG_EINEXACT (-2)     /* J or h not on the 2^-energy_shift grid    */
+#define SPG_ENOMEM (-3)       /* host or device allocation failed          */
+#define SPG_ECUDA (-4)        /* a CUDA call failed                        */
+#define SPG_ETIMEOUT (-5)     /* a bounded device wait ran out             */
+#define SPG_ENUMERIC (-6)     /* NaN/Inf or an energy consistency failure  */
+#define SPG_EUNSUPPORTED (-7) /* valid input outside the built limits      */
+
+#define SPG_SQUARE 0 /* grid edges: 4-neighbour (square lattice)            */
+#define SPG_KING 1   /* grid edges: 8-neighbour (king's graph)              */
+
+#define SPG_FP64 0  /* every contraction, SVD and marginal in FP64          */
+#define SPG_MIXED 1 /* FP32 contractions, FP64 marginal normalisation       */
+
+/* Built limits (SPG_EUNSUPPORTED beyond them). */
+#define SPG_MAX_STATES 256    /* states of one cluster (2^8 spins)          */
+#define SPG_MAX_PROJ 16       /* distinct rows/columns of a pairwise table  */
+#define SPG_MAX_CHI 64        /* boundary-MPS bond dimension                */
+#define SPG_MAX_COLS 32       /* grid columns                               */
+#define SPG_MAX_BEAM 4096     /* max_states                                 */
+
+typedef struct spg_ctx spg_ctx;
+typedef struct spg_problem spg_problem;
+typedef struct spg_result spg_result;
+
+/* Solver parameters (Sec. 3.1 of the paper: MpsParameters(bond_dim,
+ * num_sweeps), SearchParameters(max_states, cut_off_prob), MpsContractor(...;
+ * beta)).  spg_params_default fills the defaults listed per field. */
+typedef struct {
+  double beta;         /* inverse temperature, > 0 (default 1)               */
+  int32_t chi;         /* boundary-MPS bond dimension (default 16)           */
+  int32_t num_sweeps;  /* variational sweeps after each zipper (default 0)   */
+  int32_t beam;        /* max_states: partial states kept (default 256)      */
+  int32_t precision;   /* SPG_FP64 or SPG_MIXED (default SPG_FP64)           */
+  double cut_off_prob; /* drop children with p < c * max p (default 0: off)  */
+  int32_t svd_iters;   /* subspace iterations of a large truncation (def. 6) */
+  int32_t warm_start;  /* reserved, must be 0                                */
+  uint64_t seed;       /* seed of the truncation's start block (default 0)   */
+  int32_t reserved[8]; /* must be 0                                          */
+} spg_params;
+
+/* Per-result diagnostics. */
+typedef struct {
+  int32_t n_states;        /* states returned                               */
+  int32_t near_ties;       /* prune steps whose cut fell within 1e-9 in log p */
+  int32_t degenerate_cuts; /* truncations whose cut fell in a degenerate gap */
+  int32_t error_flags;     /* device-side checks that failed (0 = none)     */
+  double ms_boundary;      /* device time of the boundary-MPS phase          */
+  double ms_search;        /* device time of the search phase                */
+  double candidates;       /* sum over sites of (live beam x states)         */
+  double boundary_lognorm; /* log-norm of the last boundary MPS built        */
+} spg_info;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int spg_version(void);
+
+/* Defaults for every field of *p.  Returns SPG_EINVAL if p is NULL. */
+int spg_params_default(spg_params* p);
+
+/* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * (may be NULL: the library creates and owns a non-blocking stream).  The
+ * context owns its device workspace, grown on demand and reused. */
+int spg_create(spg_ctx** out, int device, void* cuda_stream);
+void spg_destroy(spg_ctx* ctx);
+const char* spg_last_error(const spg_ctx* ctx);
+
+/* Ising form (Eq. 2): E(s) = sum_e J_e s_ei s_ej + sum_i h_i s_i, s = +-1.
+ *   n_spins, n_edges        : sizes; spins are 0 .. n_spins-1
+ *   ei, ej, J               : [n_edges] couplings (ei != ej)
+ *   h                       : [n_spins] fields, or NULL for h = 0
+ *   cluster_of_spin         : [n_spins] cluster id 0 .. n_clusters-1
+ *   grid_rows, grid_cols    : the grid; n_clusters = grid_rows * grid_cols
+ *   cluster_row, cluster_col: [n_clusters] grid cell of each cluster (one
+ *                             cluster per cell)
+ *   energy_shift            : J and h must be multiples of 2^-energy_shift
+ *                             (else SPG_EINEXACT); energies are integers in
+ *                             that unit
+ *   node_type               : SPG_SQUARE or SPG_KING; a coupling between
+ *                             clusters that are not grid neighbours of that
+ *                             type is SPG_EINVAL
+ * A cluster's state is x = sum_k b_k 2^k over its spins in ascending index,
+ * with s = 2 b - 1 (Sec. 2: clusters become Potts variables). */
+int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei,
+                      const int32_t* ej, const double* J, const double* h,
+                      const int32_t* cluster_of_spin, int32_t grid_rows, int32_t grid_cols,
+                      const int32_t* cluster_row, const int32_t* cluster_col,
+                      int32_t energy_shift, int32_t node_type, spg_problem** out);
+
+/* Potts form (Eq. 1): sites are the grid cells in row-major order.
+ *   d        : [rows*cols] states per site
+ *   local_E  : concatenated local tables, site by site (sum d entries)
+ *   em, en   : [n_edges] grid-neighbour site pairs
+ *   pair_E   : concatenated d_em x d_en row-major tables (one per edge;
+ *              tables on the same pair are added)
+ * All energies are int64 in units of 2^-energy_shift. */
+int spg_problem_potts(spg_ctx* ctx, int32_t grid_rows, int32_t grid_cols, const int32_t* d,
+                      const int64_t* local_E, int32_t n_edges, const int32_t* em,
+                      const int32_t* en, const int64_t* pair_E, int32_t energy_shift,
+                      int32_t node_type, spg_problem** out);
+void spg_problem_destroy(spg_problem* prob);
+
+/* Grid and per-site sizes of a problem (any pointer may be NULL). */
+int spg_problem_shape(const spg_problem* prob, int32_t* rows, int32_t* cols, int32_t* d_per_site);
+
+/* Low-energy spectrum (Sec. 2 and Sec. 3.1 low_energy_spectrum): boundary
+ * MPSs bottom-up (zipper + SVD truncation to chi, num_sweeps variational
+ * sweeps), then the branch-and-bound search in row-major order keeping
+ * `beam` partial states, merging those equal on the boundary of the explored
+ * region.  Enqueued on the context's stream; *out is valid at once, its
+ * contents after spg_result_get. */
+int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_result** out);
+
+/* Copy the final states out (waits for the solve).  States are sorted by
+ * (energy ascending, state lexicographically ascending).
+ *   states        : [n_states x n_sites] cluster states, or NULL
+ *   energies_fixed: [n_states] int64 energies, or NULL
+ *   energies      : [n_states] the same as double (exact below 2^53), or NULL
+ *   log_probs     : [n_states] log of the estimated probability, or NULL
+ * Call first with all arrays NULL to read n_states and n_sites. */
+int spg_result_get(spg_result* res, int32_t* n_states, int32_t* n_sites, uint16_t* states,
+                   int64_t* energies_fixed, double* energies, double* log_probs);
+int spg_result_info(spg_result* res, spg_info* info);
+void spg_result_destroy(spg_result* res);
+
+/* Teacher-forced conditional marginals (Sec. 2, Fig. 1(d)): for each of the
+ * n_prefix prefixes (prefixes[k*site .. k*site+site-1] = states of sites
+ * 0 .. site-1), log p(x_site | prefix) for every state x of `site`, written
+ * to log_marg[k*d_site + x].  Uses the same boundary MPSs and environment
+ * kernels as spg_solve.  Synchronous. */
+int spg_debug_marginals(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm,
+                        int32_t site, int32_t n_prefix, const uint16_t* prefixes,
+                        double* log_marg);
+
+/* log Z of the problem at prm->beta from the boundary MPSs contracted down
+ * to the top row (Sec. 2: approximate contraction of the PEPS).  Exact when
+ * no truncation happens.  Synchronous. */
+int spg_log_partition(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm,
+                      double* log_z);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPG_H */

@@ -1,0 +1,167 @@
+"""Exact references that use none of the tables, projectors or MPSs.
+
+Test infrastructure only (see the package header).
+
+Everything here works on spins and Eq. 2 directly:
+* ``brute_force``: all 2^n spin configurations (n <= 24), giving the exact
+  ground energy and degeneracy, log Z = log sum exp(-beta E), and exact
+  conditional marginals of cluster states given a prefix of cluster states;
+* ``chimera_strip``: row transfer matrices of a Chimera-like strip of width
+  <= 3 cells over the 4w side-A spins of a row (the only spins with couplers
+  to the next row), giving exact log Z (log-sum-exp) and the exact ground
+  energy (min-plus, integer) for any number of rows.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .tables import _to_int
+
+
+def _spins(n, lo, hi):
+    x = np.arange(lo, hi, dtype=np.int64)[:, None]
+    return 2 * ((x >> np.arange(n, dtype=np.int64)[None, :]) & 1) - 1
+
+
+def all_energies(inst) -> np.ndarray:
+    """int64 energy of every spin configuration, index = sum_i b_i 2^i.
+
+    Eq. 2 term by term: the coupling sum is taken as s . (J_upper s) with the
+    integer couplings held exactly in float64 (all partial sums < 2^53)."""
+    n = inst.n_spins
+    if n > 24:
+        raise ValueError("brute force is limited to 24 spins")
+    J = _to_int(inst.J, inst.energy_shift)
+    h = _to_int(inst.h, inst.energy_shift)
+    if np.sum(np.abs(J)) + np.sum(np.abs(h)) >= 2 ** 52:
+        raise ValueError("energies too large for the float64 path")
+    Jm = np.zeros((n, n))
+    np.add.at(Jm, (np.asarray(inst.ei), np.asarray(inst.ej)), J.astype(np.float64))
+    hf = h.astype(np.float64)
+    out = np.empty(2 ** n, dtype=np.int64)
+    chunk = 1 << 18
+    for lo in range(0, 2 ** n, chunk):
+        hi = min(2 ** n, lo + chunk)
+        s = _spins(n, lo, hi).astype(np.float64)
+        e = np.einsum("ci,ci->c", s @ Jm, s) + s @ hf
+        out[lo:hi] = np.rint(e).astype(np.int64)
+    return out
+
+
+def logsumexp(a):
+    m = np.max(a)
+    return float(m + np.log(np.sum(np.exp(a - m))))
+
+
+def brute_force(inst, beta: float):
+    E = all_energies(inst)
+    emin = int(E.min())
+    u = 2.0 ** (-inst.energy_shift)
+    logZ = logsumexp(-beta * u * E.astype(np.float64))
+    return {"E": E, "ground": emin, "degeneracy": int(np.sum(E == emin)), "logZ": logZ}
+
+
+def cluster_states(n, sites_spins):
+    """State of every cluster (bits of its spins, ascending) for all 2^n
+    configurations: list over sites of uint16 arrays [2^n]."""
+    idx = np.arange(2 ** n, dtype=np.int64)
+    out = []
+    for sp in sites_spins:
+        x = np.zeros(2 ** n, dtype=np.int64)
+        for k, spin in enumerate(sp):
+            x |= ((idx >> int(spin)) & 1) << k
+        out.append(x.astype(np.uint16))
+    return out
+
+
+def exact_conditional(E, beta, shift, cs, site, prefix, d):
+    """log p(x_site | x_0..x_{site-1} = prefix) over all d states of ``site``.
+
+    E: all configuration energies; cs: ``cluster_states`` of every site."""
+    u = 2.0 ** (-shift)
+    mask = np.ones(E.shape[0], dtype=bool)
+    for t, xv in enumerate(prefix):
+        mask &= cs[t] == int(xv)
+    xs = cs[site][mask]
+    w = -beta * u * E[mask].astype(np.float64)
+    out = np.full(d, -np.inf)
+    for x in range(d):
+        sel = w[xs == x]
+        if sel.size:
+            out[x] = logsumexp(sel)
+    return out - logsumexp(w)
+
+
+def chimera_strip(inst, beta: float):
+    """Exact log Z and ground energy of a Chimera-like grid of width <= 3.
+
+    Spin layout: cell (i, j) owns spins 8 (i cols + j) + k, k < 4 side A.
+    Couplings may join spins of one row in any way, and side-A spins of
+    vertically adjacent cells of rows i and i+1; anything else is rejected."""
+    rows, cols = inst.grid_rows, inst.grid_cols
+    if cols > 3:
+        raise ValueError("width <= 3 only")
+    J = _to_int(inst.J, inst.energy_shift)
+    h = _to_int(inst.h, inst.energy_shift)
+    u = 2.0 ** (-inst.energy_shift)
+    row_of = np.arange(inst.n_spins) // (8 * cols)
+    k_of = np.arange(inst.n_spins) % 8
+    col_of = (np.arange(inst.n_spins) // 8) % cols
+    # position of a spin inside its row's A block (4 cols) or B block
+    posA = col_of * 4 + k_of
+    posB = col_of * 4 + (k_of - 4)
+    nA = 4 * cols
+    sA = _spins(nA, 0, 2 ** nA)
+    sB = _spins(nA, 0, 2 ** nA)
+    intra = [dict(AA=np.zeros((nA, nA), np.int64), BB=np.zeros((nA, nA), np.int64),
+                  AB=np.zeros((nA, nA), np.int64), hA=np.zeros(nA, np.int64),
+                  hB=np.zeros(nA, np.int64)) for _ in range(rows)]
+    vert = [np.zeros((nA, nA), np.int64) for _ in range(max(rows - 1, 0))]
+    for e in range(len(J)):
+        i, j = int(inst.ei[e]), int(inst.ej[e])
+        if row_of[i] > row_of[j]:
+            i, j = j, i
+        ri, rj = row_of[i], row_of[j]
+        Ai, Aj = k_of[i] < 4, k_of[j] < 4
+        if ri == rj:
+            t = intra[ri]
+            if Ai and Aj:
+                t["AA"][posA[i], posA[j]] += J[e]
+            elif not Ai and not Aj:
+                t["BB"][posB[i], posB[j]] += J[e]
+            elif Ai:
+                t["AB"][posA[i], posB[j]] += J[e]
+            else:
+                t["AB"][posA[j], posB[i]] += J[e]
+        elif rj == ri + 1 and Ai and Aj:
+            vert[ri][posA[i], posA[j]] += J[e]
+        else:
+            raise ValueError("coupling outside the strip's transfer structure")
+    for s in range(inst.n_spins):
+        t = intra[row_of[s]]
+        if k_of[s] < 4:
+            t["hA"][posA[s]] += h[s]
+        else:
+            t["hB"][posB[s]] += h[s]
+
+    def row_tables(t):
+        EA = np.einsum("xa,ab,xb->x", sA, t["AA"], sA) + sA @ t["hA"]
+        EB = np.einsum("xa,ab,xb->x", sB, t["BB"], sB) + sB @ t["hB"]
+        EAB = sA @ t["AB"] @ sB.T  # [A, B]
+        Efull = EA[:, None] + EAB + EB[None, :]
+        g = Efull.min(axis=1)
+        w = -beta * u * Efull.astype(np.float64)
+        m = w.max(axis=1)
+        lf = m + np.log(np.exp(w - m[:, None]).sum(axis=1))
+        return g, lf
+
+    g, lv = row_tables(intra[0])
+    G = g
+    for r in range(1, rows):
+        Ev = sA @ vert[r - 1] @ sA.T  # [A_prev, A_next]
+        g, lf = row_tables(intra[r])
+        G = g + (G[:, None] + Ev).min(axis=0)
+        w = lv[:, None] - beta * u * Ev.astype(np.float64)
+        m = w.max(axis=0)
+        lv = lf + m + np.log(np.exp(w - m[None, :]).sum(axis=0))
+    return {"logZ": logsumexp(lv), "ground": int(G.min())}

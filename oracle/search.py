@@ -1,0 +1,219 @@
+"""Branch-and-bound (beam) search over cluster states with branch merging.
+
+Test infrastructure only (see the package header).
+
+Paper: Sec. 2 (the search builds the most probable configurations one Potts
+variable at a time in a fixed order, keeping a predefined number of them;
+marginal and conditional probabilities come from the contracted network;
+partial configurations with identical values of the Potts variables on the
+boundary next to the unexplored region are merged), Sec. 3.1
+(``SearchParameters(max_states, cut_off_prob)``, ``merge_branches(...;
+merge_type = :nofit)``, ``low_energy_spectrum``), and the solution's states,
+energies and estimated probabilities (Sec. 2.2).
+
+Readings taken here:
+* order: row-major over the clusters of the grid;
+* conditional of site (i, j) given the fixed prefix: with u_k the down
+  projection of cluster (i-1, k), h the right projection of cluster (i, j-1),
+  Lenv = prod_{k<j} B_{i+1}[k][:, P_D(x_{i,k}), :] and the right environment
+      R_{j}[a, l] = sum_x w(x) b_left[l, P_L x] b_up[u_j, P_U x]
+                    sum_a' B_{i+1}[j][a, P_D x, a'] R_{j+1}[a', P_R x],
+  R_L = 1, the weight of state x is
+      q(x) = w(x) b_left[h, P_L x] b_up[u_j, P_U x]
+             sum_{a,a'} Lenv[a] B_{i+1}[j][a, P_D x, a'] R_{j+1}[a', P_R x]
+  and log p(x | prefix) = log q(x) - log sum_x q(x), in FP64;
+* a child's log-probability is its parent's plus the log-conditional; its
+  partial energy is the parent's plus E_j(x) and the pairwise terms with
+  already fixed neighbours (exact integers);
+* merge key (``merge`` on, the paper's example): the states of all fixed
+  clusters that have an edge to an unfixed cluster; at the last site the key
+  is empty, so one state survives.  Among children with equal key the one
+  with the lowest partial energy is kept, ties going to the
+  lexicographically smaller state; the kept
+  child keeps its own log-probability.  Within a key class the exact
+  conditional ordering and the energy ordering coincide, so no floating-point
+  comparison enters the merge;
+* cut_off_prob c > 0 drops children with p < c * max p at that step; then
+  the max_states children ranked first by (-log p, partial energy,
+  lexicographic state) survive.  A near tie (|delta log p| <= 1e-9 max(1,
+  |log p|) between the last survivor and the first dropped child) is
+  recorded, since which of the two survives is then decided by rounding;
+* the final states are reported sorted by (energy, lexicographic state), the
+  energy recomputed from the tables, probability = exp(log p).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import boundary as bnd
+from . import peps as peps_mod
+from .tables import FactorGraph, energy
+
+NEAR_TIE_RTOL = 1e-9
+
+
+@dataclass
+class Params:
+    beta: float = 1.0
+    chi: int = 16
+    num_sweeps: int = 0
+    beam: int = 256
+    cut_off_prob: float = 0.0
+    merge: bool = True
+
+
+@dataclass
+class Result:
+    states: np.ndarray  # [n, n_sites]
+    energies: np.ndarray  # int64 [n]
+    log_probs: np.ndarray  # float64 [n]
+    near_ties: int = 0
+    degenerate_cut: bool = False
+    steps: list = field(default_factory=list)  # per site: (n candidates, n kept)
+
+
+def key_sites(fg: FactorGraph, s: int) -> list:
+    """Fixed sites (index <= s) with an edge to an unfixed site (index > s)."""
+    out = []
+    for t in range(s + 1):
+        for (m, n) in fg.edges:
+            if (m == t and n > s) or (n == t and m > s):
+                out.append(t)
+                break
+    return out
+
+
+def right_envs(p: peps_mod.PEPS, B: bnd.MPS, i: int, upper_states) -> list:
+    """R_{j} for j = 1 .. L (index j -> [chi_j, DL_j]); R_L = [[1]]."""
+    L = p.cols
+    R = [None] * (L + 1)
+    R[L] = np.ones((1, 1))
+    for j in range(L - 1, 0, -1):
+        st = p.site(i, j)
+        uj = 0 if i == 0 else int(p.site(i - 1, j).PD[upper_states[j]])
+        A = B.sites[j]
+        Rn = np.zeros((A.shape[0], st.DL))
+        for x in range(st.d):
+            v = A[:, st.PD[x], :] @ R[j + 1][:, st.PR[x]]
+            Rn += (st.w[x] * st.b_up[uj, st.PU[x]]) * np.outer(v, st.b_left[:, st.PL[x]])
+        R[j] = Rn / np.max(np.abs(Rn))
+    return R
+
+
+def log_conditional(p, B, i, j, lenv, R, upper_state_j, left_state):
+    """log p(x | prefix) for all x of site (i, j) (formula in the header)."""
+    st = p.site(i, j)
+    uj = 0 if i == 0 else int(p.site(i - 1, j).PD[upper_state_j])
+    h = 0 if j == 0 else int(p.site(i, j - 1).PR[left_state])
+    A = B.sites[j]
+    q = np.empty(st.d)
+    for x in range(st.d):
+        q[x] = (st.w[x] * st.b_left[h, st.PL[x]] * st.b_up[uj, st.PU[x]]
+                * float(lenv @ A[:, st.PD[x], :] @ R[j + 1][:, st.PR[x]]))
+    with np.errstate(divide="ignore"):
+        return np.log(q) - np.log(np.sum(q))
+
+
+def delta_energy(p, i, j, x, upper_state, left_state) -> int:
+    st = p.site(i, j)
+    dE = int(st.E[x])
+    if st.E_left is not None:
+        dE += int(st.E_left[left_state, x])
+    if st.E_up is not None:
+        dE += int(st.E_up[upper_state, x])
+    return dE
+
+
+@dataclass
+class _Partial:
+    states: tuple
+    E: int
+    logp: float
+    lenv: np.ndarray
+    R: list = None
+
+
+def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
+    """``low_energy_spectrum`` with ``merge_type = :nofit`` (readings above)."""
+    p = peps_mod.build(fg, prm.beta)
+    if boundary is None:
+        boundary = bnd.boundary_mpses(p, prm.chi, prm.num_sweeps)
+    rows, cols = fg.rows, fg.cols
+    beam = [_Partial((), 0, 0.0, np.ones(1))]
+    near_ties = 0
+    steps = []
+    for s in range(fg.n_sites):
+        i, j = divmod(s, cols)
+        B = boundary[i + 1]
+        if j == 0:
+            for b in beam:
+                b.lenv = np.ones(1)
+                b.R = right_envs(p, B, i, [b.states[(i - 1) * cols + k] for k in range(cols)] if i > 0 else None)
+        ks = key_sites(fg, s)
+        children = {}
+        n_cand = 0
+        for b in beam:
+            up = b.states[s - cols] if i > 0 else 0
+            left = b.states[s - 1] if j > 0 else 0
+            lc = log_conditional(p, B, i, j, b.lenv, b.R, up, left)
+            for x in range(fg.d[s]):
+                st = b.states + (x,)
+                E = b.E + delta_energy(p, i, j, x, up, left)
+                key = tuple(st[t] for t in ks) if prm.merge else st
+                n_cand += 1
+                cur = children.get(key)
+                if cur is None or (E, st) < (cur[1], cur[0]):
+                    children[key] = (st, E, b.logp + float(lc[x]), b)
+        cands = list(children.values())
+        if prm.cut_off_prob > 0:
+            top = max(c[2] for c in cands)
+            cands = [c for c in cands if c[2] >= top + np.log(prm.cut_off_prob)]
+        cands.sort(key=lambda c: (-c[2], c[1], c[0]))
+        if len(cands) > prm.beam:
+            a, b2 = cands[prm.beam - 1][2], cands[prm.beam][2]
+            if abs(a - b2) <= NEAR_TIE_RTOL * max(1.0, abs(a)):
+                near_ties += 1
+            cands = cands[:prm.beam]
+        steps.append((n_cand, len(cands)))
+        new = []
+        for st, E, lp, parent in sorted(cands, key=lambda c: c[0]):
+            x = st[-1]
+            A = B.sites[j]
+            v = parent.lenv @ A[:, p.site(i, j).PD[x], :]
+            m = np.max(np.abs(v))
+            new.append(_Partial(st, E, lp, v / m if m > 0 else v, parent.R))
+        beam = new
+    order = sorted(range(len(beam)), key=lambda k: (energy(fg, beam[k].states), beam[k].states))
+    states = np.array([beam[k].states for k in order], dtype=np.int64)
+    energies = np.array([energy(fg, beam[k].states) for k in order], dtype=np.int64)
+    for k in order:
+        assert energy(fg, beam[k].states) == beam[k].E
+    logps = np.array([beam[k].logp for k in order])
+    deg = any(boundary[r].degenerate for r in boundary)
+    return Result(states, energies, logps, near_ties, deg, steps)
+
+
+def debug_marginals(fg: FactorGraph, prm: Params, site: int, prefixes, boundary=None):
+    """Teacher-forced log-marginals of ``site`` for given prefixes
+    (prefix = states of sites 0 .. site-1): [n_prefix, d_site]."""
+    p = peps_mod.build(fg, prm.beta)
+    if boundary is None:
+        boundary = bnd.boundary_mpses(p, prm.chi, prm.num_sweeps)
+    cols = fg.cols
+    i, j = divmod(site, cols)
+    B = boundary[i + 1]
+    out = []
+    for pre in prefixes:
+        pre = [int(v) for v in pre]
+        upper = [pre[(i - 1) * cols + k] for k in range(cols)] if i > 0 else None
+        R = right_envs(p, B, i, upper)
+        lenv = np.ones(1)
+        for k in range(j):
+            v = lenv @ B.sites[k][:, p.site(i, k).PD[pre[i * cols + k]], :]
+            lenv = v / np.max(np.abs(v))
+        up = pre[site - cols] if i > 0 else 0
+        left = pre[site - 1] if j > 0 else 0
+        out.append(log_conditional(p, B, i, j, lenv, R, up, left))
+    return np.array(out)

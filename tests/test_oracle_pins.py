@@ -1,0 +1,285 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: every expected value comes from
+brute-force enumeration of Eq. 2, from spin-level transfer matrices, from a
+hand-computed example, from a symmetry of the model, or from a limit in which
+the heuristic becomes exact.  The paper prints no worked numbers (its figures
+carry no data), so no value is quoted from it.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import boundary, exact, peps, search, tables
+
+
+def rand_states(fg, rng):
+    return [int(rng.integers(0, d)) for d in fg.d]
+
+
+# ---------------------------------------------------------------- O1 / O2
+
+@pytest.mark.parametrize("make", [
+    lambda: I.chimera(2, 3),
+    lambda: I.chimera(2, 4, couplings="gauss", h_sigma=0.1, cols=3),
+    lambda: I.square(4, 2, h_sigma=0.3),
+    lambda: I.king_ising(3, 3, 2, 1),
+])
+def test_table_energy_equals_eq2(make):
+    """Eq. 1 through the cluster tables == Eq. 2 on the decoded spins."""
+    inst = make()
+    fg = tables.from_ising(inst)
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        x = rand_states(fg, rng)
+        s = tables.spins_from_states(fg, x, inst.n_spins)
+        e2 = tables.ising_energy(inst, s)
+        assert tables.energy(fg, x) == e2
+        assert tables.energy_reduced(fg, x) == e2
+
+
+def test_projector_hand_example():
+    """Two 2-spin clusters joined by one coupler s1*s2 (J = 1)."""
+    inst = I.IsingInstance(4, np.array([1], np.int32), np.array([2], np.int32), np.array([1.0]),
+                           np.zeros(4), np.array([0, 0, 1, 1], np.int32), 1, 2,
+                           np.array([0, 0], np.int32), np.array([0, 1], np.int32), 0, I.SQUARE)
+    fg = tables.from_ising(inst)
+    e = fg.edges[(0, 1)]
+    # rows depend on bit 1 of x_m, columns on bit 0 of x_n (first occurrence order)
+    assert e.Pm.tolist() == [0, 0, 1, 1]
+    assert e.Pn.tolist() == [0, 1, 0, 1]
+    # s = 2b-1: row 0 has s1 = -1, column 0 has s2 = -1 -> +1
+    assert e.R.tolist() == [[1, -1], [-1, 1]]
+    assert fg.E_loc[0].tolist() == [0, 0, 0, 0]
+
+
+def test_projectors_reconstruct_and_chimera_dims():
+    inst = I.chimera(3, 5, couplings="gauss")
+    fg = tables.from_ising(inst)
+    for e in fg.edges.values():
+        assert np.array_equal(e.R[np.ix_(e.Pm, e.Pn)], e.E)
+        assert e.R.shape == (16, 16)  # 4 couplers with J != 0 per edge
+    # a zero coupler leaves 8 distinct rows/columns on that edge
+    inst.J = inst.J.copy()
+    # vertical couplers of cell (0,0)-(1,0) come after the 9*16 intra ones
+    inst.J[9 * 16] = 0.0
+    fg = tables.from_ising(inst)
+    e = fg.edges[(0, 3)]
+    assert e.R.shape == (8, 8)
+    assert np.array_equal(e.R[np.ix_(e.Pm, e.Pn)], e.E)
+
+
+def test_inexact_input_rejected():
+    inst = I.chimera(2, 0)
+    inst.J = inst.J.copy()
+    inst.J[0] = 0.3
+    with pytest.raises(tables.InexactEnergy):
+        tables.from_ising(inst)
+
+
+# ---------------------------------------------------------------- O3 - O5
+
+@pytest.mark.parametrize("make,beta,chi", [
+    (lambda: I.square(4, 1), 0.7, 64),
+    (lambda: I.square(3, 7, cols=5, h_sigma=0.5), 1.3, 64),
+    (lambda: I.chimera(1, 5, cols=3), 1.0, 256),
+    (lambda: I.chimera(3, 2, cols=1), 1.0, 256),
+    (lambda: I.chimera(2, 8, couplings="gauss", h_sigma=0.2, cols=1), 2.0, 256),
+])
+def test_log_partition_vs_brute_force(make, beta, chi):
+    """No truncation at this chi: log Z equals the sum over all 2^n states."""
+    inst = make()
+    bf = exact.brute_force(inst, beta)
+    p = peps.build(tables.from_ising(inst), beta)
+    assert boundary.log_partition(p, chi) == pytest.approx(bf["logZ"], rel=1e-12, abs=1e-10)
+
+
+@pytest.mark.parametrize("seed,couplings,h,beta", [(0, "pm1", 0.0, 1.0), (3, "gauss", 0.1, 1.0),
+                                                   (4, "gauss", 0.1, 4.0)])
+def test_log_partition_vs_transfer_matrix(seed, couplings, h, beta):
+    """3x3 Chimera: exact spin-level transfer matrix vs untruncated zipper."""
+    inst = I.chimera(3, seed, couplings=couplings, h_sigma=h)
+    ref = exact.chimera_strip(inst, beta)
+    p = peps.build(tables.from_ising(inst), beta)
+    assert boundary.log_partition(p, 256) == pytest.approx(ref["logZ"], rel=1e-12)
+    # truncation to chi = 16 is a heuristic, but must stay close on this size
+    assert abs(boundary.log_partition(p, 16) - ref["logZ"]) < 0.05
+
+
+def transform(inst, k):
+    """k-th of the 8 symmetries of the square grid applied to the clusters."""
+    R, C = inst.grid_rows, inst.grid_cols
+    r, c = inst.cluster_row.copy(), inst.cluster_col.copy()
+    if k & 4:
+        r, c = c, r
+        R, C = C, R
+    if k & 1:
+        r = R - 1 - r
+    if k & 2:
+        c = C - 1 - c
+    out = I.IsingInstance(**{**inst.__dict__})
+    out.grid_rows, out.grid_cols, out.cluster_row, out.cluster_col = R, C, r.astype(np.int32), c.astype(np.int32)
+    return out
+
+
+def test_lattice_transformations_same_log_partition():
+    """Sec. 3.1: the 8 lattice transformations leave the model unchanged."""
+    inst = I.chimera(3, 9)
+    ref = exact.chimera_strip(inst, 1.0)["logZ"]
+    for k in range(8):
+        p = peps.build(tables.from_ising(transform(inst, k)), 1.0)
+        assert boundary.log_partition(p, 256) == pytest.approx(ref, rel=1e-12)
+
+
+def test_mpo_site_definition_hand():
+    """W of a single-spin site with left and up neighbours, by hand."""
+    inst = I.square(2, 3)
+    fg = tables.from_ising(inst)
+    p = peps.build(fg, 0.5)
+    st = p.site(1, 1)  # bottom-right: left and up edges, no right/down
+    W = peps.mpo_site(st)
+    assert W.shape == (2, 1, 2, 1)
+    J_left = inst.J[[k for k in range(len(inst.J)) if (inst.ei[k], inst.ej[k]) == (2, 3)][0]]
+    J_up = inst.J[[k for k in range(len(inst.J)) if (inst.ei[k], inst.ej[k]) == (1, 3)][0]]
+    for l, u in itertools.product(range(2), range(2)):
+        sl, su = 2 * l - 1, 2 * u - 1
+        expect = 0.0
+        for x in range(2):
+            s = 2 * x - 1
+            eL, eU = J_left * sl * s, J_up * su * s
+            expect += np.exp(-0.5 * (eL - (-1.0))) * np.exp(-0.5 * (eU - (-1.0)))
+        assert W[l, 0, u, 0] == pytest.approx(expect, rel=1e-14)
+
+
+# ---------------------------------------------------------------- O6
+
+def test_variational_sweeps_monotone_and_exact():
+    inst = I.chimera(3, 11, couplings="gauss", h_sigma=0.1)
+    p = peps.build(tables.from_ising(inst), 1.0)
+    B2 = boundary.zipper(peps.mpo_row(p, 2), boundary.trivial_mps(3), 64)
+    Ws = peps.mpo_row(p, 1)
+    # truncating: fidelity never decreases and stays <= 1
+    z = boundary.zipper(Ws, B2, 8)
+    _, fid = boundary.variational(Ws, B2, z, 3)
+    assert all(b >= a - 1e-12 for a, b in zip(fid, fid[1:]))
+    assert all(f <= 1 + 1e-10 for f in fid)
+    # no truncation: fidelity 1 and the state is a fixed point
+    z = boundary.zipper(Ws, B2, 256)
+    v, fid = boundary.variational(Ws, B2, z, 1)
+    assert fid[-1] == pytest.approx(1.0, abs=1e-10)
+    assert v.lognorm == pytest.approx(z.lognorm, abs=1e-10)
+
+
+# ---------------------------------------------------------------- O7
+
+@pytest.mark.parametrize("make,beta,chi,sites", [
+    (lambda: I.square(4, 4, h_sigma=0.4), 0.9, 64, [0, 3, 5, 10, 15]),
+    (lambda: I.chimera(1, 6, cols=3), 1.0, 256, [0, 1, 2]),
+    (lambda: I.chimera(3, 6, cols=1, couplings="gauss", h_sigma=0.1), 1.5, 256, [1, 2]),
+])
+def test_marginals_vs_brute_force(make, beta, chi, sites):
+    """Untruncated contraction: conditionals equal the exact ones."""
+    inst = make()
+    fg = tables.from_ising(inst)
+    E = exact.all_energies(inst)
+    cs = exact.cluster_states(inst.n_spins, fg.spins_of_site)
+    rng = np.random.default_rng(1)
+    prm = search.Params(beta=beta, chi=chi)
+    for s in sites:
+        prefixes = [rand_states(fg, rng)[:s] for _ in range(3)]
+        got = search.debug_marginals(fg, prm, s, prefixes)
+        for pre, g in zip(prefixes, got):
+            ref = exact.exact_conditional(E, beta, inst.energy_shift, cs, s, pre, fg.d[s])
+            np.testing.assert_allclose(g, ref, rtol=1e-10, atol=1e-10)
+
+
+def test_marginals_uniform_at_beta_zero():
+    inst = I.chimera(2, 1, couplings="gauss", h_sigma=0.1)
+    fg = tables.from_ising(inst)
+    got = search.debug_marginals(fg, search.Params(beta=0.0, chi=16), 3, [[5, 7, 200]])
+    np.testing.assert_allclose(got[0], -np.log(256) * np.ones(256), atol=1e-12)
+
+
+def test_z2_symmetry_first_site():
+    """h = 0: flipping every spin is a symmetry, so p(x) = p(~x)."""
+    inst = I.chimera(3, 2)
+    fg = tables.from_ising(inst)
+    got = search.debug_marginals(fg, search.Params(beta=1.0, chi=16), 0, [[]])[0]
+    np.testing.assert_allclose(got, got[np.arange(256) ^ 255], rtol=1e-9)
+
+
+# ---------------------------------------------------------------- O8 / O9 / O11
+
+def test_search_exact_dp_square():
+    """beam >= (#boundary keys) x d makes merging exact DP: ground state."""
+    for seed in range(4):
+        inst = I.square(4, 10 + seed, h_sigma=0.3)
+        bf = exact.brute_force(inst, 1.0)
+        res = search.solve(tables.from_ising(inst), search.Params(beta=1.0, chi=8, beam=32))
+        assert res.energies[0] == bf["ground"]
+
+
+def test_search_exact_dp_chimera_strip():
+    inst = I.chimera(1, 4, cols=3)
+    bf = exact.brute_force(inst, 1.0)
+    fg = tables.from_ising(inst)
+    res = search.solve(fg, search.Params(beta=1.0, chi=16, beam=256))
+    assert res.energies.tolist() == [bf["ground"]]  # the empty final key merges all
+    # without merging, the beam keeps max_states states to the end
+    res = search.solve(fg, search.Params(beta=1.0, chi=16, beam=64, merge=False))
+    assert len(res.energies) == 64 and res.energies[0] >= bf["ground"]
+    E = exact.all_energies(inst)
+    cs = exact.cluster_states(inst.n_spins, fg.spins_of_site)
+    code = {tuple(int(c[k]) for c in cs): int(E[k]) for k in np.nonzero(E <= res.energies[-1])[0]}
+    for e, st in zip(res.energies, res.states):
+        assert code[tuple(int(v) for v in st)] == e
+
+
+def test_search_output_order_and_energies():
+    inst = I.chimera(2, 3, couplings="gauss", h_sigma=0.1)
+    fg = tables.from_ising(inst)
+    res = search.solve(fg, search.Params(beta=1.0, chi=16, beam=64))
+    keys = [(int(e), tuple(s)) for e, s in zip(res.energies, res.states)]
+    assert keys == sorted(keys)
+    for e, s in zip(res.energies, res.states):
+        assert e == tables.ising_energy(inst, tables.spins_from_states(fg, s, inst.n_spins))
+
+
+def test_search_chimera_3x3_ground_state():
+    """cfg: 3x3 Chimera +-1, beta 1, chi 16, beam 256 reaches the exact
+    (min-plus transfer) ground energy on these seeds, never below it."""
+    for seed in range(2):
+        inst = I.chimera(3, seed)
+        gs = exact.chimera_strip(inst, 1.0)["ground"]
+        res = search.solve(tables.from_ising(inst), search.Params(beta=1.0, chi=16, beam=256))
+        assert res.energies[0] >= gs
+        assert res.energies[0] == gs
+
+
+def test_gauge_flip_same_spectrum():
+    """s_i -> -s_i on a spin set with the matching sign changes of J and h
+    maps states bijectively and keeps every energy."""
+    inst = I.chimera(2, 7, couplings="gauss", h_sigma=0.1)
+    rng = np.random.default_rng(3)
+    flip = rng.random(inst.n_spins) < 0.5
+    g = I.IsingInstance(**{**inst.__dict__})
+    g.J = np.where(flip[inst.ei] ^ flip[inst.ej], -inst.J, inst.J)
+    g.h = np.where(flip, -inst.h, inst.h)
+    fa, fb = tables.from_ising(inst), tables.from_ising(g)
+    prm = search.Params(beta=1.0, chi=16, beam=64)
+    ra, rb = search.solve(fa, prm), search.solve(fb, prm)
+    np.testing.assert_array_equal(ra.energies, rb.energies)
+    masks = [sum(int(flip[sp]) << k for k, sp in enumerate(spins)) for spins in fa.spins_of_site]
+    mapped = sorted(tuple(int(x) ^ m for x, m in zip(st, masks)) for st in ra.states)
+    assert mapped == sorted(tuple(int(x) for x in st) for st in rb.states)
+
+
+def test_cut_off_prob_drops_improbable_children():
+    inst = I.chimera(2, 5)
+    fg = tables.from_ising(inst)
+    a = search.solve(fg, search.Params(beta=1.0, chi=16, beam=256))
+    b = search.solve(fg, search.Params(beta=1.0, chi=16, beam=256, cut_off_prob=1e-3))
+    assert len(b.states) <= len(a.states)
+    assert all(np.max(b.log_probs) - lp <= -np.log(1e-3) * len(fg.d) for lp in b.log_probs)
