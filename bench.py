@@ -1,0 +1,310 @@
+"""Throughput of the boundary-MPS PEPS search on synthetic Chimera instances.
+
+One step = one full solve (boundary MPSs bottom-up, then the branch-and-bound
+search over every site) of one 16x16 Chimera-like instance: 2048 spins in
+K_{4,4} cells (256-state clusters), J ~ N(0,1), h ~ N(0, 0.1) on the 2^-24
+grid, beta 1, chi 32, beam 1024.  Metric: beam states per second (sum over
+sites of live beam x cluster states, divided by the solve time) and the
+time to solution of the mixed-precision path next to the plain FP64 GPU
+path, whose best energy must be equal.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: independent instances per rank (replicas, weak scaling); rank 0
+prints the JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=1024)
+METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best energy"
+
+
+def make_instance(seed):
+    import instances
+    return instances.chimera(WORKLOAD["L"], seed, couplings=WORKLOAD["couplings"], h_sigma=WORKLOAD["h_sigma"])
+
+
+def config_dict(extra=None):
+    c = {"workload": "chimera16x16_gauss_K44 (2048 spins, d=256), beta=1, chi=32, beam=1024",
+         "L": WORKLOAD["L"], "spins": 8 * WORKLOAD["L"] ** 2, "cluster_states": 256, "beta": WORKLOAD["beta"],
+         "chi": WORKLOAD["chi"], "beam": WORKLOAD["beam"], "couplings": "J~N(0,1), h~N(0,0.1) on 2^-24 grid",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_oracle_sample(seed, max_sites=6):
+    """Oracle on a bounded sample: full boundary MPSs + the first sites of the
+    search (beam states counted on those sites)."""
+    import numpy as np
+
+    from oracle import boundary, peps, search, tables
+    inst = make_instance(seed)
+    t0 = time.perf_counter()
+    fg = tables.from_ising(inst)
+    p = peps.build(fg, WORKLOAD["beta"])
+    bd = boundary.boundary_mpses(p, WORKLOAD["chi"], 0)
+    # search restricted to the first max_sites sites of row 0
+    beam = [search._Partial((), 0, 0.0, np.ones(1))]
+    cols = fg.cols
+    cand = 0
+    B = bd[1]
+    for b in beam:
+        b.R = search.right_envs(p, B, 0, None)
+    for s in range(max_sites):
+        i, j = divmod(s, cols)
+        ks = search.key_sites(fg, s)
+        children = {}
+        for b in beam:
+            left = b.states[s - 1] if j > 0 else 0
+            lc = search.log_conditional(p, B, i, j, b.lenv, b.R, 0, left)
+            for x in range(fg.d[s]):
+                st = b.states + (x,)
+                E = b.E + search.delta_energy(p, i, j, x, 0, left)
+                key = tuple(st[t] for t in ks)
+                cand += 1
+                cur = children.get(key)
+                if cur is None or (E, st) < (cur[1], cur[0]):
+                    children[key] = (st, E, b.logp + float(lc[x]), b)
+        cands = sorted(children.values(), key=lambda c: (-c[2], c[1], c[0]))[:WORKLOAD["beam"]]
+        new = []
+        for st, E, lp, parent in sorted(cands, key=lambda c: c[0]):
+            v = parent.lenv @ B.sites[j][:, p.site(i, j).PD[st[-1]], :]
+            new.append(search._Partial(st, E, lp, v / np.max(np.abs(v)), parent.R))
+        beam = new
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": cand / dt, "unit": "beam states/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 instance: tables + all 15 boundary MPSs (chi=32, full SVD) + the first {max_sites} "
+                      f"search sites ({cand} beam states) in {dt:.1f} s"}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(0, max_sites=2)
+    for k in range(args.steps):
+        vals.append(cpu_oracle_sample(0, max_sites=4))
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "beam states/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(), "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "beam states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2502_02317_gb300 as spg
+
+    stream = torch.cuda.Stream()
+    ctx = spg.Context(local, stream=stream.cuda_stream)
+    inst = make_instance(1000 + rank)
+    prob = spg.spg_problem_ising(ctx, inst)
+    prec = spg.SPG_MIXED if args.precision == "mixed" else spg.SPG_FP64
+    prm = spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        r = spg.spg_solve(ctx, prob, prm)
+        r.get()
+    barrier()
+    times, cands, launches, infos = [], [], [], []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = spg.spg_solve(ctx, prob, prm)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            inf = r.info()
+            infos.append(inf)
+            cands.append(inf["candidates"])
+            launches.append(inf["kernel_launches"])
+            st, E, lp = r.get()
+    barrier()
+    ms = statistics.mean(times)
+    best = int(E[0])
+    tot_cand = sum(cands)
+    tot_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([tot_ms, tot_cand], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        tot_ms, tot_cand = float(mx[0]), float(t[1])
+    value = tot_cand / (tot_ms / 1e3)
+
+    # end to end through the C ABI from host arrays (tables built and copied,
+    # result copied back) for the same steps
+    e2e_times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = spg.spg_problem_ising(ctx, inst)
+        r2 = spg.spg_solve(ctx, p2, prm)
+        st2, E2, lp2 = r2.get()
+        e2e_times.append(time.perf_counter() - t0)
+        r2.close()
+        p2.close()
+    e2e_value = statistics.mean(cands) / statistics.mean(e2e_times)
+    n_sites = inst.grid_rows * inst.grid_cols
+    h2d = n_sites * (8 * 256 + 4 * 256 + 2 * 256 + 8 * 256 * 2 + 4 * 8 + 4 * 17 + 4 * 41) + 4 * n_sites
+    d2h = len(E2) * (2 * n_sites + 8 + 8) + 16
+
+    # plain FP64 GPU path on the same instance: time to solution, best energy
+    fp = None
+    if prec != spg.SPG_FP64:
+        prm64 = spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=spg.SPG_FP64)
+        r = spg.spg_solve(ctx, prob, prm64)
+        r.get()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = spg.spg_solve(ctx, prob, prm64)
+        e1.record(stream)
+        e1.synchronize()
+        st64, E64, lp64 = r.get()
+        fp = {"tts_s": e0.elapsed_time(e1) / 1e3, "best_energy": int(E64[0]) * 2.0 ** -inst.energy_shift,
+              "equal_best_energy": bool(int(E64[0]) == best), "speedup_mixed_vs_fp64": e0.elapsed_time(e1) / ms}
+
+    peaks, src = measured_peaks()
+    inf = infos[-1]
+    line = {"metric": METRIC, "value": value, "unit": "beam states/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == spg.SPG_MIXED else "f64", "data": "synthetic",
+            "config": config_dict({"precision": args.precision, "parallelism": f"replicas x{world}"}),
+            "tts_s": ms / 1e3, "best_energy": best * 2.0 ** -inst.energy_shift,
+            "phase_ms": {"boundary": inf["ms_boundary"], "search": inf["ms_search"]},
+            "fp64_gpu": fp, "gpu_launches": int(sum(launches)),
+            "e2e": {"value": e2e_value, "unit": "beam states/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk.summary(), "peaks_source": src}
+    line["roofline"] = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample(0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -68,7 +68,9 @@ typedef struct {
   int32_t svd_iters;   /* subspace iterations of a large truncation (def. 6) */
   int32_t warm_start;  /* reserved, must be 0                                */
   uint64_t seed;       /* seed of the truncation's start block (default 0)   */
-  int32_t reserved[8]; /* must be 0                                          */
+  int32_t merge;       /* 1: merge branches equal on the boundary of the
+                          explored region (merge_branches; default 1)        */
+  int32_t reserved[7]; /* must be 0                                          */
 } spg_params;
 
 /* Per-result diagnostics. */
@@ -81,6 +83,7 @@ typedef struct {
   double ms_search;        /* device time of the search phase                */
   double candidates;       /* sum over sites of (live beam x states)         */
   double boundary_lognorm; /* log-norm of the last boundary MPS built        */
+  int64_t kernel_launches; /* CUDA kernels this solve enqueued              */
 } spg_info;
 
 /* Library version, major*10000 + minor*100 + patch. */

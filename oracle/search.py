@@ -21,7 +21,9 @@ Readings taken here:
   R_L = 1, the weight of state x is
       q(x) = w(x) b_left[h, P_L x] b_up[u_j, P_U x]
              sum_{a,a'} Lenv[a] B_{i+1}[j][a, P_D x, a'] R_{j+1}[a', P_R x]
-  and log p(x | prefix) = log q(x) - log sum_x q(x), in FP64;
+  and log p(x | prefix) = log q(x) - log sum_x q(x), in FP64.  A truncated
+  boundary MPS can make q(x) slightly negative; such a weight counts as 0
+  (log p = -inf);
 * a child's log-probability is its parent's plus the log-conditional; its
   partial energy is the parent's plus E_j(x) and the pairwise terms with
   already fixed neighbours (exact integers);
@@ -112,6 +114,7 @@ def log_conditional(p, B, i, j, lenv, R, upper_state_j, left_state):
     for x in range(st.d):
         q[x] = (st.w[x] * st.b_left[h, st.PL[x]] * st.b_up[uj, st.PU[x]]
                 * float(lenv @ A[:, st.PD[x], :] @ R[j + 1][:, st.PR[x]]))
+    q = np.maximum(q, 0.0)
     with np.errstate(divide="ignore"):
         return np.log(q) - np.log(np.sum(q))
 

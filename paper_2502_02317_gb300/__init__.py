@@ -1,0 +1,13 @@
+"""GB300-native boundary-MPS PEPS contraction and branch-and-bound search for
+clustered Ising / Potts models (arXiv:2502.02317, SpinGlassPEPS.jl).
+
+The work runs in ``libspg`` (CUDA, sm_103a) behind the C ABI of
+``include/spg.h``; this package is its ctypes binding.
+"""
+from ._binding import (SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, Context, Problem, Result, SpgError,
+                       lib, params, spg_debug_marginals, spg_log_partition, spg_problem_ising,
+                       spg_problem_potts, spg_solve)
+
+__all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
+           "spg_problem_potts", "spg_solve", "spg_debug_marginals", "spg_log_partition",
+           "SPG_FP64", "SPG_MIXED", "SPG_SQUARE", "SPG_KING"]

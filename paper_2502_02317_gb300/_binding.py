@@ -1,0 +1,230 @@
+"""ctypes binding of libspg (include/spg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The module fails at import when the library cannot be loaded; there is no
+other implementation behind it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPG_OK = 0
+SPG_EINVAL = -1
+SPG_EINEXACT = -2
+SPG_ENOMEM = -3
+SPG_ECUDA = -4
+SPG_ETIMEOUT = -5
+SPG_ENUMERIC = -6
+SPG_EUNSUPPORTED = -7
+SPG_SQUARE = 0
+SPG_KING = 1
+SPG_FP64 = 0
+SPG_MIXED = 1
+
+_ERRNAMES = {v: k for k, v in dict(SPG_EINVAL=-1, SPG_EINEXACT=-2, SPG_ENOMEM=-3, SPG_ECUDA=-4,
+                                   SPG_ETIMEOUT=-5, SPG_ENUMERIC=-6, SPG_EUNSUPPORTED=-7).items()}
+
+
+class spg_params(C.Structure):
+    _fields_ = [("beta", C.c_double), ("chi", C.c_int32), ("num_sweeps", C.c_int32),
+                ("beam", C.c_int32), ("precision", C.c_int32), ("cut_off_prob", C.c_double),
+                ("svd_iters", C.c_int32), ("warm_start", C.c_int32), ("seed", C.c_uint64),
+                ("merge", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class spg_info(C.Structure):
+    _fields_ = [("n_states", C.c_int32), ("near_ties", C.c_int32), ("degenerate_cuts", C.c_int32),
+                ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
+                ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+def _load():
+    path = _build.LIB
+    if _build.needs_build():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libspg.so is not built (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P, I32, I64, D, U16 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint16
+    pI32, pI64, pD, pU16 = C.POINTER(I32), C.POINTER(I64), C.POINTER(D), C.POINTER(U16)
+    sig = {
+        "spg_version": (C.c_int, []),
+        "spg_params_default": (C.c_int, [C.POINTER(spg_params)]),
+        "spg_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
+        "spg_destroy": (None, [P]),
+        "spg_last_error": (C.c_char_p, [P]),
+        "spg_problem_ising": (C.c_int, [P, I32, I32, pI32, pI32, pD, pD, pI32, I32, I32, pI32, pI32, I32, I32,
+                                        C.POINTER(P)]),
+        "spg_problem_potts": (C.c_int, [P, I32, I32, pI32, pI64, I32, pI32, pI32, pI64, I32, I32, C.POINTER(P)]),
+        "spg_problem_destroy": (None, [P]),
+        "spg_problem_shape": (C.c_int, [P, pI32, pI32, pI32]),
+        "spg_solve": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P)]),
+        "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD]),
+        "spg_result_info": (C.c_int, [P, C.POINTER(spg_info)]),
+        "spg_result_destroy": (None, [P]),
+        "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
+        "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class SpgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def params(**kw) -> spg_params:
+    p = spg_params()
+    lib.spg_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """spg_create / spg_destroy.  ``stream`` is a cudaStream_t as an int
+    (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        rc = lib.spg_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        if rc != SPG_OK:
+            raise SpgError(rc, "spg_create failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != SPG_OK:
+            raise SpgError(rc, lib.spg_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib.spg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        r, c = C.c_int32(), C.c_int32()
+        ctx.check(lib.spg_problem_shape(h, C.byref(r), C.byref(c), None))
+        self.rows, self.cols = r.value, c.value
+        d = np.zeros(self.rows * self.cols, np.int32)
+        ctx.check(lib.spg_problem_shape(h, None, None, _ptr(d, C.c_int32)))
+        self.d = d
+
+    def close(self):
+        if self.h:
+            lib.spg_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spg_problem_ising(ctx: Context, inst) -> Problem:
+    ei = np.ascontiguousarray(inst.ei, np.int32)
+    ej = np.ascontiguousarray(inst.ej, np.int32)
+    J = np.ascontiguousarray(inst.J, np.float64)
+    h = np.ascontiguousarray(inst.h, np.float64)
+    cos = np.ascontiguousarray(inst.cluster_of_spin, np.int32)
+    cr = np.ascontiguousarray(inst.cluster_row, np.int32)
+    cc = np.ascontiguousarray(inst.cluster_col, np.int32)
+    out = C.c_void_p()
+    ctx.check(lib.spg_problem_ising(ctx.h, inst.n_spins, len(ei), _ptr(ei, C.c_int32), _ptr(ej, C.c_int32),
+                                    _ptr(J, C.c_double), _ptr(h, C.c_double), _ptr(cos, C.c_int32),
+                                    inst.grid_rows, inst.grid_cols, _ptr(cr, C.c_int32), _ptr(cc, C.c_int32),
+                                    inst.energy_shift, inst.node_type, C.byref(out)))
+    return Problem(ctx, out)
+
+
+def spg_problem_potts(ctx: Context, inst) -> Problem:
+    d = np.ascontiguousarray(inst.d, np.int32)
+    le = np.ascontiguousarray(inst.local_E, np.int64)
+    em = np.ascontiguousarray(inst.em, np.int32)
+    en = np.ascontiguousarray(inst.en, np.int32)
+    pe = np.ascontiguousarray(inst.pair_E, np.int64)
+    out = C.c_void_p()
+    ctx.check(lib.spg_problem_potts(ctx.h, inst.grid_rows, inst.grid_cols, _ptr(d, C.c_int32), _ptr(le, C.c_int64),
+                                    len(em), _ptr(em, C.c_int32), _ptr(en, C.c_int32), _ptr(pe, C.c_int64),
+                                    inst.energy_shift, inst.node_type, C.byref(out)))
+    return Problem(ctx, out)
+
+
+class Result:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def get(self):
+        """(states [n, N] uint16, energies int64 [n], log_probs [n])"""
+        n, N = C.c_int32(), C.c_int32()
+        self.ctx.check(lib.spg_result_get(self.h, C.byref(n), C.byref(N), None, None, None, None))
+        st = np.zeros((n.value, N.value), np.uint16)
+        E = np.zeros(n.value, np.int64)
+        lp = np.zeros(n.value, np.float64)
+        self.ctx.check(lib.spg_result_get(self.h, None, None, _ptr(st, C.c_uint16), _ptr(E, C.c_int64), None,
+                                          _ptr(lp, C.c_double)))
+        return st, E, lp
+
+    def info(self) -> dict:
+        inf = spg_info()
+        self.ctx.check(lib.spg_result_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in spg_info._fields_}
+
+    def close(self):
+        if self.h:
+            lib.spg_result_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spg_solve(ctx: Context, prob: Problem, prm: spg_params) -> Result:
+    out = C.c_void_p()
+    ctx.check(lib.spg_solve(ctx.h, prob.h, C.byref(prm), C.byref(out)))
+    return Result(ctx, out)
+
+
+def spg_debug_marginals(ctx: Context, prob: Problem, prm: spg_params, site: int, prefixes) -> np.ndarray:
+    pre = np.ascontiguousarray(np.asarray(prefixes, dtype=np.uint16).reshape(len(prefixes), site))
+    d = int(prob.d[site])
+    out = np.zeros((len(prefixes), d), np.float64)
+    ctx.check(lib.spg_debug_marginals(ctx.h, prob.h, C.byref(prm), site, len(prefixes),
+                                      _ptr(pre, C.c_uint16) if site > 0 else None, _ptr(out, C.c_double)))
+    return out
+
+
+def spg_log_partition(ctx: Context, prob: Problem, prm: spg_params) -> float:
+    v = C.c_double()
+    ctx.check(lib.spg_log_partition(ctx.h, prob.h, C.byref(prm), C.byref(v)))
+    return v.value

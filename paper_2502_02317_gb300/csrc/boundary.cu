@@ -1,0 +1,759 @@
+// Boundary-MPS kernels: Boltzmann pieces of the PEPS (S2), the left-canonical
+// QR sweep, the MPO-MPS zipper matrix and its truncated SVD (S3).
+//
+// Paper: Sec. 2 and Fig. 1(c)-(d) (PEPS of the Boltzmann distribution,
+// approximate contraction with boundary MPSs), Sec. 3.1 (MpsParameters
+// bond_dim; MpsContractor(SVDTruncate, ...)).
+#include <cfloat>
+#include <cmath>
+
+#include "spg_internal.h"
+
+namespace spg {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one value; `red` holds >= 32 T.  All threads get the sum.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? red[lane] : T(0);
+  t = warp_sum(t);
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T dexp(double x) {
+  return (T)exp(x);
+}
+
+// ---------------------------------------------------------------- weights (S2)
+// One block per site: w = exp(-beta u (E - min E)), bL/bU from RL/RU alike.
+template <typename T>
+__global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u) {
+  const int s = blockIdx.x;
+  const int d = tb.d[s];
+  __shared__ long long mn[3];
+  if (threadIdx.x == 0) {
+    long long a = LLONG_MAX, b = LLONG_MAX, c = LLONG_MAX;
+    for (int x = 0; x < d; ++x) a = min(a, (long long)tb.E[(size_t)s * tb.dmax + x]);
+    const int* dm = tb.dims + s * 8;
+    for (int i = 0; i < dm[0]; ++i)
+      for (int j = 0; j < dm[4]; ++j) b = min(b, (long long)tb.RL[(size_t)s * 256 + i * 16 + j]);
+    for (int i = 0; i < dm[2]; ++i)
+      for (int j = 0; j < dm[5]; ++j) c = min(c, (long long)tb.RU[(size_t)s * 256 + i * 16 + j]);
+    mn[0] = a;
+    mn[1] = b;
+    mn[2] = c;
+  }
+  __syncthreads();
+  const int* dm = tb.dims + s * 8;
+  for (int x = threadIdx.x; x < tb.dmax; x += blockDim.x) {
+    T v = T(0);
+    if (x < d) v = dexp<T>(-beta_u * (double)(tb.E[(size_t)s * tb.dmax + x] - mn[0]));
+    wt.w[(size_t)s * tb.dmax + x] = v;
+  }
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    const int i = e >> 4, j = e & 15;
+    T vl = T(0), vu = T(0);
+    if (i < dm[0] && j < dm[4]) vl = dexp<T>(-beta_u * (double)(tb.RL[(size_t)s * 256 + e] - mn[1]));
+    if (i < dm[2] && j < dm[5]) vu = dexp<T>(-beta_u * (double)(tb.RU[(size_t)s * 256 + e] - mn[2]));
+    wt.bL[(size_t)s * 256 + e] = vl;
+    wt.bU[(size_t)s * 256 + e] = vu;
+  }
+}
+
+// ---------------------------------------------------------------- CGS2 QR
+// In-place classical Gram-Schmidt with one re-orthogonalisation ("twice is
+// enough") of X [rows x ncols] (row-major, leading dim ld).  Q overwrites X;
+// R (ncols x ncols, upper, non-negative diagonal) goes to Rout if non-null.
+// A column whose remainder falls below rel_tol of its original norm is set
+// to zero with R_kk = 0 (numerically dependent; the product Q R keeps the
+// matrix to that tolerance).  One block, blockDim.x a multiple of 32.
+template <typename T>
+__device__ void cgs2_block(T* X, int rows, int ncols, int ld, T* Rout, T* sh_r /* >= ncols */,
+                           T* red, T rel_tol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 0; k < ncols; ++k) {
+    // original norm
+    T part = T(0);
+    for (int i = tid; i < rows; i += nt) {
+      T v = X[(size_t)i * ld + k];
+      part += v * v;
+    }
+    const T n0 = sqrt(block_sum(part, red));
+    for (int i = tid; i < ncols; i += nt) sh_r[i] = T(0);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      // r_c = X[:, c] . X[:, k] for c < k: one warp per c
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int c = wid; c < k; c += nw) {
+        T acc = T(0);
+        for (int i = lane; i < rows; i += 32) acc += X[(size_t)i * ld + c] * X[(size_t)i * ld + k];
+        acc = warp_sum(acc);
+        if (lane == 0) red[32 + c] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < rows; i += nt) {
+        T v = X[(size_t)i * ld + k];
+        for (int c = 0; c < k; ++c) v -= red[32 + c] * X[(size_t)i * ld + c];
+        X[(size_t)i * ld + k] = v;
+      }
+      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
+      __syncthreads();
+    }
+    part = T(0);
+    for (int i = tid; i < rows; i += nt) {
+      T v = X[(size_t)i * ld + k];
+      part += v * v;
+    }
+    const T nk = sqrt(block_sum(part, red));
+    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+    const T inv = dep ? T(0) : T(1) / nk;
+    for (int i = tid; i < rows; i += nt) X[(size_t)i * ld + k] *= inv;
+    if (Rout) {
+      for (int c = tid; c < ncols; c += nt)
+        Rout[(size_t)c * ncols + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__host__ __device__ constexpr T qr_tol() {
+  return sizeof(T) == 8 ? T(1e-13) : T(1e-5);
+}
+
+// CGS2 on the ROWS of X (nvec vectors of length len, row stride ld), each
+// vector contiguous so every access is coalesced; the vectors are staged in
+// shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_block:
+// x_k = sum_{c <= k} R[c][k] q_c.
+template <typename T>
+__global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);  // 32 + SMAX
+  T* sh_r = red + 32 + SMAX;                // SMAX
+  T* V = use_smem ? sh_r + SMAX : X;
+  const int vld = use_smem ? len : ld;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const T rel_tol = qr_tol<T>();
+  if (use_smem)
+    for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
+  __syncthreads();
+  for (int k = 0; k < nvec; ++k) {
+    T* xk = V + (size_t)k * vld;
+    T part = T(0);
+    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+    const T n0 = sqrt(block_sum(part, red));
+    for (int c = tid; c < nvec; c += nt) sh_r[c] = T(0);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = wid; c < k; c += nw) {
+        const T* xc = V + (size_t)c * vld;
+        T acc = T(0);
+        for (int i = lane; i < len; i += 32) acc += xc[i] * xk[i];
+        acc = warp_sum(acc);
+        if (lane == 0) red[32 + c] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < len; i += nt) {
+        T v = xk[i];
+        for (int c = 0; c < k; ++c) v -= red[32 + c] * V[(size_t)c * vld + i];
+        xk[i] = v;
+      }
+      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
+      __syncthreads();
+    }
+    part = T(0);
+    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+    const T nk = sqrt(block_sum(part, red));
+    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+    const T inv = dep ? T(0) : T(1) / nk;
+    for (int i = tid; i < len; i += nt) xk[i] *= inv;
+    if (Rout)
+      for (int c = tid; c < nvec; c += nt)
+        Rout[(size_t)c * nvec + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
+    __syncthreads();
+  }
+  if (use_smem)
+    for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
+}
+
+// ---------------------------------------------------------------- left-canonical sweep
+// Sites of row r: [p][chiL][chiR] = matrix (p*chiL) x chiR.  For j < cols-1:
+// QR of site j, then site j+1 <- R site j+1.  The last site is normalised.
+template <typename T>
+__global__ void k_left_canonical(DevMPS<T> mps, int r, int cols) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);  // 32 + SMAX
+  T* sh_r = red + 32 + SMAX;                // SMAX
+  T* R = sh_r + SMAX;                       // MAXCHI * MAXCHI
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < cols - 1; ++j) {
+    const int* dA = mps.dimA + (r * cols + j) * 3;
+    const int p = dA[0], chiL = dA[1], chiR = dA[2];
+    T* A = mps.A + (size_t)(r * cols + j) * mps.site_stride;
+    cgs2_block(A, p * chiL, chiR, chiR, R, sh_r, red, qr_tol<T>());
+    __syncthreads();
+    const int* dB = mps.dimA + (r * cols + j + 1) * 3;
+    const int p2 = dB[0], chiL2 = dB[1], chiR2 = dB[2];  // chiL2 == chiR
+    T* Bn = mps.A + (size_t)(r * cols + j + 1) * mps.site_stride;
+    // new[s][a][b] = sum_{g >= a} R[a][g] old[s][g][b], in place, a ascending
+    for (int c = tid; c < p2 * chiR2; c += nt) {
+      const int s = c / chiR2, b = c % chiR2;
+      T* col = Bn + (size_t)s * chiL2 * chiR2 + b;
+      for (int a = 0; a < chiL2; ++a) {
+        T v = T(0);
+        for (int g = a; g < chiL2; ++g) v += R[a * chiL2 + g] * col[(size_t)g * chiR2];
+        col[(size_t)a * chiR2] = v;
+      }
+    }
+    __syncthreads();
+  }
+  const int* dA = mps.dimA + (r * cols + cols - 1) * 3;
+  const int n = dA[0] * dA[1] * dA[2];
+  T* A = mps.A + (size_t)(r * cols + cols - 1) * mps.site_stride;
+  T part = T(0);
+  for (int i = tid; i < n; i += nt) part += A[i] * A[i];
+  const T nrm = sqrt(block_sum(part, red));
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+  for (int i = tid; i < n; i += nt) A[i] *= inv;
+  if (tid == 0) mps.lognorm[r] += log((double)nrm);
+}
+
+// ---------------------------------------------------------------- zipper matrix
+// T1[a][s][rr][k] = sum_a' B[s][a][a'] C[rr][a'][k]
+template <typename T>
+__global__ void k_zip_T1(const T* __restrict__ B, int chiL, int p, int chiR, const T* __restrict__ C,
+                         int DR, int K, T* __restrict__ T1) {
+  const size_t total = (size_t)chiL * p * DR * K;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = e % K;
+    size_t t = e / K;
+    const int rr = t % DR;
+    t /= DR;
+    const int s = t % p;
+    const int a = (int)(t / p);
+    const T* b = B + ((size_t)s * chiL + a) * chiR;
+    const T* c = C + (size_t)rr * chiR * K + k;
+    T acc = T(0);
+    for (int q = 0; q < chiR; ++q) acc += b[q] * c[(size_t)q * K];
+    T1[e] = acc;
+  }
+}
+
+// M[(l*chiL + a)][(u*K + k)] = sum_h bL[l][h] sum_{x: PL x = h} bU[u][PU x] w(x) T1[a][PD x][PR x][k]
+// One block per (a, chunk of k).
+template <typename T>
+__global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __restrict__ T1, int chiL,
+                        int p, int DR, int K, int DL, int DU, int kchunk, T* __restrict__ M) {
+  __shared__ T sw[MAXS];
+  __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
+  __shared__ int16_t sx[MAXS];
+  __shared__ int soff[MAXP + 1];
+  __shared__ T sbL[256], sbU[256];
+  __shared__ T sT[MAXP * MAXP];
+  __shared__ T sY[MAXP * MAXP];
+  const int a = blockIdx.x;
+  const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  const int d = tb.d[site];
+  const int NL = tb.dims[site * 8 + 4];
+  const int tid = threadIdx.x;
+  for (int x = tid; x < d; x += blockDim.x) {
+    sw[x] = wt.w[(size_t)site * tb.dmax + x];
+    sPU[x] = tb.PU[(size_t)site * tb.dmax + x];
+    sPD[x] = tb.PD[(size_t)site * tb.dmax + x];
+    sPR[x] = tb.PR[(size_t)site * tb.dmax + x];
+    sx[x] = tb.xsL[(size_t)site * tb.dmax + x];
+  }
+  for (int e = tid; e < 256; e += blockDim.x) {
+    sbL[e] = wt.bL[(size_t)site * 256 + e];
+    sbU[e] = wt.bU[(size_t)site * 256 + e];
+  }
+  for (int e = tid; e <= MAXP; e += blockDim.x) soff[e] = tb.xoffL[site * (MAXP + 1) + e];
+  __syncthreads();
+  const size_t ldM = (size_t)DU * K;
+  for (int k = k0; k < k1; ++k) {
+    for (int e = tid; e < p * DR; e += blockDim.x) {
+      const int s = e / DR, rr = e % DR;
+      sT[s * MAXP + rr] = T1[(((size_t)a * p + s) * DR + rr) * K + k];
+    }
+    __syncthreads();
+    for (int e = tid; e < DU * NL; e += blockDim.x) {
+      const int u = e / NL, h = e % NL;
+      T acc = T(0);
+      for (int q = soff[h]; q < soff[h + 1]; ++q) {
+        const int x = sx[q];
+        acc += sbU[u * 16 + sPU[x]] * sw[x] * sT[sPD[x] * MAXP + sPR[x]];
+      }
+      sY[u * MAXP + h] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < DL * DU; e += blockDim.x) {
+      const int l = e / DU, u = e % DU;
+      T acc = T(0);
+      for (int h = 0; h < NL; ++h) acc += sbL[l * 16 + h] * sY[u * MAXP + h];
+      M[((size_t)l * chiL + a) * ldM + (size_t)u * K + k] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+// C[m x n] = op(A) op(B), row-major; op(A) = A (m x k, lda) or A^T (A stored
+// k x m); op(B) = B (k x n, ldb) or B^T (B stored n x k).  32x32 tile, 256
+// threads, 2x2 outputs per thread.
+template <typename T, bool TA, bool TB>
+__global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                       int ldb, T* __restrict__ C, int ldc) {
+  constexpr int BM = 32, BN = 32, BK = 32;
+  __shared__ T sA[BK][BM + 1];
+  __shared__ T sB[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  T acc[2][2] = {};
+  for (int kk = 0; kk < k; kk += BK) {
+    for (int e = threadIdx.x; e < BK * BM; e += 256) {
+      int kq, i;
+      if (TA) {  // contiguous along m
+        kq = e / BM;
+        i = e % BM;
+      } else {  // contiguous along k
+        i = e / BK;
+        kq = e % BK;
+      }
+      const int gi = row0 + i, gk = kk + kq;
+      T v = T(0);
+      if (gi < m && gk < k) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+      sA[kq][i] = v;
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      int kq, j;
+      if (TB) {  // contiguous along k
+        j = e / BK;
+        kq = e % BK;
+      } else {  // contiguous along n
+        kq = e / BN;
+        j = e % BN;
+      }
+      const int gj = col0 + j, gk = kk + kq;
+      T v = T(0);
+      if (gj < n && gk < k) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+      sB[kq][j] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kq = 0; kq < BK; ++kq) {
+      const T a0 = sA[kq][ty * 2], a1 = sA[kq][ty * 2 + 1];
+      const T b0 = sB[kq][tx * 2], b1 = sB[kq][tx * 2 + 1];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int gi = row0 + ty * 2 + i;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gj = col0 + tx * 2 + j;
+      if (gj < n) C[(size_t)gi * ldc + gj] = acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- one-sided Jacobi
+// On the s x s matrix R (row-major in global), accumulating V (s x s).
+// Columns are rotated pairwise in round-robin order until every pair is
+// orthogonal to tol; then columns are sorted by norm (descending) and
+// written as RV (= U Sigma) and V, row-major s x s, plus sigma[s].
+// s1_dev = sigma[0]; flag_dev |= degenerate cut at `keep`.
+template <typename T>
+__global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout, T* __restrict__ Vout,
+                         T* __restrict__ sig_out, int keep, double* s1_dev, int* flag_dev,
+                         T* __restrict__ gbuf, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);  // 64
+  T* sig = red + 64;                        // SMAX
+  int* rank = reinterpret_cast<int*>(sig + SMAX);  // SMAX
+  T* buf = use_smem ? reinterpret_cast<T*>(rank + SMAX) : gbuf;
+  // column-major: Rc[c*s + i], Vc[c*s + i]
+  T* Rc = buf;
+  T* Vc = buf + (size_t)s * s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < s * s; e += nt) {
+    const int i = e / s, c = e % s;
+    Rc[(size_t)c * s + i] = Rin[e];
+    Vc[(size_t)c * s + i] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int se = s + (s & 1);
+  const T tol = sizeof(T) == 8 ? T(1e-15) : T(2e-7);
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  __shared__ int s_conv;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) s_conv = 1;
+    __syncthreads();
+    for (int r = 0; r < se - 1; ++r) {
+      for (int pk = wid; pk < se / 2; pk += nw) {
+        int i = pk == 0 ? 0 : ((pk + r - 1) % (se - 1)) + 1;
+        int j = ((se - 1 - pk + r - 1) % (se - 1)) + 1;
+        if (i >= s || j >= s) continue;
+        if (i > j) {
+          int t = i;
+          i = j;
+          j = t;
+        }
+        T* ci = Rc + (size_t)i * s;
+        T* cj = Rc + (size_t)j * s;
+        T al = T(0), be = T(0), ga = T(0);
+        for (int q = lane; q < s; q += 32) {
+          const T x = ci[q], y = cj[q];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al == T(0) || be == T(0)) continue;
+        if (fabs((double)ga) <= (double)tol * sqrt((double)al * (double)be)) continue;
+        if (lane == 0) s_conv = 0;
+        const T zeta = (be - al) / (T(2) * ga);
+        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + t * t);
+        const T sn = c * t;
+        T* vi = Vc + (size_t)i * s;
+        T* vj = Vc + (size_t)j * s;
+        for (int q = lane; q < s; q += 32) {
+          const T x = ci[q], y = cj[q];
+          ci[q] = c * x - sn * y;
+          cj[q] = sn * x + c * y;
+          const T u = vi[q], v = vj[q];
+          vi[q] = c * u - sn * v;
+          vj[q] = sn * u + c * v;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_conv) break;
+    __syncthreads();
+  }
+  // singular values and descending order (ties by index)
+  for (int c = wid; c < s; c += nw) {
+    T a = T(0);
+    for (int q = lane; q < s; q += 32) a += Rc[(size_t)c * s + q] * Rc[(size_t)c * s + q];
+    a = warp_sum(a);
+    if (lane == 0) sig[c] = sqrt(a);
+  }
+  __syncthreads();
+  for (int c = tid; c < s; c += nt) {
+    int rk = 0;
+    for (int o = 0; o < s; ++o) rk += (sig[o] > sig[c]) || (sig[o] == sig[c] && o < c);
+    rank[c] = rk;
+  }
+  __syncthreads();
+  for (int e = tid; e < s * s; e += nt) {
+    const int c = e / s, i = e % s;
+    RVout[(size_t)i * s + rank[c]] = Rc[e];
+    Vout[(size_t)i * s + rank[c]] = Vc[e];
+  }
+  for (int c = tid; c < s; c += nt) sig_out[rank[c]] = sig[c];
+  __syncthreads();
+  if (tid == 0) {
+    T s1 = T(0);
+    for (int c = 0; c < s; ++c)
+      if (rank[c] == 0) s1 = sig[c];
+    *s1_dev = (double)s1;
+    if (keep < s && flag_dev) {
+      T sk = T(0), sk1 = T(0);
+      for (int c = 0; c < s; ++c) {
+        if (rank[c] == keep - 1) sk = sig[c];
+        if (rank[c] == keep) sk1 = sig[c];
+      }
+      if ((double)(sk - sk1) <= 1e-12 * (double)s1) atomicAdd(flag_dev, 1);
+    }
+  }
+}
+
+// deterministic pseudo-random block in (-1, 1): splitmix64 of (seed, index)
+__device__ __forceinline__ double hash_unit(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + 0x9e3779b97f4a7c15ull * (i + 1);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z = z ^ (z >> 31);
+  return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// Zt [s x n]: identity rows (direct case, s == n) or the pseudo-random block.
+template <typename T>
+__global__ void k_fill_start(T* Zt, int n, int s, uint64_t seed, int identity) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * s; e += gridDim.x * blockDim.x) {
+    const int c = e / n, i = e % n;
+    Zt[e] = identity ? (i == c ? T(1) : T(0)) : (T)hash_unit(seed, (uint64_t)e);
+  }
+}
+
+template <typename T>
+__global__ void k_set_strided(T* base, size_t stride, int count, T v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) base[e * stride] = v;
+}
+
+// site[u][kp][k] = V[(u*K + k)][kp];  carry[l][a][kp] = US[(l*chiL + a)][kp] / s1
+template <typename T>
+__global__ void k_zip_write(const T* __restrict__ V, const T* __restrict__ US, int DL, int chiL, int DU,
+                            int K, int keep, T* __restrict__ site, T* __restrict__ carry, const double* s1,
+                            double* lognorm_r) {
+  const double sv = *s1;
+  const T inv = sv > 0 ? (T)(1.0 / sv) : T(0);
+  const int nsite = DU * keep * K, ncar = DL * chiL * keep;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nsite + ncar; e += gridDim.x * blockDim.x) {
+    if (e < nsite) {
+      const int k = e % K, kp = (e / K) % keep, u = e / (K * keep);
+      site[e] = V[(size_t)(u * K + k) * keep + kp];
+    } else {
+      const int f = e - nsite;
+      const int kp = f % keep, la = f / keep;
+      carry[f] = US[(size_t)la * keep + kp] * inv;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *lognorm_r += log(sv);
+}
+
+template <typename T>
+__global__ void k_zip_site0(const T* __restrict__ M, int n, T* __restrict__ site, double* lognorm_r) {
+  __shared__ T red[64];
+  T part = T(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) part += M[i] * M[i];
+  const T nrm = sqrt(block_sum(part, red));
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) site[i] = M[i] * inv;
+  if (threadIdx.x == 0) *lognorm_r += log((double)nrm);
+}
+
+template <typename T>
+__global__ void k_mps_value(DevMPS<T> mps, int r, int cols, double* out) {
+  __shared__ T v[MAXCHI], nv[MAXCHI];
+  const int tid = threadIdx.x;
+  if (tid == 0) v[0] = T(1);
+  __syncthreads();
+  int chi = 1;
+  for (int j = 0; j < cols; ++j) {
+    const int* dA = mps.dimA + (r * cols + j) * 3;
+    const int chiL = dA[1], chiR = dA[2];
+    const T* A = mps.A + (size_t)(r * cols + j) * mps.site_stride;  // p == 1
+    for (int b = tid; b < chiR; b += blockDim.x) {
+      T acc = T(0);
+      for (int a = 0; a < chiL && a < chi; ++a) acc += v[a] * A[(size_t)a * chiR + b];
+      nv[b] = acc;
+    }
+    __syncthreads();
+    for (int b = tid; b < chiR; b += blockDim.x) v[b] = nv[b];
+    chi = chiR;
+    __syncthreads();
+  }
+  if (tid == 0) *out = (double)v[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_weights(const DevTables& tb, DevWeights<T> wt, double beta_u, cudaStream_t st) {
+  count_launches(1);
+  k_weights<T><<<tb.n, 256, 0, st>>>(tb, wt, beta_u);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static size_t lc_smem() {
+  return sizeof(T) * (32 + SMAX + SMAX + MAXCHI * MAXCHI);
+}
+
+template <typename T>
+cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T*, cudaStream_t st) {
+  const size_t sm = lc_smem<T>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  count_launches(1);
+  k_left_canonical<T><<<1, 512, sm, st>>>(mps, r, cols);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B, int chiL, int p, int chiR,
+                              const T* C, int DR, int K, int site, int DL, int DU, T* T1, T* M,
+                              cudaStream_t st) {
+  const size_t total = (size_t)chiL * p * DR * K;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  count_launches(1);
+  k_zip_T1<T><<<blocks, 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1);
+  const int kchunk = K >= 8 ? 4 : 1;
+  dim3 grid(chiL, (K + kchunk - 1) / kchunk);
+  count_launches(1);
+  k_zip_M<T><<<grid, 256, 0, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gemm(bool transA, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
+                 cudaStream_t st) {
+  return gemm2<T>(transA, false, m, n, k, A, lda, B, ldb, C, ldc, st);
+}
+
+template <typename T>
+cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
+                  int ldc, cudaStream_t st) {
+  dim3 grid((n + 31) / 32, (m + 31) / 32);
+  count_launches(1);
+  if (transA && transB)
+    k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  else if (transA)
+    k_gemm<T, true, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  else if (transB)
+    k_gemm<T, false, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  else
+    k_gemm<T, false, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st) {
+  count_launches(1);
+  k_set_strided<T><<<(count + 255) / 256, 256, 0, st>>>(base, stride, count, v);
+  return cudaGetLastError();
+}
+
+static int block_cols(int n, int keep) {
+  if (n <= SMAX) return n;
+  int s = std::max(2 * keep, keep + 8);
+  return std::min(std::min(s, n), SMAX);
+}
+
+size_t truncated_svd_work(int m, int n, int) {
+  const size_t s = (size_t)SMAX;  // upper bound of block_cols for any call
+  // Z (n s), Y (m s), R (s s), RV (s s), VJ (s s), sig (s), jacobi global buf (2 s s)
+  return s * n + s * m + 5 * s * s + s + 64;
+}
+
+template <typename T>
+static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
+  const size_t base = sizeof(T) * (32 + 2 * SMAX);
+  const size_t full = base + sizeof(T) * (size_t)nvec * len;
+  const int use_smem = full <= 200 * 1024 ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+    attr = true;
+  }
+  count_launches(1);
+  k_cgs2_rows<T><<<1, 1024, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
+}
+
+// Work layout: Zt [s x n], Yt [s x m] (rows = the block's column vectors),
+// R, RV, VJ [s x s], sig [s], Jacobi spill buffer [2 s s].
+template <typename T>
+cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US, T* work,
+                          size_t, double* s1_dev, int* flag_dev, cudaStream_t st) {
+  const int s = block_cols(n, keep);
+  T* Zt = work;
+  T* Yt = Zt + (size_t)n * s;
+  T* R = Yt + (size_t)m * s;
+  T* RV = R + (size_t)s * s;
+  T* VJ = RV + (size_t)s * s;
+  T* sig = VJ + (size_t)s * s;
+  T* jbuf = sig + s + 64;
+  const bool direct = n <= SMAX;
+  count_launches(1);
+  k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
+  if (!direct) {
+    cgs2_rows(Zt, s, n, (T*)nullptr, st);
+    for (int it = 0; it < iters; ++it) {
+      gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);  // Y = M Z
+      cgs2_rows(Yt, s, m, (T*)nullptr, st);
+      gemm2<T>(false, false, s, n, m, Yt, m, M, n, Zt, n, st);  // Z = M^T Y
+      cgs2_rows(Zt, s, n, (T*)nullptr, st);
+    }
+  }
+  // P = M Z = Q R (rows of Yt become the columns of Q); R = U_R Sigma V_J^T
+  gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);
+  cgs2_rows(Yt, s, m, R, st);
+  const size_t jsm_base = sizeof(T) * (64 + SMAX) + sizeof(int) * SMAX;
+  const size_t jsm_full = jsm_base + sizeof(T) * 2 * (size_t)s * s;
+  const int use_smem = jsm_full <= 200 * 1024 ? 1 : 0;
+  const size_t jsm = use_smem ? jsm_full : jsm_base;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+    attr = true;
+  }
+  count_launches(1);
+  k_jacobi<T><<<1, 1024, jsm, st>>>(R, s, RV, VJ, sig, keep, s1_dev, flag_dev, jbuf, use_smem);
+  // V = Z VJ[:, :keep] = Zt^T VJ,  US = Q RV[:, :keep] = Yt^T RV
+  gemm2<T>(true, false, n, keep, s, Zt, n, VJ, s, V, keep, st);
+  gemm2<T>(true, false, m, keep, s, Yt, m, RV, s, US, keep, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, int K, int keep, T* site_out,
+                             T* carry_out, const double* s1_dev, double* lognorm_r, cudaStream_t st) {
+  const int tot = DU * keep * K + DL * chiL * keep;
+  count_launches(1);
+  k_zip_write<T><<<std::min((tot + 255) / 256, 1024), 256, 0, st>>>(V, US, DL, chiL, DU, K, keep, site_out,
+                                                                   carry_out, s1_dev, lognorm_r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zip_site0(const T* M, int DU, int K, T* site_out, double* lognorm_r, cudaStream_t st) {
+  count_launches(1);
+  k_zip_site0<T><<<1, 1024, 0, st>>>(M, DU * K, site_out, lognorm_r);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaStream_t st) {
+  count_launches(1);
+  k_mps_value<T><<<1, 64, 0, st>>>(mps, r, cols, out);
+  return cudaGetLastError();
+}
+
+#define SPG_INST(T)                                                                                       \
+  template cudaError_t launch_weights<T>(const DevTables&, DevWeights<T>, double, cudaStream_t);        \
+  template cudaError_t launch_left_canonical<T>(DevMPS<T>, int, int, const int*, T*, cudaStream_t);     \
+  template cudaError_t launch_zip_matrix<T>(const DevTables&, DevWeights<T>, const T*, int, int, int,   \
+                                            const T*, int, int, int, int, int, T*, T*, cudaStream_t);   \
+  template cudaError_t truncated_svd<T>(const T*, int, int, int, int, uint64_t, T*, T*, T*, size_t,     \
+                                        double*, int*, cudaStream_t);                                   \
+  template cudaError_t launch_zip_write<T>(const T*, const T*, int, int, int, int, int, T*, T*,         \
+                                           const double*, double*, cudaStream_t);                       \
+  template cudaError_t launch_zip_site0<T>(const T*, int, int, T*, double*, cudaStream_t);              \
+  template cudaError_t launch_mps_value<T>(DevMPS<T>, int, int, double*, cudaStream_t);                 \
+  template cudaError_t gemm<T>(bool, int, int, int, const T*, int, const T*, int, T*, int, cudaStream_t);   \
+  template cudaError_t gemm2<T>(bool, bool, int, int, int, const T*, int, const T*, int, T*, int,         \
+                                cudaStream_t);                                                          \
+  template cudaError_t launch_set_strided<T>(T*, size_t, int, T, cudaStream_t);
+
+SPG_INST(double)
+SPG_INST(float)
+
+}  // namespace spg

@@ -1,0 +1,743 @@
+// Search kernels: right environments (S5), conditional marginals (S6),
+// branch merging and pruning to max_states (S7), exact final energies (S8).
+//
+// Paper: Sec. 2 (branch and bound in the probability space, one Potts
+// variable at a time in a fixed order; marginals from the contracted network;
+// merging of partial configurations equal on the boundary of the explored
+// region), Sec. 3.1 (SearchParameters(max_states, cut_off_prob),
+// merge_branches, low_energy_spectrum), Fig. 1(d)-(e).
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "spg_internal.h"
+
+namespace spg {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? red[lane] : T(0);
+  return warp_sum(t);
+}
+template <typename T>
+__device__ T block_max(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? red[lane] : T(-INFINITY);
+  return warp_max(t);
+}
+
+// order-preserving map double -> u64 (NaN treated as -inf)
+__device__ __forceinline__ unsigned long long ord_f64(double v) {
+  if (v != v) v = -INFINITY;
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord_f64(unsigned long long k) {
+  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long ord_i64(int64_t v) {
+  return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+
+__device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { return tb.dims[s * 8 + k]; }
+
+// ---------------------------------------------------------------- S5 right environments
+// For beam element b (one block) at the start of row i, with B = B_{i+1}:
+//   R_L = 1;  R_j[a][l] = sum_x w(x) bL[l][PL x] bU[u_j][PU x]
+//                          sum_a' B_j[PD x][a][a'] R_{j+1}[a'][PR x]
+// stored at R[((b*(cols+1) + j)*chi + a)*MAXP + l], each R_j scaled to max |.| = 1.
+template <typename T>
+__global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int row, DevSearch ds,
+                             DevBeamT<T> bt, int cur) {
+  const int b = blockIdx.x;
+  if (b >= ds.n_beam[cur]) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* Rn = reinterpret_cast<T*>(smem_raw);  // [chi][MAXP] next (j+1)
+  T* Y = Rn + MAXCHI * MAXP;               // [MAXP][chi]
+  T* red = Y + MAXP * MAXCHI;              // 32
+  const int cols = tb.cols, chi = bt.chi;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T* Rb = bt.R + (size_t)b * (cols + 1) * chi * MAXP;
+  for (int e = tid; e < chi * MAXP; e += nt) {
+    const T v = e == 0 ? T(1) : T(0);
+    Rb[(size_t)cols * chi * MAXP + e] = v;
+    Rn[e] = v;
+  }
+  if (tid == 0) ds.rid[cur][b] = b;
+  for (int a = tid; a < chi; a += nt) bt.lenv[cur][(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
+  __syncthreads();
+  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  for (int j = cols - 1; j >= 1; --j) {
+    const int s = row * cols + j;
+    const int* dA = mps.dimA + ((row + 1) * cols + j) * 3;
+    const int chiL = dA[1], chiR = dA[2];
+    const T* A = mps.A + (size_t)((row + 1) * cols + j) * mps.site_stride;
+    const int DL = dim_of(tb, s, 0), NL = dim_of(tb, s, 4);
+    const int u = row > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + stb[s - cols]] : 0;
+    const size_t so = (size_t)s * tb.dmax;
+    const int* off = tb.xoffL + s * (MAXP + 1);
+    // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rn[a'][PR x]
+    for (int e = tid; e < NL * chiL; e += nt) {
+      const int h = e / chiL, a = e % chiL;
+      T acc = T(0);
+      for (int q = off[h]; q < off[h + 1]; ++q) {
+        const int x = tb.xsL[so + q];
+        const T c = wt.w[so + x] * wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
+        const T* arow = A + ((size_t)tb.PD[so + x] * chiL + a) * chiR;
+        const int pr = tb.PR[so + x];
+        T t = T(0);
+        for (int ap = 0; ap < chiR; ++ap) t += arow[ap] * Rn[ap * MAXP + pr];
+        acc += c * t;
+      }
+      Y[h * MAXCHI + a] = acc;
+    }
+    __syncthreads();
+    T mx = T(0);
+    T* Rj = Rb + (size_t)j * chi * MAXP;
+    for (int e = tid; e < chiL * DL; e += nt) {
+      const int a = e / DL, l = e % DL;
+      T acc = T(0);
+      for (int h = 0; h < NL; ++h) acc += wt.bL[(size_t)s * 256 + l * 16 + h] * Y[h * MAXCHI + a];
+      Rj[a * MAXP + l] = acc;
+      mx = max(mx, (T)fabs((double)acc));
+    }
+    mx = block_max(mx, red);
+    const T inv = mx > T(0) ? T(1) / mx : T(0);
+    __syncthreads();
+    for (int e = tid; e < chi * MAXP; e += nt) {
+      const int a = e / MAXP, l = e % MAXP;
+      T v = (a < chiL && l < DL) ? Rj[e] * inv : T(0);
+      Rj[e] = v;
+      Rn[e] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- S6 marginals
+// One block per beam element b at site s = (i, j):
+//   v[p][a'] = sum_a lenv[a] B[p][a][a'];  Z[p][rr] = sum_a' v[p][a'] R_{j+1}[a'][rr]
+//   q(x) = w(x) bL[h][PL x] bU[u][PU x] Z[PD x][PR x]   (FP64 weights, q < 0 -> 0)
+//   logc[b][x] = log q(x) - log sum_x q(x)
+//   candE[b][x] = E[b] + E_s(x) + RL[h][PL x] + RU[u][PU x]
+template <typename T>
+__global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, int site, DevSearch ds,
+                            DevBeamT<T> bt, int cur) {
+  const int b = blockIdx.x;
+  if (b >= ds.n_beam[cur]) return;
+  __shared__ T sl[MAXCHI];
+  __shared__ T sv[MAXP * MAXCHI];
+  __shared__ double sZ[MAXP * MAXP];
+  __shared__ double red[32];
+  const int cols = tb.cols, chi = bt.chi;
+  const int i = site / cols, j = site % cols;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int* dA = mps.dimA + ((i + 1) * cols + j) * 3;
+  const int p = dA[0], chiL = dA[1], chiR = dA[2];
+  const T* A = mps.A + (size_t)((i + 1) * cols + j) * mps.site_stride;
+  const int DR = dim_of(tb, site, 1);
+  for (int a = tid; a < chiL; a += nt) sl[a] = bt.lenv[cur][(size_t)b * chi + a];
+  __syncthreads();
+  for (int e = tid; e < p * chiR; e += nt) {
+    const int s = e / chiR, ap = e % chiR;
+    T acc = T(0);
+    for (int a = 0; a < chiL; ++a) acc += sl[a] * A[((size_t)s * chiL + a) * chiR + ap];
+    sv[s * MAXCHI + ap] = acc;
+  }
+  __syncthreads();
+  const int rb = ds.rid[cur][b];
+  const T* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * MAXP;
+  for (int e = tid; e < p * DR; e += nt) {
+    const int s = e / DR, rr = e % DR;
+    T acc = T(0);
+    for (int ap = 0; ap < chiR; ++ap) acc += sv[s * MAXCHI + ap] * Rj[ap * MAXP + rr];
+    sZ[s * MAXP + rr] = (double)acc;
+  }
+  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  const size_t so = (size_t)site * tb.dmax;
+  const int h = j > 0 ? tb.PR[(size_t)(site - 1) * tb.dmax + stb[site - 1]] : 0;
+  const int u = i > 0 ? tb.PD[(size_t)(site - cols) * tb.dmax + stb[site - cols]] : 0;
+  __syncthreads();
+  const int d = tb.d[site];
+  double part = 0.0;
+  for (int x = tid; x < d; x += nt) {
+    double q = wd.w[so + x] * wd.bL[(size_t)site * 256 + h * 16 + tb.PL[so + x]] *
+               wd.bU[(size_t)site * 256 + u * 16 + tb.PU[so + x]] * sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
+    q = q > 0.0 ? q : 0.0;
+    part += q;
+  }
+  const double tot = block_sum(part, red);
+  const double lt = log(tot);
+  const int64_t E0 = ds.E[cur][b];
+  for (int x = tid; x < d; x += nt) {
+    const int pl = tb.PL[so + x], pu = tb.PU[so + x];
+    double q = wd.w[so + x] * wd.bL[(size_t)site * 256 + h * 16 + pl] * wd.bU[(size_t)site * 256 + u * 16 + pu] *
+               sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
+    q = q > 0.0 ? q : 0.0;
+    const double lc = (tot > 0.0) ? (q > 0.0 ? log(q) - lt : -INFINITY) : -INFINITY;
+    ds.logc[(size_t)b * ds.dmax + x] = lc;
+    ds.candE[(size_t)b * ds.dmax + x] =
+        E0 + tb.E[so + x] + tb.RL[(size_t)site * 256 + h * 16 + pl] + tb.RU[(size_t)site * 256 + u * 16 + pu];
+  }
+  if (tid == 0 && !(tot >= 0.0)) atomicOr(ds.err, ERR_NAN);
+}
+
+// ---------------------------------------------------------------- S7 merge
+// Reduced parent key: states (packed `bits` each) of the key sites at this
+// step other than the current site.  Class representative = first parent
+// (lowest lex rank) with the same key; members linked through nxt.
+__global__ void k_parent_keys(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ds.n_beam[cur]) return;
+  unsigned long long k[KEYW] = {0, 0, 0, 0};
+  if (merge) {
+    const int* ks = tb.keys + site * (MAXKEY + 1);
+    const int n = ks[0], bits = *tb.kshift;
+    const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+    for (int q = 0; q < n; ++q) {
+      const int pos = q * bits;
+      const int w = pos >> 6, o = pos & 63;
+      if (w < KEYW) k[w] |= (unsigned long long)stb[ks[1 + q]] << o;
+      else atomicOr(ds.err, ERR_KEY);
+    }
+  }
+  for (int w = 0; w < KEYW; ++w) ds.key[(size_t)b * KEYW + w] = k[w];
+}
+
+__global__ void k_classes(DevSearch ds, int cur, int merge) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = ds.n_beam[cur];
+  if (b >= nb) return;
+  if (!merge) {
+    ds.rep[b] = b;
+    ds.nxt[b] = -1;
+    return;
+  }
+  const unsigned long long* kb = ds.key + (size_t)b * KEYW;
+  const unsigned long long k0 = kb[0], k1 = kb[1], k2 = kb[2], k3 = kb[3];
+  int rep = b, nx = -1;
+  for (int o = 0; o < nb; ++o) {
+    if (o == b) continue;
+    const unsigned long long* ko = ds.key + (size_t)o * KEYW;
+    if (ko[0] == k0 && ko[1] == k1 && ko[2] == k2 && ko[3] == k3) {
+      if (o < rep) rep = o;
+      if (o > b && nx < 0) nx = o;
+    }
+  }
+  ds.rep[b] = rep;
+  ds.nxt[b] = nx;
+}
+
+// For each (class representative b, x): the member with the lowest
+// (candidate energy, lex rank) wins.  When the site's own state is not part
+// of the key (no edge to a later site), one winner is taken per class over
+// all states x, lex order (member, x).
+__global__ void k_winners(DevTables tb, int site, DevSearch ds, int cur) {
+  const int nb = ds.n_beam[cur];
+  const int d = tb.d[site];
+  const bool xin = tb.dims[site * 8 + 6] != 0;
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
+    if (xin) {
+      int w = -1;
+      if (b < nb && x < d && ds.rep[b] == b) {
+        w = b;
+        int64_t be = ds.candE[(size_t)b * ds.dmax + x];
+        for (int m = ds.nxt[b]; m >= 0; m = ds.nxt[m]) {
+          const int64_t e = ds.candE[(size_t)m * ds.dmax + x];
+          if (e < be) {  // members are visited in increasing lex rank
+            be = e;
+            w = m;
+          }
+        }
+      }
+      ds.win[c] = w;
+    } else if (x == 0) {
+      int bw = -1, bx = 0;
+      if (b < nb && ds.rep[b] == b) {
+        int64_t be = 0;
+        for (int m = b; m >= 0; m = ds.nxt[m])
+          for (int y = 0; y < d; ++y) {
+            const int64_t e = ds.candE[(size_t)m * ds.dmax + y];
+            if (bw < 0 || e < be) {
+              be = e;
+              bw = m;
+              bx = y;
+            }
+          }
+      }
+      for (int y = 0; y < ds.dmax; ++y) ds.win[(size_t)b * ds.dmax + y] = (y == bx) ? bw : -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- S7 prune: radix select
+// Composite key of candidate c = b*dmax + x (ascending order = rank order):
+//   k0 = ~ord(log p), k1 = ord(E), k2 = (winner << 16) | x.
+// sel_state words: 0..2 prefix, 3 need, 4 status (0 running, 1 done), 5
+// pass, 6 max logp key, 7 min selected logp key, 8 max rejected logp key,
+// 9 log cut offset (as double bits, +inf when off), 10 total valid.
+struct CandKey {
+  unsigned long long k[3];
+  bool valid;
+  double lp;
+};
+
+__device__ __forceinline__ CandKey cand_key(const DevSearch& ds, int cur, size_t c, int nb, int d,
+                                            double log_cut, unsigned long long maxkey) {
+  CandKey r;
+  r.valid = false;
+  const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
+  if (b >= nb || x >= d) return r;
+  const int w = ds.win[c];
+  if (w < 0) return r;
+  const double lp = ds.logp[cur][w] + ds.logc[(size_t)w * ds.dmax + x];
+  if (log_cut > -INFINITY) {
+    const double mx = unord_f64(maxkey);
+    if (!(lp >= mx + log_cut)) return r;
+  }
+  r.valid = true;
+  r.lp = lp;
+  r.k[0] = ~ord_f64(lp);
+  r.k[1] = ord_i64(ds.candE[(size_t)w * ds.dmax + x]);
+  r.k[2] = ((unsigned long long)w << 16) | (unsigned long long)x;
+  return r;
+}
+
+__global__ void k_logp_max(DevTables tb, int site, DevSearch ds, int cur) {
+  const int nb = ds.n_beam[cur], d = tb.d[site];
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  unsigned long long best = 0;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    CandKey k = cand_key(ds, cur, c, nb, d, -INFINITY, 0);
+    if (k.valid) best = max(best, ord_f64(k.lp));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(ds.sel_state + 6, best);
+}
+
+__global__ void k_select_init(DevSearch ds) {
+  if (threadIdx.x == 0) {
+    ds.sel_state[0] = ds.sel_state[1] = ds.sel_state[2] = 0;
+    ds.sel_state[3] = (unsigned long long)ds.cap;
+    ds.sel_state[4] = 0;
+    ds.sel_state[5] = 0;
+    ds.sel_state[6] = 0;
+    ds.sel_state[7] = ~0ull;
+    ds.sel_state[8] = 0;
+    ds.sel_state[10] = 0;
+    *ds.sel_count = 0;
+    *ds.done_ctr = 0;
+  }
+  for (int e = threadIdx.x; e < 65536; e += blockDim.x) ds.hist[e] = 0;
+}
+
+__device__ __forceinline__ bool prefix_match(const CandKey& k, const unsigned long long* pre, int pass) {
+  // bits determined before this pass: 16*pass of the 192-bit key
+  const int full = pass >> 2, part = (pass & 3) * 16;
+  for (int w = 0; w < full; ++w)
+    if (k.k[w] != pre[w]) return false;
+  if (part > 0) {
+    const unsigned long long m = ~0ull << (64 - part);
+    if ((k.k[full] & m) != (pre[full] & m)) return false;
+  }
+  return true;
+}
+
+__global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int pass, double log_cut) {
+  __shared__ bool s_last;
+  const unsigned long long status = ds.sel_state[4];
+  if (status != 0) return;
+  const int nb = ds.n_beam[cur], d = tb.d[site];
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  unsigned long long pre[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
+  const unsigned long long maxkey = ds.sel_state[6];
+  const int w = pass >> 2, sh = 48 - (pass & 3) * 16;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
+    if (!k.valid || !prefix_match(k, pre, pass)) continue;
+    atomicAdd(ds.hist + ((k.k[w] >> sh) & 0xffff), 1u);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ds.done_ctr, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: scan the histogram, pick the digit holding the need-th key
+  __shared__ unsigned long long part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;  // nt == 1024
+  const int per = 65536 / nt;
+  unsigned long long loc = 0;
+  for (int q = 0; q < per; ++q) loc += ((volatile unsigned*)ds.hist)[tid * per + q];
+  part[tid] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long need = ds.sel_state[3];
+    unsigned long long total = 0;
+    for (int t = 0; t < nt; ++t) total += part[t];
+    if (pass == 0) ds.sel_state[10] = total;
+    if (pass == 0 && total <= need) {
+      ds.sel_state[0] = ds.sel_state[1] = ds.sel_state[2] = ~0ull;  // select all valid
+      ds.sel_state[4] = 1;
+    } else {
+      unsigned long long cum = 0;
+      int t = 0;
+      while (t < nt && cum + part[t] < need) cum += part[t++];
+      if (t == nt) t = nt - 1;  // cannot happen while counts are consistent
+      int digit = t * per;
+      for (; digit < (t + 1) * per - 1; ++digit) {
+        const unsigned long long hv = ((volatile unsigned*)ds.hist)[digit];
+        if (cum + hv >= need) break;
+        cum += hv;
+      }
+      const unsigned long long hv = ((volatile unsigned*)ds.hist)[digit];
+      need = need > cum ? need - cum : 1;
+      ds.sel_state[w] |= (unsigned long long)digit << sh;
+      ds.sel_state[3] = need;
+      if (hv == need || pass == 11) {
+        // every key matching the prefix up to here is selected: fill the rest with ones
+        if (sh > 0) ds.sel_state[w] |= (1ull << sh) - 1ull;
+        for (int q = w + 1; q < 3; ++q) ds.sel_state[q] = ~0ull;
+        ds.sel_state[4] = 1;
+      }
+    }
+    ds.sel_state[5] = pass + 1;
+    *ds.done_ctr = 0;
+  }
+  __syncthreads();
+  for (int e = tid; e < 65536; e += nt) ds.hist[e] = 0;
+}
+
+__device__ __forceinline__ bool key_le(const CandKey& k, const unsigned long long* t) {
+  if (k.k[0] != t[0]) return k.k[0] < t[0];
+  if (k.k[1] != t[1]) return k.k[1] < t[1];
+  return k.k[2] <= t[2];
+}
+
+__global__ void k_select_compact(DevTables tb, int site, DevSearch ds, int cur, double log_cut) {
+  const int nb = ds.n_beam[cur], d = tb.d[site];
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  const unsigned long long thr[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
+  const unsigned long long maxkey = ds.sel_state[6];
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
+    if (!k.valid) continue;
+    if (key_le(k, thr)) {
+      const int pos = atomicAdd(ds.sel_count, 1);
+      if (pos < ds.cap) ds.sel_list[pos] = (int)c;
+      atomicMin(ds.sel_state + 7, ord_f64(k.lp));
+    } else {
+      atomicMax(ds.sel_state + 8, ord_f64(k.lp) + 1ull);  // +1 keeps 0 = "none"
+    }
+  }
+}
+
+// One block: sort the selected ids by lex key (winner, x); record near ties.
+__global__ void k_select_sort(DevTables tb, int site, DevSearch ds, int cur, int nxt_buf) {
+  extern __shared__ unsigned long long sk[];  // [pow2 >= cap]
+  const int n = min(*ds.sel_count, ds.cap);
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    unsigned long long v = ~0ull;
+    if (e < n) {
+      const int c = ds.sel_list[e];
+      const int x = c % ds.dmax;
+      const int w = ds.win[c];
+      v = ((unsigned long long)w << 40) | ((unsigned long long)x << 24) | (unsigned long long)e;
+    }
+    sk[e] = v;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        const int o = e ^ jj;
+        if (o > e) {
+          const bool up = (e & k) == 0;
+          const unsigned long long a = sk[e], b = sk[o];
+          if ((a > b) == up) {
+            sk[e] = b;
+            sk[o] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // rewrite sel_list in lex order (through the original slot index in the low bits)
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int slot = (int)(sk[e] & 0xffffffull);
+    sk[e] = (unsigned long long)ds.sel_list[slot];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) ds.sel_list[e] = (int)sk[e];
+  if (threadIdx.x == 0) {
+    ds.n_beam[nxt_buf] = n;
+    *ds.candidates += (double)ds.n_beam[cur] * (double)tb.d[site];
+    const unsigned long long rj = ds.sel_state[8];
+    if (rj != 0 && n > 0) {
+      const double a = unord_f64(ds.sel_state[7]);
+      const double bb = unord_f64(rj - 1ull);
+      if (fabs(a - bb) <= 1e-9 * fmax(1.0, fabs(a))) atomicAdd(ds.near_ties, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- update
+// New beam element i from selected candidate c = rep*dmax + x with parent w.
+template <typename T>
+__global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, DevBeamT<T> bt, int cur) {
+  const int i = blockIdx.x;
+  const int nxt = cur ^ 1;
+  if (i >= ds.n_beam[nxt]) return;
+  __shared__ T red[32];
+  const int c = ds.sel_list[i];
+  const int x = c % ds.dmax;
+  const int w = ds.win[c];
+  const int N = ds.N;
+  for (int q = threadIdx.x; q < N; q += blockDim.x)
+    ds.states[nxt][(size_t)i * N + q] = q == site ? (uint16_t)x : ds.states[cur][(size_t)w * N + q];
+  if (threadIdx.x == 0) {
+    ds.E[nxt][i] = ds.candE[(size_t)w * ds.dmax + x];
+    ds.logp[nxt][i] = ds.logp[cur][w] + ds.logc[(size_t)w * ds.dmax + x];
+    ds.rid[nxt][i] = ds.rid[cur][w];
+  }
+  const int cols = tb.cols, chi = bt.chi;
+  const int r = site / cols, j = site % cols;
+  const int* dA = mps.dimA + ((r + 1) * cols + j) * 3;
+  const int chiL = dA[1], chiR = dA[2];
+  const T* A = mps.A + (size_t)((r + 1) * cols + j) * mps.site_stride;
+  const int pd = tb.PD[(size_t)site * tb.dmax + x];
+  const T* lw = bt.lenv[cur] + (size_t)w * chi;
+  T mx = T(0);
+  T v = T(0);
+  const int ap = threadIdx.x;
+  if (ap < chiR) {
+    for (int a = 0; a < chiL; ++a) v += lw[a] * A[((size_t)pd * chiL + a) * chiR + ap];
+    mx = (T)fabs((double)v);
+  }
+  mx = block_max(mx, red);
+  const T inv = mx > T(0) ? T(1) / mx : T(0);
+  if (ap < chi) bt.lenv[nxt][(size_t)i * chi + ap] = ap < chiR ? v * inv : T(0);
+}
+
+// lenv of teacher-forced prefixes: prod_{k<j} B_{i+1}[k][:, PD x_k, :], scaled.
+template <typename T>
+__global__ void k_lenv_prefix(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, DevBeamT<T> bt, int cur) {
+  const int b = blockIdx.x;
+  if (b >= ds.n_beam[cur]) return;
+  __shared__ T v[MAXCHI], nv[MAXCHI], red[32];
+  const int cols = tb.cols, chi = bt.chi;
+  const int r = site / cols, j = site % cols;
+  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  if (threadIdx.x < MAXCHI) v[threadIdx.x] = threadIdx.x == 0 ? T(1) : T(0);
+  __syncthreads();
+  for (int k = 0; k < j; ++k) {
+    const int s = r * cols + k;
+    const int* dA = mps.dimA + ((r + 1) * cols + k) * 3;
+    const int chiL = dA[1], chiR = dA[2];
+    const T* A = mps.A + (size_t)((r + 1) * cols + k) * mps.site_stride;
+    const int pd = tb.PD[(size_t)s * tb.dmax + stb[s]];
+    T val = T(0);
+    if (threadIdx.x < chiR)
+      for (int a = 0; a < chiL; ++a) val += v[a] * A[((size_t)pd * chiL + a) * chiR + threadIdx.x];
+    T mx = block_max(threadIdx.x < chiR ? (T)fabs((double)val) : T(0), red);
+    __syncthreads();
+    if (threadIdx.x < MAXCHI) nv[threadIdx.x] = threadIdx.x < chiR ? val / mx : T(0);
+    __syncthreads();
+    if (threadIdx.x < MAXCHI) v[threadIdx.x] = nv[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x < chi) bt.lenv[cur][(size_t)b * chi + threadIdx.x] = v[threadIdx.x];
+}
+
+__global__ void k_reset_beam(DevSearch ds, int cur) {
+  if (threadIdx.x == 0) {
+    ds.n_beam[cur] = 1;
+    ds.E[cur][0] = 0;
+    ds.logp[cur][0] = 0.0;
+    ds.rid[cur][0] = 0;
+    *ds.near_ties = 0;
+    *ds.err = 0;
+    *ds.candidates = 0.0;
+  }
+  for (int q = threadIdx.x; q < ds.N; q += blockDim.x) ds.states[cur][q] = 0;
+}
+
+// ---------------------------------------------------------------- S8 final
+// Exact energy of each final state from the tables (checked against the
+// running energy), then order by (energy, lex rank).
+__global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_states, int64_t* out_E,
+                        double* out_logp, int* out_n) {
+  extern __shared__ unsigned long long fin_smem[];
+  long long* sE = reinterpret_cast<long long*>(fin_smem);   // [SPG_MAXFINAL]
+  int* rank = reinterpret_cast<int*>(sE + SPG_MAXFINAL);    // [SPG_MAXFINAL]
+  const int n = min(ds.n_beam[cur], SPG_MAXFINAL);
+  const int N = ds.N, cols = tb.cols;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    const uint16_t* st = ds.states[cur] + (size_t)b * N;
+    int64_t E = 0;
+    for (int s = 0; s < N; ++s) {
+      const size_t so = (size_t)s * tb.dmax;
+      const int x = st[s];
+      E += tb.E[so + x];
+      if (s % cols > 0) E += tb.RL[(size_t)s * 256 + tb.PR[so - tb.dmax + st[s - 1]] * 16 + tb.PL[so + x]];
+      if (s >= cols)
+        E += tb.RU[(size_t)s * 256 + tb.PD[(size_t)(s - cols) * tb.dmax + st[s - cols]] * 16 + tb.PU[so + x]];
+    }
+    if (E != ds.E[cur][b]) atomicOr(ds.err, ERR_ENERGY);
+    sE[b] = E;
+  }
+  __syncthreads();
+  // rank by (E, lex rank b); O(n^2) with n <= SPG_MAXFINAL
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    int rk = 0;
+    for (int o = 0; o < n; ++o) rk += (sE[o] < sE[b]) || (sE[o] == sE[b] && o < b);
+    rank[b] = rk;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    const int rk = rank[b];
+    out_E[rk] = sE[b];
+    out_logp[rk] = ds.logp[cur][b];
+  }
+  for (size_t e = threadIdx.x; e < (size_t)n * N; e += blockDim.x) {
+    const int b = (int)(e / N), s = (int)(e % N);
+    out_states[(size_t)rank[b] * N + s] = ds.states[cur][e];
+  }
+  if (threadIdx.x == 0) *out_n = n;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, const DevSearch& ds,
+                              DevBeamT<T> bt, int cur, cudaStream_t st) {
+  const size_t sm = sizeof(T) * (2 * MAXCHI * MAXP + 32);
+  count_launches(1);
+  k_right_envs<T><<<ds.cap, 256, sm, st>>>(tb, wt, mps, row, ds, bt, cur);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
+                                  const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
+  count_launches(1);
+  k_marginals<T><<<ds.cap, 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
+  const int nbk = (ds.cap + 255) / 256;
+  count_launches(1);
+  k_parent_keys<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
+  count_launches(1);
+  k_classes<<<nbk, 256, 0, st>>>(ds, cur, merge);
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  count_launches(1);
+  k_winners<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>(tb, site, ds, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, int cur, double log_cut,
+                          cudaStream_t st) {
+  const size_t tot = (size_t)ds.cap * ds.dmax;
+  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 1024);
+  count_launches(1);
+  k_select_init<<<1, 1024, 0, st>>>(ds);
+  if (log_cut > -INFINITY) {
+    count_launches(1);
+    k_logp_max<<<blocks, 1024, 0, st>>>(tb, site, ds, cur);
+  }
+  for (int pass = 0; pass < 12; ++pass) {
+    count_launches(1);
+    k_select_pass<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, pass, log_cut);
+  }
+  count_launches(1);
+  k_select_compact<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, log_cut);
+  int P = 1;
+  while (P < ds.cap) P <<= 1;
+  count_launches(1);
+  k_select_sort<<<1, 1024, sizeof(unsigned long long) * P, st>>>(tb, site, ds, cur, cur ^ 1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds, DevBeamT<T> bt, int cur,
+                          cudaStream_t st) {
+  count_launches(1);
+  k_update<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds,
+                                    DevBeamT<T> bt, int cur, cudaStream_t st) {
+  count_launches(1);
+  k_lenv_prefix<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
+  count_launches(1);
+  k_reset_beam<<<1, 256, 0, st>>>(ds, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint16_t* out_states, int64_t* out_E,
+                         double* out_logp, int* out_n, cudaStream_t st) {
+  const int sm = (int)((sizeof(long long) + sizeof(int)) * SPG_MAXFINAL);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    attr = true;
+  }
+  count_launches(1);
+  k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_right_envs<double>(const DevTables&, DevWeights<double>, DevMPS<double>, int,
+                                               const DevSearch&, DevBeamT<double>, int, cudaStream_t);
+template cudaError_t launch_right_envs<float>(const DevTables&, DevWeights<float>, DevMPS<float>, int,
+                                              const DevSearch&, DevBeamT<float>, int, cudaStream_t);
+template cudaError_t launch_marginals<double>(const DevTables&, DevWeights<double>, DevMPS<double>, int,
+                                                   const DevSearch&, DevBeamT<double>, int, cudaStream_t);
+template cudaError_t launch_marginals<float>(const DevTables&, DevWeights<double>, DevMPS<float>, int,
+                                                  const DevSearch&, DevBeamT<float>, int, cudaStream_t);
+template cudaError_t launch_update<double>(const DevTables&, DevMPS<double>, int, const DevSearch&,
+                                           DevBeamT<double>, int, cudaStream_t);
+template cudaError_t launch_update<float>(const DevTables&, DevMPS<float>, int, const DevSearch&, DevBeamT<float>,
+                                          int, cudaStream_t);
+template cudaError_t launch_lenv_from_prefix<double>(const DevTables&, DevMPS<double>, int, const DevSearch&,
+                                                     DevBeamT<double>, int, cudaStream_t);
+template cudaError_t launch_lenv_from_prefix<float>(const DevTables&, DevMPS<float>, int, const DevSearch&,
+                                                    DevBeamT<float>, int, cudaStream_t);
+
+}  // namespace spg

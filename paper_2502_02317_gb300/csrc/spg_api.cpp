@@ -1,0 +1,1086 @@
+// C ABI of libspg (include/spg.h): problem construction (S1: cluster factor
+// graph, integer local and pairwise tables, projectors), the device
+// workspace, and the orchestration of the boundary-MPS (S2-S4) and search
+// (S5-S8) kernels.
+//
+// Paper: Eq. 1 and Eq. 2 (generalised Potts and Ising energies), Sec. 2
+// (clusters of spins as Potts variables; PEPS of the Boltzmann distribution;
+// branch and bound with merging), Sec. 3.1 (the solver's parameters).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spg.h"
+#include "spg_internal.h"
+
+using namespace spg;
+
+struct spg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // grow-only device arena, bump-allocated per solve
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+struct spg_problem {
+  spg_ctx* ctx = nullptr;
+  int rows = 0, cols = 0, n = 0, dmax = 0, node_type = 0, shift = 0;
+  std::vector<int> d;
+  std::vector<int64_t> E;  // [n][dmax]
+  std::vector<uint8_t> PL, PR, PU, PD;
+  std::vector<int> dims;  // [n][8]
+  std::vector<int64_t> RL, RU;  // [n][256]
+  std::vector<int16_t> xsL;
+  std::vector<int> xoffL;  // [n][MAXP+1]
+  std::vector<int> keys;   // [n][MAXKEY+1]
+  int kbits = 1;
+  double min_sum = 0.0;  // sum of the minima of all local and reduced tables
+  void* dev = nullptr;
+  DevTables tb{};
+};
+
+struct spg_result {
+  spg_ctx* ctx = nullptr;
+  int N = 0, cap = 0;
+  uint16_t* d_states = nullptr;
+  int64_t* d_E = nullptr;
+  double* d_logp = nullptr;
+  int* d_n = nullptr;
+  // diagnostics copied at the end of the solve
+  int* d_diag = nullptr;  // near_ties, err, deg_cuts
+  double* d_cand = nullptr;
+  float ms_boundary = 0.f, ms_search = 0.f;
+  double lognorm = 0.0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool fetched = false;
+  int n = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+int fail(spg_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, SPG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+// ---------------------------------------------------------------- S1 helpers
+struct EdgeTab {
+  int Dm = 1, Dn = 1;
+  std::vector<int64_t> R;       // Dm x Dn
+  std::vector<uint8_t> Pm, Pn;  // d_m, d_n
+};
+
+// Distinct rows / columns of a full table T (dm x dn) in order of first
+// occurrence; projectors and reduced table.  Returns false if > MAXP.
+bool reduce_full(const std::vector<int64_t>& T, int dm, int dn, EdgeTab& out) {
+  std::map<std::vector<int64_t>, int> rows, colsm;
+  std::vector<int> firstr, firstc;
+  out.Pm.assign(dm, 0);
+  out.Pn.assign(dn, 0);
+  for (int x = 0; x < dm; ++x) {
+    std::vector<int64_t> r(T.begin() + (size_t)x * dn, T.begin() + (size_t)(x + 1) * dn);
+    auto it = rows.find(r);
+    if (it == rows.end()) {
+      it = rows.emplace(r, (int)rows.size()).first;
+      firstr.push_back(x);
+    }
+    if (it->second >= MAXP) return false;
+    out.Pm[x] = (uint8_t)it->second;
+  }
+  for (int y = 0; y < dn; ++y) {
+    std::vector<int64_t> c(dm);
+    for (int x = 0; x < dm; ++x) c[x] = T[(size_t)x * dn + y];
+    auto it = colsm.find(c);
+    if (it == colsm.end()) {
+      it = colsm.emplace(c, (int)colsm.size()).first;
+      firstc.push_back(y);
+    }
+    if (it->second >= MAXP) return false;
+    out.Pn[y] = (uint8_t)it->second;
+  }
+  out.Dm = (int)firstr.size();
+  out.Dn = (int)firstc.size();
+  out.R.assign((size_t)out.Dm * out.Dn, 0);
+  for (int a = 0; a < out.Dm; ++a)
+    for (int b = 0; b < out.Dn; ++b) out.R[(size_t)a * out.Dn + b] = T[(size_t)firstr[a] * dn + firstc[b]];
+  return true;
+}
+
+int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, EdgeTab>& edges) {
+  const int n = P->n, dmax = P->dmax, cols = P->cols;
+  P->PL.assign((size_t)n * dmax, 0);
+  P->PR.assign((size_t)n * dmax, 0);
+  P->PU.assign((size_t)n * dmax, 0);
+  P->PD.assign((size_t)n * dmax, 0);
+  P->dims.assign((size_t)n * 8, 1);
+  P->RL.assign((size_t)n * 256, 0);
+  P->RU.assign((size_t)n * 256, 0);
+  P->xsL.assign((size_t)n * dmax, 0);
+  P->xoffL.assign((size_t)n * (MAXP + 1), 0);
+  double mins = 0.0;
+  for (int s = 0; s < n; ++s) {
+    int64_t mn = INT64_MAX;
+    for (int x = 0; x < P->d[s]; ++x) mn = std::min(mn, P->E[(size_t)s * dmax + x]);
+    mins += (double)mn;
+  }
+  for (auto& kv : edges) {
+    const int m = kv.first.first, nn = kv.first.second;
+    EdgeTab& e = kv.second;
+    int64_t mn = INT64_MAX;
+    for (auto v : e.R) mn = std::min(mn, v);
+    mins += (double)mn;
+    const bool horiz = (nn == m + 1) && (m / cols == nn / cols);
+    const bool vert = nn == m + cols;
+    if (!horiz && !vert)
+      return fail(ctx, SPG_EUNSUPPORTED, "diagonal (king's graph) edges are not built in this version");
+    if (horiz) {
+      for (int x = 0; x < P->d[m]; ++x) P->PR[(size_t)m * dmax + x] = e.Pm[x];
+      for (int x = 0; x < P->d[nn]; ++x) P->PL[(size_t)nn * dmax + x] = e.Pn[x];
+      P->dims[m * 8 + 1] = e.Dm;
+      P->dims[nn * 8 + 0] = e.Dm;
+      P->dims[nn * 8 + 4] = e.Dn;
+      for (int a = 0; a < e.Dm; ++a)
+        for (int b = 0; b < e.Dn; ++b) P->RL[(size_t)nn * 256 + a * 16 + b] = e.R[(size_t)a * e.Dn + b];
+    } else {
+      for (int x = 0; x < P->d[m]; ++x) P->PD[(size_t)m * dmax + x] = e.Pm[x];
+      for (int x = 0; x < P->d[nn]; ++x) P->PU[(size_t)nn * dmax + x] = e.Pn[x];
+      P->dims[m * 8 + 3] = e.Dm;
+      P->dims[nn * 8 + 2] = e.Dm;
+      P->dims[nn * 8 + 5] = e.Dn;
+      for (int a = 0; a < e.Dm; ++a)
+        for (int b = 0; b < e.Dn; ++b) P->RU[(size_t)nn * 256 + a * 16 + b] = e.R[(size_t)a * e.Dn + b];
+    }
+  }
+  P->min_sum = mins;
+  // states grouped by PL
+  for (int s = 0; s < n; ++s) {
+    const int NL = P->dims[s * 8 + 4];
+    int pos = 0;
+    for (int h = 0; h < NL; ++h) {
+      P->xoffL[s * (MAXP + 1) + h] = pos;
+      for (int x = 0; x < P->d[s]; ++x)
+        if (P->PL[(size_t)s * dmax + x] == h) P->xsL[(size_t)s * dmax + pos++] = (int16_t)x;
+    }
+    for (int h = NL; h <= MAXP; ++h) P->xoffL[s * (MAXP + 1) + h] = pos;
+  }
+  // merge keys: sites t <= s (t != s) with an edge to a site > s
+  int bits = 1;
+  while ((1 << bits) < dmax) ++bits;
+  int kb = 1;
+  while (kb < bits) kb <<= 1;
+  P->kbits = kb;
+  P->keys.assign((size_t)n * (MAXKEY + 1), 0);
+  std::vector<int> far(n, -1);  // largest neighbour index of each site
+  for (auto& kv : edges) {
+    const int a = kv.first.first, b = kv.first.second;
+    far[a] = std::max(far[a], b);
+    far[b] = std::max(far[b], a);
+  }
+  for (int s = 0; s < n; ++s) {
+    std::vector<int> ks;
+    for (int t = 0; t < s; ++t)
+      if (far[t] > s) ks.push_back(t);
+    P->dims[s * 8 + 6] = far[s] > s ? 1 : 0;  // the site's own state is part of its key
+    if ((int)ks.size() > MAXKEY || (int)ks.size() * kb > KEYW * 64)
+      return fail(ctx, SPG_EUNSUPPORTED, "merge key longer than the built limit");
+    P->keys[(size_t)s * (MAXKEY + 1)] = (int)ks.size();
+    for (size_t q = 0; q < ks.size(); ++q) P->keys[(size_t)s * (MAXKEY + 1) + 1 + q] = ks[q];
+  }
+  // upload
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_d = take(sizeof(int) * n), o_E = take(sizeof(int64_t) * n * dmax),
+               o_PL = take((size_t)n * dmax), o_PR = take((size_t)n * dmax), o_PU = take((size_t)n * dmax),
+               o_PD = take((size_t)n * dmax), o_dims = take(sizeof(int) * n * 8),
+               o_RL = take(sizeof(int64_t) * n * 256), o_RU = take(sizeof(int64_t) * n * 256),
+               o_xs = take(sizeof(int16_t) * n * dmax), o_xo = take(sizeof(int) * n * (MAXP + 1)),
+               o_k = take(sizeof(int) * n * (MAXKEY + 1)), o_kb = take(sizeof(int));
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMalloc(&P->dev, off));
+  char* base = (char*)P->dev;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(base + o_d, P->d.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_E, P->E.data(), sizeof(int64_t) * n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_PL, P->PL.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_PR, P->PR.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_PU, P->PU.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_PD, P->PD.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_dims, P->dims.data(), sizeof(int) * n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_RL, P->RL.data(), sizeof(int64_t) * n * 256, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_RU, P->RU.data(), sizeof(int64_t) * n * 256, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_xs, P->xsL.data(), sizeof(int16_t) * n * dmax, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_xo, P->xoffL.data(), sizeof(int) * n * (MAXP + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_k, P->keys.data(), sizeof(int) * n * (MAXKEY + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_kb, &P->kbits, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  DevTables& tb = P->tb;
+  tb.rows = P->rows;
+  tb.cols = P->cols;
+  tb.n = n;
+  tb.dmax = dmax;
+  tb.d = (const int*)(base + o_d);
+  tb.E = (const int64_t*)(base + o_E);
+  tb.PL = (const uint8_t*)(base + o_PL);
+  tb.PR = (const uint8_t*)(base + o_PR);
+  tb.PU = (const uint8_t*)(base + o_PU);
+  tb.PD = (const uint8_t*)(base + o_PD);
+  tb.dims = (const int*)(base + o_dims);
+  tb.RL = (const int64_t*)(base + o_RL);
+  tb.RU = (const int64_t*)(base + o_RU);
+  tb.xsL = (const int16_t*)(base + o_xs);
+  tb.xoffL = (const int*)(base + o_xo);
+  tb.keys = (const int*)(base + o_k);
+  tb.kshift = (const int*)(base + o_kb);
+  return SPG_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+struct Arena {
+  char* base;
+  size_t off = 0, cap;
+  template <typename T>
+  T* get(size_t count) {
+    size_t o = off;
+    off += (sizeof(T) * count + 255) & ~size_t(255);
+    return off <= cap ? reinterpret_cast<T*>(base + o) : nullptr;
+  }
+};
+
+int ensure_arena(spg_ctx* ctx, size_t bytes) {
+  if (ctx->arena_bytes >= bytes) return SPG_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->arena) CK(cudaFree(ctx->arena));
+  ctx->arena = nullptr;
+  ctx->arena_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SPG_ENOMEM, "device workspace allocation failed");
+  }
+  ctx->arena_bytes = bytes;
+  return SPG_OK;
+}
+
+// Host-side bond dimensions of every boundary MPS (structural: they depend
+// only on the tables' dimensions, chi, and the zipper's keep rule).
+struct Plan {
+  int rows, cols, chi;
+  std::vector<int> dimA;  // [(rows+1)*cols][3] p, chiL, chiR
+  size_t stride;
+};
+
+Plan make_plan(const spg_problem* P, int chi, int down_to) {
+  Plan pl;
+  pl.rows = P->rows;
+  pl.cols = P->cols;
+  pl.chi = chi;
+  const int cols = P->cols;
+  pl.dimA.assign((size_t)(P->rows + 1) * cols * 3, 1);
+  for (int r = P->rows - 1; r >= down_to; --r) {
+    int K = 1;
+    for (int j = cols - 1; j >= 0; --j) {
+      const int s = r * cols + j;
+      const int DL = P->dims[s * 8 + 0], DU = P->dims[s * 8 + 2];
+      const int chiL_in = pl.dimA[(((size_t)(r + 1) * cols + j) * 3) + 1];
+      int* o = &pl.dimA[((size_t)r * cols + j) * 3];
+      if (j == 0) {
+        o[0] = DU;
+        o[1] = 1;
+        o[2] = K;
+      } else {
+        const int m = DL * chiL_in, n = DU * K;
+        const int keep = std::min(chi, std::min(m, n));
+        o[0] = DU;
+        o[1] = keep;
+        o[2] = K;
+        K = keep;
+      }
+    }
+  }
+  pl.stride = (size_t)MAXP * chi * chi;
+  return pl;
+}
+
+template <typename T>
+struct BoundaryBufs {
+  DevMPS<T> mps;
+  int* dimA_dev;
+  DevWeights<T> wt;
+  DevWeights<double> wd;
+  T* T1;
+  T* M;
+  T* V;
+  T* US;
+  T* carry[2];
+  T* svdw;
+  size_t svdw_elems;
+  double* s1;
+  int* degc;
+};
+
+template <typename T>
+size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
+  const int chi = pl.chi;
+  const size_t sites = (size_t)(P->rows + 1) * P->cols;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
+  add(sizeof(T) * sites * pl.stride);
+  add(sizeof(int) * sites * 3);
+  add(sizeof(double) * (P->rows + 1));
+  add(sizeof(T) * P->n * P->dmax);
+  add(sizeof(T) * P->n * 256 * 2);
+  add(sizeof(double) * P->n * P->dmax);
+  add(sizeof(double) * P->n * 256 * 2);
+  const size_t mmax = (size_t)MAXP * chi, nmax = (size_t)MAXP * chi;
+  add(sizeof(T) * (size_t)chi * MAXP * MAXP * chi);  // T1
+  add(sizeof(T) * mmax * nmax);                     // M
+  add(sizeof(T) * nmax * chi);                      // V
+  add(sizeof(T) * mmax * chi);                      // US
+  add(sizeof(T) * MAXP * chi * chi * 2);            // carries
+  add(sizeof(T) * truncated_svd_work((int)mmax, (int)nmax, chi));
+  add(sizeof(double) * 4);
+  add(sizeof(int) * 4);
+  return b + 4096;
+}
+
+template <typename T>
+int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar, BoundaryBufs<T>& bb) {
+  const int chi = pl.chi;
+  const size_t sites = (size_t)(P->rows + 1) * P->cols;
+  bb.mps.A = ar.get<T>(sites * pl.stride);
+  bb.mps.site_stride = pl.stride;
+  bb.dimA_dev = ar.get<int>(sites * 3);
+  bb.mps.dimA = bb.dimA_dev;
+  bb.mps.lognorm = ar.get<double>(P->rows + 1);
+  bb.wt.w = ar.get<T>((size_t)P->n * P->dmax);
+  bb.wt.bL = ar.get<T>((size_t)P->n * 256);
+  bb.wt.bU = ar.get<T>((size_t)P->n * 256);
+  bb.wd.w = ar.get<double>((size_t)P->n * P->dmax);
+  bb.wd.bL = ar.get<double>((size_t)P->n * 256);
+  bb.wd.bU = ar.get<double>((size_t)P->n * 256);
+  const size_t mmax = (size_t)MAXP * chi, nmax = (size_t)MAXP * chi;
+  bb.T1 = ar.get<T>((size_t)chi * MAXP * MAXP * chi);
+  bb.M = ar.get<T>(mmax * nmax);
+  bb.V = ar.get<T>(nmax * chi);
+  bb.US = ar.get<T>(mmax * chi);
+  bb.carry[0] = ar.get<T>((size_t)MAXP * chi * chi);
+  bb.carry[1] = ar.get<T>((size_t)MAXP * chi * chi);
+  bb.svdw_elems = truncated_svd_work((int)mmax, (int)nmax, chi);
+  bb.svdw = ar.get<T>(bb.svdw_elems);
+  bb.s1 = ar.get<double>(4);
+  bb.degc = ar.get<int>(4);
+  if (!bb.degc) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * sites * 3, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
+  CK(cudaMemsetAsync(bb.degc, 0, sizeof(int) * 4, st));
+  return SPG_OK;
+}
+
+// Boundary MPSs B_r for r = rows-1 .. down_to (S2-S3).
+template <typename T>
+int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const Plan& pl, BoundaryBufs<T>& bb,
+                 int down_to) {
+  cudaStream_t st = ctx->stream;
+  const int cols = P->cols;
+  const double beta_u = prm->beta * std::ldexp(1.0, -P->shift);
+  CK(launch_weights<T>(P->tb, bb.wt, beta_u, st));
+  if (sizeof(T) != sizeof(double)) CK(launch_weights<double>(P->tb, bb.wd, beta_u, st));
+  // B_L: trivial sites (value 1)
+  CK(launch_set_strided<T>(bb.mps.A + (size_t)P->rows * cols * pl.stride, pl.stride, cols, T(1), st));
+  for (int r = P->rows - 1; r >= down_to; --r) {
+    CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, nullptr, st));
+    CK(cudaMemcpyAsync(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(launch_set_strided<T>(bb.carry[0], 1, 1, T(1), st));
+    int K = 1, cur = 0;
+    for (int j = cols - 1; j >= 0; --j) {
+      const int s = r * cols + j;
+      const int DL = P->dims[s * 8 + 0], DR = P->dims[s * 8 + 1], DU = P->dims[s * 8 + 2];
+      const int* din = &pl.dimA[((size_t)(r + 1) * cols + j) * 3];
+      const int p = din[0], chiL = din[1], chiR = din[2];
+      const T* Bsite = bb.mps.A + (size_t)((r + 1) * cols + j) * pl.stride;
+      T* out = bb.mps.A + (size_t)(r * cols + j) * pl.stride;
+      CK(launch_zip_matrix<T>(P->tb, bb.wt, Bsite, chiL, p, chiR, bb.carry[cur], DR, K, s, DL, DU, bb.T1, bb.M,
+                              st));
+      if (j == 0) {
+        CK(launch_zip_site0<T>(bb.M, DU, K, out, bb.mps.lognorm + r, st));
+      } else {
+        const int m = DL * chiL, n = DU * K;
+        const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
+        CK(truncated_svd<T>(bb.M, m, n, keep, prm->svd_iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
+                            bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st));
+        CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1,
+                               bb.mps.lognorm + r, st));
+        cur ^= 1;
+        K = keep;
+      }
+    }
+  }
+  return SPG_OK;
+}
+
+template <typename T>
+struct SearchBufs {
+  DevSearch ds;
+  DevBeamT<T> bt;
+};
+
+template <typename T>
+size_t search_bytes(const spg_problem* P, int cap, int chi) {
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
+  const size_t N = P->n, dmax = P->dmax;
+  for (int k = 0; k < 2; ++k) {
+    add(sizeof(uint16_t) * cap * N);
+    add(sizeof(int64_t) * cap);
+    add(sizeof(double) * cap);
+    add(sizeof(int) * cap);
+    add(sizeof(T) * cap * chi);
+  }
+  add(sizeof(int) * 2);
+  add(sizeof(double) * cap * dmax);
+  add(sizeof(int64_t) * cap * dmax);
+  add(sizeof(int) * cap * dmax);
+  add(sizeof(unsigned long long) * cap * KEYW);
+  add(sizeof(int) * cap * 3);
+  add(sizeof(unsigned) * 65536);
+  add(sizeof(unsigned long long) * 16);
+  add(sizeof(int) * 8);
+  add(sizeof(double) * 2);
+  add(sizeof(T) * cap * (P->cols + 1) * chi * MAXP);
+  return b + 4096;
+}
+
+template <typename T>
+int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar, SearchBufs<T>& sb) {
+  DevSearch& ds = sb.ds;
+  ds.cap = cap;
+  ds.N = P->n;
+  ds.dmax = P->dmax;
+  for (int k = 0; k < 2; ++k) {
+    ds.states[k] = ar.get<uint16_t>((size_t)cap * P->n);
+    ds.E[k] = ar.get<int64_t>(cap);
+    ds.logp[k] = ar.get<double>(cap);
+    ds.rid[k] = ar.get<int>(cap);
+    sb.bt.lenv[k] = ar.get<T>((size_t)cap * chi);
+  }
+  ds.n_beam = ar.get<int>(2);
+  ds.logc = ar.get<double>((size_t)cap * P->dmax);
+  ds.candE = ar.get<int64_t>((size_t)cap * P->dmax);
+  ds.win = ar.get<int>((size_t)cap * P->dmax);
+  ds.key = ar.get<unsigned long long>((size_t)cap * KEYW);
+  ds.rep = ar.get<int>(cap);
+  ds.nxt = ar.get<int>(cap);
+  ds.sel_list = ar.get<int>(cap);
+  ds.hist = ar.get<unsigned>(65536);
+  ds.sel_state = ar.get<unsigned long long>(16);
+  int* misc = ar.get<int>(8);
+  ds.sel_count = misc;
+  ds.done_ctr = (unsigned*)(misc + 1);
+  ds.near_ties = misc + 2;
+  ds.err = misc + 3;
+  ds.deg_cuts = misc + 4;
+  ds.candidates = ar.get<double>(2);
+  sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * MAXP);
+  sb.bt.chi = chi;
+  if (!sb.bt.R) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ds.hist, 0, sizeof(unsigned) * 65536, st));
+  CK(cudaMemsetAsync(misc, 0, sizeof(int) * 8, st));
+  CK(cudaMemsetAsync(sb.bt.R, 0, sizeof(T) * (size_t)cap * (P->cols + 1) * chi * MAXP, st));
+  CK(cudaMemsetAsync(sb.bt.lenv[0], 0, sizeof(T) * (size_t)cap * chi, st));
+  CK(cudaMemsetAsync(sb.bt.lenv[1], 0, sizeof(T) * (size_t)cap * chi, st));
+  return SPG_OK;
+}
+
+int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
+  if (!prm) return fail(ctx, SPG_EINVAL, "params is NULL");
+  if (!(prm->beta >= 0.0) || !std::isfinite(prm->beta)) return fail(ctx, SPG_EINVAL, "beta must be finite, >= 0");
+  if (prm->chi < 1 || prm->chi > SPG_MAX_CHI) return fail(ctx, SPG_EUNSUPPORTED, "chi outside 1..64");
+  if (prm->beam < 1 || prm->beam > SPG_MAX_BEAM) return fail(ctx, SPG_EUNSUPPORTED, "beam outside 1..4096");
+  if (prm->num_sweeps != 0) return fail(ctx, SPG_EUNSUPPORTED, "variational sweeps are not built in this version");
+  if (prm->precision != SPG_FP64 && prm->precision != SPG_MIXED) return fail(ctx, SPG_EINVAL, "bad precision");
+  if (prm->svd_iters < 0 || prm->svd_iters > 64) return fail(ctx, SPG_EINVAL, "svd_iters outside 0..64");
+  if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");
+  if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
+  if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
+  return SPG_OK;
+}
+
+template <typename T>
+int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result* R) {
+  cudaStream_t st = ctx->stream;
+  const int chi = prm->chi, cap = prm->beam;
+  Plan pl = make_plan(P, chi, 1);
+  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi);
+  int rc = ensure_arena(ctx, need);
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  SearchBufs<T> sb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
+  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb))) return rc;
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  CK(cudaEventRecord(R->ev[0], st));
+  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, 1))) return rc;
+  CK(cudaEventRecord(R->ev[1], st));
+  DevSearch& ds = sb.ds;
+  ds.deg_cuts = bb.degc;
+  const int cols = P->cols;
+  const double log_cut = prm->cut_off_prob > 0 ? std::log(prm->cut_off_prob) : -INFINITY;
+  int cur = 0;
+  CK(launch_reset_beam(ds, cur, st));
+  for (int s = 0; s < P->n; ++s) {
+    const int i = s / cols, j = s % cols;
+    if (j == 0) CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, i, ds, sb.bt, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    CK(launch_merge(P->tb, s, ds, cur, prm->merge, st));
+    CK(launch_select(P->tb, s, ds, cur, log_cut, st));
+    CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
+    cur ^= 1;
+  }
+  CK(launch_final(P->tb, ds, cur, R->d_states, R->d_E, R->d_logp, R->d_n, st));
+  CK(cudaMemcpyAsync(R->d_diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_diag + 2, bb.degc, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaEventRecord(R->ev[2], st));
+  return SPG_OK;
+}
+
+template <typename T>
+int debug_marginals_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int site, int n_prefix,
+                         const uint16_t* prefixes, double* out) {
+  cudaStream_t st = ctx->stream;
+  const int chi = prm->chi;
+  const int cap = std::max(1, n_prefix);
+  Plan pl = make_plan(P, chi, 1);
+  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi);
+  int rc = ensure_arena(ctx, need);
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  SearchBufs<T> sb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
+  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb))) return rc;
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  const int row = site / P->cols;
+  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, std::max(1, row + 1)))) return rc;
+  DevSearch& ds = sb.ds;
+  std::vector<uint16_t> st_h((size_t)cap * P->n, 0);
+  for (int k = 0; k < n_prefix; ++k)
+    for (int t = 0; t < site; ++t) st_h[(size_t)k * P->n + t] = prefixes[(size_t)k * site + t];
+  CK(cudaMemcpyAsync(ds.states[0], st_h.data(), sizeof(uint16_t) * st_h.size(), cudaMemcpyHostToDevice, st));
+  int nb[2] = {n_prefix, 0};
+  CK(cudaMemcpyAsync(ds.n_beam, nb, sizeof(nb), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ds.E[0], 0, sizeof(int64_t) * cap, st));
+  CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, row, ds, sb.bt, 0, st));
+  CK(launch_lenv_from_prefix<T>(P->tb, bb.mps, site, ds, sb.bt, 0, st));
+  CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, site, ds, sb.bt, 0, st));
+  const int d = P->d[site];
+  std::vector<double> lc((size_t)cap * P->dmax);
+  CK(cudaMemcpyAsync(lc.data(), ds.logc, sizeof(double) * lc.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < n_prefix; ++k)
+    for (int x = 0; x < d; ++x) out[(size_t)k * d + x] = lc[(size_t)k * P->dmax + x];
+  return SPG_OK;
+}
+
+template <typename T>
+int logz_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, double* log_z) {
+  cudaStream_t st = ctx->stream;
+  Plan pl = make_plan(P, prm->chi, 0);
+  int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl));
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, 0))) return rc;
+  double* dv = reinterpret_cast<double*>(bb.s1) + 2;
+  CK(launch_mps_value<T>(bb.mps, 0, P->cols, dv, st));
+  double h[2];
+  CK(cudaMemcpyAsync(h, bb.mps.lognorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 1, dv, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double beta_u = prm->beta * std::ldexp(1.0, -P->shift);
+  *log_z = h[0] + std::log(h[1]) - beta_u * P->min_sum;
+  return SPG_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+int spg_version(void) { return 100; }
+
+int spg_params_default(spg_params* p) {
+  if (!p) return SPG_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->beta = 1.0;
+  p->chi = 16;
+  p->num_sweeps = 0;
+  p->beam = 256;
+  p->precision = SPG_FP64;
+  p->cut_off_prob = 0.0;
+  p->svd_iters = 6;
+  p->merge = 1;
+  return SPG_OK;
+}
+
+int spg_create(spg_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SPG_EINVAL;
+  *out = nullptr;
+  spg_ctx* ctx = new (std::nothrow) spg_ctx();
+  if (!ctx) return SPG_ENOMEM;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete ctx;
+    return SPG_ECUDA;
+  }
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return SPG_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return SPG_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return SPG_OK;
+}
+
+void spg_destroy(spg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* spg_last_error(const spg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei, const int32_t* ej,
+                      const double* J, const double* h, const int32_t* cluster_of_spin, int32_t grid_rows,
+                      int32_t grid_cols, const int32_t* cluster_row, const int32_t* cluster_col,
+                      int32_t energy_shift, int32_t node_type, spg_problem** out) {
+  if (!ctx || !out) return SPG_EINVAL;
+  *out = nullptr;
+  if (n_spins <= 0 || n_edges < 0 || grid_rows <= 0 || grid_cols <= 0 || !cluster_of_spin || !cluster_row ||
+      !cluster_col || (n_edges > 0 && (!ei || !ej || !J)))
+    return fail(ctx, SPG_EINVAL, "bad sizes or NULL arrays");
+  if (energy_shift < 0 || energy_shift > 52) return fail(ctx, SPG_EINVAL, "energy_shift outside 0..52");
+  if (node_type != SPG_SQUARE && node_type != SPG_KING) return fail(ctx, SPG_EINVAL, "bad node_type");
+  if (grid_cols > SPG_MAX_COLS) return fail(ctx, SPG_EUNSUPPORTED, "grid wider than the built limit");
+  const int n = grid_rows * grid_cols;
+  std::vector<int> site_of_cluster(n, -1), used(n, 0);
+  for (int c = 0; c < n; ++c) {
+    const int r = cluster_row[c], cc = cluster_col[c];
+    if (r < 0 || r >= grid_rows || cc < 0 || cc >= grid_cols) return fail(ctx, SPG_EINVAL, "cluster outside grid");
+    const int s = r * grid_cols + cc;
+    if (used[s]) return fail(ctx, SPG_EINVAL, "two clusters on one grid cell");
+    used[s] = 1;
+    site_of_cluster[c] = s;
+  }
+  std::vector<int> site_of_spin(n_spins);
+  std::vector<std::vector<int>> spins(n);
+  for (int i = 0; i < n_spins; ++i) {
+    const int c = cluster_of_spin[i];
+    if (c < 0 || c >= n) return fail(ctx, SPG_EINVAL, "cluster id out of range");
+    site_of_spin[i] = site_of_cluster[c];
+    spins[site_of_cluster[c]].push_back(i);  // ascending spin index
+  }
+  const double scale = std::ldexp(1.0, energy_shift);
+  auto to_int = [&](double v, int64_t* o) {
+    const double x = v * scale;
+    if (!std::isfinite(x) || std::rint(x) != x || std::fabs(x) >= 4503599627370496.0) return false;
+    *o = (int64_t)x;
+    return true;
+  };
+  spg_problem* P = new (std::nothrow) spg_problem();
+  if (!P) return SPG_ENOMEM;
+  P->ctx = ctx;
+  P->rows = grid_rows;
+  P->cols = grid_cols;
+  P->n = n;
+  P->node_type = node_type;
+  P->shift = energy_shift;
+  P->d.resize(n);
+  int dmax = 1;
+  std::vector<int> pos(n_spins);
+  for (int s = 0; s < n; ++s) {
+    const int k = (int)spins[s].size();
+    if (k > 8) {
+      delete P;
+      return fail(ctx, SPG_EUNSUPPORTED, "cluster with more than 8 spins");
+    }
+    P->d[s] = 1 << k;
+    dmax = std::max(dmax, P->d[s]);
+    for (int q = 0; q < k; ++q) pos[spins[s][q]] = q;
+  }
+  P->dmax = dmax;
+  P->E.assign((size_t)n * dmax, 0);
+  auto spin = [](int x, int q) { return ((x >> q) & 1) ? 1 : -1; };
+  for (int i = 0; i < n_spins; ++i) {
+    int64_t hv = 0;
+    if (h && !to_int(h[i], &hv)) {
+      delete P;
+      return fail(ctx, SPG_EINEXACT, "h not on the 2^-energy_shift grid");
+    }
+    if (hv == 0) continue;
+    const int s = site_of_spin[i];
+    for (int x = 0; x < P->d[s]; ++x) P->E[(size_t)s * dmax + x] += hv * spin(x, pos[i]);
+  }
+  struct Coupler {
+    int pa, pb;
+    int64_t J;
+  };
+  std::map<std::pair<int, int>, std::vector<Coupler>> inter;
+  for (int e = 0; e < n_edges; ++e) {
+    const int a = ei[e], b = ej[e];
+    if (a < 0 || a >= n_spins || b < 0 || b >= n_spins || a == b) {
+      delete P;
+      return fail(ctx, SPG_EINVAL, "bad coupling endpoints");
+    }
+    int64_t Jv;
+    if (!to_int(J[e], &Jv)) {
+      delete P;
+      return fail(ctx, SPG_EINEXACT, "J not on the 2^-energy_shift grid");
+    }
+    int sa = site_of_spin[a], sb = site_of_spin[b];
+    if (sa == sb) {
+      for (int x = 0; x < P->d[sa]; ++x) P->E[(size_t)sa * dmax + x] += Jv * spin(x, pos[a]) * spin(x, pos[b]);
+      continue;
+    }
+    int pa = pos[a], pb = pos[b];
+    if (sa > sb) {
+      std::swap(sa, sb);
+      std::swap(pa, pb);
+    }
+    const int dr = std::abs(sa / grid_cols - sb / grid_cols), dc = std::abs(sa % grid_cols - sb % grid_cols);
+    const bool adj = node_type == SPG_SQUARE ? (dr + dc == 1) : (std::max(dr, dc) == 1);
+    if (!adj) {
+      delete P;
+      return fail(ctx, SPG_EINVAL, "coupling between clusters that are not grid neighbours");
+    }
+    inter[{sa, sb}].push_back({pa, pb, Jv});
+  }
+  // pairwise tables over the spins that carry couplers, then projectors
+  std::map<std::pair<int, int>, EdgeTab> edges;
+  for (auto& kv : inter) {
+    const int m = kv.first.first, nn = kv.first.second;
+    std::vector<int> Sm, Sn;
+    for (auto& c : kv.second) {
+      Sm.push_back(c.pa);
+      Sn.push_back(c.pb);
+    }
+    std::sort(Sm.begin(), Sm.end());
+    Sm.erase(std::unique(Sm.begin(), Sm.end()), Sm.end());
+    std::sort(Sn.begin(), Sn.end());
+    Sn.erase(std::unique(Sn.begin(), Sn.end()), Sn.end());
+    const int am = 1 << Sm.size(), an = 1 << Sn.size();
+    // sub-configuration of a state: bits of the involved spins, ascending
+    auto sub = [](int x, const std::vector<int>& S) {
+      int a = 0;
+      for (size_t q = 0; q < S.size(); ++q) a |= ((x >> S[q]) & 1) << q;
+      return a;
+    };
+    std::vector<int64_t> Tsub((size_t)am * an, 0);
+    for (auto& c : kv.second) {
+      const int qa = (int)(std::lower_bound(Sm.begin(), Sm.end(), c.pa) - Sm.begin());
+      const int qb = (int)(std::lower_bound(Sn.begin(), Sn.end(), c.pb) - Sn.begin());
+      for (int a = 0; a < am; ++a)
+        for (int b = 0; b < an; ++b) Tsub[(size_t)a * an + b] += c.J * spin(a, qa) * spin(b, qb);
+    }
+    EdgeTab sube;
+    if (!reduce_full(Tsub, am, an, sube)) {
+      delete P;
+      return fail(ctx, SPG_EUNSUPPORTED, "pairwise table with more than 16 distinct rows or columns");
+    }
+    // first occurrence over x ascending equals first occurrence over the
+    // sub-configuration ascending (the embedding keeps bit order)
+    EdgeTab e;
+    e.Dm = sube.Dm;
+    e.Dn = sube.Dn;
+    e.R = sube.R;
+    e.Pm.resize(P->d[m]);
+    e.Pn.resize(P->d[nn]);
+    for (int x = 0; x < P->d[m]; ++x) e.Pm[x] = sube.Pm[sub(x, Sm)];
+    for (int y = 0; y < P->d[nn]; ++y) e.Pn[y] = sube.Pn[sub(y, Sn)];
+    edges[{m, nn}] = e;
+  }
+  int rc = finish_problem(ctx, P, edges);
+  if (rc) {
+    spg_problem_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return SPG_OK;
+}
+
+int spg_problem_potts(spg_ctx* ctx, int32_t grid_rows, int32_t grid_cols, const int32_t* d, const int64_t* local_E,
+                      int32_t n_edges, const int32_t* em, const int32_t* en, const int64_t* pair_E,
+                      int32_t energy_shift, int32_t node_type, spg_problem** out) {
+  if (!ctx || !out) return SPG_EINVAL;
+  *out = nullptr;
+  if (grid_rows <= 0 || grid_cols <= 0 || !d || !local_E || n_edges < 0 || (n_edges > 0 && (!em || !en || !pair_E)))
+    return fail(ctx, SPG_EINVAL, "bad sizes or NULL arrays");
+  if (node_type != SPG_SQUARE && node_type != SPG_KING) return fail(ctx, SPG_EINVAL, "bad node_type");
+  if (grid_cols > SPG_MAX_COLS) return fail(ctx, SPG_EUNSUPPORTED, "grid wider than the built limit");
+  const int n = grid_rows * grid_cols;
+  spg_problem* P = new (std::nothrow) spg_problem();
+  if (!P) return SPG_ENOMEM;
+  P->ctx = ctx;
+  P->rows = grid_rows;
+  P->cols = grid_cols;
+  P->n = n;
+  P->node_type = node_type;
+  P->shift = energy_shift;
+  P->d.assign(d, d + n);
+  int dmax = 1;
+  for (int s = 0; s < n; ++s) {
+    if (d[s] < 1 || d[s] > SPG_MAX_STATES) {
+      delete P;
+      return fail(ctx, d[s] < 1 ? SPG_EINVAL : SPG_EUNSUPPORTED, "states per site outside 1..256");
+    }
+    dmax = std::max(dmax, d[s]);
+  }
+  P->dmax = dmax;
+  P->E.assign((size_t)n * dmax, 0);
+  size_t off = 0;
+  for (int s = 0; s < n; ++s)
+    for (int x = 0; x < d[s]; ++x) P->E[(size_t)s * dmax + x] = local_E[off++];
+  std::map<std::pair<int, int>, std::vector<int64_t>> full;
+  off = 0;
+  for (int k = 0; k < n_edges; ++k) {
+    int m = em[k], nn = en[k];
+    if (m < 0 || m >= n || nn < 0 || nn >= n || m == nn) {
+      delete P;
+      return fail(ctx, SPG_EINVAL, "bad edge endpoints");
+    }
+    const int dm = d[m], dn = d[nn];
+    const int64_t* T = pair_E + off;
+    off += (size_t)dm * dn;
+    const int dr = std::abs(m / grid_cols - nn / grid_cols), dc = std::abs(m % grid_cols - nn % grid_cols);
+    const bool adj = node_type == SPG_SQUARE ? (dr + dc == 1) : (std::max(dr, dc) == 1);
+    if (!adj) {
+      delete P;
+      return fail(ctx, SPG_EINVAL, "pairwise table between sites that are not grid neighbours");
+    }
+    const bool swap = m > nn;
+    const int a = swap ? nn : m, b = swap ? m : nn;
+    auto& acc = full[{a, b}];
+    if (acc.empty()) acc.assign((size_t)d[a] * d[b], 0);
+    for (int x = 0; x < dm; ++x)
+      for (int y = 0; y < dn; ++y) {
+        const int64_t v = T[(size_t)x * dn + y];
+        if (swap)
+          acc[(size_t)y * dm + x] += v;
+        else
+          acc[(size_t)x * dn + y] += v;
+      }
+  }
+  std::map<std::pair<int, int>, EdgeTab> edges;
+  for (auto& kv : full) {
+    EdgeTab e;
+    if (!reduce_full(kv.second, d[kv.first.first], d[kv.first.second], e)) {
+      delete P;
+      return fail(ctx, SPG_EUNSUPPORTED, "pairwise table with more than 16 distinct rows or columns");
+    }
+    edges[kv.first] = e;
+  }
+  int rc = finish_problem(ctx, P, edges);
+  if (rc) {
+    spg_problem_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return SPG_OK;
+}
+
+void spg_problem_destroy(spg_problem* P) {
+  if (!P) return;
+  if (P->dev) {
+    cudaSetDevice(P->ctx->device);
+    cudaStreamSynchronize(P->ctx->stream);
+    cudaFree(P->dev);
+  }
+  delete P;
+}
+
+int spg_problem_shape(const spg_problem* P, int32_t* rows, int32_t* cols, int32_t* d_per_site) {
+  if (!P) return SPG_EINVAL;
+  if (rows) *rows = P->rows;
+  if (cols) *cols = P->cols;
+  if (d_per_site)
+    for (int s = 0; s < P->n; ++s) d_per_site[s] = P->d[s];
+  return SPG_OK;
+}
+
+int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result** out) {
+  if (!ctx || !P || !out) return SPG_EINVAL;
+  *out = nullptr;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  spg_result* R = new (std::nothrow) spg_result();
+  if (!R) return SPG_ENOMEM;
+  R->ctx = ctx;
+  R->N = P->n;
+  R->cap = prm->beam;
+  cudaStream_t st = ctx->stream;
+  auto cleanup = [&](int code) {
+    spg_result_destroy(R);
+    return code;
+  };
+  for (int k = 0; k < 3; ++k)
+    if (cudaEventCreate(&R->ev[k]) != cudaSuccess) return cleanup(fail(ctx, SPG_ECUDA, "event create"));
+  if (cudaMallocAsync((void**)&R->d_states, sizeof(uint16_t) * (size_t)R->cap * R->N, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_E, sizeof(int64_t) * R->cap, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_logp, sizeof(double) * R->cap, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_n, sizeof(int) * 4, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_diag, sizeof(int) * 4, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
+  }
+  const long long l0 = launch_counter().load();
+  rc = prm->precision == SPG_FP64 ? solve_impl<double>(ctx, P, prm, R) : solve_impl<float>(ctx, P, prm, R);
+  R->launches = launch_counter().load() - l0;
+  if (rc) return cleanup(rc);
+  *out = R;
+  return SPG_OK;
+}
+
+static int fetch(spg_result* R) {
+  spg_ctx* ctx = R->ctx;
+  if (R->fetched) return SPG_OK;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventSynchronize(R->ev[2]));
+  CK(cudaMemcpy(&R->n, R->d_n, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaEventElapsedTime(&R->ms_boundary, R->ev[0], R->ev[1]));
+  CK(cudaEventElapsedTime(&R->ms_search, R->ev[1], R->ev[2]));
+  R->fetched = true;
+  return SPG_OK;
+}
+
+int spg_result_get(spg_result* R, int32_t* n_states, int32_t* n_sites, uint16_t* states, int64_t* energies_fixed,
+                   double* energies, double* log_probs) {
+  if (!R) return SPG_EINVAL;
+  spg_ctx* ctx = R->ctx;
+  int rc = fetch(R);
+  if (rc) return rc;
+  int diag[4];
+  CK(cudaMemcpy(diag, R->d_diag, sizeof(int) * 4, cudaMemcpyDeviceToHost));
+  if (n_states) *n_states = R->n;
+  if (n_sites) *n_sites = R->N;
+  if (states)
+    CK(cudaMemcpy(states, R->d_states, sizeof(uint16_t) * (size_t)R->n * R->N, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> E(R->n);
+  if (energies_fixed || energies) CK(cudaMemcpy(E.data(), R->d_E, sizeof(int64_t) * R->n, cudaMemcpyDeviceToHost));
+  if (energies_fixed) std::memcpy(energies_fixed, E.data(), sizeof(int64_t) * R->n);
+  if (energies)
+    for (int k = 0; k < R->n; ++k) energies[k] = (double)E[k];
+  if (log_probs) CK(cudaMemcpy(log_probs, R->d_logp, sizeof(double) * R->n, cudaMemcpyDeviceToHost));
+  if (diag[1] & ERR_ENERGY) return fail(ctx, SPG_ENUMERIC, "final energies disagree with the running energies");
+  if (diag[1] & ERR_KEY) return fail(ctx, SPG_EUNSUPPORTED, "merge key overflow");
+  return SPG_OK;
+}
+
+int spg_result_info(spg_result* R, spg_info* info) {
+  if (!R || !info) return SPG_EINVAL;
+  spg_ctx* ctx = R->ctx;
+  int rc = fetch(R);
+  if (rc) return rc;
+  int diag[4];
+  double cand[2];
+  CK(cudaMemcpy(diag, R->d_diag, sizeof(int) * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(cand, R->d_cand, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+  std::memset(info, 0, sizeof(*info));
+  info->n_states = R->n;
+  info->near_ties = diag[0];
+  info->error_flags = diag[1];
+  info->degenerate_cuts = diag[2];
+  info->ms_boundary = R->ms_boundary;
+  info->ms_search = R->ms_search;
+  info->candidates = cand[0];
+  info->boundary_lognorm = cand[1];
+  info->kernel_launches = R->launches;
+  return SPG_OK;
+}
+
+void spg_result_destroy(spg_result* R) {
+  if (!R) return;
+  cudaSetDevice(R->ctx->device);
+  cudaStream_t st = R->ctx->stream;
+  cudaStreamSynchronize(st);
+  if (R->d_states) cudaFreeAsync(R->d_states, st);
+  if (R->d_E) cudaFreeAsync(R->d_E, st);
+  if (R->d_logp) cudaFreeAsync(R->d_logp, st);
+  if (R->d_n) cudaFreeAsync(R->d_n, st);
+  if (R->d_diag) cudaFreeAsync(R->d_diag, st);
+  if (R->d_cand) cudaFreeAsync(R->d_cand, st);
+  for (int k = 0; k < 3; ++k)
+    if (R->ev[k]) cudaEventDestroy(R->ev[k]);
+  cudaGetLastError();
+  delete R;
+}
+
+int spg_debug_marginals(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int32_t site, int32_t n_prefix,
+                        const uint16_t* prefixes, double* log_marg) {
+  if (!ctx || !P || !log_marg) return SPG_EINVAL;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (site < 0 || site >= P->n || n_prefix < 1 || n_prefix > SPG_MAX_BEAM || (site > 0 && !prefixes))
+    return fail(ctx, SPG_EINVAL, "bad site or prefixes");
+  for (int k = 0; k < n_prefix; ++k)
+    for (int t = 0; t < site; ++t)
+      if (prefixes[(size_t)k * site + t] >= P->d[t]) return fail(ctx, SPG_EINVAL, "prefix state out of range");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return prm->precision == SPG_FP64
+             ? debug_marginals_impl<double>(ctx, P, prm, site, n_prefix, prefixes, log_marg)
+             : debug_marginals_impl<float>(ctx, P, prm, site, n_prefix, prefixes, log_marg);
+}
+
+int spg_log_partition(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, double* log_z) {
+  if (!ctx || !P || !log_z) return SPG_EINVAL;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return prm->precision == SPG_FP64 ? logz_impl<double>(ctx, P, prm, log_z) : logz_impl<float>(ctx, P, prm, log_z);
+}
+
+}  // extern "C"

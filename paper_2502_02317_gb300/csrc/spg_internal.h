@@ -1,0 +1,190 @@
+// Internal declarations shared by the host orchestration and the kernels of
+// libspg.  Not part of the C ABI.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spg {
+
+// Kernels enqueued by this library since load (every launcher adds its own).
+inline std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+inline void count_launches(int n) { launch_counter().fetch_add(n, std::memory_order_relaxed); }
+
+constexpr int MAXS = 256;   // states of one cluster
+constexpr int MAXP = 16;    // projected (reduced-table) dimension
+constexpr int MAXCHI = 64;  // boundary-MPS bond
+constexpr int KEYW = 4;     // 64-bit words of a packed merge key
+constexpr int SMAX = 128;   // columns of the truncation's working block
+#define SPG_MAXFINAL 4096   // final states ordered by the last kernel
+
+// Device error flags (OR-ed into DevSearch::err).
+enum : int {
+  ERR_ENERGY = 1,     // incremental energy != energy recomputed from the tables
+  ERR_NAN = 2,        // NaN / Inf in a normalisation
+  ERR_KEY = 4,        // a packed key overflowed its words
+};
+
+// Integer tables of the cluster factor graph (S1) in device memory.
+// Per site s (row-major), padded to dmax states and MAXP x MAXP tables:
+//   E[s][x]        local energy (int64, units of 2^-shift)
+//   PL/PR/PU/PD    projections of state x on the left/right/up/down edge
+//                  (row index for the site that comes first in row-major
+//                  order, column index for the other); 0 where no edge
+//   dims[s][8]     DL, DR, DU, DD: rows of the left/right/up/down reduced
+//                  tables (1 where no edge); NL, NU: columns of the left/up
+//                  tables (distinct PL / PU values); XIN: 1 if the site
+//                  has an edge to a later site (its state is part of the
+//                  merge key after it is fixed); 1 unused
+//   RL[s][a][b]    reduced table of the edge from the left neighbour,
+//                  a = left neighbour's PR, b = this site's PL
+//   RU[s][a][b]    the same for the edge from the site above
+//   xsL[s][..]     states of s grouped by PL (CSR with xoffL[s][0..MAXP])
+struct DevTables {
+  int rows, cols, n, dmax;
+  const int* d;
+  const int64_t* E;
+  const uint8_t *PL, *PR, *PU, *PD;
+  const int* dims;
+  const int64_t* RL;
+  const int64_t* RU;
+  const int16_t* xsL;
+  const int* xoffL;
+  const int* keys;   // [n][MAXKEY+1]: count, then sites of the reduced parent key
+  const int* kshift; // bits per packed state
+};
+constexpr int MAXKEY = 40;
+
+// Boltzmann pieces (S2): w[s][x], bL[s][a][b] = exp(-beta u (RL - min RL)),
+// bU likewise, all shifted so that every weight is <= 1.
+template <typename T>
+struct DevWeights {
+  T* w;
+  T* bL;
+  T* bU;
+};
+
+// Boundary MPSs: site (r, j) of B_r at A + (r*cols + j)*site_stride, laid out
+// [p][chiL][chiR] with the dims of dimA[(r*cols + j)*3 + {0,1,2}].
+template <typename T>
+struct DevMPS {
+  T* A;
+  size_t site_stride;
+  const int* dimA;  // device copy
+  double* lognorm;  // [rows+1]
+};
+
+// ------------------------------------------------------------------ kernels
+// All launchers enqueue on `st` and return cudaGetLastError().
+
+template <typename T>
+cudaError_t launch_weights(const DevTables& tb, DevWeights<T> wt, double beta_u, cudaStream_t st);
+
+// QR sweep of B (row r) to left-canonical form, in place; lognorm[r] += log
+// of the last site's norm.  Scratch: 2*MAXCHI*MAXCHI T.
+template <typename T>
+cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int* dimA_host,
+                                  T* scratch, cudaStream_t st);
+
+// M[(l,a),(u,k)] = sum_{x} bL[l,PL x] bU[u,PU x] w(x) sum_a' B[PD x][a][a'] C[PR x][a'][k]
+// for site (r, j) of the MPO applied to B_{r+1} (site j); carry C [DR][chiR][K].
+template <typename T>
+cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B, int chiL, int p,
+                              int chiR, const T* C, int DR, int K, int site, int DL, int DU,
+                              T* T1, T* M, cudaStream_t st);
+
+// Truncated SVD of M (m x n row-major): V (n x keep, column k = k-th right
+// singular vector) and US (m x keep); s1 = sigma_1 written to *s1_dev,
+// degenerate-cut flag OR-ed into *flag_dev.
+template <typename T>
+cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US,
+                          T* work, size_t work_elems, double* s1_dev, int* flag_dev, cudaStream_t st);
+size_t truncated_svd_work(int m, int n, int keep);
+
+// New site j of B_r ([DU][keep][K]) from V, next carry ([DL][chiL][keep]) from US / s1;
+// lognorm[r] += log s1.
+template <typename T>
+cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, int K, int keep,
+                             T* site_out, T* carry_out, const double* s1_dev, double* lognorm_r,
+                             cudaStream_t st);
+// Site 0: [DU][1][K] = M / ||M||; lognorm[r] += log ||M||.
+template <typename T>
+cudaError_t launch_zip_site0(const T* M, int DU, int K, T* site_out, double* lognorm_r, cudaStream_t st);
+
+// Value of an MPS whose physical dims are all 1 (row 0 closed from above).
+template <typename T>
+cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaStream_t st);
+
+// Generic small GEMM: C[m x n] = op(A) * B, row-major, op(A) = A or A^T.
+template <typename T>
+cudaError_t gemm(bool transA, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
+                 int ldc, cudaStream_t st);
+// C[m x n] = op(A) op(B), row-major; op(B) = B^T reads B stored n x k.
+template <typename T>
+cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb,
+                  T* C, int ldc, cudaStream_t st);
+// base[e * stride] = v for e < count.
+template <typename T>
+cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st);
+
+// ------------------------------------------------------------------ search
+struct DevSearch {
+  int cap;        // beam capacity
+  int N;          // sites
+  int dmax;
+  uint16_t* states[2];  // [cap][N]
+  int64_t* E[2];        // [cap]
+  double* logp[2];      // [cap]
+  int* rid[2];          // [cap] row-start index of the right environments
+  int* n_beam;          // [2] live count of each buffer
+  double* logc;         // [cap][dmax] log-conditionals
+  int64_t* candE;       // [cap][dmax]
+  int* win;             // [cap][dmax] winner parent of (class rep b, x), -1 otherwise
+  unsigned long long* key;  // [cap][KEYW]
+  int* rep;             // [cap] class representative
+  int* nxt;             // [cap] next member of the class (-1 at the end)
+  unsigned* hist;       // [65536]
+  unsigned long long* sel_state;  // select-state words
+  int* sel_list;        // [cap] selected candidate ids (b*dmax + x)
+  int* sel_count;
+  unsigned* done_ctr;
+  int* near_ties;
+  int* err;
+  double* candidates;   // running sum of live beam x d
+  int* deg_cuts;
+};
+
+template <typename T>
+struct DevBeamT {
+  T* lenv[2];  // [cap][chi]
+  T* R;        // [cap][cols+1][chi][MAXP]
+  int chi;
+};
+
+template <typename T>
+cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row,
+                              const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
+template <typename T>
+cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
+                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
+cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge,
+                         cudaStream_t st);
+cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, int cur,
+                          double log_cut, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds,
+                          DevBeamT<T> bt, int cur, cudaStream_t st);
+cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint16_t* out_states,
+                         int64_t* out_E, double* out_logp, int* out_n, cudaStream_t st);
+// Teacher forcing: fill beam buffer `cur` from host-given prefixes (already
+// copied to states[cur]); lenv from B_{i+1} sites 0..j-1.
+template <typename T>
+cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site,
+                                    const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
+cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st);
+
+}  // namespace spg
