@@ -172,6 +172,17 @@ int spg_debug_marginals(spg_ctx* ctx, const spg_problem* prob, const spg_params*
 int spg_log_partition(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm,
                       double* log_z);
 
+/* Per-kernel device timing (tracing aid).  spg_profile(ctx, 1) starts
+ * recording one CUDA event before every kernel the library launches;
+ * spg_profile_report waits for the context's stream and writes a JSON object
+ * {"kernel name": [launches, total_ms], ...} (times between consecutive
+ * events on the stream; the last kernel of the window is closed by an event
+ * recorded in the report call) into json_out (NUL-terminated, truncated to
+ * cap bytes), then clears the record.  spg_profile(ctx, 0) stops recording.
+ * Recording adds one event per launch; timed runs keep it off. */
+int spg_profile(spg_ctx* ctx, int enable);
+int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,8 +6,10 @@ other implementation behind it.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -70,6 +72,8 @@ def _load():
         "spg_result_destroy": (None, [P]),
         "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
         "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
+        "spg_profile": (C.c_int, [P, C.c_int]),
+        "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -79,6 +83,21 @@ def _load():
 
 
 lib = _load()
+
+
+# Handles still open at interpreter exit are released results -> problems ->
+# contexts, before the CUDA runtime is torn down.
+_LIVE = {"result": weakref.WeakSet(), "problem": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("result", "problem", "ctx"):
+        for obj in list(_LIVE[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
 
 
 class SpgError(RuntimeError):
@@ -109,6 +128,7 @@ class Context:
         if rc != SPG_OK:
             raise SpgError(rc, "spg_create failed")
         self.h = h
+        _LIVE["ctx"].add(self)
 
     def check(self, rc):
         if rc != SPG_OK:
@@ -129,6 +149,7 @@ class Context:
 class Problem:
     def __init__(self, ctx: Context, h):
         self.ctx, self.h = ctx, h
+        _LIVE["problem"].add(self)
         r, c = C.c_int32(), C.c_int32()
         ctx.check(lib.spg_problem_shape(h, C.byref(r), C.byref(c), None))
         self.rows, self.cols = r.value, c.value
@@ -180,6 +201,7 @@ def spg_problem_potts(ctx: Context, inst) -> Problem:
 class Result:
     def __init__(self, ctx, h):
         self.ctx, self.h = ctx, h
+        _LIVE["result"].add(self)
 
     def get(self):
         """(states [n, N] uint16, energies int64 [n], log_probs [n])"""
@@ -228,3 +250,15 @@ def spg_log_partition(ctx: Context, prob: Problem, prm: spg_params) -> float:
     v = C.c_double()
     ctx.check(lib.spg_log_partition(ctx.h, prob.h, C.byref(prm), C.byref(v)))
     return v.value
+
+
+def spg_profile(ctx: Context, enable: bool) -> None:
+    ctx.check(lib.spg_profile(ctx.h, int(bool(enable))))
+
+
+def spg_profile_report(ctx: Context) -> dict:
+    """{kernel: (launches, total_ms)} since profiling was enabled."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    ctx.check(lib.spg_profile_report(ctx.h, buf, len(buf)))
+    return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}

@@ -168,9 +168,16 @@ __global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_sm
       }
       __syncthreads();
       for (int i = tid; i < len; i += nt) {
-        T v = xk[i];
-        for (int c = 0; c < k; ++c) v -= red[32 + c] * V[(size_t)c * vld + i];
-        xk[i] = v;
+        T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
+        int c = 0;
+        for (; c + 3 < k; c += 4) {
+          v0 -= red[32 + c] * V[(size_t)c * vld + i];
+          v1 -= red[33 + c] * V[(size_t)(c + 1) * vld + i];
+          v2 -= red[34 + c] * V[(size_t)(c + 2) * vld + i];
+          v3 -= red[35 + c] * V[(size_t)(c + 3) * vld + i];
+        }
+        for (; c < k; ++c) v0 -= red[32 + c] * V[(size_t)c * vld + i];
+        xk[i] = (v0 + v1) + (v2 + v3);
       }
       for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
       __syncthreads();
@@ -193,18 +200,73 @@ __global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_sm
 // ---------------------------------------------------------------- left-canonical sweep
 // Sites of row r: [p][chiL][chiR] = matrix (p*chiL) x chiR.  For j < cols-1:
 // QR of site j, then site j+1 <- R site j+1.  The last site is normalised.
+// The chiR columns of a site are staged as contiguous vectors in `work`
+// (shared memory when they fit, else the global scratch) for the CGS2.
 template <typename T>
-__global__ void k_left_canonical(DevMPS<T> mps, int r, int cols) {
+__device__ void cgs2_vectors(T* V, int nvec, int len, T* Rout, T* sh_r, T* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const T rel_tol = qr_tol<T>();
+  for (int k = 0; k < nvec; ++k) {
+    T* xk = V + (size_t)k * len;
+    T part = T(0);
+    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+    const T n0 = sqrt(block_sum(part, red));
+    for (int c = tid; c < nvec; c += nt) sh_r[c] = T(0);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = wid; c < k; c += nw) {
+        const T* xc = V + (size_t)c * len;
+        T acc = T(0);
+        for (int i = lane; i < len; i += 32) acc += xc[i] * xk[i];
+        acc = warp_sum(acc);
+        if (lane == 0) red[32 + c] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < len; i += nt) {
+        T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
+        int c = 0;
+        for (; c + 3 < k; c += 4) {
+          v0 -= red[32 + c] * V[(size_t)c * len + i];
+          v1 -= red[33 + c] * V[(size_t)(c + 1) * len + i];
+          v2 -= red[34 + c] * V[(size_t)(c + 2) * len + i];
+          v3 -= red[35 + c] * V[(size_t)(c + 3) * len + i];
+        }
+        for (; c < k; ++c) v0 -= red[32 + c] * V[(size_t)c * len + i];
+        xk[i] = (v0 + v1) + (v2 + v3);
+      }
+      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
+      __syncthreads();
+    }
+    part = T(0);
+    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+    const T nk = sqrt(block_sum(part, red));
+    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+    const T inv = dep ? T(0) : T(1) / nk;
+    for (int i = tid; i < len; i += nt) xk[i] *= inv;
+    for (int c = tid; c < nvec; c += nt)
+      Rout[(size_t)c * nvec + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 32 + SMAX
   T* sh_r = red + 32 + SMAX;                // SMAX
   T* R = sh_r + SMAX;                       // MAXCHI * MAXCHI
+  T* W = use_smem ? R + MAXCHI * MAXCHI : gwork;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < cols - 1; ++j) {
     const int* dA = mps.dimA + (r * cols + j) * 3;
     const int p = dA[0], chiL = dA[1], chiR = dA[2];
+    const int len = p * chiL;
     T* A = mps.A + (size_t)(r * cols + j) * mps.site_stride;
-    cgs2_block(A, p * chiL, chiR, chiR, R, sh_r, red, qr_tol<T>());
+    for (int e = tid; e < len * chiR; e += nt) W[(size_t)(e % chiR) * len + e / chiR] = A[e];
+    __syncthreads();
+    cgs2_vectors(W, chiR, len, R, sh_r, red);
+    for (int e = tid; e < len * chiR; e += nt) A[e] = W[(size_t)(e % chiR) * len + e / chiR];
     __syncthreads();
     const int* dB = mps.dimA + (r * cols + j + 1) * 3;
     const int p2 = dB[0], chiL2 = dB[1], chiR2 = dB[2];  // chiL2 == chiR
@@ -403,7 +465,8 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
   }
   __syncthreads();
   const int se = s + (s & 1);
-  const T tol = sizeof(T) == 8 ? T(1e-15) : T(2e-7);
+  // rotate while |gamma| > s * eps * sqrt(alpha beta)
+  const T tol = (sizeof(T) == 8 ? T(2.22e-16) : T(1.19e-7)) * T(s > 8 ? s : 8);
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   __shared__ int s_conv;
   for (int sweep = 0; sweep < 60; ++sweep) {
@@ -575,26 +638,25 @@ __global__ void k_mps_value(DevMPS<T> mps, int r, int cols, double* out) {
 // ---------------------------------------------------------------- launchers
 template <typename T>
 cudaError_t launch_weights(const DevTables& tb, DevWeights<T> wt, double beta_u, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_weights", st);
   k_weights<T><<<tb.n, 256, 0, st>>>(tb, wt, beta_u);
   return cudaGetLastError();
 }
 
 template <typename T>
-static size_t lc_smem() {
-  return sizeof(T) * (32 + SMAX + SMAX + MAXCHI * MAXCHI);
-}
-
-template <typename T>
-cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T*, cudaStream_t st) {
-  const size_t sm = lc_smem<T>();
+cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T* scratch, cudaStream_t st) {
+  // staged site: (MAXP * chi) x chi elements
+  const size_t chi = (size_t)std::sqrt((double)(mps.site_stride / MAXP));
+  const size_t base = sizeof(T) * (32 + 2 * SMAX + MAXCHI * MAXCHI);
+  const size_t full = base + sizeof(T) * MAXP * chi * chi;
+  const int use_smem = full <= 200 * 1024 ? 1 : 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     attr = true;
   }
-  count_launches(1);
-  k_left_canonical<T><<<1, 512, sm, st>>>(mps, r, cols);
+  count_launches("k_left_canonical", st);
+  k_left_canonical<T><<<1, 1024, use_smem ? full : base, st>>>(mps, r, cols, scratch, use_smem);
   return cudaGetLastError();
 }
 
@@ -604,11 +666,11 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
                               cudaStream_t st) {
   const size_t total = (size_t)chiL * p * DR * K;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  count_launches(1);
+  count_launches("k_zip_T1", st);
   k_zip_T1<T><<<blocks, 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1);
   const int kchunk = K >= 8 ? 4 : 1;
   dim3 grid(chiL, (K + kchunk - 1) / kchunk);
-  count_launches(1);
+  count_launches("k_zip_M", st);
   k_zip_M<T><<<grid, 256, 0, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M);
   return cudaGetLastError();
 }
@@ -623,7 +685,7 @@ template <typename T>
 cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
                   int ldc, cudaStream_t st) {
   dim3 grid((n + 31) / 32, (m + 31) / 32);
-  count_launches(1);
+  count_launches("k_gemm", st);
   if (transA && transB)
     k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
   else if (transA)
@@ -637,7 +699,7 @@ cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int
 
 template <typename T>
 cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_set_strided", st);
   k_set_strided<T><<<(count + 255) / 256, 256, 0, st>>>(base, stride, count, v);
   return cudaGetLastError();
 }
@@ -664,7 +726,7 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
     cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     attr = true;
   }
-  count_launches(1);
+  count_launches("k_cgs2_rows", st);
   k_cgs2_rows<T><<<1, 1024, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
 }
 
@@ -682,7 +744,7 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   T* sig = VJ + (size_t)s * s;
   T* jbuf = sig + s + 64;
   const bool direct = n <= SMAX;
-  count_launches(1);
+  count_launches("k_fill_start", st);
   k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
   if (!direct) {
     cgs2_rows(Zt, s, n, (T*)nullptr, st);
@@ -705,7 +767,7 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
     cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     attr = true;
   }
-  count_launches(1);
+  count_launches("k_jacobi", st);
   k_jacobi<T><<<1, 1024, jsm, st>>>(R, s, RV, VJ, sig, keep, s1_dev, flag_dev, jbuf, use_smem);
   // V = Z VJ[:, :keep] = Zt^T VJ,  US = Q RV[:, :keep] = Yt^T RV
   gemm2<T>(true, false, n, keep, s, Zt, n, VJ, s, V, keep, st);
@@ -717,7 +779,7 @@ template <typename T>
 cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, int K, int keep, T* site_out,
                              T* carry_out, const double* s1_dev, double* lognorm_r, cudaStream_t st) {
   const int tot = DU * keep * K + DL * chiL * keep;
-  count_launches(1);
+  count_launches("k_zip_write", st);
   k_zip_write<T><<<std::min((tot + 255) / 256, 1024), 256, 0, st>>>(V, US, DL, chiL, DU, K, keep, site_out,
                                                                    carry_out, s1_dev, lognorm_r);
   return cudaGetLastError();
@@ -725,14 +787,14 @@ cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, 
 
 template <typename T>
 cudaError_t launch_zip_site0(const T* M, int DU, int K, T* site_out, double* lognorm_r, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_zip_site0", st);
   k_zip_site0<T><<<1, 1024, 0, st>>>(M, DU * K, site_out, lognorm_r);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_mps_value", st);
   k_mps_value<T><<<1, 64, 0, st>>>(mps, r, cols, out);
   return cudaGetLastError();
 }

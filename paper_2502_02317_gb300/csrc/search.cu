@@ -64,75 +64,100 @@ __device__ __forceinline__ unsigned long long ord_i64(int64_t v) {
 __device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { return tb.dims[s * 8 + k]; }
 
 // ---------------------------------------------------------------- S5 right environments
-// For beam element b (one block) at the start of row i, with B = B_{i+1}:
+// For beam element b at the start of row i, with B = B_{i+1}:
 //   R_L = 1;  R_j[a][l] = sum_x w(x) bL[l][PL x] bU[u_j][PU x]
 //                          sum_a' B_j[PD x][a][a'] R_{j+1}[a'][PR x]
 // stored at R[((b*(cols+1) + j)*chi + a)*MAXP + l], each R_j scaled to max |.| = 1.
+// One block handles G consecutive beam elements; the site B_j, shared by
+// all of them, is staged in shared memory once per column when it fits.
 template <typename T>
 __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int row, DevSearch ds,
-                             DevBeamT<T> bt, int cur) {
-  const int b = blockIdx.x;
-  if (b >= ds.n_beam[cur]) return;
+                             DevBeamT<T> bt, int cur, int G, int use_smem) {
+  const int nb = ds.n_beam[cur];
+  const int b0 = blockIdx.x * G;
+  if (b0 >= nb) return;
+  const int gn = min(G, nb - b0);
   extern __shared__ unsigned char smem_raw[];
-  T* Rn = reinterpret_cast<T*>(smem_raw);  // [chi][MAXP] next (j+1)
-  T* Y = Rn + MAXCHI * MAXP;               // [MAXP][chi]
-  T* red = Y + MAXP * MAXCHI;              // 32
+  T* Rn = reinterpret_cast<T*>(smem_raw);       // [G][chi*MAXP]
+  T* Y = Rn + (size_t)G * MAXCHI * MAXP;        // [MAXP][MAXCHI]
+  T* Rt = Y + MAXP * MAXCHI;                    // [MAXCHI][MAXP]
+  T* red = Rt + MAXCHI * MAXP;                  // 32
+  T* Bs = red + 32;                             // staged site (use_smem)
   const int cols = tb.cols, chi = bt.chi;
   const int tid = threadIdx.x, nt = blockDim.x;
-  T* Rb = bt.R + (size_t)b * (cols + 1) * chi * MAXP;
-  for (int e = tid; e < chi * MAXP; e += nt) {
-    const T v = e == 0 ? T(1) : T(0);
-    Rb[(size_t)cols * chi * MAXP + e] = v;
-    Rn[e] = v;
+  for (int g = 0; g < gn; ++g) {
+    const int b = b0 + g;
+    T* Rb = bt.R + (size_t)b * (cols + 1) * chi * MAXP;
+    for (int e = tid; e < chi * MAXP; e += nt) {
+      const T v = e == 0 ? T(1) : T(0);
+      Rb[(size_t)cols * chi * MAXP + e] = v;
+      Rn[(size_t)g * MAXCHI * MAXP + e] = v;
+    }
+    if (tid == 0) ds.rid[cur][b] = b;
+    for (int a = tid; a < chi; a += nt) bt.lenv[cur][(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
   }
-  if (tid == 0) ds.rid[cur][b] = b;
-  for (int a = tid; a < chi; a += nt) bt.lenv[cur][(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
   __syncthreads();
-  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
   for (int j = cols - 1; j >= 1; --j) {
     const int s = row * cols + j;
     const int* dA = mps.dimA + ((row + 1) * cols + j) * 3;
-    const int chiL = dA[1], chiR = dA[2];
-    const T* A = mps.A + (size_t)((row + 1) * cols + j) * mps.site_stride;
+    const int p = dA[0], chiL = dA[1], chiR = dA[2];
+    const T* Ag = mps.A + (size_t)((row + 1) * cols + j) * mps.site_stride;
+    if (use_smem)
+      for (int e = tid; e < p * chiL * chiR; e += nt) Bs[e] = Ag[e];
+    const T* A = use_smem ? Bs : Ag;
     const int DL = dim_of(tb, s, 0), NL = dim_of(tb, s, 4);
-    const int u = row > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + stb[s - cols]] : 0;
     const size_t so = (size_t)s * tb.dmax;
     const int* off = tb.xoffL + s * (MAXP + 1);
-    // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rn[a'][PR x]
-    for (int e = tid; e < NL * chiL; e += nt) {
-      const int h = e / chiL, a = e % chiL;
-      T acc = T(0);
-      for (int q = off[h]; q < off[h + 1]; ++q) {
-        const int x = tb.xsL[so + q];
-        const T c = wt.w[so + x] * wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
-        const T* arow = A + ((size_t)tb.PD[so + x] * chiL + a) * chiR;
-        const int pr = tb.PR[so + x];
-        T t = T(0);
-        for (int ap = 0; ap < chiR; ++ap) t += arow[ap] * Rn[ap * MAXP + pr];
-        acc += c * t;
+    __syncthreads();
+    for (int g = 0; g < gn; ++g) {
+      const int b = b0 + g;
+      const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+      const int u = row > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + stb[s - cols]] : 0;
+      const T* Rg = Rn + (size_t)g * MAXCHI * MAXP;
+      // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rg[a'][PR x]
+      for (int e = tid; e < NL * chiL; e += nt) {
+        const int h = e / chiL, a = e % chiL;
+        T acc = T(0);
+        for (int q = off[h]; q < off[h + 1]; ++q) {
+          const int x = tb.xsL[so + q];
+          const T c = wt.w[so + x] * wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
+          const T* arow = A + ((size_t)tb.PD[so + x] * chiL + a) * chiR;
+          const int pr = tb.PR[so + x];
+          T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+          int ap = 0;
+          for (; ap + 3 < chiR; ap += 4) {
+            t0 += arow[ap] * Rg[ap * MAXP + pr];
+            t1 += arow[ap + 1] * Rg[(ap + 1) * MAXP + pr];
+            t2 += arow[ap + 2] * Rg[(ap + 2) * MAXP + pr];
+            t3 += arow[ap + 3] * Rg[(ap + 3) * MAXP + pr];
+          }
+          for (; ap < chiR; ++ap) t0 += arow[ap] * Rg[ap * MAXP + pr];
+          acc += c * ((t0 + t1) + (t2 + t3));
+        }
+        Y[h * MAXCHI + a] = acc;
       }
-      Y[h * MAXCHI + a] = acc;
+      __syncthreads();
+      // R_j[a][l] = sum_h bL[l][h] Y[h][a] into Rt, then scaled to max |.| = 1
+      T mx = T(0);
+      for (int e = tid; e < chi * MAXP; e += nt) {
+        const int a = e / MAXP, l = e % MAXP;
+        T acc = T(0);
+        if (a < chiL && l < DL)
+          for (int h = 0; h < NL; ++h) acc += wt.bL[(size_t)s * 256 + l * 16 + h] * Y[h * MAXCHI + a];
+        Rt[e] = acc;
+        mx = max(mx, (T)fabs((double)acc));
+      }
+      mx = block_max(mx, red);  // contains __syncthreads: Rt complete
+      const T inv = mx > T(0) ? T(1) / mx : T(0);
+      T* Rj = bt.R + ((size_t)b * (cols + 1) + j) * chi * MAXP;
+      T* Rgw = Rn + (size_t)g * MAXCHI * MAXP;
+      for (int e = tid; e < chi * MAXP; e += nt) {
+        const T v = Rt[e] * inv;
+        Rj[e] = v;
+        Rgw[e] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    T mx = T(0);
-    T* Rj = Rb + (size_t)j * chi * MAXP;
-    for (int e = tid; e < chiL * DL; e += nt) {
-      const int a = e / DL, l = e % DL;
-      T acc = T(0);
-      for (int h = 0; h < NL; ++h) acc += wt.bL[(size_t)s * 256 + l * 16 + h] * Y[h * MAXCHI + a];
-      Rj[a * MAXP + l] = acc;
-      mx = max(mx, (T)fabs((double)acc));
-    }
-    mx = block_max(mx, red);
-    const T inv = mx > T(0) ? T(1) / mx : T(0);
-    __syncthreads();
-    for (int e = tid; e < chi * MAXP; e += nt) {
-      const int a = e / MAXP, l = e % MAXP;
-      T v = (a < chiL && l < DL) ? Rj[e] * inv : T(0);
-      Rj[e] = v;
-      Rn[e] = v;
-    }
-    __syncthreads();
   }
 }
 
@@ -639,28 +664,37 @@ __global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_state
 template <typename T>
 cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, const DevSearch& ds,
                               DevBeamT<T> bt, int cur, cudaStream_t st) {
-  const size_t sm = sizeof(T) * (2 * MAXCHI * MAXP + 32);
-  count_launches(1);
-  k_right_envs<T><<<ds.cap, 256, sm, st>>>(tb, wt, mps, row, ds, bt, cur);
+  const int G = sizeof(T) == 4 ? 8 : 4;
+  const size_t base = sizeof(T) * ((size_t)G * MAXCHI * MAXP + 2 * MAXP * MAXCHI + 32);
+  const size_t full = base + sizeof(T) * mps.site_stride;
+  const int use_smem = full <= 200 * 1024 ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+    attr = true;
+  }
+  count_launches("k_right_envs", st);
+  k_right_envs<T><<<(ds.cap + G - 1) / G, 512, use_smem ? full : base, st>>>(tb, wt, mps, row, ds, bt, cur, G,
+                                                                           use_smem);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
                                   const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_marginals", st);
   k_marginals<T><<<ds.cap, 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
   const int nbk = (ds.cap + 255) / 256;
-  count_launches(1);
+  count_launches("k_parent_keys", st);
   k_parent_keys<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
-  count_launches(1);
+  count_launches("k_classes", st);
   k_classes<<<nbk, 256, 0, st>>>(ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
-  count_launches(1);
+  count_launches("k_winners", st);
   k_winners<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>(tb, site, ds, cur);
   return cudaGetLastError();
 }
@@ -669,21 +703,21 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
                           cudaStream_t st) {
   const size_t tot = (size_t)ds.cap * ds.dmax;
   const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 1024);
-  count_launches(1);
+  count_launches("k_select_init", st);
   k_select_init<<<1, 1024, 0, st>>>(ds);
   if (log_cut > -INFINITY) {
-    count_launches(1);
+    count_launches("k_logp_max", st);
     k_logp_max<<<blocks, 1024, 0, st>>>(tb, site, ds, cur);
   }
   for (int pass = 0; pass < 12; ++pass) {
-    count_launches(1);
+    count_launches("k_select_pass", st);
     k_select_pass<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, pass, log_cut);
   }
-  count_launches(1);
+  count_launches("k_select_compact", st);
   k_select_compact<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, log_cut);
   int P = 1;
   while (P < ds.cap) P <<= 1;
-  count_launches(1);
+  count_launches("k_select_sort", st);
   k_select_sort<<<1, 1024, sizeof(unsigned long long) * P, st>>>(tb, site, ds, cur, cur ^ 1);
   return cudaGetLastError();
 }
@@ -691,7 +725,7 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
 template <typename T>
 cudaError_t launch_update(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds, DevBeamT<T> bt, int cur,
                           cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_update", st);
   k_update<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
   return cudaGetLastError();
 }
@@ -699,13 +733,13 @@ cudaError_t launch_update(const DevTables& tb, DevMPS<T> mps, int site, const De
 template <typename T>
 cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds,
                                     DevBeamT<T> bt, int cur, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_lenv_prefix", st);
   k_lenv_prefix<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
-  count_launches(1);
+  count_launches("k_reset_beam", st);
   k_reset_beam<<<1, 256, 0, st>>>(ds, cur);
   return cudaGetLastError();
 }
@@ -718,7 +752,7 @@ cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint
     cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     attr = true;
   }
-  count_launches(1);
+  count_launches("k_final", st);
   k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
   return cudaGetLastError();
 }

@@ -412,7 +412,7 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
   // B_L: trivial sites (value 1)
   CK(launch_set_strided<T>(bb.mps.A + (size_t)P->rows * cols * pl.stride, pl.stride, cols, T(1), st));
   for (int r = P->rows - 1; r >= down_to; --r) {
-    CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, nullptr, st));
+    CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, bb.T1, st));
     CK(cudaMemcpyAsync(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(launch_set_strided<T>(bb.carry[0], 1, 1, T(1), st));
     int K = 1, cur = 0;
@@ -1081,6 +1081,54 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* P, const spg_params* prm,
   if (rc) return rc;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
   return prm->precision == SPG_FP64 ? logz_impl<double>(ctx, P, prm, log_z) : logz_impl<float>(ctx, P, prm, log_z);
+}
+
+int spg_profile(spg_ctx* ctx, int enable) {
+  if (!ctx) return SPG_EINVAL;
+  KernelProfile& p = kernel_profile();
+  p.on = enable != 0;
+  return SPG_OK;
+}
+
+int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
+  if (!ctx || !json_out || cap == 0) return SPG_EINVAL;
+  KernelProfile& p = kernel_profile();
+  CK(cudaSetDevice(ctx->device));
+  std::map<std::string, std::pair<long long, double>> agg;
+  if (p.used > 0) {
+    cudaEvent_t end;
+    CK(cudaEventCreate(&end));
+    CK(cudaEventRecord(end, p.streams[p.used - 1]));
+    CK(cudaEventSynchronize(end));
+    for (size_t i = 0; i < p.used; ++i) {
+      float ms = 0.f;
+      cudaEvent_t nxt = i + 1 < p.used && p.streams[i + 1] == p.streams[i] ? p.pool[i + 1] : end;
+      if (cudaEventElapsedTime(&ms, p.pool[i], nxt) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;
+      }
+      auto& a = agg[p.names[i]];
+      a.first += 1;
+      a.second += ms;
+    }
+    cudaEventDestroy(end);
+  }
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+                  kv.second.second);
+    out += buf;
+    first = false;
+  }
+  out += "}";
+  std::strncpy(json_out, out.c_str(), cap - 1);
+  json_out[cap - 1] = 0;
+  p.names.clear();
+  p.streams.clear();
+  p.used = 0;
+  return SPG_OK;
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace spg {
@@ -13,7 +14,37 @@ inline std::atomic<long long>& launch_counter() {
   static std::atomic<long long> c{0};
   return c;
 }
-inline void count_launches(int n) { launch_counter().fetch_add(n, std::memory_order_relaxed); }
+
+// Opt-in per-kernel timing: while enabled, an event is recorded on the
+// launching stream just before every kernel, so that after a synchronize the
+// time between consecutive events is the device time of each kernel (kernels
+// on one stream run one after another).
+struct KernelProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<const char*> names;
+  std::vector<cudaStream_t> streams;
+  size_t used = 0;
+};
+inline KernelProfile& kernel_profile() {
+  static KernelProfile p;
+  return p;
+}
+
+inline void count_launches(const char* name, cudaStream_t st) {
+  launch_counter().fetch_add(1, std::memory_order_relaxed);
+  KernelProfile& p = kernel_profile();
+  if (!p.on) return;
+  if (p.used == p.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    p.pool.push_back(e);
+  }
+  cudaEventRecord(p.pool[p.used], st);
+  p.names.push_back(name);
+  p.streams.push_back(st);
+  ++p.used;
+}
 
 constexpr int MAXS = 256;   // states of one cluster
 constexpr int MAXP = 16;    // projected (reduced-table) dimension
@@ -85,7 +116,8 @@ template <typename T>
 cudaError_t launch_weights(const DevTables& tb, DevWeights<T> wt, double beta_u, cudaStream_t st);
 
 // QR sweep of B (row r) to left-canonical form, in place; lognorm[r] += log
-// of the last site's norm.  Scratch: 2*MAXCHI*MAXCHI T.
+// of the last site's norm.  Scratch: MAXP*chi*chi T (used when the staged
+// site does not fit in shared memory).
 template <typename T>
 cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int* dimA_host,
                                   T* scratch, cudaStream_t st);
