@@ -172,6 +172,21 @@ int spg_debug_marginals(spg_ctx* ctx, const spg_problem* prob, const spg_params*
 int spg_log_partition(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm,
                       double* log_z);
 
+/* Truncated SVD of one zipper matrix (the SVDTruncate step, Sec. 3.1; the
+ * same kernels the zipper uses): for M (m x n, row-major, FP64) return the
+ * keep largest singular triplets
+ *   V     : n x keep row-major, column k = k-th right singular vector
+ *   US    : m x keep row-major, column k = sigma_k times the k-th left one
+ *   sigma : keep values, descending
+ * All four are DEVICE pointers owned by the caller.  n <= 128 is exact
+ * (Jacobi on the QR of M); larger n uses `iters` rounds of subspace
+ * iteration on a block of min(n, max(2 keep, keep + 8), 128) columns.
+ * Limits: 1 <= m, n <= 1024, 1 <= keep <= min(64, m, n), 0 <= iters <= 64.
+ * Workspace comes from the context (allocated on first use).  Enqueued on
+ * the context's stream; returns after the stream has finished the work. */
+int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters,
+                 double* V, double* US, double* sigma);
+
 /* Per-kernel device timing (tracing aid).  spg_profile(ctx, 1) starts
  * recording one CUDA event before every kernel the library launches;
  * spg_profile_report waits for the context's stream and writes a JSON object

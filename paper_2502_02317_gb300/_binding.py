@@ -72,6 +72,7 @@ def _load():
         "spg_result_destroy": (None, [P]),
         "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
         "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
+        "spg_truncate": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
@@ -262,3 +263,18 @@ def spg_profile_report(ctx: Context) -> dict:
     buf = C.create_string_buffer(1 << 16)
     ctx.check(lib.spg_profile_report(ctx.h, buf, len(buf)))
     return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def spg_truncate(ctx: Context, M, keep: int, iters: int = 6):
+    """M: torch.float64 CUDA tensor (m x n, contiguous).  Returns device
+    tensors (V [n, keep], US [m, keep], sigma [keep])."""
+    import torch
+    m, n = M.shape
+    V = torch.empty((n, keep), dtype=torch.float64, device=M.device)
+    US = torch.empty((m, keep), dtype=torch.float64, device=M.device)
+    sig = torch.empty(keep, dtype=torch.float64, device=M.device)
+    torch.cuda.synchronize(M.device)
+    ctx.check(lib.spg_truncate(ctx.h, C.c_void_p(M.data_ptr()), m, n, keep, iters, C.c_void_p(V.data_ptr()),
+                               C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr())))
+    return V, US, sig
+

@@ -716,6 +716,11 @@ size_t truncated_svd_work(int m, int n, int) {
   return s * n + s * m + 5 * s * s + s + 64;
 }
 
+size_t truncated_svd_sigma_offset(int m, int n, int keep) {
+  const size_t s = (size_t)block_cols(n, keep);
+  return s * n + s * m + 3 * s * s;
+}
+
 template <typename T>
 static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   const size_t base = sizeof(T) * (32 + 2 * SMAX);

@@ -1083,6 +1083,31 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* P, const spg_params* prm,
   return prm->precision == SPG_FP64 ? logz_impl<double>(ctx, P, prm, log_z) : logz_impl<float>(ctx, P, prm, log_z);
 }
 
+int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters, double* V,
+                 double* US, double* sigma) {
+  if (!ctx || !M || !V || !US || !sigma) return SPG_EINVAL;
+  if (m < 1 || n < 1 || m > 1024 || n > 1024 || keep < 1 || keep > std::min(64, std::min(m, n)) || iters < 0 ||
+      iters > 64)
+    return fail(ctx, SPG_EINVAL, "spg_truncate: sizes outside the limits");
+  CK(cudaSetDevice(ctx->device));
+  const size_t work = truncated_svd_work(m, n, keep);
+  const size_t bytes = sizeof(double) * work + 1024;
+  int rc = ensure_arena(ctx, bytes);
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  double* w = ar.get<double>(work);
+  double* s1 = ar.get<double>(2);
+  int* flag = ar.get<int>(2);
+  if (!flag) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int) * 2, st));
+  CK(truncated_svd<double>(M, m, n, keep, iters, 0x5eedull, V, US, w, work, s1, flag, st));
+  CK(cudaMemcpyAsync(sigma, w + truncated_svd_sigma_offset(m, n, keep), sizeof(double) * keep,
+                     cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return SPG_OK;
+}
+
 int spg_profile(spg_ctx* ctx, int enable) {
   if (!ctx) return SPG_EINVAL;
   KernelProfile& p = kernel_profile();

@@ -136,6 +136,8 @@ template <typename T>
 cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US,
                           T* work, size_t work_elems, double* s1_dev, int* flag_dev, cudaStream_t st);
 size_t truncated_svd_work(int m, int n, int keep);
+// Offset (elements) of the sigma array inside the truncation's work buffer.
+size_t truncated_svd_sigma_offset(int m, int n, int keep);
 
 // New site j of B_r ([DU][keep][K]) from V, next carry ([DL][chiL][keep]) from US / s1;
 // lognorm[r] += log s1.
