@@ -187,6 +187,40 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* prob, const spg_params* p
 int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters,
                  double* V, double* US, double* sigma);
 
+/* spg_truncate_static -- the truncation of spg_truncate for callers that
+ * cannot allocate device memory.  The paper has no counterpart: it is an
+ * interface addition of this library.
+ *
+ * Who needs it: code whose device memory is all owned by its own pool
+ * allocator (a framework's caching allocator or an arena reserved at
+ * start-up, which leaves nothing to allocate and may forbid raw cudaMalloc),
+ * latency-critical loops that cannot pay the device synchronisation an
+ * allocation may cause, and plug-ins that may not grow their host's device
+ * footprint after initialisation.  This entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine; it needs no spg_ctx.
+ *
+ * Scratch: one fixed array of SPG_TRUNC_STATIC_SCRATCH_BYTES compiled into
+ * the library; every GPU on which the library is loaded holds it until the
+ * process exits.  Hence the limits m, n <= SPG_TRUNC_STATIC_MAX_DIM and
+ * keep <= SPG_TRUNC_STATIC_MAX_KEEP; a larger call returns
+ * SPG_EUNSUPPORTED without touching the device.  All calls share the array
+ * and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (two streams, or two host threads) race and give wrong results, so
+ * serialise them.  The first call on a device (that device current) looks
+ * up the array's device address once and caches it; make that first call
+ * before any stream capture.
+ *
+ * Arguments as spg_truncate (M, V, US, sigma are DEVICE pointers owned by
+ * the caller), on the current device; cuda_stream is a cudaStream_t (NULL:
+ * the legacy default stream).  Returns after the stream has finished the
+ * work.  SPG_EINVAL for NULL pointers or inconsistent sizes, SPG_ECUDA if a
+ * CUDA call fails. */
+#define SPG_TRUNC_STATIC_MAX_DIM 256
+#define SPG_TRUNC_STATIC_MAX_KEEP 32
+#define SPG_TRUNC_STATIC_SCRATCH_BYTES 1181696 /* 147712 doubles, 1.13 MiB */
+int spg_truncate_static(const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters, double* V,
+                        double* US, double* sigma, void* cuda_stream);
+
 /* Per-kernel device timing (tracing aid).  spg_profile(ctx, 1) starts
  * recording one CUDA event before every kernel the library launches;
  * spg_profile_report waits for the context's stream and writes a JSON object

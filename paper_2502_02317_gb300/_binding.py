@@ -73,6 +73,7 @@ def _load():
         "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
         "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
         "spg_truncate": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
+        "spg_truncate_static": (C.c_int, [P, I32, I32, I32, I32, P, P, P, P]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
@@ -278,3 +279,20 @@ def spg_truncate(ctx: Context, M, keep: int, iters: int = 6):
                                C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr())))
     return V, US, sig
 
+
+def spg_truncate_static(M, keep: int, iters: int = 6, stream=None):
+    """spg_truncate without any device allocation inside the library (the
+    scratch is a fixed array in the library image; m, n <= 256, keep <= 32).
+    Outputs are allocated here by torch, on the caller's side."""
+    import torch
+    m, n = M.shape
+    V = torch.empty((n, keep), dtype=torch.float64, device=M.device)
+    US = torch.empty((m, keep), dtype=torch.float64, device=M.device)
+    sig = torch.empty(keep, dtype=torch.float64, device=M.device)
+    torch.cuda.synchronize(M.device)
+    rc = lib.spg_truncate_static(C.c_void_p(M.data_ptr()), m, n, keep, iters, C.c_void_p(V.data_ptr()),
+                                 C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr()),
+                                 C.c_void_p(stream) if stream else None)
+    if rc != SPG_OK:
+        raise SpgError(rc, "spg_truncate_static failed")
+    return V, US, sig
