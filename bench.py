@@ -38,7 +38,8 @@ def make_instance(seed):
 
 
 def config_dict(extra=None):
-    c = {"workload": "chimera16x16_gauss_K44 (2048 spins, d=256), beta=1, chi=32, beam=1024",
+    L = WORKLOAD["L"]
+    c = {"workload": f"chimera{L}x{L}_gauss_K44 ({8 * L * L} spins, d=256), beta=1, chi=32, beam=1024",
          "L": WORKLOAD["L"], "spins": 8 * WORKLOAD["L"] ** 2, "cluster_states": 256, "beta": WORKLOAD["beta"],
          "chi": WORKLOAD["chi"], "beam": WORKLOAD["beam"], "couplings": "J~N(0,1), h~N(0,0.1) on 2^-24 grid",
          "l2": "flushed between timed steps (256 MiB write)"}
@@ -191,9 +192,13 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--L", type=int, default=None,
+                    help="grid side override (profiling of a smaller case of the same kernels)")
     ap.add_argument("--only-main", action="store_true",
                     help="timed solves only (no end-to-end or FP64 comparison runs): the ncu launch list")
     args = ap.parse_args()
+    if args.L:
+        WORKLOAD["L"] = args.L
     if args.impl == "reference":
         return run_reference(args)
 
@@ -288,7 +293,27 @@ def main():
         fp = {"tts_s": e0.elapsed_time(e1) / 1e3, "best_energy": int(E64[0]) * 2.0 ** -inst.energy_shift,
               "equal_best_energy": bool(int(E64[0]) == best), "speedup_mixed_vs_fp64": e0.elapsed_time(e1) / ms}
 
+    # one extra solve with per-kernel CUDA events (not part of the timed steps)
+    spg.spg_profile(ctx, True)
+    rp = spg.spg_solve(ctx, prob, prm)
+    rp.get()
+    kern = spg.spg_profile_report(ctx)
+    spg.spg_profile(ctx, False)
+    ktot = sum(v[1] for v in kern.values())
+    top = sorted(kern.items(), key=lambda kv: -kv[1][1])
+    kernels = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4),
+                   "avg_us": round(1e3 * v[1] / v[0], 2)} for k, v in top[:8]}
     peaks, src = measured_peaks()
+    clk_mhz = 2070.0
+    # ALU peaks from unit counts: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2 flop x clock
+    alu_peak = 152 * (128 if prec == spg.SPG_MIXED else 2) * 2 * clk_mhz * 1e6 / 1e12
+    name, (nl, ms_k, fl_k) = next((kv for kv in top if kv[1][2] > 0), top[0])
+    achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_source": f"derived: 152 SMs x {'128 FP32' if prec == spg.SPG_MIXED else '2 FP64'} FMA/clk x 2 x "
+                           f"{clk_mhz:.0f} MHz", "share_of_solve": round(ms_k / ktot, 4),
+            "flops_per_launch": fl_k / nl, "avg_launch_us": 1e3 * ms_k / nl}
     inf = infos[-1]
     line = {"metric": METRIC, "value": value, "unit": "beam states/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -300,7 +325,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": "beam states/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary(), "peaks_source": src}
-    line["roofline"] = None
+    line["roofline"] = roof
+    line["kernels"] = kernels
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(0)
     if rank == 0:

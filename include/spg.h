@@ -65,7 +65,8 @@ typedef struct {
   int32_t beam;        /* max_states: partial states kept (default 256)      */
   int32_t precision;   /* SPG_FP64 or SPG_MIXED (default SPG_FP64)           */
   double cut_off_prob; /* drop children with p < c * max p (default 0: off)  */
-  int32_t svd_iters;   /* subspace iterations of a large truncation (def. 6) */
+  int32_t svd_iters;   /* subspace iterations of a large truncation; -1 (the
+                          default): 6 in SPG_FP64, 4 in SPG_MIXED            */
   int32_t warm_start;  /* reserved, must be 0                                */
   uint64_t seed;       /* seed of the truncation's start block (default 0)   */
   int32_t merge;       /* 1: merge branches equal on the boundary of the
@@ -224,7 +225,8 @@ int spg_truncate_static(const double* M, int32_t m, int32_t n, int32_t keep, int
 /* Per-kernel device timing (tracing aid).  spg_profile(ctx, 1) starts
  * recording one CUDA event before every kernel the library launches;
  * spg_profile_report waits for the context's stream and writes a JSON object
- * {"kernel name": [launches, total_ms], ...} (times between consecutive
+ * {"kernel name": [launches, total_ms, algorithmic_flops], ...} (times
+ * between consecutive
  * events on the stream; the last kernel of the window is closed by an event
  * recorded in the report call) into json_out (NUL-terminated, truncated to
  * cap bytes), then clears the record.  spg_profile(ctx, 0) stops recording.

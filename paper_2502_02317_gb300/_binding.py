@@ -259,7 +259,7 @@ def spg_profile(ctx: Context, enable: bool) -> None:
 
 
 def spg_profile_report(ctx: Context) -> dict:
-    """{kernel: (launches, total_ms)} since profiling was enabled."""
+    """{kernel: (launches, total_ms, algorithmic_flops)} since profiling was enabled."""
     import json
     buf = C.create_string_buffer(1 << 16)
     ctx.check(lib.spg_profile_report(ctx.h, buf, len(buf)))

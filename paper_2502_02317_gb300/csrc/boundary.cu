@@ -129,6 +129,8 @@ __device__ void cgs2_block(T* X, int rows, int ncols, int ld, T* Rout, T* sh_r /
   }
 }
 
+__device__ __forceinline__ int wid_of() { return (int)(threadIdx.x >> 5); }
+
 template <typename T>
 __host__ __device__ constexpr T qr_tol() {
   return sizeof(T) == 8 ? T(1e-13) : T(1e-5);
@@ -464,6 +466,14 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
     Vc[(size_t)c * s + i] = (i == c) ? T(1) : T(0);
   }
   __syncthreads();
+  T* nrm = sig;  // squared column norms, kept current by every rotation
+  for (int c = wid_of(); c < s; c += (int)(blockDim.x >> 5)) {
+    T a = T(0);
+    for (int q = (int)(threadIdx.x & 31); q < s; q += 32) a += Rc[(size_t)c * s + q] * Rc[(size_t)c * s + q];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) nrm[c] = a;
+  }
+  __syncthreads();
   const int se = s + (s & 1);
   // rotate while |gamma| > s * eps * sqrt(alpha beta)
   const T tol = (sizeof(T) == 8 ? T(2.22e-16) : T(1.19e-7)) * T(s > 8 ? s : 8);
@@ -484,16 +494,10 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
         }
         T* ci = Rc + (size_t)i * s;
         T* cj = Rc + (size_t)j * s;
-        T al = T(0), be = T(0), ga = T(0);
-        for (int q = lane; q < s; q += 32) {
-          const T x = ci[q], y = cj[q];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        T ga = T(0);
+        for (int q = lane; q < s; q += 32) ga += ci[q] * cj[q];
         ga = warp_sum(ga);
+        const T al = nrm[i], be = nrm[j];
         if (al == T(0) || be == T(0)) continue;
         if (fabs((double)ga) <= (double)tol * sqrt((double)al * (double)be)) continue;
         if (lane == 0) s_conv = 0;
@@ -503,13 +507,23 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
         const T sn = c * t;
         T* vi = Vc + (size_t)i * s;
         T* vj = Vc + (size_t)j * s;
+        T ni = T(0), nj = T(0);
         for (int q = lane; q < s; q += 32) {
           const T x = ci[q], y = cj[q];
-          ci[q] = c * x - sn * y;
-          cj[q] = sn * x + c * y;
+          const T xn = c * x - sn * y, yn = sn * x + c * y;
+          ci[q] = xn;
+          cj[q] = yn;
+          ni += xn * xn;
+          nj += yn * yn;
           const T u = vi[q], v = vj[q];
           vi[q] = c * u - sn * v;
           vj[q] = sn * u + c * v;
+        }
+        ni = warp_sum(ni);
+        nj = warp_sum(nj);
+        if (lane == 0) {
+          nrm[i] = ni;
+          nrm[j] = nj;
         }
       }
       __syncthreads();
@@ -666,7 +680,7 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
                               cudaStream_t st) {
   const size_t total = (size_t)chiL * p * DR * K;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  count_launches("k_zip_T1", st);
+  count_launches("k_zip_T1", st, 2.0 * chiL * p * DR * K * chiR);
   k_zip_T1<T><<<blocks, 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1);
   const int kchunk = K >= 8 ? 4 : 1;
   dim3 grid(chiL, (K + kchunk - 1) / kchunk);
@@ -685,7 +699,7 @@ template <typename T>
 cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
                   int ldc, cudaStream_t st) {
   dim3 grid((n + 31) / 32, (m + 31) / 32);
-  count_launches("k_gemm", st);
+  count_launches("k_gemm", st, 2.0 * m * n * k);
   if (transA && transB)
     k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
   else if (transA)
@@ -704,9 +718,13 @@ cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStrea
   return cudaGetLastError();
 }
 
+// Columns of the subspace-iteration block: FP64 keeps a wide block (fast
+// convergence, reference accuracy); FP32 resolves ~1e-7 relative anyway, so a
+// narrower block of keep + 16 columns suffices and halves the work.
+template <typename T>
 static int block_cols(int n, int keep) {
   if (n <= SMAX) return n;
-  int s = std::max(2 * keep, keep + 8);
+  int s = sizeof(T) == 8 ? std::max(2 * keep, keep + 8) : keep + 16;
   return std::min(std::min(s, n), SMAX);
 }
 
@@ -717,7 +735,7 @@ size_t truncated_svd_work(int m, int n, int) {
 }
 
 size_t truncated_svd_sigma_offset(int m, int n, int keep) {
-  const size_t s = (size_t)block_cols(n, keep);
+  const size_t s = (size_t)block_cols<double>(n, keep);
   return s * n + s * m + 3 * s * s;
 }
 
@@ -731,7 +749,7 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
     cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     attr = true;
   }
-  count_launches("k_cgs2_rows", st);
+  count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
   k_cgs2_rows<T><<<1, 1024, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
 }
 
@@ -740,7 +758,7 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
 template <typename T>
 cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US, T* work,
                           size_t, double* s1_dev, int* flag_dev, cudaStream_t st) {
-  const int s = block_cols(n, keep);
+  const int s = block_cols<T>(n, keep);
   T* Zt = work;
   T* Yt = Zt + (size_t)n * s;
   T* R = Yt + (size_t)m * s;

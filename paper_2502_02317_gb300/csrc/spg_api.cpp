@@ -430,7 +430,8 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
       } else {
         const int m = DL * chiL, n = DU * K;
         const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
-        CK(truncated_svd<T>(bb.M, m, n, keep, prm->svd_iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
+        const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 4);
+        CK(truncated_svd<T>(bb.M, m, n, keep, iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
                             bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st));
         CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1,
                                bb.mps.lognorm + r, st));
@@ -523,7 +524,7 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (prm->beam < 1 || prm->beam > SPG_MAX_BEAM) return fail(ctx, SPG_EUNSUPPORTED, "beam outside 1..4096");
   if (prm->num_sweeps != 0) return fail(ctx, SPG_EUNSUPPORTED, "variational sweeps are not built in this version");
   if (prm->precision != SPG_FP64 && prm->precision != SPG_MIXED) return fail(ctx, SPG_EINVAL, "bad precision");
-  if (prm->svd_iters < 0 || prm->svd_iters > 64) return fail(ctx, SPG_EINVAL, "svd_iters outside 0..64");
+  if (prm->svd_iters < -1 || prm->svd_iters > 64) return fail(ctx, SPG_EINVAL, "svd_iters outside -1..64");
   if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
   if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
@@ -648,7 +649,7 @@ int spg_params_default(spg_params* p) {
   p->beam = 256;
   p->precision = SPG_FP64;
   p->cut_off_prob = 0.0;
-  p->svd_iters = 6;
+  p->svd_iters = -1;
   p->merge = 1;
   return SPG_OK;
 }
@@ -1119,7 +1120,11 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
   if (!ctx || !json_out || cap == 0) return SPG_EINVAL;
   KernelProfile& p = kernel_profile();
   CK(cudaSetDevice(ctx->device));
-  std::map<std::string, std::pair<long long, double>> agg;
+  struct Agg {
+    long long n = 0;
+    double ms = 0.0, flops = 0.0;
+  };
+  std::map<std::string, Agg> agg;
   if (p.used > 0) {
     cudaEvent_t end;
     CK(cudaEventCreate(&end));
@@ -1133,8 +1138,9 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
         ms = 0.f;
       }
       auto& a = agg[p.names[i]];
-      a.first += 1;
-      a.second += ms;
+      a.n += 1;
+      a.ms += ms;
+      a.flops += p.flops[i];
     }
     cudaEventDestroy(end);
   }
@@ -1142,8 +1148,8 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
   bool first = true;
   for (auto& kv : agg) {
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
-                  kv.second.second);
+    std::snprintf(buf, sizeof(buf), "%s\"%s\": [%lld, %.6f, %.6e]", first ? "" : ", ", kv.first.c_str(), kv.second.n,
+                  kv.second.ms, kv.second.flops);
     out += buf;
     first = false;
   }
@@ -1152,6 +1158,7 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
   json_out[cap - 1] = 0;
   p.names.clear();
   p.streams.clear();
+  p.flops.clear();
   p.used = 0;
   return SPG_OK;
 }

@@ -24,6 +24,7 @@ struct KernelProfile {
   std::vector<cudaEvent_t> pool;
   std::vector<const char*> names;
   std::vector<cudaStream_t> streams;
+  std::vector<double> flops;  // algorithmic flops of each launch (0: not counted)
   size_t used = 0;
 };
 inline KernelProfile& kernel_profile() {
@@ -31,7 +32,7 @@ inline KernelProfile& kernel_profile() {
   return p;
 }
 
-inline void count_launches(const char* name, cudaStream_t st) {
+inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0) {
   launch_counter().fetch_add(1, std::memory_order_relaxed);
   KernelProfile& p = kernel_profile();
   if (!p.on) return;
@@ -43,6 +44,7 @@ inline void count_launches(const char* name, cudaStream_t st) {
   cudaEventRecord(p.pool[p.used], st);
   p.names.push_back(name);
   p.streams.push_back(st);
+  p.flops.push_back(flops);
   ++p.used;
 }
 

@@ -27,7 +27,7 @@ def test_params_defaults_and_struct_layout():
     import paper_2502_02317_gb300 as spg
     from paper_2502_02317_gb300 import _binding as b
     p = spg.params()
-    assert (p.beta, p.chi, p.beam, p.num_sweeps, p.precision, p.merge, p.svd_iters) == (1.0, 16, 256, 0, 0, 1, 6)
+    assert (p.beta, p.chi, p.beam, p.num_sweeps, p.precision, p.merge, p.svd_iters) == (1.0, 16, 256, 0, 0, 1, -1)
     assert ctypes.sizeof(b.spg_params) == 80
     assert ctypes.sizeof(b.spg_info) == 56
     assert spg.lib.spg_version() == 100
