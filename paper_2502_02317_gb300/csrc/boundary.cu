@@ -74,61 +74,6 @@ __global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u) {
 }
 
 // ---------------------------------------------------------------- CGS2 QR
-// In-place classical Gram-Schmidt with one re-orthogonalisation ("twice is
-// enough") of X [rows x ncols] (row-major, leading dim ld).  Q overwrites X;
-// R (ncols x ncols, upper, non-negative diagonal) goes to Rout if non-null.
-// A column whose remainder falls below rel_tol of its original norm is set
-// to zero with R_kk = 0 (numerically dependent; the product Q R keeps the
-// matrix to that tolerance).  One block, blockDim.x a multiple of 32.
-template <typename T>
-__device__ void cgs2_block(T* X, int rows, int ncols, int ld, T* Rout, T* sh_r /* >= ncols */,
-                           T* red, T rel_tol) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int k = 0; k < ncols; ++k) {
-    // original norm
-    T part = T(0);
-    for (int i = tid; i < rows; i += nt) {
-      T v = X[(size_t)i * ld + k];
-      part += v * v;
-    }
-    const T n0 = sqrt(block_sum(part, red));
-    for (int i = tid; i < ncols; i += nt) sh_r[i] = T(0);
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      // r_c = X[:, c] . X[:, k] for c < k: one warp per c
-      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-      for (int c = wid; c < k; c += nw) {
-        T acc = T(0);
-        for (int i = lane; i < rows; i += 32) acc += X[(size_t)i * ld + c] * X[(size_t)i * ld + k];
-        acc = warp_sum(acc);
-        if (lane == 0) red[32 + c] = acc;
-      }
-      __syncthreads();
-      for (int i = tid; i < rows; i += nt) {
-        T v = X[(size_t)i * ld + k];
-        for (int c = 0; c < k; ++c) v -= red[32 + c] * X[(size_t)i * ld + c];
-        X[(size_t)i * ld + k] = v;
-      }
-      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
-      __syncthreads();
-    }
-    part = T(0);
-    for (int i = tid; i < rows; i += nt) {
-      T v = X[(size_t)i * ld + k];
-      part += v * v;
-    }
-    const T nk = sqrt(block_sum(part, red));
-    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
-    const T inv = dep ? T(0) : T(1) / nk;
-    for (int i = tid; i < rows; i += nt) X[(size_t)i * ld + k] *= inv;
-    if (Rout) {
-      for (int c = tid; c < ncols; c += nt)
-        Rout[(size_t)c * ncols + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
-    }
-    __syncthreads();
-  }
-}
-
 __device__ __forceinline__ int wid_of() { return (int)(threadIdx.x >> 5); }
 
 template <typename T>
@@ -136,65 +81,117 @@ __host__ __device__ constexpr T qr_tol() {
   return sizeof(T) == 8 ? T(1e-13) : T(1e-5);
 }
 
-// CGS2 on the ROWS of X (nvec vectors of length len, row stride ld), each
-// vector contiguous so every access is coalesced; the vectors are staged in
-// shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_block:
-// x_k = sum_{c <= k} R[c][k] q_c.
+// CGS2 core on nvec contiguous vectors of length len (stride ld) in place:
+// per vector two projection passes against the earlier (orthonormal)
+// vectors, then normalisation.  The squared norm is accumulated in the second
+// update and the original norm follows from Pythagoras (||x||^2 = sum r^2 +
+// ||x'||^2), so a vector costs five barriers.  A vector whose remainder falls
+// below rel_tol of its norm is numerically dependent: zeroed, R_kk = 0.
+// R (nvec x nvec, row-major): x_k = sum_{c <= k} R[c][k] q_c.
+// Scratch: red >= 64 + 2 * SMAX T.
 template <typename T>
-__global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
-  extern __shared__ unsigned char smem_raw[];
-  T* red = reinterpret_cast<T*>(smem_raw);  // 32 + SMAX
-  T* sh_r = red + 32 + SMAX;                // SMAX
-  T* V = use_smem ? sh_r + SMAX : X;
-  const int vld = use_smem ? len : ld;
+__device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  T* rc = red + 64;          // coefficients of the current pass [SMAX]
+  T* racc = rc + SMAX;       // accumulated coefficients [SMAX]
   const T rel_tol = qr_tol<T>();
-  if (use_smem)
-    for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
-  __syncthreads();
   for (int k = 0; k < nvec; ++k) {
-    T* xk = V + (size_t)k * vld;
+    T* xk = V + (size_t)k * ld;
     T part = T(0);
-    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
-    const T n0 = sqrt(block_sum(part, red));
-    for (int c = tid; c < nvec; c += nt) sh_r[c] = T(0);
-    __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
-      for (int c = wid; c < k; c += nw) {
-        const T* xc = V + (size_t)c * vld;
-        T acc = T(0);
-        for (int i = lane; i < len; i += 32) acc += xc[i] * xk[i];
-        acc = warp_sum(acc);
-        if (lane == 0) red[32 + c] = acc;
+      // dots <q_c, x_k>: warp w takes c = w, w + nw, ... up to four at a time
+      // (independent accumulators, x_k loaded once per element)
+      for (int c0 = wid; c0 < k; c0 += 4 * nw) {
+        const int c1 = c0 + nw, c2 = c0 + 2 * nw, c3 = c0 + 3 * nw;
+        const T* x0 = V + (size_t)c0 * ld;
+        const T* x1 = V + (size_t)(c1 < k ? c1 : c0) * ld;
+        const T* x2 = V + (size_t)(c2 < k ? c2 : c0) * ld;
+        const T* x3 = V + (size_t)(c3 < k ? c3 : c0) * ld;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        for (int i = lane; i < len; i += 32) {
+          const T v = xk[i];
+          a0 += x0[i] * v;
+          a1 += x1[i] * v;
+          a2 += x2[i] * v;
+          a3 += x3[i] * v;
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        a3 = warp_sum(a3);
+        if (lane == 0) {
+          rc[c0] = a0;
+          racc[c0] = pass == 0 ? a0 : racc[c0] + a0;
+          if (c1 < k) {
+            rc[c1] = a1;
+            racc[c1] = pass == 0 ? a1 : racc[c1] + a1;
+          }
+          if (c2 < k) {
+            rc[c2] = a2;
+            racc[c2] = pass == 0 ? a2 : racc[c2] + a2;
+          }
+          if (c3 < k) {
+            rc[c3] = a3;
+            racc[c3] = pass == 0 ? a3 : racc[c3] + a3;
+          }
+        }
       }
       __syncthreads();
       for (int i = tid; i < len; i += nt) {
         T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
         int c = 0;
         for (; c + 3 < k; c += 4) {
-          v0 -= red[32 + c] * V[(size_t)c * vld + i];
-          v1 -= red[33 + c] * V[(size_t)(c + 1) * vld + i];
-          v2 -= red[34 + c] * V[(size_t)(c + 2) * vld + i];
-          v3 -= red[35 + c] * V[(size_t)(c + 3) * vld + i];
+          v0 -= rc[c] * V[(size_t)c * ld + i];
+          v1 -= rc[c + 1] * V[(size_t)(c + 1) * ld + i];
+          v2 -= rc[c + 2] * V[(size_t)(c + 2) * ld + i];
+          v3 -= rc[c + 3] * V[(size_t)(c + 3) * ld + i];
         }
-        for (; c < k; ++c) v0 -= red[32 + c] * V[(size_t)c * vld + i];
-        xk[i] = (v0 + v1) + (v2 + v3);
+        for (; c < k; ++c) v0 -= rc[c] * V[(size_t)c * ld + i];
+        const T v = (v0 + v1) + (v2 + v3);
+        xk[i] = v;
+        if (pass == 1) part += v * v;
       }
-      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
-      __syncthreads();
+      if (k == 0 && pass == 0) {  // no projection for the first vector
+        for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+        break;
+      }
+      if (pass == 0) __syncthreads();
     }
-    part = T(0);
-    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
-    const T nk = sqrt(block_sum(part, red));
+    part = warp_sum(part);
+    if (lane == 0) red[wid] = part;
+    __syncthreads();
+    T nk2 = T(0);
+    for (int w = 0; w < nw; ++w) nk2 += red[w];
+    T r2 = T(0);
+    for (int c = 0; c < k; ++c) r2 += racc[c] * racc[c];
+    const T nk = sqrt(nk2);
+    const T n0 = sqrt(nk2 + r2);
     const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
     const T inv = dep ? T(0) : T(1) / nk;
     for (int i = tid; i < len; i += nt) xk[i] *= inv;
     if (Rout)
       for (int c = tid; c < nvec; c += nt)
-        Rout[(size_t)c * nvec + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
+        Rout[(size_t)c * nvec + k] = c < k ? racc[c] : (c == k ? (dep ? T(0) : nk) : T(0));
     __syncthreads();
   }
+}
+
+// CGS2 on the ROWS of X (nvec vectors of length len, row stride ld), each
+// vector contiguous so every access is coalesced; the vectors are staged in
+// shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_core:
+// x_k = sum_{c <= k} R[c][k] q_c.
+template <typename T>
+__global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
+  T* V = use_smem ? red + 64 + 2 * SMAX : X;
+  const int vld = use_smem ? len : ld;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (use_smem)
+    for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
+  __syncthreads();
+  cgs2_core(V, nvec, len, vld, Rout, red);
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
 }
@@ -205,59 +202,10 @@ __global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_sm
 // The chiR columns of a site are staged as contiguous vectors in `work`
 // (shared memory when they fit, else the global scratch) for the CGS2.
 template <typename T>
-__device__ void cgs2_vectors(T* V, int nvec, int len, T* Rout, T* sh_r, T* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const T rel_tol = qr_tol<T>();
-  for (int k = 0; k < nvec; ++k) {
-    T* xk = V + (size_t)k * len;
-    T part = T(0);
-    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
-    const T n0 = sqrt(block_sum(part, red));
-    for (int c = tid; c < nvec; c += nt) sh_r[c] = T(0);
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int c = wid; c < k; c += nw) {
-        const T* xc = V + (size_t)c * len;
-        T acc = T(0);
-        for (int i = lane; i < len; i += 32) acc += xc[i] * xk[i];
-        acc = warp_sum(acc);
-        if (lane == 0) red[32 + c] = acc;
-      }
-      __syncthreads();
-      for (int i = tid; i < len; i += nt) {
-        T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
-        int c = 0;
-        for (; c + 3 < k; c += 4) {
-          v0 -= red[32 + c] * V[(size_t)c * len + i];
-          v1 -= red[33 + c] * V[(size_t)(c + 1) * len + i];
-          v2 -= red[34 + c] * V[(size_t)(c + 2) * len + i];
-          v3 -= red[35 + c] * V[(size_t)(c + 3) * len + i];
-        }
-        for (; c < k; ++c) v0 -= red[32 + c] * V[(size_t)c * len + i];
-        xk[i] = (v0 + v1) + (v2 + v3);
-      }
-      for (int c = tid; c < k; c += nt) sh_r[c] += red[32 + c];
-      __syncthreads();
-    }
-    part = T(0);
-    for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
-    const T nk = sqrt(block_sum(part, red));
-    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
-    const T inv = dep ? T(0) : T(1) / nk;
-    for (int i = tid; i < len; i += nt) xk[i] *= inv;
-    for (int c = tid; c < nvec; c += nt)
-      Rout[(size_t)c * nvec + k] = c < k ? sh_r[c] : (c == k ? (dep ? T(0) : nk) : T(0));
-    __syncthreads();
-  }
-}
-
-template <typename T>
 __global__ void k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
-  T* red = reinterpret_cast<T*>(smem_raw);  // 32 + SMAX
-  T* sh_r = red + 32 + SMAX;                // SMAX
-  T* R = sh_r + SMAX;                       // MAXCHI * MAXCHI
+  T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
+  T* R = red + 64 + 2 * SMAX;               // MAXCHI * MAXCHI
   T* W = use_smem ? R + MAXCHI * MAXCHI : gwork;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < cols - 1; ++j) {
@@ -267,7 +215,7 @@ __global__ void k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int u
     T* A = mps.A + (size_t)(r * cols + j) * mps.site_stride;
     for (int e = tid; e < len * chiR; e += nt) W[(size_t)(e % chiR) * len + e / chiR] = A[e];
     __syncthreads();
-    cgs2_vectors(W, chiR, len, R, sh_r, red);
+    cgs2_core(W, chiR, len, len, R, red);
     for (int e = tid; e < len * chiR; e += nt) A[e] = W[(size_t)(e % chiR) * len + e / chiR];
     __syncthreads();
     const int* dB = mps.dimA + (r * cols + j + 1) * 3;
@@ -661,7 +609,7 @@ template <typename T>
 cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T* scratch, cudaStream_t st) {
   // staged site: (MAXP * chi) x chi elements
   const size_t chi = (size_t)std::sqrt((double)(mps.site_stride / MAXP));
-  const size_t base = sizeof(T) * (32 + 2 * SMAX + MAXCHI * MAXCHI);
+  const size_t base = sizeof(T) * (64 + 2 * SMAX + MAXCHI * MAXCHI);
   const size_t full = base + sizeof(T) * MAXP * chi * chi;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
   static bool attr = false;
@@ -741,7 +689,7 @@ size_t truncated_svd_sigma_offset(int m, int n, int keep) {
 
 template <typename T>
 static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
-  const size_t base = sizeof(T) * (32 + 2 * SMAX);
+  const size_t base = sizeof(T) * (64 + 2 * SMAX);
   const size_t full = base + sizeof(T) * (size_t)nvec * len;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
   static bool attr = false;
@@ -749,8 +697,10 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
     cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     attr = true;
   }
+  // one thread per element when the vectors are short, at least 4 warps
+  const int threads = std::max(128, std::min(1024, (len + 31) / 32 * 32));
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
-  k_cgs2_rows<T><<<1, 1024, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
+  k_cgs2_rows<T><<<1, threads, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
 }
 
 // Work layout: Zt [s x n], Yt [s x m] (rows = the block's column vectors),

@@ -83,6 +83,10 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
   T* Rt = Y + MAXP * MAXCHI;                    // [MAXCHI][MAXP]
   T* red = Rt + MAXCHI * MAXP;                  // 32
   T* Bs = red + 32;                             // staged site (use_smem)
+  __shared__ T sw[MAXS], sbU[256], sbL[256];
+  __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
+  __shared__ int16_t sxs[MAXS];
+  __shared__ int soff[MAXP + 1];
   const int cols = tb.cols, chi = bt.chi;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int g = 0; g < gn; ++g) {
@@ -102,12 +106,29 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
     const int* dA = mps.dimA + ((row + 1) * cols + j) * 3;
     const int p = dA[0], chiL = dA[1], chiR = dA[2];
     const T* Ag = mps.A + (size_t)((row + 1) * cols + j) * mps.site_stride;
+    // staged transposed, Bs[(s*chiR + a')*chiL + a]: consecutive lanes (a)
+    // then read consecutive words (no bank conflicts)
     if (use_smem)
-      for (int e = tid; e < p * chiL * chiR; e += nt) Bs[e] = Ag[e];
-    const T* A = use_smem ? Bs : Ag;
+      for (int e = tid; e < p * chiL * chiR; e += nt) {
+        const int ap = e % chiR, a = (e / chiR) % chiL, sg = e / (chiR * chiL);
+        Bs[((size_t)sg * chiR + ap) * chiL + a] = Ag[e];
+      }
     const int DL = dim_of(tb, s, 0), NL = dim_of(tb, s, 4);
     const size_t so = (size_t)s * tb.dmax;
-    const int* off = tb.xoffL + s * (MAXP + 1);
+    const int d = tb.d[s];
+    // this column's tables, staged once for all G beam elements
+    for (int x = tid; x < d; x += nt) {
+      sw[x] = wt.w[so + x];
+      sPU[x] = tb.PU[so + x];
+      sPD[x] = tb.PD[so + x];
+      sPR[x] = tb.PR[so + x];
+      sxs[x] = tb.xsL[so + x];
+    }
+    for (int e = tid; e < 256; e += nt) {
+      sbU[e] = wt.bU[(size_t)s * 256 + e];
+      sbL[e] = wt.bL[(size_t)s * 256 + e];
+    }
+    for (int e = tid; e <= MAXP; e += nt) soff[e] = tb.xoffL[s * (MAXP + 1) + e];
     __syncthreads();
     for (int g = 0; g < gn; ++g) {
       const int b = b0 + g;
@@ -118,20 +139,24 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
       for (int e = tid; e < NL * chiL; e += nt) {
         const int h = e / chiL, a = e % chiL;
         T acc = T(0);
-        for (int q = off[h]; q < off[h + 1]; ++q) {
-          const int x = tb.xsL[so + q];
-          const T c = wt.w[so + x] * wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
-          const T* arow = A + ((size_t)tb.PD[so + x] * chiL + a) * chiR;
-          const int pr = tb.PR[so + x];
+        for (int q = soff[h]; q < soff[h + 1]; ++q) {
+          const int x = sxs[q];
+          const T c = sw[x] * sbU[u * 16 + sPU[x]];
+          const int pr = sPR[x];
+          // element (a, a') of slice PD x: Bs[(PD*chiR + a')*chiL + a] when
+          // staged, else A[(PD*chiL + a)*chiR + a']
+          const size_t sa = use_smem ? (size_t)chiL : 1;
+          const T* arow = use_smem ? Bs + (size_t)sPD[x] * chiR * chiL + a
+                                   : Ag + ((size_t)sPD[x] * chiL + a) * chiR;
           T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
           int ap = 0;
           for (; ap + 3 < chiR; ap += 4) {
-            t0 += arow[ap] * Rg[ap * MAXP + pr];
-            t1 += arow[ap + 1] * Rg[(ap + 1) * MAXP + pr];
-            t2 += arow[ap + 2] * Rg[(ap + 2) * MAXP + pr];
-            t3 += arow[ap + 3] * Rg[(ap + 3) * MAXP + pr];
+            t0 += arow[ap * sa] * Rg[ap * MAXP + pr];
+            t1 += arow[(ap + 1) * sa] * Rg[(ap + 1) * MAXP + pr];
+            t2 += arow[(ap + 2) * sa] * Rg[(ap + 2) * MAXP + pr];
+            t3 += arow[(ap + 3) * sa] * Rg[(ap + 3) * MAXP + pr];
           }
-          for (; ap < chiR; ++ap) t0 += arow[ap] * Rg[ap * MAXP + pr];
+          for (; ap < chiR; ++ap) t0 += arow[ap * sa] * Rg[ap * MAXP + pr];
           acc += c * ((t0 + t1) + (t2 + t3));
         }
         Y[h * MAXCHI + a] = acc;
@@ -143,7 +168,7 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
         const int a = e / MAXP, l = e % MAXP;
         T acc = T(0);
         if (a < chiL && l < DL)
-          for (int h = 0; h < NL; ++h) acc += wt.bL[(size_t)s * 256 + l * 16 + h] * Y[h * MAXCHI + a];
+          for (int h = 0; h < NL; ++h) acc += sbL[l * 16 + h] * Y[h * MAXCHI + a];
         Rt[e] = acc;
         mx = max(mx, (T)fabs((double)acc));
       }
@@ -251,28 +276,69 @@ __global__ void k_parent_keys(DevTables tb, int site, DevSearch ds, int cur, int
   for (int w = 0; w < KEYW; ++w) ds.key[(size_t)b * KEYW + w] = k[w];
 }
 
+// Classes by sorting (key, index) in one block (bitonic, in shared memory):
+// within a run of equal keys the first index is the representative and the
+// next index is the member that follows.
 __global__ void k_classes(DevSearch ds, int cur, int merge) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ unsigned long long cls_smem[];
   const int nb = ds.n_beam[cur];
-  if (b >= nb) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (!merge) {
-    ds.rep[b] = b;
-    ds.nxt[b] = -1;
+    for (int b = tid; b < nb; b += nt) {
+      ds.rep[b] = b;
+      ds.nxt[b] = -1;
+    }
     return;
   }
-  const unsigned long long* kb = ds.key + (size_t)b * KEYW;
-  const unsigned long long k0 = kb[0], k1 = kb[1], k2 = kb[2], k3 = kb[3];
-  int rep = b, nx = -1;
-  for (int o = 0; o < nb; ++o) {
-    if (o == b) continue;
-    const unsigned long long* ko = ds.key + (size_t)o * KEYW;
-    if (ko[0] == k0 && ko[1] == k1 && ko[2] == k2 && ko[3] == k3) {
-      if (o < rep) rep = o;
-      if (o > b && nx < 0) nx = o;
+  int P = 1;
+  while (P < nb) P <<= 1;
+  unsigned long long* K = cls_smem;           // [P][KEYW]
+  int* idx = reinterpret_cast<int*>(K + (size_t)P * KEYW);  // [P]
+  for (int e = tid; e < P; e += nt) {
+    for (int w = 0; w < KEYW; ++w) K[(size_t)e * KEYW + w] = e < nb ? ds.key[(size_t)e * KEYW + w] : ~0ull;
+    idx[e] = e < nb ? e : 0x7fffffff;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int e = tid; e < P; e += nt) {
+        const int o = e ^ jj;
+        if (o <= e) continue;
+        const bool up = (e & k) == 0;
+        // compare (key, idx) of e and o
+        int cmp = 0;
+        for (int w = KEYW - 1; w >= 0 && cmp == 0; --w) {
+          const unsigned long long a = K[(size_t)e * KEYW + w], b = K[(size_t)o * KEYW + w];
+          cmp = a < b ? -1 : (a > b ? 1 : 0);
+        }
+        if (cmp == 0) cmp = idx[e] < idx[o] ? -1 : (idx[e] > idx[o] ? 1 : 0);
+        if ((cmp > 0) == up) {
+          for (int w = 0; w < KEYW; ++w) {
+            const unsigned long long t = K[(size_t)e * KEYW + w];
+            K[(size_t)e * KEYW + w] = K[(size_t)o * KEYW + w];
+            K[(size_t)o * KEYW + w] = t;
+          }
+          const int t = idx[e];
+          idx[e] = idx[o];
+          idx[o] = t;
+        }
+      }
+      __syncthreads();
     }
   }
-  ds.rep[b] = rep;
-  ds.nxt[b] = nx;
+  for (int e = tid; e < nb; e += nt) {
+    int f = e;
+    while (f > 0) {
+      bool same = true;
+      for (int w = 0; w < KEYW; ++w) same &= K[(size_t)(f - 1) * KEYW + w] == K[(size_t)e * KEYW + w];
+      if (!same) break;
+      --f;
+    }
+    bool nsame = e + 1 < nb;
+    for (int w = 0; w < KEYW && nsame; ++w) nsame = K[(size_t)(e + 1) * KEYW + w] == K[(size_t)e * KEYW + w];
+    ds.rep[idx[e]] = idx[f];
+    ds.nxt[idx[e]] = nsame ? idx[e + 1] : -1;
+  }
 }
 
 // For each (class representative b, x): the member with the lowest
@@ -468,16 +534,45 @@ __global__ void k_select_compact(DevTables tb, int site, DevSearch ds, int cur, 
   const size_t tot = (size_t)ds.cap * ds.dmax;
   const unsigned long long thr[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
   const unsigned long long maxkey = ds.sel_state[6];
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
-    if (!k.valid) continue;
-    if (key_le(k, thr)) {
-      const int pos = atomicAdd(ds.sel_count, 1);
-      if (pos < ds.cap) ds.sel_list[pos] = (int)c;
-      atomicMin(ds.sel_state + 7, ord_f64(k.lp));
-    } else {
-      atomicMax(ds.sel_state + 8, ord_f64(k.lp) + 1ull);  // +1 keeps 0 = "none"
+  unsigned long long min_sel = ~0ull, max_rej = 0ull;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t c0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // every lane runs the same number of iterations so that the warp-wide
+  // ballot below sees all 32 lanes
+  const size_t iters = (tot + stride - 1) / stride;
+  const int lane = threadIdx.x & 31;
+  for (size_t it = 0; it < iters; ++it) {
+    const size_t c = c0 + it * stride;
+    bool take = false;
+    CandKey k;
+    k.valid = false;
+    if (c < tot) k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
+    if (k.valid) {
+      if (key_le(k, thr)) {
+        take = true;
+        min_sel = min(min_sel, ord_f64(k.lp));
+      } else {
+        max_rej = max(max_rej, ord_f64(k.lp) + 1ull);  // +1 keeps 0 = "none"
+      }
     }
+    const unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (mask) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(ds.sel_count, __popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (take) {
+        const int pos = base + __popc(mask & ((1u << lane) - 1u));
+        if (pos < ds.cap) ds.sel_list[pos] = (int)c;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    min_sel = min(min_sel, __shfl_xor_sync(0xffffffffu, min_sel, o));
+    max_rej = max(max_rej, __shfl_xor_sync(0xffffffffu, max_rej, o));
+  }
+  if (lane == 0) {
+    if (min_sel != ~0ull) atomicMin(ds.sel_state + 7, min_sel);
+    if (max_rej != 0ull) atomicMax(ds.sel_state + 8, max_rej);
   }
 }
 
@@ -691,8 +786,16 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
   const int nbk = (ds.cap + 255) / 256;
   count_launches("k_parent_keys", st);
   k_parent_keys<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
+  int P = 1;
+  while (P < ds.cap) P <<= 1;
+  const int csm = (int)((sizeof(unsigned long long) * KEYW + sizeof(int)) * P);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
   count_launches("k_classes", st);
-  k_classes<<<nbk, 256, 0, st>>>(ds, cur, merge);
+  k_classes<<<1, 1024, csm, st>>>(ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
   count_launches("k_winners", st);
   k_winners<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>(tb, site, ds, cur);
