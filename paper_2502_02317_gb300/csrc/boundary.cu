@@ -703,6 +703,11 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   k_cgs2_rows<T><<<1, threads, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
 }
 
+template <typename T>
+void launch_cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
+  cgs2_rows<T>(X, nvec, len, Rout, st);
+}
+
 // Work layout: Zt [s x n], Yt [s x m] (rows = the block's column vectors),
 // R, RV, VJ [s x s], sig [s], Jacobi spill buffer [2 s s].
 template <typename T>
@@ -786,7 +791,8 @@ cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaSt
   template cudaError_t gemm<T>(bool, int, int, int, const T*, int, const T*, int, T*, int, cudaStream_t);   \
   template cudaError_t gemm2<T>(bool, bool, int, int, int, const T*, int, const T*, int, T*, int,         \
                                 cudaStream_t);                                                          \
-  template cudaError_t launch_set_strided<T>(T*, size_t, int, T, cudaStream_t);
+  template cudaError_t launch_set_strided<T>(T*, size_t, int, T, cudaStream_t);                          \
+  template void launch_cgs2_rows<T>(T*, int, int, T*, cudaStream_t);
 
 SPG_INST(double)
 SPG_INST(float)

@@ -339,6 +339,8 @@ struct BoundaryBufs {
   size_t svdw_elems;
   double* s1;
   int* degc;
+  T* swork;
+  double* sdbl;
 };
 
 template <typename T>
@@ -363,6 +365,8 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
   add(sizeof(T) * truncated_svd_work((int)mmax, (int)nmax, chi));
   add(sizeof(double) * 4);
   add(sizeof(int) * 4);
+  add(sizeof(T) * sweep_work_elems<T>(P->cols, chi));
+  add(sizeof(double) * 4);
   return b + 4096;
 }
 
@@ -392,7 +396,9 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.svdw = ar.get<T>(bb.svdw_elems);
   bb.s1 = ar.get<double>(4);
   bb.degc = ar.get<int>(4);
-  if (!bb.degc) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  bb.swork = ar.get<T>(sweep_work_elems<T>(P->cols, chi));
+  bb.sdbl = ar.get<double>(4);
+  if (!bb.sdbl) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * sites * 3, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
@@ -439,6 +445,9 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
         K = keep;
       }
     }
+    if (prm->num_sweeps > 0)
+      CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, r, cols, pl.dimA.data(), P->dims.data(), prm->num_sweeps,
+                               bb.swork, bb.sdbl, st));
   }
   return SPG_OK;
 }
@@ -522,7 +531,7 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (!(prm->beta >= 0.0) || !std::isfinite(prm->beta)) return fail(ctx, SPG_EINVAL, "beta must be finite, >= 0");
   if (prm->chi < 1 || prm->chi > SPG_MAX_CHI) return fail(ctx, SPG_EUNSUPPORTED, "chi outside 1..64");
   if (prm->beam < 1 || prm->beam > SPG_MAX_BEAM) return fail(ctx, SPG_EUNSUPPORTED, "beam outside 1..4096");
-  if (prm->num_sweeps != 0) return fail(ctx, SPG_EUNSUPPORTED, "variational sweeps are not built in this version");
+  if (prm->num_sweeps < 0 || prm->num_sweeps > 16) return fail(ctx, SPG_EINVAL, "num_sweeps outside 0..16");
   if (prm->precision != SPG_FP64 && prm->precision != SPG_MIXED) return fail(ctx, SPG_EINVAL, "bad precision");
   if (prm->svd_iters < -1 || prm->svd_iters > 64) return fail(ctx, SPG_EINVAL, "svd_iters outside -1..64");
   if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");

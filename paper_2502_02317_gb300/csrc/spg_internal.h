@@ -151,6 +151,21 @@ cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, 
 template <typename T>
 cudaError_t launch_zip_site0(const T* M, int DU, int K, T* site_out, double* lognorm_r, cudaStream_t st);
 
+// CGS2 orthonormalisation of nvec contiguous vectors of length len (in place);
+// R (nvec x nvec) to Rout when non-null.
+template <typename T>
+void launch_cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st);
+
+// num_sweeps variational sweeps of row `row`'s boundary MPS (S4) against
+// W_row B_{row+1}; dimA / hdims are the host copies of the MPS dims and the
+// table dims; work holds sweep_work_elems<T>(cols, chi) T, dscratch 2 doubles.
+template <typename T>
+size_t sweep_work_elems(int cols, int chi);
+template <typename T>
+cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
+                               const int* dimA, const int* hdims, int sweeps, T* work, double* dscratch,
+                               cudaStream_t st);
+
 // Value of an MPS whose physical dims are all 1 (row 0 closed from above).
 template <typename T>
 cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaStream_t st);

@@ -165,3 +165,43 @@ def test_errors(spg, ctx):
     prob = spg.spg_problem_ising(ctx, I.chimera(2, 0))
     with pytest.raises(spg.SpgError):
         spg.spg_solve(ctx, prob, spg.params(chi=65))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("make,beta,chi,sweeps", [
+    (lambda: I.chimera(3, 0), 1.0, 8, 1),
+    (lambda: I.chimera(3, 3, couplings="gauss", h_sigma=0.1), 1.0, 12, 2),
+    (lambda: I.chimera(4, 6, cols=5, couplings="gauss", h_sigma=0.1), 1.0, 16, 1),
+    (lambda: I.square(5, 2, cols=7, h_sigma=0.3), 1.0, 3, 2),
+    (lambda: I.chimera(3, 8, cols=1), 1.0, 8, 1),
+])
+def test_variational_sweeps(spg, ctx, make, beta, chi, sweeps, prec):
+    """S4: num_sweeps variational sweeps after every zipper (log Z and
+    teacher-forced conditionals)."""
+    inst = make()
+    fg = tables.from_ising(inst)
+    p = peps.build(fg, beta)
+    ref = boundary.log_partition(p, chi, num_sweeps=sweeps)
+    prob = spg.spg_problem_ising(ctx, inst)
+    prm = spg.params(beta=beta, chi=chi, num_sweeps=sweeps, precision=prec)
+    got = spg.spg_log_partition(ctx, prob, prm)
+    assert abs(got - ref) <= TOL[prec] * max(1.0, abs(ref))
+    bd = boundary.boundary_mpses(p, chi, sweeps)
+    rng = np.random.default_rng(3)
+    for s in sorted({1, fg.cols, fg.n_sites // 2}):
+        pre = np.array([[rng.integers(0, d) for d in fg.d[:s]] for _ in range(4)], dtype=np.int64).reshape(4, s)
+        refm = search.debug_marginals(fg, search.Params(beta=beta, chi=chi, num_sweeps=sweeps), s, pre, boundary=bd)
+        gotm = spg.spg_debug_marginals(ctx, prob, prm, s, pre)
+        close(gotm, refm, TOL[prec], None if prec == 0 else LOG_FLOOR)
+
+
+def test_solve_with_sweeps(spg, ctx):
+    inst = I.chimera(3, 2)
+    fg = tables.from_ising(inst)
+    ref = search.solve(fg, search.Params(beta=1.0, chi=8, beam=128, num_sweeps=1))
+    prob = spg.spg_problem_ising(ctx, inst)
+    st, E, lp = spg.spg_solve(ctx, prob, spg.params(beta=1.0, chi=8, beam=128, num_sweeps=1)).get()
+    if ref.near_ties == 0:
+        np.testing.assert_array_equal(E, ref.energies)
+        np.testing.assert_array_equal(st.astype(np.int64), ref.states)
+    assert E[0] == ref.energies[0]
