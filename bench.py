@@ -324,6 +324,8 @@ def main():
             "config": config_dict({"precision": args.precision, "parallelism": f"replicas x{world}"}),
             "tts_s": ms / 1e3, "best_energy": best * 2.0 ** -inst.energy_shift,
             "phase_ms": {"boundary": inf["ms_boundary"], "search": inf["ms_search"]},
+            "diagnostics": {"near_ties": inf["near_ties"], "degenerate_cuts": inf["degenerate_cuts"],
+                            "jacobi_sweeps_max": inf["jacobi_sweeps_max"], "error_flags": inf["error_flags"]},
             "fp64_gpu": fp, "gpu_launches": int(sum(launches)),
             "e2e": {"value": e2e_value, "unit": "beam states/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

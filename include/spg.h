@@ -66,7 +66,8 @@ typedef struct {
   int32_t precision;   /* SPG_FP64 or SPG_MIXED (default SPG_FP64)           */
   double cut_off_prob; /* drop children with p < c * max p (default 0: off)  */
   int32_t svd_iters;   /* subspace iterations of a large truncation; -1 (the
-                          default): 6 in SPG_FP64, 4 in SPG_MIXED            */
+                          default): 6 in SPG_FP64, 2 in SPG_MIXED (FP32
+                          accuracy does not improve beyond 2)                */
   int32_t warm_start;  /* reserved, must be 0                                */
   uint64_t seed;       /* seed of the truncation's start block (default 0)   */
   int32_t merge;       /* 1: merge branches equal on the boundary of the
@@ -85,6 +86,8 @@ typedef struct {
   double candidates;       /* sum over sites of (live beam x states)         */
   double boundary_lognorm; /* log-norm of the last boundary MPS built        */
   int64_t kernel_launches; /* CUDA kernels this solve enqueued              */
+  int32_t jacobi_sweeps_max; /* most sweeps one small Jacobi SVD needed (cap 60) */
+  int32_t reserved;
 } spg_info;
 
 /* Library version, major*10000 + minor*100 + patch. */

@@ -43,7 +43,7 @@ class spg_info(C.Structure):
     _fields_ = [("n_states", C.c_int32), ("near_ties", C.c_int32), ("degenerate_cuts", C.c_int32),
                 ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
                 ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("reserved", C.c_int32)]
 
 
 def _load():

@@ -422,12 +422,25 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
     if ((threadIdx.x & 31) == 0) nrm[c] = a;
   }
   __syncthreads();
+  // columns below zero_rel of ||R||_F are numerically zero (R is often rank
+  // deficient): pairs that involve one carry no information and are skipped
+  __shared__ T s_fro2;
+  if (tid == 0) {
+    T f = T(0);
+    for (int c = 0; c < s; ++c) f += nrm[c];
+    s_fro2 = f;
+  }
+  __syncthreads();
+  const T zero2 = (sizeof(T) == 8 ? T(1e-28) : T(1e-12)) * s_fro2;
   const int se = s + (s & 1);
-  // rotate while |gamma| > s * eps * sqrt(alpha beta)
-  const T tol = (sizeof(T) == 8 ? T(2.22e-16) : T(1.19e-7)) * T(s > 8 ? s : 8);
+  // rotate while |gamma| > tol * sqrt(alpha beta): s * eps in FP64; in FP32
+  // rounding noise of ill-conditioned pairs stays above s * eps, so the bound
+  // is 1e-5 (below the ~1e-4 accuracy of an FP32 truncation)
+  const T tol = sizeof(T) == 8 ? T(2.22e-16) * T(s > 8 ? s : 8) : T(1e-5);
+  const int max_sweeps = sizeof(T) == 8 ? 60 : 30;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   __shared__ int s_conv;
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_conv = 1;
     __syncthreads();
     for (int r = 0; r < se - 1; ++r) {
@@ -446,7 +459,7 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
         for (int q = lane; q < s; q += 32) ga += ci[q] * cj[q];
         ga = warp_sum(ga);
         const T al = nrm[i], be = nrm[j];
-        if (al == T(0) || be == T(0)) continue;
+        if (al <= zero2 || be <= zero2) continue;
         if (fabs((double)ga) <= (double)tol * sqrt((double)al * (double)be)) continue;
         if (lane == 0) s_conv = 0;
         const T zeta = (be - al) / (T(2) * ga);
@@ -476,7 +489,11 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
       }
       __syncthreads();
     }
-    if (s_conv) break;
+    if (s_conv) {
+      if (tid == 0 && flag_dev) atomicMax(flag_dev + 1, sweep + 1);
+      break;
+    }
+    if (sweep == max_sweeps - 1 && tid == 0 && flag_dev) atomicMax(flag_dev + 1, max_sweeps);
     __syncthreads();
   }
   // singular values and descending order (ties by index)
@@ -725,7 +742,10 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   count_launches("k_fill_start", st);
   k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
   if (!direct) {
-    cgs2_rows(Zt, s, n, (T*)nullptr, st);
+    // the pseudo-random start block is well conditioned, so the power steps
+    // need no orthonormalisation of it; the Rayleigh-Ritz step below does
+    // need an orthonormal Z, hence the QR when there are no power steps
+    if (iters == 0) cgs2_rows(Zt, s, n, (T*)nullptr, st);
     for (int it = 0; it < iters; ++it) {
       gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);  // Y = M Z
       cgs2_rows(Yt, s, m, (T*)nullptr, st);

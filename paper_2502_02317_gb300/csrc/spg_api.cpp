@@ -436,7 +436,7 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
       } else {
         const int m = DL * chiL, n = DU * K;
         const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
-        const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 4);
+        const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 2);
         CK(truncated_svd<T>(bb.M, m, n, keep, iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
                             bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st));
         CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1,
@@ -446,8 +446,8 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
       }
     }
     if (prm->num_sweeps > 0)
-      CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, r, cols, pl.dimA.data(), P->dims.data(), prm->num_sweeps,
-                               bb.swork, bb.sdbl, st));
+      CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, r, cols, pl.dimA.data(), P->dims.data(), P->d.data(),
+                               prm->num_sweeps, bb.swork, bb.sdbl, st));
   }
   return SPG_OK;
 }
@@ -575,7 +575,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   CK(launch_final(P->tb, ds, cur, R->d_states, R->d_E, R->d_logp, R->d_n, st));
   CK(cudaMemcpyAsync(R->d_diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_diag + 2, bb.degc, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(R->ev[2], st));
@@ -1049,6 +1049,7 @@ int spg_result_info(spg_result* R, spg_info* info) {
   info->candidates = cand[0];
   info->boundary_lognorm = cand[1];
   info->kernel_launches = R->launches;
+  info->jacobi_sweeps_max = diag[3];
   return SPG_OK;
 }
 

@@ -163,8 +163,8 @@ template <typename T>
 size_t sweep_work_elems(int cols, int chi);
 template <typename T>
 cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
-                               const int* dimA, const int* hdims, int sweeps, T* work, double* dscratch,
-                               cudaStream_t st);
+                               const int* dimA, const int* hdims, const int* hstates, int sweeps, T* work,
+                               double* dscratch, cudaStream_t st);
 
 // Value of an MPS whose physical dims are all 1 (row 0 closed from above).
 template <typename T>

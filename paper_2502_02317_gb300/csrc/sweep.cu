@@ -7,7 +7,7 @@
 //
 // Layouts (row r of the MPO, psi = B_{r+1} sites B[s][b][b'], phi sites
 // P[u][a][a'], both [p][chi_l][chi_r]):
-//   environments  E[a][l][b]  (phi bond, MPO bond < 16, psi bond)
+//   environments  E[l][a][b]  (MPO bond < 16, phi bond, psi bond)
 //   W[l,r,u,s] = sum_x w(x) bL[l][PL x] bU[u][PU x] [r = PR x][s = PD x]
 // Every contraction groups the cluster states x by their projections, so the
 // dense MPO is never formed.
@@ -25,214 +25,98 @@ __device__ __forceinline__ T warp_max_abs(T v) {
   return v;
 }
 
-// Per-site tables staged in shared memory.
-template <typename T>
-struct SiteSmem {
-  T w[MAXS];
-  T bL[256];
-  T bU[256];
-  uint8_t PL[MAXS], PR[MAXS], PU[MAXS], PD[MAXS];
+// Batched strided GEMM over a "state" index q (one grid.z slice per q):
+//   C_q[i][j] = sum_k A[offA(q) + i*sAi + k*sAk] * B[offB(q) + k*sBk + j*sBj]
+// written to C + q*M*N (row-major M x N).  The operand offsets follow from
+// q through the site's projections: off = c1 * v(id1, q) + c2 * v(id2, q)
+// with id 0: none, 1: P_L, 2: P_R, 3: P_U, 4: P_D, 5: q / n2, 6: q % n2.
+struct XOff {
+  int id1, id2;
+  long long c1, c2;
 };
 
-template <typename T>
-__device__ void stage_site(SiteSmem<T>& sm, const DevTables& tb, const DevWeights<T>& wt, int s) {
+__device__ __forceinline__ long long xval(const DevTables& tb, int s, int id, int q, int n2) {
   const size_t so = (size_t)s * tb.dmax;
+  switch (id) {
+    case 1: return tb.PL[so + q];
+    case 2: return tb.PR[so + q];
+    case 3: return tb.PU[so + q];
+    case 4: return tb.PD[so + q];
+    case 5: return q / n2;
+    case 6: return q % n2;
+    default: return 0;
+  }
+}
+
+template <typename T>
+__global__ void k_xgemm(DevTables tb, int s, int n2, int M, int N, int K, const T* __restrict__ A, XOff oa, int sAi,
+                        int sAk, const T* __restrict__ B, XOff ob, int sBk, int sBj, T* __restrict__ C) {
+  constexpr int BM = 32, BN = 32, BK = 32;
+  __shared__ T sA[BK][BM + 1];
+  __shared__ T sB[BK][BN + 1];
+  const int q = blockIdx.z;
+  const long long offA = oa.c1 * xval(tb, s, oa.id1, q, n2) + oa.c2 * xval(tb, s, oa.id2, q, n2);
+  const long long offB = ob.c1 * xval(tb, s, ob.id1, q, n2) + ob.c2 * xval(tb, s, ob.id2, q, n2);
+  const T* Aq = A + offA;
+  const T* Bq = B + offB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  T acc[2][2] = {};
+  for (int kk = 0; kk < K; kk += BK) {
+    for (int e = threadIdx.x; e < BK * BM; e += 256) {
+      const int i = e / BK, kq = e % BK;
+      const int gi = row0 + i, gk = kk + kq;
+      sA[kq][i] = (gi < M && gk < K) ? Aq[(long long)gi * sAi + (long long)gk * sAk] : T(0);
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      const int kq = e / BN, j = e % BN;
+      const int gj = col0 + j, gk = kk + kq;
+      sB[kq][j] = (gj < N && gk < K) ? Bq[(long long)gk * sBk + (long long)gj * sBj] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kq = 0; kq < BK; ++kq) {
+      const T a0 = sA[kq][ty * 2], a1 = sA[kq][ty * 2 + 1];
+      const T b0 = sB[kq][tx * 2], b1 = sB[kq][tx * 2 + 1];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+  T* Cq = C + (size_t)q * M * N;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int gi = row0 + ty * 2 + i;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gj = col0 + tx * 2 + j;
+      if (gj < N) Cq[(size_t)gi * N + gj] = acc[i][j];
+    }
+  }
+}
+
+// Coefficients of the weighted sum over states (K x d, row-major):
+//   mode 0: coef[u][x] = bU[u][PU x] w(x)      (local tensor)
+//   mode 1: coef[l][x] = bL[l][PL x] w(x)      (right environment)
+//   mode 2: coef[r][x] = [PR x == r] w(x)      (left environment)
+template <typename T>
+__global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, int K, T* __restrict__ coef) {
   const int d = tb.d[s];
-  for (int x = threadIdx.x; x < d; x += blockDim.x) {
-    sm.w[x] = wt.w[so + x];
-    sm.PL[x] = tb.PL[so + x];
-    sm.PR[x] = tb.PR[so + x];
-    sm.PU[x] = tb.PU[so + x];
-    sm.PD[x] = tb.PD[so + x];
+  const size_t so = (size_t)s * tb.dmax;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * d; e += gridDim.x * blockDim.x) {
+    const int k = e / d, x = e % d;
+    T v;
+    if (mode == 0)
+      v = wt.bU[(size_t)s * 256 + k * 16 + tb.PU[so + x]];
+    else if (mode == 1)
+      v = wt.bL[(size_t)s * 256 + k * 16 + tb.PL[so + x]];
+    else
+      v = tb.PR[so + x] == k ? T(1) : T(0);
+    coef[e] = v * wt.w[so + x];
   }
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    sm.bL[e] = wt.bL[(size_t)s * 256 + e];
-    sm.bU[e] = wt.bU[(size_t)s * 256 + e];
-  }
-}
-
-// F[v][a][a'] = sum_u bU[u][v] P[u][a][a']   (v < NU)
-template <typename T>
-__global__ void k_phi_prime(DevTables tb, DevWeights<T> wt, int s, const T* __restrict__ P, int DU, int chiL,
-                            int chiR, T* __restrict__ F) {
-  const int NU = tb.dims[s * 8 + 5];
-  const int n = NU * chiL * chiR;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int v = e / (chiL * chiR), rest = e % (chiL * chiR);
-    T acc = T(0);
-    for (int u = 0; u < DU; ++u) acc += wt.bU[(size_t)s * 256 + u * 16 + v] * P[(size_t)u * chiL * chiR + rest];
-    F[e] = acc;
-  }
-}
-
-// Lp[a][h][b] = sum_l L[a][l][b] bL[l][h]   (h < NL)
-template <typename T>
-__global__ void k_left_prime(DevTables tb, DevWeights<T> wt, int s, const T* __restrict__ L, int chiA, int DL,
-                             int chiB, T* __restrict__ Lp) {
-  const int NL = tb.dims[s * 8 + 4];
-  const int n = chiA * NL * chiB;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int b = e % chiB, h = (e / chiB) % NL, a = e / (chiB * NL);
-    T acc = T(0);
-    for (int l = 0; l < DL; ++l) acc += L[((size_t)a * MAXP + l) * chiB + b] * wt.bL[(size_t)s * 256 + l * 16 + h];
-    Lp[((size_t)a * MAXP + h) * chiB + b] = acc;
-  }
-}
-
-// Pr[s][r][b][a'] = sum_b' B[s][b][b'] R[a'][r][b']       (right pairs)
-template <typename T>
-__global__ void k_pairs_right(const T* __restrict__ B, int p, int chiBl, int chiBr, const T* __restrict__ R,
-                              int chiA, int DR, T* __restrict__ Pr) {
-  const size_t n = (size_t)p * DR * chiBl * chiA;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int ap = e % chiA;
-    size_t t = e / chiA;
-    const int b = t % chiBl;
-    t /= chiBl;
-    const int r = t % DR, sg = (int)(t / DR);
-    const T* brow = B + ((size_t)sg * chiBl + b) * chiBr;
-    const T* rrow = R + ((size_t)ap * MAXP + r) * chiBr;
-    T acc = T(0);
-    for (int bp = 0; bp < chiBr; ++bp) acc += brow[bp] * rrow[bp];
-    Pr[e] = acc;
-  }
-}
-
-// Ql[h][s][a][b'] = sum_b Lp[a][h][b] B[s][b][b']           (left pairs)
-template <typename T>
-__global__ void k_pairs_left(const T* __restrict__ Lp, int NL, int chiA, int chiBl, const T* __restrict__ B, int p,
-                             int chiBr, T* __restrict__ Ql) {
-  const size_t n = (size_t)NL * p * chiA * chiBr;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int bp = e % chiBr;
-    size_t t = e / chiBr;
-    const int a = t % chiA;
-    t /= chiA;
-    const int sg = t % p, h = (int)(t / p);
-    const T* lrow = Lp + ((size_t)a * MAXP + h) * chiBl;
-    const T* bcol = B + (size_t)sg * chiBl * chiBr + bp;
-    T acc = T(0);
-    for (int b = 0; b < chiBl; ++b) acc += lrow[b] * bcol[(size_t)b * chiBr];
-    Ql[e] = acc;
-  }
-}
-
-// local: C[u][a][a'] = sum_x w(x) bU[u][PU x] sum_b Lp[a][PL x][b] Pr[PD x][PR x][b][a']
-// one thread per (a, a'), states grouped into the NU accumulators of PU x.
-template <typename T>
-__global__ void k_local_x(DevTables tb, DevWeights<T> wt, int s, const T* __restrict__ Lp, const T* __restrict__ Pr,
-                          int chiA, int chiAr, int chiBl, int DR, int DU, T* __restrict__ C) {
-  __shared__ SiteSmem<T> sm;
-  stage_site(sm, tb, wt, s);
-  __syncthreads();
-  const int d = tb.d[s], NU = tb.dims[s * 8 + 5];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= chiA * chiAr) return;
-  const int a = e / chiAr, ap = e % chiAr;
-  T H[MAXP];
-#pragma unroll
-  for (int v = 0; v < MAXP; ++v) H[v] = T(0);
-  for (int x = 0; x < d; ++x) {
-    const T* lrow = Lp + ((size_t)a * MAXP + sm.PL[x]) * chiBl;
-    const T* pcol = Pr + (((size_t)sm.PD[x] * DR + sm.PR[x]) * chiBl) * chiAr + ap;
-    T g0 = T(0), g1 = T(0);
-    int b = 0;
-    for (; b + 1 < chiBl; b += 2) {
-      g0 += lrow[b] * pcol[(size_t)b * chiAr];
-      g1 += lrow[b + 1] * pcol[(size_t)(b + 1) * chiAr];
-    }
-    if (b < chiBl) g0 += lrow[b] * pcol[(size_t)b * chiAr];
-    const T g = sm.w[x] * (g0 + g1);
-    const int v = sm.PU[x];
-#pragma unroll
-    for (int q = 0; q < MAXP; ++q)
-      if (q == v) H[q] += g;
-  }
-  for (int u = 0; u < DU; ++u) {
-    T acc = T(0);
-#pragma unroll
-    for (int v = 0; v < MAXP; ++v)
-      if (v < NU) acc += sm.bU[u * 16 + v] * H[v];
-    C[((size_t)u * chiA + a) * chiAr + ap] = acc;
-  }
-}
-
-// right environment: Rn[a][l][b] = sum_h bL[l][h] sum_{x: PL x = h} w(x)
-//                    sum_a' F[PU x][a][a'] Pr[PD x][PR x][b][a']
-// one thread per (a, b).
-template <typename T>
-__global__ void k_env_right_x(DevTables tb, DevWeights<T> wt, int s, const T* __restrict__ F, const T* __restrict__ Pr,
-                              int chiA, int chiAr, int chiBl, int DR, int DL, T* __restrict__ Rn) {
-  __shared__ SiteSmem<T> sm;
-  stage_site(sm, tb, wt, s);
-  __syncthreads();
-  const int d = tb.d[s], NL = tb.dims[s * 8 + 4];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= chiA * chiBl) return;
-  const int a = e / chiBl, b = e % chiBl;
-  T Y[MAXP];
-#pragma unroll
-  for (int h = 0; h < MAXP; ++h) Y[h] = T(0);
-  for (int x = 0; x < d; ++x) {
-    const T* frow = F + ((size_t)sm.PU[x] * chiA + a) * chiAr;
-    const T* prow = Pr + (((size_t)sm.PD[x] * DR + sm.PR[x]) * chiBl + b) * chiAr;
-    T g0 = T(0), g1 = T(0);
-    int ap = 0;
-    for (; ap + 1 < chiAr; ap += 2) {
-      g0 += frow[ap] * prow[ap];
-      g1 += frow[ap + 1] * prow[ap + 1];
-    }
-    if (ap < chiAr) g0 += frow[ap] * prow[ap];
-    const T g = sm.w[x] * (g0 + g1);
-    const int h = sm.PL[x];
-#pragma unroll
-    for (int q = 0; q < MAXP; ++q)
-      if (q == h) Y[q] += g;
-  }
-  for (int l = 0; l < MAXP; ++l) {
-    T acc = T(0);
-    if (l < DL) {
-#pragma unroll
-      for (int h = 0; h < MAXP; ++h)
-        if (h < NL) acc += sm.bL[l * 16 + h] * Y[h];
-    }
-    Rn[((size_t)a * MAXP + l) * chiBl + b] = acc;
-  }
-}
-
-// left environment: Ln[a'][r][b'] = sum_{x: PR x = r} w(x)
-//                   sum_a F[PU x][a][a'] Ql[PL x][PD x][a][b']
-// one thread per (a', b').
-template <typename T>
-__global__ void k_env_left_x(DevTables tb, DevWeights<T> wt, int s, const T* __restrict__ F, const T* __restrict__ Ql,
-                             int chiA, int chiAr, int chiBr, int p, int DR, T* __restrict__ Ln) {
-  __shared__ SiteSmem<T> sm;
-  stage_site(sm, tb, wt, s);
-  __syncthreads();
-  const int d = tb.d[s];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= chiAr * chiBr) return;
-  const int ap = e / chiBr, bp = e % chiBr;
-  T O[MAXP];
-#pragma unroll
-  for (int r = 0; r < MAXP; ++r) O[r] = T(0);
-  for (int x = 0; x < d; ++x) {
-    const T* fcol = F + (size_t)sm.PU[x] * chiA * chiAr + ap;
-    const T* qcol = Ql + (((size_t)sm.PL[x] * p + sm.PD[x]) * chiA) * chiBr + bp;
-    T g0 = T(0), g1 = T(0);
-    int a = 0;
-    for (; a + 1 < chiA; a += 2) {
-      g0 += fcol[(size_t)a * chiAr] * qcol[(size_t)a * chiBr];
-      g1 += fcol[(size_t)(a + 1) * chiAr] * qcol[(size_t)(a + 1) * chiBr];
-    }
-    if (a < chiA) g0 += fcol[(size_t)a * chiAr] * qcol[(size_t)a * chiBr];
-    const T g = sm.w[x] * (g0 + g1);
-    const int r = sm.PR[x];
-#pragma unroll
-    for (int q = 0; q < MAXP; ++q)
-      if (q == r) O[q] += g;
-  }
-  for (int r = 0; r < MAXP; ++r) Ln[((size_t)ap * MAXP + r) * chiBr + bp] = r < DR ? O[r] : T(0);
 }
 
 // In-place scaling of buf[0..n) to max |.| = 1, log of the scale added to *logacc.
@@ -310,14 +194,16 @@ size_t sweep_work_elems(int cols, int chi) {
   const size_t env = (size_t)chi * MAXP * chi;
   // Lcache (cols+1 envs), R (cols+1 envs), Rcur, pairs (16*16*chi*chi), F and
   // Lp (16*chi*chi each), C (16*chi*chi), vectors (16*chi*chi), doubles
-  return (size_t)(2 * (cols + 1) + 2) * env + (size_t)MAXP * MAXP * chi * chi + 4 * (size_t)MAXP * chi * chi + 64;
+  return (size_t)(2 * (cols + 1) + 2) * env + (size_t)MAXP * MAXP * chi * chi + 4 * (size_t)MAXP * chi * chi +
+         (size_t)MAXS * chi * chi + (size_t)MAXP * MAXS + 64;
 }
 
 template <typename T>
 cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
-                               const int* dimA, const int* hdims, int sweeps, T* work, double* dscratch,
-                               cudaStream_t st) {
+                               const int* dimA, const int* hdims, const int* hstates, int sweeps, T* work,
+                               double* dscratch, cudaStream_t st) {
   auto tb_dims_host = [&](int s, int k) { return hdims[s * 8 + k]; };
+  auto hd_states = [&](int s) { return hstates[s]; };
   auto cgs_rows = [&](T* X, int nvec, int len, cudaStream_t stm) { launch_cgs2_rows<T>(X, nvec, len, nullptr, stm); };
   const int chi = (int)std::lround(std::sqrt((double)(mps.site_stride / MAXP)));
   const size_t env = (size_t)chi * MAXP * chi;
@@ -330,6 +216,8 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   T* Lp = F + (size_t)MAXP * chi * chi;         // [chi*16*chi]
   T* C = Lp + (size_t)MAXP * chi * chi;         // [16*chi*chi]
   T* Vv = C + (size_t)MAXP * chi * chi;         // vectors [16*chi*chi]
+  T* G = Vv + (size_t)MAXP * chi * chi;         // per-state products [MAXS*chi*chi]
+  T* Cf = G + (size_t)MAXS * chi * chi;         // state coefficients [16*MAXS]
   double* rsum = dscratch;                      // [1]
   double* junk = dscratch + 1;
   auto site_ptr = [&](int r, int j) { return mps.A + (size_t)(r * cols + j) * mps.site_stride; };
@@ -341,22 +229,51 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     if ((err = (x)) != cudaSuccess) return err; \
   } while (0)
 
-  // local tensor C at site j from left env Lenv, right env Renv
+  // Environments are E[m][a][b] (MPO bond m < 16 outermost, phi bond a, psi
+  // bond b).  Per site: tables' dims from the host copy.
+  auto xgemm = [&](int s, int nq, int n2, int M, int N, int K, const T* A, XOff oa, int sAi, int sAk, const T* B,
+                   XOff ob, int sBk, int sBj, T* C) {
+    dim3 grid((N + 31) / 32, (M + 31) / 32, nq);
+    count_launches("k_xgemm", st, 2.0 * nq * M * N * K);
+    k_xgemm<T><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C);
+  };
+  auto coef = [&](int s, int mode, int K) {
+    const int d = hd_states(s);
+    count_launches("k_state_coef", st);
+    k_state_coef<T><<<nblk((size_t)K * d), 256, 0, st>>>(tb, wt, s, mode, K, Cf);
+  };
+  // Lp[h][a][b] = sum_l bL[l][h] E[l][a][b]
+  auto left_prime = [&](int s, const T* Lenv, int chiA, int chiB) {
+    const int DL = tb_dims_host(s, 0), NL = tb_dims_host(s, 4);
+    gemm2<T>(true, false, NL, chiA * chiB, DL, wt.bL + (size_t)s * 256, 16, Lenv, chiA * chiB, Lp, chiA * chiB, st);
+  };
+  // F[v][a][a'] = sum_u bU[u][v] P[u][a][a']
+  auto phi_prime = [&](int s, const T* P, int DU, int chiA, int chiAr) {
+    const int NU = tb_dims_host(s, 5);
+    gemm2<T>(true, false, NU, chiA * chiAr, DU, wt.bU + (size_t)s * 256, 16, P, chiA * chiAr, F, chiA * chiAr, st);
+  };
+  // Pr[s'][r][b][a'] = sum_b' B[s'][b][b'] R[r][a'][b']
+  auto pairs_right = [&](int s, const T* B, int p, int chiBl, int chiBr, const T* Renv, int chiAr) {
+    const int DR = tb_dims_host(s, 1);
+    xgemm(s, p * DR, DR, chiBl, chiAr, chiBr, B, XOff{5, 0, (long long)chiBl * chiBr, 0}, chiBr, 1, Renv,
+          XOff{6, 0, (long long)chiAr * chiBr, 0}, 1, chiBr, Pp);
+  };
+  // local tensor C[u][a][a'] at site j from left env Lenv, right env Renv
   auto local = [&](int j, const T* Lenv, const T* Renv) -> cudaError_t {
     const int s = row * cols + j;
     const int* dB = dims(row + 1, j);
     const int* dP = dims(row, j);
     const int p = dB[0], chiBl = dB[1], chiBr = dB[2];
     const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
-    const int DL = tb_dims_host(s, 0), DR = tb_dims_host(s, 1), NL = tb_dims_host(s, 4);
-    (void)NL;
+    const int DR = tb_dims_host(s, 1), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
-    count_launches("k_left_prime", st);
-    k_left_prime<T><<<nblk((size_t)chiA * MAXP * chiBl), 256, 0, st>>>(tb, wt, s, Lenv, chiA, DL, chiBl, Lp);
-    count_launches("k_pairs_right", st, 2.0 * p * DR * chiBl * chiAr * chiBr);
-    k_pairs_right<T><<<nblk((size_t)p * DR * chiBl * chiAr), 256, 0, st>>>(B, p, chiBl, chiBr, Renv, chiAr, DR, Pp);
-    count_launches("k_local_x", st);
-    k_local_x<T><<<nblk((size_t)chiA * chiAr, 128), 128, 0, st>>>(tb, wt, s, Lp, Pp, chiA, chiAr, chiBl, DR, DU, C);
+    left_prime(s, Lenv, chiA, chiBl);
+    pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
+    // G_x[a][a'] = sum_b Lp[PL x][a][b] Pr[PD x][PR x][b][a']
+    xgemm(s, d, 1, chiA, chiAr, chiBl, Lp, XOff{1, 0, (long long)chiA * chiBl, 0}, chiBl, 1, Pp,
+          XOff{4, 2, (long long)DR * chiBl * chiAr, (long long)chiBl * chiAr}, chiAr, 1, G);
+    coef(s, 0, DU);
+    gemm2<T>(false, false, DU, chiA * chiAr, d, Cf, d, G, chiA * chiAr, C, chiA * chiAr, st);
     return cudaGetLastError();
   };
   auto env_right = [&](int j, const T* Renv, T* out, double* logacc) -> cudaError_t {
@@ -365,17 +282,17 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     const int* dP = dims(row, j);
     const int p = dB[0], chiBl = dB[1], chiBr = dB[2];
     const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
-    const int DL = tb_dims_host(s, 0), DR = tb_dims_host(s, 1);
+    const int DL = tb_dims_host(s, 0), DR = tb_dims_host(s, 1), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
     const T* P = site_ptr(row, j);
-    count_launches("k_phi_prime", st);
-    k_phi_prime<T><<<nblk((size_t)MAXP * chiA * chiAr), 256, 0, st>>>(tb, wt, s, P, DU, chiA, chiAr, F);
-    count_launches("k_pairs_right", st, 2.0 * p * DR * chiBl * chiAr * chiBr);
-    k_pairs_right<T><<<nblk((size_t)p * DR * chiBl * chiAr), 256, 0, st>>>(B, p, chiBl, chiBr, Renv, chiAr, DR, Pp);
+    phi_prime(s, P, DU, chiA, chiAr);
+    pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
+    // Y_x[a][b] = sum_a' F[PU x][a][a'] Pr[PD x][PR x][b][a']
+    xgemm(s, d, 1, chiA, chiBl, chiAr, F, XOff{3, 0, (long long)chiA * chiAr, 0}, chiAr, 1, Pp,
+          XOff{4, 2, (long long)DR * chiBl * chiAr, (long long)chiBl * chiAr}, 1, chiAr, G);
+    coef(s, 1, DL);
     SPG_TRY(zero_env(out));
-    count_launches("k_env_right_x", st);
-    k_env_right_x<T><<<nblk((size_t)chiA * chiBl, 128), 128, 0, st>>>(tb, wt, s, F, Pp, chiA, chiAr, chiBl, DR, DL,
-                                                                      out);
+    gemm2<T>(false, false, DL, chiA * chiBl, d, Cf, d, G, chiA * chiBl, out, chiA * chiBl, st);
     count_launches("k_scale_max", st);
     k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, logacc);
     return cudaGetLastError();
@@ -386,19 +303,20 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     const int* dP = dims(row, j);
     const int p = dB[0], chiBl = dB[1], chiBr = dB[2];
     const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
-    const int DL = tb_dims_host(s, 0), DR = tb_dims_host(s, 1), NL = tb_dims_host(s, 4);
+    const int DR = tb_dims_host(s, 1), NL = tb_dims_host(s, 4), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
     const T* P = site_ptr(row, j);
-    count_launches("k_left_prime", st);
-    k_left_prime<T><<<nblk((size_t)chiA * MAXP * chiBl), 256, 0, st>>>(tb, wt, s, Lenv, chiA, DL, chiBl, Lp);
-    count_launches("k_pairs_left", st, 2.0 * NL * p * chiA * chiBr * chiBl);
-    k_pairs_left<T><<<nblk((size_t)NL * p * chiA * chiBr), 256, 0, st>>>(Lp, NL, chiA, chiBl, B, p, chiBr, Pp);
-    count_launches("k_phi_prime", st);
-    k_phi_prime<T><<<nblk((size_t)MAXP * chiA * chiAr), 256, 0, st>>>(tb, wt, s, P, DU, chiA, chiAr, F);
+    left_prime(s, Lenv, chiA, chiBl);
+    // Ql[h][s'][a][b'] = sum_b Lp[h][a][b] B[s'][b][b']
+    xgemm(s, NL * p, p, chiA, chiBr, chiBl, Lp, XOff{5, 0, (long long)chiA * chiBl, 0}, chiBl, 1, B,
+          XOff{6, 0, (long long)chiBl * chiBr, 0}, chiBr, 1, Pp);
+    phi_prime(s, P, DU, chiA, chiAr);
+    // Z_x[a'][b'] = sum_a F[PU x][a][a'] Ql[PL x][PD x][a][b']
+    xgemm(s, d, 1, chiAr, chiBr, chiA, F, XOff{3, 0, (long long)chiA * chiAr, 0}, 1, chiAr, Pp,
+          XOff{1, 4, (long long)p * chiA * chiBr, (long long)chiA * chiBr}, chiBr, 1, G);
+    coef(s, 2, DR);
     SPG_TRY(zero_env(out));
-    count_launches("k_env_left_x", st);
-    k_env_left_x<T><<<nblk((size_t)chiAr * chiBr, 128), 128, 0, st>>>(tb, wt, s, F, Pp, chiA, chiAr, chiBr, p, DR,
-                                                                     out);
+    gemm2<T>(false, false, DR, chiAr * chiBr, d, Cf, d, G, chiAr * chiBr, out, chiAr * chiBr, st);
     count_launches("k_scale_max", st);
     k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, junk);
     return cudaGetLastError();
@@ -457,8 +375,10 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
 template size_t sweep_work_elems<double>(int, int);
 template size_t sweep_work_elems<float>(int, int);
 template cudaError_t variational_sweeps<double>(const DevTables&, DevWeights<double>, DevMPS<double>, int, int,
-                                                const int*, const int*, int, double*, double*, cudaStream_t);
+                                                const int*, const int*, const int*, int, double*, double*,
+                                                cudaStream_t);
 template cudaError_t variational_sweeps<float>(const DevTables&, DevWeights<float>, DevMPS<float>, int, int,
-                                               const int*, const int*, int, float*, double*, cudaStream_t);
+                                               const int*, const int*, const int*, int, float*, double*,
+                                               cudaStream_t);
 
 }  // namespace spg
