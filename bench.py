@@ -159,6 +159,26 @@ def cpu_oracle_sample(seed, max_sites=6):
                       f"search sites ({cand} beam states) in {dt:.1f} s"}
 
 
+def rank_instance_seed(rank: int) -> int:
+    """Replicas: every rank solves its own independent instance."""
+    return 1000 + rank
+
+
+def aggregate_over_ranks(tot_ms: float, tot_cand: float, device="cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the beam states of all ranks (no data-path collective; this reduction of
+    two scalars happens once, after the timed region)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return tot_ms, tot_cand
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+    c = torch.tensor([tot_cand], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,7 +235,7 @@ def main():
 
     stream = torch.cuda.Stream()
     ctx = spg.Context(local, stream=stream.cuda_stream)
-    inst = make_instance(1000 + rank)
+    inst = make_instance(rank_instance_seed(rank))
     prob = spg.spg_problem_ising(ctx, inst)
     prec = spg.SPG_MIXED if args.precision == "mixed" else spg.SPG_FP64
     prm = spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=prec,
@@ -252,12 +272,7 @@ def main():
     best = int(E[0])
     tot_cand = sum(cands)
     tot_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([tot_ms, tot_cand], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        tot_ms, tot_cand = float(mx[0]), float(t[1])
+    tot_ms, tot_cand = aggregate_over_ranks(tot_ms, tot_cand, device="cuda")
     value = tot_cand / (tot_ms / 1e3)
 
     # end to end through the C ABI from host arrays (tables built and copied,

@@ -442,6 +442,14 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
   __shared__ int s_conv;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_conv = 1;
+    // exact squared column norms once per sweep (the per-rotation updates
+    // below follow the Hestenes recurrence and would otherwise drift)
+    for (int c = wid; c < s; c += nw) {
+      T a = T(0);
+      for (int q = lane; q < s; q += 32) a += Rc[(size_t)c * s + q] * Rc[(size_t)c * s + q];
+      a = warp_sum(a);
+      if (lane == 0) nrm[c] = a;
+    }
     __syncthreads();
     for (int r = 0; r < se - 1; ++r) {
       for (int pk = wid; pk < se / 2; pk += nw) {
@@ -453,14 +461,14 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
           i = j;
           j = t;
         }
+        const T al = nrm[i], be = nrm[j];
+        if (al <= zero2 || be <= zero2) continue;
         T* ci = Rc + (size_t)i * s;
         T* cj = Rc + (size_t)j * s;
         T ga = T(0);
         for (int q = lane; q < s; q += 32) ga += ci[q] * cj[q];
         ga = warp_sum(ga);
-        const T al = nrm[i], be = nrm[j];
-        if (al <= zero2 || be <= zero2) continue;
-        if (fabs((double)ga) <= (double)tol * sqrt((double)al * (double)be)) continue;
+        if (fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
         if (lane == 0) s_conv = 0;
         const T zeta = (be - al) / (T(2) * ga);
         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
@@ -468,23 +476,17 @@ __global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout
         const T sn = c * t;
         T* vi = Vc + (size_t)i * s;
         T* vj = Vc + (size_t)j * s;
-        T ni = T(0), nj = T(0);
         for (int q = lane; q < s; q += 32) {
           const T x = ci[q], y = cj[q];
-          const T xn = c * x - sn * y, yn = sn * x + c * y;
-          ci[q] = xn;
-          cj[q] = yn;
-          ni += xn * xn;
-          nj += yn * yn;
+          ci[q] = c * x - sn * y;
+          cj[q] = sn * x + c * y;
           const T u = vi[q], v = vj[q];
           vi[q] = c * u - sn * v;
           vj[q] = sn * u + c * v;
         }
-        ni = warp_sum(ni);
-        nj = warp_sum(nj);
         if (lane == 0) {
-          nrm[i] = ni;
-          nrm[j] = nj;
+          nrm[i] = al - t * ga;
+          nrm[j] = be + t * ga;
         }
       }
       __syncthreads();
