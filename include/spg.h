@@ -149,6 +149,17 @@ int spg_problem_shape(const spg_problem* prob, int32_t* rows, int32_t* cols, int
  * contents after spg_result_get. */
 int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_result** out);
 
+/* Batching: solve n independent problems concurrently (instances of uneven
+ * size, each with its own parameters prms[i]); every problem is solved
+ * exactly as by spg_solve.  The solves run on up to 16 worker streams owned
+ * by the context (each with its own workspace), enqueued from as many host
+ * threads, so that the instances' chains of dependent kernels overlap on the
+ * GPU.  out: n result handles, each waited for by spg_result_get.  Returns
+ * once everything is enqueued; work enqueued later on the context's stream
+ * runs after the batch.  On failure no handle is returned. */
+int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prms,
+                    spg_result** out);
+
 /* Copy the final states out (waits for the solve).  States are sorted by
  * (energy ascending, state lexicographically ascending).
  *   states        : [n_states x n_sites] cluster states, or NULL

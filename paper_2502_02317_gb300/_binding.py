@@ -67,6 +67,7 @@ def _load():
         "spg_problem_destroy": (None, [P]),
         "spg_problem_shape": (C.c_int, [P, pI32, pI32, pI32]),
         "spg_solve": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P)]),
+        "spg_solve_batch": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
         "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD]),
         "spg_result_info": (C.c_int, [P, C.POINTER(spg_info)]),
         "spg_result_destroy": (None, [P]),
@@ -237,6 +238,16 @@ def spg_solve(ctx: Context, prob: Problem, prm: spg_params) -> Result:
     out = C.c_void_p()
     ctx.check(lib.spg_solve(ctx.h, prob.h, C.byref(prm), C.byref(out)))
     return Result(ctx, out)
+
+
+def spg_solve_batch(ctx: Context, probs, prms) -> list:
+    """Concurrent solves of independent problems (one params per problem)."""
+    n = len(probs)
+    ph = (C.c_void_p * n)(*[p.h for p in probs])
+    pa = (spg_params * n)(*prms)
+    out = (C.c_void_p * n)()
+    ctx.check(lib.spg_solve_batch(ctx.h, n, ph, pa, out))
+    return [Result(ctx, C.c_void_p(out[i])) for i in range(n)]
 
 
 def spg_debug_marginals(ctx: Context, prob: Problem, prm: spg_params, site: int, prefixes) -> np.ndarray:

@@ -6,6 +6,7 @@
 // bond_dim; MpsContractor(SVDTruncate, ...)).
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "spg_internal.h"
 
@@ -631,11 +632,8 @@ cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T*
   const size_t base = sizeof(T) * (64 + 2 * SMAX + MAXCHI * MAXCHI);
   const size_t full = base + sizeof(T) * MAXP * chi * chi;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_left_canonical", st);
   k_left_canonical<T><<<1, 1024, use_smem ? full : base, st>>>(mps, r, cols, scratch, use_smem);
   return cudaGetLastError();
@@ -711,11 +709,8 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   const size_t base = sizeof(T) * (64 + 2 * SMAX);
   const size_t full = base + sizeof(T) * (size_t)nvec * len;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   // one thread per element when the vectors are short, at least 4 warps
   const int threads = std::max(128, std::min(1024, (len + 31) / 32 * 32));
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
@@ -762,11 +757,8 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   const size_t jsm_full = jsm_base + sizeof(T) * 2 * (size_t)s * s;
   const int use_smem = jsm_full <= 200 * 1024 ? 1 : 0;
   const size_t jsm = use_smem ? jsm_full : jsm_base;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_jacobi", st);
   k_jacobi<T><<<1, 1024, jsm, st>>>(R, s, RV, VJ, sig, keep, s1_dev, flag_dev, jbuf, use_smem);
   // V = Z VJ[:, :keep] = Zt^T VJ,  US = Q RV[:, :keep] = Yt^T RV

@@ -9,6 +9,7 @@
 #include <cfloat>
 #include <climits>
 #include <cmath>
+#include <mutex>
 
 #include "spg_internal.h"
 
@@ -763,11 +764,8 @@ cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> m
   const size_t base = sizeof(T) * ((size_t)G * MAXCHI * MAXP + 2 * MAXP * MAXCHI + 32);
   const size_t full = base + sizeof(T) * mps.site_stride;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_right_envs", st);
   k_right_envs<T><<<(ds.cap + G - 1) / G, 512, use_smem ? full : base, st>>>(tb, wt, mps, row, ds, bt, cur, G,
                                                                            use_smem);
@@ -789,11 +787,8 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
   int P = 1;
   while (P < ds.cap) P <<= 1;
   const int csm = (int)((sizeof(unsigned long long) * KEYW + sizeof(int)) * P);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
   count_launches("k_classes", st);
   k_classes<<<1, 1024, csm, st>>>(ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
@@ -850,11 +845,8 @@ cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
 cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint16_t* out_states, int64_t* out_E,
                          double* out_logp, int* out_n, cudaStream_t st) {
   const int sm = (int)((sizeof(long long) + sizeof(int)) * SPG_MAXFINAL);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    attr = true;
-  }
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); });
   count_launches("k_final", st);
   k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
   return cudaGetLastError();

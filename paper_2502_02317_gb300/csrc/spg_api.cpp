@@ -13,6 +13,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -31,6 +32,20 @@ struct spg_ctx {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // worker contexts (own stream and workspace) of spg_solve_batch
+  std::vector<spg_ctx*> workers;
+  // captured solves (see solve_impl)
+  struct Graph {
+    const void* problem = nullptr;
+    spg_params prm{};
+    int tsize = 0;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    int uses = 0;
+    cudaGraphExec_t boundary = nullptr, search = nullptr;
+    long long launches = 0;
+  };
+  std::vector<Graph> graphs;
 };
 
 struct spg_problem {
@@ -269,9 +284,12 @@ struct Arena {
   }
 };
 
+void drop_graphs(spg_ctx* ctx, const void* problem);
+
 int ensure_arena(spg_ctx* ctx, size_t bytes) {
   if (ctx->arena_bytes >= bytes) return SPG_OK;
   CK(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx, nullptr);  // captured solves address the old workspace
   if (ctx->arena) CK(cudaFree(ctx->arena));
   ctx->arena = nullptr;
   ctx->arena_bytes = 0;
@@ -371,7 +389,8 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
 }
 
 template <typename T>
-int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar, BoundaryBufs<T>& bb) {
+int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar, BoundaryBufs<T>& bb,
+                   bool init = true) {
   const int chi = pl.chi;
   const size_t sites = (size_t)(P->rows + 1) * P->cols;
   bb.mps.A = ar.get<T>(sites * pl.stride);
@@ -399,6 +418,7 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.swork = ar.get<T>(sweep_work_elems<T>(P->cols, chi));
   bb.sdbl = ar.get<double>(4);
   if (!bb.sdbl) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * sites * 3, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
@@ -485,7 +505,8 @@ size_t search_bytes(const spg_problem* P, int cap, int chi) {
 }
 
 template <typename T>
-int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar, SearchBufs<T>& sb) {
+int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar, SearchBufs<T>& sb,
+                 bool init = true) {
   DevSearch& ds = sb.ds;
   ds.cap = cap;
   ds.N = P->n;
@@ -517,6 +538,7 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * MAXP);
   sb.bt.chi = chi;
   if (!sb.bt.R) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(ds.hist, 0, sizeof(unsigned) * 65536, st));
   CK(cudaMemsetAsync(misc, 0, sizeof(int) * 8, st));
@@ -540,23 +562,34 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   return SPG_OK;
 }
 
+// Output staging at fixed workspace addresses, so that a captured solve can
+// be replayed; copied into the result's own buffers after each run.
+struct OutStage {
+  uint16_t* states;
+  int64_t* E;
+  double* logp;
+  int* n;
+  int* diag;  // near_ties, err, degenerate cuts, Jacobi sweeps
+  double* cand;  // candidates, log-norm of B_1
+};
+
+size_t out_stage_bytes(const spg_problem* P, int cap) {
+  return sizeof(uint16_t) * (size_t)cap * P->n + sizeof(int64_t) * cap + sizeof(double) * cap + 4096;
+}
+
 template <typename T>
-int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result* R) {
+int enqueue_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const Plan& pl,
+                     BoundaryBufs<T>& bb) {
   cudaStream_t st = ctx->stream;
-  const int chi = prm->chi, cap = prm->beam;
-  Plan pl = make_plan(P, chi, 1);
-  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi);
-  int rc = ensure_arena(ctx, need);
-  if (rc) return rc;
-  Arena ar{ctx->arena, 0, ctx->arena_bytes};
-  BoundaryBufs<T> bb;
-  SearchBufs<T> sb;
-  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
-  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb))) return rc;
-  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
-  CK(cudaEventRecord(R->ev[0], st));
-  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, 1))) return rc;
-  CK(cudaEventRecord(R->ev[1], st));
+  CK(cudaMemsetAsync(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
+  CK(cudaMemsetAsync(bb.degc, 0, sizeof(int) * 4, st));
+  return run_boundary<T>(ctx, P, prm, pl, bb, 1);
+}
+
+template <typename T>
+int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, BoundaryBufs<T>& bb,
+                   SearchBufs<T>& sb, const OutStage& o) {
+  cudaStream_t st = ctx->stream;
   DevSearch& ds = sb.ds;
   ds.deg_cuts = bb.degc;
   const int cols = P->cols;
@@ -572,14 +605,130 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
     cur ^= 1;
   }
-  CK(launch_final(P->tb, ds, cur, R->d_states, R->d_E, R->d_logp, R->d_n, st));
-  CK(cudaMemcpyAsync(R->d_diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(launch_final(P->tb, ds, cur, o.states, o.E, o.logp, o.n, st));
+  CK(cudaMemcpyAsync(o.diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(o.diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(o.diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(o.cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(o.cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SPG_OK;
+}
+
+// A solve is a fixed sequence of stream operations given the problem, the
+// parameters and the workspace (everything data-dependent lives on the
+// device), so it is captured into two CUDA graphs (boundary phase, search
+// phase) on its second occurrence and replayed from then on: one graph launch
+// instead of tens of thousands of kernel launches from the host.  The first
+// occurrence runs uncaptured (it also performs the one-time kernel set-up).
+template <typename T>
+int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result* R) {
+  cudaStream_t st = ctx->stream;
+  const int chi = prm->chi, cap = prm->beam;
+  Plan pl = make_plan(P, chi, 1);
+  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi) + out_stage_bytes(P, cap);
+  int rc = ensure_arena(ctx, need);
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  SearchBufs<T> sb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false))) return rc;
+  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false))) return rc;
+  OutStage o;
+  o.states = ar.get<uint16_t>((size_t)cap * P->n);
+  o.E = ar.get<int64_t>(cap);
+  o.logp = ar.get<double>(cap);
+  o.n = ar.get<int>(4);
+  o.diag = ar.get<int>(4);
+  o.cand = ar.get<double>(2);
+  if (!o.cand) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  // plan dims: host data, uploaded outside any capture
+  CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
+
+  spg_ctx::Graph* g = nullptr;
+  for (auto& e : ctx->graphs)
+    if (e.problem == P && e.tsize == (int)sizeof(T) && e.arena == ctx->arena && e.arena_bytes == ctx->arena_bytes &&
+        std::memcmp(&e.prm, prm, sizeof(spg_params)) == 0)
+      g = &e;
+  const bool profiling = kernel_profile().on;
+  const long long l0 = thread_launches();
+  CK(cudaEventRecord(R->ev[0], st));
+  if (g && g->boundary && !profiling) {
+    CK(cudaGraphLaunch(g->boundary, st));
+    CK(cudaEventRecord(R->ev[1], st));
+    CK(cudaGraphLaunch(g->search, st));
+    R->launches = g->launches;
+  } else if (g && !profiling) {
+    cudaGraph_t gb = nullptr, gs = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
+    cudaError_t e1 = cudaStreamEndCapture(st, &gb);
+    if (rc || e1 != cudaSuccess) {
+      if (gb) cudaGraphDestroy(gb);
+      return rc ? rc : fail(ctx, SPG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+    }
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_search<T>(ctx, P, prm, bb, sb, o);
+    e1 = cudaStreamEndCapture(st, &gs);
+    if (rc || e1 != cudaSuccess) {
+      cudaGraphDestroy(gb);
+      if (gs) cudaGraphDestroy(gs);
+      return rc ? rc : fail(ctx, SPG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+    }
+    CK(cudaGraphInstantiate(&g->boundary, gb, 0));
+    CK(cudaGraphInstantiate(&g->search, gs, 0));
+    cudaGraphDestroy(gb);
+    cudaGraphDestroy(gs);
+    g->launches = thread_launches() - l0;
+    CK(cudaGraphLaunch(g->boundary, st));
+    CK(cudaEventRecord(R->ev[1], st));
+    CK(cudaGraphLaunch(g->search, st));
+    R->launches = g->launches;
+  } else {
+    if ((rc = enqueue_boundary<T>(ctx, P, prm, pl, bb))) return rc;
+    CK(cudaEventRecord(R->ev[1], st));
+    if ((rc = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return rc;
+    R->launches = thread_launches() - l0;
+    if (!g && !profiling) {
+      if (ctx->graphs.size() >= 8) {  // keep the most recent entries
+        auto& old = ctx->graphs.front();
+        if (old.boundary) cudaGraphExecDestroy(old.boundary);
+        if (old.search) cudaGraphExecDestroy(old.search);
+        ctx->graphs.erase(ctx->graphs.begin());
+      }
+      spg_ctx::Graph ne;
+      ne.problem = P;
+      ne.prm = *prm;
+      ne.tsize = (int)sizeof(T);
+      ne.arena = ctx->arena;
+      ne.arena_bytes = ctx->arena_bytes;
+      ctx->graphs.push_back(ne);
+    }
+  }
+  // staged outputs into the result's own buffers
+  CK(cudaMemcpyAsync(R->d_states, o.states, sizeof(uint16_t) * (size_t)cap * P->n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_E, o.E, sizeof(int64_t) * cap, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_logp, o.logp, sizeof(double) * cap, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_n, o.n, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_diag, o.diag, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_cand, o.cand, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(R->ev[2], st));
   return SPG_OK;
+}
+
+void drop_graphs(spg_ctx* ctx, const void* problem) {
+  for (spg_ctx* c : std::vector<spg_ctx*>{ctx}) {
+    for (size_t k = 0; k < c->graphs.size();) {
+      auto& e = c->graphs[k];
+      if (problem == nullptr || e.problem == problem) {
+        if (e.boundary) cudaGraphExecDestroy(e.boundary);
+        if (e.search) cudaGraphExecDestroy(e.search);
+        c->graphs.erase(c->graphs.begin() + k);
+      } else {
+        ++k;
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -694,7 +843,11 @@ int spg_create(spg_ctx** out, int device, void* cuda_stream) {
 
 void spg_destroy(spg_ctx* ctx) {
   if (!ctx) return;
+  for (spg_ctx* w : ctx->workers) spg_destroy(w);
+  ctx->workers.clear();
   cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx, nullptr);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -943,6 +1096,11 @@ int spg_problem_potts(spg_ctx* ctx, int32_t grid_rows, int32_t grid_cols, const 
 
 void spg_problem_destroy(spg_problem* P) {
   if (!P) return;
+  if (P->ctx) {
+    cudaSetDevice(P->ctx->device);
+    drop_graphs(P->ctx, P);
+    for (spg_ctx* w : P->ctx->workers) drop_graphs(w, P);
+  }
   if (P->dev) {
     cudaSetDevice(P->ctx->device);
     cudaStreamSynchronize(P->ctx->stream);
@@ -987,11 +1145,60 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
     cudaGetLastError();
     return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
   }
-  const long long l0 = launch_counter().load();
   rc = prm->precision == SPG_FP64 ? solve_impl<double>(ctx, P, prm, R) : solve_impl<float>(ctx, P, prm, R);
-  R->launches = launch_counter().load() - l0;
   if (rc) return cleanup(rc);
   *out = R;
+  return SPG_OK;
+}
+
+int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prms,
+                    spg_result** out) {
+  if (!ctx || !probs || !prms || !out || n < 1) return SPG_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    out[i] = nullptr;
+    if (!probs[i]) return fail(ctx, SPG_EINVAL, "NULL problem in batch");
+    const int rc = check_params(ctx, probs[i], &prms[i]);
+    if (rc) return rc;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  const int K = std::min(n, 16);
+  while ((int)ctx->workers.size() < K) {
+    spg_ctx* w = nullptr;
+    const int rc = spg_create(&w, ctx->device, nullptr);
+    if (rc) return fail(ctx, rc, "worker context creation failed");
+    ctx->workers.push_back(w);
+  }
+  // the batch starts after the work already on the context's stream
+  cudaEvent_t start;
+  CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CK(cudaEventRecord(start, ctx->stream));
+  for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(ctx->workers[k]->stream, start, 0));
+  std::vector<int> rcs(n, SPG_OK);
+  std::vector<std::thread> threads;
+  for (int k = 0; k < K; ++k)
+    threads.emplace_back([&, k] {
+      cudaSetDevice(ctx->device);
+      for (int i = k; i < n; i += K) rcs[i] = spg_solve(ctx->workers[k], probs[i], &prms[i], &out[i]);
+    });
+  for (auto& t : threads) t.join();
+  // later work on the context's stream runs after the batch
+  for (int k = 0; k < K; ++k) {
+    cudaEvent_t done;
+    CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CK(cudaEventRecord(done, ctx->workers[k]->stream));
+    CK(cudaStreamWaitEvent(ctx->stream, done, 0));
+    cudaEventDestroy(done);
+  }
+  cudaEventDestroy(start);
+  for (int i = 0; i < n; ++i)
+    if (rcs[i] != SPG_OK) {
+      const std::string msg = ctx->workers[i % K]->err;
+      for (int j = 0; j < n; ++j) {
+        spg_result_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      return fail(ctx, rcs[i], "batch item " + std::to_string(i) + ": " + msg);
+    }
   return SPG_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -20,6 +21,7 @@ inline std::atomic<long long>& launch_counter() {
 // time between consecutive events is the device time of each kernel (kernels
 // on one stream run one after another).
 struct KernelProfile {
+  std::mutex mu;
   bool on = false;
   std::vector<cudaEvent_t> pool;
   std::vector<const char*> names;
@@ -32,10 +34,18 @@ inline KernelProfile& kernel_profile() {
   return p;
 }
 
+// Kernels enqueued by the calling host thread (a solve counts its own).
+inline long long& thread_launches() {
+  thread_local long long c = 0;
+  return c;
+}
+
 inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0) {
   launch_counter().fetch_add(1, std::memory_order_relaxed);
+  ++thread_launches();
   KernelProfile& p = kernel_profile();
   if (!p.on) return;
+  std::lock_guard<std::mutex> lock(p.mu);
   if (p.used == p.pool.size()) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return;

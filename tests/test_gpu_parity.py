@@ -213,3 +213,23 @@ def test_solve_with_sweeps(spg, ctx):
         np.testing.assert_array_equal(E, ref.energies)
         np.testing.assert_array_equal(st.astype(np.int64), ref.states)
     assert E[0] == ref.energies[0]
+
+
+def test_solve_batch_matches_single_solves(spg, ctx):
+    """Batching: instances of uneven size and per-instance chi solved
+    concurrently give exactly the results of separate solves (and of the
+    oracle when no near tie decides a prune)."""
+    insts = [I.chimera(L, 40 + k, couplings=("pm1" if k % 2 else "gauss"), h_sigma=(0.0 if k % 2 else 0.1))
+             for k, L in enumerate([2, 3, 4, 3, 2, 4, 3])]
+    chis = [8, 16, 12, 8, 16, 16, 4]
+    probs = [spg.spg_problem_ising(ctx, inst) for inst in insts]
+    prms = [spg.params(beta=1.0, chi=c, beam=64, num_sweeps=k % 2) for k, c in enumerate(chis)]
+    batch = spg.spg_solve_batch(ctx, probs, prms)
+    for k, (inst, prob, prm, res) in enumerate(zip(insts, probs, prms, batch)):
+        st, E, lp = res.get()
+        st1, E1, lp1 = spg.spg_solve(ctx, prob, prm).get()
+        np.testing.assert_array_equal(st, st1)
+        np.testing.assert_array_equal(E, E1)
+        np.testing.assert_array_equal(lp, lp1)
+        ref = search.solve(tables.from_ising(inst), search.Params(beta=1.0, chi=chis[k], beam=64, num_sweeps=k % 2))
+        assert E[0] == ref.energies[0]
