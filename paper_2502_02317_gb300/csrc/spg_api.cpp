@@ -653,12 +653,39 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   const bool profiling = kernel_profile().on;
   const long long l0 = thread_launches();
   CK(cudaEventRecord(R->ev[0], st));
-  if (g && g->boundary && !profiling) {
+  if (profiling) {
+    // captured with the profiler's per-kernel event records as graph nodes,
+    // so that the times between them are device times without host gaps
+    cudaGraph_t gb = nullptr, gs = nullptr;
+    cudaGraphExec_t eb = nullptr, es = nullptr;
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
+      ok = cudaStreamEndCapture(st, &gb) == cudaSuccess && rc == SPG_OK;
+    }
+    if (ok && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      rc = enqueue_search<T>(ctx, P, prm, bb, sb, o);
+      ok = cudaStreamEndCapture(st, &gs) == cudaSuccess && rc == SPG_OK;
+    } else {
+      ok = false;
+    }
+    ok = ok && cudaGraphInstantiate(&eb, gb, 0) == cudaSuccess && cudaGraphInstantiate(&es, gs, 0) == cudaSuccess;
+    if (gb) cudaGraphDestroy(gb);
+    if (gs) cudaGraphDestroy(gs);
+    if (!ok) return fail(ctx, SPG_ECUDA, "profiled capture failed");
+    CK(cudaGraphLaunch(eb, st));
+    CK(cudaEventRecord(R->ev[1], st));
+    CK(cudaGraphLaunch(es, st));
+    R->launches = thread_launches() - l0;
+    CK(cudaStreamSynchronize(st));
+    cudaGraphExecDestroy(eb);
+    cudaGraphExecDestroy(es);
+  } else if (g && g->boundary) {
     CK(cudaGraphLaunch(g->boundary, st));
     CK(cudaEventRecord(R->ev[1], st));
     CK(cudaGraphLaunch(g->search, st));
     R->launches = g->launches;
-  } else if (g && !profiling) {
+  } else if (g) {
     cudaGraph_t gb = nullptr, gs = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
@@ -689,7 +716,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     CK(cudaEventRecord(R->ev[1], st));
     if ((rc = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return rc;
     R->launches = thread_launches() - l0;
-    if (!g && !profiling) {
+    if (!g) {
       if (ctx->graphs.size() >= 8) {  // keep the most recent entries
         auto& old = ctx->graphs.front();
         if (old.boundary) cudaGraphExecDestroy(old.boundary);

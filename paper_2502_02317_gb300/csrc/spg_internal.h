@@ -51,7 +51,8 @@ inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0
     if (cudaEventCreate(&e) != cudaSuccess) return;
     p.pool.push_back(e);
   }
-  cudaEventRecord(p.pool[p.used], st);
+  // external: inside a stream capture this becomes an event-record node
+  cudaEventRecordWithFlags(p.pool[p.used], st, cudaEventRecordExternal);
   p.names.push_back(name);
   p.streams.push_back(st);
   p.flops.push_back(flops);
