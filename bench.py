@@ -1,7 +1,8 @@
 """Throughput of the boundary-MPS PEPS search on synthetic Chimera instances.
 
-One step = one full solve (boundary MPSs bottom-up, then the branch-and-bound
-search over every site) of one 16x16 Chimera-like instance: 2048 spins in
+One step = one batch of 8 independent 16x16 Chimera-like instances solved
+concurrently (each a full solve: boundary MPSs bottom-up, then the
+branch-and-bound search over every site), every instance 2048 spins in
 K_{4,4} cells (256-state clusters), J ~ N(0,1), h ~ N(0, 0.1) on the 2^-24
 grid, beta 1, chi 32, one variational sweep per boundary row (the value of
 the paper's example), beam 1024.  Metric: beam states per second (sum over
@@ -29,7 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=1024, sweeps=1)
+WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=1024, sweeps=1, batch=8)
 METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best energy"
 
 
@@ -40,7 +41,8 @@ def make_instance(seed):
 
 def config_dict(extra=None):
     L = WORKLOAD["L"]
-    c = {"workload": f"chimera{L}x{L}_gauss_K44 ({8 * L * L} spins, d=256), beta=1, chi=32, 1 sweep, beam=1024",
+    c = {"workload": f"{WORKLOAD['batch']} x chimera{L}x{L}_gauss_K44 ({8 * L * L} spins, d=256), beta=1, chi=32, "
+                     f"1 sweep, beam=1024",
          "L": WORKLOAD["L"], "spins": 8 * WORKLOAD["L"] ** 2, "cluster_states": 256, "beta": WORKLOAD["beta"],
          "chi": WORKLOAD["chi"], "num_sweeps": WORKLOAD["sweeps"], "beam": WORKLOAD["beam"], "couplings": "J~N(0,1), h~N(0,0.1) on 2^-24 grid",
          "l2": "flushed between timed steps (256 MiB write)"}
@@ -179,6 +181,16 @@ def aggregate_over_ranks(tot_ms: float, tot_cand: float, device="cpu"):
     return float(t.item()), float(c.item())
 
 
+def kernel_profile(spg, ctx, prob, prm):
+    """{kernel: [launches, device ms, flops]} of one solve, timed by event
+    nodes captured into the solve's graph (device times, no host gaps)."""
+    spg.spg_profile(ctx, True)
+    spg.spg_solve(ctx, prob, prm).get()
+    kern = spg.spg_profile_report(ctx)
+    spg.spg_profile(ctx, False)
+    return kern
+
+
 def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -212,18 +224,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--batch", type=int, default=8, help="instances solved concurrently per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--L", type=int, default=None,
                     help="grid side override (profiling of a smaller case of the same kernels)")
     ap.add_argument("--only-main", action="store_true",
-                    help="timed solves only (no end-to-end or FP64 comparison runs): the ncu launch list")
+                    help="timed steps only (no end-to-end, FP64, uneven-batch or profile runs): the ncu "
+                         "launch list")
     args = ap.parse_args()
     if args.L:
         WORKLOAD["L"] = args.L
+    WORKLOAD["batch"] = args.batch
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
 
     world, rank, local = dist_info()
@@ -233,13 +247,19 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2502_02317_gb300 as spg
 
+    NB = args.batch
     stream = torch.cuda.Stream()
     ctx = spg.Context(local, stream=stream.cuda_stream)
-    inst = make_instance(rank_instance_seed(rank))
-    prob = spg.spg_problem_ising(ctx, inst)
+    insts = [make_instance(rank_instance_seed(rank) * 100 + k) for k in range(NB)]
+    probs = [spg.spg_problem_ising(ctx, i) for i in insts]
     prec = spg.SPG_MIXED if args.precision == "mixed" else spg.SPG_FP64
-    prm = spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=prec,
-                     num_sweeps=WORKLOAD["sweeps"])
+
+    def params(p):
+        return spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=p,
+                          num_sweeps=WORKLOAD["sweeps"])
+
+    prm = params(prec)
+    prms = [prm] * NB
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -247,106 +267,133 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    for _ in range(args.warmup):
-        r = spg.spg_solve(ctx, prob, prm)
-        r.get()
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    # warm-up: the first solve of a (problem, params) runs uncaptured, the
+    # second is captured into CUDA graphs, later ones replay them
+    for _ in range(max(args.warmup, 3)):
+        for r in spg.spg_solve_batch(ctx, probs, prms):
+            r.get()
     barrier()
-    times, cands, launches, infos = [], [], [], []
+    times, cands, launches, infos, bests = [], [], [], [], []
     with Clocks(local) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = spg.spg_solve(ctx, prob, prm)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            inf = r.info()
-            infos.append(inf)
-            cands.append(inf["candidates"])
-            launches.append(inf["kernel_launches"])
-            st, E, lp = r.get()
+            rs, ms_step = timed(lambda: spg.spg_solve_batch(ctx, probs, prms))
+            times.append(ms_step)
+            inf = [r.info() for r in rs]
+            infos.append(inf[0])
+            cands.append(sum(i["candidates"] for i in inf))
+            launches.append(sum(i["kernel_launches"] for i in inf))
+            bests = [int(r.get()[1][0]) for r in rs]
     barrier()
     ms = statistics.mean(times)
-    best = int(E[0])
-    tot_cand = sum(cands)
-    tot_ms = sum(times)
-    tot_ms, tot_cand = aggregate_over_ranks(tot_ms, tot_cand, device="cuda")
+    tot_ms, tot_cand = aggregate_over_ranks(sum(times), sum(cands), device="cuda")
     value = tot_cand / (tot_ms / 1e3)
 
-    # end to end through the C ABI from host arrays (tables built and copied,
-    # result copied back) for the same steps
+    line = {"metric": METRIC, "value": value, "unit": "beam states/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == spg.SPG_MIXED else "f64", "data": "synthetic",
+            "config": config_dict({"precision": args.precision,
+                                   "parallelism": f"replicas x{world}, {NB} instances in flight per GPU"}),
+            "gpu_launches": int(sum(launches)), "clocks": clk.summary()}
+    if args.only_main:
+        # per-kernel device times of one more solve (after the timed steps),
+        # to set beside an ncu launch list of the timed step
+        kern = kernel_profile(spg, ctx, probs[0], prm)
+        ktot = sum(v[1] for v in kern.values())
+        line["kernels"] = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4)}
+                           for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+        if rank == 0:
+            print(json.dumps(line))
+        return 0
+
+    # time to solution of one instance (graph replay), its phases
+    for _ in range(3):
+        spg.spg_solve(ctx, probs[0], prm).get()
+    r1, tts_ms = timed(lambda: spg.spg_solve(ctx, probs[0], prm))
+    inf1 = r1.info()
+    line["tts_s"] = tts_ms / 1e3
+    line["best_energies"] = [b * 2.0 ** -insts[0].energy_shift for b in bests]
+    line["phase_ms"] = {"boundary": inf1["ms_boundary"], "search": inf1["ms_search"]}
+    line["diagnostics"] = {"near_ties": inf1["near_ties"], "degenerate_cuts": inf1["degenerate_cuts"],
+                           "jacobi_sweeps_max": inf1["jacobi_sweeps_max"], "error_flags": inf1["error_flags"]}
+
+    # end to end through the C ABI from host arrays: problems built and
+    # copied, the batch solved, results copied back
     e2e_times = []
-    for _ in range(0 if args.only_main else args.steps):
+    for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p2 = spg.spg_problem_ising(ctx, inst)
-        r2 = spg.spg_solve(ctx, p2, prm)
-        st2, E2, lp2 = r2.get()
+        ps = [spg.spg_problem_ising(ctx, i) for i in insts]
+        rs = spg.spg_solve_batch(ctx, ps, prms)
+        outs = [r.get() for r in rs]
         e2e_times.append(time.perf_counter() - t0)
-        r2.close()
-        p2.close()
-    e2e_value = statistics.mean(cands) / statistics.mean(e2e_times) if e2e_times else None
-    n_sites = inst.grid_rows * inst.grid_cols
-    # device tables of the problem: E (int64) + 4 projectors (uint8) per state,
+        for r in rs:
+            r.close()
+        for p_ in ps:
+            p_.close()
+    n_sites = insts[0].grid_rows * insts[0].grid_cols
+    # device tables per problem: E (int64) + 4 projectors (uint8) per state,
     # 2 reduced 16x16 int64 tables, dims, state lists, merge keys per site
-    h2d = n_sites * (8 * 256 + 4 * 256 + 2 * 256 + 8 * 256 * 2 + 4 * 8 + 4 * 17 + 4 * 41) + 4 * n_sites
-    d2h = len(E) * (2 * n_sites + 8 + 8) + 16
+    h2d = NB * (n_sites * (8 * 256 + 4 * 256 + 2 * 256 + 8 * 256 * 2 + 4 * 8 + 4 * 17 + 4 * 41 + 4) + 4)
+    d2h = sum(len(o[1]) * (2 * n_sites + 8 + 8) + 16 for o in outs)
+    line["e2e"] = {"value": statistics.mean(cands) / statistics.mean(e2e_times), "unit": "beam states/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # plain FP64 GPU path on the same instance: time to solution, best energy
-    fp = None
-    if prec != spg.SPG_FP64 and not args.only_main:
-        prm64 = spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=spg.SPG_FP64,
-                           num_sweeps=WORKLOAD["sweeps"])
-        r = spg.spg_solve(ctx, prob, prm64)
-        r.get()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = spg.spg_solve(ctx, prob, prm64)
-        e1.record(stream)
-        e1.synchronize()
-        st64, E64, lp64 = r.get()
-        fp = {"tts_s": e0.elapsed_time(e1) / 1e3, "best_energy": int(E64[0]) * 2.0 ** -inst.energy_shift,
-              "equal_best_energy": bool(int(E64[0]) == best), "speedup_mixed_vs_fp64": e0.elapsed_time(e1) / ms}
+    # plain FP64 GPU path on the same batch: time, equal best energies
+    if prec != spg.SPG_FP64:
+        p64 = [params(spg.SPG_FP64)] * NB
+        rs64, ms64 = timed(lambda: spg.spg_solve_batch(ctx, probs, p64))
+        b64 = [int(r.get()[1][0]) for r in rs64]
+        r641, ms641 = timed(lambda: spg.spg_solve(ctx, probs[0], p64[0]))
+        r641.get()
+        line["fp64_gpu"] = {"batch_ms": ms64, "tts_s": ms641 / 1e3,
+                            "equal_best_energy": all(a == b for a, b in zip(b64, bests)),
+                            "speedup_mixed_vs_fp64": {"batch": ms64 / ms, "single_instance": ms641 / tts_ms}}
 
-    # one extra solve with per-kernel CUDA events (not part of the timed steps)
-    spg.spg_profile(ctx, True)
-    rp = spg.spg_solve(ctx, prob, prm)
-    rp.get()
-    kern = spg.spg_profile_report(ctx)
-    spg.spg_profile(ctx, False)
+    # batching pattern on uneven instances: 64 Chimera L ~ U{6..12}, +-1,
+    # chi in {16, 32} per instance, beam 512, all in flight together
+    import instances as I
+    if WORKLOAD["L"] == 16:
+        un = I.batch_chimera(64, 6, 12, 5000 + rank)
+        up = [spg.spg_problem_ising(ctx, inst) for inst, _ in un]
+        upr = [spg.params(beta=1.0, chi=c, beam=512, precision=prec) for _, c in un]
+        for _ in range(2):
+            for r in spg.spg_solve_batch(ctx, up, upr):
+                r.get()
+        rsu, msu = timed(lambda: spg.spg_solve_batch(ctx, up, upr))
+        cu = sum(r.info()["candidates"] for r in rsu)
+        line["batch_uneven"] = {"instances": 64, "L": "U{6..12}", "chi": "{16,32}", "beam": 512, "ms": msu,
+                                "beam_states_per_s": cu / (msu / 1e3)}
+
+    # one extra solve with per-kernel device times (graph-captured event
+    # nodes; not part of the timed steps): the roofline of the top kernel
+    kern = kernel_profile(spg, ctx, probs[0], prm)
     ktot = sum(v[1] for v in kern.values())
     top = sorted(kern.items(), key=lambda kv: -kv[1][1])
-    kernels = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4),
-                   "avg_us": round(1e3 * v[1] / v[0], 2)} for k, v in top[:8]}
-    peaks, src = measured_peaks()
+    line["kernels"] = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4),
+                           "avg_us": round(1e3 * v[1] / v[0], 2)} for k, v in top[:10]}
     clk_mhz = 2070.0
     # ALU peaks from unit counts: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2 flop x clock
     alu_peak = 152 * (128 if prec == spg.SPG_MIXED else 2) * 2 * clk_mhz * 1e6 / 1e12
     name, (nl, ms_k, fl_k) = next((kv for kv in top if kv[1][2] > 0), top[0])
     achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
-    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": achieved / alu_peak, "traffic": None,
-            "peak_source": f"derived: 152 SMs x {'128 FP32' if prec == spg.SPG_MIXED else '2 FP64'} FMA/clk x 2 x "
-                           f"{clk_mhz:.0f} MHz", "share_of_solve": round(ms_k / ktot, 4),
-            "flops_per_launch": fl_k / nl, "avg_launch_us": 1e3 * ms_k / nl}
-    inf = infos[-1]
-    line = {"metric": METRIC, "value": value, "unit": "beam states/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if prec == spg.SPG_MIXED else "f64", "data": "synthetic",
-            "config": config_dict({"precision": args.precision, "parallelism": f"replicas x{world}"}),
-            "tts_s": ms / 1e3, "best_energy": best * 2.0 ** -inst.energy_shift,
-            "phase_ms": {"boundary": inf["ms_boundary"], "search": inf["ms_search"]},
-            "diagnostics": {"near_ties": inf["near_ties"], "degenerate_cuts": inf["degenerate_cuts"],
-                            "jacobi_sweeps_max": inf["jacobi_sweeps_max"], "error_flags": inf["error_flags"]},
-            "fp64_gpu": fp, "gpu_launches": int(sum(launches)),
-            "e2e": {"value": e2e_value, "unit": "beam states/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "clocks": clk.summary(), "peaks_source": src}
-    line["roofline"] = roof
-    line["kernels"] = kernels
+    peaks, src = measured_peaks()
+    line["roofline"] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                        "frac": achieved / alu_peak, "traffic": None,
+                        "peak_source": f"derived: 152 SMs x {'128 FP32' if prec == spg.SPG_MIXED else '2 FP64'} "
+                                       f"FMA/clk x 2 x {clk_mhz:.0f} MHz",
+                        "share_of_solve": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
+                        "avg_launch_us": 1e3 * ms_k / nl, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                        "peaks_source": src}
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(0)
     if rank == 0:
