@@ -138,11 +138,10 @@ def cpu_oracle_sample(seed, max_sites=6):
         ks = search.key_sites(fg, s)
         children = {}
         for b in beam:
-            left = b.states[s - 1] if j > 0 else 0
-            lc = search.log_conditional(p, B, i, j, b.lenv, b.R, 0, left)
+            lc = search.log_conditional(p, B, i, j, b.lenv, b.R, b.states)
             for x in range(fg.d[s]):
                 st = b.states + (x,)
-                E = b.E + search.delta_energy(p, i, j, x, 0, left)
+                E = b.E + search.delta_energy(fg, s, x, b.states)
                 key = tuple(st[t] for t in ks)
                 cand += 1
                 cur = children.get(key)

@@ -14,7 +14,7 @@ no blocking, fusion or reordering beyond what each step states:
   and the pairwise table of every grid edge, reduced to its distinct rows and
   columns with projectors (Sec. 3.1, "Sparsity").
 * ``peps``     -- Sec. 2, Fig. 1(c): Boltzmann weights at inverse temperature
-  beta and the row MPOs of the PEPS on the square lattice.
+  beta and the row MPOs of the PEPS on the square and king's lattices.
 * ``boundary`` -- Sec. 2, Fig. 1(d) and Sec. 3.1 (``MpsParameters``,
   ``SVDTruncate``): bottom-up boundary MPSs by MPO-MPS zipper application with
   SVD truncation to bond dimension chi, then variational sweeps.

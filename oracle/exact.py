@@ -2,10 +2,12 @@
 
 Test infrastructure only (see the package header).
 
-Everything here works on spins and Eq. 2 directly:
+Everything here works on spins and Eq. 2, or on Potts configurations and
+Eq. 1, directly:
 * ``brute_force``: all 2^n spin configurations (n <= 24), giving the exact
   ground energy and degeneracy, log Z = log sum exp(-beta E), and exact
   conditional marginals of cluster states given a prefix of cluster states;
+* ``potts_all_energies``: every configuration of a small Potts instance;
 * ``chimera_strip``: row transfer matrices of a Chimera-like strip of width
   <= 3 cells over the 4w side-A spins of a row (the only spins with couplers
   to the next row), giving exact log Z (log-sum-exp) and the exact ground
@@ -90,6 +92,36 @@ def exact_conditional(E, beta, shift, cs, site, prefix, d):
         if sel.size:
             out[x] = logsumexp(sel)
     return out - logsumexp(w)
+
+
+def potts_all_energies(inst):
+    """Eq. 1 directly on a Potts instance: the int64 energy of every
+    configuration (mixed radix, site 0 the slowest digit) and the state of
+    every site in each ([n_sites] arrays [prod d]).  Limited to 2^24
+    configurations."""
+    d = [int(v) for v in inst.d]
+    n = len(d)
+    total = int(np.prod(d))
+    if total > 2 ** 24:
+        raise ValueError("brute force is limited to 2^24 configurations")
+    cs = []
+    stride = total
+    for s in range(n):
+        stride //= d[s]
+        cs.append(((np.arange(total, dtype=np.int64) // stride) % d[s]).astype(np.uint16))
+    offs = np.concatenate([[0], np.cumsum(d)]).astype(np.int64)
+    local = np.asarray(inst.local_E, dtype=np.int64)
+    E = np.zeros(total, dtype=np.int64)
+    for s in range(n):
+        E += local[offs[s] + cs[s].astype(np.int64)]
+    off = 0
+    pair = np.asarray(inst.pair_E, dtype=np.int64)
+    for k in range(len(inst.em)):
+        m, q = int(inst.em[k]), int(inst.en[k])
+        T = pair[off:off + d[m] * d[q]].reshape(d[m], d[q])
+        off += d[m] * d[q]
+        E += T[cs[m].astype(np.int64), cs[q].astype(np.int64)]
+    return E, cs
 
 
 def chimera_strip(inst, beta: float):

@@ -1,27 +1,48 @@
-"""Boltzmann weights and the row MPOs of the PEPS (square lattice).
+"""Boltzmann weights and the row MPOs of the PEPS (square and king's lattices).
 
 Test infrastructure only (see the package header).
 
-Paper: Sec. 2 and Fig. 1(c): the Boltzmann distribution p(x) ~ exp(-beta E(x))
-of the clustered Potts model is a PEPS on the square lattice of clusters;
-Sec. 3.1 (``PEPSNetwork``, ``Sparsity``): a site tensor is built from the
-local weights of the cluster and from the pairwise interactions, which reach
-the cluster only through projections of its state.
+Paper: Sec. 2 and Fig. 1(b)-(c): the Boltzmann distribution p(x) ~
+exp(-beta E(x)) of the clustered Potts model on a king's graph (square
+lattice of clusters, with or without the two diagonal couplings of every
+plaquette) is a PEPS on the square lattice of clusters; Sec. 3.1
+(``PEPSNetwork{KingSingleNode, ...}``, ``Sparsity``): a site tensor is built
+from the local weights of the cluster and from the pairwise interactions,
+which reach the cluster only through projections of its state.
 
-Readings taken here:
+Readings taken here (the paper gives no formula for the site tensors):
 * weights are shifted by the minimum of each table so that every weight is
   <= 1: w_s(x) = exp(-beta u (E_s(x) - min E_s)), b_e = exp(-beta u
-  (R_e - min R_e)), u = 2**-energy_shift; the shifts add back into log Z;
-* the Boltzmann matrix of an edge is absorbed into its right (horizontal edge)
-  or lower (vertical edge) site;
-* the MPO of row i maps the up index u (row projection of the cluster above,
-  on the vertical edge into site (i,j)) to the down index s (row projection
-  of this cluster on the vertical edge below it):
-      W[l, r, u, s] = sum_x w(x) b_left[l, P_L(x)] b_up[u, P_U(x)]
-                              [r == P_R(x)] [s == P_D(x)]
-  where l and r are the horizontal bonds (row projections of the left
-  neighbour and of this site on the horizontal edges).  A missing edge is a
-  bond of dimension 1 with projector 0 and weight 1.
+  (E_e - min E_e)), u = 2**-energy_shift; the shifts add back into log Z;
+* a projection of cluster (i, j) onto a set of its edges numbers the distinct
+  combinations of table rows (x as the table's row variable) or columns (x as
+  its column variable) of those edges in order of first occurrence, x
+  ascending; an empty set gives the single class 0.  The classes used:
+      P_L(x): edges to (i, j-1) and (i-1, j-1)        (left, up-left)
+      P_U(x): edge to (i-1, j)                         (up)
+      P_R(x): edges to (i, j+1) and (i-1, j+1)        (right, up-right)
+      P_D(x): edges to (i+1, j-1), (i+1, j), (i+1, j+1) (everything below)
+      P_G(x): edge to (i+1, j+1)                       (down-right)
+  On the square lattice P_L, P_U, P_R, P_D are the projections of the single
+  left, up, right and down edges and P_G has one class;
+* the physical index of the boundary MPS below row i-1 at column j is P_D of
+  cluster (i-1, j), so every edge between rows i-1 and i is carried in the
+  tensors of row i: the up and up-left edges by b_up and b_left below, the
+  up-right edge (i-1, j+1)-(i, j) by site (i, j+1), which sees the P_R
+  class a of (i, j) on its left bond and the P_D class u of (i-1, j+1)
+  above;
+* the horizontal bond between columns j-1 and j of row i is the pair
+  l = (a, g) = a * G + g: a the P_R class of (i, j-1), g the P_G class of
+  (i-1, j-1) (G classes; g carries the up-left edge of (i, j));
+* the MPO of row i maps the up index u (P_D class of cluster (i-1, j)) to the
+  down index s (P_D class of cluster (i, j)):
+      W[(a, g), (a', g'), u, s] = b_ad[a, u] [g' == P_G(u)]
+          sum_x w(x) b_left[(a, g), P_L x] b_up[u, P_U x] [a' == P_R x] [s == P_D x]
+  with b_left[(a, g), h] the product of the Boltzmann factors of the left and
+  up-left edges between class representatives (first states of the
+  classes), b_up the up edge's, b_ad the up-right edge's of the left
+  neighbour, and P_G(u) the down-right class of the upper cluster's states
+  in class u.  Row 0 has u of dimension 1, the last row s of dimension 1.
 """
 from __future__ import annotations
 
@@ -29,7 +50,20 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .tables import SQUARE, FactorGraph
+from .tables import FactorGraph
+
+
+def classes(d: int, vectors: list):
+    """First-occurrence classes of x in range(d) by the tuple of vectors[k][x]
+    (each an array [d, n_k]); returns (P [d], representatives [n_classes])."""
+    index, P, reps = {}, np.empty(d, dtype=np.int64), []
+    for x in range(d):
+        key = b"".join(np.ascontiguousarray(v[x]).tobytes() for v in vectors)
+        if key not in index:
+            index[key] = len(index)
+            reps.append(x)
+        P[x] = index[key]
+    return P, np.array(reps, dtype=np.int64)
 
 
 @dataclass
@@ -38,17 +72,26 @@ class SiteData:
     E: np.ndarray  # int64 [d] local table
     w: np.ndarray  # float64 [d] shifted local weights
     PL: np.ndarray
-    PR: np.ndarray
     PU: np.ndarray
+    PR: np.ndarray
     PD: np.ndarray
-    DL: int
-    DR: int
-    DU: int
-    DD: int
-    b_left: np.ndarray  # [DL, ncols] Boltzmann matrix of the edge from the left
-    b_up: np.ndarray  # [DU, ncols] Boltzmann matrix of the edge from above
-    E_left: np.ndarray  # int64 full table of the left edge [d_left, d] (or None)
-    E_up: np.ndarray  # int64 full table of the up edge [d_up, d] (or None)
+    PG: np.ndarray
+    repR: np.ndarray  # first state of each P_R class
+    repD: np.ndarray  # first state of each P_D class
+    NL: int
+    NU: int
+    NR: int
+    ND: int
+    NG: int
+    DL: int  # left bond = NR(i, j-1) * NG(i-1, j-1)
+    DR: int  # right bond = NR(i, j) * NG(i-1, j)
+    DU: int  # up index = ND(i-1, j)
+    Gin: int  # NG(i-1, j-1): the g range of the left bond
+    Gout: int  # NG(i-1, j): the g range of the right bond
+    b_left: np.ndarray  # [DL, NL]
+    b_up: np.ndarray  # [DU, NU]
+    b_ad: np.ndarray  # [NR(i, j-1), DU]
+    g_of_u: np.ndarray  # [DU] P_G class of the upper cluster's P_D class u
 
 
 @dataclass
@@ -70,12 +113,54 @@ class PEPS:
         return self.sites[i * self.fg.cols + j]
 
 
+def _incident(fg: FactorGraph, s: int, t: int):
+    """Table rows of cluster s on the edge to cluster t ([d_s, d_t]), or None."""
+    e = fg.edge(min(s, t), max(s, t))
+    if e is None:
+        return None
+    return e.E if s < t else e.E.T
+
+
+def _class_of(fg: FactorGraph, s: int, nbrs: list):
+    vecs = []
+    for t in nbrs:
+        if t is None:
+            continue
+        T = _incident(fg, s, t)
+        if T is not None:
+            vecs.append(T)
+    return classes(fg.d[s], vecs)
+
+
 def build(fg: FactorGraph, beta: float) -> PEPS:
-    if fg.node_type != SQUARE:
-        raise NotImplementedError("only the square lattice is built here")
     u = 2.0 ** (-fg.shift)
     rows, cols = fg.rows, fg.cols
+
+    def at(i, j):
+        return i * cols + j if 0 <= i < rows and 0 <= j < cols else None
+
     log_offset = 0.0
+    cls = []
+    for s in range(fg.n_sites):
+        i, j = divmod(s, cols)
+        PL, repL = _class_of(fg, s, [at(i, j - 1), at(i - 1, j - 1)])
+        PU, repU = _class_of(fg, s, [at(i - 1, j)])
+        PR, repR = _class_of(fg, s, [at(i, j + 1), at(i - 1, j + 1)])
+        PD, repD = _class_of(fg, s, [at(i + 1, j - 1), at(i + 1, j), at(i + 1, j + 1)])
+        PG, repG = _class_of(fg, s, [at(i + 1, j + 1)])
+        cls.append(dict(PL=PL, repL=repL, PU=PU, repU=repU, PR=PR, repR=repR, PD=PD, repD=repD, PG=PG,
+                        repG=repG))
+
+    def boltz(s, t, rs, rt):
+        """Boltzmann factors of edge (s, t) between state lists rs of s and
+        rt of t, shifted by the table's minimum ([len(rs), len(rt)]), or
+        ones when there is no edge."""
+        T = _incident(fg, s, t) if (s is not None and t is not None) else None
+        if T is None:
+            return np.ones((len(rs), len(rt)))
+        mn = float(T.min())
+        return np.exp(-beta * u * (T[np.ix_(rs, rt)] - mn).astype(np.float64))
+
     sites = []
     for s in range(fg.n_sites):
         i, j = divmod(s, cols)
@@ -83,32 +168,56 @@ def build(fg: FactorGraph, beta: float) -> PEPS:
         E = fg.E_loc[s]
         w = np.exp(-beta * u * (E - E.min()).astype(np.float64))
         log_offset += -beta * u * float(E.min())
-        zeros = np.zeros(d, dtype=np.int64)
-        one = np.ones((1, 1))
-        eL = fg.edge(s - 1, s) if j > 0 else None
-        eR = fg.edge(s, s + 1) if j + 1 < cols else None
-        eU = fg.edge(s - cols, s) if i > 0 else None
-        eD = fg.edge(s, s + cols) if i + 1 < rows else None
-        PL, DL, bL = (eL.Pn, eL.R.shape[0], None) if eL is not None else (zeros, 1, one)
-        PU, DU, bU = (eU.Pn, eU.R.shape[0], None) if eU is not None else (zeros, 1, one)
-        PR, DR = (eR.Pm, eR.R.shape[0]) if eR is not None else (zeros, 1)
-        PD, DD = (eD.Pm, eD.R.shape[0]) if eD is not None else (zeros, 1)
-        if eL is not None:
-            bL = np.exp(-beta * u * (eL.R - eL.R.min()).astype(np.float64))
-        if eU is not None:
-            bU = np.exp(-beta * u * (eU.R - eU.R.min()).astype(np.float64))
-        sites.append(SiteData(d, E, w, PL, PR, PU, PD, DL, DR, DU, DD, bL, bU,
-                              eL.E if eL is not None else None, eU.E if eU is not None else None))
+        c = cls[s]
+        left, upleft, up = at(i, j - 1), at(i - 1, j - 1), at(i - 1, j)
+        one = np.zeros(1, np.int64)
+        # left bond (a, g): P_R class of the left cluster, P_G class of the
+        # up-left one
+        repRl = cls[left]["repR"] if left is not None else one
+        repGul = cls[upleft]["repG"] if upleft is not None else one
+        NRl, Gin = len(repRl), len(repGul)
+        bh = boltz(left, s, repRl, c["repL"])  # [NRl, NL]
+        bd = boltz(upleft, s, repGul, c["repL"])  # [Gin, NL]
+        b_left = (bh[:, None, :] * bd[None, :, :]).reshape(NRl * Gin, len(c["repL"]))
+        # up index: P_D class of the upper cluster
+        repDu = cls[up]["repD"] if up is not None else one
+        b_up = boltz(up, s, repDu, c["repU"])  # [DU, NU]
+        # up-right edge (i-1, j) - (i, j-1) of the left neighbour
+        b_ad = boltz(up, left, repDu, repRl).T  # [NRl, DU]
+        if up is not None:
+            Gout = len(cls[up]["repG"])
+            g_of_u = cls[up]["PG"][repDu]
+        else:
+            Gout, g_of_u = 1, np.zeros(1, np.int64)
+        NR = len(c["repR"])
+        sites.append(SiteData(d, E, w, c["PL"], c["PU"], c["PR"], c["PD"], c["PG"], c["repR"], c["repD"],
+                              len(c["repL"]), len(c["repU"]), NR, len(c["repD"]), len(c["repG"]),
+                              NRl * Gin, NR * Gout, len(repDu), Gin, Gout, b_left, b_up, b_ad, g_of_u))
     for e in fg.edges.values():
-        log_offset += -beta * u * float(e.R.min())
+        log_offset += -beta * u * float(e.E.min())
     return PEPS(fg, beta, sites, log_offset)
+
+
+def site_terms(st: SiteData, l: int, u: int):
+    """The terms of W[l, :, u, :] one state x at a time: for every x the
+    weight (everything in W's definition but the sum over x) and the output
+    indices r = (P_R x, P_G(u)), s = P_D x.  Returns (coef [d], r [d], s [d])."""
+    a = l // st.Gin
+    coef = st.b_ad[a, u] * st.w * st.b_left[l, st.PL] * st.b_up[u, st.PU]
+    r = st.PR * st.Gout + int(st.g_of_u[u])
+    return coef, r, st.PD
 
 
 def mpo_site(st: SiteData) -> np.ndarray:
     """Dense W[l, r, u, s] of one site (definition in the module header)."""
-    W = np.zeros((st.DL, st.DR, st.DU, st.DD))
-    for x in range(st.d):
-        W[:, st.PR[x], :, st.PD[x]] += st.w[x] * np.outer(st.b_left[:, st.PL[x]], st.b_up[:, st.PU[x]])
+    W = np.zeros((st.DL, st.DR, st.DU, st.ND))
+    for u in range(st.DU):
+        terms = [site_terms(st, l, u) for l in range(st.DL)]
+        C = np.stack([t[0] for t in terms])  # [DL, d]
+        _, r, s = terms[0]  # r and s do not depend on l
+        onehot = np.zeros((st.d, st.DR * st.ND))
+        onehot[np.arange(st.d), r * st.ND + s] = 1.0
+        W[:, :, u, :] = (C @ onehot).reshape(st.DL, st.DR, st.ND)
     return W
 
 

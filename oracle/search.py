@@ -13,17 +13,18 @@ energies and estimated probabilities (Sec. 2.2).
 
 Readings taken here:
 * order: row-major over the clusters of the grid;
-* conditional of site (i, j) given the fixed prefix: with u_k the down
-  projection of cluster (i-1, k), h the right projection of cluster (i, j-1),
-  Lenv = prod_{k<j} B_{i+1}[k][:, P_D(x_{i,k}), :] and the right environment
-      R_{j}[a, l] = sum_x w(x) b_left[l, P_L x] b_up[u_j, P_U x]
-                    sum_a' B_{i+1}[j][a, P_D x, a'] R_{j+1}[a', P_R x],
+* conditional of site (i, j) given the fixed prefix (W and its single-state
+  terms as in ``peps``): with u_k the up index of site (i, k) (P_D class of
+  cluster (i-1, k)), l the left bond fixed by clusters (i, j-1) and
+  (i-1, j-1), Lenv = prod_{k<j} B_{i+1}[k][:, P_D(x_{i,k}), :] and the right
+  environment
+      R_j[a, l] = sum_{r, s, a'} W_j[l, r, u_j, s] B_{i+1}[j][a, s, a'] R_{j+1}[a', r],
   R_L = 1, the weight of state x is
-      q(x) = w(x) b_left[h, P_L x] b_up[u_j, P_U x]
-             sum_{a,a'} Lenv[a] B_{i+1}[j][a, P_D x, a'] R_{j+1}[a', P_R x]
-  and log p(x | prefix) = log q(x) - log sum_x q(x), in FP64.  A truncated
-  boundary MPS can make q(x) slightly negative; such a weight counts as 0
-  (log p = -inf);
+      q(x) = c_x sum_{a,a'} Lenv[a] B_{i+1}[j][a, s_x, a'] R_{j+1}[a', r_x]
+  where c_x, r_x, s_x are the coefficient and the output indices of x's term
+  of W_j[l, :, u_j, :], and log p(x | prefix) = log q(x) - log sum_x q(x), in
+  FP64.  A truncated boundary MPS can make q(x) slightly negative; such a
+  weight counts as 0 (log p = -inf);
 * a child's log-probability is its parent's plus the log-conditional; its
   partial energy is the parent's plus E_j(x) and the pairwise terms with
   already fixed neighbours (exact integers);
@@ -87,8 +88,26 @@ def key_sites(fg: FactorGraph, s: int) -> list:
     return out
 
 
+def _u(p: peps_mod.PEPS, i: int, j: int, prefix) -> int:
+    """Up index of site (i, j): P_D class of the fixed cluster (i-1, j)."""
+    return 0 if i == 0 else int(p.site(i - 1, j).PD[prefix[(i - 1) * p.cols + j]])
+
+
+def _l(p: peps_mod.PEPS, i: int, j: int, prefix) -> int:
+    """Left bond of site (i, j) given the fixed clusters (i, j-1) and
+    (i-1, j-1): (P_R class, P_G class)."""
+    if j == 0:
+        return 0
+    st = p.site(i, j)
+    a = int(p.site(i, j - 1).PR[prefix[i * p.cols + j - 1]])
+    g = int(p.site(i - 1, j - 1).PG[prefix[(i - 1) * p.cols + j - 1]]) if i > 0 else 0
+    return a * st.Gin + g
+
+
 def right_envs(p: peps_mod.PEPS, B: bnd.MPS, i: int, upper_states) -> list:
-    """R_{j} for j = 1 .. L (index j -> [chi_j, DL_j]); R_L = [[1]]."""
+    """R_{j} for j = 1 .. L (index j -> [chi_j, DL_j]); R_L = [[1]]:
+        R_j[a, l] = sum_{r, s, a'} W_j[l, r, u_j, s] B[j][a, s, a'] R_{j+1}[a', r]
+    with u_j the up index of site (i, j) (the row above fixed)."""
     L = p.cols
     R = [None] * (L + 1)
     R[L] = np.ones((1, 1))
@@ -97,35 +116,34 @@ def right_envs(p: peps_mod.PEPS, B: bnd.MPS, i: int, upper_states) -> list:
         uj = 0 if i == 0 else int(p.site(i - 1, j).PD[upper_states[j]])
         A = B.sites[j]
         Rn = np.zeros((A.shape[0], st.DL))
-        for x in range(st.d):
-            v = A[:, st.PD[x], :] @ R[j + 1][:, st.PR[x]]
-            Rn += (st.w[x] * st.b_up[uj, st.PU[x]]) * np.outer(v, st.b_left[:, st.PL[x]])
+        for l in range(st.DL):
+            coef, r, s = peps_mod.site_terms(st, l, uj)
+            V = np.einsum("axb,bx->ax", A[:, s, :], R[j + 1][:, r])  # [chi, d]
+            Rn[:, l] = V @ coef
         R[j] = Rn / np.max(np.abs(Rn))
     return R
 
 
-def log_conditional(p, B, i, j, lenv, R, upper_state_j, left_state):
-    """log p(x | prefix) for all x of site (i, j) (formula in the header)."""
+def log_conditional(p, B, i, j, lenv, R, prefix):
+    """log p(x | prefix) for all x of site (i, j) (formula in the header);
+    prefix = states of the sites before (i, j) in row-major order."""
     st = p.site(i, j)
-    uj = 0 if i == 0 else int(p.site(i - 1, j).PD[upper_state_j])
-    h = 0 if j == 0 else int(p.site(i, j - 1).PR[left_state])
+    coef, r, s = peps_mod.site_terms(st, _l(p, i, j, prefix), _u(p, i, j, prefix))
     A = B.sites[j]
     q = np.empty(st.d)
     for x in range(st.d):
-        q[x] = (st.w[x] * st.b_left[h, st.PL[x]] * st.b_up[uj, st.PU[x]]
-                * float(lenv @ A[:, st.PD[x], :] @ R[j + 1][:, st.PR[x]]))
+        q[x] = coef[x] * float(lenv @ A[:, s[x], :] @ R[j + 1][:, r[x]])
     q = np.maximum(q, 0.0)
     with np.errstate(divide="ignore"):
         return np.log(q) - np.log(np.sum(q))
 
 
-def delta_energy(p, i, j, x, upper_state, left_state) -> int:
-    st = p.site(i, j)
-    dE = int(st.E[x])
-    if st.E_left is not None:
-        dE += int(st.E_left[left_state, x])
-    if st.E_up is not None:
-        dE += int(st.E_up[upper_state, x])
+def delta_energy(fg: FactorGraph, s: int, x: int, prefix) -> int:
+    """E_s(x) plus the pairwise terms of x with the fixed clusters."""
+    dE = int(fg.E_loc[s][x])
+    for (m, n), e in fg.edges.items():
+        if n == s:
+            dE += int(e.E[prefix[m], x])
     return dE
 
 
@@ -158,12 +176,10 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
         children = {}
         n_cand = 0
         for b in beam:
-            up = b.states[s - cols] if i > 0 else 0
-            left = b.states[s - 1] if j > 0 else 0
-            lc = log_conditional(p, B, i, j, b.lenv, b.R, up, left)
+            lc = log_conditional(p, B, i, j, b.lenv, b.R, b.states)
             for x in range(fg.d[s]):
                 st = b.states + (x,)
-                E = b.E + delta_energy(p, i, j, x, up, left)
+                E = b.E + delta_energy(fg, s, x, b.states)
                 key = tuple(st[t] for t in ks) if prm.merge else st
                 n_cand += 1
                 cur = children.get(key)
@@ -216,7 +232,5 @@ def debug_marginals(fg: FactorGraph, prm: Params, site: int, prefixes, boundary=
         for k in range(j):
             v = lenv @ B.sites[k][:, p.site(i, k).PD[pre[i * cols + k]], :]
             lenv = v / np.max(np.abs(v))
-        up = pre[site - cols] if i > 0 else 0
-        left = pre[site - 1] if j > 0 else 0
-        out.append(log_conditional(p, B, i, j, lenv, R, up, left))
+        out.append(log_conditional(p, B, i, j, lenv, R, pre))
     return np.array(out)

@@ -283,3 +283,116 @@ def test_cut_off_prob_drops_improbable_children():
     b = search.solve(fg, search.Params(beta=1.0, chi=16, beam=256, cut_off_prob=1e-3))
     assert len(b.states) <= len(a.states)
     assert all(np.max(b.log_probs) - lp <= -np.log(1e-3) * len(fg.d) for lp in b.log_probs)
+
+
+# ---------------------------------------------------------------- king's graph (diagonal couplings)
+
+def _potts_brute(inst, beta):
+    E, cs = exact.potts_all_energies(inst)
+    u = 2.0 ** (-inst.energy_shift)
+    return E, cs, exact.logsumexp(-beta * u * E.astype(np.float64))
+
+
+@pytest.mark.parametrize("L,cols,d,seed,beta", [(2, 3, 3, 5, 0.7), (3, 3, 3, 1, 1.3), (3, 4, 2, 2, 0.5),
+                                                (4, 3, 2, 3, 1.0)])
+def test_king_potts_log_partition_brute_force(L, cols, d, seed, beta):
+    """King's-graph Potts (all 8-neighbour edges): untruncated boundary MPSs
+    give the exact log Z of Eq. 1."""
+    inst = I.king_potts(L, d, seed, cols=cols)
+    _, _, ref = _potts_brute(inst, beta)
+    p = peps.build(tables.from_potts(inst), beta)
+    assert boundary.log_partition(p, 512) == pytest.approx(ref, rel=1e-12)
+
+
+def test_king_ising_example_shape_log_partition():
+    """The paper's example shape and beta: 3x3 king's graph of 2-spin
+    clusters (18 spins), beta 2, against Eq. 2 enumerated over all spins.
+    No truncation happens (the value is the same at chi 64 and 1024); the
+    SVDs carry an absolute error ~eps * s_1, which reaches weights 1e-7
+    below the largest at beta 2, hence the looser bound there."""
+    inst = I.king_ising(3, 3, 2, 4)
+    for beta, rel in ((1.0, 1e-12), (2.0, 1e-9)):
+        ref = exact.brute_force(inst, beta)["logZ"]
+        p = peps.build(tables.from_ising(inst), beta)
+        assert boundary.log_partition(p, 256) == pytest.approx(ref, rel=rel)
+
+
+def test_king_diagonals_change_log_partition():
+    """Dropping the diagonal tables changes Z: the pin above sees them."""
+    inst = I.king_potts(3, 3, 7)
+    keep = [k for k in range(len(inst.em))
+            if abs(int(inst.em[k]) // 3 - int(inst.en[k]) // 3) + abs(int(inst.em[k]) % 3 - int(inst.en[k]) % 3) == 1]
+    d = 3
+    pair = np.concatenate([inst.pair_E[k * d * d:(k + 1) * d * d] for k in keep])
+    sq = I.PottsInstance(inst.grid_rows, inst.grid_cols, inst.d, inst.local_E, inst.em[keep], inst.en[keep], pair,
+                         inst.energy_shift, I.SQUARE)
+    _, _, ref_sq = _potts_brute(sq, 1.0)
+    _, _, ref_k = _potts_brute(inst, 1.0)
+    assert abs(ref_sq - ref_k) > 1e-3
+    p = peps.build(tables.from_potts(sq), 1.0)
+    assert boundary.log_partition(p, 512) == pytest.approx(ref_sq, rel=1e-12)
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_king_lattice_transforms_log_partition(k):
+    """The 8 symmetries of the square grid map a king's graph onto itself
+    and leave Z unchanged (rotations and reflections move diagonals onto
+    anti-diagonals)."""
+    inst = I.king_potts(3, 2, 11, cols=4)
+    _, _, ref = _potts_brute(inst, 0.8)
+    rows, cols = inst.grid_rows, inst.grid_cols
+    # k < 4: rotate k times by 90 degrees, (i, j) -> (j, rows - 1 - i) on the
+    # current grid; k >= 4: reflect j first
+    R2, C2 = (rows, cols) if k % 2 == 0 else (cols, rows)
+    new_of = {}
+    for i in range(rows):
+        for j in range(cols):
+            a, b = i, j
+            if k >= 4:
+                b = cols - 1 - b  # reflect first
+            for t in range(k % 4):
+                a, b = b, ((rows if t % 2 == 0 else cols) - 1) - a
+            new_of[i * cols + j] = a * C2 + b
+    n = rows * cols
+    d = int(inst.d[0])
+    old_of = {v: u for u, v in new_of.items()}
+    local = np.concatenate([inst.local_E[old_of[s] * d:(old_of[s] + 1) * d] for s in range(n)])
+    em = np.array([new_of[int(v)] for v in inst.em], np.int32)
+    en = np.array([new_of[int(v)] for v in inst.en], np.int32)
+    t = I.PottsInstance(R2, C2, inst.d, local, em, en, inst.pair_E, inst.energy_shift, I.KING)
+    p = peps.build(tables.from_potts(t), 0.8)
+    assert boundary.log_partition(p, 512) == pytest.approx(ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("make,beta,sites", [
+    (lambda: I.king_potts(3, 3, 21), 1.0, [0, 2, 3, 4, 5, 7, 8]),
+    (lambda: I.king_potts(3, 2, 22, cols=4), 0.6, [1, 4, 5, 6, 9, 11]),
+])
+def test_king_marginals_vs_brute_force(make, beta, sites):
+    """Untruncated contraction on a king's graph: the search's conditionals
+    equal the exact conditionals of Eq. 1 for random prefixes."""
+    inst = make()
+    fg = tables.from_potts(inst)
+    E, cs, _ = _potts_brute(inst, beta)
+    rng = np.random.default_rng(3)
+    prm = search.Params(beta=beta, chi=512)
+    for s in sites:
+        prefixes = [rand_states(fg, rng)[:s] for _ in range(3)]
+        got = search.debug_marginals(fg, prm, s, prefixes)
+        for pre, g in zip(prefixes, got):
+            ref = exact.exact_conditional(E, beta, inst.energy_shift, cs, s, pre, fg.d[s])
+            np.testing.assert_allclose(g, ref, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_king_search_finds_brute_force_ground_state(seed):
+    """Exact marginals and a beam wide enough to hold every merge class: the
+    search returns the brute-force ground state and its energy."""
+    inst = I.king_potts(3, 3, 30 + seed)
+    fg = tables.from_potts(inst)
+    E, cs, _ = _potts_brute(inst, 1.0)
+    k = int(np.argmin(E))
+    res = search.solve(fg, search.Params(beta=1.0, chi=512, beam=4096))
+    assert int(res.energies[0]) == int(E.min())
+    assert [int(v) for v in res.states[0]] == [int(c[k]) for c in cs]
+    assert tables.energy(fg, res.states[0]) == int(E.min())
