@@ -118,7 +118,15 @@ const char* spg_last_error(const spg_ctx* ctx);
  *                             clusters that are not grid neighbours of that
  *                             type is SPG_EINVAL
  * A cluster's state is x = sum_k b_k 2^k over its spins in ascending index,
- * with s = 2 b - 1 (Sec. 2: clusters become Potts variables). */
+ * with s = 2 b - 1 (Sec. 2: clusters become Potts variables).
+ * King's graphs (Sec. 2, Fig. 1(b)): diagonal couplings are carried by the
+ * PEPS through joint projections of each cluster onto its edges (the
+ * boundary-MPS physical index of a cluster is its projection onto all three
+ * edges below it; the row MPO's bond pairs the left cluster's projection with
+ * the up-left cluster's down-right projection, up to 16 x 16).  A joint
+ * projection with more than 16 classes is SPG_EUNSUPPORTED.  Variational
+ * sweeps (num_sweeps > 0) are built for the square lattice only: a problem
+ * with diagonal couplings solved with num_sweeps > 0 is SPG_EUNSUPPORTED. */
 int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei,
                       const int32_t* ej, const double* J, const double* h,
                       const int32_t* cluster_of_spin, int32_t grid_rows, int32_t grid_cols,

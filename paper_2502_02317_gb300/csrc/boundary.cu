@@ -39,38 +39,58 @@ __device__ __forceinline__ T dexp(double x) {
 }
 
 // ---------------------------------------------------------------- weights (S2)
-// One block per site: w = exp(-beta u (E - min E)), bL/bU from RL/RU alike.
+// One block per site: w = exp(-beta u (E - min E)); bL, bU, bA from RL, RU,
+// RA alike, each over its valid entries (zero elsewhere).
 template <typename T>
 __global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u) {
   const int s = blockIdx.x;
   const int d = tb.d[s];
-  __shared__ long long mn[3];
-  if (threadIdx.x == 0) {
-    long long a = LLONG_MAX, b = LLONG_MAX, c = LLONG_MAX;
-    for (int x = 0; x < d; ++x) a = min(a, (long long)tb.E[(size_t)s * tb.dmax + x]);
-    const int* dm = tb.dims + s * 8;
-    for (int i = 0; i < dm[0]; ++i)
-      for (int j = 0; j < dm[4]; ++j) b = min(b, (long long)tb.RL[(size_t)s * 256 + i * 16 + j]);
-    for (int i = 0; i < dm[2]; ++i)
-      for (int j = 0; j < dm[5]; ++j) c = min(c, (long long)tb.RU[(size_t)s * 256 + i * 16 + j]);
-    mn[0] = a;
-    mn[1] = b;
-    mn[2] = c;
+  const int* dm = tb.dims + s * DIMW;
+  const int DL = dm[D_DL], NL = dm[D_NL], DU = dm[D_DU], NU = dm[D_NU], NRl = dm[D_NRL];
+  const int64_t* RL = tb.RL + (size_t)s * tb.lstride;
+  __shared__ long long mn[4];
+  __shared__ long long red[32];
+  // minima: one pass per table, warp 0 folds the block's partial minima
+  for (int t = 0; t < 4; ++t) {
+    long long m = LLONG_MAX;
+    if (t == 0)
+      for (int x = threadIdx.x; x < d; x += blockDim.x) m = min(m, (long long)tb.E[(size_t)s * tb.dmax + x]);
+    else if (t == 1)
+      for (int e = threadIdx.x; e < DL * NL; e += blockDim.x) m = min(m, (long long)RL[(e / NL) * MAXP + e % NL]);
+    else if (t == 2)
+      for (int e = threadIdx.x; e < DU * NU; e += blockDim.x)
+        m = min(m, (long long)tb.RU[(size_t)s * 256 + (e / NU) * 16 + e % NU]);
+    else
+      for (int e = threadIdx.x; e < NRl * DU; e += blockDim.x)
+        m = min(m, (long long)tb.RA[(size_t)s * 256 + (e / DU) * 16 + e % DU]);
+    for (int o = 16; o > 0; o >>= 1) m = min(m, (long long)__shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long r = LLONG_MAX;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = min(r, red[w]);
+      mn[t] = r;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const int* dm = tb.dims + s * 8;
   for (int x = threadIdx.x; x < tb.dmax; x += blockDim.x) {
     T v = T(0);
     if (x < d) v = dexp<T>(-beta_u * (double)(tb.E[(size_t)s * tb.dmax + x] - mn[0]));
     wt.w[(size_t)s * tb.dmax + x] = v;
   }
+  for (int e = threadIdx.x; e < tb.lstride; e += blockDim.x) {
+    const int l = e / MAXP, h = e % MAXP;
+    T v = T(0);
+    if (l < DL && h < NL) v = dexp<T>(-beta_u * (double)(RL[e] - mn[1]));
+    wt.bL[(size_t)s * tb.lstride + e] = v;
+  }
   for (int e = threadIdx.x; e < 256; e += blockDim.x) {
     const int i = e >> 4, j = e & 15;
-    T vl = T(0), vu = T(0);
-    if (i < dm[0] && j < dm[4]) vl = dexp<T>(-beta_u * (double)(tb.RL[(size_t)s * 256 + e] - mn[1]));
-    if (i < dm[2] && j < dm[5]) vu = dexp<T>(-beta_u * (double)(tb.RU[(size_t)s * 256 + e] - mn[2]));
-    wt.bL[(size_t)s * 256 + e] = vl;
+    T vu = T(0), va = T(0);
+    if (i < DU && j < NU) vu = dexp<T>(-beta_u * (double)(tb.RU[(size_t)s * 256 + e] - mn[2]));
+    if (i < NRl && j < DU) va = dexp<T>(-beta_u * (double)(tb.RA[(size_t)s * 256 + e] - mn[3]));
     wt.bU[(size_t)s * 256 + e] = vu;
+    wt.bA[(size_t)s * 256 + e] = va;
   }
 }
 
@@ -267,22 +287,30 @@ __global__ void k_zip_T1(const T* __restrict__ B, int chiL, int p, int chiR, con
   }
 }
 
-// M[(l*chiL + a)][(u*K + k)] = sum_h bL[l][h] sum_{x: PL x = h} bU[u][PU x] w(x) T1[a][PD x][PR x][k]
-// One block per (a, chunk of k).
+// M[(l*chiL + a)][(u*K + k)] = bA[l / Gin][u] sum_h bL[l][h] Y_u[h],
+//   Y_u[h] = sum_{x: PL x = h} bU[u][PU x] w(x) T1[a][PD x][PR x * Gout + gD_up[u]][k]
+// (gD_up: the upper site's PD -> PG map; 0 in row 0).  One block per
+// (a, chunk of k); dynamic shared memory holds the k-slice of T1 [p][DR] and
+// the site's bL [DL][NL].
 template <typename T>
 __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __restrict__ T1, int chiL,
                         int p, int DR, int K, int DL, int DU, int kchunk, T* __restrict__ M) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sT = reinterpret_cast<T*>(smem_raw);  // [p][DR]
+  T* sbL = sT + (size_t)p * DR;            // [DL][NL]
   __shared__ T sw[MAXS];
   __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
   __shared__ int16_t sx[MAXS];
   __shared__ int soff[MAXP + 1];
-  __shared__ T sbL[256], sbU[256];
-  __shared__ T sT[MAXP * MAXP];
+  __shared__ T sbU[256], sbA[256];
   __shared__ T sY[MAXP * MAXP];
+  __shared__ int sg[MAXP];
   const int a = blockIdx.x;
   const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
   const int d = tb.d[site];
-  const int NL = tb.dims[site * 8 + 4];
+  const int* dm = tb.dims + site * DIMW;
+  const int NL = dm[D_NL], Gin = dm[D_GIN], Gout = dm[D_GOUT];
+  const int cols = tb.cols;
   const int tid = threadIdx.x;
   for (int x = tid; x < d; x += blockDim.x) {
     sw[x] = wt.w[(size_t)site * tb.dmax + x];
@@ -292,24 +320,25 @@ __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __res
     sx[x] = tb.xsL[(size_t)site * tb.dmax + x];
   }
   for (int e = tid; e < 256; e += blockDim.x) {
-    sbL[e] = wt.bL[(size_t)site * 256 + e];
     sbU[e] = wt.bU[(size_t)site * 256 + e];
+    sbA[e] = wt.bA[(size_t)site * 256 + e];
   }
+  for (int e = tid; e < DL * NL; e += blockDim.x)
+    sbL[e] = wt.bL[(size_t)site * tb.lstride + (e / NL) * MAXP + e % NL];
   for (int e = tid; e <= MAXP; e += blockDim.x) soff[e] = tb.xoffL[site * (MAXP + 1) + e];
+  for (int u = tid; u < MAXP; u += blockDim.x) sg[u] = (site >= cols && u < DU) ? tb.gD[(size_t)(site - cols) * MAXP + u] : 0;
   __syncthreads();
   const size_t ldM = (size_t)DU * K;
   for (int k = k0; k < k1; ++k) {
-    for (int e = tid; e < p * DR; e += blockDim.x) {
-      const int s = e / DR, rr = e % DR;
-      sT[s * MAXP + rr] = T1[(((size_t)a * p + s) * DR + rr) * K + k];
-    }
+    for (int e = tid; e < p * DR; e += blockDim.x) sT[e] = T1[((size_t)a * p * DR + e) * K + k];
     __syncthreads();
     for (int e = tid; e < DU * NL; e += blockDim.x) {
       const int u = e / NL, h = e % NL;
+      const int g = sg[u];
       T acc = T(0);
       for (int q = soff[h]; q < soff[h + 1]; ++q) {
         const int x = sx[q];
-        acc += sbU[u * 16 + sPU[x]] * sw[x] * sT[sPD[x] * MAXP + sPR[x]];
+        acc += sbU[u * 16 + sPU[x]] * sw[x] * sT[sPD[x] * DR + sPR[x] * Gout + g];
       }
       sY[u * MAXP + h] = acc;
     }
@@ -317,8 +346,8 @@ __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __res
     for (int e = tid; e < DL * DU; e += blockDim.x) {
       const int l = e / DU, u = e % DU;
       T acc = T(0);
-      for (int h = 0; h < NL; ++h) acc += sbL[l * 16 + h] * sY[u * MAXP + h];
-      M[((size_t)l * chiL + a) * ldM + (size_t)u * K + k] = acc;
+      for (int h = 0; h < NL; ++h) acc += sbL[l * NL + h] * sY[u * MAXP + h];
+      M[((size_t)l * chiL + a) * ldM + (size_t)u * K + k] = sbA[(l / Gin) * 16 + u] * acc;
     }
     __syncthreads();
   }
@@ -649,8 +678,14 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
   k_zip_T1<T><<<blocks, 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1);
   const int kchunk = K >= 8 ? 4 : 1;
   dim3 grid(chiL, (K + kchunk - 1) / kchunk);
+  const size_t smem = sizeof(T) * ((size_t)p * DR + (size_t)DL * MAXP);
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] {
+    cudaFuncSetAttribute(k_zip_M<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * 2 * (size_t)MAXP * MAXBOND));
+  });
   count_launches("k_zip_M", st);
-  k_zip_M<T><<<grid, 256, 0, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M);
+  k_zip_M<T><<<grid, 256, smem, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M);
   return cudaGetLastError();
 }
 

@@ -62,41 +62,46 @@ __device__ __forceinline__ unsigned long long ord_i64(int64_t v) {
   return (unsigned long long)v ^ 0x8000000000000000ull;
 }
 
-__device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { return tb.dims[s * 8 + k]; }
+__device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { return tb.dims[s * DIMW + k]; }
 
 // ---------------------------------------------------------------- S5 right environments
-// For beam element b at the start of row i, with B = B_{i+1}:
-//   R_L = 1;  R_j[a][l] = sum_x w(x) bL[l][PL x] bU[u_j][PU x]
-//                          sum_a' B_j[PD x][a][a'] R_{j+1}[a'][PR x]
-// stored at R[((b*(cols+1) + j)*chi + a)*MAXP + l], each R_j scaled to max |.| = 1.
+// For beam element b at the start of row i, with B = B_{i+1}, u_j the PD
+// class of the fixed cluster (i-1, j) and g_j = gD_{(i-1, j)}[u_j]:
+//   R_L = 1;  R_j[a][l] = bA[l / Gin][u_j] sum_h bL[l][h] Y[h][a],
+//   Y[h][a] = sum_{x: PL x = h} w(x) bU[u_j][PU x]
+//             sum_a' B_j[PD x][a][a'] R_{j+1}[a'][PR x * Gout + g_j]
+// stored at R[((b*(cols+1) + j)*chi + a)*rs + l], each R_j scaled to max |.| = 1.
 // One block handles G consecutive beam elements; the site B_j, shared by
-// all of them, is staged in shared memory once per column when it fits.
+// all of them, is staged in shared memory once per column when it fits, and
+// so are the G current environments when the bond is small (use_rn).
 template <typename T>
 __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int row, DevSearch ds,
-                             DevBeamT<T> bt, int cur, int G, int use_smem) {
+                             DevBeamT<T> bt, int cur, int G, int use_smem, int use_rn) {
   const int nb = ds.n_beam[cur];
   const int b0 = blockIdx.x * G;
   if (b0 >= nb) return;
   const int gn = min(G, nb - b0);
+  const int rs = bt.rs;
   extern __shared__ unsigned char smem_raw[];
-  T* Rn = reinterpret_cast<T*>(smem_raw);       // [G][chi*MAXP]
-  T* Y = Rn + (size_t)G * MAXCHI * MAXP;        // [MAXP][MAXCHI]
-  T* Rt = Y + MAXP * MAXCHI;                    // [MAXCHI][MAXP]
-  T* red = Rt + MAXCHI * MAXP;                  // 32
-  T* Bs = red + 32;                             // staged site (use_smem)
-  __shared__ T sw[MAXS], sbU[256], sbL[256];
+  T* Y = reinterpret_cast<T*>(smem_raw);           // [MAXP][MAXCHI]
+  T* red = Y + MAXP * MAXCHI;                      // 32
+  T* sbL = red + 32;                               // [rs][MAXP]
+  T* Rn = sbL + (size_t)rs * MAXP;                 // [G][chi*rs] (use_rn)
+  T* Bs = Rn + (use_rn ? (size_t)G * MAXCHI * rs : 0);  // staged site (use_smem)
+  __shared__ T sw[MAXS], sbU[256], sbA[256];
   __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
   __shared__ int16_t sxs[MAXS];
   __shared__ int soff[MAXP + 1];
   const int cols = tb.cols, chi = bt.chi;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t renv = (size_t)chi * rs;  // one environment
   for (int g = 0; g < gn; ++g) {
     const int b = b0 + g;
-    T* Rb = bt.R + (size_t)b * (cols + 1) * chi * MAXP;
-    for (int e = tid; e < chi * MAXP; e += nt) {
+    T* Rb = bt.R + (size_t)b * (cols + 1) * renv;
+    for (int e = tid; e < (int)renv; e += nt) {
       const T v = e == 0 ? T(1) : T(0);
-      Rb[(size_t)cols * chi * MAXP + e] = v;
-      Rn[(size_t)g * MAXCHI * MAXP + e] = v;
+      Rb[(size_t)cols * renv + e] = v;
+      if (use_rn) Rn[(size_t)g * renv + e] = v;
     }
     if (tid == 0) ds.rid[cur][b] = b;
     for (int a = tid; a < chi; a += nt) bt.lenv[cur][(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
@@ -114,7 +119,8 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
         const int ap = e % chiR, a = (e / chiR) % chiL, sg = e / (chiR * chiL);
         Bs[((size_t)sg * chiR + ap) * chiL + a] = Ag[e];
       }
-    const int DL = dim_of(tb, s, 0), NL = dim_of(tb, s, 4);
+    const int DL = dim_of(tb, s, D_DL), NL = dim_of(tb, s, D_NL), Gin = dim_of(tb, s, D_GIN);
+    const int Gout = dim_of(tb, s, D_GOUT);
     const size_t so = (size_t)s * tb.dmax;
     const int d = tb.d[s];
     // this column's tables, staged once for all G beam elements
@@ -127,23 +133,25 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
     }
     for (int e = tid; e < 256; e += nt) {
       sbU[e] = wt.bU[(size_t)s * 256 + e];
-      sbL[e] = wt.bL[(size_t)s * 256 + e];
+      sbA[e] = wt.bA[(size_t)s * 256 + e];
     }
+    for (int e = tid; e < DL * MAXP; e += nt) sbL[e] = wt.bL[(size_t)s * tb.lstride + e];
     for (int e = tid; e <= MAXP; e += nt) soff[e] = tb.xoffL[s * (MAXP + 1) + e];
     __syncthreads();
     for (int g = 0; g < gn; ++g) {
       const int b = b0 + g;
       const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
       const int u = row > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + stb[s - cols]] : 0;
-      const T* Rg = Rn + (size_t)g * MAXCHI * MAXP;
-      // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rg[a'][PR x]
+      const int gu = row > 0 ? tb.gD[(size_t)(s - cols) * MAXP + u] : 0;
+      const T* Rg = use_rn ? Rn + (size_t)g * renv : bt.R + ((size_t)b * (cols + 1) + j + 1) * renv;
+      // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rg[a'][PR x * Gout + gu]
       for (int e = tid; e < NL * chiL; e += nt) {
         const int h = e / chiL, a = e % chiL;
         T acc = T(0);
         for (int q = soff[h]; q < soff[h + 1]; ++q) {
           const int x = sxs[q];
           const T c = sw[x] * sbU[u * 16 + sPU[x]];
-          const int pr = sPR[x];
+          const int pr = sPR[x] * Gout + gu;
           // element (a, a') of slice PD x: Bs[(PD*chiR + a')*chiL + a] when
           // staged, else A[(PD*chiL + a)*chiR + a']
           const size_t sa = use_smem ? (size_t)chiL : 1;
@@ -152,35 +160,39 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
           T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
           int ap = 0;
           for (; ap + 3 < chiR; ap += 4) {
-            t0 += arow[ap * sa] * Rg[ap * MAXP + pr];
-            t1 += arow[(ap + 1) * sa] * Rg[(ap + 1) * MAXP + pr];
-            t2 += arow[(ap + 2) * sa] * Rg[(ap + 2) * MAXP + pr];
-            t3 += arow[(ap + 3) * sa] * Rg[(ap + 3) * MAXP + pr];
+            t0 += arow[ap * sa] * Rg[(size_t)ap * rs + pr];
+            t1 += arow[(ap + 1) * sa] * Rg[(size_t)(ap + 1) * rs + pr];
+            t2 += arow[(ap + 2) * sa] * Rg[(size_t)(ap + 2) * rs + pr];
+            t3 += arow[(ap + 3) * sa] * Rg[(size_t)(ap + 3) * rs + pr];
           }
-          for (; ap < chiR; ++ap) t0 += arow[ap * sa] * Rg[ap * MAXP + pr];
+          for (; ap < chiR; ++ap) t0 += arow[ap * sa] * Rg[(size_t)ap * rs + pr];
           acc += c * ((t0 + t1) + (t2 + t3));
         }
         Y[h * MAXCHI + a] = acc;
       }
       __syncthreads();
-      // R_j[a][l] = sum_h bL[l][h] Y[h][a] into Rt, then scaled to max |.| = 1
+      // R_j[a][l] = bA[l / Gin][u] sum_h bL[l][h] Y[h][a], written unscaled,
+      // then scaled in place to max |.| = 1 (each thread rescales its own
+      // entries)
+      T* Rj = bt.R + ((size_t)b * (cols + 1) + j) * renv;
+      T* Rgw = use_rn ? Rn + (size_t)g * renv : nullptr;
       T mx = T(0);
-      for (int e = tid; e < chi * MAXP; e += nt) {
-        const int a = e / MAXP, l = e % MAXP;
+      for (int e = tid; e < (int)renv; e += nt) {
+        const int a = e / rs, l = e % rs;
         T acc = T(0);
-        if (a < chiL && l < DL)
-          for (int h = 0; h < NL; ++h) acc += sbL[l * 16 + h] * Y[h * MAXCHI + a];
-        Rt[e] = acc;
+        if (a < chiL && l < DL) {
+          for (int h = 0; h < NL; ++h) acc += sbL[l * MAXP + h] * Y[h * MAXCHI + a];
+          acc *= sbA[(l / Gin) * 16 + u];
+        }
+        Rj[e] = acc;
         mx = max(mx, (T)fabs((double)acc));
       }
-      mx = block_max(mx, red);  // contains __syncthreads: Rt complete
+      mx = block_max(mx, red);  // contains __syncthreads
       const T inv = mx > T(0) ? T(1) / mx : T(0);
-      T* Rj = bt.R + ((size_t)b * (cols + 1) + j) * chi * MAXP;
-      T* Rgw = Rn + (size_t)g * MAXCHI * MAXP;
-      for (int e = tid; e < chi * MAXP; e += nt) {
-        const T v = Rt[e] * inv;
+      for (int e = tid; e < (int)renv; e += nt) {
+        const T v = Rj[e] * inv;
         Rj[e] = v;
-        Rgw[e] = v;
+        if (use_rn) Rgw[e] = v;
       }
       __syncthreads();
     }
@@ -188,11 +200,16 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
 }
 
 // ---------------------------------------------------------------- S6 marginals
-// One block per beam element b at site s = (i, j):
-//   v[p][a'] = sum_a lenv[a] B[p][a][a'];  Z[p][rr] = sum_a' v[p][a'] R_{j+1}[a'][rr]
-//   q(x) = w(x) bL[h][PL x] bU[u][PU x] Z[PD x][PR x]   (FP64 weights, q < 0 -> 0)
+// One block per beam element b at site s = (i, j), with l the left bond
+// fixed by clusters (i, j-1) and (i-1, j-1), u the PD class of (i-1, j) and
+// g = gD_{(i-1, j)}[u]:
+//   v[p][a'] = sum_a lenv[a] B[p][a][a'];  Z[p][r] = sum_a' v[p][a'] R_{j+1}[a'][r * Gout + g]
+//   q(x) = w(x) bL[l][PL x] bU[u][PU x] Z[PD x][PR x]   (FP64 weights, q < 0 -> 0)
 //   logc[b][x] = log q(x) - log sum_x q(x)
-//   candE[b][x] = E[b] + E_s(x) + RL[h][PL x] + RU[u][PU x]
+//   candE[b][x] = E[b] + E_s(x) + RL[l][PL x] + RU[u][PU x] + RA_{s+1}[PR x][u']
+// (u' the PD class of (i-1, j+1); RA of site s+1 holds the anti-diagonal
+// edge (i-1, j+1)-(i, j)).  The factor bA[l / Gin][u] is the same for every
+// x and cancels.
 template <typename T>
 __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, int site, DevSearch ds,
                             DevBeamT<T> bt, int cur) {
@@ -202,13 +219,22 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   __shared__ T sv[MAXP * MAXCHI];
   __shared__ double sZ[MAXP * MAXP];
   __shared__ double red[32];
-  const int cols = tb.cols, chi = bt.chi;
+  const int cols = tb.cols, chi = bt.chi, rs = bt.rs;
   const int i = site / cols, j = site % cols;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int* dA = mps.dimA + ((i + 1) * cols + j) * 3;
   const int p = dA[0], chiL = dA[1], chiR = dA[2];
   const T* A = mps.A + (size_t)((i + 1) * cols + j) * mps.site_stride;
-  const int DR = dim_of(tb, site, 1);
+  const int NR = dim_of(tb, site, D_NR), Gin = dim_of(tb, site, D_GIN), Gout = dim_of(tb, site, D_GOUT);
+  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  const size_t dm = tb.dmax;
+  const int a_l = j > 0 ? tb.PR[(size_t)(site - 1) * dm + stb[site - 1]] : 0;
+  const int g_l = (j > 0 && i > 0) ? tb.PG[(size_t)(site - cols - 1) * dm + stb[site - cols - 1]] : 0;
+  const int l = a_l * Gin + g_l;
+  const int u = i > 0 ? tb.PD[(size_t)(site - cols) * dm + stb[site - cols]] : 0;
+  const int gu = i > 0 ? tb.gD[(size_t)(site - cols) * MAXP + u] : 0;
+  const bool adr = i > 0 && j + 1 < cols;
+  const int ur = adr ? tb.PD[(size_t)(site - cols + 1) * dm + stb[site - cols + 1]] : 0;
   for (int a = tid; a < chiL; a += nt) sl[a] = bt.lenv[cur][(size_t)b * chi + a];
   __syncthreads();
   for (int e = tid; e < p * chiR; e += nt) {
@@ -219,38 +245,39 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   }
   __syncthreads();
   const int rb = ds.rid[cur][b];
-  const T* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * MAXP;
-  for (int e = tid; e < p * DR; e += nt) {
-    const int s = e / DR, rr = e % DR;
+  const T* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * rs;
+  for (int e = tid; e < p * NR; e += nt) {
+    const int s = e / NR, rr = e % NR;
+    const int col = rr * Gout + gu;
     T acc = T(0);
-    for (int ap = 0; ap < chiR; ++ap) acc += sv[s * MAXCHI + ap] * Rj[ap * MAXP + rr];
+    for (int ap = 0; ap < chiR; ++ap) acc += sv[s * MAXCHI + ap] * Rj[(size_t)ap * rs + col];
     sZ[s * MAXP + rr] = (double)acc;
   }
-  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
-  const size_t so = (size_t)site * tb.dmax;
-  const int h = j > 0 ? tb.PR[(size_t)(site - 1) * tb.dmax + stb[site - 1]] : 0;
-  const int u = i > 0 ? tb.PD[(size_t)(site - cols) * tb.dmax + stb[site - cols]] : 0;
+  const size_t so = (size_t)site * dm;
+  const double* bLl = wd.bL + (size_t)site * tb.lstride + (size_t)l * MAXP;
+  const double* bUu = wd.bU + (size_t)site * 256 + u * 16;
   __syncthreads();
   const int d = tb.d[site];
   double part = 0.0;
   for (int x = tid; x < d; x += nt) {
-    double q = wd.w[so + x] * wd.bL[(size_t)site * 256 + h * 16 + tb.PL[so + x]] *
-               wd.bU[(size_t)site * 256 + u * 16 + tb.PU[so + x]] * sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
+    double q = wd.w[so + x] * bLl[tb.PL[so + x]] * bUu[tb.PU[so + x]] * sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
     q = q > 0.0 ? q : 0.0;
     part += q;
   }
   const double tot = block_sum(part, red);
   const double lt = log(tot);
   const int64_t E0 = ds.E[cur][b];
+  const int64_t* RLl = tb.RL + (size_t)site * tb.lstride + (size_t)l * MAXP;
+  const int64_t* RUu = tb.RU + (size_t)site * 256 + u * 16;
   for (int x = tid; x < d; x += nt) {
-    const int pl = tb.PL[so + x], pu = tb.PU[so + x];
-    double q = wd.w[so + x] * wd.bL[(size_t)site * 256 + h * 16 + pl] * wd.bU[(size_t)site * 256 + u * 16 + pu] *
-               sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
+    const int pl = tb.PL[so + x], pu = tb.PU[so + x], pr = tb.PR[so + x];
+    double q = wd.w[so + x] * bLl[pl] * bUu[pu] * sZ[tb.PD[so + x] * MAXP + pr];
     q = q > 0.0 ? q : 0.0;
     const double lc = (tot > 0.0) ? (q > 0.0 ? log(q) - lt : -INFINITY) : -INFINITY;
     ds.logc[(size_t)b * ds.dmax + x] = lc;
-    ds.candE[(size_t)b * ds.dmax + x] =
-        E0 + tb.E[so + x] + tb.RL[(size_t)site * 256 + h * 16 + pl] + tb.RU[(size_t)site * 256 + u * 16 + pu];
+    int64_t e = E0 + tb.E[so + x] + RLl[pl] + RUu[pu];
+    if (adr) e += tb.RA[(size_t)(site + 1) * 256 + pr * 16 + ur];
+    ds.candE[(size_t)b * ds.dmax + x] = e;
   }
   if (tid == 0 && !(tot >= 0.0)) atomicOr(ds.err, ERR_NAN);
 }
@@ -345,44 +372,61 @@ __global__ void k_classes(DevSearch ds, int cur, int merge) {
 // For each (class representative b, x): the member with the lowest
 // (candidate energy, lex rank) wins.  When the site's own state is not part
 // of the key (no edge to a later site), one winner is taken per class over
-// all states x, lex order (member, x).
-__global__ void k_winners(DevTables tb, int site, DevSearch ds, int cur) {
+// all states x, lex order (member, x).  The beam is kept in lex order, so
+// the lex rank of a member is its index.  Three passes over all candidates:
+// the class minimum of the energy (atomicMin on its order-preserving bits),
+// the lowest member (and x) reaching it, and the winner table.  wmin is
+// reset to all ones and win / wkey to WIN_NONE (byte memsets) before.
+constexpr int WIN_NONE = 0x7f7f7f7f;
+
+__global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur) {
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
-  const bool xin = tb.dims[site * 8 + 6] != 0;
+  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
+  const size_t tot = (size_t)nb * ds.dmax;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
+    if (x >= d) continue;
+    const int r = ds.rep[b];
+    atomicMin(&ds.wmin[(size_t)r * ds.dmax + (xin ? x : 0)], ord_i64(ds.candE[c]));
+  }
+}
+
+__global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur) {
+  const int nb = ds.n_beam[cur];
+  const int d = tb.d[site];
+  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
+  const size_t tot = (size_t)nb * ds.dmax;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
+    if (x >= d) continue;
+    const int r = ds.rep[b];
+    if (ord_i64(ds.candE[c]) != ds.wmin[(size_t)r * ds.dmax + (xin ? x : 0)]) continue;
+    if (xin)
+      atomicMin(&ds.win[(size_t)r * ds.dmax + x], b);
+    else
+      atomicMin(&ds.wkey[r], (int)c);
+  }
+}
+
+__global__ void k_win_fix(DevTables tb, int site, DevSearch ds, int cur) {
+  const int nb = ds.n_beam[cur];
+  const int d = tb.d[site];
+  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
   const size_t tot = (size_t)ds.cap * ds.dmax;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
-    if (xin) {
-      int w = -1;
-      if (b < nb && x < d && ds.rep[b] == b) {
-        w = b;
-        int64_t be = ds.candE[(size_t)b * ds.dmax + x];
-        for (int m = ds.nxt[b]; m >= 0; m = ds.nxt[m]) {
-          const int64_t e = ds.candE[(size_t)m * ds.dmax + x];
-          if (e < be) {  // members are visited in increasing lex rank
-            be = e;
-            w = m;
-          }
-        }
+    int w = -1;
+    if (b < nb && x < d && ds.rep[b] == b) {
+      if (xin) {
+        const int v = ds.win[c];
+        w = v != WIN_NONE ? v : -1;
+      } else {
+        const int k = ds.wkey[b];
+        if (k != WIN_NONE && k % ds.dmax == x) w = k / ds.dmax;
       }
-      ds.win[c] = w;
-    } else if (x == 0) {
-      int bw = -1, bx = 0;
-      if (b < nb && ds.rep[b] == b) {
-        int64_t be = 0;
-        for (int m = b; m >= 0; m = ds.nxt[m])
-          for (int y = 0; y < d; ++y) {
-            const int64_t e = ds.candE[(size_t)m * ds.dmax + y];
-            if (bw < 0 || e < be) {
-              be = e;
-              bw = m;
-              bx = y;
-            }
-          }
-      }
-      for (int y = 0; y < ds.dmax; ++y) ds.win[(size_t)b * ds.dmax + y] = (y == bx) ? bw : -1;
     }
+    ds.win[c] = w;
   }
 }
 
@@ -723,13 +767,20 @@ __global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_state
   for (int b = threadIdx.x; b < n; b += blockDim.x) {
     const uint16_t* st = ds.states[cur] + (size_t)b * N;
     int64_t E = 0;
+    // every edge once: left and up-left in RL, up in RU, the anti-diagonal
+    // (i-1, j)-(i, j-1) in RA (tables are zero where an edge is missing)
     for (int s = 0; s < N; ++s) {
       const size_t so = (size_t)s * tb.dmax;
       const int x = st[s];
+      const int i = s / cols, j = s % cols;
+      const int a = j > 0 ? tb.PR[so - tb.dmax + st[s - 1]] : 0;
+      const int g = (i > 0 && j > 0) ? tb.PG[(size_t)(s - cols - 1) * tb.dmax + st[s - cols - 1]] : 0;
+      const int u = i > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + st[s - cols]] : 0;
+      const int l = a * tb.dims[s * DIMW + D_GIN] + g;
       E += tb.E[so + x];
-      if (s % cols > 0) E += tb.RL[(size_t)s * 256 + tb.PR[so - tb.dmax + st[s - 1]] * 16 + tb.PL[so + x]];
-      if (s >= cols)
-        E += tb.RU[(size_t)s * 256 + tb.PD[(size_t)(s - cols) * tb.dmax + st[s - cols]] * 16 + tb.PU[so + x]];
+      E += tb.RL[(size_t)s * tb.lstride + (size_t)l * MAXP + tb.PL[so + x]];
+      E += tb.RU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
+      E += tb.RA[(size_t)s * 256 + a * 16 + u];
     }
     if (E != ds.E[cur][b]) atomicOr(ds.err, ERR_ENERGY);
     sE[b] = E;
@@ -760,15 +811,19 @@ __global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_state
 template <typename T>
 cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, const DevSearch& ds,
                               DevBeamT<T> bt, int cur, cudaStream_t st) {
-  const int G = sizeof(T) == 4 ? 8 : 4;
-  const size_t base = sizeof(T) * ((size_t)G * MAXCHI * MAXP + 2 * MAXP * MAXCHI + 32);
+  // small bonds: G environments per block kept in shared memory; large
+  // bonds: one beam element per block, environments read from global memory
+  const int use_rn = bt.rs <= MAXP ? 1 : 0;
+  const int G = use_rn ? (sizeof(T) == 4 ? 8 : 4) : 1;
+  const size_t base = sizeof(T) * ((size_t)MAXP * MAXCHI + 32 + (size_t)bt.rs * MAXP +
+                                   (use_rn ? (size_t)G * MAXCHI * bt.rs : 0));
   const size_t full = base + sizeof(T) * mps.site_stride;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_right_envs", st);
   k_right_envs<T><<<(ds.cap + G - 1) / G, 512, use_smem ? full : base, st>>>(tb, wt, mps, row, ds, bt, cur, G,
-                                                                           use_smem);
+                                                                           use_smem, use_rn);
   return cudaGetLastError();
 }
 
@@ -792,8 +847,16 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
   count_launches("k_classes", st);
   k_classes<<<1, 1024, csm, st>>>(ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
-  count_launches("k_winners", st);
-  k_winners<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>(tb, site, ds, cur);
+  const int wb = (int)std::min<size_t>((tot + 255) / 256, 8192);
+  cudaMemsetAsync(ds.wmin, 0xff, sizeof(unsigned long long) * tot, st);
+  cudaMemsetAsync(ds.win, 0x7f, sizeof(int) * tot, st);
+  cudaMemsetAsync(ds.wkey, 0x7f, sizeof(int) * ds.cap, st);
+  count_launches("k_win_min", st);
+  k_win_min<<<wb, 256, 0, st>>>(tb, site, ds, cur);
+  count_launches("k_win_arg", st);
+  k_win_arg<<<wb, 256, 0, st>>>(tb, site, ds, cur);
+  count_launches("k_win_fix", st);
+  k_win_fix<<<wb, 256, 0, st>>>(tb, site, ds, cur);
   return cudaGetLastError();
 }
 

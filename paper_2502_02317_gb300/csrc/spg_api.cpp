@@ -53,9 +53,14 @@ struct spg_problem {
   int rows = 0, cols = 0, n = 0, dmax = 0, node_type = 0, shift = 0;
   std::vector<int> d;
   std::vector<int64_t> E;  // [n][dmax]
-  std::vector<uint8_t> PL, PR, PU, PD;
-  std::vector<int> dims;  // [n][8]
-  std::vector<int64_t> RL, RU;  // [n][256]
+  std::vector<uint8_t> PL, PR, PU, PD, PG;
+  std::vector<int> dims;  // [n][DIMW]
+  std::vector<int64_t> RL;      // [n][lstride]
+  std::vector<int64_t> RU, RA;  // [n][256]
+  std::vector<uint8_t> gD;      // [n][MAXP]
+  int bmax = 1, lstride = MAXP;
+  bool ucpl = false;  // some site's MPO tensor depends on its up index beyond b_up (king's graph)
+  size_t dev_bytes = 0;
   std::vector<int16_t> xsL;
   std::vector<int> xoffL;  // [n][MAXP+1]
   std::vector<int> keys;   // [n][MAXKEY+1]
@@ -140,55 +145,149 @@ bool reduce_full(const std::vector<int64_t>& T, int dm, int dn, EdgeTab& out) {
   return true;
 }
 
+// Joint projections, bond tables and device upload (S1).  The class of a
+// state on a set of edges is its tuple of per-edge projections, numbered in
+// order of first occurrence (x ascending); the pairwise energy between class
+// representatives (first states) is exact because classes only merge states
+// with equal table rows.
 int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, EdgeTab>& edges) {
-  const int n = P->n, dmax = P->dmax, cols = P->cols;
+  const int n = P->n, dmax = P->dmax, rows = P->rows, cols = P->cols;
+  auto at = [&](int i, int j) { return (i >= 0 && i < rows && j >= 0 && j < cols) ? i * cols + j : -1; };
+  auto edge = [&](int s, int t) -> const EdgeTab* {
+    if (s < 0 || t < 0) return nullptr;
+    auto it = edges.find({std::min(s, t), std::max(s, t)});
+    return it == edges.end() ? nullptr : &it->second;
+  };
+  // projection of state x of s on its edge to t
+  auto proj = [&](const EdgeTab* e, int s, int t, int x) { return s < t ? (int)e->Pm[x] : (int)e->Pn[x]; };
+  // pairwise energy between state xs of s and xt of t (0 without an edge)
+  auto pairE = [&](int s, int xs, int t, int xt) -> int64_t {
+    const EdgeTab* e = edge(s, t);
+    if (!e) return 0;
+    if (s > t) {
+      std::swap(s, t);
+      std::swap(xs, xt);
+    }
+    return e->R[(size_t)e->Pm[xs] * e->Dn + e->Pn[xt]];
+  };
+  struct Cls {
+    std::vector<uint8_t> P;
+    std::vector<int> rep;
+  };
+  auto joint = [&](int s, std::initializer_list<int> nbrs, Cls& c) -> bool {
+    std::map<std::vector<int>, int> idx;
+    c.P.assign(dmax, 0);
+    c.rep.clear();
+    for (int x = 0; x < P->d[s]; ++x) {
+      std::vector<int> key;
+      for (int t : nbrs) {
+        const EdgeTab* e = edge(s, t);
+        if (e) key.push_back(proj(e, s, t, x));
+      }
+      auto it = idx.find(key);
+      if (it == idx.end()) {
+        if ((int)idx.size() >= MAXP) return false;
+        it = idx.emplace(key, (int)idx.size()).first;
+        c.rep.push_back(x);
+      }
+      c.P[x] = (uint8_t)it->second;
+    }
+    return true;
+  };
+  std::vector<Cls> L(n), U(n), R(n), D(n), G(n);
+  for (int s = 0; s < n; ++s) {
+    const int i = s / cols, j = s % cols;
+    if (!joint(s, {at(i, j - 1), at(i - 1, j - 1)}, L[s]) || !joint(s, {at(i - 1, j)}, U[s]) ||
+        !joint(s, {at(i, j + 1), at(i - 1, j + 1)}, R[s]) ||
+        !joint(s, {at(i + 1, j - 1), at(i + 1, j), at(i + 1, j + 1)}, D[s]) || !joint(s, {at(i + 1, j + 1)}, G[s]))
+      return fail(ctx, SPG_EUNSUPPORTED, "a joint projection has more than 16 classes");
+  }
+  auto ncls = [&](std::vector<Cls>& c, int s) { return s < 0 ? 1 : (int)c[s].rep.size(); };
   P->PL.assign((size_t)n * dmax, 0);
   P->PR.assign((size_t)n * dmax, 0);
   P->PU.assign((size_t)n * dmax, 0);
   P->PD.assign((size_t)n * dmax, 0);
-  P->dims.assign((size_t)n * 8, 1);
-  P->RL.assign((size_t)n * 256, 0);
+  P->PG.assign((size_t)n * dmax, 0);
+  P->dims.assign((size_t)n * DIMW, 0);
+  int bmax = 1;
+  for (int s = 0; s < n; ++s) {
+    const int i = s / cols, j = s % cols;
+    const int left = at(i, j - 1), upleft = at(i - 1, j - 1), up = at(i - 1, j);
+    int* dm = &P->dims[(size_t)s * DIMW];
+    dm[D_NRL] = ncls(R, left);
+    dm[D_GIN] = ncls(G, upleft);
+    dm[D_GOUT] = ncls(G, up);
+    dm[D_NR] = ncls(R, s);
+    dm[D_DL] = dm[D_NRL] * dm[D_GIN];
+    dm[D_DR] = dm[D_NR] * dm[D_GOUT];
+    dm[D_DU] = ncls(D, up);
+    dm[D_DD] = ncls(D, s);
+    dm[D_NL] = ncls(L, s);
+    dm[D_NU] = ncls(U, s);
+    dm[D_UCPL] = (dm[D_GOUT] > 1 || (edge(up, left) != nullptr)) ? 1 : 0;
+    bmax = std::max(bmax, std::max(dm[D_DL], dm[D_DR]));
+    std::copy(L[s].P.begin(), L[s].P.end(), P->PL.begin() + (size_t)s * dmax);
+    std::copy(U[s].P.begin(), U[s].P.end(), P->PU.begin() + (size_t)s * dmax);
+    std::copy(R[s].P.begin(), R[s].P.end(), P->PR.begin() + (size_t)s * dmax);
+    std::copy(D[s].P.begin(), D[s].P.end(), P->PD.begin() + (size_t)s * dmax);
+    std::copy(G[s].P.begin(), G[s].P.end(), P->PG.begin() + (size_t)s * dmax);
+  }
+  P->bmax = bmax;
+  P->lstride = bmax * MAXP;
+  P->ucpl = false;
+  for (int s = 0; s < n; ++s) P->ucpl = P->ucpl || P->dims[(size_t)s * DIMW + D_UCPL] != 0;
+  P->RL.assign((size_t)n * P->lstride, 0);
   P->RU.assign((size_t)n * 256, 0);
-  P->xsL.assign((size_t)n * dmax, 0);
-  P->xoffL.assign((size_t)n * (MAXP + 1), 0);
+  P->RA.assign((size_t)n * 256, 0);
+  P->gD.assign((size_t)n * MAXP, 0);
   double mins = 0.0;
   for (int s = 0; s < n; ++s) {
+    const int i = s / cols, j = s % cols;
+    const int left = at(i, j - 1), upleft = at(i - 1, j - 1), up = at(i - 1, j);
+    const int* dm = &P->dims[(size_t)s * DIMW];
     int64_t mn = INT64_MAX;
     for (int x = 0; x < P->d[s]; ++x) mn = std::min(mn, P->E[(size_t)s * dmax + x]);
     mins += (double)mn;
-  }
-  for (auto& kv : edges) {
-    const int m = kv.first.first, nn = kv.first.second;
-    EdgeTab& e = kv.second;
-    int64_t mn = INT64_MAX;
-    for (auto v : e.R) mn = std::min(mn, v);
-    mins += (double)mn;
-    const bool horiz = (nn == m + 1) && (m / cols == nn / cols);
-    const bool vert = nn == m + cols;
-    if (!horiz && !vert)
-      return fail(ctx, SPG_EUNSUPPORTED, "diagonal (king's graph) edges are not built in this version");
-    if (horiz) {
-      for (int x = 0; x < P->d[m]; ++x) P->PR[(size_t)m * dmax + x] = e.Pm[x];
-      for (int x = 0; x < P->d[nn]; ++x) P->PL[(size_t)nn * dmax + x] = e.Pn[x];
-      P->dims[m * 8 + 1] = e.Dm;
-      P->dims[nn * 8 + 0] = e.Dm;
-      P->dims[nn * 8 + 4] = e.Dn;
-      for (int a = 0; a < e.Dm; ++a)
-        for (int b = 0; b < e.Dn; ++b) P->RL[(size_t)nn * 256 + a * 16 + b] = e.R[(size_t)a * e.Dn + b];
-    } else {
-      for (int x = 0; x < P->d[m]; ++x) P->PD[(size_t)m * dmax + x] = e.Pm[x];
-      for (int x = 0; x < P->d[nn]; ++x) P->PU[(size_t)nn * dmax + x] = e.Pn[x];
-      P->dims[m * 8 + 3] = e.Dm;
-      P->dims[nn * 8 + 2] = e.Dm;
-      P->dims[nn * 8 + 5] = e.Dn;
-      for (int a = 0; a < e.Dm; ++a)
-        for (int b = 0; b < e.Dn; ++b) P->RU[(size_t)nn * 256 + a * 16 + b] = e.R[(size_t)a * e.Dn + b];
+    // left and up-left edges
+    int64_t mnL = INT64_MAX;
+    for (int l = 0; l < dm[D_DL]; ++l) {
+      const int a = l / dm[D_GIN], g = l % dm[D_GIN];
+      for (int h = 0; h < dm[D_NL]; ++h) {
+        const int xh = L[s].rep[h];
+        int64_t v = 0;
+        if (left >= 0) v += pairE(left, R[left].rep[a], s, xh);
+        if (upleft >= 0) v += pairE(upleft, G[upleft].rep[g], s, xh);
+        P->RL[(size_t)s * P->lstride + (size_t)l * MAXP + h] = v;
+        mnL = std::min(mnL, v);
+      }
     }
+    mins += (double)mnL;
+    // up edge
+    int64_t mnU = INT64_MAX;
+    for (int u = 0; u < dm[D_DU]; ++u)
+      for (int h = 0; h < dm[D_NU]; ++h) {
+        const int64_t v = up >= 0 ? pairE(up, D[up].rep[u], s, U[s].rep[h]) : 0;
+        P->RU[(size_t)s * 256 + u * 16 + h] = v;
+        mnU = std::min(mnU, v);
+      }
+    mins += (double)mnU;
+    // anti-diagonal edge (i-1, j)-(i, j-1)
+    int64_t mnA = INT64_MAX;
+    for (int a = 0; a < dm[D_NRL]; ++a)
+      for (int u = 0; u < dm[D_DU]; ++u) {
+        const int64_t v = (up >= 0 && left >= 0) ? pairE(up, D[up].rep[u], left, R[left].rep[a]) : 0;
+        P->RA[(size_t)s * 256 + a * 16 + u] = v;
+        mnA = std::min(mnA, v);
+      }
+    mins += (double)mnA;
+    for (int u = 0; u < dm[D_DD]; ++u) P->gD[(size_t)s * MAXP + u] = G[s].P[D[s].rep[u]];
   }
   P->min_sum = mins;
   // states grouped by PL
+  P->xsL.assign((size_t)n * dmax, 0);
+  P->xoffL.assign((size_t)n * (MAXP + 1), 0);
   for (int s = 0; s < n; ++s) {
-    const int NL = P->dims[s * 8 + 4];
+    const int NL = P->dims[(size_t)s * DIMW + D_NL];
     int pos = 0;
     for (int h = 0; h < NL; ++h) {
       P->xoffL[s * (MAXP + 1) + h] = pos;
@@ -214,7 +313,7 @@ int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, E
     std::vector<int> ks;
     for (int t = 0; t < s; ++t)
       if (far[t] > s) ks.push_back(t);
-    P->dims[s * 8 + 6] = far[s] > s ? 1 : 0;  // the site's own state is part of its key
+    P->dims[(size_t)s * DIMW + D_XIN] = far[s] > s ? 1 : 0;  // the site's own state is part of its key
     if ((int)ks.size() > MAXKEY || (int)ks.size() * kb > KEYW * 64)
       return fail(ctx, SPG_EUNSUPPORTED, "merge key longer than the built limit");
     P->keys[(size_t)s * (MAXKEY + 1)] = (int)ks.size();
@@ -227,44 +326,57 @@ int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, E
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t o_d = take(sizeof(int) * n), o_E = take(sizeof(int64_t) * n * dmax),
-               o_PL = take((size_t)n * dmax), o_PR = take((size_t)n * dmax), o_PU = take((size_t)n * dmax),
-               o_PD = take((size_t)n * dmax), o_dims = take(sizeof(int) * n * 8),
-               o_RL = take(sizeof(int64_t) * n * 256), o_RU = take(sizeof(int64_t) * n * 256),
-               o_xs = take(sizeof(int16_t) * n * dmax), o_xo = take(sizeof(int) * n * (MAXP + 1)),
+  const size_t nd = (size_t)n * dmax;
+  const size_t o_d = take(sizeof(int) * n), o_E = take(sizeof(int64_t) * nd), o_PL = take(nd), o_PR = take(nd),
+               o_PU = take(nd), o_PD = take(nd), o_PG = take(nd), o_dims = take(sizeof(int) * n * DIMW),
+               o_RL = take(sizeof(int64_t) * P->RL.size()), o_RU = take(sizeof(int64_t) * n * 256),
+               o_RA = take(sizeof(int64_t) * n * 256), o_gD = take((size_t)n * MAXP),
+               o_xs = take(sizeof(int16_t) * nd), o_xo = take(sizeof(int) * n * (MAXP + 1)),
                o_k = take(sizeof(int) * n * (MAXKEY + 1)), o_kb = take(sizeof(int));
   CK(cudaSetDevice(ctx->device));
   CK(cudaMalloc(&P->dev, off));
+  P->dev_bytes = off;
   char* base = (char*)P->dev;
   cudaStream_t st = ctx->stream;
-  CK(cudaMemcpyAsync(base + o_d, P->d.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_E, P->E.data(), sizeof(int64_t) * n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_PL, P->PL.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_PR, P->PR.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_PU, P->PU.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_PD, P->PD.data(), (size_t)n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_dims, P->dims.data(), sizeof(int) * n * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_RL, P->RL.data(), sizeof(int64_t) * n * 256, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_RU, P->RU.data(), sizeof(int64_t) * n * 256, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_xs, P->xsL.data(), sizeof(int16_t) * n * dmax, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_xo, P->xoffL.data(), sizeof(int) * n * (MAXP + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_k, P->keys.data(), sizeof(int) * n * (MAXKEY + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + o_kb, &P->kbits, sizeof(int), cudaMemcpyHostToDevice, st));
+  auto up = [&](size_t o, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  CK(up(o_d, P->d.data(), sizeof(int) * n));
+  CK(up(o_E, P->E.data(), sizeof(int64_t) * nd));
+  CK(up(o_PL, P->PL.data(), nd));
+  CK(up(o_PR, P->PR.data(), nd));
+  CK(up(o_PU, P->PU.data(), nd));
+  CK(up(o_PD, P->PD.data(), nd));
+  CK(up(o_PG, P->PG.data(), nd));
+  CK(up(o_dims, P->dims.data(), sizeof(int) * n * DIMW));
+  CK(up(o_RL, P->RL.data(), sizeof(int64_t) * P->RL.size()));
+  CK(up(o_RU, P->RU.data(), sizeof(int64_t) * n * 256));
+  CK(up(o_RA, P->RA.data(), sizeof(int64_t) * n * 256));
+  CK(up(o_gD, P->gD.data(), (size_t)n * MAXP));
+  CK(up(o_xs, P->xsL.data(), sizeof(int16_t) * nd));
+  CK(up(o_xo, P->xoffL.data(), sizeof(int) * n * (MAXP + 1)));
+  CK(up(o_k, P->keys.data(), sizeof(int) * n * (MAXKEY + 1)));
+  CK(up(o_kb, &P->kbits, sizeof(int)));
   CK(cudaStreamSynchronize(st));
   DevTables& tb = P->tb;
   tb.rows = P->rows;
   tb.cols = P->cols;
   tb.n = n;
   tb.dmax = dmax;
+  tb.lstride = P->lstride;
+  tb.bmax = P->bmax;
   tb.d = (const int*)(base + o_d);
   tb.E = (const int64_t*)(base + o_E);
   tb.PL = (const uint8_t*)(base + o_PL);
   tb.PR = (const uint8_t*)(base + o_PR);
   tb.PU = (const uint8_t*)(base + o_PU);
   tb.PD = (const uint8_t*)(base + o_PD);
+  tb.PG = (const uint8_t*)(base + o_PG);
   tb.dims = (const int*)(base + o_dims);
   tb.RL = (const int64_t*)(base + o_RL);
   tb.RU = (const int64_t*)(base + o_RU);
+  tb.RA = (const int64_t*)(base + o_RA);
+  tb.gD = (const uint8_t*)(base + o_gD);
   tb.xsL = (const int16_t*)(base + o_xs);
   tb.xoffL = (const int*)(base + o_xo);
   tb.keys = (const int*)(base + o_k);
@@ -321,7 +433,7 @@ Plan make_plan(const spg_problem* P, int chi, int down_to) {
     int K = 1;
     for (int j = cols - 1; j >= 0; --j) {
       const int s = r * cols + j;
-      const int DL = P->dims[s * 8 + 0], DU = P->dims[s * 8 + 2];
+      const int DL = P->dims[(size_t)s * DIMW + D_DL], DU = P->dims[(size_t)s * DIMW + D_DU];
       const int chiL_in = pl.dimA[(((size_t)(r + 1) * cols + j) * 3) + 1];
       int* o = &pl.dimA[((size_t)r * cols + j) * 3];
       if (j == 0) {
@@ -371,15 +483,17 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
   add(sizeof(int) * sites * 3);
   add(sizeof(double) * (P->rows + 1));
   add(sizeof(T) * P->n * P->dmax);
+  add(sizeof(T) * P->n * P->lstride);
   add(sizeof(T) * P->n * 256 * 2);
   add(sizeof(double) * P->n * P->dmax);
+  add(sizeof(double) * P->n * P->lstride);
   add(sizeof(double) * P->n * 256 * 2);
-  const size_t mmax = (size_t)MAXP * chi, nmax = (size_t)MAXP * chi;
-  add(sizeof(T) * (size_t)chi * MAXP * MAXP * chi);  // T1
-  add(sizeof(T) * mmax * nmax);                     // M
-  add(sizeof(T) * nmax * chi);                      // V
-  add(sizeof(T) * mmax * chi);                      // US
-  add(sizeof(T) * MAXP * chi * chi * 2);            // carries
+  const size_t mmax = (size_t)P->bmax * chi, nmax = (size_t)MAXP * chi;
+  add(sizeof(T) * (size_t)chi * MAXP * P->bmax * chi);  // T1
+  add(sizeof(T) * mmax * nmax);                        // M
+  add(sizeof(T) * nmax * chi);                         // V
+  add(sizeof(T) * mmax * chi);                         // US
+  add(sizeof(T) * P->bmax * chi * chi * 2);            // carries
   add(sizeof(T) * truncated_svd_work((int)mmax, (int)nmax, chi));
   add(sizeof(double) * 4);
   add(sizeof(int) * 4);
@@ -399,18 +513,20 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.mps.dimA = bb.dimA_dev;
   bb.mps.lognorm = ar.get<double>(P->rows + 1);
   bb.wt.w = ar.get<T>((size_t)P->n * P->dmax);
-  bb.wt.bL = ar.get<T>((size_t)P->n * 256);
+  bb.wt.bL = ar.get<T>((size_t)P->n * P->lstride);
   bb.wt.bU = ar.get<T>((size_t)P->n * 256);
+  bb.wt.bA = ar.get<T>((size_t)P->n * 256);
   bb.wd.w = ar.get<double>((size_t)P->n * P->dmax);
-  bb.wd.bL = ar.get<double>((size_t)P->n * 256);
+  bb.wd.bL = ar.get<double>((size_t)P->n * P->lstride);
   bb.wd.bU = ar.get<double>((size_t)P->n * 256);
-  const size_t mmax = (size_t)MAXP * chi, nmax = (size_t)MAXP * chi;
-  bb.T1 = ar.get<T>((size_t)chi * MAXP * MAXP * chi);
+  bb.wd.bA = ar.get<double>((size_t)P->n * 256);
+  const size_t mmax = (size_t)P->bmax * chi, nmax = (size_t)MAXP * chi;
+  bb.T1 = ar.get<T>((size_t)chi * MAXP * P->bmax * chi);
   bb.M = ar.get<T>(mmax * nmax);
   bb.V = ar.get<T>(nmax * chi);
   bb.US = ar.get<T>(mmax * chi);
-  bb.carry[0] = ar.get<T>((size_t)MAXP * chi * chi);
-  bb.carry[1] = ar.get<T>((size_t)MAXP * chi * chi);
+  bb.carry[0] = ar.get<T>((size_t)P->bmax * chi * chi);
+  bb.carry[1] = ar.get<T>((size_t)P->bmax * chi * chi);
   bb.svdw_elems = truncated_svd_work((int)mmax, (int)nmax, chi);
   bb.svdw = ar.get<T>(bb.svdw_elems);
   bb.s1 = ar.get<double>(4);
@@ -444,7 +560,8 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
     int K = 1, cur = 0;
     for (int j = cols - 1; j >= 0; --j) {
       const int s = r * cols + j;
-      const int DL = P->dims[s * 8 + 0], DR = P->dims[s * 8 + 1], DU = P->dims[s * 8 + 2];
+      const int* dm = &P->dims[(size_t)s * DIMW];
+      const int DL = dm[D_DL], DR = dm[D_DR], DU = dm[D_DU];
       const int* din = &pl.dimA[((size_t)(r + 1) * cols + j) * 3];
       const int p = din[0], chiL = din[1], chiR = din[2];
       const T* Bsite = bb.mps.A + (size_t)((r + 1) * cols + j) * pl.stride;
@@ -494,13 +611,15 @@ size_t search_bytes(const spg_problem* P, int cap, int chi) {
   add(sizeof(double) * cap * dmax);
   add(sizeof(int64_t) * cap * dmax);
   add(sizeof(int) * cap * dmax);
+  add(sizeof(unsigned long long) * cap * dmax);
+  add(sizeof(int) * cap);
   add(sizeof(unsigned long long) * cap * KEYW);
   add(sizeof(int) * cap * 3);
   add(sizeof(unsigned) * 65536);
   add(sizeof(unsigned long long) * 16);
   add(sizeof(int) * 8);
   add(sizeof(double) * 2);
-  add(sizeof(T) * cap * (P->cols + 1) * chi * MAXP);
+  add(sizeof(T) * cap * (P->cols + 1) * chi * P->bmax);
   return b + 4096;
 }
 
@@ -522,6 +641,8 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   ds.logc = ar.get<double>((size_t)cap * P->dmax);
   ds.candE = ar.get<int64_t>((size_t)cap * P->dmax);
   ds.win = ar.get<int>((size_t)cap * P->dmax);
+  ds.wmin = ar.get<unsigned long long>((size_t)cap * P->dmax);
+  ds.wkey = ar.get<int>(cap);
   ds.key = ar.get<unsigned long long>((size_t)cap * KEYW);
   ds.rep = ar.get<int>(cap);
   ds.nxt = ar.get<int>(cap);
@@ -535,14 +656,15 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   ds.err = misc + 3;
   ds.deg_cuts = misc + 4;
   ds.candidates = ar.get<double>(2);
-  sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * MAXP);
+  sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * P->bmax);
+  sb.bt.rs = P->bmax;
   sb.bt.chi = chi;
   if (!sb.bt.R) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(ds.hist, 0, sizeof(unsigned) * 65536, st));
   CK(cudaMemsetAsync(misc, 0, sizeof(int) * 8, st));
-  CK(cudaMemsetAsync(sb.bt.R, 0, sizeof(T) * (size_t)cap * (P->cols + 1) * chi * MAXP, st));
+  CK(cudaMemsetAsync(sb.bt.R, 0, sizeof(T) * (size_t)cap * (P->cols + 1) * chi * P->bmax, st));
   CK(cudaMemsetAsync(sb.bt.lenv[0], 0, sizeof(T) * (size_t)cap * chi, st));
   CK(cudaMemsetAsync(sb.bt.lenv[1], 0, sizeof(T) * (size_t)cap * chi, st));
   return SPG_OK;
@@ -559,6 +681,8 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
   if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
+  if (prm->num_sweeps > 0 && P->ucpl)
+    return fail(ctx, SPG_EUNSUPPORTED, "variational sweeps are built for the square lattice only");
   return SPG_OK;
 }
 

@@ -73,43 +73,70 @@ enum : int {
   ERR_KEY = 4,        // a packed key overflowed its words
 };
 
-// Integer tables of the cluster factor graph (S1) in device memory.
-// Per site s (row-major), padded to dmax states and MAXP x MAXP tables:
+// Integer tables of the cluster factor graph (S1) in device memory, for the
+// square lattice and the king's graph (diagonal couplings).  Per site s
+// (row-major, (i, j)), padded to dmax states:
 //   E[s][x]        local energy (int64, units of 2^-shift)
-//   PL/PR/PU/PD    projections of state x on the left/right/up/down edge
-//                  (row index for the site that comes first in row-major
-//                  order, column index for the other); 0 where no edge
-//   dims[s][8]     DL, DR, DU, DD: rows of the left/right/up/down reduced
-//                  tables (1 where no edge); NL, NU: columns of the left/up
-//                  tables (distinct PL / PU values); XIN: 1 if the site
-//                  has an edge to a later site (its state is part of the
-//                  merge key after it is fixed); 1 unused
-//   RL[s][a][b]    reduced table of the edge from the left neighbour,
-//                  a = left neighbour's PR, b = this site's PL
-//   RU[s][a][b]    the same for the edge from the site above
+//   PL/PU/PR/PD/PG joint projections of state x (classes of equal table rows
+//                  in order of first occurrence, all <= MAXP):
+//                    PL: edges to (i, j-1), (i-1, j-1)   PU: edge to (i-1, j)
+//                    PR: edges to (i, j+1), (i-1, j+1)   PG: edge to (i+1, j+1)
+//                    PD: edges to (i+1, j-1), (i+1, j), (i+1, j+1)
+//   dims[s][DIMW]  D_* entries below
+//   RL[s][l][h]    energy of the left and up-left edges, l = a * Gin + g the
+//                  left bond (a: PR class of (i, j-1), g: PG class of
+//                  (i-1, j-1)), h = PL class (row stride MAXP, site stride
+//                  lstride)
+//   RU[s][u][h]    energy of the up edge, u = PD class of (i-1, j), h = PU
+//   RA[s][a][u]    energy of the anti-diagonal edge (i-1, j)-(i, j-1),
+//                  a = PR class of (i, j-1), u = PD class of (i-1, j)
+//   gD[s][u]       PG class of the states in PD class u of site s
 //   xsL[s][..]     states of s grouped by PL (CSR with xoffL[s][0..MAXP])
+// On the square lattice every G is 1 and RA is 0.
+enum : int {
+  D_DL = 0,    // left bond = NRl * Gin
+  D_DR = 1,    // right bond = NR * Gout
+  D_DU = 2,    // up index = ND of (i-1, j)
+  D_DD = 3,    // ND: boundary-MPS physical dimension below this site
+  D_NL = 4,
+  D_NU = 5,
+  D_XIN = 6,   // 1 if the site has an edge to a later site (merge key)
+  D_NR = 7,
+  D_GIN = 8,   // NG of (i-1, j-1)
+  D_GOUT = 9,  // NG of (i-1, j)
+  D_NRL = 10,  // NR of (i, j-1)
+  D_UCPL = 11, // 1 if W depends on u beyond b_up (Gout > 1 or an anti-diagonal edge)
+  DIMW = 16
+};
 struct DevTables {
   int rows, cols, n, dmax;
+  int lstride;  // elements per site of RL / bL (bmax * MAXP)
+  int bmax;     // largest bond dimension of any site
   const int* d;
   const int64_t* E;
-  const uint8_t *PL, *PR, *PU, *PD;
+  const uint8_t *PL, *PR, *PU, *PD, *PG;
   const int* dims;
   const int64_t* RL;
   const int64_t* RU;
+  const int64_t* RA;
+  const uint8_t* gD;
   const int16_t* xsL;
   const int* xoffL;
   const int* keys;   // [n][MAXKEY+1]: count, then sites of the reduced parent key
   const int* kshift; // bits per packed state
 };
 constexpr int MAXKEY = 40;
+constexpr int MAXBOND = MAXP * MAXP;
 
-// Boltzmann pieces (S2): w[s][x], bL[s][a][b] = exp(-beta u (RL - min RL)),
-// bU likewise, all shifted so that every weight is <= 1.
+// Boltzmann pieces (S2), each table shifted by its minimum so that every
+// weight is <= 1: w[s][x], bL[s][l][h] (stride lstride), bU[s][u][h] and
+// bA[s][a][u] (16 x 16) from RL, RU, RA.
 template <typename T>
 struct DevWeights {
   T* w;
   T* bL;
   T* bU;
+  T* bA;
 };
 
 // Boundary MPSs: site (r, j) of B_r at A + (r*cols + j)*site_stride, laid out
@@ -135,7 +162,8 @@ template <typename T>
 cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int* dimA_host,
                                   T* scratch, cudaStream_t st);
 
-// M[(l,a),(u,k)] = sum_{x} bL[l,PL x] bU[u,PU x] w(x) sum_a' B[PD x][a][a'] C[PR x][a'][k]
+// M[(l,a),(u,k)] = bA[a(l),u] sum_{x} bL[l,PL x] bU[u,PU x] w(x)
+//                  sum_a' B[PD x][a][a'] C[PR x * Gout + gD_up(u)][a'][k]
 // for site (r, j) of the MPO applied to B_{r+1} (site j); carry C [DR][chiR][K].
 template <typename T>
 cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B, int chiL, int p,
@@ -206,6 +234,8 @@ struct DevSearch {
   double* logc;         // [cap][dmax] log-conditionals
   int64_t* candE;       // [cap][dmax]
   int* win;             // [cap][dmax] winner parent of (class rep b, x), -1 otherwise
+  unsigned long long* wmin;  // [cap][dmax] class minimum of the candidate energy (ordered bits)
+  int* wkey;            // [cap] winner (member * dmax + x) of a class when the site is not in the key
   unsigned long long* key;  // [cap][KEYW]
   int* rep;             // [cap] class representative
   int* nxt;             // [cap] next member of the class (-1 at the end)
@@ -223,7 +253,8 @@ struct DevSearch {
 template <typename T>
 struct DevBeamT {
   T* lenv[2];  // [cap][chi]
-  T* R;        // [cap][cols+1][chi][MAXP]
+  T* R;        // [cap][cols+1][chi][rs]
+  int rs;      // bond stride of R (the largest bond dimension)
   int chi;
 };
 

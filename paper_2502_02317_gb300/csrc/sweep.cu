@@ -8,6 +8,8 @@
 // Layouts (row r of the MPO, psi = B_{r+1} sites B[s][b][b'], phi sites
 // P[u][a][a'], both [p][chi_l][chi_r]):
 //   environments  E[l][a][b]  (MPO bond < 16, phi bond, psi bond)
+// These sweeps are built for MPOs whose tensors depend on the up index only
+// through b_up (the square lattice); the caller rejects the others.
 //   W[l,r,u,s] = sum_x w(x) bL[l][PL x] bU[u][PU x] [r = PR x][s = PD x]
 // Every contraction groups the cluster states x by their projections, so the
 // dense MPO is never formed.
@@ -112,7 +114,7 @@ __global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, in
     if (mode == 0)
       v = wt.bU[(size_t)s * 256 + k * 16 + tb.PU[so + x]];
     else if (mode == 1)
-      v = wt.bL[(size_t)s * 256 + k * 16 + tb.PL[so + x]];
+      v = wt.bL[(size_t)s * tb.lstride + k * MAXP + tb.PL[so + x]];
     else
       v = tb.PR[so + x] == k ? T(1) : T(0);
     coef[e] = v * wt.w[so + x];
@@ -202,7 +204,7 @@ template <typename T>
 cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
                                const int* dimA, const int* hdims, const int* hstates, int sweeps, T* work,
                                double* dscratch, cudaStream_t st) {
-  auto tb_dims_host = [&](int s, int k) { return hdims[s * 8 + k]; };
+  auto tb_dims_host = [&](int s, int k) { return hdims[(size_t)s * DIMW + k]; };
   auto hd_states = [&](int s) { return hstates[s]; };
   auto cgs_rows = [&](T* X, int nvec, int len, cudaStream_t stm) { launch_cgs2_rows<T>(X, nvec, len, nullptr, stm); };
   const int chi = (int)std::lround(std::sqrt((double)(mps.site_stride / MAXP)));
@@ -245,7 +247,8 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   // Lp[h][a][b] = sum_l bL[l][h] E[l][a][b]
   auto left_prime = [&](int s, const T* Lenv, int chiA, int chiB) {
     const int DL = tb_dims_host(s, 0), NL = tb_dims_host(s, 4);
-    gemm2<T>(true, false, NL, chiA * chiB, DL, wt.bL + (size_t)s * 256, 16, Lenv, chiA * chiB, Lp, chiA * chiB, st);
+    gemm2<T>(true, false, NL, chiA * chiB, DL, wt.bL + (size_t)s * tb.lstride, MAXP, Lenv, chiA * chiB, Lp,
+             chiA * chiB, st);
   };
   // F[v][a][a'] = sum_u bU[u][v] P[u][a][a']
   auto phi_prime = [&](int s, const T* P, int DU, int chiA, int chiAr) {
