@@ -217,6 +217,74 @@ __global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_sm
     for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
 }
 
+// ---------------------------------------------------------------- tall QR (TSQR)
+// QR of nvec long vectors (rows of X, length len, row stride len) across
+// many CTAs: the entries are cut into nb blocks of bl (the last one
+// shorter); (1) k_tsqr_leaf: CGS2 of every block in its own CTA, its R_b
+// written as the block's slice of the stacked factor S (nvec vectors of
+// length nb * nvec, S[k][b * nvec + c] = R_b[c][k]); (2) QR of S, whose R is
+// the R of X; (3) k_tsqr_apply: every block's Q_b times its slice of S's Q,
+// x_k[block b] = sum_c S[k][b * nvec + c] q_c[block b].  A block with fewer
+// entries than vectors leaves the dependent ones zero, with zero rows in
+// R_b, which the stacked QR carries through.
+template <typename T>
+__global__ void k_tsqr_leaf(T* X, int nvec, int len, int bl, T* S, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
+  T* R = red + 64 + 2 * SMAX;               // nvec * nvec
+  T* Vs = R + (size_t)nvec * nvec;          // nvec * bl (use_smem)
+  const int b = blockIdx.x, nb = gridDim.x;
+  const int i0 = b * bl, w = min(bl, len - i0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T* V = use_smem ? Vs : X + i0;
+  const int ld = use_smem ? w : len;
+  if (use_smem)
+    for (int e = tid; e < nvec * w; e += nt) Vs[e] = X[(size_t)(e / w) * len + i0 + e % w];
+  __syncthreads();
+  cgs2_core(V, nvec, w, ld, R, red);
+  if (use_smem)
+    for (int e = tid; e < nvec * w; e += nt) X[(size_t)(e / w) * len + i0 + e % w] = Vs[e];
+  const size_t sl = (size_t)nb * nvec;
+  for (int e = tid; e < nvec * nvec; e += nt) {
+    const int c = e / nvec, k = e % nvec;
+    S[(size_t)k * sl + (size_t)b * nvec + c] = R[e];
+  }
+}
+
+// Step (3), 64 entries of the block at a time through shared memory (the
+// outputs of a chunk depend only on that chunk's entries, so X is updated in
+// place).
+template <typename T>
+__global__ void k_tsqr_apply(T* X, int nvec, int len, int bl, const T* __restrict__ S) {
+  constexpr int CH = 64;
+  extern __shared__ unsigned char smem_raw[];
+  T* Sb = reinterpret_cast<T*>(smem_raw);  // [k][c] nvec * nvec
+  T* Qs = Sb + (size_t)nvec * nvec;        // [c][i] nvec * CH
+  const int b = blockIdx.x, nb = gridDim.x;
+  const int i0 = b * bl, w = min(bl, len - i0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t sl = (size_t)nb * nvec;
+  for (int e = tid; e < nvec * nvec; e += nt) Sb[e] = S[(size_t)(e / nvec) * sl + (size_t)b * nvec + e % nvec];
+  for (int c0 = 0; c0 < w; c0 += CH) {
+    const int cw = min(CH, w - c0);
+    __syncthreads();
+    for (int e = tid; e < nvec * cw; e += nt) Qs[(e / cw) * CH + e % cw] = X[(size_t)(e / cw) * len + i0 + c0 + e % cw];
+    __syncthreads();
+    for (int e = tid; e < nvec * cw; e += nt) {
+      const int k = e / cw, i = e % cw;
+      const T* sk = Sb + (size_t)k * nvec;
+      T a0 = T(0), a1 = T(0);
+      int c = 0;
+      for (; c + 1 < nvec; c += 2) {
+        a0 += sk[c] * Qs[c * CH + i];
+        a1 += sk[c + 1] * Qs[(c + 1) * CH + i];
+      }
+      if (c < nvec) a0 += sk[c] * Qs[c * CH + i];
+      X[(size_t)k * len + i0 + c0 + i] = a0 + a1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- left-canonical sweep
 // Sites of row r: [p][chiL][chiR] = matrix (p*chiL) x chiR.  For j < cols-1:
 // QR of site j, then site j+1 <- R site j+1.  The last site is normalised.
@@ -728,15 +796,64 @@ static int block_cols(int n, int keep) {
   return std::min(std::min(s, n), SMAX);
 }
 
+// Vectors this long or longer go through the multi-CTA TSQR.
+constexpr int TSQR_MIN_LEN = 2048;
+
+// Stacked R factors of a TSQR of vectors of length len and of its recursion
+// (blocks of >= 256 entries; every level at most half the previous).
+size_t tsqr_scratch_elems(int len) { return 2 * (size_t)SMAX * SMAX * ((size_t)len / 256 + 2); }
+
 size_t truncated_svd_work(int m, int n, int) {
   const size_t s = (size_t)SMAX;  // upper bound of block_cols for any call
-  // Z (n s), Y (m s), R (s s), RV (s s), VJ (s s), sig (s), jacobi global buf (2 s s)
-  return s * n + s * m + 5 * s * s + s + 64;
+  // Z (n s), Y (m s), R (s s), RV (s s), VJ (s s), sig (s), jacobi global buf
+  // (2 s s), then the TSQR scratch when a dimension is long
+  const int mx = std::max(m, n);
+  return s * n + s * m + 5 * s * s + s + 64 + (mx >= TSQR_MIN_LEN ? tsqr_scratch_elems(mx) : 0);
 }
 
 size_t truncated_svd_sigma_offset(int m, int n, int keep) {
   const size_t s = (size_t)block_cols<double>(n, keep);
   return s * n + s * m + 3 * s * s;
+}
+
+template <typename T>
+static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st);
+
+// Entries per TSQR block: staged in shared memory when it fits (FP32), else
+// 1024 entries worked on in global memory (L2); never fewer than nvec.
+template <typename T>
+static int tsqr_block(int nvec, int* use_smem) {
+  const size_t room = (200 * 1024) / sizeof(T) - (64 + 2 * SMAX) - (size_t)nvec * nvec;
+  int bl = (int)(room / nvec) / 32 * 32;
+  if (bl >= 256 && bl >= nvec) {
+    *use_smem = 1;
+    return std::min(bl, 1024);
+  }
+  *use_smem = 0;
+  return 1024;
+}
+
+template <typename T>
+static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
+  int use_smem = 0;
+  const int bl = tsqr_block<T>(nvec, &use_smem);
+  const int nb = (len + bl - 1) / bl;
+  const size_t leaf_smem = sizeof(T) * ((64 + 2 * SMAX) + (size_t)nvec * nvec + (use_smem ? (size_t)nvec * bl : 0));
+  const size_t apply_smem = sizeof(T) * ((size_t)nvec * nvec + (size_t)nvec * 64);
+  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
+  std::call_once(attr_once, [&] {
+    cudaFuncSetAttribute(k_tsqr_leaf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+    cudaFuncSetAttribute(k_tsqr_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+  });
+  count_launches("k_tsqr_leaf", st, 4.0 * len * nvec * nvec);
+  k_tsqr_leaf<T><<<nb, 512, leaf_smem, st>>>(X, nvec, len, bl, S, use_smem);
+  const int slen = nb * nvec;
+  if (slen >= TSQR_MIN_LEN && slen < len)
+    tall_qr<T>(S, nvec, slen, Rout, S + (size_t)nvec * slen, st);
+  else
+    cgs2_rows<T>(S, nvec, slen, Rout, st);
+  count_launches("k_tsqr_apply", st, 2.0 * len * nvec * nvec);
+  k_tsqr_apply<T><<<nb, 512, apply_smem, st>>>(X, nvec, len, bl, S);
 }
 
 template <typename T>
@@ -757,6 +874,16 @@ void launch_cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   cgs2_rows<T>(X, nvec, len, Rout, st);
 }
 
+// QR of the rows of X: one CTA for short vectors, TSQR for long ones (tsq:
+// tsqr_scratch_elems(len) elements).
+template <typename T>
+static void qr_rows(T* X, int nvec, int len, T* Rout, T* tsq, cudaStream_t st) {
+  if (len >= TSQR_MIN_LEN)
+    tall_qr<T>(X, nvec, len, Rout, tsq, st);
+  else
+    cgs2_rows<T>(X, nvec, len, Rout, st);
+}
+
 // Work layout: Zt [s x n], Yt [s x m] (rows = the block's column vectors),
 // R, RV, VJ [s x s], sig [s], Jacobi spill buffer [2 s s].
 template <typename T>
@@ -770,6 +897,7 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   T* VJ = RV + (size_t)s * s;
   T* sig = VJ + (size_t)s * s;
   T* jbuf = sig + s + 64;
+  T* tsq = jbuf + 2 * (size_t)s * s;
   const bool direct = n <= SMAX;
   count_launches("k_fill_start", st);
   k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
@@ -777,17 +905,17 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
     // the pseudo-random start block is well conditioned, so the power steps
     // need no orthonormalisation of it; the Rayleigh-Ritz step below does
     // need an orthonormal Z, hence the QR when there are no power steps
-    if (iters == 0) cgs2_rows(Zt, s, n, (T*)nullptr, st);
+    if (iters == 0) qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
     for (int it = 0; it < iters; ++it) {
       gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);  // Y = M Z
-      cgs2_rows(Yt, s, m, (T*)nullptr, st);
+      qr_rows(Yt, s, m, (T*)nullptr, tsq, st);
       gemm2<T>(false, false, s, n, m, Yt, m, M, n, Zt, n, st);  // Z = M^T Y
-      cgs2_rows(Zt, s, n, (T*)nullptr, st);
+      qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
     }
   }
   // P = M Z = Q R (rows of Yt become the columns of Q); R = U_R Sigma V_J^T
   gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);
-  cgs2_rows(Yt, s, m, R, st);
+  qr_rows(Yt, s, m, R, tsq, st);
   const size_t jsm_base = sizeof(T) * (64 + SMAX) + sizeof(int) * SMAX;
   const size_t jsm_full = jsm_base + sizeof(T) * 2 * (size_t)s * s;
   const int use_smem = jsm_full <= 200 * 1024 ? 1 : 0;
