@@ -225,6 +225,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=8, help="instances solved concurrently per step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-king", action="store_true", help="skip the king's-graph Potts solves")
     ap.add_argument("--L", type=int, default=None,
                     help="grid side override (profiling of a smaller case of the same kernels)")
     ap.add_argument("--only-main", action="store_true",
@@ -372,6 +373,31 @@ def main():
         cu = sum(r.info()["candidates"] for r in rsu)
         line["batch_uneven"] = {"instances": 64, "L": "U{6..12}", "chi": "{16,32}", "beam": 512, "ms": msu,
                                 "beam_states_per_s": cu / (msu / 1e3)}
+
+    # king's graph: 16x16 Potts sites with 16 states, N(0,1) local and
+    # pairwise tables on all 8-neighbour edges, chi 64, beam 2048 (left bonds
+    # of 16 x 16); time to solution of the mixed path next to the plain FP64
+    # path, same instance, best energies compared
+    if WORKLOAD["L"] == 16 and not args.no_king:
+        kinst = I.king_potts(16, 16, 7)
+        kp = spg.spg_problem_potts(ctx, kinst)
+        kres = {}
+        for kprec, reps in ((prec, 3), (spg.SPG_FP64, 1)):
+            kprm = spg.params(beta=1.0, chi=64, beam=2048, precision=kprec)
+            for _ in range(reps - 1):
+                spg.spg_solve(ctx, kp, kprm).get()
+            rk, msk = timed(lambda: spg.spg_solve(ctx, kp, kprm))
+            stk, Ek, _ = rk.get()
+            ik = rk.info()
+            kres[kprec] = {"tts_s": msk / 1e3, "best_energy_fixed": int(Ek[0]),
+                           "beam_states_per_s": ik["candidates"] / (msk / 1e3),
+                           "phase_ms": {"boundary": ik["ms_boundary"], "search": ik["ms_search"]},
+                           "error_flags": ik["error_flags"]}
+        line["king_potts16x16_d16"] = {
+            "workload": "king's graph 16x16, Potts d=16, E~N(0,1) on 2^-24 grid, 930 edges, beta=1, chi=64, beam=2048",
+            "mixed": kres[prec], "fp64": kres[spg.SPG_FP64],
+            "equal_best_energy": kres[prec]["best_energy_fixed"] == kres[spg.SPG_FP64]["best_energy_fixed"],
+            "speedup_mixed_vs_fp64": kres[spg.SPG_FP64]["tts_s"] / kres[prec]["tts_s"]}
 
     # one extra solve with per-kernel device times (graph-captured event
     # nodes; not part of the timed steps): the roofline of the top kernel

@@ -204,11 +204,33 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* prob, const spg_params* p
  * All four are DEVICE pointers owned by the caller.  n <= 128 is exact
  * (Jacobi on the QR of M); larger n uses `iters` rounds of subspace
  * iteration on a block of min(n, max(2 keep, keep + 8), 128) columns.
- * Limits: 1 <= m, n <= 1024, 1 <= keep <= min(64, m, n), 0 <= iters <= 64.
+ * Limits: 1 <= m, n <= 16384, 1 <= keep <= min(64, m, n), 0 <= iters <= 64
+ * (vectors of 2048 or more entries are orthonormalised by a multi-CTA tall
+ * QR).
  * Workspace comes from the context (allocated on first use).  Enqueued on
  * the context's stream; returns after the stream has finished the work. */
 int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters,
                  double* V, double* US, double* sigma);
+
+/* spg_tc_product -- the product step of the FP32 truncated SVD on the
+ * tensor cores (Sec. 2 and Sec. 3.1 SVDTruncate: the subspace iteration of
+ * the truncation multiplies the zipper matrix M, and its transpose, by the
+ * current block of vectors).  All pointers are device pointers:
+ *   M    [m x n] row-major FP32 (the zipper matrix)
+ *   Bt   [s x K] row-major FP32, K = n when trans == 0, K = m when trans == 1
+ *   out  trans == 0: [s x m], out[j][i] = sum_k M[i][k] Bt[j][k]
+ *        trans == 1: [s x n], out[j][i] = sum_k M[k][i] Bt[j][k]
+ * Each FP32 operand is split into a TF32 high part and its FP32 remainder;
+ * three tcgen05 products (hi*hi + hi*lo + lo*hi) accumulate in FP32, which
+ * keeps FP32-level accuracy.  This is the path the mixed-precision solve
+ * takes for large zipper matrices; it is exported for parity tests and for
+ * callers that run their own truncations.  Limits (those of that path): s a
+ * multiple of 16 in 16..128, m >= 1024, n >= 256, m * n * s >= 2^26, else
+ * SPG_EUNSUPPORTED.  Workspace comes from the context; enqueued on the
+ * context's stream; returns after the stream has finished the work
+ * (SPG_ECUDA with an error flag set if a bounded wait in the kernel gave up). */
+int spg_tc_product(spg_ctx* ctx, const float* M, int32_t m, int32_t n, const float* Bt, int32_t s, int32_t trans,
+                   float* out);
 
 /* spg_truncate_static -- the truncation of spg_truncate for callers that
  * cannot allocate device memory.  The paper has no counterpart: it is an

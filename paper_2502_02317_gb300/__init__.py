@@ -6,11 +6,11 @@ The work runs in ``libspg`` (CUDA, sm_103a) behind the C ABI of
 """
 from ._binding import (SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, Context, Problem, Result, SpgError,
                        lib, params, spg_debug_marginals, spg_log_partition, spg_problem_ising,
-                       spg_problem_potts, spg_profile, spg_profile_report, spg_solve, spg_solve_batch, spg_truncate,
-                       spg_truncate_static)
+                       spg_problem_potts, spg_profile, spg_profile_report, spg_solve, spg_solve_batch, spg_tc_product,
+                       spg_truncate, spg_truncate_static)
 
 __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
            "spg_problem_potts", "spg_solve", "spg_solve_batch", "spg_debug_marginals", "spg_log_partition",
-           "spg_profile", "spg_profile_report", "spg_truncate",
+           "spg_profile", "spg_profile_report", "spg_tc_product", "spg_truncate",
            "spg_truncate_static",
            "SPG_FP64", "SPG_MIXED", "SPG_SQUARE", "SPG_KING"]

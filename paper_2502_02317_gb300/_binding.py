@@ -75,6 +75,7 @@ def _load():
         "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
         "spg_truncate": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
         "spg_truncate_static": (C.c_int, [P, I32, I32, I32, I32, P, P, P, P]),
+        "spg_tc_product": (C.c_int, [P, P, I32, I32, P, I32, I32, P]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
@@ -289,6 +290,20 @@ def spg_truncate(ctx: Context, M, keep: int, iters: int = 6):
     ctx.check(lib.spg_truncate(ctx.h, C.c_void_p(M.data_ptr()), m, n, keep, iters, C.c_void_p(V.data_ptr()),
                                C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr())))
     return V, US, sig
+
+
+def spg_tc_product(ctx: Context, M, Bt, trans: bool):
+    """Tensor-core product step of the FP32 truncation.  M: torch.float32
+    CUDA tensor [m, n]; Bt: [s, n] (trans False) or [s, m] (trans True).
+    Returns out [s, m] = (M Bt^T)^T or [s, n] = (M^T Bt^T)^T."""
+    import torch
+    m, n = M.shape
+    s = Bt.shape[0]
+    out = torch.empty((s, n if trans else m), dtype=torch.float32, device=M.device)
+    torch.cuda.synchronize(M.device)
+    ctx.check(lib.spg_tc_product(ctx.h, C.c_void_p(M.data_ptr()), m, n, C.c_void_p(Bt.data_ptr()), s,
+                                 1 if trans else 0, C.c_void_p(out.data_ptr())))
+    return out
 
 
 def spg_truncate_static(M, keep: int, iters: int = 6, stream=None):

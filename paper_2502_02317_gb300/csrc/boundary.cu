@@ -7,6 +7,8 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <optional>
+#include <type_traits>
 
 #include "spg_internal.h"
 
@@ -888,7 +890,7 @@ static void qr_rows(T* X, int nvec, int len, T* Rout, T* tsq, cudaStream_t st) {
 // R, RV, VJ [s x s], sig [s], Jacobi spill buffer [2 s s].
 template <typename T>
 cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US, T* work,
-                          size_t, double* s1_dev, int* flag_dev, cudaStream_t st) {
+                          size_t, double* s1_dev, int* flag_dev, cudaStream_t st, float* tcw, size_t tcw_elems) {
   const int s = block_cols<T>(n, keep);
   T* Zt = work;
   T* Yt = Zt + (size_t)n * s;
@@ -899,6 +901,23 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   T* jbuf = sig + s + 64;
   T* tsq = jbuf + 2 * (size_t)s * s;
   const bool direct = n <= SMAX;
+  // FP32 products on the tensor cores when the matrix is large
+  std::optional<TcGemm> tc;
+  if constexpr (std::is_same<T, float>::value) {
+    if (!direct && tcw && tc_gemm_eligible(m, n, s) && tcw_elems >= tc_gemm_elems(m, n, s))
+      tc.emplace(tcw, tcw_elems, M, m, n, flag_dev + 2, st);
+  }
+  // Yt = (M Z)^T and Zt = (M^T Y)^T
+  auto prod_y = [&]() -> cudaError_t {
+    if constexpr (std::is_same<T, float>::value)
+      if (tc) return tc->run(false, Zt, s, Yt);
+    return gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);
+  };
+  auto prod_z = [&]() -> cudaError_t {
+    if constexpr (std::is_same<T, float>::value)
+      if (tc) return tc->run(true, Yt, s, Zt);
+    return gemm2<T>(false, false, s, n, m, Yt, m, M, n, Zt, n, st);
+  };
   count_launches("k_fill_start", st);
   k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
   if (!direct) {
@@ -907,14 +926,21 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
     // need an orthonormal Z, hence the QR when there are no power steps
     if (iters == 0) qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
     for (int it = 0; it < iters; ++it) {
-      gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);  // Y = M Z
+      cudaError_t e = prod_y();  // Y = M Z
+      if (e != cudaSuccess) return e;
       qr_rows(Yt, s, m, (T*)nullptr, tsq, st);
-      gemm2<T>(false, false, s, n, m, Yt, m, M, n, Zt, n, st);  // Z = M^T Y
+      e = prod_z();  // Z = M^T Y
+      if (e != cudaSuccess) return e;
       qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
     }
   }
   // P = M Z = Q R (rows of Yt become the columns of Q); R = U_R Sigma V_J^T
-  gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);
+  if (direct) {
+    gemm2<T>(false, true, s, m, n, Zt, n, M, n, Yt, m, st);
+  } else {
+    const cudaError_t e = prod_y();
+    if (e != cudaSuccess) return e;
+  }
   qr_rows(Yt, s, m, R, tsq, st);
   const size_t jsm_base = sizeof(T) * (64 + SMAX) + sizeof(int) * SMAX;
   const size_t jsm_full = jsm_base + sizeof(T) * 2 * (size_t)s * s;
@@ -960,7 +986,7 @@ cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaSt
   template cudaError_t launch_zip_matrix<T>(const DevTables&, DevWeights<T>, const T*, int, int, int,   \
                                             const T*, int, int, int, int, int, T*, T*, cudaStream_t);   \
   template cudaError_t truncated_svd<T>(const T*, int, int, int, int, uint64_t, T*, T*, T*, size_t,     \
-                                        double*, int*, cudaStream_t);                                   \
+                                        double*, int*, cudaStream_t, float*, size_t);                   \
   template cudaError_t launch_zip_write<T>(const T*, const T*, int, int, int, int, int, T*, T*,         \
                                            const double*, double*, cudaStream_t);                       \
   template cudaError_t launch_zip_site0<T>(const T*, int, int, T*, double*, cudaStream_t);              \

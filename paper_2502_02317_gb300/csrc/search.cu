@@ -899,6 +899,18 @@ cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_or_flag(int* dst, const int* src) {
+  if (threadIdx.x == 0) *dst |= *src;
+}
+}  // namespace
+
+cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st) {
+  count_launches("k_or_flag", st);
+  k_or_flag<<<1, 32, 0, st>>>(dst, src);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
   count_launches("k_reset_beam", st);
   k_reset_beam<<<1, 256, 0, st>>>(ds, cur);

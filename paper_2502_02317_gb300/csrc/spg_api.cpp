@@ -471,7 +471,18 @@ struct BoundaryBufs {
   int* degc;
   T* swork;
   double* sdbl;
+  float* tcw;  // tensor-core product workspace (FP32 solves on large zipper matrices)
+  size_t tcw_elems;
 };
+
+// Tensor-core workspace of a problem's largest zipper matrix (FP32 only).
+template <typename T>
+size_t tc_work(const spg_problem* P, int chi) {
+  if (sizeof(T) != sizeof(float)) return 0;
+  const int mmax = P->bmax * chi, nmax = MAXP * chi;
+  const int s = std::min(SMAX, (chi + 16 + 15) / 16 * 16);
+  return tc_gemm_eligible(mmax, nmax, s) ? tc_gemm_elems(mmax, nmax, s) : 0;
+}
 
 template <typename T>
 size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
@@ -499,6 +510,7 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
   add(sizeof(int) * 4);
   add(sizeof(T) * sweep_work_elems<T>(P->cols, chi));
   add(sizeof(double) * 4);
+  add(sizeof(float) * tc_work<T>(P, chi));
   return b + 4096;
 }
 
@@ -533,7 +545,9 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.degc = ar.get<int>(4);
   bb.swork = ar.get<T>(sweep_work_elems<T>(P->cols, chi));
   bb.sdbl = ar.get<double>(4);
-  if (!bb.sdbl) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  bb.tcw_elems = tc_work<T>(P, chi);
+  bb.tcw = bb.tcw_elems ? ar.get<float>(bb.tcw_elems) : nullptr;
+  if (!bb.sdbl || (bb.tcw_elems && !bb.tcw)) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * sites * 3, cudaMemcpyHostToDevice, st));
@@ -575,7 +589,7 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
         const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
         const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 2);
         CK(truncated_svd<T>(bb.M, m, n, keep, iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
-                            bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st));
+                            bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st, bb.tcw, bb.tcw_elems));
         CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1,
                                bb.mps.lognorm + r, st));
         cur ^= 1;
@@ -733,6 +747,7 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
   CK(cudaMemcpyAsync(o.diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
+  CK(launch_or_flag(o.diag + 1, bb.degc + 2, st));  // truncation kernels' error flags
   CK(cudaMemcpyAsync(o.cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
   return SPG_OK;
@@ -1455,7 +1470,7 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* P, const spg_params* prm,
 int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters, double* V,
                  double* US, double* sigma) {
   if (!ctx || !M || !V || !US || !sigma) return SPG_EINVAL;
-  if (m < 1 || n < 1 || m > 1024 || n > 1024 || keep < 1 || keep > std::min(64, std::min(m, n)) || iters < 0 ||
+  if (m < 1 || n < 1 || m > 16384 || n > 16384 || keep < 1 || keep > std::min(64, std::min(m, n)) || iters < 0 ||
       iters > 64)
     return fail(ctx, SPG_EINVAL, "spg_truncate: sizes outside the limits");
   CK(cudaSetDevice(ctx->device));
@@ -1474,6 +1489,30 @@ int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t ke
   CK(cudaMemcpyAsync(sigma, w + truncated_svd_sigma_offset(m, n, keep), sizeof(double) * keep,
                      cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
+  return SPG_OK;
+}
+
+int spg_tc_product(spg_ctx* ctx, const float* M, int32_t m, int32_t n, const float* Bt, int32_t s, int32_t trans,
+                   float* out) {
+  if (!ctx || !M || !Bt || !out) return SPG_EINVAL;
+  if (m < 1 || n < 1 || s < 1) return fail(ctx, SPG_EINVAL, "spg_tc_product: sizes must be positive");
+  if (!tc_gemm_eligible(m, n, s)) return fail(ctx, SPG_EUNSUPPORTED, "spg_tc_product: sizes outside the limits");
+  CK(cudaSetDevice(ctx->device));
+  const size_t work = tc_gemm_elems(m, n, s);
+  int rc = ensure_arena(ctx, sizeof(float) * work + 1024);
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  float* w = ar.get<float>(work);
+  int* flag = ar.get<int>(1);
+  if (!flag) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  TcGemm tc(w, work, M, m, n, flag, st);
+  CK(tc.run(trans != 0, Bt, s, out));
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) return fail(ctx, SPG_ECUDA, "spg_tc_product: a bounded wait in the kernel gave up");
   return SPG_OK;
 }
 

@@ -71,6 +71,7 @@ enum : int {
   ERR_ENERGY = 1,     // incremental energy != energy recomputed from the tables
   ERR_NAN = 2,        // NaN / Inf in a normalisation
   ERR_KEY = 4,        // a packed key overflowed its words
+  ERR_TIMEOUT = 8,    // a bounded wait inside a kernel gave up
 };
 
 // Integer tables of the cluster factor graph (S1) in device memory, for the
@@ -173,9 +174,33 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
 // Truncated SVD of M (m x n row-major): V (n x keep, column k = k-th right
 // singular vector) and US (m x keep); s1 = sigma_1 written to *s1_dev,
 // degenerate-cut flag OR-ed into *flag_dev.
+// tcw / tcw_elems: optional FP32 workspace of the tensor-core products
+// (used by the FP32 instance when tc_gemm_eligible and large enough); flag_dev
+// holds 4 ints: degenerate cuts, Jacobi sweeps, error flags, unused.
 template <typename T>
 cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_t seed, T* V, T* US,
-                          T* work, size_t work_elems, double* s1_dev, int* flag_dev, cudaStream_t st);
+                          T* work, size_t work_elems, double* s1_dev, int* flag_dev, cudaStream_t st,
+                          float* tcw = nullptr, size_t tcw_elems = 0);
+
+// Tensor-core (tcgen05, split TF32) products of an FP32 truncation with one
+// zipper matrix M (m x n, row-major), whose high/low TF32 parts and those of
+// M^T are prepared once by the constructor (in `work`, tc_gemm_elems
+// elements).  run(false, Zt, s, Yt): Yt = (M Z)^T; run(true, Yt, s, Zt):
+// Zt = (M^T Y)^T, with Zt [s x n] and Yt [s x m] row-major.
+size_t tc_gemm_elems(int m, int n, int s);
+bool tc_gemm_eligible(int m, int n, int s);
+class TcGemm {
+ public:
+  TcGemm(float* work, size_t elems, const float* M, int m, int n, int* err, cudaStream_t st);
+  cudaError_t run(bool trans, const float* Bt, int s, float* out);
+
+ private:
+  int m_, n_, mp_, np_;
+  int* err_;
+  cudaStream_t st_;
+  float *Mh_, *Ml_, *MTh_, *MTl_, *Bh_, *Bl_, *part_;
+};
+cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st);
 size_t truncated_svd_work(int m, int n, int keep);
 // Offset (elements) of the sigma array inside the truncation's work buffer.
 size_t truncated_svd_sigma_offset(int m, int n, int keep);

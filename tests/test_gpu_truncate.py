@@ -32,6 +32,8 @@ def decaying(m, n, rate, seed):
     (512, 512, 32, 0.25, 6),    # the zipper's 512 x 512 at chi = 32
     (100, 300, 7, 0.4, 8),      # ragged sizes
     (5, 400, 5, 0.1, 4),        # fewer rows than the block
+    (4096, 512, 64, 0.05, 6),   # long vectors: multi-CTA tall QR
+    (3000, 2500, 40, 0.08, 4),  # ragged tall QR on both sides (one level of recursion)
 ])
 def test_truncate_vs_lapack(env, m, n, keep, rate, iters):
     spg, torch, ctx = env
