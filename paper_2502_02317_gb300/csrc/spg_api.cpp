@@ -800,10 +800,12 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
+      profile_mark(st);
       ok = cudaStreamEndCapture(st, &gb) == cudaSuccess && rc == SPG_OK;
     }
     if (ok && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       rc = enqueue_search<T>(ctx, P, prm, bb, sb, o);
+      profile_mark(st);
       ok = cudaStreamEndCapture(st, &gs) == cudaSuccess && rc == SPG_OK;
     } else {
       ok = false;
@@ -1539,6 +1541,7 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
     CK(cudaEventSynchronize(end));
     for (size_t i = 0; i < p.used; ++i) {
       float ms = 0.f;
+      if (!p.names[i]) continue;  // a closing mark
       cudaEvent_t nxt = i + 1 < p.used && p.streams[i + 1] == p.streams[i] ? p.pool[i + 1] : end;
       if (cudaEventElapsedTime(&ms, p.pool[i], nxt) != cudaSuccess) {
         cudaGetLastError();

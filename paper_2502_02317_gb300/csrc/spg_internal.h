@@ -40,6 +40,16 @@ inline long long& thread_launches() {
   return c;
 }
 
+// Inside a stream capture an external record becomes an event-record node of
+// the graph (timed when the graph runs); outside, a plain record.
+inline void record_mark(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, st);
+}
+
 inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0) {
   launch_counter().fetch_add(1, std::memory_order_relaxed);
   ++thread_launches();
@@ -51,11 +61,29 @@ inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0
     if (cudaEventCreate(&e) != cudaSuccess) return;
     p.pool.push_back(e);
   }
-  // external: inside a stream capture this becomes an event-record node
-  cudaEventRecordWithFlags(p.pool[p.used], st, cudaEventRecordExternal);
+  record_mark(p.pool[p.used], st);
   p.names.push_back(name);
   p.streams.push_back(st);
   p.flops.push_back(flops);
+  ++p.used;
+}
+
+// Closing mark of a profiled stretch of work: an event record without a
+// kernel, so that the last kernel's time ends where the work ends (report
+// entries without a name are not listed).
+inline void profile_mark(cudaStream_t st) {
+  KernelProfile& p = kernel_profile();
+  if (!p.on) return;
+  std::lock_guard<std::mutex> lock(p.mu);
+  if (p.used == p.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    p.pool.push_back(e);
+  }
+  record_mark(p.pool[p.used], st);
+  p.names.push_back(nullptr);
+  p.streams.push_back(st);
+  p.flops.push_back(0.0);
   ++p.used;
 }
 
