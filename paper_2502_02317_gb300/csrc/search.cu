@@ -512,10 +512,21 @@ __global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int
   unsigned long long pre[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
   const unsigned long long maxkey = ds.sel_state[6];
   const int w = pass >> 2, sh = 48 - (pass & 3) * 16;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
-    if (!k.valid || !prefix_match(k, pre, pass)) continue;
-    atomicAdd(ds.hist + ((k.k[w] >> sh) & 0xffff), 1u);
+  // every lane runs the same number of iterations so that the warp-wide
+  // match below sees all 32 lanes; lanes with the same digit add once
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t c0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t iters = (tot + stride - 1) / stride;
+  const int lane = threadIdx.x & 31;
+  for (size_t it = 0; it < iters; ++it) {
+    const size_t c = c0 + it * stride;
+    int digit = -1;
+    if (c < tot) {
+      CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
+      if (k.valid && prefix_match(k, pre, pass)) digit = (int)((k.k[w] >> sh) & 0xffff);
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, digit);
+    if (digit >= 0 && lane == __ffs(same) - 1) atomicAdd(ds.hist + digit, (unsigned)__popc(same));
   }
   __threadfence();
   __syncthreads();
@@ -523,33 +534,81 @@ __global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: scan the histogram, pick the digit holding the need-th key
+  // last block: scan the histogram, pick the digit holding the need-th key.
+  // part[t] = keys in digits [64 t, 64 t + 64); an inclusive block scan of
+  // part finds the group, one warp's scan of its 64 digits the digit.
   __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long wsum[32];
+  __shared__ int s_group, s_dig;
+  __shared__ unsigned long long s_before;
   const int tid = threadIdx.x, nt = blockDim.x;  // nt == 1024
   const int per = 65536 / nt;
+  const int wid = tid >> 5;
   unsigned long long loc = 0;
   for (int q = 0; q < per; ++q) loc += ((volatile unsigned*)ds.hist)[tid * per + q];
-  part[tid] = loc;
+  // inclusive scan: within the warp, then over the 32 warp totals
+  unsigned long long inc = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long v = wsum[lane], x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x - v;  // exclusive prefix of the warps
+  }
+  __syncthreads();
+  inc += wsum[wid];
+  part[tid] = inc;
+  const unsigned long long need0 = ds.sel_state[3];
+  if (tid == 0) s_group = nt - 1;
+  __syncthreads();
+  // the first group whose inclusive count reaches need
+  if (inc >= need0 && (tid == 0 || part[tid - 1] < need0)) s_group = tid;
+  __syncthreads();
+  const int t = s_group;
+  if (wid == 0) {
+    // digits 64 t .. 64 t + 63, two per lane
+    const unsigned long long before = t > 0 ? part[t - 1] : 0ull;
+    const unsigned a = ((volatile unsigned*)ds.hist)[t * per + 2 * lane];
+    const unsigned b = ((volatile unsigned*)ds.hist)[t * per + 2 * lane + 1];
+    unsigned long long x = (unsigned long long)a + b, xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    const unsigned long long ex = before + xi - x;  // keys in digits before 2 lane
+    // digit 2 lane reaches need if ex + a >= need, else 2 lane + 1 if ex + a + b >= need
+    int cand = 1 << 30;
+    if (ex + a >= need0) cand = 2 * lane;
+    else if (ex + a + b >= need0) cand = 2 * lane + 1;
+    int best = cand;
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) s_dig = best >= (1 << 30) ? per - 1 : best;  // the last digit of the group if counts were short
+    // count of keys before the chosen digit
+    const int dsel = __shfl_sync(0xffffffffu, best >= (1 << 30) ? per - 1 : best, 0);
+    unsigned long long mine = 0;
+    if (2 * lane < dsel) mine += a;
+    if (2 * lane + 1 < dsel) mine += b;
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) s_before = before + mine;
+  }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long need = ds.sel_state[3];
-    unsigned long long total = 0;
-    for (int t = 0; t < nt; ++t) total += part[t];
+    unsigned long long need = need0;
+    const unsigned long long total = part[nt - 1];
     if (pass == 0) ds.sel_state[10] = total;
     if (pass == 0 && total <= need) {
       ds.sel_state[0] = ds.sel_state[1] = ds.sel_state[2] = ~0ull;  // select all valid
       ds.sel_state[4] = 1;
     } else {
-      unsigned long long cum = 0;
-      int t = 0;
-      while (t < nt && cum + part[t] < need) cum += part[t++];
-      if (t == nt) t = nt - 1;  // cannot happen while counts are consistent
-      int digit = t * per;
-      for (; digit < (t + 1) * per - 1; ++digit) {
-        const unsigned long long hv = ((volatile unsigned*)ds.hist)[digit];
-        if (cum + hv >= need) break;
-        cum += hv;
-      }
+      const int digit = t * per + s_dig;
+      const unsigned long long cum = s_before;
       const unsigned long long hv = ((volatile unsigned*)ds.hist)[digit];
       need = need > cum ? need - cum : 1;
       ds.sel_state[w] |= (unsigned long long)digit << sh;
