@@ -225,7 +225,7 @@ int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t ke
  * keeps FP32-level accuracy.  This is the path the mixed-precision solve
  * takes for large zipper matrices; it is exported for parity tests and for
  * callers that run their own truncations.  Limits (those of that path): s a
- * multiple of 16 in 16..128, m >= 1024, n >= 256, m * n * s >= 2^26, else
+ * multiple of 16 in 16..128, m >= 256, n >= 256, m * n * s >= 2^22, else
  * SPG_EUNSUPPORTED.  Workspace comes from the context; enqueued on the
  * context's stream; returns after the stream has finished the work
  * (SPG_ECUDA with an error flag set if a bounded wait in the kernel gave up). */

@@ -314,7 +314,7 @@ size_t tc_gemm_elems(int m, int n, int s) {
 }
 
 bool tc_gemm_eligible(int m, int n, int s) {
-  return s % 16 == 0 && s >= 16 && s <= 128 && m >= 1024 && n >= 256 && (double)m * n * s >= (double)(1 << 26);
+  return s % 16 == 0 && s >= 16 && s <= 128 && m >= 256 && n >= 256 && (double)m * n * s >= (double)(1 << 22);
 }
 
 TcGemm::TcGemm(float* work, size_t elems, const float* M, int m, int n, int* err, cudaStream_t st)

@@ -19,7 +19,7 @@ def env():
 
 
 @pytest.mark.parametrize("m,n,s", [(2048, 512, 80), (3000, 700, 48), (16384, 1024, 80), (1024, 4096, 16),
-                                   (1100, 1000, 128)])
+                                   (1100, 1000, 128), (512, 512, 48), (300, 260, 64)])
 @pytest.mark.parametrize("trans", [False, True])
 def test_tc_product_vs_fp64(env, m, n, s, trans):
     spg, torch, ctx = env
@@ -41,7 +41,7 @@ def test_tc_product_vs_fp64(env, m, n, s, trans):
 def test_tc_product_rejects_small(env):
     spg, torch, ctx = env
     M = torch.zeros((512, 512), dtype=torch.float32, device="cuda")
-    B = torch.zeros((48, 512), dtype=torch.float32, device="cuda")
+    B = torch.zeros((40, 512), dtype=torch.float32, device="cuda")  # s not a multiple of 16
     with pytest.raises(spg.SpgError) as e:
         spg.spg_tc_product(ctx, M, B, False)
     assert e.value.code == -7
