@@ -163,14 +163,16 @@ __device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
       __syncthreads();
       for (int i = tid; i < len; i += nt) {
         T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
+        const T* vp = V + i;
         int c = 0;
         for (; c + 3 < k; c += 4) {
-          v0 -= rc[c] * V[(size_t)c * ld + i];
-          v1 -= rc[c + 1] * V[(size_t)(c + 1) * ld + i];
-          v2 -= rc[c + 2] * V[(size_t)(c + 2) * ld + i];
-          v3 -= rc[c + 3] * V[(size_t)(c + 3) * ld + i];
+          v0 -= rc[c] * vp[0];
+          v1 -= rc[c + 1] * vp[ld];
+          v2 -= rc[c + 2] * vp[2 * ld];
+          v3 -= rc[c + 3] * vp[3 * ld];
+          vp += 4 * ld;
         }
-        for (; c < k; ++c) v0 -= rc[c] * V[(size_t)c * ld + i];
+        for (; c < k; ++c, vp += ld) v0 -= rc[c] * vp[0];
         const T v = (v0 + v1) + (v2 + v3);
         xk[i] = v;
         if (pass == 1) part += v * v;
@@ -184,18 +186,28 @@ __device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
     part = warp_sum(part);
     if (lane == 0) red[wid] = part;
     __syncthreads();
-    T nk2 = T(0);
-    for (int w = 0; w < nw; ++w) nk2 += red[w];
-    T r2 = T(0);
-    for (int c = 0; c < k; ++c) r2 += racc[c] * racc[c];
-    const T nk = sqrt(nk2);
-    const T n0 = sqrt(nk2 + r2);
-    const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
-    const T inv = dep ? T(0) : T(1) / nk;
+    // one warp combines the partial norms with the projection coefficients
+    // (Pythagoras) and publishes the scale and the diagonal entry
+    if (wid == 0) {
+      T nk2 = lane < nw ? red[lane] : T(0);
+      nk2 = warp_sum(nk2);
+      T r2 = T(0);
+      for (int c = lane; c < k; c += 32) r2 += racc[c] * racc[c];
+      r2 = warp_sum(r2);
+      if (lane == 0) {
+        const T nk = sqrt(nk2);
+        const T n0 = sqrt(nk2 + r2);
+        const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+        red[40] = dep ? T(0) : T(1) / nk;
+        red[41] = dep ? T(0) : nk;
+      }
+    }
+    __syncthreads();
+    const T inv = red[40];
     for (int i = tid; i < len; i += nt) xk[i] *= inv;
     if (Rout)
       for (int c = tid; c < nvec; c += nt)
-        Rout[(size_t)c * nvec + k] = c < k ? racc[c] : (c == k ? (dep ? T(0) : nk) : T(0));
+        Rout[(size_t)c * nvec + k] = c < k ? racc[c] : (c == k ? red[41] : T(0));
     __syncthreads();
   }
 }
@@ -205,7 +217,7 @@ __device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
 // shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_core:
 // x_k = sum_{c <= k} R[c][k] q_c.
 template <typename T>
-__global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
+__global__ void __launch_bounds__(1024) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* V = use_smem ? red + 64 + 2 * SMAX : X;
@@ -230,7 +242,7 @@ __global__ void k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_sm
 // entries than vectors leaves the dependent ones zero, with zero rows in
 // R_b, which the stacked QR carries through.
 template <typename T>
-__global__ void k_tsqr_leaf(T* X, int nvec, int len, int bl, T* S, int use_smem) {
+__global__ void __launch_bounds__(512) k_tsqr_leaf(T* X, int nvec, int len, int bl, T* S, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* R = red + 64 + 2 * SMAX;               // nvec * nvec
@@ -293,7 +305,7 @@ __global__ void k_tsqr_apply(T* X, int nvec, int len, int bl, const T* __restric
 // The chiR columns of a site are staged as contiguous vectors in `work`
 // (shared memory when they fit, else the global scratch) for the CGS2.
 template <typename T>
-__global__ void k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int use_smem) {
+__global__ void __launch_bounds__(1024) k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* R = red + 64 + 2 * SMAX;               // MAXCHI * MAXCHI

@@ -304,69 +304,58 @@ __global__ void k_parent_keys(DevTables tb, int site, DevSearch ds, int cur, int
   for (int w = 0; w < KEYW; ++w) ds.key[(size_t)b * KEYW + w] = k[w];
 }
 
-// Classes by sorting (key, index) in one block (bitonic, in shared memory):
-// within a run of equal keys the first index is the representative and the
-// next index is the member that follows.
-__global__ void k_classes(DevSearch ds, int cur, int merge) {
-  extern __shared__ unsigned long long cls_smem[];
+// Classes of equal reduced parent keys by open addressing: every beam
+// element inserts its key into a table of hsize (a power of two >= 2 cap)
+// slots (slot = owner index + 1, 0 empty), joining the slot whose owner has
+// the same key; the representative of a class is the lowest index of the
+// slot's members (atomicMin), which is the class's lowest lex rank.  The
+// slot of element b is kept in nxt[b].  Table and minima are reset by the
+// launcher (byte memsets).
+
+__device__ __forceinline__ unsigned key_hash(const unsigned long long* k) {
+  unsigned long long h = 0x9e3779b97f4a7c15ull;
+  for (int w = 0; w < KEYW; ++w) {
+    h ^= k[w] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h *= 0xff51afd7ed558ccdull;
+  }
+  return (unsigned)(h ^ (h >> 32));
+}
+
+__global__ void k_class_insert(DevSearch ds, int cur, int merge) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int nb = ds.n_beam[cur];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  if (b >= nb) return;
   if (!merge) {
-    for (int b = tid; b < nb; b += nt) {
-      ds.rep[b] = b;
-      ds.nxt[b] = -1;
-    }
+    ds.nxt[b] = -1;
     return;
   }
-  int P = 1;
-  while (P < nb) P <<= 1;
-  unsigned long long* K = cls_smem;           // [P][KEYW]
-  int* idx = reinterpret_cast<int*>(K + (size_t)P * KEYW);  // [P]
-  for (int e = tid; e < P; e += nt) {
-    for (int w = 0; w < KEYW; ++w) K[(size_t)e * KEYW + w] = e < nb ? ds.key[(size_t)e * KEYW + w] : ~0ull;
-    idx[e] = e < nb ? e : 0x7fffffff;
-  }
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int e = tid; e < P; e += nt) {
-        const int o = e ^ jj;
-        if (o <= e) continue;
-        const bool up = (e & k) == 0;
-        // compare (key, idx) of e and o
-        int cmp = 0;
-        for (int w = KEYW - 1; w >= 0 && cmp == 0; --w) {
-          const unsigned long long a = K[(size_t)e * KEYW + w], b = K[(size_t)o * KEYW + w];
-          cmp = a < b ? -1 : (a > b ? 1 : 0);
-        }
-        if (cmp == 0) cmp = idx[e] < idx[o] ? -1 : (idx[e] > idx[o] ? 1 : 0);
-        if ((cmp > 0) == up) {
-          for (int w = 0; w < KEYW; ++w) {
-            const unsigned long long t = K[(size_t)e * KEYW + w];
-            K[(size_t)e * KEYW + w] = K[(size_t)o * KEYW + w];
-            K[(size_t)o * KEYW + w] = t;
-          }
-          const int t = idx[e];
-          idx[e] = idx[o];
-          idx[o] = t;
-        }
-      }
-      __syncthreads();
+  const unsigned long long* kb = ds.key + (size_t)b * KEYW;
+  const unsigned mask = (unsigned)ds.hsize - 1u;
+  unsigned slot = key_hash(kb) & mask;
+  int mine = -1;
+  for (int t = 0; t < ds.hsize; ++t, slot = (slot + 1) & mask) {
+    const int owner = atomicCAS(ds.htab + slot, 0, b + 1);
+    if (owner == 0) {
+      mine = (int)slot;
+      break;
+    }
+    const unsigned long long* ko = ds.key + (size_t)(owner - 1) * KEYW;
+    bool eq = true;
+    for (int w = 0; w < KEYW; ++w) eq = eq && ko[w] == kb[w];
+    if (eq) {
+      mine = (int)slot;
+      break;
     }
   }
-  for (int e = tid; e < nb; e += nt) {
-    int f = e;
-    while (f > 0) {
-      bool same = true;
-      for (int w = 0; w < KEYW; ++w) same &= K[(size_t)(f - 1) * KEYW + w] == K[(size_t)e * KEYW + w];
-      if (!same) break;
-      --f;
-    }
-    bool nsame = e + 1 < nb;
-    for (int w = 0; w < KEYW && nsame; ++w) nsame = K[(size_t)(e + 1) * KEYW + w] == K[(size_t)e * KEYW + w];
-    ds.rep[idx[e]] = idx[f];
-    ds.nxt[idx[e]] = nsame ? idx[e + 1] : -1;
-  }
+  ds.nxt[b] = mine;  // never -1: the table has more slots than elements
+  if (mine >= 0) atomicMin(ds.hmin + mine, b);
+}
+
+__global__ void k_class_rep(DevSearch ds, int cur, int merge) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ds.n_beam[cur]) return;
+  const int slot = ds.nxt[b];
+  ds.rep[b] = (merge && slot >= 0) ? ds.hmin[slot] : b;
 }
 
 // For each (class representative b, x): the member with the lowest
@@ -486,6 +475,7 @@ __global__ void k_select_init(DevSearch ds) {
     ds.sel_state[8] = 0;
     ds.sel_state[10] = 0;
     *ds.sel_count = 0;
+    *ds.pend_n = 0;
     *ds.done_ctr = 0;
   }
   for (int e = threadIdx.x; e < 65536; e += blockDim.x) ds.hist[e] = 0;
@@ -503,12 +493,16 @@ __device__ __forceinline__ bool prefix_match(const CandKey& k, const unsigned lo
   return true;
 }
 
-__global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int pass, double log_cut) {
+// One radix pass: histogram of the 16-bit digit `pass` of the keys that
+// match the prefix chosen so far, over all candidates (list == nullptr) or
+// over the candidate ids list[0 .. *list_n).
+__global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int pass, double log_cut,
+                              const int* list, const int* list_n) {
   __shared__ bool s_last;
   const unsigned long long status = ds.sel_state[4];
   if (status != 0) return;
   const int nb = ds.n_beam[cur], d = tb.d[site];
-  const size_t tot = (size_t)ds.cap * ds.dmax;
+  const size_t tot = list ? (size_t)*list_n : (size_t)ds.cap * ds.dmax;
   unsigned long long pre[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
   const unsigned long long maxkey = ds.sel_state[6];
   const int w = pass >> 2, sh = 48 - (pass & 3) * 16;
@@ -519,9 +513,10 @@ __global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int
   const size_t iters = (tot + stride - 1) / stride;
   const int lane = threadIdx.x & 31;
   for (size_t it = 0; it < iters; ++it) {
-    const size_t c = c0 + it * stride;
+    const size_t i = c0 + it * stride;
     int digit = -1;
-    if (c < tot) {
+    if (i < tot) {
+      const size_t c = list ? (size_t)list[i] : i;
       CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
       if (k.valid && prefix_match(k, pre, pass)) digit = (int)((k.k[w] >> sh) & 0xffff);
     }
@@ -633,41 +628,66 @@ __device__ __forceinline__ bool key_le(const CandKey& k, const unsigned long lon
   return k.k[2] <= t[2];
 }
 
-__global__ void k_select_compact(DevTables tb, int site, DevSearch ds, int cur, double log_cut) {
+// Candidates (all, or the ids list[0 .. *list_n)) against the selection:
+// with split set and the selection still open after the first pass, the
+// top digit decides (below the chosen digit: selected, equal: pending for
+// the later passes, above: rejected); otherwise the full threshold key
+// decides (key <= threshold: selected).  Selected ids go to sel_list,
+// pending ones to pend; the extremes of the selected and rejected log p feed
+// the near-tie test.
+__global__ void k_select_classify(DevTables tb, int site, DevSearch ds, int cur, double log_cut, const int* list,
+                                  const int* list_n, int split) {
+  if (!split && ds.sel_state[4] == 2) return;  // resolved by k_select_refine
   const int nb = ds.n_beam[cur], d = tb.d[site];
-  const size_t tot = (size_t)ds.cap * ds.dmax;
+  const size_t tot = list ? (size_t)*list_n : (size_t)ds.cap * ds.dmax;
   const unsigned long long thr[3] = {ds.sel_state[0], ds.sel_state[1], ds.sel_state[2]};
   const unsigned long long maxkey = ds.sel_state[6];
+  const bool by_digit = split && ds.sel_state[4] == 0;
+  const unsigned long long d0 = thr[0] >> 48;
   unsigned long long min_sel = ~0ull, max_rej = 0ull;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t c0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   // every lane runs the same number of iterations so that the warp-wide
-  // ballot below sees all 32 lanes
+  // ballots below see all 32 lanes
   const size_t iters = (tot + stride - 1) / stride;
   const int lane = threadIdx.x & 31;
   for (size_t it = 0; it < iters; ++it) {
-    const size_t c = c0 + it * stride;
-    bool take = false;
-    CandKey k;
-    k.valid = false;
-    if (c < tot) k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
-    if (k.valid) {
-      if (key_le(k, thr)) {
-        take = true;
-        min_sel = min(min_sel, ord_f64(k.lp));
-      } else {
-        max_rej = max(max_rej, ord_f64(k.lp) + 1ull);  // +1 keeps 0 = "none"
+    const size_t i = c0 + it * stride;
+    bool take = false, pend = false;
+    size_t c = 0;
+    if (i < tot) {
+      c = list ? (size_t)list[i] : i;
+      CandKey k = cand_key(ds, cur, c, nb, d, log_cut, maxkey);
+      if (k.valid) {
+        if (by_digit) {
+          const unsigned long long dg = k.k[0] >> 48;
+          take = dg < d0;
+          pend = dg == d0;
+        } else {
+          take = key_le(k, thr);
+        }
+        if (take)
+          min_sel = min(min_sel, ord_f64(k.lp));
+        else if (!pend)
+          max_rej = max(max_rej, ord_f64(k.lp) + 1ull);  // +1 keeps 0 = "none"
       }
     }
-    const unsigned mask = __ballot_sync(0xffffffffu, take);
-    if (mask) {
+    const unsigned mt = __ballot_sync(0xffffffffu, take);
+    if (mt) {
       int base = 0;
-      if (lane == 0) base = atomicAdd(ds.sel_count, __popc(mask));
+      if (lane == 0) base = atomicAdd(ds.sel_count, __popc(mt));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (take) {
-        const int pos = base + __popc(mask & ((1u << lane) - 1u));
+        const int pos = base + __popc(mt & ((1u << lane) - 1u));
         if (pos < ds.cap) ds.sel_list[pos] = (int)c;
       }
+    }
+    const unsigned mp = __ballot_sync(0xffffffffu, pend);
+    if (mp) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(ds.pend_n, __popc(mp));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (pend) ds.pend[base + __popc(mp & ((1u << lane) - 1u))] = (int)c;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -677,6 +697,144 @@ __global__ void k_select_compact(DevTables tb, int site, DevSearch ds, int cur, 
   if (lane == 0) {
     if (min_sel != ~0ull) atomicMin(ds.sel_state + 7, min_sel);
     if (max_rej != 0ull) atomicMax(ds.sel_state + 8, max_rej);
+  }
+}
+
+// The pending candidates (those sharing the top digit chosen by the first
+// pass) resolved in one block: 8-bit radix rounds over the rest of the key
+// (histograms in shared memory, keys recomputed from the candidate arrays),
+// then the pending ids up to the final threshold appended to sel_list.  The
+// selection is marked resolved (state 2).
+__global__ void k_select_refine(DevTables tb, int site, DevSearch ds, int cur, double log_cut) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_pre[3];
+  __shared__ unsigned long long s_need;
+  __shared__ int s_done, s_base;
+  __shared__ unsigned long long s_min, s_max;
+  if (ds.sel_state[4] != 0) return;
+  const int n = *ds.pend_n;
+  const int nb = ds.n_beam[cur], d = tb.d[site];
+  const unsigned long long maxkey = ds.sel_state[6];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  if (tid == 0) {
+    s_pre[0] = ds.sel_state[0];
+    s_pre[1] = ds.sel_state[1];
+    s_pre[2] = ds.sel_state[2];
+    s_need = ds.sel_state[3];
+    s_done = 0;
+    s_min = ~0ull;
+    s_max = 0ull;
+  }
+  __syncthreads();
+  // bits fixed so far: 16 (the first pass); round r fixes 8 more
+  for (int fixed = 16; fixed < 192 && !s_done; fixed += 8) {
+    for (int e = tid; e < 256; e += nt) hist[e] = 0u;
+    __syncthreads();
+    const int w = fixed >> 6, sh = 56 - (fixed & 63);
+    const unsigned long long pre0 = s_pre[0], pre1 = s_pre[1], pre2 = s_pre[2];
+    for (int i = tid; i < n; i += nt) {
+      const CandKey k = cand_key(ds, cur, (size_t)ds.pend[i], nb, d, log_cut, maxkey);
+      if (!k.valid) continue;
+      // the key's bits above this digit must equal the prefix
+      bool match = true;
+      const unsigned long long pre[3] = {pre0, pre1, pre2};
+      for (int q = 0; q < w; ++q) match = match && k.k[q] == pre[q];
+      const unsigned long long m = (fixed & 63) ? (~0ull << (64 - (fixed & 63))) : 0ull;
+      match = match && ((k.k[w] & m) == (pre[w] & m));
+      if (match) atomicAdd(&hist[(k.k[w] >> sh) & 0xff], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      // inclusive scan of the 256 bins, 8 per lane
+      unsigned loc[8];
+      unsigned sum = 0;
+      for (int q = 0; q < 8; ++q) {
+        loc[q] = hist[lane * 8 + q];
+        sum += loc[q];
+      }
+      unsigned incl = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      unsigned long long cum = incl - sum;  // keys in the digits before this lane's first
+      const unsigned long long need = s_need;
+      int digit = 1 << 30;
+      unsigned long long before = 0, hv = 0;
+      for (int q = 0; q < 8; ++q) {
+        if (digit == (1 << 30) && cum + loc[q] >= need) {
+          digit = lane * 8 + q;
+          before = cum;
+          hv = loc[q];
+        }
+        cum += loc[q];
+      }
+      // the lowest lane that found the digit publishes it
+      const unsigned found = __ballot_sync(0xffffffffu, digit != (1 << 30));
+      const int src = found ? __ffs(found) - 1 : 31;
+      digit = __shfl_sync(0xffffffffu, digit, src);
+      before = __shfl_sync(0xffffffffu, before, src);
+      hv = __shfl_sync(0xffffffffu, hv, src);
+      if (lane == 0) {
+        if (!found) digit = 255;  // cannot happen while the counts are consistent
+        s_pre[w] |= (unsigned long long)digit << sh;
+        const unsigned long long nn = need > before ? need - before : 1ull;
+        s_need = nn;
+        if (hv == nn || fixed + 8 >= 192) {
+          if (sh > 0) s_pre[w] |= (1ull << sh) - 1ull;
+          for (int q = w + 1; q < 3; ++q) s_pre[q] = ~0ull;
+          s_done = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // classify the pending ids against the final threshold
+  const unsigned long long thr[3] = {s_pre[0], s_pre[1], s_pre[2]};
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  unsigned long long mn = ~0ull, mx = 0ull;
+  for (int i0 = 0; i0 < n; i0 += nt) {
+    const int i = i0 + tid;
+    bool take = false;
+    int c = 0;
+    if (i < n) {
+      c = ds.pend[i];
+      const CandKey k = cand_key(ds, cur, (size_t)c, nb, d, log_cut, maxkey);
+      if (k.valid) {
+        take = key_le(k, thr);
+        if (take)
+          mn = min(mn, ord_f64(k.lp));
+        else
+          mx = max(mx, ord_f64(k.lp) + 1ull);
+      }
+    }
+    const unsigned msk = __ballot_sync(0xffffffffu, take);
+    int base = 0;
+    if (lane == 0 && msk) base = atomicAdd(&s_base, __popc(msk));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
+      const int pos = *ds.sel_count + base + __popc(msk & ((1u << lane) - 1u));
+      if (pos < ds.cap) ds.sel_list[pos] = c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    if (mn != ~0ull) atomicMin(&s_min, mn);
+    if (mx != 0ull) atomicMax(&s_max, mx);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *ds.sel_count += s_base;
+    if (s_min != ~0ull) atomicMin(ds.sel_state + 7, s_min);
+    if (s_max != 0ull) atomicMax(ds.sel_state + 8, s_max);
+    ds.sel_state[0] = thr[0];
+    ds.sel_state[1] = thr[1];
+    ds.sel_state[2] = thr[2];
+    ds.sel_state[4] = 2;
   }
 }
 
@@ -898,13 +1056,14 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
   const int nbk = (ds.cap + 255) / 256;
   count_launches("k_parent_keys", st);
   k_parent_keys<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
-  int P = 1;
-  while (P < ds.cap) P <<= 1;
-  const int csm = (int)((sizeof(unsigned long long) * KEYW + sizeof(int)) * P);
-  static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
-  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
-  count_launches("k_classes", st);
-  k_classes<<<1, 1024, csm, st>>>(ds, cur, merge);
+  if (merge) {
+    cudaMemsetAsync(ds.htab, 0, sizeof(int) * ds.hsize, st);
+    cudaMemsetAsync(ds.hmin, 0x7f, sizeof(int) * ds.hsize, st);
+  }
+  count_launches("k_class_insert", st);
+  k_class_insert<<<nbk, 256, 0, st>>>(ds, cur, merge);
+  count_launches("k_class_rep", st);
+  k_class_rep<<<nbk, 256, 0, st>>>(ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
   const int wb = (int)std::min<size_t>((tot + 255) / 256, 8192);
   cudaMemsetAsync(ds.wmin, 0xff, sizeof(unsigned long long) * tot, st);
@@ -929,12 +1088,14 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
     count_launches("k_logp_max", st);
     k_logp_max<<<blocks, 1024, 0, st>>>(tb, site, ds, cur);
   }
-  for (int pass = 0; pass < 12; ++pass) {
-    count_launches("k_select_pass", st);
-    k_select_pass<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, pass, log_cut);
-  }
-  count_launches("k_select_compact", st);
-  k_select_compact<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, log_cut);
+  // pass 0 and the split scan every candidate; the later passes and the
+  // final classification only the candidates of the chosen top digit
+  count_launches("k_select_pass", st);
+  k_select_pass<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, 0, log_cut, nullptr, nullptr);
+  count_launches("k_select_classify", st);
+  k_select_classify<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, log_cut, nullptr, nullptr, 1);
+  count_launches("k_select_refine", st);
+  k_select_refine<<<1, 1024, 0, st>>>(tb, site, ds, cur, log_cut);
   int P = 1;
   while (P < ds.cap) P <<= 1;
   count_launches("k_select_sort", st);

@@ -629,6 +629,8 @@ size_t search_bytes(const spg_problem* P, int cap, int chi) {
   add(sizeof(int) * cap);
   add(sizeof(unsigned long long) * cap * KEYW);
   add(sizeof(int) * cap * 3);
+  add(sizeof(int) * 4 * (size_t)cap * 2 + 1024);  // class hash table and minima
+  add(sizeof(int) * cap * dmax);
   add(sizeof(unsigned) * 65536);
   add(sizeof(unsigned long long) * 16);
   add(sizeof(int) * 8);
@@ -660,7 +662,12 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   ds.key = ar.get<unsigned long long>((size_t)cap * KEYW);
   ds.rep = ar.get<int>(cap);
   ds.nxt = ar.get<int>(cap);
+  ds.hsize = 1;
+  while (ds.hsize < 2 * cap) ds.hsize <<= 1;
+  ds.htab = ar.get<int>(ds.hsize);
+  ds.hmin = ar.get<int>(ds.hsize);
   ds.sel_list = ar.get<int>(cap);
+  ds.pend = ar.get<int>((size_t)cap * P->dmax);
   ds.hist = ar.get<unsigned>(65536);
   ds.sel_state = ar.get<unsigned long long>(16);
   int* misc = ar.get<int>(8);
@@ -669,6 +676,7 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   ds.near_ties = misc + 2;
   ds.err = misc + 3;
   ds.deg_cuts = misc + 4;
+  ds.pend_n = misc + 5;
   ds.candidates = ar.get<double>(2);
   sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * P->bmax);
   sb.bt.rs = P->bmax;

@@ -291,11 +291,16 @@ struct DevSearch {
   int* wkey;            // [cap] winner (member * dmax + x) of a class when the site is not in the key
   unsigned long long* key;  // [cap][KEYW]
   int* rep;             // [cap] class representative
-  int* nxt;             // [cap] next member of the class (-1 at the end)
+  int* nxt;             // [cap] hash slot of the element's class
+  int* htab;            // [hsize] class table: owner index + 1 (0 empty)
+  int* hmin;            // [hsize] lowest member index of each slot
+  int hsize;            // power of two >= 2 cap
   unsigned* hist;       // [65536]
   unsigned long long* sel_state;  // select-state words
   int* sel_list;        // [cap] selected candidate ids (b*dmax + x)
   int* sel_count;
+  int* pend;            // [cap][dmax] candidate ids of the chosen top digit, refined by later passes
+  int* pend_n;
   unsigned* done_ctr;
   int* near_ties;
   int* err;
