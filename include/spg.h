@@ -125,8 +125,7 @@ const char* spg_last_error(const spg_ctx* ctx);
  * edges below it; the row MPO's bond pairs the left cluster's projection with
  * the up-left cluster's down-right projection, up to 16 x 16).  A joint
  * projection with more than 16 classes is SPG_EUNSUPPORTED.  Variational
- * sweeps (num_sweeps > 0) are built for the square lattice only: a problem
- * with diagonal couplings solved with num_sweeps > 0 is SPG_EUNSUPPORTED. */
+ * sweeps (num_sweeps > 0) contract such sites one up index at a time. */
 int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei,
                       const int32_t* ej, const double* J, const double* h,
                       const int32_t* cluster_of_spin, int32_t grid_rows, int32_t grid_cols,

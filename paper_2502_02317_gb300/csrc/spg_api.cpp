@@ -508,7 +508,7 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
   add(sizeof(T) * truncated_svd_work((int)mmax, (int)nmax, chi));
   add(sizeof(double) * 4);
   add(sizeof(int) * 4);
-  add(sizeof(T) * sweep_work_elems<T>(P->cols, chi));
+  add(sizeof(T) * sweep_work_elems<T>(P->cols, chi, P->bmax));
   add(sizeof(double) * 4);
   add(sizeof(float) * tc_work<T>(P, chi));
   return b + 4096;
@@ -543,7 +543,7 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.svdw = ar.get<T>(bb.svdw_elems);
   bb.s1 = ar.get<double>(4);
   bb.degc = ar.get<int>(4);
-  bb.swork = ar.get<T>(sweep_work_elems<T>(P->cols, chi));
+  bb.swork = ar.get<T>(sweep_work_elems<T>(P->cols, chi, P->bmax));
   bb.sdbl = ar.get<double>(4);
   bb.tcw_elems = tc_work<T>(P, chi);
   bb.tcw = bb.tcw_elems ? ar.get<float>(bb.tcw_elems) : nullptr;
@@ -598,7 +598,7 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
     }
     if (prm->num_sweeps > 0)
       CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, r, cols, pl.dimA.data(), P->dims.data(), P->d.data(),
-                               prm->num_sweeps, bb.swork, bb.sdbl, st));
+                               P->gD.data(), prm->num_sweeps, bb.swork, bb.sdbl, st));
   }
   return SPG_OK;
 }
@@ -703,8 +703,6 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
   if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
-  if (prm->num_sweeps > 0 && P->ucpl)
-    return fail(ctx, SPG_EUNSUPPORTED, "variational sweeps are built for the square lattice only");
   return SPG_OK;
 }
 

@@ -250,13 +250,14 @@ void launch_cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st);
 
 // num_sweeps variational sweeps of row `row`'s boundary MPS (S4) against
 // W_row B_{row+1}; dimA / hdims are the host copies of the MPS dims and the
-// table dims; work holds sweep_work_elems<T>(cols, chi) T, dscratch 2 doubles.
+// table dims, hgD the host copy of gD; work holds sweep_work_elems<T>(cols,
+// chi, bmax) T, dscratch 2 doubles.
 template <typename T>
-size_t sweep_work_elems(int cols, int chi);
+size_t sweep_work_elems(int cols, int chi, int bmax);
 template <typename T>
 cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
-                               const int* dimA, const int* hdims, const int* hstates, int sweeps, T* work,
-                               double* dscratch, cudaStream_t st);
+                               const int* dimA, const int* hdims, const int* hstates, const uint8_t* hgD,
+                               int sweeps, T* work, double* dscratch, cudaStream_t st);
 
 // Value of an MPS whose physical dims are all 1 (row 0 closed from above).
 template <typename T>

@@ -8,8 +8,9 @@
 // Layouts (row r of the MPO, psi = B_{r+1} sites B[s][b][b'], phi sites
 // P[u][a][a'], both [p][chi_l][chi_r]):
 //   environments  E[l][a][b]  (MPO bond < 16, phi bond, psi bond)
-// These sweeps are built for MPOs whose tensors depend on the up index only
-// through b_up (the square lattice); the caller rejects the others.
+// Sites whose tensor depends on the up index beyond b_up (king's graph: the
+// anti-diagonal factor and the down-right offset of the right bond) are
+// contracted one up index at a time with per-u coefficient tables.
 //   W[l,r,u,s] = sum_x w(x) bL[l][PL x] bU[u][PU x] [r = PR x][s = PD x]
 // Every contraction groups the cluster states x by their projections, so the
 // dense MPO is never formed.
@@ -104,10 +105,17 @@ __global__ void k_xgemm(DevTables tb, int s, int n2, int M, int N, int K, const 
 //   mode 0: coef[u][x] = bU[u][PU x] w(x)      (local tensor)
 //   mode 1: coef[l][x] = bL[l][PL x] w(x)      (right environment)
 //   mode 2: coef[r][x] = [PR x == r] w(x)      (left environment)
+// and, for one up index u of a site whose tensor depends on u beyond b_up
+// (king's graph: the anti-diagonal factor bA and the right-bond offset g):
+//   mode 3: coef[0][x] = bU[u][PU x] w(x)
+//   mode 4: coef[l][x] = bA[l / Gin][u] bL[l][PL x] bU[u][PU x] w(x)
+//   mode 5: coef[r][x] = [PR x * Gout + g == r] bU[u][PU x] w(x)
 template <typename T>
-__global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, int K, T* __restrict__ coef) {
+__global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, int K, int u, int g,
+                             T* __restrict__ coef) {
   const int d = tb.d[s];
   const size_t so = (size_t)s * tb.dmax;
+  const int* dm = tb.dims + s * DIMW;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * d; e += gridDim.x * blockDim.x) {
     const int k = e / d, x = e % d;
     T v;
@@ -115,10 +123,34 @@ __global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, in
       v = wt.bU[(size_t)s * 256 + k * 16 + tb.PU[so + x]];
     else if (mode == 1)
       v = wt.bL[(size_t)s * tb.lstride + k * MAXP + tb.PL[so + x]];
-    else
+    else if (mode == 2)
       v = tb.PR[so + x] == k ? T(1) : T(0);
+    else if (mode == 3)
+      v = wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
+    else if (mode == 4)
+      v = wt.bA[(size_t)s * 256 + (k / dm[D_GIN]) * 16 + u] * wt.bL[(size_t)s * tb.lstride + k * MAXP + tb.PL[so + x]] *
+          wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
+    else
+      v = (tb.PR[so + x] * dm[D_GOUT] + g == k) ? wt.bU[(size_t)s * 256 + u * 16 + tb.PU[so + x]] : T(0);
     coef[e] = v * wt.w[so + x];
   }
+}
+
+// bLu[l][h] = bA[l / Gin][u] bL[l][h]: the left weights of one up index u.
+template <typename T>
+__global__ void k_left_weights_u(DevTables tb, DevWeights<T> wt, int s, int u, T* __restrict__ out) {
+  const int* dm = tb.dims + s * DIMW;
+  const int DL = dm[D_DL];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < DL * MAXP; e += gridDim.x * blockDim.x) {
+    const int l = e / MAXP;
+    out[e] = wt.bA[(size_t)s * 256 + (l / dm[D_GIN]) * 16 + u] * wt.bL[(size_t)s * tb.lstride + e];
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] += x[e];
 }
 
 // In-place scaling of buf[0..n) to max |.| = 1, log of the scale added to *logacc.
@@ -192,34 +224,39 @@ inline int nblk(size_t n, int t = 256) { return (int)std::min<size_t>((n + t - 1
 
 // ---------------------------------------------------------------- host driver
 template <typename T>
-size_t sweep_work_elems(int cols, int chi) {
-  const size_t env = (size_t)chi * MAXP * chi;
-  // Lcache (cols+1 envs), R (cols+1 envs), Rcur, pairs (16*16*chi*chi), F and
-  // Lp (16*chi*chi each), C (16*chi*chi), vectors (16*chi*chi), doubles
-  return (size_t)(2 * (cols + 1) + 2) * env + (size_t)MAXP * MAXP * chi * chi + 4 * (size_t)MAXP * chi * chi +
-         (size_t)MAXS * chi * chi + (size_t)MAXP * MAXS + 64;
+size_t sweep_work_elems(int cols, int chi, int bmax) {
+  const size_t env = (size_t)chi * bmax * chi;
+  // Lcache (cols+1 envs), R (cols+1 envs), Rcur, Rtmp, pairs
+  // (16 * max(16, bmax) * chi * chi), F, Lp, C, vectors (16*chi*chi each),
+  // per-state products (MAXS*chi*chi), coefficients (max(16, bmax) * MAXS), one
+  // more env (per-u partial sums), per-u left weights (bmax * 16)
+  return (size_t)(2 * (cols + 1) + 3) * env + (size_t)MAXP * std::max(MAXP, bmax) * chi * chi +
+         4 * (size_t)MAXP * chi * chi + (size_t)MAXS * chi * chi + (size_t)std::max(MAXP, bmax) * MAXS +
+         (size_t)bmax * MAXP + 64;
 }
 
 template <typename T>
 cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row, int cols,
-                               const int* dimA, const int* hdims, const int* hstates, int sweeps, T* work,
-                               double* dscratch, cudaStream_t st) {
+                               const int* dimA, const int* hdims, const int* hstates, const uint8_t* hgD,
+                               int sweeps, T* work, double* dscratch, cudaStream_t st) {
   auto tb_dims_host = [&](int s, int k) { return hdims[(size_t)s * DIMW + k]; };
   auto hd_states = [&](int s) { return hstates[s]; };
   auto cgs_rows = [&](T* X, int nvec, int len, cudaStream_t stm) { launch_cgs2_rows<T>(X, nvec, len, nullptr, stm); };
   const int chi = (int)std::lround(std::sqrt((double)(mps.site_stride / MAXP)));
-  const size_t env = (size_t)chi * MAXP * chi;
+  const size_t env = (size_t)chi * tb.bmax * chi;
   T* Lc = work;                                 // [cols+1][env]
   T* Rs = Lc + (size_t)(cols + 1) * env;        // [cols+1][env]
   T* Rcur = Rs + (size_t)(cols + 1) * env;      // [env]
   T* Rtmp = Rcur + env;                         // [env]
-  T* Pp = Rtmp + env;                           // pairs [16*16*chi*chi]
-  T* F = Pp + (size_t)MAXP * MAXP * chi * chi;  // [16*chi*chi]
+  T* Ctmp = Rtmp + env;                         // [env] per-u partial sums
+  T* Pp = Ctmp + env;                           // pairs [16*max(16,bmax)*chi*chi]
+  T* F = Pp + (size_t)MAXP * std::max(MAXP, tb.bmax) * chi * chi;  // [16*chi*chi]
   T* Lp = F + (size_t)MAXP * chi * chi;         // [chi*16*chi]
   T* C = Lp + (size_t)MAXP * chi * chi;         // [16*chi*chi]
   T* Vv = C + (size_t)MAXP * chi * chi;         // vectors [16*chi*chi]
   T* G = Vv + (size_t)MAXP * chi * chi;         // per-state products [MAXS*chi*chi]
-  T* Cf = G + (size_t)MAXS * chi * chi;         // state coefficients [16*MAXS]
+  T* Cf = G + (size_t)MAXS * chi * chi;         // state coefficients [max(16,bmax)*MAXS] (K <= DU, DL or DR)
+  T* Bu = Cf + (size_t)std::max(MAXP, tb.bmax) * MAXS;  // left weights of one up index [bmax*16]
   double* rsum = dscratch;                      // [1]
   double* junk = dscratch + 1;
   auto site_ptr = [&](int r, int j) { return mps.A + (size_t)(r * cols + j) * mps.site_stride; };
@@ -239,10 +276,24 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     count_launches("k_xgemm", st, 2.0 * nq * M * N * K);
     k_xgemm<T><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C);
   };
-  auto coef = [&](int s, int mode, int K) {
+  auto coef = [&](int s, int mode, int K, int u = 0, int g = 0) {
     const int d = hd_states(s);
     count_launches("k_state_coef", st);
-    k_state_coef<T><<<nblk((size_t)K * d), 256, 0, st>>>(tb, wt, s, mode, K, Cf);
+    k_state_coef<T><<<nblk((size_t)K * d), 256, 0, st>>>(tb, wt, s, mode, K, u, g, Cf);
+  };
+  // king's graph: per up index u, the right-bond offset g = gD_up[u]
+  auto g_of = [&](int s, int u) { return s >= cols ? (int)hgD[(size_t)(s - cols) * MAXP + u] : 0; };
+  auto u_coupled = [&](int s) { return tb_dims_host(s, D_UCPL) != 0; };
+  auto axpy = [&](T* y, const T* x, size_t n) {
+    count_launches("k_axpy", st);
+    k_axpy<T><<<nblk(n), 256, 0, st>>>(y, x, n);
+  };
+  // Lp[h][a][b] = sum_l bA[l / Gin][u] bL[l][h] E[l][a][b]
+  auto left_prime_u = [&](int s, const T* Lenv, int chiA, int chiB, int u) {
+    const int DL = tb_dims_host(s, 0), NL = tb_dims_host(s, 4);
+    count_launches("k_left_weights_u", st);
+    k_left_weights_u<T><<<nblk((size_t)DL * MAXP), 256, 0, st>>>(tb, wt, s, u, Bu);
+    gemm2<T>(true, false, NL, chiA * chiB, DL, Bu, MAXP, Lenv, chiA * chiB, Lp, chiA * chiB, st);
   };
   // Lp[h][a][b] = sum_l bL[l][h] E[l][a][b]
   auto left_prime = [&](int s, const T* Lenv, int chiA, int chiB) {
@@ -270,6 +321,22 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
     const int DR = tb_dims_host(s, 1), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
+    if (u_coupled(s)) {
+      // one up index at a time: C[u] = sum_x bU[u][PU x] w(x) Lp_u[PL x] Pr[PD x][PR x * Gout + g_u]
+      const int Gout = tb_dims_host(s, D_GOUT);
+      pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
+      for (int u = 0; u < DU; ++u) {
+        const int g = g_of(s, u);
+        left_prime_u(s, Lenv, chiA, chiBl, u);
+        xgemm(s, d, 1, chiA, chiAr, chiBl, Lp, XOff{1, 0, (long long)chiA * chiBl, 0}, chiBl, 1,
+              Pp + (size_t)g * chiBl * chiAr,
+              XOff{4, 2, (long long)DR * chiBl * chiAr, (long long)Gout * chiBl * chiAr}, chiAr, 1, G);
+        coef(s, 3, 1, u, g);
+        gemm2<T>(false, false, 1, chiA * chiAr, d, Cf, d, G, chiA * chiAr, C + (size_t)u * chiA * chiAr,
+                 chiA * chiAr, st);
+      }
+      return cudaGetLastError();
+    }
     left_prime(s, Lenv, chiA, chiBl);
     pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
     // G_x[a][a'] = sum_b Lp[PL x][a][b] Pr[PD x][PR x][b][a']
@@ -288,6 +355,24 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     const int DL = tb_dims_host(s, 0), DR = tb_dims_host(s, 1), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
     const T* P = site_ptr(row, j);
+    if (u_coupled(s)) {
+      // out[l] = sum_u sum_x bA[l/Gin][u] bL[l][PL x] bU[u][PU x] w(x) P[u] Pr[PD x][PR x * Gout + g_u]
+      const int Gout = tb_dims_host(s, D_GOUT);
+      pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
+      SPG_TRY(zero_env(out));
+      for (int u = 0; u < DU; ++u) {
+        const int g = g_of(s, u);
+        xgemm(s, d, 1, chiA, chiBl, chiAr, P + (size_t)u * chiA * chiAr, XOff{0, 0, 0, 0}, chiAr, 1,
+              Pp + (size_t)g * chiBl * chiAr,
+              XOff{4, 2, (long long)DR * chiBl * chiAr, (long long)Gout * chiBl * chiAr}, 1, chiAr, G);
+        coef(s, 4, DL, u, g);
+        gemm2<T>(false, false, DL, chiA * chiBl, d, Cf, d, G, chiA * chiBl, Ctmp, chiA * chiBl, st);
+        axpy(out, Ctmp, (size_t)DL * chiA * chiBl);
+      }
+      count_launches("k_scale_max", st);
+      k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, logacc);
+      return cudaGetLastError();
+    }
     phi_prime(s, P, DU, chiA, chiAr);
     pairs_right(s, B, p, chiBl, chiBr, Renv, chiAr);
     // Y_x[a][b] = sum_a' F[PU x][a][a'] Pr[PD x][PR x][b][a']
@@ -309,6 +394,24 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     const int DR = tb_dims_host(s, 1), NL = tb_dims_host(s, 4), d = hd_states(s);
     const T* B = site_ptr(row + 1, j);
     const T* P = site_ptr(row, j);
+    if (u_coupled(s)) {
+      // out[r] = sum_u sum_x [PR x * Gout + g_u == r] bU[u][PU x] w(x) P[u]^T Ql_u[PL x][PD x]
+      SPG_TRY(zero_env(out));
+      for (int u = 0; u < DU; ++u) {
+        const int g = g_of(s, u);
+        left_prime_u(s, Lenv, chiA, chiBl, u);
+        xgemm(s, NL * p, p, chiA, chiBr, chiBl, Lp, XOff{5, 0, (long long)chiA * chiBl, 0}, chiBl, 1, B,
+              XOff{6, 0, (long long)chiBl * chiBr, 0}, chiBr, 1, Pp);
+        xgemm(s, d, 1, chiAr, chiBr, chiA, P + (size_t)u * chiA * chiAr, XOff{0, 0, 0, 0}, 1, chiAr, Pp,
+              XOff{1, 4, (long long)p * chiA * chiBr, (long long)chiA * chiBr}, chiBr, 1, G);
+        coef(s, 5, DR, u, g);
+        gemm2<T>(false, false, DR, chiAr * chiBr, d, Cf, d, G, chiAr * chiBr, Ctmp, chiAr * chiBr, st);
+        axpy(out, Ctmp, (size_t)DR * chiAr * chiBr);
+      }
+      count_launches("k_scale_max", st);
+      k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, junk);
+      return cudaGetLastError();
+    }
     left_prime(s, Lenv, chiA, chiBl);
     // Ql[h][s'][a][b'] = sum_b Lp[h][a][b] B[s'][b][b']
     xgemm(s, NL * p, p, chiA, chiBr, chiBl, Lp, XOff{5, 0, (long long)chiA * chiBl, 0}, chiBl, 1, B,
@@ -375,13 +478,13 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   return cudaGetLastError();
 }
 
-template size_t sweep_work_elems<double>(int, int);
-template size_t sweep_work_elems<float>(int, int);
+template size_t sweep_work_elems<double>(int, int, int);
+template size_t sweep_work_elems<float>(int, int, int);
 template cudaError_t variational_sweeps<double>(const DevTables&, DevWeights<double>, DevMPS<double>, int, int,
-                                                const int*, const int*, const int*, int, double*, double*,
-                                                cudaStream_t);
+                                                const int*, const int*, const int*, const uint8_t*, int, double*,
+                                                double*, cudaStream_t);
 template cudaError_t variational_sweeps<float>(const DevTables&, DevWeights<float>, DevMPS<float>, int, int,
-                                               const int*, const int*, const int*, int, float*, double*,
-                                               cudaStream_t);
+                                               const int*, const int*, const int*, const uint8_t*, int, float*,
+                                               double*, cudaStream_t);
 
 }  // namespace spg

@@ -125,11 +125,44 @@ def test_king_solve(spg, ctx, make, beta, chi, beam):
         assert tables.energy(fg, st[k]) == E[k]
 
 
-def test_king_sweeps_rejected(spg, ctx):
-    prob = problem(spg, ctx, I.king_potts(3, 3, 1))
-    with pytest.raises(spg.SpgError) as e:
-        spg.spg_solve(ctx, prob, spg.params(chi=8, num_sweeps=1))
-    assert e.value.code == -7
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("make,beta,chi,sweeps", [
+    (lambda: I.king_potts(4, 3, 2, cols=5), 0.8, 6, 1),
+    (lambda: I.king_potts(3, 3, 1), 1.0, 4, 1),
+    (lambda: I.king_ising(4, 4, 2, 5), 1.0, 8, 2),
+])
+def test_king_variational_sweeps(spg, ctx, make, beta, chi, sweeps, prec):
+    """S4 on a king's graph: sites whose tensor depends on the up index are
+    swept one up index at a time (log Z and teacher-forced conditionals)."""
+    inst = make()
+    fg = fg_of(inst)
+    p = peps.build(fg, beta)
+    ref = boundary.log_partition(p, chi, num_sweeps=sweeps)
+    prob = problem(spg, ctx, inst)
+    prm = spg.params(beta=beta, chi=chi, num_sweeps=sweeps, precision=prec)
+    got = spg.spg_log_partition(ctx, prob, prm)
+    assert abs(got - ref) <= TOL[prec] * max(1.0, abs(ref))
+    bd = boundary.boundary_mpses(p, chi, sweeps)
+    rng = np.random.default_rng(5)
+    for s in sorted({1, fg.cols, fg.cols + 1, fg.n_sites // 2, fg.n_sites - 1}):
+        pre = np.array([[rng.integers(0, d) for d in fg.d[:s]] for _ in range(4)], dtype=np.int64).reshape(4, s)
+        refm = search.debug_marginals(fg, search.Params(beta=beta, chi=chi, num_sweeps=sweeps), s, pre, boundary=bd)
+        gotm = spg.spg_debug_marginals(ctx, prob, prm, s, pre)
+        close(gotm, refm, TOL[prec], None if prec == 0 else LOG_FLOOR)
+
+
+def test_king_solve_with_sweeps(spg, ctx):
+    inst = I.king_potts(4, 4, 23, cols=5)
+    fg = fg_of(inst)
+    ref = search.solve(fg, search.Params(beta=1.0, chi=8, beam=128, num_sweeps=1))
+    prob = problem(spg, ctx, inst)
+    res = spg.spg_solve(ctx, prob, spg.params(beta=1.0, chi=8, beam=128, num_sweeps=1))
+    st, E, lp = res.get()
+    assert res.info()["error_flags"] == 0
+    if ref.near_ties == 0 and res.info()["near_ties"] == 0:
+        np.testing.assert_array_equal(E, ref.energies)
+        np.testing.assert_array_equal(st.astype(np.int64), ref.states)
+    assert E[0] == ref.energies[0]
 
 
 @pytest.mark.parametrize("L,chi,beam", [(6, 32, 256), (8, 64, 512)])
