@@ -76,7 +76,7 @@ __device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { retur
 // so are the G current environments when the bond is small (use_rn).
 template <typename T>
 __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int row, DevSearch ds,
-                             DevBeamT<T> bt, int cur, int G, int use_smem, int use_rn) {
+                             DevBeamT<T> bt, int cur, int G, int use_smem, int use_rn, int use_t) {
   const int nb = ds.n_beam[cur];
   const int b0 = blockIdx.x * G;
   if (b0 >= nb) return;
@@ -88,6 +88,7 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
   T* sbL = red + 32;                               // [rs][MAXP]
   T* Rn = sbL + (size_t)rs * MAXP;                 // [G][chi*rs] (use_rn)
   T* Bs = Rn + (use_rn ? (size_t)G * MAXCHI * rs : 0);  // staged site (use_smem)
+  T* Tp = Bs + mps.site_stride;                    // [p][DR][chiL] products (use_t)
   __shared__ T sw[MAXS], sbU[256], sbA[256];
   __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
   __shared__ int16_t sxs[MAXS];
@@ -145,6 +146,41 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
       const int gu = row > 0 ? tb.gD[(size_t)(s - cols) * MAXP + u] : 0;
       const T* Rg = use_rn ? Rn + (size_t)g * renv : bt.R + ((size_t)b * (cols + 1) + j + 1) * renv;
       // Y[h][a] = sum_{x in group h} w(x) bU[u][PU x] sum_a' A[PD x][a][a'] Rg[a'][PR x * Gout + gu]
+      if (use_t) {
+        // first every product Tp[pd][r][a] = sum_a' A[pd][a][a'] Rg[a'][r] (r < DR),
+        // four consecutive a per thread (one R load per four multiply-adds),
+        // then the weighted sums over the states of each class from Tp
+        const int DR = dim_of(tb, s, D_DR);
+        const int na4 = (chiL + 3) >> 2;
+        for (int e = tid; e < p * DR * na4; e += nt) {
+          const int a0 = (e % na4) * 4, r = (e / na4) % DR, pd = e / (na4 * DR);
+          const T* ab = Bs + (size_t)pd * chiR * chiL + a0;
+          T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
+          for (int ap = 0; ap < chiR; ++ap) {
+            const T rv = Rg[(size_t)ap * rs + r];
+            const T* av = ab + (size_t)ap * chiL;
+            t0 += av[0] * rv;
+            if (a0 + 1 < chiL) t1 += av[1] * rv;
+            if (a0 + 2 < chiL) t2 += av[2] * rv;
+            if (a0 + 3 < chiL) t3 += av[3] * rv;
+          }
+          T* tp = Tp + ((size_t)pd * DR + r) * chiL + a0;
+          tp[0] = t0;
+          if (a0 + 1 < chiL) tp[1] = t1;
+          if (a0 + 2 < chiL) tp[2] = t2;
+          if (a0 + 3 < chiL) tp[3] = t3;
+        }
+        __syncthreads();
+        for (int e = tid; e < NL * chiL; e += nt) {
+          const int h = e / chiL, a = e % chiL;
+          T acc = T(0);
+          for (int q = soff[h]; q < soff[h + 1]; ++q) {
+            const int x = sxs[q];
+            acc += sw[x] * sbU[u * 16 + sPU[x]] * Tp[((size_t)sPD[x] * DR + sPR[x] * Gout + gu) * chiL + a];
+          }
+          Y[h * MAXCHI + a] = acc;
+        }
+      } else
       for (int e = tid; e < NL * chiL; e += nt) {
         const int h = e / chiL, a = e % chiL;
         T acc = T(0);
@@ -1036,11 +1072,15 @@ cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> m
                                    (use_rn ? (size_t)G * MAXCHI * bt.rs : 0));
   const size_t full = base + sizeof(T) * mps.site_stride;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
+  // the per-(class pair) products, when they fit beside the staged site
+  const size_t chi = (size_t)bt.chi;
+  const size_t tbytes = sizeof(T) * (size_t)MAXP * bt.rs * chi;
+  const int use_t = (use_smem && full + tbytes <= 200 * 1024) ? 1 : 0;
+  const size_t smem = use_t ? full + tbytes : (use_smem ? full : base);
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_right_envs", st);
-  k_right_envs<T><<<(ds.cap + G - 1) / G, 512, use_smem ? full : base, st>>>(tb, wt, mps, row, ds, bt, cur, G,
-                                                                           use_smem, use_rn);
+  k_right_envs<T><<<(ds.cap + G - 1) / G, 512, smem, st>>>(tb, wt, mps, row, ds, bt, cur, G, use_smem, use_rn, use_t);
   return cudaGetLastError();
 }
 
