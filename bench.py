@@ -34,6 +34,13 @@ WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=102
 METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best energy"
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
+# capture of two mid-solve launches of the 16x16 solve (48 x 512 block;
+# dram__bytes_read.sum + dram__bytes_write.sum, mean of the two); a kernel
+# not listed here reports null.
+NCU_TRAFFIC_BYTES = {"k_cgs2_rows": 128640}
+
+
 def make_instance(seed):
     import instances
     return instances.chimera(WORKLOAD["L"], seed, couplings=WORKLOAD["couplings"], h_sigma=WORKLOAD["h_sigma"])
@@ -413,7 +420,7 @@ def main():
     achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
     peaks, src = measured_peaks()
     line["roofline"] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                        "frac": achieved / alu_peak, "traffic": None,
+                        "frac": achieved / alu_peak, "traffic": NCU_TRAFFIC_BYTES.get(name),
                         "peak_source": f"derived: 152 SMs x {'128 FP32' if prec == spg.SPG_MIXED else '2 FP64'} "
                                        f"FMA/clk x 2 x {clk_mhz:.0f} MHz",
                         "share_of_solve": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
