@@ -158,10 +158,15 @@ int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_
 
 /* Batching: solve n independent problems concurrently (instances of uneven
  * size, each with its own parameters prms[i]); every problem is solved
- * exactly as by spg_solve.  The solves run on up to 16 worker streams owned
+ * exactly as by spg_solve.  The solves run on up to 32 worker streams owned
  * by the context (each with its own workspace), enqueued from as many host
  * threads, so that the instances' chains of dependent kernels overlap on the
- * GPU.  out: n result handles, each waited for by spg_result_get.  Returns
+ * GPU.  The streams only overlap when the process has as many hardware work
+ * queues: loading the library sets CUDA_DEVICE_MAX_CONNECTIONS=32 unless it
+ * is already set, which takes effect if the process creates its CUDA
+ * context afterwards (with CUDA's default of 8 queues, more than 8 solves
+ * in flight share queues and serialise).  out: n result handles, each
+ * waited for by spg_result_get.  Returns
  * once everything is enqueued; work enqueued later on the context's stream
  * runs after the batch.  On failure no handle is returned. */
 int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prms,

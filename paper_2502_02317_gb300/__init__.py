@@ -4,6 +4,14 @@ clustered Ising / Potts models (arXiv:2502.02317, SpinGlassPEPS.jl).
 The work runs in ``libspg`` (CUDA, sm_103a) behind the C ABI of
 ``include/spg.h``; this package is its ctypes binding.
 """
+import os as _os
+
+# spg_solve_batch overlaps up to 32 worker streams, which needs as many
+# hardware work queues (CUDA's default is 8); the variable is read when the
+# process creates its CUDA context, so import this package before the first
+# CUDA call for it to apply.  A value set by the user is kept.
+_os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 from ._binding import (SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, Context, Problem, Result, SpgError,
                        lib, params, spg_debug_marginals, spg_log_partition, spg_problem_ising,
                        spg_problem_potts, spg_profile, spg_profile_report, spg_solve, spg_solve_batch, spg_tc_product,

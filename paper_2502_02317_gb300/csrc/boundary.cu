@@ -104,111 +104,232 @@ __host__ __device__ constexpr T qr_tol() {
   return sizeof(T) == 8 ? T(1e-13) : T(1e-5);
 }
 
-// CGS2 core on nvec contiguous vectors of length len (stride ld) in place:
-// per vector two projection passes against the earlier (orthonormal)
-// vectors, then normalisation.  The squared norm is accumulated in the second
-// update and the original norm follows from Pythagoras (||x||^2 = sum r^2 +
-// ||x'||^2), so a vector costs five barriers.  A vector whose remainder falls
-// below rel_tol of its norm is numerically dependent: zeroed, R_kk = 0.
-// R (nvec x nvec, row-major): x_k = sum_{c <= k} R[c][k] q_c.
+// One CGS2 step on vector k of nvec contiguous vectors of length len (stride
+// ld), in place: two projection passes against the (orthonormal) vectors
+// clo .. k-1, then normalisation.  The squared norm is accumulated in the
+// second update and the norm before any projection follows from Pythagoras
+// (||x||^2 = sum r^2 + ||x'||^2, the sum also over the coefficients inter[c *
+// istride] of vectors c < clo that a block step removed earlier), so a vector
+// costs five barriers.  A vector whose remainder falls below rel_tol of its
+// norm is numerically dependent: zeroed, R_kk = 0.  Column k of R (nvec x
+// nvec, row-major; x_k = sum_{c <= k} R[c][k] q_c) is written when Rout is set.
 // Scratch: red >= 64 + 2 * SMAX T.
 template <typename T>
-__device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
+__device__ void cgs2_vec(T* V, int k, int clo, int nvec, int len, int ld, T* Rout, T* red, const T* inter,
+                         int istride) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   T* rc = red + 64;          // coefficients of the current pass [SMAX]
   T* racc = rc + SMAX;       // accumulated coefficients [SMAX]
   const T rel_tol = qr_tol<T>();
-  for (int k = 0; k < nvec; ++k) {
-    T* xk = V + (size_t)k * ld;
-    T part = T(0);
-    for (int pass = 0; pass < 2; ++pass) {
-      // dots <q_c, x_k>: warp w takes c = w, w + nw, ... up to four at a time
-      // (independent accumulators, x_k loaded once per element)
-      for (int c0 = wid; c0 < k; c0 += 4 * nw) {
-        const int c1 = c0 + nw, c2 = c0 + 2 * nw, c3 = c0 + 3 * nw;
-        const T* x0 = V + (size_t)c0 * ld;
-        const T* x1 = V + (size_t)(c1 < k ? c1 : c0) * ld;
-        const T* x2 = V + (size_t)(c2 < k ? c2 : c0) * ld;
-        const T* x3 = V + (size_t)(c3 < k ? c3 : c0) * ld;
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        for (int i = lane; i < len; i += 32) {
-          const T v = xk[i];
-          a0 += x0[i] * v;
-          a1 += x1[i] * v;
-          a2 += x2[i] * v;
-          a3 += x3[i] * v;
-        }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        a3 = warp_sum(a3);
-        if (lane == 0) {
-          rc[c0] = a0;
-          racc[c0] = pass == 0 ? a0 : racc[c0] + a0;
-          if (c1 < k) {
-            rc[c1] = a1;
-            racc[c1] = pass == 0 ? a1 : racc[c1] + a1;
-          }
-          if (c2 < k) {
-            rc[c2] = a2;
-            racc[c2] = pass == 0 ? a2 : racc[c2] + a2;
-          }
-          if (c3 < k) {
-            rc[c3] = a3;
-            racc[c3] = pass == 0 ? a3 : racc[c3] + a3;
-          }
-        }
+  T* xk = V + (size_t)k * ld;
+  T part = T(0);
+  for (int pass = 0; pass < 2; ++pass) {
+    // dots <q_c, x_k>: warp w takes c = clo + w, clo + w + nw, ... up to four
+    // at a time (independent accumulators, x_k loaded once per element)
+    for (int c0 = clo + wid; c0 < k; c0 += 4 * nw) {
+      const int c1 = c0 + nw, c2 = c0 + 2 * nw, c3 = c0 + 3 * nw;
+      const T* x0 = V + (size_t)c0 * ld;
+      const T* x1 = V + (size_t)(c1 < k ? c1 : c0) * ld;
+      const T* x2 = V + (size_t)(c2 < k ? c2 : c0) * ld;
+      const T* x3 = V + (size_t)(c3 < k ? c3 : c0) * ld;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      for (int i = lane; i < len; i += 32) {
+        const T v = xk[i];
+        a0 += x0[i] * v;
+        a1 += x1[i] * v;
+        a2 += x2[i] * v;
+        a3 += x3[i] * v;
       }
-      __syncthreads();
-      for (int i = tid; i < len; i += nt) {
-        T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
-        const T* vp = V + i;
-        int c = 0;
-        for (; c + 3 < k; c += 4) {
-          v0 -= rc[c] * vp[0];
-          v1 -= rc[c + 1] * vp[ld];
-          v2 -= rc[c + 2] * vp[2 * ld];
-          v3 -= rc[c + 3] * vp[3 * ld];
-          vp += 4 * ld;
-        }
-        for (; c < k; ++c, vp += ld) v0 -= rc[c] * vp[0];
-        const T v = (v0 + v1) + (v2 + v3);
-        xk[i] = v;
-        if (pass == 1) part += v * v;
-      }
-      if (k == 0 && pass == 0) {  // no projection for the first vector
-        for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
-        break;
-      }
-      if (pass == 0) __syncthreads();
-    }
-    part = warp_sum(part);
-    if (lane == 0) red[wid] = part;
-    __syncthreads();
-    // one warp combines the partial norms with the projection coefficients
-    // (Pythagoras) and publishes the scale and the diagonal entry
-    if (wid == 0) {
-      T nk2 = lane < nw ? red[lane] : T(0);
-      nk2 = warp_sum(nk2);
-      T r2 = T(0);
-      for (int c = lane; c < k; c += 32) r2 += racc[c] * racc[c];
-      r2 = warp_sum(r2);
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      a3 = warp_sum(a3);
       if (lane == 0) {
-        const T nk = sqrt(nk2);
-        const T n0 = sqrt(nk2 + r2);
-        const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
-        red[40] = dep ? T(0) : T(1) / nk;
-        red[41] = dep ? T(0) : nk;
+        rc[c0] = a0;
+        racc[c0] = pass == 0 ? a0 : racc[c0] + a0;
+        if (c1 < k) {
+          rc[c1] = a1;
+          racc[c1] = pass == 0 ? a1 : racc[c1] + a1;
+        }
+        if (c2 < k) {
+          rc[c2] = a2;
+          racc[c2] = pass == 0 ? a2 : racc[c2] + a2;
+        }
+        if (c3 < k) {
+          rc[c3] = a3;
+          racc[c3] = pass == 0 ? a3 : racc[c3] + a3;
+        }
       }
     }
     __syncthreads();
-    const T inv = red[40];
-    for (int i = tid; i < len; i += nt) xk[i] *= inv;
-    if (Rout)
-      for (int c = tid; c < nvec; c += nt)
-        Rout[(size_t)c * nvec + k] = c < k ? racc[c] : (c == k ? red[41] : T(0));
-    __syncthreads();
+    for (int i = tid; i < len; i += nt) {
+      T v0 = xk[i], v1 = T(0), v2 = T(0), v3 = T(0);
+      const T* vp = V + (size_t)clo * ld + i;
+      int c = clo;
+      for (; c + 3 < k; c += 4) {
+        v0 -= rc[c] * vp[0];
+        v1 -= rc[c + 1] * vp[ld];
+        v2 -= rc[c + 2] * vp[2 * ld];
+        v3 -= rc[c + 3] * vp[3 * ld];
+        vp += 4 * ld;
+      }
+      for (; c < k; ++c, vp += ld) v0 -= rc[c] * vp[0];
+      const T v = (v0 + v1) + (v2 + v3);
+      xk[i] = v;
+      if (pass == 1) part += v * v;
+    }
+    if (k == clo && pass == 0) {  // nothing to project against
+      for (int i = tid; i < len; i += nt) part += xk[i] * xk[i];
+      break;
+    }
+    if (pass == 0) __syncthreads();
+  }
+  part = warp_sum(part);
+  if (lane == 0) red[wid] = part;
+  __syncthreads();
+  // one warp combines the partial norms with the projection coefficients
+  // (Pythagoras) and publishes the scale and the diagonal entry
+  if (wid == 0) {
+    T nk2 = lane < nw ? red[lane] : T(0);
+    nk2 = warp_sum(nk2);
+    T r2 = T(0);
+    for (int c = clo + lane; c < k; c += 32) r2 += racc[c] * racc[c];
+    for (int c = lane; c < clo; c += 32) r2 += inter[(size_t)c * istride] * inter[(size_t)c * istride];
+    r2 = warp_sum(r2);
+    if (lane == 0) {
+      const T nk = sqrt(nk2);
+      const T n0 = sqrt(nk2 + r2);
+      const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+      red[40] = dep ? T(0) : T(1) / nk;
+      red[41] = dep ? T(0) : nk;
+    }
+  }
+  __syncthreads();
+  const T inv = red[40];
+  for (int i = tid; i < len; i += nt) xk[i] *= inv;
+  if (Rout)
+    for (int c = tid; c < nvec; c += nt)
+      Rout[(size_t)c * nvec + k] =
+          c < clo ? inter[(size_t)c * istride] : (c < k ? racc[c] : (c == k ? red[41] : T(0)));
+  __syncthreads();
+}
+
+// CGS2 on nvec contiguous vectors of length len (stride ld) in place, one
+// vector at a time (cgs2_vec against all earlier vectors).
+template <typename T>
+__device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
+  for (int k = 0; k < nvec; ++k) cgs2_vec(V, k, 0, nvec, len, ld, Rout, red, (const T*)nullptr, 0);
+}
+
+// Block Gram-Schmidt: panels of QR_PB vectors.  A panel is first projected
+// twice against all earlier panels at once (bgs_project), then
+// orthonormalised vector by vector inside the panel (cgs2_vec), which only
+// projects against the panel's earlier vectors.  The same two-pass
+// projections as cgs2_core, grouped so that most of the multiply-adds run as
+// register-tiled panel products instead of one dot per (vector, earlier
+// vector) pair.
+constexpr int QR_PB = 16;
+
+// Tile of the panel Gram step: TC earlier vectors x 4 panel vectors (FP64
+// keeps 2 x 4 to stay inside the register budget of a 1024-thread CTA).
+template <typename T>
+struct BgsTile {
+  static constexpr int TC = sizeof(T) == 8 ? 2 : 4;
+  static constexpr int NV = TC * 4;
+};
+
+// One projection pass of panel k0 .. k0+b-1 against vectors 0 .. k0-1:
+// C[c][j] = <q_c, x_{k0+j}> (one warp per tile of (c, j), entries strided
+// over the lanes, the tile's partial sums reduced by a transposed butterfly:
+// every shuffle halves the values a lane holds), Racc[c][j] (+)= C[c][j],
+// then x_{k0+j} -= sum_c C[c][j] q_c (one thread per entry, the panel's
+// vectors in registers).  Cs, Racc: [SMAX][QR_PB].
+template <typename T>
+__device__ void bgs_project(T* V, int k0, int b, int len, int ld, T* Cs, T* Racc, bool first) {
+  constexpr int TC = BgsTile<T>::TC, NV = BgsTile<T>::NV;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int tc = (k0 + TC - 1) / TC, tj = (b + 3) >> 2;
+  for (int t = wid; t < tc * tj; t += nw) {
+    const int c0 = (t / tj) * TC, j0 = (t % tj) * 4;
+    int qo[TC], xo[4];
+#pragma unroll
+    for (int u = 0; u < TC; ++u) qo[u] = min(c0 + u, k0 - 1) * ld;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) xo[w] = (k0 + min(j0 + w, b - 1)) * ld;
+    T a[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a[v] = T(0);
+    for (int i = lane; i < len; i += 32) {
+      T qv[TC], xv[4];
+#pragma unroll
+      for (int u = 0; u < TC; ++u) qv[u] = V[qo[u] + i];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) xv[w] = V[xo[w] + i];
+#pragma unroll
+      for (int u = 0; u < TC; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) a[u * 4 + w] += qv[u] * xv[w];
+    }
+    // transposed butterfly: at lane bit B the lane with the bit clear keeps
+    // the lower half of its values and receives the partner's lower half; the
+    // one with the bit set keeps and receives the upper half
+    constexpr int stages = NV == 16 ? 4 : 3;
+    int o = 0;
+#pragma unroll
+    for (int stg = 0; stg < stages; ++stg) {
+      const int h = NV >> (stg + 1), bit = 16 >> stg;
+      const bool up = (lane & bit) != 0;
+#pragma unroll
+      for (int v = 0; v < h; ++v) {
+        const T send = up ? a[v] : a[v + h];
+        const T keep = up ? a[v + h] : a[v];
+        a[v] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+      }
+      if (up) o += h;
+    }
+    // lanes that differ only in the bits below the last stage hold the same
+    // output: sum them
+    constexpr int rest = 32 / NV;  // 2 (NV 16) or 4 (NV 8)
+#pragma unroll
+    for (int m = rest / 2; m >= 1; m >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], m);
+    const int c = c0 + o / 4, j = j0 + (o & 3);
+    if ((lane & (rest - 1)) == 0 && c < k0 && j < b) {
+      Cs[c * QR_PB + j] = a[0];
+      Racc[c * QR_PB + j] = first ? a[0] : Racc[c * QR_PB + j] + a[0];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < len; i += nt) {
+    T acc[QR_PB];
+#pragma unroll
+    for (int j = 0; j < QR_PB; ++j) acc[j] = j < b ? V[(k0 + j) * ld + i] : T(0);
+    for (int c = 0; c < k0; ++c) {
+      const T qv = V[c * ld + i];
+      const T* cr = Cs + c * QR_PB;
+#pragma unroll
+      for (int j = 0; j < QR_PB; ++j) acc[j] -= cr[j] * qv;
+    }
+#pragma unroll
+    for (int j = 0; j < QR_PB; ++j)
+      if (j < b) V[(k0 + j) * ld + i] = acc[j];
+  }
+  __syncthreads();
+}
+
+// Scratch: red (64 + 2 SMAX), Cs and Racc (SMAX * QR_PB each).  Offsets into
+// V are int: nvec * ld stays below 2^31 for every caller (staged blocks and
+// zipper blocks of at most SMAX vectors).
+template <typename T>
+__device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* Cs, T* Racc) {
+  for (int k0 = 0; k0 < nvec; k0 += QR_PB) {
+    const int b = min(QR_PB, nvec - k0);
+    if (k0 > 0) {
+      bgs_project(V, k0, b, len, ld, Cs, Racc, true);
+      bgs_project(V, k0, b, len, ld, Cs, Racc, false);
+    }
+    for (int j = 0; j < b; ++j) cgs2_vec(V, k0 + j, k0, nvec, len, ld, Rout, red, Racc + j, QR_PB);
   }
 }
 
@@ -217,16 +338,18 @@ __device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
 // shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_core:
 // x_k = sum_{c <= k} R[c][k] q_c.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
+__global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
-  T* V = use_smem ? red + 64 + 2 * SMAX : X;
+  T* Cs = red + 64 + 2 * SMAX;              // SMAX * QR_PB
+  T* Racc = Cs + SMAX * QR_PB;              // SMAX * QR_PB
+  T* V = use_smem ? Racc + SMAX * QR_PB : X;
   const int vld = use_smem ? len : ld;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
   __syncthreads();
-  cgs2_core(V, nvec, len, vld, Rout, red);
+  bcgs2_core(V, nvec, len, vld, Rout, red, Cs, Racc);
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
 }
@@ -872,13 +995,14 @@ static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
 
 template <typename T>
 static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
-  const size_t base = sizeof(T) * (64 + 2 * SMAX);
+  const size_t base = sizeof(T) * (64 + 2 * SMAX + 2 * SMAX * QR_PB);
   const size_t full = base + sizeof(T) * (size_t)nvec * len;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
-  // one thread per element when the vectors are short, at least 4 warps
-  const int threads = std::max(128, std::min(1024, (len + 31) / 32 * 32));
+  // one thread per element up to 512 (the register budget of the panel
+  // products), at least 4 warps
+  const int threads = std::max(128, std::min(512, (len + 31) / 32 * 32));
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
   k_cgs2_rows<T><<<1, threads, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
 }

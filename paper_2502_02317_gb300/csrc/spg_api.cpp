@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -22,6 +23,16 @@
 #include "spg_internal.h"
 
 using namespace spg;
+
+// The worker streams of spg_solve_batch need as many hardware work queues as
+// there are streams in flight; CUDA gives a process 8 unless
+// CUDA_DEVICE_MAX_CONNECTIONS asks for more (up to 32), and streams beyond
+// the queue count share a queue and run one after another.  The variable is
+// read when the process creates its CUDA context, so it is set (unless the
+// user set it) when the library is loaded.
+__attribute__((constructor)) static void spg_default_connections() {
+  setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0);
+}
 
 struct spg_ctx {
   int device = 0;
@@ -1335,7 +1346,7 @@ int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, co
     if (rc) return rc;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
-  const int K = std::min(n, 16);
+  const int K = std::min(n, 32);
   while ((int)ctx->workers.size() < K) {
     spg_ctx* w = nullptr;
     const int rc = spg_create(&w, ctx->device, nullptr);
