@@ -35,10 +35,11 @@ METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best ene
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from an ncu
-# capture of two mid-solve launches of the 16x16 solve (48 x 512 block;
+# capture of two mid-solve launches of the 16x16 solve (48 x 512 block, block
+# Gram-Schmidt kernel;
 # dram__bytes_read.sum + dram__bytes_write.sum, mean of the two); a kernel
 # not listed here reports null.
-NCU_TRAFFIC_BYTES = {"k_cgs2_rows": 128640}
+NCU_TRAFFIC_BYTES = {"k_cgs2_rows": 118400}
 
 
 def make_instance(seed):
