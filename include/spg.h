@@ -100,6 +100,8 @@ int spg_params_default(spg_params* p);
  * (may be NULL: the library creates and owns a non-blocking stream).  The
  * context owns its device workspace, grown on demand and reused. */
 int spg_create(spg_ctx** out, int device, void* cuda_stream);
+/* Problems and results created through a context (including the results of
+ * spg_solve_batch) are destroyed before the context. */
 void spg_destroy(spg_ctx* ctx);
 const char* spg_last_error(const spg_ctx* ctx);
 

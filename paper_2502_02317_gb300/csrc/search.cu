@@ -1171,6 +1171,21 @@ cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+// The GPU's global nanosecond timer at the moment this kernel runs.
+__global__ void k_stamp(unsigned long long* slot) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  if (threadIdx.x == 0) *slot = t;
+}
+}  // namespace
+
+cudaError_t launch_stamp(unsigned long long* slot, cudaStream_t st) {
+  count_launches("k_stamp", st);
+  k_stamp<<<1, 32, 0, st>>>(slot);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
   count_launches("k_reset_beam", st);
   k_reset_beam<<<1, 256, 0, st>>>(ds, cur);

@@ -53,7 +53,7 @@ struct spg_ctx {
     char* arena = nullptr;
     size_t arena_bytes = 0;
     int uses = 0;
-    cudaGraphExec_t boundary = nullptr, search = nullptr;
+    cudaGraphExec_t exec = nullptr;  // the whole solve, one launch
     long long launches = 0;
   };
   std::vector<Graph> graphs;
@@ -91,6 +91,7 @@ struct spg_result {
   // diagnostics copied at the end of the solve
   int* d_diag = nullptr;  // near_ties, err, deg_cuts
   double* d_cand = nullptr;
+  unsigned long long* d_stamp = nullptr;  // GPU timer at start, phase boundary, end (ns)
   float ms_boundary = 0.f, ms_search = 0.f;
   double lognorm = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -726,6 +727,7 @@ struct OutStage {
   int* n;
   int* diag;  // near_ties, err, degenerate cuts, Jacobi sweeps
   double* cand;  // candidates, log-norm of B_1
+  unsigned long long* stamp;  // GPU timer at start, phase boundary, end
 };
 
 size_t out_stage_bytes(const spg_problem* P, int cap) {
@@ -772,10 +774,13 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
 
 // A solve is a fixed sequence of stream operations given the problem, the
 // parameters and the workspace (everything data-dependent lives on the
-// device), so it is captured into two CUDA graphs (boundary phase, search
-// phase) on its second occurrence and replayed from then on: one graph launch
-// instead of tens of thousands of kernel launches from the host.  The first
-// occurrence runs uncaptured (it also performs the one-time kernel set-up).
+// device), so it is captured into one CUDA graph on its second occurrence and
+// replayed from then on: one graph launch instead of tens of thousands of
+// kernel launches from the host.  One graph, not one per phase: a second graph
+// launch on the same stream can hold the host until the first graph has run,
+// which serialises the worker threads of spg_solve_batch.  The phase times
+// come from GPU timer stamps inside the sequence.  The first occurrence runs
+// uncaptured (it also performs the one-time kernel set-up).
 template <typename T>
 int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result* R) {
   cudaStream_t st = ctx->stream;
@@ -796,7 +801,8 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   o.n = ar.get<int>(4);
   o.diag = ar.get<int>(4);
   o.cand = ar.get<double>(2);
-  if (!o.cand) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  o.stamp = ar.get<unsigned long long>(4);
+  if (!o.stamp) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
   // plan dims: host data, uploaded outside any capture
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
@@ -808,87 +814,65 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
       g = &e;
   const bool profiling = kernel_profile().on;
   const long long l0 = thread_launches();
-  CK(cudaEventRecord(R->ev[0], st));
+  // the whole solve: stamp, boundary phase, stamp, search phase, stamp
+  auto enqueue_all = [&]() -> int {
+    CK(launch_stamp(o.stamp + 0, st));
+    int r2 = enqueue_boundary<T>(ctx, P, prm, pl, bb);
+    if (r2) return r2;
+    if (profiling) profile_mark(st);
+    CK(launch_stamp(o.stamp + 1, st));
+    if ((r2 = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return r2;
+    if (profiling) profile_mark(st);
+    CK(launch_stamp(o.stamp + 2, st));
+    return SPG_OK;
+  };
+  // capture into an executable graph (nullptr on failure, rc set)
+  auto capture = [&](cudaGraphExec_t* ex) -> int {
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int r2 = enqueue_all();
+    const cudaError_t e1 = cudaStreamEndCapture(st, &gr);
+    if (r2 || e1 != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return r2 ? r2 : fail(ctx, SPG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e2 != cudaSuccess) return fail(ctx, SPG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    return SPG_OK;
+  };
   if (profiling) {
     // captured with the profiler's per-kernel event records as graph nodes,
     // so that the times between them are device times without host gaps
-    cudaGraph_t gb = nullptr, gs = nullptr;
-    cudaGraphExec_t eb = nullptr, es = nullptr;
-    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (ok) {
-      rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
-      profile_mark(st);
-      ok = cudaStreamEndCapture(st, &gb) == cudaSuccess && rc == SPG_OK;
-    }
-    if (ok && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      rc = enqueue_search<T>(ctx, P, prm, bb, sb, o);
-      profile_mark(st);
-      ok = cudaStreamEndCapture(st, &gs) == cudaSuccess && rc == SPG_OK;
-    } else {
-      ok = false;
-    }
-    ok = ok && cudaGraphInstantiate(&eb, gb, 0) == cudaSuccess && cudaGraphInstantiate(&es, gs, 0) == cudaSuccess;
-    if (gb) cudaGraphDestroy(gb);
-    if (gs) cudaGraphDestroy(gs);
-    if (!ok) return fail(ctx, SPG_ECUDA, "profiled capture failed");
-    CK(cudaGraphLaunch(eb, st));
-    CK(cudaEventRecord(R->ev[1], st));
-    CK(cudaGraphLaunch(es, st));
+    cudaGraphExec_t ex = nullptr;
+    if ((rc = capture(&ex))) return rc;
+    CK(cudaGraphLaunch(ex, st));
     R->launches = thread_launches() - l0;
     CK(cudaStreamSynchronize(st));
-    cudaGraphExecDestroy(eb);
-    cudaGraphExecDestroy(es);
-  } else if (g && g->boundary) {
-    CK(cudaGraphLaunch(g->boundary, st));
-    CK(cudaEventRecord(R->ev[1], st));
-    CK(cudaGraphLaunch(g->search, st));
+    cudaGraphExecDestroy(ex);
+  } else if (g && g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
     R->launches = g->launches;
   } else if (g) {
-    cudaGraph_t gb = nullptr, gs = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_boundary<T>(ctx, P, prm, pl, bb);
-    cudaError_t e1 = cudaStreamEndCapture(st, &gb);
-    if (rc || e1 != cudaSuccess) {
-      if (gb) cudaGraphDestroy(gb);
-      return rc ? rc : fail(ctx, SPG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
-    }
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_search<T>(ctx, P, prm, bb, sb, o);
-    e1 = cudaStreamEndCapture(st, &gs);
-    if (rc || e1 != cudaSuccess) {
-      cudaGraphDestroy(gb);
-      if (gs) cudaGraphDestroy(gs);
-      return rc ? rc : fail(ctx, SPG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
-    }
-    CK(cudaGraphInstantiate(&g->boundary, gb, 0));
-    CK(cudaGraphInstantiate(&g->search, gs, 0));
-    cudaGraphDestroy(gb);
-    cudaGraphDestroy(gs);
+    if ((rc = capture(&g->exec))) return rc;
     g->launches = thread_launches() - l0;
-    CK(cudaGraphLaunch(g->boundary, st));
-    CK(cudaEventRecord(R->ev[1], st));
-    CK(cudaGraphLaunch(g->search, st));
+    CK(cudaGraphLaunch(g->exec, st));
     R->launches = g->launches;
   } else {
-    if ((rc = enqueue_boundary<T>(ctx, P, prm, pl, bb))) return rc;
-    CK(cudaEventRecord(R->ev[1], st));
-    if ((rc = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return rc;
+    if ((rc = enqueue_all())) return rc;
     R->launches = thread_launches() - l0;
-    if (!g) {
-      if (ctx->graphs.size() >= 8) {  // keep the most recent entries
-        auto& old = ctx->graphs.front();
-        if (old.boundary) cudaGraphExecDestroy(old.boundary);
-        if (old.search) cudaGraphExecDestroy(old.search);
-        ctx->graphs.erase(ctx->graphs.begin());
-      }
-      spg_ctx::Graph ne;
-      ne.problem = P;
-      ne.prm = *prm;
-      ne.tsize = (int)sizeof(T);
-      ne.arena = ctx->arena;
-      ne.arena_bytes = ctx->arena_bytes;
-      ctx->graphs.push_back(ne);
+    if (ctx->graphs.size() >= 8) {  // keep the most recent entries
+      auto& old = ctx->graphs.front();
+      if (old.exec) cudaGraphExecDestroy(old.exec);
+      ctx->graphs.erase(ctx->graphs.begin());
     }
+    spg_ctx::Graph ne;
+    ne.problem = P;
+    ne.prm = *prm;
+    ne.tsize = (int)sizeof(T);
+    ne.arena = ctx->arena;
+    ne.arena_bytes = ctx->arena_bytes;
+    ctx->graphs.push_back(ne);
   }
   // staged outputs into the result's own buffers
   CK(cudaMemcpyAsync(R->d_states, o.states, sizeof(uint16_t) * (size_t)cap * P->n, cudaMemcpyDeviceToDevice, st));
@@ -897,6 +881,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   CK(cudaMemcpyAsync(R->d_n, o.n, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_diag, o.diag, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_cand, o.cand, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_stamp, o.stamp, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(R->ev[2], st));
   return SPG_OK;
 }
@@ -906,8 +891,7 @@ void drop_graphs(spg_ctx* ctx, const void* problem) {
     for (size_t k = 0; k < c->graphs.size();) {
       auto& e = c->graphs[k];
       if (problem == nullptr || e.problem == problem) {
-        if (e.boundary) cudaGraphExecDestroy(e.boundary);
-        if (e.search) cudaGraphExecDestroy(e.search);
+        if (e.exec) cudaGraphExecDestroy(e.exec);
         c->graphs.erase(c->graphs.begin() + k);
       } else {
         ++k;
@@ -1319,14 +1303,16 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
     spg_result_destroy(R);
     return code;
   };
-  for (int k = 0; k < 3; ++k)
-    if (cudaEventCreate(&R->ev[k]) != cudaSuccess) return cleanup(fail(ctx, SPG_ECUDA, "event create"));
+  // completion event (the phase times come from GPU timer stamps)
+  if (cudaEventCreateWithFlags(&R->ev[2], cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(ctx, SPG_ECUDA, "event create"));
   if (cudaMallocAsync((void**)&R->d_states, sizeof(uint16_t) * (size_t)R->cap * R->N, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_E, sizeof(int64_t) * R->cap, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_logp, sizeof(double) * R->cap, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_n, sizeof(int) * 4, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_diag, sizeof(int) * 4, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess) {
+      cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_stamp, sizeof(unsigned long long) * 3, st) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
   }
@@ -1393,8 +1379,10 @@ static int fetch(spg_result* R) {
   CK(cudaSetDevice(ctx->device));
   CK(cudaEventSynchronize(R->ev[2]));
   CK(cudaMemcpy(&R->n, R->d_n, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaEventElapsedTime(&R->ms_boundary, R->ev[0], R->ev[1]));
-  CK(cudaEventElapsedTime(&R->ms_search, R->ev[1], R->ev[2]));
+  unsigned long long ts[3];
+  CK(cudaMemcpy(ts, R->d_stamp, sizeof(ts), cudaMemcpyDeviceToHost));
+  R->ms_boundary = (float)((double)(ts[1] - ts[0]) * 1e-6);
+  R->ms_search = (float)((double)(ts[2] - ts[1]) * 1e-6);
   R->fetched = true;
   return SPG_OK;
 }
@@ -1448,14 +1436,16 @@ int spg_result_info(spg_result* R, spg_info* info) {
 void spg_result_destroy(spg_result* R) {
   if (!R) return;
   cudaSetDevice(R->ctx->device);
+  // stream-ordered frees: after the solve that wrote the buffers, without
+  // holding the host (a worker stream may already run the next batch)
   cudaStream_t st = R->ctx->stream;
-  cudaStreamSynchronize(st);
   if (R->d_states) cudaFreeAsync(R->d_states, st);
   if (R->d_E) cudaFreeAsync(R->d_E, st);
   if (R->d_logp) cudaFreeAsync(R->d_logp, st);
   if (R->d_n) cudaFreeAsync(R->d_n, st);
   if (R->d_diag) cudaFreeAsync(R->d_diag, st);
   if (R->d_cand) cudaFreeAsync(R->d_cand, st);
+  if (R->d_stamp) cudaFreeAsync(R->d_stamp, st);
   for (int k = 0; k < 3; ++k)
     if (R->ev[k]) cudaEventDestroy(R->ev[k]);
   cudaGetLastError();

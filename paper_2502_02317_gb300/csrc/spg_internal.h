@@ -229,6 +229,8 @@ class TcGemm {
   float *Mh_, *Ml_, *MTh_, *MTl_, *Bh_, *Bl_, *part_;
 };
 cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st);
+// Writes the GPU's global nanosecond timer into *slot when the stream reaches it.
+cudaError_t launch_stamp(unsigned long long* slot, cudaStream_t st);
 size_t truncated_svd_work(int m, int n, int keep);
 // Offset (elements) of the sigma array inside the truncation's work buffer.
 size_t truncated_svd_sigma_offset(int m, int n, int keep);
