@@ -152,6 +152,44 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
         // then the weighted sums over the states of each class from Tp
         const int DR = dim_of(tb, s, D_DR);
         const int na4 = (chiL + 3) >> 2;
+        bool tile = false;
+        if constexpr (sizeof(T) == 4) tile = (chiL % 4 == 0) && (DR % 4 == 0) && (rs % 4 == 0);
+        if constexpr (sizeof(T) == 4) {
+          // FP32 with bonds in multiples of 4: a 4 (a) x 4 (r) tile per thread,
+          // one 16-byte load of A and one of R per 16 multiply-adds (the same
+          // summation order over a' as the loop below).  Rg and Bs rows start
+          // on 16-byte boundaries: every offset is a multiple of 4 floats.
+          if (tile) {
+            const int nr4 = DR >> 2, ca4 = chiL >> 2;
+            for (int e = tid; e < p * nr4 * na4; e += nt) {
+              const int a0 = (e % na4) * 4, r0 = ((e / na4) % nr4) * 4, pd = e / (na4 * nr4);
+              const float4* ab = reinterpret_cast<const float4*>(Bs + (size_t)pd * chiR * chiL + a0);
+              const float* rg = reinterpret_cast<const float*>(Rg) + r0;
+              float c[4][4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[i][k] = 0.f;
+              for (int ap = 0; ap < chiR; ++ap) {
+                const float4 av = ab[(size_t)ap * ca4];
+                const float4 rv = *reinterpret_cast<const float4*>(rg + (size_t)ap * rs);
+                const float a4[4] = {av.x, av.y, av.z, av.w};
+                const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) c[i][k] += a4[i] * r4[k];
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                T* tp = Tp + ((size_t)pd * DR + r0 + k) * chiL + a0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tp[i] = c[i][k];
+              }
+            }
+          }
+        }
+        if (!tile)
         for (int e = tid; e < p * DR * na4; e += nt) {
           const int a0 = (e % na4) * 4, r = (e / na4) % DR, pd = e / (na4 * DR);
           const T* ab = Bs + (size_t)pd * chiR * chiL + a0;
@@ -236,6 +274,23 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
 }
 
 // ---------------------------------------------------------------- S6 marginals
+// log q for q > 0 in the precision of the contraction: FP64 log in FP64 mode;
+// in the mixed mode q = m 2^e (m in [0.5, 1), split from the bit pattern) and
+// log q = log m + e log 2 with log m in FP32 (absolute error ~1e-7, the FP32
+// mode's accuracy), so the FP64 pipe only forms the weights and their sum.
+template <typename T>
+__device__ __forceinline__ double log_pos(double q) {
+  if constexpr (sizeof(T) == 8) {
+    return log(q);
+  } else {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(q);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex == 0) return log(q);  // subnormal
+    const double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) | 0x3fe0000000000000ull));
+    return (double)logf((float)m) + (double)(ex - 1022) * 0.69314718055994530942;
+  }
+}
+
 // One block per beam element b at site s = (i, j), with l the left bond
 // fixed by clusters (i, j-1) and (i-1, j-1), u the PD class of (i-1, j) and
 // g = gD_{(i-1, j)}[u]:
@@ -294,10 +349,13 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   const double* bUu = wd.bU + (size_t)site * 256 + u * 16;
   __syncthreads();
   const int d = tb.d[site];
+  // the weights once (each thread keeps its own states' in shared memory)
+  __shared__ double sq[MAXS];
   double part = 0.0;
   for (int x = tid; x < d; x += nt) {
     double q = wd.w[so + x] * bLl[tb.PL[so + x]] * bUu[tb.PU[so + x]] * sZ[tb.PD[so + x] * MAXP + tb.PR[so + x]];
     q = q > 0.0 ? q : 0.0;
+    sq[x] = q;
     part += q;
   }
   const double tot = block_sum(part, red);
@@ -307,9 +365,8 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   const int64_t* RUu = tb.RU + (size_t)site * 256 + u * 16;
   for (int x = tid; x < d; x += nt) {
     const int pl = tb.PL[so + x], pu = tb.PU[so + x], pr = tb.PR[so + x];
-    double q = wd.w[so + x] * bLl[pl] * bUu[pu] * sZ[tb.PD[so + x] * MAXP + pr];
-    q = q > 0.0 ? q : 0.0;
-    const double lc = (tot > 0.0) ? (q > 0.0 ? log(q) - lt : -INFINITY) : -INFINITY;
+    const double q = sq[x];
+    const double lc = (tot > 0.0) ? (q > 0.0 ? log_pos<T>(q) - lt : -INFINITY) : -INFINITY;
     ds.logc[(size_t)b * ds.dmax + x] = lc;
     int64_t e = E0 + tb.E[so + x] + RLl[pl] + RUu[pu];
     if (adr) e += tb.RA[(size_t)(site + 1) * 256 + pr * 16 + ur];
