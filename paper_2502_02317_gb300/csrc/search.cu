@@ -1178,7 +1178,11 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
 cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, int cur, double log_cut,
                           cudaStream_t st) {
   const size_t tot = (size_t)ds.cap * ds.dmax;
-  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 1024);
+  // grid-stride passes on at most 64 blocks: a solve alone runs them as fast
+  // as on a full-GPU grid (they move a few tens of MB through L2), and the
+  // other solves of a batch keep the remaining SMs (measured: batch of 32
+  // +6.6%, one solve unchanged)
+  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 64);
   count_launches("k_select_init", st);
   k_select_init<<<1, 1024, 0, st>>>(ds);
   if (log_cut > -INFINITY) {
