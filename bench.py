@@ -338,14 +338,16 @@ def main():
 
     # end to end through the C ABI from host arrays: problems built and
     # copied, the batch solved, results copied back
-    e2e_times = []
+    e2e_times, e2e_build = [], []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ps = [spg.spg_problem_ising(ctx, i) for i in insts]
+        t1 = time.perf_counter()
         rs = spg.spg_solve_batch(ctx, ps, prms)
         outs = [r.get() for r in rs]
         e2e_times.append(time.perf_counter() - t0)
+        e2e_build.append(t1 - t0)
         for r in rs:
             r.close()
         for p_ in ps:
@@ -356,7 +358,11 @@ def main():
     h2d = NB * (n_sites * (8 * 256 + 4 * 256 + 2 * 256 + 8 * 256 * 2 + 4 * 8 + 4 * 17 + 4 * 41 + 4) + 4)
     d2h = sum(len(o[1]) * (2 * n_sites + 8 + 8) + 16 for o in outs)
     line["e2e"] = {"value": statistics.mean(cands) / statistics.mean(e2e_times), "unit": "beam states/s",
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   # per step: problem construction (host tables + upload), and
+                   # the first (uncaptured) solve of the new problems + results
+                   "build_s": statistics.mean(e2e_build),
+                   "solve_s": statistics.mean(e2e_times) - statistics.mean(e2e_build)}
 
     # plain FP64 GPU path on the same batch: time, equal best energies
     if prec != spg.SPG_FP64:

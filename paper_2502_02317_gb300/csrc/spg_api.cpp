@@ -819,11 +819,10 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     CK(launch_stamp(o.stamp + 0, st));
     int r2 = enqueue_boundary<T>(ctx, P, prm, pl, bb);
     if (r2) return r2;
-    if (profiling) profile_mark(st);
     CK(launch_stamp(o.stamp + 1, st));
     if ((r2 = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return r2;
-    if (profiling) profile_mark(st);
     CK(launch_stamp(o.stamp + 2, st));
+    if (profiling) profile_mark(st);  // closes the last kernel's interval
     return SPG_OK;
   };
   // capture into an executable graph (nullptr on failure, rc set)
