@@ -81,8 +81,9 @@ typedef struct {
   int32_t near_ties;       /* prune steps whose cut fell within 1e-9 in log p */
   int32_t degenerate_cuts; /* truncations whose cut fell in a degenerate gap */
   int32_t error_flags;     /* device-side checks that failed (0 = none)     */
-  double ms_boundary;      /* device time of the boundary-MPS phase          */
-  double ms_search;        /* device time of the search phase                */
+  double ms_boundary;      /* device time of the boundary-MPS phase (GPU
+                              global timer at the phase's ends)              */
+  double ms_search;        /* device time of the search phase (same timer)   */
   double candidates;       /* sum over sites of (live beam x states)         */
   double boundary_lognorm; /* log-norm of the last boundary MPS built        */
   int64_t kernel_launches; /* CUDA kernels this solve enqueued              */
@@ -155,7 +156,10 @@ int spg_problem_shape(const spg_problem* prob, int32_t* rows, int32_t* cols, int
  * sweeps), then the branch-and-bound search in row-major order keeping
  * `beam` partial states, merging those equal on the boundary of the explored
  * region.  Enqueued on the context's stream; *out is valid at once, its
- * contents after spg_result_get. */
+ * contents after spg_result_get.  The solve is a fixed sequence of kernels
+ * for a given (problem, params, workspace): from its second occurrence on a
+ * context it is captured into one CUDA graph and replayed (the context keeps
+ * the 8 most recent). */
 int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_result** out);
 
 /* Batching: solve n independent problems concurrently (instances of uneven

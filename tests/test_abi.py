@@ -41,3 +41,31 @@ def test_no_device_is_a_loud_error():
     import paper_2502_02317_gb300 as spg
     with pytest.raises(spg.SpgError):
         spg.Context(0)
+
+
+def _run(code, env):
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    return out.stdout.strip()
+
+
+def test_batch_streams_get_their_own_hardware_queues():
+    """spg_solve_batch overlaps up to 32 worker streams, which needs as many
+    hardware work queues: the package and the library both ask for 32 unless
+    the user chose a value."""
+    env = {k: v for k, v in os.environ.items() if k != "CUDA_DEVICE_MAX_CONNECTIONS"}
+    assert _run("import os, paper_2502_02317_gb300; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])", env) == "32"
+    # the library alone, loaded without the package (C environment, read
+    # back through libc)
+    import paper_2502_02317_gb300 as spg  # builds the library if needed
+    lib = spg.lib._name
+    code = ("import ctypes; ctypes.CDLL(%r); "
+            "libc = ctypes.CDLL(None); libc.getenv.restype = ctypes.c_char_p; "
+            "print(libc.getenv(b'CUDA_DEVICE_MAX_CONNECTIONS').decode())") % lib
+    assert _run(code, env) == "32"
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "8"
+    assert _run("import os, paper_2502_02317_gb300; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])", env) == "8"
+    assert _run(code, env) == "8"
