@@ -318,16 +318,211 @@ __device__ void bgs_project(T* V, int k0, int b, int len, int ld, T* Cs, T* Racc
   __syncthreads();
 }
 
+// Gram of the panel k0 .. k0+b-1: G[i][j] = <x_{k0+i}, x_{k0+j}> (i, j < b),
+// one warp per 4 x 4 tile, entries strided over the lanes, the tile's 16
+// partial sums reduced by the transposed butterfly of bgs_project.
+template <typename T>
+__device__ void panel_gram(const T* V, int k0, int b, int len, int ld, T* G) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int tb = (b + 3) >> 2;
+  for (int t = wid; t < tb * tb; t += nw) {
+    const int i0 = (t / tb) * 4, j0 = (t % tb) * 4;
+    int io[4], jo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      io[u] = (k0 + min(i0 + u, b - 1)) * ld;
+      jo[u] = (k0 + min(j0 + u, b - 1)) * ld;
+    }
+    T a[16];
+#pragma unroll
+    for (int v = 0; v < 16; ++v) a[v] = T(0);
+    for (int i = lane; i < len; i += 32) {
+      T xi[4], xj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xi[u] = V[io[u] + i];
+        xj[u] = V[jo[u] + i];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) a[u * 4 + w] += xi[u] * xj[w];
+    }
+    int o = 0;
+#pragma unroll
+    for (int stg = 0; stg < 4; ++stg) {
+      const int h = 16 >> (stg + 1), bit = 16 >> stg;
+      const bool up = (lane & bit) != 0;
+#pragma unroll
+      for (int v = 0; v < h; ++v) {
+        const T send = up ? a[v] : a[v + h];
+        const T keep = up ? a[v + h] : a[v];
+        a[v] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+      }
+      if (up) o += h;
+    }
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    const int i = i0 + o / 4, j = j0 + (o & 3);
+    if ((lane & 1) == 0 && i < b && j < b) G[i * QR_PB + j] = a[0];
+  }
+  __syncthreads();
+}
+
+// Cholesky of the panel's Gram, G = L L^T, by warp 0 (lane r owns row r).  A
+// pivot is dependent (zero column of L, zero vector in Q) when it falls below
+// tol_c^2 of its diagonal entry (the Gram's rounding floor) or below
+// tol_d^2 * ref2[k] (the dependency rule of cgs2_vec against the column's
+// norm before any projection; ref2 == nullptr: not used).  inv[k] = 1 / L_kk
+// or 0.
+template <typename T>
+__device__ void panel_cholesky(const T* G, int b, const T* ref2, T tol_c, T tol_d, T* L, T* inv) {
+  if ((threadIdx.x >> 5) == 0) {
+    const int r = threadIdx.x & 31;
+    for (int e = r; e < QR_PB * QR_PB; e += 32) L[e] = T(0);
+    __syncwarp();
+    for (int k = 0; k < b; ++k) {
+      if (r == k) {
+        T d = G[k * QR_PB + k];
+        for (int c = 0; c < k; ++c) d -= L[k * QR_PB + c] * L[k * QR_PB + c];
+        T thr = tol_c * tol_c * G[k * QR_PB + k];
+        if (ref2) thr = max(thr, tol_d * tol_d * ref2[k]);
+        const bool dep = !(d > thr) || !(G[k * QR_PB + k] > T(0));
+        const T lkk = dep ? T(0) : sqrt(d);
+        L[k * QR_PB + k] = lkk;
+        inv[k] = dep ? T(0) : T(1) / lkk;
+      }
+      __syncwarp();
+      const T ik = inv[k];
+      if (r > k && r < b) {
+        T v = G[r * QR_PB + k];
+        for (int c = 0; c < k; ++c) v -= L[r * QR_PB + c] * L[k * QR_PB + c];
+        L[r * QR_PB + k] = v * ik;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// x_k <- (x_k - sum_{c < k} L[k][c] q_c) * inv[k] for the panel's vectors,
+// one thread per entry with the panel in registers.
+template <typename T>
+__device__ void panel_solve(T* V, int k0, int b, int len, int ld, const T* L, const T* inv) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    T q[QR_PB];
+#pragma unroll
+    for (int k = 0; k < QR_PB; ++k) {
+      if (k < b) {
+        T v = V[(k0 + k) * ld + i];
+#pragma unroll
+        for (int c = 0; c < k; ++c) v -= L[k * QR_PB + c] * q[c];
+        q[k] = v * inv[k];
+        V[(k0 + k) * ld + i] = q[k];
+      } else {
+        q[k] = T(0);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Panel scratch of the Cholesky-QR path: G, L1, L2 (QR_PB^2 each), inv,
+// ref2 (QR_PB each), one flag word.
+template <typename T>
+__host__ __device__ constexpr int chol_scratch_elems() { return 3 * QR_PB * QR_PB + 2 * QR_PB + 4; }
+
+// Orthonormalises panel k0 .. k0+b-1 (already projected against the earlier
+// panels; Racc holds those coefficients) by Cholesky-QR twice: P = Q1 L1^T,
+// Q1 = Q2 L2^T, so R_panel = L2^T L1^T.  The result is accepted when the Gram
+// of Q1 is within 0.1 of the identity and that of Q2 within 1e-5 (over the
+// columns that are not dependent); otherwise the panel is restored from Pc
+// and orthonormalised vector by vector (cgs2_vec).  Writes the panel's
+// columns of R either way.
+template <typename T>
+__device__ void panel_cholqr(T* V, int k0, int b, int nvec, int len, int ld, T* Rout, T* red, T* Racc, T* Pc,
+                             T* cs) {
+  T* G = cs;
+  T* L1 = G + QR_PB * QR_PB;
+  T* L2 = L1 + QR_PB * QR_PB;
+  T* inv = L2 + QR_PB * QR_PB;
+  T* ref2 = inv + QR_PB;
+  int* flag = reinterpret_cast<int*>(ref2 + QR_PB);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T tol_c = T(3e-4), tol_d = qr_tol<T>();
+  for (int e = tid; e < b * len; e += nt) Pc[e] = V[(k0 + e / len) * ld + e % len];
+  panel_gram(V, k0, b, len, ld, G);
+  // squared norm of every column before the projections (Pythagoras)
+  for (int j = tid; j < b; j += nt) {
+    T r2 = G[j * QR_PB + j];
+    for (int c = 0; c < k0; ++c) r2 += Racc[c * QR_PB + j] * Racc[c * QR_PB + j];
+    ref2[j] = r2;
+  }
+  if (tid == 0) *flag = 1;
+  __syncthreads();
+  panel_cholesky(G, b, ref2, tol_c, tol_d, L1, inv);
+  panel_solve(V, k0, b, len, ld, L1, inv);
+  panel_gram(V, k0, b, len, ld, G);
+  for (int e = tid; e < b * b; e += nt) {
+    const int i = e / b, j = e % b;
+    if (L1[i * QR_PB + i] != T(0) && L1[j * QR_PB + j] != T(0) &&
+        !(fabs(G[i * QR_PB + j] - (i == j ? T(1) : T(0))) <= T(0.1)))
+      *flag = 0;
+  }
+  __syncthreads();
+  if (*flag) {
+    panel_cholesky(G, b, (const T*)nullptr, tol_c, tol_d, L2, inv);
+    panel_solve(V, k0, b, len, ld, L2, inv);
+    panel_gram(V, k0, b, len, ld, G);
+    for (int e = tid; e < b * b; e += nt) {
+      const int i = e / b, j = e % b;
+      if (L2[i * QR_PB + i] != T(0) && L2[j * QR_PB + j] != T(0) &&
+          !(fabs(G[i * QR_PB + j] - (i == j ? T(1) : T(0))) <= T(1e-5)))
+        *flag = 0;
+    }
+    __syncthreads();
+  }
+  if (*flag) {
+    // R column k0 + j: the earlier panels' coefficients, then (L2^T L1^T)[c][j]
+    if (Rout)
+      for (int e = tid; e < nvec * b; e += nt) {
+        const int c = e / b, j = e % b;
+        T v = T(0);
+        if (c < k0) {
+          v = Racc[c * QR_PB + j];
+        } else if (c < k0 + b) {
+          const int ci = c - k0;
+          // (L2^T L1^T)[ci][j] = sum_m L2[m][ci] L1[j][m], m from ci to j
+          for (int m = ci; m <= j; ++m) v += L2[m * QR_PB + ci] * L1[j * QR_PB + m];
+        }
+        Rout[(size_t)c * nvec + k0 + j] = v;
+      }
+    __syncthreads();
+    return;
+  }
+  for (int e = tid; e < b * len; e += nt) V[(k0 + e / len) * ld + e % len] = Pc[e];
+  __syncthreads();
+  for (int j = 0; j < b; ++j) cgs2_vec(V, k0 + j, k0, nvec, len, ld, Rout, red, Racc + j, QR_PB);
+}
+
 // Scratch: red (64 + 2 SMAX), Cs and Racc (SMAX * QR_PB each).  Offsets into
 // V are int: nvec * ld stays below 2^31 for every caller (staged blocks and
-// zipper blocks of at most SMAX vectors).
+// zipper blocks of at most SMAX vectors).  With Pc (QR_PB * len) and cs
+// (chol_scratch_elems) given, FP32 panels go through panel_cholqr.
 template <typename T>
-__device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* Cs, T* Racc) {
+__device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* Cs, T* Racc, T* Pc = nullptr,
+                           T* cs = nullptr) {
   for (int k0 = 0; k0 < nvec; k0 += QR_PB) {
     const int b = min(QR_PB, nvec - k0);
     if (k0 > 0) {
       bgs_project(V, k0, b, len, ld, Cs, Racc, true);
       bgs_project(V, k0, b, len, ld, Cs, Racc, false);
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (Pc && cs) {
+        panel_cholqr(V, k0, b, nvec, len, ld, Rout, red, Racc, Pc, cs);
+        continue;
+      }
     }
     for (int j = 0; j < b; ++j) cgs2_vec(V, k0 + j, k0, nvec, len, ld, Rout, red, Racc + j, QR_PB);
   }
@@ -338,18 +533,21 @@ __device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* 
 // shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_core:
 // x_k = sum_{c <= k} R[c][k] q_c.
 template <typename T>
-__global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem) {
+__global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem,
+                                                      int use_chol) {
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* Cs = red + 64 + 2 * SMAX;              // SMAX * QR_PB
   T* Racc = Cs + SMAX * QR_PB;              // SMAX * QR_PB
-  T* V = use_smem ? Racc + SMAX * QR_PB : X;
+  T* cs = Racc + SMAX * QR_PB;              // chol_scratch_elems
+  T* V = use_smem ? cs + chol_scratch_elems<T>() : X;
+  T* Pc = use_chol ? V + (size_t)nvec * len : nullptr;  // QR_PB * len (use_smem only)
   const int vld = use_smem ? len : ld;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
   __syncthreads();
-  bcgs2_core(V, nvec, len, vld, Rout, red, Cs, Racc);
+  bcgs2_core(V, nvec, len, vld, Rout, red, Cs, Racc, Pc, use_chol ? cs : (T*)nullptr);
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
 }
@@ -995,16 +1193,24 @@ static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
 
 template <typename T>
 static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
-  const size_t base = sizeof(T) * (64 + 2 * SMAX + 2 * SMAX * QR_PB);
+  const size_t base = sizeof(T) * (64 + 2 * SMAX + 2 * SMAX * QR_PB + chol_scratch_elems<T>());
   const size_t full = base + sizeof(T) * (size_t)nvec * len;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
+  // FP32 panels by guarded Cholesky-QR when a copy of one panel fits too and
+  // the block is large (>= 32 vectors of >= 256 entries), where the
+  // per-vector chain costs most; small blocks keep per-vector CGS2 (with
+  // Cholesky panels on them the mixed log Z of a 3 x 3 king's Ising lattice
+  // at beta 2 moved beyond 1e-3 of the FP64 value)
+  const size_t with_copy = full + sizeof(T) * (size_t)QR_PB * len;
+  const int use_chol = (sizeof(T) == 4 && use_smem && with_copy <= 200 * 1024 && nvec >= 32 && len >= 256) ? 1 : 0;
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_cgs2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   // one thread per element up to 512 (the register budget of the panel
   // products), at least 4 warps
   const int threads = std::max(128, std::min(512, (len + 31) / 32 * 32));
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
-  k_cgs2_rows<T><<<1, threads, use_smem ? full : base, st>>>(X, nvec, len, len, Rout, use_smem);
+  k_cgs2_rows<T><<<1, threads, use_chol ? with_copy : (use_smem ? full : base), st>>>(X, nvec, len, len, Rout,
+                                                                                       use_smem, use_chol);
 }
 
 template <typename T>
