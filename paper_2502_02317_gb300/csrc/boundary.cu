@@ -435,10 +435,11 @@ __host__ __device__ constexpr int chol_scratch_elems() { return 3 * QR_PB * QR_P
 // Orthonormalises panel k0 .. k0+b-1 (already projected against the earlier
 // panels; Racc holds those coefficients) by Cholesky-QR twice: P = Q1 L1^T,
 // Q1 = Q2 L2^T, so R_panel = L2^T L1^T.  The result is accepted when the Gram
-// of Q1 is within 0.1 of the identity and that of Q2 within 1e-5 (over the
-// columns that are not dependent); otherwise the panel is restored from Pc
-// and orthonormalised vector by vector (cgs2_vec).  Writes the panel's
-// columns of R either way.
+// of Q1 is within 0.1 of the identity, that of Q2 within 1e-5 (over the
+// columns that are not dependent) and the second pass finds no column
+// dependent that the first kept; otherwise the panel is restored from Pc and
+// orthonormalised vector by vector (cgs2_vec).  Writes the panel's columns
+// of R either way.
 template <typename T>
 __device__ void panel_cholqr(T* V, int k0, int b, int nvec, int len, int ld, T* Rout, T* red, T* Racc, T* Pc,
                              T* cs) {
@@ -479,6 +480,10 @@ __device__ void panel_cholqr(T* V, int k0, int b, int nvec, int len, int ld, T* 
       if (L2[i * QR_PB + i] != T(0) && L2[j * QR_PB + j] != T(0) &&
           !(fabs(G[i * QR_PB + j] - (i == j ? T(1) : T(0))) <= T(1e-5)))
         *flag = 0;
+      // a column the first pass kept but the second found dependent: Q1 was
+      // too ill-conditioned for the Gram to resolve it, and that direction
+      // would be lost (the columns compared above exclude it)
+      if (i == j && L1[i * QR_PB + i] != T(0) && L2[i * QR_PB + i] == T(0)) *flag = 0;
     }
     __syncthreads();
   }
