@@ -50,8 +50,9 @@ def make_instance(seed):
 
 def config_dict(extra=None):
     L = WORKLOAD["L"]
-    c = {"workload": f"{WORKLOAD['batch']} x chimera{L}x{L}_gauss_K44 ({8 * L * L} spins, d=256), beta=1, chi=32, "
-                     f"1 sweep, beam=1024",
+    c = {"workload": f"{WORKLOAD['batch']} x chimera{L}x{L}_gauss_K44 ({8 * L * L} spins, d=256), "
+                     f"beta={WORKLOAD['beta']:g}, chi={WORKLOAD['chi']}, {WORKLOAD['sweeps']} sweep, "
+                     f"beam={WORKLOAD['beam']}",
          "L": WORKLOAD["L"], "spins": 8 * WORKLOAD["L"] ** 2, "cluster_states": 256, "beta": WORKLOAD["beta"],
          "chi": WORKLOAD["chi"], "num_sweeps": WORKLOAD["sweeps"], "beam": WORKLOAD["beam"], "couplings": "J~N(0,1), h~N(0,0.1) on 2^-24 grid",
          "l2": "flushed between timed steps (256 MiB write)"}
@@ -237,12 +238,16 @@ def main():
     ap.add_argument("--no-king", action="store_true", help="skip the king's-graph Potts solves")
     ap.add_argument("--L", type=int, default=None,
                     help="grid side override (profiling of a smaller case of the same kernels)")
+    ap.add_argument("--beam", type=int, default=None,
+                    help="beam override (batches of small-beam solves; not the benchmark workload)")
     ap.add_argument("--only-main", action="store_true",
                     help="timed steps only (no end-to-end, FP64, uneven-batch or profile runs): the ncu "
                          "launch list")
     args = ap.parse_args()
     if args.L:
         WORKLOAD["L"] = args.L
+    if args.beam:
+        WORKLOAD["beam"] = args.beam
     WORKLOAD["batch"] = args.batch
     if args.impl == "reference":
         return run_reference(args)
