@@ -22,6 +22,9 @@ no blocking, fusion or reordering beyond what each step states:
   ``merge_branches``): conditional marginals from the cached environments,
   branch merging on the boundary of the explored region, pruning to
   ``max_states``, and exact energies of the final states.
+* ``lattice``  -- Sec. 3.1 (lattice transformations): the instance solved on
+  each of the 8 rotations / reflections of the grid, states mapped back to
+  the original sites, the best of 8 kept.
 * ``exact``    -- pins that do not use any of the above: brute force over all
   spin configurations (<= 24 spins) and spin-level row transfer matrices for
   width-3 Chimera strips (exact log Z and exact ground energy).
