@@ -21,7 +21,8 @@ no blocking, fusion or reordering beyond what each step states:
 * ``search``   -- Sec. 2 and Sec. 3.1 (``SearchParameters``,
   ``merge_branches``): conditional marginals from the cached environments,
   branch merging on the boundary of the explored region, pruning to
-  ``max_states``, and exact energies of the final states.
+  ``max_states``, exact energies of the final states, and the droplets
+  (low-energy excitations) collected in the merges.
 * ``lattice``  -- Sec. 3.1 (lattice transformations): the instance solved on
   each of the 8 rotations / reflections of the grid, states mapped back to
   the original sites, the best of 8 kept.

@@ -65,6 +65,8 @@ class Params:
     beam: int = 256
     cut_off_prob: float = 0.0
     merge: bool = True
+    droplet_energy: int = -1  # energy cutoff of droplets (units of the tables); < 0: no droplets
+    droplet_hamming: int = 0  # an accepted droplet differs in more than this many Potts variables
 
 
 @dataclass
@@ -75,6 +77,7 @@ class Result:
     near_ties: int = 0
     degenerate_cut: bool = False
     steps: list = field(default_factory=list)  # per site: (n candidates, n kept)
+    droplets: list = field(default_factory=list)  # (energy, state) excitations of the best state
 
 
 def key_sites(fg: FactorGraph, s: int) -> list:
@@ -154,6 +157,47 @@ class _Partial:
     logp: float
     lenv: np.ndarray
     R: list = None
+    drops: list = field(default_factory=list)  # droplets: (dE, ((site, state), ...)) relative to states
+
+
+def _apply(states, diff):
+    st = list(states)
+    for t, x in diff:
+        st[t] = x
+    return tuple(st)
+
+
+def _hamming(a, b) -> int:
+    return sum(1 for u, v in zip(a, b) if u != v)
+
+
+def _droplets(w_st, w_E, w_parent, losers, prm: "Params") -> list:
+    """Droplets of a merge winner (Sec. 2 and Sec. 3.1 ``SingleLayerDroplets``,
+    ``energy_cutoff``, ``hamming_cutoff``).  Reading: a partial configuration
+    that loses a merge agrees with the winner on every fixed variable next to
+    the unexplored region, so where they differ is a region that no later
+    variable touches; the loser is an excitation of the winner localised
+    there, dE = E_loser - E_winner, valid for every descendant of the winner.
+    The winner keeps its parent's droplets; the candidates are each loser and
+    each loser with one of its own droplets applied, taken in (dE, state)
+    order; a candidate is accepted when dE <= energy cutoff and it differs
+    from the winner and from every droplet accepted so far in more than
+    hamming cutoff Potts variables."""
+    acc = list(w_parent.drops)
+    seen = [w_st] + [_apply(w_st, d) for _, d in acc]
+    cand = []
+    for l_st, l_E, l_parent in losers:
+        cand.append((l_E - w_E, l_st))
+        for dE, diff in l_parent.drops:
+            cand.append((l_E + dE - w_E, _apply(l_st, diff)))
+    for dE, st in sorted(cand):
+        if dE > prm.droplet_energy:
+            continue
+        if any(_hamming(st, a) <= prm.droplet_hamming for a in seen):
+            continue
+        acc.append((dE, tuple((t, st[t]) for t in range(len(st)) if st[t] != w_st[t])))
+        seen.append(st)
+    return acc
 
 
 def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
@@ -174,6 +218,8 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
                 b.R = right_envs(p, B, i, [b.states[(i - 1) * cols + k] for k in range(cols)] if i > 0 else None)
         ks = key_sites(fg, s)
         children = {}
+        drop_on = prm.merge and prm.droplet_energy >= 0
+        members = {}
         n_cand = 0
         for b in beam:
             lc = log_conditional(p, B, i, j, b.lenv, b.R, b.states)
@@ -182,6 +228,8 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
                 E = b.E + delta_energy(fg, s, x, b.states)
                 key = tuple(st[t] for t in ks) if prm.merge else st
                 n_cand += 1
+                if drop_on:
+                    members.setdefault(key, []).append((st, E, b))
                 cur = children.get(key)
                 if cur is None or (E, st) < (cur[1], cur[0]):
                     children[key] = (st, E, b.logp + float(lc[x]), b)
@@ -202,7 +250,12 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
             A = B.sites[j]
             v = parent.lenv @ A[:, p.site(i, j).PD[x], :]
             m = np.max(np.abs(v))
-            new.append(_Partial(st, E, lp, v / m if m > 0 else v, parent.R))
+            drops = []
+            if drop_on:
+                key = tuple(st[t] for t in ks)
+                losers = [mb for mb in members[key] if mb[0] != st]
+                drops = _droplets(st, E, parent, losers, prm)
+            new.append(_Partial(st, E, lp, v / m if m > 0 else v, parent.R, drops))
         beam = new
     order = sorted(range(len(beam)), key=lambda k: (energy(fg, beam[k].states), beam[k].states))
     states = np.array([beam[k].states for k in order], dtype=np.int64)
@@ -211,7 +264,12 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
         assert energy(fg, beam[k].states) == beam[k].E
     logps = np.array([beam[k].logp for k in order])
     deg = any(boundary[r].degenerate for r in boundary)
-    return Result(states, energies, logps, near_ties, deg, steps)
+    # unpack_droplets: the best state's excitations as full states
+    drops = []
+    if order:
+        top = beam[order[0]]
+        drops = sorted((top.E + dE, _apply(top.states, diff)) for dE, diff in top.drops)
+    return Result(states, energies, logps, near_ties, deg, steps, drops)
 
 
 def debug_marginals(fg: FactorGraph, prm: Params, site: int, prefixes, boundary=None):
