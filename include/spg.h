@@ -97,6 +97,18 @@ int spg_version(void);
 /* Defaults for every field of *p.  Returns SPG_EINVAL if p is NULL. */
 int spg_params_default(spg_params* p);
 
+/* Lattice transformations (Sec. 3.1: the instance solved on every rotation
+ * and reflection of its grid).  Transformation k in 0..7 of an R x C grid of
+ * clusters: bit 4 transposes (i, j) -> (j, i) (the grid becomes C x R), then
+ * bit 1 reverses the rows and bit 2 the columns of the resulting grid; k = 0
+ * is the identity.  Writes site_map[s] (R*C entries, caller-owned) = the
+ * row-major site of the transformed grid that holds original site s, and the
+ * transformed grid's shape (either pointer may be NULL).  Host only, no
+ * device needed.  SPG_EINVAL for rows, cols < 1, k outside 0..7 or a NULL
+ * site_map. */
+int spg_lattice_site_map(int32_t rows, int32_t cols, int32_t k, int32_t* site_map, int32_t* new_rows,
+                         int32_t* new_cols);
+
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
  * (may be NULL: the library creates and owns a non-blocking stream).  The
  * context owns its device workspace, grown on demand and reused. */

@@ -13,12 +13,12 @@ import os as _os
 _os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from ._binding import (SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, Context, Problem, Result, SpgError,
-                       lib, params, spg_debug_marginals, spg_log_partition, spg_problem_ising,
+                       lib, params, spg_debug_marginals, spg_lattice_site_map, spg_log_partition, spg_problem_ising,
                        spg_problem_potts, spg_profile, spg_profile_report, spg_solve, spg_solve_batch, spg_tc_product,
                        spg_truncate, spg_truncate_static)
 
 __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
            "spg_problem_potts", "spg_solve", "spg_solve_batch", "spg_debug_marginals", "spg_log_partition",
-           "spg_profile", "spg_profile_report", "spg_tc_product", "spg_truncate",
+           "spg_profile", "spg_profile_report", "spg_tc_product", "spg_truncate", "spg_lattice_site_map",
            "spg_truncate_static",
            "SPG_FP64", "SPG_MIXED", "SPG_SQUARE", "SPG_KING"]

@@ -57,6 +57,8 @@ def _load():
     pI32, pI64, pD, pU16 = C.POINTER(I32), C.POINTER(I64), C.POINTER(D), C.POINTER(U16)
     sig = {
         "spg_version": (C.c_int, []),
+        "spg_lattice_site_map": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "spg_params_default": (C.c_int, [C.POINTER(spg_params)]),
         "spg_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
         "spg_destroy": (None, [P]),
@@ -112,6 +114,17 @@ class SpgError(RuntimeError):
 
 def _ptr(a, ct):
     return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def spg_lattice_site_map(rows: int, cols: int, k: int):
+    """(site_map [rows*cols] int32, new_rows, new_cols) of lattice
+    transformation k (include/spg.h)."""
+    out = np.zeros(rows * cols, np.int32)
+    r, c = C.c_int32(), C.c_int32()
+    rc = lib.spg_lattice_site_map(rows, cols, k, _ptr(out, C.c_int32), C.byref(r), C.byref(c))
+    if rc != SPG_OK:
+        raise SpgError(rc, "spg_lattice_site_map: invalid arguments")
+    return out, r.value, c.value
 
 
 def params(**kw) -> spg_params:

@@ -966,6 +966,26 @@ extern "C" {
 
 int spg_version(void) { return 100; }
 
+int spg_lattice_site_map(int32_t rows, int32_t cols, int32_t k, int32_t* site_map, int32_t* new_rows,
+                         int32_t* new_cols) {
+  if (rows < 1 || cols < 1 || k < 0 || k > 7 || !site_map) return SPG_EINVAL;
+  const int R = (k & 4) ? cols : rows, C = (k & 4) ? rows : cols;
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) {
+      int a = i, b = j;
+      if (k & 4) {
+        a = j;
+        b = i;
+      }
+      if (k & 1) a = R - 1 - a;
+      if (k & 2) b = C - 1 - b;
+      site_map[i * cols + j] = a * C + b;
+    }
+  if (new_rows) *new_rows = R;
+  if (new_cols) *new_cols = C;
+  return SPG_OK;
+}
+
 int spg_params_default(spg_params* p) {
   if (!p) return SPG_EINVAL;
   std::memset(p, 0, sizeof(*p));

@@ -69,3 +69,25 @@ def test_batch_streams_get_their_own_hardware_queues():
     env["CUDA_DEVICE_MAX_CONNECTIONS"] = "8"
     assert _run("import os, paper_2502_02317_gb300; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])", env) == "8"
     assert _run(code, env) == "8"
+
+
+@pytest.mark.parametrize("rows,cols", [(3, 3), (3, 5), (1, 4), (16, 16), (6, 12)])
+def test_lattice_site_map_matches_the_oracle(rows, cols):
+    """spg_lattice_site_map (host only) against the oracle's transformation
+    of grid positions, for all 8 transformations."""
+    import paper_2502_02317_gb300 as spg
+    from oracle import lattice
+    for k in range(8):
+        m, R, C = spg.spg_lattice_site_map(rows, cols, k)
+        _, _, R2, C2 = lattice.position(0, 0, rows, cols, k)
+        assert (R, C) == (R2, C2)
+        assert m.tolist() == lattice.site_map(rows, cols, k).tolist()
+
+
+def test_lattice_site_map_rejects_bad_arguments():
+    import paper_2502_02317_gb300 as spg
+    for args in [(0, 3, 0), (3, 0, 0), (3, 3, 8), (3, 3, -1)]:
+        with pytest.raises(spg.SpgError):
+            spg.spg_lattice_site_map(*args)
+    from paper_2502_02317_gb300 import _binding as b
+    assert spg.lib.spg_lattice_site_map(3, 3, 0, None, None, None) == b.SPG_EINVAL
