@@ -25,6 +25,13 @@ Workload shapes (paper Sec. 2 Eq. 1-2; Fig. 4 for the Chimera unit cell):
   clusters (the quasi-2D graph of the paper's Fig. 1(a)).
 * ``king_potts``: an L x L grid of Potts variables with d states, local tables
   and d x d pairwise tables on all 8-neighbour edges.
+* ``inpainting``: an L x L grid of d labels shaped like an inpainting problem
+  (Sec. 3 example, Fig. 5: data on a circular boundary, the inside to be
+  filled in): pixels on or outside a ring observe one of d labels in d equal
+  arcs (a seeded rotation), local cost 0 for the observed label and
+  ``data_cost`` for the others, no data inside; Potts smoothness
+  w [x_m != x_n] on the 8-neighbour edges, w = 1 for axis and 1/sqrt(2) for
+  diagonal edges.
 """
 from __future__ import annotations
 
@@ -219,6 +226,43 @@ def king_potts(L: int, d: int, seed: int, cols: int | None = None) -> PottsInsta
                          np.array(em, np.int32), np.array(en, np.int32),
                          np.concatenate(pair) if pair else np.zeros(0, np.int64), shift, KING,
                          name=f"kingpotts{rows}x{cols}_d{d}_s{seed}")
+
+
+def inpainting(L: int, d: int, seed: int, data_cost: float = 4.0, ring: float = 1.5) -> PottsInstance:
+    """Inpainting-shaped Potts model on an L x L king's graph (module header):
+    pixel (i, j) at distance r from the grid centre observes a label when
+    r >= L / 2 - ring, the label of the angular arc it lies in (d arcs,
+    rotated by a seeded angle).  Values on the 2**-24 grid."""
+    rng = _rng(seed)
+    shift = 24
+    unit = 2.0 ** shift
+    rot = float(rng.uniform(0.0, 2.0 * np.pi))
+    c = (L - 1) / 2.0
+    local = np.zeros((L * L, d), np.int64)
+    cost = int(round(data_cost * unit))
+    for i in range(L):
+        for j in range(L):
+            y, x = i - c, j - c
+            if np.hypot(y, x) >= L / 2.0 - ring:
+                lab = int(((np.arctan2(y, x) + rot) % (2.0 * np.pi)) // (2.0 * np.pi / d)) % d
+                local[i * L + j, :] = cost
+                local[i * L + j, lab] = 0
+    w_axis, w_diag = int(round(unit)), int(round(unit / np.sqrt(2.0)))
+    em, en, pair = [], [], []
+    for i in range(L):
+        for j in range(L):
+            s = i * L + j
+            for di, dj in ((0, 1), (1, -1), (1, 0), (1, 1)):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < L and 0 <= jj < L:
+                    w = w_axis if di == 0 or dj == 0 else w_diag
+                    em.append(s)
+                    en.append(ii * L + jj)
+                    pair.append((w * (1 - np.eye(d, dtype=np.int64))).reshape(-1))
+    return PottsInstance(L, L, np.full(L * L, d, np.int32), local.reshape(-1),
+                         np.array(em, np.int32), np.array(en, np.int32),
+                         np.concatenate(pair) if pair else np.zeros(0, np.int64), shift, KING,
+                         name=f"inpainting{L}x{L}_d{d}_s{seed}")
 
 
 def batch_chimera(n_instances: int, L_lo: int, L_hi: int, base_seed: int,
