@@ -17,7 +17,20 @@ from __future__ import annotations
 
 import numpy as np
 
-from .tables import _to_int
+
+
+def _grid_ints(values, shift):
+    """Integers k with value = k * 2^-shift, from each float's exact rational
+    value (independent of the tables' conversion, so that a scaling mistake
+    there cannot pass the brute-force pins)."""
+    out = []
+    for v in np.asarray(values, dtype=np.float64).ravel():
+        num, den = float(v).as_integer_ratio()  # den is a power of two
+        scaled = num * (1 << shift)
+        if scaled % den:
+            raise ValueError("value not on the 2**-shift grid")
+        out.append(scaled // den)
+    return np.array(out, dtype=np.int64)
 
 
 def _spins(n, lo, hi):
@@ -33,8 +46,8 @@ def all_energies(inst) -> np.ndarray:
     n = inst.n_spins
     if n > 24:
         raise ValueError("brute force is limited to 24 spins")
-    J = _to_int(inst.J, inst.energy_shift)
-    h = _to_int(inst.h, inst.energy_shift)
+    J = _grid_ints(inst.J, inst.energy_shift)
+    h = _grid_ints(inst.h, inst.energy_shift)
     if np.sum(np.abs(J)) + np.sum(np.abs(h)) >= 2 ** 52:
         raise ValueError("energies too large for the float64 path")
     Jm = np.zeros((n, n))
@@ -133,8 +146,8 @@ def chimera_strip(inst, beta: float):
     rows, cols = inst.grid_rows, inst.grid_cols
     if cols > 3:
         raise ValueError("width <= 3 only")
-    J = _to_int(inst.J, inst.energy_shift)
-    h = _to_int(inst.h, inst.energy_shift)
+    J = _grid_ints(inst.J, inst.energy_shift)
+    h = _grid_ints(inst.h, inst.energy_shift)
     u = 2.0 ** (-inst.energy_shift)
     row_of = np.arange(inst.n_spins) // (8 * cols)
     k_of = np.arange(inst.n_spins) % 8

@@ -78,6 +78,11 @@ class Result:
     degenerate_cut: bool = False
     steps: list = field(default_factory=list)  # per site: (n candidates, n kept)
     droplets: list = field(default_factory=list)  # (energy, state) excitations of the best state
+    # smallest relative log-probability gap between the last survivor and the
+    # first dropped child over all prune steps (inf when no step dropped a
+    # child); a search in lower precision keeps the same children when its
+    # log-probability error stays below half of it
+    min_cut_gap: float = float("inf")
 
 
 def key_sites(fg: FactorGraph, s: int) -> list:
@@ -208,6 +213,7 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
     rows, cols = fg.rows, fg.cols
     beam = [_Partial((), 0, 0.0, np.ones(1))]
     near_ties = 0
+    min_gap = float("inf")
     steps = []
     for s in range(fg.n_sites):
         i, j = divmod(s, cols)
@@ -242,6 +248,7 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
             a, b2 = cands[prm.beam - 1][2], cands[prm.beam][2]
             if abs(a - b2) <= NEAR_TIE_RTOL * max(1.0, abs(a)):
                 near_ties += 1
+            min_gap = min(min_gap, abs(a - b2) / max(1.0, abs(a)))
             cands = cands[:prm.beam]
         steps.append((n_cand, len(cands)))
         new = []
@@ -269,7 +276,7 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
     if order:
         top = beam[order[0]]
         drops = sorted((top.E + dE, _apply(top.states, diff)) for dE, diff in top.drops)
-    return Result(states, energies, logps, near_ties, deg, steps, drops)
+    return Result(states, energies, logps, near_ties, deg, steps, drops, min_gap)
 
 
 def debug_marginals(fg: FactorGraph, prm: Params, site: int, prefixes, boundary=None):

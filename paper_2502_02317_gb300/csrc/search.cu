@@ -453,18 +453,19 @@ __global__ void k_class_rep(DevSearch ds, int cur, int merge) {
 
 // For each (class representative b, x): the member with the lowest
 // (candidate energy, lex rank) wins.  When the site's own state is not part
-// of the key (no edge to a later site), one winner is taken per class over
-// all states x, lex order (member, x).  The beam is kept in lex order, so
+// of the key (no edge to a later site) and branches are merged, one winner
+// is taken per class over all states x, lex order (member, x); without
+// merging every child is its own class.  The beam is kept in lex order, so
 // the lex rank of a member is its index.  Three passes over all candidates:
 // the class minimum of the energy (atomicMin on its order-preserving bits),
 // the lowest member (and x) reaching it, and the winner table.  wmin is
 // reset to all ones and win / wkey to WIN_NONE (byte memsets) before.
 constexpr int WIN_NONE = 0x7f7f7f7f;
 
-__global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur) {
+__global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur, int merge) {
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
-  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
+  const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
   const size_t tot = (size_t)nb * ds.dmax;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
@@ -474,10 +475,10 @@ __global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur) {
   }
 }
 
-__global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur) {
+__global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur, int merge) {
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
-  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
+  const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
   const size_t tot = (size_t)nb * ds.dmax;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
@@ -491,10 +492,10 @@ __global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur) {
   }
 }
 
-__global__ void k_win_fix(DevTables tb, int site, DevSearch ds, int cur) {
+__global__ void k_win_fix(DevTables tb, int site, DevSearch ds, int cur, int merge) {
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
-  const bool xin = tb.dims[site * DIMW + D_XIN] != 0;
+  const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
   const size_t tot = (size_t)ds.cap * ds.dmax;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
@@ -1064,6 +1065,77 @@ __global__ void k_reset_beam(DevSearch ds, int cur) {
   for (int q = threadIdx.x; q < ds.N; q += blockDim.x) ds.states[cur][q] = 0;
 }
 
+// ---------------------------------------------------------------- forced paths
+// Teacher forcing along n given full states (the per-result FP64 check):
+// beam element b follows targets[b]; the search kernels compute the
+// conditionals of its prefix as for any beam element, and k_force selects
+// the target state as the only child (its own parent) and records that
+// state's log-conditional at out[b][site].
+__global__ void k_force_init(DevSearch ds, const int* n_dev, int cur) {
+  const int n = min(*n_dev, ds.cap);
+  const size_t N = ds.N;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ds.n_beam[cur] = n;
+    *ds.near_ties = 0;
+    *ds.err = 0;
+    *ds.candidates = 0.0;
+  }
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)n * N;
+       e += (size_t)gridDim.x * blockDim.x) {
+    ds.states[cur][e] = 0;
+    if (e % N == 0) {
+      const size_t b = e / N;
+      ds.E[cur][b] = 0;
+      ds.logp[cur][b] = 0.0;
+      ds.rid[cur][b] = 0;
+    }
+  }
+}
+
+__global__ void k_force(int site, DevSearch ds, int cur, const uint16_t* __restrict__ targets,
+                        double* __restrict__ out) {
+  const int n = ds.n_beam[cur];
+  const size_t N = ds.N;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+    const int x = targets[(size_t)b * N + site];
+    const int c = b * ds.dmax + x;
+    ds.sel_list[b] = c;
+    ds.win[c] = b;
+    out[(size_t)b * N + site] = ds.logc[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ds.n_beam[cur ^ 1] = n;
+}
+
+// max over b < n and sites of |a - r| / max(1, |r|) (a state's own
+// conditionals in two precisions); a finite value against -inf counts as inf.
+__global__ void k_logmarg_err(const double* __restrict__ a, const double* __restrict__ r, const int* n_dev,
+                              int N, double* out) {
+  __shared__ double red[32];
+  const size_t tot = (size_t)max(0, *n_dev) * N;
+  double m = 0.0;
+  for (size_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const double x = a[e], y = r[e];
+    double d;
+    if (isinf(y) || isinf(x))
+      d = (isinf(x) && isinf(y)) ? 0.0 : INFINITY;
+    else
+      d = fabs(x - y) / fmax(1.0, fabs(y));
+    if (!(d <= m)) m = d;  // NaN propagates
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, m, o);
+    if (!(t <= m)) m = t;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (!(red[w] <= v)) v = red[w];
+    *out = v;
+  }
+}
+
 // ---------------------------------------------------------------- S8 final
 // Exact energy of each final state from the tables (checked against the
 // running energy), then order by (energy, lex rank).
@@ -1167,11 +1239,11 @@ cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int
   cudaMemsetAsync(ds.win, 0x7f, sizeof(int) * tot, st);
   cudaMemsetAsync(ds.wkey, 0x7f, sizeof(int) * ds.cap, st);
   count_launches("k_win_min", st);
-  k_win_min<<<wb, 256, 0, st>>>(tb, site, ds, cur);
+  k_win_min<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
   count_launches("k_win_arg", st);
-  k_win_arg<<<wb, 256, 0, st>>>(tb, site, ds, cur);
+  k_win_arg<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
   count_launches("k_win_fix", st);
-  k_win_fix<<<wb, 256, 0, st>>>(tb, site, ds, cur);
+  k_win_fix<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
   return cudaGetLastError();
 }
 
@@ -1260,6 +1332,26 @@ cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); });
   count_launches("k_final", st);
   k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_init(const DevSearch& ds, const int* n_dev, int cur, cudaStream_t st) {
+  count_launches("k_force_init", st);
+  k_force_init<<<64, 256, 0, st>>>(ds, n_dev, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force(int site, const DevSearch& ds, int cur, const uint16_t* targets, double* out,
+                         cudaStream_t st) {
+  count_launches("k_force", st);
+  k_force<<<(ds.cap + 255) / 256, 256, 0, st>>>(site, ds, cur, targets, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logmarg_err(const double* a, const double* r, const int* n_dev, int N, double* out,
+                               cudaStream_t st) {
+  count_launches("k_logmarg_err", st);
+  k_logmarg_err<<<1, 1024, 0, st>>>(a, r, n_dev, N, out);
   return cudaGetLastError();
 }
 

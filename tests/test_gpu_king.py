@@ -119,7 +119,7 @@ def test_king_solve(spg, ctx, make, beta, chi, beam):
     if ref.near_ties == 0 and res.info()["near_ties"] == 0:
         np.testing.assert_array_equal(E, ref.energies)
         np.testing.assert_array_equal(st.astype(np.int64), ref.states)
-        close(lp, ref.log_probs, 1e-5)
+        close(lp, ref.log_probs, 1e-6)
     assert E[0] == ref.energies[0]
     for k in range(len(E)):
         assert tables.energy(fg, st[k]) == E[k]

@@ -2,7 +2,8 @@
 
 Tolerances: returned states and int64 energies bit-exact; log-marginals and
 log-probabilities |gpu - oracle| <= 1e-6 * max(1, |oracle|) in FP64 mode,
-1e-3 * max(1, |oracle|) in mixed mode.  In mixed mode the bound applies to
+1e-3 * max(1, |oracle|) in mixed mode.  Mixed-mode states are compared
+exactly when every prune cut of the oracle is wider than twice that bound.  In mixed mode the bound applies to
 conditionals >= 1e-9 (log >= LOG_FLOOR); FP32 contractions do not resolve
 smaller ones, which must then also be reported below 1e-9.  A run whose
 oracle records a near tie at a prune step compares only the energies of the
@@ -113,14 +114,14 @@ def compare_solve(spg, ctx, inst, beta, chi, beam, prec=0, merge=True, cut=0.0):
     st, E, lp = res.get()
     info = res.info()
     assert info["error_flags"] == 0
-    if prec == 1:
-        assert E[0] == ref.energies[0]
-    elif ref.near_ties == 0 and info["near_ties"] == 0:
+    # the same children survive every prune unless a cut of the oracle is a
+    # near tie, or (mixed mode) narrower than twice the mixed tolerance
+    same = ref.near_ties == 0 and info["near_ties"] == 0 and (prec == 0 or ref.min_cut_gap > 2 * TOL[prec])
+    if same:
         np.testing.assert_array_equal(E, ref.energies)
         np.testing.assert_array_equal(st.astype(np.int64), ref.states)
-        close(lp, ref.log_probs, TOL[prec] * 10)
-    else:
-        assert E[0] == ref.energies[0]
+        close(lp, ref.log_probs, TOL[prec])
+    assert E[0] == ref.energies[0]
     return ref, (st, E, lp, info)
 
 
