@@ -36,14 +36,16 @@ class spg_params(C.Structure):
     _fields_ = [("beta", C.c_double), ("chi", C.c_int32), ("num_sweeps", C.c_int32),
                 ("beam", C.c_int32), ("precision", C.c_int32), ("cut_off_prob", C.c_double),
                 ("svd_iters", C.c_int32), ("warm_start", C.c_int32), ("seed", C.c_uint64),
-                ("merge", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("merge", C.c_int32), ("fp64_rows", C.c_int32), ("check_fp64", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class spg_info(C.Structure):
     _fields_ = [("n_states", C.c_int32), ("near_ties", C.c_int32), ("degenerate_cuts", C.c_int32),
                 ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
                 ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
-                ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("reserved", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("fp64_rows", C.c_int32),
+                ("max_logmarg_err", C.c_double)]
 
 
 def _load():
@@ -70,7 +72,7 @@ def _load():
         "spg_problem_shape": (C.c_int, [P, pI32, pI32, pI32]),
         "spg_solve": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P)]),
         "spg_solve_batch": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
-        "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD]),
+        "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD, pD]),
         "spg_result_info": (C.c_int, [P, C.POINTER(spg_info)]),
         "spg_result_destroy": (None, [P]),
         "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
@@ -78,6 +80,18 @@ def _load():
         "spg_truncate": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
         "spg_truncate_static": (C.c_int, [P, I32, I32, I32, I32, P, P, P, P]),
         "spg_tc_product": (C.c_int, [P, P, I32, I32, P, I32, I32, P]),
+        "spg_warm_features": (C.c_int, [P, I32, C.POINTER(C.c_float)]),
+        "spg_boundary_export": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, P, pI32]),
+        "spg_mlp_create": (C.c_int, [P, I32, I32, I32, C.c_uint64, C.POINTER(P)]),
+        "spg_mlp_destroy": (None, [P]),
+        "spg_mlp_num_params": (C.c_int64, [P]),
+        "spg_mlp_params": (C.c_int, [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+        "spg_mlp_forward": (C.c_int, [P, P, I32, P, I32]),
+        "spg_mlp_loss_grad": (C.c_int, [P, P, P, I32, pD, C.POINTER(C.c_float)]),
+        "spg_mlp_train": (C.c_int, [P, P, P, C.c_int64, I32, I32, D, C.c_uint64, pD]),
+        "spg_set_warm_start": (C.c_int, [P, P]),
+        "spg_sweep_trace": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, I32, pD]),
+        "spg_peak_probe_stream": (C.c_int, [P, I32, pD]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
@@ -93,12 +107,13 @@ lib = _load()
 
 # Handles still open at interpreter exit are released results -> problems ->
 # contexts, before the CUDA runtime is torn down.
-_LIVE = {"result": weakref.WeakSet(), "problem": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+_LIVE = {"result": weakref.WeakSet(), "problem": weakref.WeakSet(), "mlp": weakref.WeakSet(),
+         "ctx": weakref.WeakSet()}
 
 
 @atexit.register
 def _close_all():
-    for kind in ("result", "problem", "ctx"):
+    for kind in ("result", "problem", "mlp", "ctx"):
         for obj in list(_LIVE[kind]):
             try:
                 obj.close()
@@ -135,16 +150,43 @@ def params(**kw) -> spg_params:
     return p
 
 
+def _stream_handle(stream):
+    """cudaStream_t of a torch.cuda.Stream, a raw handle (int) or None."""
+    if stream is None:
+        return None
+    handle = getattr(stream, "cuda_stream", stream)
+    return C.c_void_p(int(handle)) if handle else None
+
+
+def _device_tensor(t, dtype, name, ndim=2, device=None):
+    """Reject, before any launch, a tensor the C ABI would misread: the
+    library reads plain row-major device arrays of one dtype."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dim() != ndim or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous {ndim}-D tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name}: tensor on cuda:{t.device.index}, the context runs on cuda:{device}")
+    return t
+
+
 class Context:
-    """spg_create / spg_destroy.  ``stream`` is a cudaStream_t as an int
-    (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+    """spg_create / spg_destroy.  ``stream``: a torch.cuda.Stream, a
+    cudaStream_t as an int (e.g. ``torch.cuda.current_stream().cuda_stream``)
+    or None (the library creates its own)."""
 
     def __init__(self, device: int = 0, stream=None):
         h = C.c_void_p()
-        rc = lib.spg_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        rc = lib.spg_create(C.byref(h), device, _stream_handle(stream))
         if rc != SPG_OK:
             raise SpgError(rc, "spg_create failed")
         self.h = h
+        self.device = device
         _LIVE["ctx"].add(self)
 
     def check(self, rc):
@@ -223,13 +265,20 @@ class Result:
     def get(self):
         """(states [n, N] uint16, energies int64 [n], log_probs [n])"""
         n, N = C.c_int32(), C.c_int32()
-        self.ctx.check(lib.spg_result_get(self.h, C.byref(n), C.byref(N), None, None, None, None))
+        self.ctx.check(lib.spg_result_get(self.h, C.byref(n), C.byref(N), None, None, None, None, None))
         st = np.zeros((n.value, N.value), np.uint16)
         E = np.zeros(n.value, np.int64)
         lp = np.zeros(n.value, np.float64)
         self.ctx.check(lib.spg_result_get(self.h, None, None, _ptr(st, C.c_uint16), _ptr(E, C.c_int64), None,
-                                          _ptr(lp, C.c_double)))
+                                          _ptr(lp, C.c_double), None))
         return st, E, lp
+
+    def max_logmarg_err(self) -> float:
+        """Log-marginal error of the result against plain FP64 (params
+        check_fp64; NaN when unchecked, 0 in the FP64 mode)."""
+        v = C.c_double()
+        self.ctx.check(lib.spg_result_get(self.h, None, None, None, None, None, None, C.byref(v)))
+        return v.value
 
     def info(self) -> dict:
         inf = spg_info()
@@ -295,6 +344,7 @@ def spg_truncate(ctx: Context, M, keep: int, iters: int = 6):
     """M: torch.float64 CUDA tensor (m x n, contiguous).  Returns device
     tensors (V [n, keep], US [m, keep], sigma [keep])."""
     import torch
+    _device_tensor(M, torch.float64, "M", device=ctx.device)
     m, n = M.shape
     V = torch.empty((n, keep), dtype=torch.float64, device=M.device)
     US = torch.empty((m, keep), dtype=torch.float64, device=M.device)
@@ -310,8 +360,12 @@ def spg_tc_product(ctx: Context, M, Bt, trans: bool):
     CUDA tensor [m, n]; Bt: [s, n] (trans False) or [s, m] (trans True).
     Returns out [s, m] = (M Bt^T)^T or [s, n] = (M^T Bt^T)^T."""
     import torch
+    _device_tensor(M, torch.float32, "M", device=ctx.device)
+    _device_tensor(Bt, torch.float32, "Bt", device=ctx.device)
     m, n = M.shape
     s = Bt.shape[0]
+    if Bt.shape[1] != (m if trans else n):
+        raise ValueError("Bt: second dimension must be m (trans) or n")
     out = torch.empty((s, n if trans else m), dtype=torch.float32, device=M.device)
     torch.cuda.synchronize(M.device)
     ctx.check(lib.spg_tc_product(ctx.h, C.c_void_p(M.data_ptr()), m, n, C.c_void_p(Bt.data_ptr()), s,
@@ -322,16 +376,156 @@ def spg_tc_product(ctx: Context, M, Bt, trans: bool):
 def spg_truncate_static(M, keep: int, iters: int = 6, stream=None):
     """spg_truncate without any device allocation inside the library (the
     scratch is a fixed array in the library image; m, n <= 256, keep <= 32).
-    Outputs are allocated here by torch, on the caller's side."""
+    Outputs are allocated here by torch, on the caller's side.  M: contiguous
+    torch.float64 CUDA tensor; the call runs on M's device, on ``stream`` (a
+    torch.cuda.Stream or a raw handle; default: torch's current stream of
+    that device, so it is ordered after the caller's work on it)."""
     import torch
+    _device_tensor(M, torch.float64, "M")
     m, n = M.shape
-    V = torch.empty((n, keep), dtype=torch.float64, device=M.device)
-    US = torch.empty((m, keep), dtype=torch.float64, device=M.device)
-    sig = torch.empty(keep, dtype=torch.float64, device=M.device)
-    torch.cuda.synchronize(M.device)
-    rc = lib.spg_truncate_static(C.c_void_p(M.data_ptr()), m, n, keep, iters, C.c_void_p(V.data_ptr()),
-                                 C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr()),
-                                 C.c_void_p(stream) if stream else None)
+    with torch.cuda.device(M.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(M.device)
+        V = torch.empty((n, keep), dtype=torch.float64, device=M.device)
+        US = torch.empty((m, keep), dtype=torch.float64, device=M.device)
+        sig = torch.empty(keep, dtype=torch.float64, device=M.device)
+        rc = lib.spg_truncate_static(C.c_void_p(M.data_ptr()), m, n, keep, iters, C.c_void_p(V.data_ptr()),
+                                     C.c_void_p(US.data_ptr()), C.c_void_p(sig.data_ptr()),
+                                     _stream_handle(stream))
     if rc != SPG_OK:
         raise SpgError(rc, "spg_truncate_static failed")
     return V, US, sig
+
+
+# ---------------------------------------------------------------- warm start
+SPG_WS_FEATURES = 800
+SPG_WS_PER_CLUSTER = 52
+
+
+def spg_warm_features(prob: Problem, row: int) -> np.ndarray:
+    """Network inputs of the sites of boundary row `row`: [cols, 800] float32."""
+    out = np.zeros((prob.cols, SPG_WS_FEATURES), np.float32)
+    rc = lib.spg_warm_features(prob.h, row, _ptr(out, C.c_float))
+    if rc != SPG_OK:
+        raise SpgError(rc, "spg_warm_features failed")
+    return out
+
+
+def spg_boundary_export(ctx: Context, prob: Problem, prm: spg_params, row: int, fix_signs: bool = True):
+    """(sites, dims): the boundary MPS B_row as a device tensor [cols, 16,
+    chi, chi] (float64 in SPG_FP64, float32 in SPG_MIXED) and the sites'
+    dims [cols, 3] = (p, chi_l, chi_r)."""
+    import torch
+    chi = prm.chi
+    dtype = torch.float64 if prm.precision == SPG_FP64 else torch.float32
+    with torch.cuda.device(ctx.device):
+        out = torch.empty((prob.cols, 16, chi, chi), dtype=dtype, device=f"cuda:{ctx.device}")
+        torch.cuda.synchronize()
+        dims = np.zeros((prob.cols, 3), np.int32)
+        ctx.check(lib.spg_boundary_export(ctx.h, prob.h, C.byref(prm), row, int(bool(fix_signs)),
+                                          C.c_void_p(out.data_ptr()), _ptr(dims, C.c_int32)))
+    return out, dims
+
+
+class Mlp:
+    """spg_mlp_*: the warm-start network (parameters and Adam state on the
+    context's device).  Inputs and targets are contiguous float32 CUDA
+    tensors."""
+
+    def __init__(self, ctx: Context, n_in: int, n_hidden: int, n_out: int, seed: int = 0):
+        h = C.c_void_p()
+        ctx.check(lib.spg_mlp_create(ctx.h, n_in, n_hidden, n_out, seed, C.byref(h)))
+        self.ctx, self.h = ctx, h
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        _LIVE["mlp"].add(self)
+
+    def num_params(self) -> int:
+        return int(lib.spg_mlp_num_params(self.h))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.num_params(), np.float32)
+        self.ctx.check(lib.spg_mlp_params(self.h, _ptr(out, C.c_float), None))
+        return out
+
+    def set_params(self, flat) -> None:
+        flat = np.ascontiguousarray(flat, np.float32)
+        if flat.size != self.num_params():
+            raise ValueError("parameter count mismatch")
+        self.ctx.check(lib.spg_mlp_params(self.h, None, _ptr(flat, C.c_float)))
+
+    def forward(self, X, bf16: bool = False):
+        import torch
+        _device_tensor(X, torch.float32, "X", device=self.ctx.device)
+        if X.shape[1] != self.n_in:
+            raise ValueError("X: wrong number of inputs")
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        torch.cuda.synchronize(X.device)
+        self.ctx.check(lib.spg_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr()),
+                                           int(bool(bf16))))
+        return Y
+
+    def loss_grad(self, X, T):
+        """(loss, flat gradient) over all rows of X, T."""
+        import torch
+        _device_tensor(X, torch.float32, "X", device=self.ctx.device)
+        _device_tensor(T, torch.float32, "T", device=self.ctx.device)
+        g = np.zeros(self.num_params(), np.float32)
+        loss = C.c_double()
+        torch.cuda.synchronize(X.device)
+        self.ctx.check(lib.spg_mlp_loss_grad(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), X.shape[0],
+                                             C.byref(loss), _ptr(g, C.c_float)))
+        return loss.value, g
+
+    def train(self, X, T, batch: int, steps: int, lr: float, seed: int = 0) -> float:
+        import torch
+        _device_tensor(X, torch.float32, "X", device=self.ctx.device)
+        _device_tensor(T, torch.float32, "T", device=self.ctx.device)
+        loss = C.c_double()
+        torch.cuda.synchronize(X.device)
+        self.ctx.check(lib.spg_mlp_train(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), X.shape[0],
+                                         batch, steps, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def split(self, flat) -> dict:
+        """The flat layout as {W1, b1, W2, b2, W3, b3} views."""
+        I, H, O = self.n_in, self.n_hidden, self.n_out
+        out, o = {}, 0
+        for k, shape in (("W1", (H, I)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (O, H)), ("b3", (O,))):
+            n = int(np.prod(shape))
+            out[k] = flat[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def close(self):
+        if self.h:
+            lib.spg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spg_set_warm_start(ctx: Context, mlp) -> None:
+    ctx.check(lib.spg_set_warm_start(ctx.h, mlp.h if mlp is not None else None))
+    ctx._warm = mlp  # keep it alive while attached
+
+
+def spg_sweep_trace(ctx: Context, prob: Problem, prm: spg_params, row: int, init: int, n_sweeps: int) -> np.ndarray:
+    """log <phi_k | W psi> after each of n_sweeps sweeps of row `row`
+    started from the zipper (init 0) or the attached network (init 1)."""
+    out = np.zeros(n_sweeps, np.float64)
+    ctx.check(lib.spg_sweep_trace(ctx.h, prob.h, C.byref(prm), row, init, n_sweeps, _ptr(out, C.c_double)))
+    return out
+
+
+def spg_peak_probe(kind: str, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s ("fp32" or
+    "fp64")."""
+    v = C.c_double()
+    rc = lib.spg_peak_probe_stream(_stream_handle(stream), {"fp32": 0, "fp64": 1}[kind], C.byref(v))
+    if rc != SPG_OK:
+        raise SpgError(rc, "spg_peak_probe failed")
+    return v.value

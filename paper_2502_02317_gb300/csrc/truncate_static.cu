@@ -68,10 +68,19 @@ extern "C" int spg_truncate_static(const double* M, int32_t m, int32_t n, int32_
     return SPG_EUNSUPPORTED;  // beyond the static scratch
   const size_t work = truncated_svd_work(m, n, keep);
   if (work + 8 > kStaticScratchDoubles) return SPG_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the call waits for its stream before returning, which a stream under
+  // capture does not allow (the wait would invalidate the caller's capture):
+  // such a stream is rejected before anything is enqueued on it
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return SPG_ECUDA;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return SPG_EINVAL;
   double* base = nullptr;
   const int rc = scratch_address(&base);
   if (rc != SPG_OK) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* s1 = base + work;
   int* flag = reinterpret_cast<int*>(base + work + 2);
   // the degenerate-cut counter must start at zero; every other word of the

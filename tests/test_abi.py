@@ -29,7 +29,8 @@ def test_params_defaults_and_struct_layout():
     p = spg.params()
     assert (p.beta, p.chi, p.beam, p.num_sweeps, p.precision, p.merge, p.svd_iters) == (1.0, 16, 256, 0, 0, 1, -1)
     assert ctypes.sizeof(b.spg_params) == 80
-    assert ctypes.sizeof(b.spg_info) == 64
+    assert ctypes.sizeof(b.spg_info) == 72
+    assert (p.fp64_rows, p.check_fp64) == (-1, 0)
     assert spg.lib.spg_version() == 100
     assert spg.lib.spg_params_default(None) == b.SPG_EINVAL
 
@@ -91,3 +92,25 @@ def test_lattice_site_map_rejects_bad_arguments():
             spg.spg_lattice_site_map(*args)
     from paper_2502_02317_gb300 import _binding as b
     assert spg.lib.spg_lattice_site_map(3, 3, 0, None, None, None) == b.SPG_EINVAL
+
+
+def test_binding_rejects_misread_tensors_before_any_launch():
+    """Tensors the C ABI would misread (wrong dtype, not contiguous, not on
+    a CUDA device) are refused by the binding before the library is called;
+    these checks need no GPU."""
+    import torch
+    import paper_2502_02317_gb300 as spg
+    from paper_2502_02317_gb300 import _binding as b
+    bad = [torch.zeros((8, 8), dtype=torch.float32),            # wrong dtype
+           torch.zeros((8, 8), dtype=torch.float64),            # host memory
+           torch.zeros((8, 16), dtype=torch.float64)[:, ::2]]   # strided
+    for t in bad:
+        with pytest.raises(ValueError):
+            spg.spg_truncate_static(t, 4)
+        with pytest.raises(ValueError):
+            b._device_tensor(t, torch.float64, "M")
+    with pytest.raises(ValueError):
+        b._device_tensor(torch.zeros(8, dtype=torch.float64), torch.float64, "M")
+    assert b._stream_handle(None) is None
+    assert b._stream_handle(0) is None
+    assert b._stream_handle(1234).value == 1234
