@@ -126,8 +126,12 @@ def measured_peaks():
 
 
 def cpu_oracle_sample(seed, max_sites=6):
-    """Oracle on a bounded sample: full boundary MPSs + the first sites of the
-    search (beam states counted on those sites)."""
+    """Oracle on a bounded sample of one 16x16 solve: the full boundary phase
+    (all 15 boundary MPSs) and the first max_sites sites of the search.  From
+    the third site on the beam is full (1024 x 256 candidates per site), so
+    the per-site cost of sites 2 .. max_sites-1 projects the search over all
+    256 sites; the value is the projected full solve's beam states per
+    second."""
     import numpy as np
 
     from oracle import boundary, peps, search, tables
@@ -136,14 +140,17 @@ def cpu_oracle_sample(seed, max_sites=6):
     fg = tables.from_ising(inst)
     p = peps.build(fg, WORKLOAD["beta"])
     bd = boundary.boundary_mpses(p, WORKLOAD["chi"], WORKLOAD["sweeps"])
-    # search restricted to the first max_sites sites of row 0
+    t_boundary = time.perf_counter() - t0
     beam = [search._Partial((), 0, 0.0, np.ones(1))]
     cols = fg.cols
     cand = 0
     B = bd[1]
     for b in beam:
         b.R = search.right_envs(p, B, 0, None)
+    site_t, site_c = [], []
     for s in range(max_sites):
+        ts = time.perf_counter()
+        c0 = cand
         i, j = divmod(s, cols)
         ks = search.key_sites(fg, s)
         children = {}
@@ -163,11 +170,117 @@ def cpu_oracle_sample(seed, max_sites=6):
             v = parent.lenv @ B.sites[j][:, p.site(i, j).PD[st[-1]], :]
             new.append(search._Partial(st, E, lp, v / np.max(np.abs(v)), parent.R))
         beam = new
+        site_t.append(time.perf_counter() - ts)
+        site_c.append(cand - c0)
     dt = time.perf_counter() - t0
+    n_sites = fg.n_sites
+    full = 2  # sites 0 and 1 fill the beam
+    per_site_t = statistics.mean(site_t[full:]) if len(site_t) > full else site_t[-1]
+    per_site_c = statistics.mean(site_c[full:]) if len(site_c) > full else site_c[-1]
+    proj_t = t_boundary + sum(site_t[:full]) + per_site_t * (n_sites - full)
+    proj_c = sum(site_c[:full]) + per_site_c * (n_sites - full)
     cores = len(os.sched_getaffinity(0))
-    return {"value": cand / dt, "unit": "beam states/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 instance: tables + all 15 boundary MPSs (chi=32, full SVD, 1 sweep) + the first {max_sites} "
-                      f"search sites ({cand} beam states) in {dt:.1f} s"}
+    return {"value": proj_c / proj_t, "unit": "beam states/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 instance (chimera16x16 gauss, chi=32, 1 sweep, beam=1024): all 15 boundary MPSs "
+                      f"({t_boundary:.1f} s) + the first {max_sites} search sites ({cand} beam states, "
+                      f"{sum(site_t):.1f} s); value = projected full solve ({proj_c:.3g} beam states in "
+                      f"{proj_t:.0f} s, sites {full}.. at the measured per-site cost {per_site_t:.2f} s)",
+            "sampled_rate": cand / dt, "boundary_s": t_boundary, "projected_solve_s": proj_t}
+
+
+def cpu_oracle_cfg1(seeds=(0, 1)):
+    """Full oracle solves of the plain FP64 workload (3x3 Chimera, +-1, beta
+    1, chi 16, beam 256): beam states per second, no sampling."""
+    import instances as I
+    from oracle import search, tables
+    cand, t = 0.0, 0.0
+    for sd in seeds:
+        fg = tables.from_ising(I.chimera(3, sd))
+        t0 = time.perf_counter()
+        res = search.solve(fg, search.Params(beta=1.0, chi=16, beam=256))
+        t += time.perf_counter() - t0
+        cand += sum(c for c, _ in res.steps)
+    return {"value": cand / t, "unit": "beam states/s", "seeds": len(seeds), "s": t}
+
+
+def cpu_oracle_cfg1_one_thread():
+    """cpu_oracle_cfg1 in a child process with every BLAS pool at 1 thread
+    (the variables are read when NumPy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = "import bench, json; print(json.dumps(bench.cpu_oracle_cfg1()))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def sweeps_to_fidelity(trace, best, tol=1e-6):
+    """Sweeps until F_k / F_best = exp(2 (log_overlap_k - best)) >= 1 - tol
+    (len(trace) + 1 when never reached)."""
+    import numpy as np
+    ok = np.nonzero(2.0 * (np.asarray(trace) - best) >= np.log1p(-tol))[0]
+    return int(ok[0]) + 1 if ok.size else len(trace) + 1
+
+
+def warm_start_leg(spg, ctx, torch, n_train=16, n_eval=2, eval_rows=(2, 9), n_sweeps=12, steps=1500, chi=64,
+                   hidden=256):
+    """The learned warm start (BASELINE config 5, scaled down to bench
+    minutes): an MLP from the couplings near a boundary row to that row's MPS
+    sites, trained by the library's own kernels on every row the method
+    builds for n_train 12x12 +-1 Chimera instances at chi 64, then judged on
+    unseen 16x16 instances by the plain contraction: sweeps until the
+    fidelity with W psi reaches 1 - 1e-6 of the best compression, from the
+    network's start and from the SVD zipper's."""
+    import numpy as np
+
+    import instances as I
+    prm = spg.params(beta=1.0, chi=chi, num_sweeps=1, precision=spg.SPG_MIXED)
+    t0 = time.perf_counter()
+    X, T = [], []
+    for k in range(n_train):
+        inst = I.chimera(12, 10000 + k)
+        prob = spg.spg_problem_ising(ctx, inst)
+        out, _ = spg.spg_boundary_export(ctx, prob, prm, 0)
+        T.append(out.reshape((inst.grid_rows - 1) * inst.grid_cols, -1))
+        X.append(np.concatenate([spg.spg_warm_features(prob, r) for r in range(1, inst.grid_rows)]))
+        prob.close()
+    Xd = torch.tensor(np.concatenate(X), device="cuda")
+    Td = torch.cat(T).contiguous()
+    del T
+    t_gen = time.perf_counter() - t0
+    net = spg.Mlp(ctx, spg.SPG_WS_FEATURES, hidden, 16 * chi * chi, seed=0)
+    l0, _ = net.loss_grad(Xd[:256], Td[:256])
+    t1 = time.perf_counter()
+    loss = net.train(Xd, Td, batch=64, steps=steps, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t1
+    spg.spg_set_warm_start(ctx, net)
+    counts = {"zipper": [], "network": []}
+    first = []
+    t2 = time.perf_counter()
+    for k in range(n_eval):
+        inst = I.chimera(16, 20000 + k)
+        prob = spg.spg_problem_ising(ctx, inst)
+        for row in eval_rows:
+            tz, tn = spg.spg_sweep_trace(ctx, prob, prm, row, 2, n_sweeps)
+            best = max(tz.max(), tn.max())
+            counts["zipper"].append(sweeps_to_fidelity(tz, best))
+            counts["network"].append(sweeps_to_fidelity(tn, best))
+            first.append({"zipper": float(tz[0] - best), "network": float(tn[0] - best)})
+        prob.close()
+    t_eval = time.perf_counter() - t2
+    spg.spg_set_warm_start(ctx, None)
+    samples = int(Xd.shape[0])
+    del Xd, Td
+    return {"workload": f"train: every boundary row of {n_train} chimera12x12 +-1 instances at chi={chi} "
+                        f"({samples} sites, 1 sweep per row); evaluate: rows {list(eval_rows)} of {n_eval} unseen "
+                        f"chimera16x16 +-1 at chi={chi}, {n_sweeps} sweeps from each start",
+            "network": f"{spg.SPG_WS_FEATURES}-{hidden}-{hidden}-{16 * chi * chi} tanh MLP, FP32 training "
+                       f"(Adam, lr 1e-3, batch 64, {steps} steps), BF16 inference",
+            "loss_initial": l0, "loss_final": loss,
+            "sweeps_to_1e-6": counts, "mean_sweeps": {k: float(np.mean(v)) for k, v in counts.items()},
+            "log_overlap_deficit_after_1_sweep": first,
+            "seconds": {"generate": t_gen, "train": t_train, "evaluate": t_eval}}
 
 
 def rank_instance_seed(rank: int) -> int:
@@ -236,6 +349,7 @@ def main():
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="instances solved concurrently per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-king", action="store_true", help="skip the king's-graph Potts solves")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--L", type=int, default=None,
                     help="grid side override (profiling of a smaller case of the same kernels)")
     ap.add_argument("--beam", type=int, default=None,
@@ -342,44 +456,93 @@ def main():
     line["diagnostics"] = {"near_ties": inf1["near_ties"], "degenerate_cuts": inf1["degenerate_cuts"],
                            "jacobi_sweeps_max": inf1["jacobi_sweeps_max"], "error_flags": inf1["error_flags"]}
 
-    # end to end through the C ABI from host arrays: problems built and
-    # copied, the batch solved, results copied back
-    e2e_times, e2e_build = [], []
-    for _ in range(args.steps):
+    # end to end through the C ABI from host arrays: every step a new batch
+    # of instances (drawn before the timed region) enters through the public
+    # API -- new couplings written into the existing problems (tables built
+    # on the host, uploaded in place, 32 host threads), the batch solved by
+    # replaying the captured solves, results read back to the host
+    from concurrent.futures import ThreadPoolExecutor
+    steps_insts = [[make_instance(rank_instance_seed(rank) * 100 + 50000 + st_ * NB + k) for k in range(NB)]
+                   for st_ in range(args.steps)]
+    pool = ThreadPoolExecutor(max_workers=NB)
+    e2e_times, e2e_build, e2e_cands = [], [], []
+    for st_ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ps = [spg.spg_problem_ising(ctx, i) for i in insts]
+        list(pool.map(lambda pi: spg.spg_problem_update_ising(pi[0], pi[1].J, pi[1].h),
+                      zip(probs, steps_insts[st_])))
         t1 = time.perf_counter()
-        rs = spg.spg_solve_batch(ctx, ps, prms)
+        rs = spg.spg_solve_batch(ctx, probs, prms)
         outs = [r.get() for r in rs]
         e2e_times.append(time.perf_counter() - t0)
         e2e_build.append(t1 - t0)
-        for r in rs:
-            r.close()
-        for p_ in ps:
-            p_.close()
+        e2e_cands.append(sum(r.info()["candidates"] for r in rs))
+    pool.shutdown()
     n_sites = insts[0].grid_rows * insts[0].grid_cols
-    # device tables per problem: E (int64) + 4 projectors (uint8) per state,
-    # 2 reduced 16x16 int64 tables, dims, state lists, merge keys per site
-    h2d = NB * (n_sites * (8 * 256 + 4 * 256 + 2 * 256 + 8 * 256 * 2 + 4 * 8 + 4 * 17 + 4 * 41 + 4) + 4)
+    # per problem and step: the value tables written in place (local E and
+    # the left, up and anti-diagonal reduced tables, int64)
+    h2d = NB * 8 * n_sites * (256 + 3 * 256)
     d2h = sum(len(o[1]) * (2 * n_sites + 8 + 8) + 16 for o in outs)
-    line["e2e"] = {"value": statistics.mean(cands) / statistics.mean(e2e_times), "unit": "beam states/s",
+    line["e2e"] = {"value": sum(e2e_cands) / sum(e2e_times), "unit": "beam states/s",
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                   # per step: problem construction (host tables + upload), and
-                   # the first (uncaptured) solve of the new problems + results
+                   # per step: the tables of the new instances (host build +
+                   # upload), then the batch solved from its captured graphs
                    "build_s": statistics.mean(e2e_build),
-                   "solve_s": statistics.mean(e2e_times) - statistics.mean(e2e_build)}
+                   "solve_s": statistics.mean(e2e_times) - statistics.mean(e2e_build),
+                   "path": "spg_problem_update_ising + spg_solve_batch (graph replay) + spg_result_get"}
+    # the problems hold the last step's instances now: restore the timed batch
+    for pr, inst in zip(probs, insts):
+        spg.spg_problem_update_ising(pr, inst.J, inst.h)
 
-    # plain FP64 GPU path on the same batch: time, equal best energies
+    # plain FP64 GPU path: the same instance's time to solution, timed like
+    # the mixed one (graph replay after warm-up runs), and the best energies
+    # of 8 instances of the batch against the mixed path's
     if prec != spg.SPG_FP64:
-        p64 = [params(spg.SPG_FP64)] * NB
-        rs64, ms64 = timed(lambda: spg.spg_solve_batch(ctx, probs, p64))
+        p64 = params(spg.SPG_FP64)
+        for _ in range(2):  # uncaptured first solve, then the graph capture
+            spg.spg_solve(ctx, probs[0], p64).get()
+        t64 = []
+        for _ in range(min(args.steps, 2)):
+            r641, ms641 = timed(lambda: spg.spg_solve(ctx, probs[0], p64))
+            r641.get()
+            t64.append(ms641)
+        nb8 = min(8, NB)
+        rs64, ms64 = timed(lambda: spg.spg_solve_batch(ctx, probs[:nb8], [p64] * nb8))
         b64 = [int(r.get()[1][0]) for r in rs64]
-        r641, ms641 = timed(lambda: spg.spg_solve(ctx, probs[0], p64[0]))
-        r641.get()
-        line["fp64_gpu"] = {"batch_ms": ms64, "tts_s": ms641 / 1e3,
-                            "equal_best_energy": all(a == b for a, b in zip(b64, bests)),
-                            "speedup_mixed_vs_fp64": {"batch": ms64 / ms, "single_instance": ms641 / tts_ms}}
+        tts64 = statistics.mean(t64) / 1e3
+        line["fp64_gpu"] = {"tts_s": tts64, "tts_runs": len(t64), "batch8_first_run_ms": ms64,
+                            "equal_best_energy": all(a == b for a, b in zip(b64, bests[:nb8])),
+                            "instances_compared": nb8,
+                            "speedup_mixed_vs_fp64": {"single_instance": tts64 / line["tts_s"]}}
+        # the mixed result's own log-marginal error against plain FP64 (every
+        # returned state's conditionals along its path)
+        rc_ = spg.spg_solve(ctx, probs[0], spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"],
+                                                      beam=WORKLOAD["beam"], precision=prec,
+                                                      num_sweeps=WORKLOAD["sweeps"], check_fp64=1))
+        line["max_logmarg_err"] = rc_.max_logmarg_err()
+        line["fp64_rows"] = rc_.info()["fp64_rows"]
+
+    # beta = 4 (the precision config's second temperature): one instance,
+    # mixed against plain FP64, times after warm-up, best energies, and the
+    # mixed result's log-marginal error against FP64
+    if WORKLOAD["L"] == 16 and prec != spg.SPG_FP64:
+        b4 = {}
+        for bprec in (prec, spg.SPG_FP64):
+            bprm = spg.params(beta=4.0, chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=bprec,
+                              num_sweeps=WORKLOAD["sweeps"])
+            for _ in range(2):
+                spg.spg_solve(ctx, probs[0], bprm).get()
+            rb, msb = timed(lambda: spg.spg_solve(ctx, probs[0], bprm))
+            _, Eb, _ = rb.get()
+            b4[bprec] = {"tts_s": msb / 1e3, "best_energy_fixed": int(Eb[0]),
+                         "beam_states_per_s": rb.info()["candidates"] / (msb / 1e3)}
+        rcb = spg.spg_solve(ctx, probs[0], spg.params(beta=4.0, chi=WORKLOAD["chi"], beam=WORKLOAD["beam"],
+                                                      precision=prec, num_sweeps=WORKLOAD["sweeps"], check_fp64=1))
+        line["beta4"] = {"workload": "chimera16x16 gauss (first instance), beta=4, chi=32, 1 sweep, beam=1024",
+                         "mixed": b4[prec], "fp64": b4[spg.SPG_FP64],
+                         "equal_best_energy": b4[prec]["best_energy_fixed"] == b4[spg.SPG_FP64]["best_energy_fixed"],
+                         "speedup_mixed_vs_fp64": b4[spg.SPG_FP64]["tts_s"] / b4[prec]["tts_s"],
+                         "max_logmarg_err": rcb.max_logmarg_err()}
 
     # batching pattern on uneven instances: 64 Chimera L ~ U{6..12}, +-1,
     # chi in {16, 32} per instance, beam 512, all in flight together
@@ -421,6 +584,10 @@ def main():
             "equal_best_energy": kres[prec]["best_energy_fixed"] == kres[spg.SPG_FP64]["best_energy_fixed"],
             "speedup_mixed_vs_fp64": kres[spg.SPG_FP64]["tts_s"] / kres[prec]["tts_s"]}
 
+    # the learned warm start of the variational compression
+    if WORKLOAD["L"] == 16 and not args.no_warm:
+        line["warm_start"] = warm_start_leg(spg, ctx, torch)
+
     # one extra solve with per-kernel device times (graph-captured event
     # nodes; not part of the timed steps): the roofline of the top kernel
     kern = kernel_profile(spg, ctx, probs[0], prm)
@@ -428,21 +595,33 @@ def main():
     top = sorted(kern.items(), key=lambda kv: -kv[1][1])
     line["kernels"] = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4),
                            "avg_us": round(1e3 * v[1] / v[0], 2)} for k, v in top[:10]}
-    clk_mhz = 2070.0
-    # ALU peaks from unit counts: 152 SMs x (128 FP32 | 2 FP64) FMA/clk x 2 flop x clock
-    alu_peak = 152 * (128 if prec == spg.SPG_MIXED else 2) * 2 * clk_mhz * 1e6 / 1e12
+    # ALU peaks measured on this device (FMA throughput of all SMs), next to
+    # the unit-count figure at the clock seen during the timed region
+    props = torch.cuda.get_device_properties(local)
+    clk_mhz = line["clocks"].get("sm_max_mhz") or 2070.0
+    peak32 = spg.spg_peak_probe("fp32", stream=stream)
+    peak64 = spg.spg_peak_probe("fp64", stream=stream)
+    line["alu_peaks"] = {"fp32_tflops": peak32, "fp64_tflops": peak64, "sms": props.multi_processor_count,
+                         "fp32_units_tflops": props.multi_processor_count * 128 * 2 * clk_mhz * 1e6 / 1e12,
+                         "source": "measured: k_fma_probe (8 independent FMA chains per thread, 8 blocks of 256 "
+                                   "threads per SM), CUDA events"}
+    alu_peak = peak32 if prec == spg.SPG_MIXED else peak64
     name, (nl, ms_k, fl_k) = next((kv for kv in top if kv[1][2] > 0), top[0])
     achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
     peaks, src = measured_peaks()
     line["roofline"] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                         "frac": achieved / alu_peak, "traffic": NCU_TRAFFIC_BYTES.get(name),
-                        "peak_source": f"derived: 152 SMs x {'128 FP32' if prec == spg.SPG_MIXED else '2 FP64'} "
-                                       f"FMA/clk x 2 x {clk_mhz:.0f} MHz",
+                        "peak_source": f"measured {'FP32' if prec == spg.SPG_MIXED else 'FP64'} FMA throughput "
+                                       f"(k_fma_probe, {props.multi_processor_count} SMs)",
                         "share_of_solve": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
                         "avg_launch_us": 1e3 * ms_k / nl, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                         "peaks_source": src}
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(0)
+        line["cpu_baseline_cfg1"] = {"all_cores": {**cpu_oracle_cfg1(), "cores": len(os.sched_getaffinity(0))},
+                                     "one_thread": {**cpu_oracle_cfg1_one_thread(), "cores": 1},
+                                     "workload": "full oracle solves of 3x3 Chimera +-1, beta 1, chi 16, beam 256 "
+                                                 "(seeds 0, 1)"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

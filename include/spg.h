@@ -44,11 +44,20 @@ extern "C" {
 #define SPG_FP64 0  /* every contraction, SVD and marginal in FP64          */
 #define SPG_MIXED 1 /* FP32 contractions, FP64 marginal normalisation       */
 
+/* SPG_MIXED solves, log Z and marginals run the FP64 path instead when
+ * beta times the largest summed span (max - min) of one site's weight
+ * tables (local, left, up, anti-diagonal) exceeds this: the product of a
+ * site's weight factors may then fall below FP32's normal range (e^-87)
+ * for states that matter, whose conditionals would come out as zero.
+ * spg_info.precision_used reports it.  (Measured: beta = 4 on Gaussian
+ * Chimera cells spans e^-91 .. e^-142, beta = 1 about e^-35.) */
+#define SPG_FP32_WEIGHT_SPAN 80.0
+
 /* Built limits (SPG_EUNSUPPORTED beyond them). */
 #define SPG_MAX_STATES 256    /* states of one cluster (2^8 spins)          */
 #define SPG_MAX_PROJ 16       /* distinct rows/columns of a pairwise table  */
 #define SPG_MAX_CHI 64        /* boundary-MPS bond dimension                */
-#define SPG_MAX_COLS 32       /* grid columns                               */
+#define SPG_MAX_COLS 128      /* grid columns                               */
 #define SPG_MAX_BEAM 4096     /* max_states                                 */
 
 typedef struct spg_ctx spg_ctx;
@@ -68,12 +77,40 @@ typedef struct {
   int32_t svd_iters;   /* subspace iterations of a large truncation; -1 (the
                           default): 6 in SPG_FP64, 2 in SPG_MIXED (FP32
                           accuracy does not improve beyond 2)                */
-  int32_t warm_start;  /* reserved, must be 0                                */
+  int32_t warm_start;  /* 1: start the variational compression of every
+                          boundary row from the network attached with
+                          spg_set_warm_start instead of the SVD zipper (which
+                          stays the fallback for rows the network does not
+                          cover); needs num_sweeps >= 1 (default 0: off)    */
   uint64_t seed;       /* seed of the truncation's start block (default 0)   */
   int32_t merge;       /* 1: merge branches equal on the boundary of the
                           explored region (merge_branches; default 1)        */
-  int32_t reserved[7]; /* must be 0                                          */
+  int32_t fp64_rows;   /* SPG_MIXED: the truncations of the boundary MPSs of
+                          rows 1 .. fp64_rows (the final rows of the bottom-up
+                          sweep; also row 0, which only spg_log_partition
+                          builds, when fp64_rows >= 1) run in FP64 on the
+                          FP32 zipper matrices: the left-canonical QR of the
+                          MPS below, the QRs and the Jacobi SVD; results are
+                          rounded back to FP32.  0: none; -1 (the default):
+                          every row of problems with at most
+                          SPG_FP64_ROWS_AUTO_SITES sites, none above.
+                          Ignored in SPG_FP64.                              */
+  int32_t check_fp64;  /* SPG_MIXED, 1: after the search, compare the
+                          log-conditionals of every returned state along its
+                          path (teacher-forced, site by site) with those from
+                          plain FP64 boundary MPSs; the largest difference is
+                          the result's max_logmarg_err.  Costs a plain FP64
+                          boundary phase per solve (default 0: off).        */
+  int32_t reserved[5]; /* must be 0                                          */
 } spg_params;
+
+/* fp64_rows = -1 truncates every row in FP64 on problems of at most this
+ * many sites: there the truncations are often near-exact (chi close to the
+ * cut's rank), the discarded directions sit at the FP32 noise floor and an
+ * FP32 truncation rotates noise into the kept ones; FP64 rows cost little
+ * on such lattices and much on large ones, where truncation error
+ * dominates. */
+#define SPG_FP64_ROWS_AUTO_SITES 64
 
 /* Per-result diagnostics. */
 typedef struct {
@@ -88,7 +125,15 @@ typedef struct {
   double boundary_lognorm; /* log-norm of the last boundary MPS built        */
   int64_t kernel_launches; /* CUDA kernels this solve enqueued              */
   int32_t jacobi_sweeps_max; /* most sweeps one small Jacobi SVD needed (cap 60) */
-  int32_t reserved;
+  int32_t fp64_rows;       /* boundary rows truncated in FP64 (SPG_MIXED)    */
+  int32_t precision_used;  /* SPG_FP64 when an SPG_MIXED solve ran the FP64
+                              path because its weights exceed FP32's range
+                              (see SPG_FP32_WEIGHT_SPAN), else as asked     */
+  int32_t reserved2;
+  double max_logmarg_err;  /* check_fp64: max over returned states and sites
+                              of |log p_mixed - log p_FP64| / max(1,
+                              |log p_FP64|) of the state's own conditional;
+                              0 in SPG_FP64; NaN when not checked           */
 } spg_info;
 
 /* Library version, major*10000 + minor*100 + patch. */
@@ -147,6 +192,16 @@ int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int3
                       const int32_t* cluster_row, const int32_t* cluster_col,
                       int32_t energy_shift, int32_t node_type, spg_problem** out);
 
+/* New couplings and fields for an Ising problem (same spins, edge list and
+ * clusters as at creation; J [n_edges], h [n_spins] or NULL): the tables
+ * are recomputed and written in place of the old ones, so solves captured
+ * for this problem replay with the new values (a stream of instances of one
+ * structure runs from captured graphs).  Waits for the work already
+ * enqueued on the context and its batch workers.  SPG_EUNSUPPORTED (problem
+ * unchanged) when the new values change the tables' structure (their
+ * distinct rows and columns), SPG_EINEXACT as spg_problem_ising. */
+int spg_problem_update_ising(spg_problem* prob, const double* J, const double* h);
+
 /* Potts form (Eq. 1): sites are the grid cells in row-major order.
  *   d        : [rows*cols] states per site
  *   local_E  : concatenated local tables, site by site (sum d entries)
@@ -190,15 +245,33 @@ int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_
 int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prms,
                     spg_result** out);
 
+/* The 8 lattice transformations solved as one batch (Sec. 3.1: the
+ * example solves the instance on every rotation and reflection of its grid
+ * and keeps the best): transformation k of spg_lattice_site_map applied to
+ * the problem as it was given (Ising form: the clusters' grid positions
+ * move, spins and couplings stay; Potts form: sites move with their local
+ * tables, every pairwise table stays on its renumbered edge), the 8
+ * problems solved concurrently as by spg_solve_batch with the same
+ * parameters, and the result of the first lowest best energy (ties to the
+ * lowest k) returned with its states on the ORIGINAL sites, in that
+ * lattice's order (energy, then its own lexicographic order).  best_k
+ * (may be NULL): the chosen k; best_per_lattice (may be NULL, 8 entries):
+ * every lattice's best energy.  Synchronous.  SPG_EUNSUPPORTED when a
+ * transposed grid exceeds SPG_MAX_COLS. */
+int spg_solve_lattice8(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_result** out,
+                       int32_t* best_k, int64_t* best_per_lattice);
+
 /* Copy the final states out (waits for the solve).  States are sorted by
  * (energy ascending, state lexicographically ascending).
- *   states        : [n_states x n_sites] cluster states, or NULL
- *   energies_fixed: [n_states] int64 energies, or NULL
- *   energies      : [n_states] the same as double (exact below 2^53), or NULL
- *   log_probs     : [n_states] log of the estimated probability, or NULL
+ *   states         : [n_states x n_sites] cluster states, or NULL
+ *   energies_fixed : [n_states] int64 energies, or NULL
+ *   energies       : [n_states] the same as double (exact below 2^53), or NULL
+ *   log_probs      : [n_states] log of the estimated probability, or NULL
+ *   max_logmarg_err: the result's log-marginal error against plain FP64
+ *                    (spg_info.max_logmarg_err), or NULL
  * Call first with all arrays NULL to read n_states and n_sites. */
 int spg_result_get(spg_result* res, int32_t* n_states, int32_t* n_sites, uint16_t* states,
-                   int64_t* energies_fixed, double* energies, double* log_probs);
+                   int64_t* energies_fixed, double* energies, double* log_probs, double* max_logmarg_err);
 int spg_result_info(spg_result* res, spg_info* info);
 void spg_result_destroy(spg_result* res);
 
@@ -280,13 +353,127 @@ int spg_tc_product(spg_ctx* ctx, const float* M, int32_t m, int32_t n, const flo
  * Arguments as spg_truncate (M, V, US, sigma are DEVICE pointers owned by
  * the caller), on the current device; cuda_stream is a cudaStream_t (NULL:
  * the legacy default stream).  Returns after the stream has finished the
- * work.  SPG_EINVAL for NULL pointers or inconsistent sizes, SPG_ECUDA if a
- * CUDA call fails. */
+ * work (it waits for the stream), so a stream that is being captured is
+ * rejected with SPG_EINVAL before anything is enqueued on it.  SPG_EINVAL
+ * for NULL pointers or inconsistent sizes, SPG_ECUDA if a CUDA call fails. */
 #define SPG_TRUNC_STATIC_MAX_DIM 256
 #define SPG_TRUNC_STATIC_MAX_KEEP 32
 #define SPG_TRUNC_STATIC_SCRATCH_BYTES 1181696 /* 147712 doubles, 1.13 MiB */
 int spg_truncate_static(const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters, double* V,
                         double* US, double* sigma, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start of the variational compression.  The paper compresses
+ * every boundary MPS by num_sweeps variational sweeps started from the SVD
+ * zipper (Sec. 3.1, MpsParameters(bond_dim, num_sweeps)).  The warm start
+ * predicts the starting MPS of row r from the couplings near that row with a
+ * small MLP trained on the boundary MPSs this library itself produces; the
+ * sweeps then refine it.  The paper has no learned part: these calls are
+ * an addition of this library, and the zipper remains the default.
+ * ------------------------------------------------------------------------ */
+
+/* Inputs of the network for the sites of boundary row `row` of an Ising
+ * problem (clusters of <= 8 spins): out[j*SPG_WS_FEATURES + f], host array
+ * of cols * SPG_WS_FEATURES floats owned by the caller.  For every cluster
+ * (i, k) with i in row .. row+2 and k in j-2 .. j+2 (zeros outside the
+ * grid), i outer, SPG_WS_PER_CLUSTER numbers: the couplings between the
+ * cluster's spin positions q1 < q2 (28 slots in lexicographic order; the
+ * position of a spin is its rank in the cluster, the order of the state
+ * encoding), the fields of the 8 positions, and per position the summed
+ * couplings to the cluster below (8) and to the cluster on the right (8).
+ * Then j == 0, j == cols-1, j == 1, j == cols-2, min(rows - row, 8) / 8,
+ * then zeros.  Host only.  SPG_EUNSUPPORTED for Potts problems. */
+#define SPG_WS_FEATURES 800
+#define SPG_WS_PER_CLUSTER 52
+int spg_warm_features(const spg_problem* prob, int32_t row, float* out);
+
+/* The boundary MPS B_row that the method builds (the zipper, then
+ * prm->num_sweeps sweeps, at prm's precision), written to the DEVICE array
+ * out: cols sites, each padded to [16][chi][chi] (entry (s, a, a') at
+ * (s*chi + a)*chi + a', zeros beyond the site's dims), double in SPG_FP64
+ * and float in SPG_MIXED.  fix_signs = 1 negates every left-bond row of
+ * site j >= 1 whose largest-magnitude entry (first on ties, entries in
+ * (s, a') order) is negative, together with the matching column of site
+ * j-1, from the last site down (the same MPS in the sign gauge of the
+ * zipper's SVDs).  dims (host, may be NULL): cols x {p, chi_l, chi_r}.
+ * 1 <= row < rows; row = 0 exports every row 1 .. rows-1, each as it is
+ * finished, to out [rows-1][cols][16][chi][chi] (row r at index r-1) with
+ * dims [rows-1][cols][3].  Synchronous. */
+int spg_boundary_export(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, int32_t row,
+                        int32_t fix_signs, void* out, int32_t* dims);
+
+/* A three-layer perceptron y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 with
+ * its training state, on the context's device and stream.  Parameters are
+ * one flat FP32 array [W1 (hidden x in) | b1 | W2 (hidden x hidden) | b2 |
+ * W3 (out x hidden) | b3], row-major, initialised from seed with
+ * uniform(+-1/sqrt(fan_in)) weights and zero biases.  Limits: n_in <= 4096,
+ * n_hidden <= 1024, n_out <= 65536. */
+typedef struct spg_mlp spg_mlp;
+int spg_mlp_create(spg_ctx* ctx, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, spg_mlp** out);
+void spg_mlp_destroy(spg_mlp* mlp);
+/* Number of parameters; copy them out to / in from host arrays (either may
+ * be NULL; a set resets the Adam moments and refreshes the BF16 copy). */
+int64_t spg_mlp_num_params(const spg_mlp* mlp);
+int spg_mlp_params(spg_mlp* mlp, float* get_host, const float* set_host);
+/* Forward pass of n samples: X [n x n_in] -> Y [n x n_out], DEVICE arrays
+ * owned by the caller.  bf16 = 1: weights and layer inputs rounded to
+ * BF16, products accumulated in FP32 (inference); 0: FP32.  Synchronous. */
+int spg_mlp_forward(spg_mlp* mlp, const float* X, int32_t n, float* Y, int32_t bf16);
+/* Loss 0.5/n * sum (Y - T)^2 over n samples (X [n x n_in], T [n x n_out],
+ * DEVICE) and its gradient, in the flat parameter layout, to grad_host
+ * (host array of spg_mlp_num_params floats, may be NULL).  FP32. */
+int spg_mlp_loss_grad(spg_mlp* mlp, const float* X, const float* T, int32_t n, double* loss, float* grad_host);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
+ * on minibatches of `batch` samples drawn with replacement from the n
+ * samples (X, T as in spg_mlp_loss_grad) by a counter-based hash of
+ * (seed, step, slot).  *loss (may be NULL) = the mean minibatch loss of the
+ * last min(steps, 50) steps.  FP32.  Synchronous. */
+int spg_mlp_train(spg_mlp* mlp, const float* X, const float* T, int64_t n, int32_t batch, int32_t steps, double lr,
+                  uint64_t seed, double* loss);
+
+/* Attach a network (n_in = SPG_WS_FEATURES, n_out = 16 * chi * chi) for
+ * solves with params.warm_start = 1 on this context (NULL detaches).  The
+ * context does not own it; keep it alive while such solves run.  Rows whose
+ * sites the network does not cover (another chi, a Potts problem) fall
+ * back to the SVD zipper. */
+int spg_set_warm_start(spg_ctx* ctx, spg_mlp* mlp);
+
+/* Sweeps to fidelity: build the boundary MPSs of rows rows-1 .. row+1 as a
+ * solve does, then start row `row` from the SVD zipper (init = 0) or from
+ * the attached network (init = 1) and run n_sweeps single variational
+ * sweeps, writing after sweep k (1-based) log_overlap[k-1] =
+ * log <phi_k | W psi> with psi = B_{row+1} and phi_k normalised.  init = 2
+ * runs both on the same B_{row+1}: the zipper's trace to log_overlap[0 ..
+ * n_sweeps), the network's to log_overlap[n_sweeps .. 2 n_sweeps).  The
+ * sweeps maximise this overlap, so F_k / F_best = exp(2 (log_overlap[k-1]
+ * - best)) is the fidelity relative to the best compression reached.
+ * Synchronous. */
+int spg_sweep_trace(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, int32_t row, int32_t init,
+                    int32_t n_sweeps, double* log_overlap);
+
+/* Failure detection (no counterpart in the paper).  Every wait inside the
+ * library's kernels is bounded: on a timeout the kernel records the event,
+ * finishes its copies in flight, releases its tensor memory and returns, and
+ * the call or result reports SPG_ETIMEOUT.
+ *
+ * spg_check_bounded_wait runs that failure path on purpose: one kernel
+ * waits `polls` polls on an mbarrier that nothing completes.  Returns
+ * SPG_ETIMEOUT (the expected outcome, message in spg_last_error), after
+ * which the context stays usable; any other code means the bounded wait
+ * did not report its timeout.
+ *
+ * spg_inject_alloc_failure(after): test hook, process-wide; the (after+1)-th
+ * device workspace or problem-table allocation from now on fails as if the
+ * device were out of memory (the call returns SPG_ENOMEM); after < 0 turns
+ * the hook off.  Host only. */
+int spg_check_bounded_wait(spg_ctx* ctx, int64_t polls);
+int spg_inject_alloc_failure(int32_t after);
+
+/* Measured ALU peak of the current device (measurement aid, no counterpart
+ * in the paper): the fused multiply-add throughput of all SMs, kind 0 FP32,
+ * kind 1 FP64, in TFLOP/s (2 flops per FMA), timed with CUDA events on
+ * cuda_stream (NULL: the legacy default stream).  Synchronous. */
+int spg_peak_probe_stream(void* cuda_stream, int32_t kind, double* tflops);
 
 /* Per-kernel device timing (tracing aid).  spg_profile(ctx, 1) starts
  * recording one CUDA event before every kernel the library launches;

@@ -45,7 +45,7 @@ class spg_info(C.Structure):
                 ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
                 ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
                 ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("fp64_rows", C.c_int32),
-                ("max_logmarg_err", C.c_double)]
+                ("precision_used", C.c_int32), ("reserved2", C.c_int32), ("max_logmarg_err", C.c_double)]
 
 
 def _load():
@@ -69,6 +69,7 @@ def _load():
                                         C.POINTER(P)]),
         "spg_problem_potts": (C.c_int, [P, I32, I32, pI32, pI64, I32, pI32, pI32, pI64, I32, I32, C.POINTER(P)]),
         "spg_problem_destroy": (None, [P]),
+        "spg_problem_update_ising": (C.c_int, [P, pD, pD]),
         "spg_problem_shape": (C.c_int, [P, pI32, pI32, pI32]),
         "spg_solve": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P)]),
         "spg_solve_batch": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
@@ -92,6 +93,9 @@ def _load():
         "spg_set_warm_start": (C.c_int, [P, P]),
         "spg_sweep_trace": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, I32, pD]),
         "spg_peak_probe_stream": (C.c_int, [P, I32, pD]),
+        "spg_check_bounded_wait": (C.c_int, [P, C.c_int64]),
+        "spg_solve_lattice8": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P), pI32, pI64]),
+        "spg_inject_alloc_failure": (C.c_int, [I32]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
     }
@@ -195,6 +199,17 @@ class Context:
 
     def close(self):
         if self.h:
+            # handles made through this context go first: the garbage
+            # collector may finalise a cycle (a failed test's frame, say) in
+            # any order, and a handle released after its context would read
+            # freed memory
+            for kind in ("result", "problem", "mlp"):
+                for obj in list(_LIVE[kind]):
+                    if getattr(obj, "ctx", None) is self:
+                        try:
+                            obj.close()
+                        except Exception:
+                            pass
             lib.spg_destroy(self.h)
             self.h = None
 
@@ -414,14 +429,16 @@ def spg_warm_features(prob: Problem, row: int) -> np.ndarray:
 def spg_boundary_export(ctx: Context, prob: Problem, prm: spg_params, row: int, fix_signs: bool = True):
     """(sites, dims): the boundary MPS B_row as a device tensor [cols, 16,
     chi, chi] (float64 in SPG_FP64, float32 in SPG_MIXED) and the sites'
-    dims [cols, 3] = (p, chi_l, chi_r)."""
+    dims [cols, 3] = (p, chi_l, chi_r); row 0: every row 1 .. rows-1,
+    [rows-1, cols, 16, chi, chi] and [rows-1, cols, 3]."""
     import torch
     chi = prm.chi
     dtype = torch.float64 if prm.precision == SPG_FP64 else torch.float32
+    lead = (prob.rows - 1, prob.cols) if row == 0 else (prob.cols,)
     with torch.cuda.device(ctx.device):
-        out = torch.empty((prob.cols, 16, chi, chi), dtype=dtype, device=f"cuda:{ctx.device}")
+        out = torch.empty(lead + (16, chi, chi), dtype=dtype, device=f"cuda:{ctx.device}")
         torch.cuda.synchronize()
-        dims = np.zeros((prob.cols, 3), np.int32)
+        dims = np.zeros(lead + (3,), np.int32)
         ctx.check(lib.spg_boundary_export(ctx.h, prob.h, C.byref(prm), row, int(bool(fix_signs)),
                                           C.c_void_p(out.data_ptr()), _ptr(dims, C.c_int32)))
     return out, dims
@@ -515,8 +532,9 @@ def spg_set_warm_start(ctx: Context, mlp) -> None:
 
 def spg_sweep_trace(ctx: Context, prob: Problem, prm: spg_params, row: int, init: int, n_sweeps: int) -> np.ndarray:
     """log <phi_k | W psi> after each of n_sweeps sweeps of row `row`
-    started from the zipper (init 0) or the attached network (init 1)."""
-    out = np.zeros(n_sweeps, np.float64)
+    started from the zipper (init 0) or the attached network (init 1);
+    init 2: both, [2, n_sweeps] (zipper first)."""
+    out = np.zeros((2, n_sweeps) if init == 2 else n_sweeps, np.float64)
     ctx.check(lib.spg_sweep_trace(ctx.h, prob.h, C.byref(prm), row, init, n_sweeps, _ptr(out, C.c_double)))
     return out
 
@@ -529,3 +547,31 @@ def spg_peak_probe(kind: str, stream=None) -> float:
     if rc != SPG_OK:
         raise SpgError(rc, "spg_peak_probe failed")
     return v.value
+
+
+def spg_check_bounded_wait(ctx: Context, polls: int) -> int:
+    """Return code of the bounded-wait failure path (SPG_ETIMEOUT expected)."""
+    return int(lib.spg_check_bounded_wait(ctx.h, polls))
+
+
+def spg_inject_alloc_failure(after: int) -> None:
+    """Test hook: the (after+1)-th device allocation from now fails (-1: off)."""
+    lib.spg_inject_alloc_failure(after)
+
+
+def spg_solve_lattice8(ctx: Context, prob: Problem, prm: spg_params):
+    """(result, best_k, best energy of every lattice): the 8 lattice
+    transformations solved as one batch, best of 8, states on the original
+    sites."""
+    out = C.c_void_p()
+    k = C.c_int32()
+    per = np.zeros(8, np.int64)
+    ctx.check(lib.spg_solve_lattice8(ctx.h, prob.h, C.byref(prm), C.byref(out), C.byref(k), _ptr(per, C.c_int64)))
+    return Result(ctx, out), k.value, per
+
+
+def spg_problem_update_ising(prob: Problem, J, h=None) -> None:
+    """New couplings (and fields) of the same structure, written in place."""
+    J = np.ascontiguousarray(J, np.float64)
+    h = None if h is None else np.ascontiguousarray(h, np.float64)
+    prob.ctx.check(lib.spg_problem_update_ising(prob.h, _ptr(J, C.c_double), _ptr(h, C.c_double)))

@@ -4,6 +4,7 @@
 // Paper: Sec. 2 and Fig. 1(c)-(d) (PEPS of the Boltzmann distribution,
 // approximate contraction with boundary MPSs), Sec. 3.1 (MpsParameters
 // bond_dim; MpsContractor(SVDTruncate, ...)).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -991,6 +992,14 @@ __global__ void k_fill_start(T* Zt, int n, int s, uint64_t seed, int identity) {
   }
 }
 
+// dst[e] = (To) src[e]: a contiguous block changes precision (the FP64
+// truncation of the final boundary rows in the mixed mode).
+template <typename From, typename To>
+__global__ void k_convert(const From* __restrict__ src, To* __restrict__ dst, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (To)src[e];
+}
+
 template <typename T>
 __global__ void k_set_strided(T* base, size_t stride, int count, T v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) base[e * stride] = v;
@@ -1118,6 +1127,17 @@ cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int
     k_gemm<T, false, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
   return cudaGetLastError();
 }
+
+template <typename From, typename To>
+cudaError_t launch_convert(const From* src, To* dst, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 8);
+  count_launches("k_convert", st);
+  k_convert<From, To><<<(unsigned)blocks, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st) {

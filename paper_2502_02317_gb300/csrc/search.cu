@@ -382,7 +382,7 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
 __global__ void k_parent_keys(DevTables tb, int site, DevSearch ds, int cur, int merge) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ds.n_beam[cur]) return;
-  unsigned long long k[KEYW] = {0, 0, 0, 0};
+  unsigned long long k[KEYW] = {};
   if (merge) {
     const int* ks = tb.keys + site * (MAXKEY + 1);
     const int n = ks[0], bits = *tb.kshift;

@@ -15,6 +15,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -57,6 +58,7 @@ struct spg_ctx {
     long long launches = 0;
   };
   std::vector<Graph> graphs;
+  spg_mlp* warm = nullptr;  // warm-start network (not owned)
 };
 
 struct spg_problem {
@@ -77,8 +79,24 @@ struct spg_problem {
   std::vector<int> keys;   // [n][MAXKEY+1]
   int kbits = 1;
   double min_sum = 0.0;  // sum of the minima of all local and reduced tables
+  // largest span over sites of the site's weight factors (local, left, up,
+  // anti-diagonal tables: max - min, summed), units of 2^-shift
+  double wspan = 0.0;
   void* dev = nullptr;
+  size_t o_E = 0, o_RL = 0, o_RU = 0, o_RA = 0;  // device offsets of the value tables
   DevTables tb{};
+  // Ising problems: per site the SPG_WS_PER_CLUSTER coupling numbers of the
+  // warm-start features (empty for Potts problems)
+  std::vector<double> wsblk;
+  // the caller's inputs, kept to build the problem on transformed lattices
+  struct Raw {
+    bool potts = false;
+    int n_spins = 0;
+    std::vector<int32_t> ei, ej, cos, crow, ccol;  // Ising
+    std::vector<double> J, h;                      // Ising (h empty: no fields)
+    std::vector<int32_t> d, em, en;                // Potts
+    std::vector<int64_t> local, pair;              // Potts
+  } raw;
 };
 
 struct spg_result {
@@ -92,6 +110,9 @@ struct spg_result {
   int* d_diag = nullptr;  // near_ties, err, deg_cuts
   double* d_cand = nullptr;
   unsigned long long* d_stamp = nullptr;  // GPU timer at start, phase boundary, end (ns)
+  double* d_err = nullptr;                // log-marginal error against FP64 (check_fp64)
+  int fp64_rows = 0;
+  int precision_used = 0;
   float ms_boundary = 0.f, ms_search = 0.f;
   double lognorm = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -113,6 +134,57 @@ int fail(spg_ctx* ctx, int code, const std::string& msg) {
     if (e_ != cudaSuccess)                                                                  \
       return fail(ctx, SPG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
   } while (0)
+
+}  // namespace
+std::atomic<int>& spg::alloc_failure_countdown() {
+  static std::atomic<int> c{-1};
+  return c;
+}
+namespace {
+
+// A device allocation, or the injected failure of the test hook.
+cudaError_t device_alloc(void** p, size_t bytes) {
+  int c = alloc_failure_countdown().load();
+  while (c >= 0 && !alloc_failure_countdown().compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 0) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+// ---------------------------------------------------------------- warm-start inputs
+// Index of the pair q1 < q2 of 8 spin positions in lexicographic order.
+int ws_pair_slot(int q1, int q2) { return q1 * 8 - q1 * (q1 + 1) / 2 + (q2 - q1 - 1); }
+
+// Inputs of the sites of boundary row r (include/spg.h spg_warm_features):
+// the coupling blocks of the clusters in rows r .. r+2, columns j-2 .. j+2,
+// then five position features, then zeros.
+void ws_features(const spg_problem* P, int r, float* out) {
+  const int rows = P->rows, cols = P->cols;
+  for (int j = 0; j < cols; ++j) {
+    float* x = out + (size_t)j * SPG_WS_FEATURES;
+    std::fill(x, x + SPG_WS_FEATURES, 0.f);
+    int o = 0;
+    for (int i = r; i < r + 3; ++i)
+      for (int k = j - 2; k <= j + 2; ++k, o += SPG_WS_PER_CLUSTER)
+        if (i >= 0 && i < rows && k >= 0 && k < cols)
+          for (int f = 0; f < SPG_WS_PER_CLUSTER; ++f)
+            x[o + f] = (float)P->wsblk[(size_t)(i * cols + k) * SPG_WS_PER_CLUSTER + f];
+    x[o + 0] = j == 0 ? 1.f : 0.f;
+    x[o + 1] = j == cols - 1 ? 1.f : 0.f;
+    x[o + 2] = j == 1 ? 1.f : 0.f;
+    x[o + 3] = j == cols - 2 ? 1.f : 0.f;
+    x[o + 4] = (float)(std::min(rows - r, 8) / 8.0);
+  }
+}
+
+// The attached network when a solve with these parameters starts its rows
+// from it: warm_start set, an Ising problem, and sites of this chi.
+const spg_mlp* warm_of(const spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
+  const spg_mlp* m = ctx->warm;
+  if (!prm->warm_start || !m || P->wsblk.empty()) return nullptr;
+  if (m->n_in != SPG_WS_FEATURES || m->n_out != MAXP * prm->chi * prm->chi) return nullptr;
+  return m;
+}
 
 // ---------------------------------------------------------------- S1 helpers
 struct EdgeTab {
@@ -162,7 +234,8 @@ bool reduce_full(const std::vector<int64_t>& T, int dm, int dn, EdgeTab& out) {
 // order of first occurrence (x ascending); the pairwise energy between class
 // representatives (first states) is exact because classes only merge states
 // with equal table rows.
-int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, EdgeTab>& edges) {
+int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, EdgeTab>& edges,
+                   bool upload = true) {
   const int n = P->n, dmax = P->dmax, rows = P->rows, cols = P->cols;
   auto at = [&](int i, int j) { return (i >= 0 && i < rows && j >= 0 && j < cols) ? i * cols + j : -1; };
   auto edge = [&](int s, int t) -> const EdgeTab* {
@@ -295,6 +368,43 @@ int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, E
     for (int u = 0; u < dm[D_DD]; ++u) P->gD[(size_t)s * MAXP + u] = G[s].P[D[s].rep[u]];
   }
   P->min_sum = mins;
+  double wspan = 0.0;
+  for (int s = 0; s < n; ++s) {
+    const int* dm = &P->dims[(size_t)s * DIMW];
+    auto span = [](int64_t lo, int64_t hi) { return hi >= lo ? (double)(hi - lo) : 0.0; };
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
+    for (int x = 0; x < P->d[s]; ++x) {
+      lo = std::min(lo, P->E[(size_t)s * dmax + x]);
+      hi = std::max(hi, P->E[(size_t)s * dmax + x]);
+    }
+    double t = span(lo, hi);
+    lo = INT64_MAX, hi = INT64_MIN;
+    for (int l = 0; l < dm[D_DL]; ++l)
+      for (int h = 0; h < dm[D_NL]; ++h) {
+        const int64_t v = P->RL[(size_t)s * P->lstride + (size_t)l * MAXP + h];
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+    t += span(lo, hi);
+    lo = INT64_MAX, hi = INT64_MIN;
+    for (int u = 0; u < dm[D_DU]; ++u)
+      for (int h = 0; h < dm[D_NU]; ++h) {
+        const int64_t v = P->RU[(size_t)s * 256 + u * 16 + h];
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+    t += span(lo, hi);
+    lo = INT64_MAX, hi = INT64_MIN;
+    for (int a = 0; a < dm[D_NRL]; ++a)
+      for (int u = 0; u < dm[D_DU]; ++u) {
+        const int64_t v = P->RA[(size_t)s * 256 + a * 16 + u];
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+    t += span(lo, hi);
+    wspan = std::max(wspan, t);
+  }
+  P->wspan = wspan;
   // states grouped by PL
   P->xsL.assign((size_t)n * dmax, 0);
   P->xoffL.assign((size_t)n * (MAXP + 1), 0);
@@ -331,6 +441,7 @@ int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, E
     P->keys[(size_t)s * (MAXKEY + 1)] = (int)ks.size();
     for (size_t q = 0; q < ks.size(); ++q) P->keys[(size_t)s * (MAXKEY + 1) + 1 + q] = ks[q];
   }
+  if (!upload) return SPG_OK;  // host tables only (spg_problem_update_ising)
   // upload
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -345,8 +456,16 @@ int finish_problem(spg_ctx* ctx, spg_problem* P, std::map<std::pair<int, int>, E
                o_RA = take(sizeof(int64_t) * n * 256), o_gD = take((size_t)n * MAXP),
                o_xs = take(sizeof(int16_t) * nd), o_xo = take(sizeof(int) * n * (MAXP + 1)),
                o_k = take(sizeof(int) * n * (MAXKEY + 1)), o_kb = take(sizeof(int));
+  P->o_E = o_E;
+  P->o_RL = o_RL;
+  P->o_RU = o_RU;
+  P->o_RA = o_RA;
   CK(cudaSetDevice(ctx->device));
-  CK(cudaMalloc(&P->dev, off));
+  if (device_alloc(&P->dev, off) != cudaSuccess) {
+    cudaGetLastError();
+    P->dev = nullptr;
+    return fail(ctx, SPG_ENOMEM, "problem tables: device allocation failed");
+  }
   P->dev_bytes = off;
   char* base = (char*)P->dev;
   cudaStream_t st = ctx->stream;
@@ -417,7 +536,7 @@ int ensure_arena(spg_ctx* ctx, size_t bytes) {
   if (ctx->arena) CK(cudaFree(ctx->arena));
   ctx->arena = nullptr;
   ctx->arena_bytes = 0;
-  cudaError_t e = cudaMalloc(&ctx->arena, bytes);
+  cudaError_t e = device_alloc((void**)&ctx->arena, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, SPG_ENOMEM, "device workspace allocation failed");
@@ -485,7 +604,40 @@ struct BoundaryBufs {
   double* sdbl;
   float* tcw;  // tensor-core product workspace (FP32 solves on large zipper matrices)
   size_t tcw_elems;
+  // FP64 truncation of the final rows in the mixed mode (fp64 > 0, T = float):
+  // the zipper matrix, V, US, the truncation's work, one MPS row and the
+  // left-canonical scratch, all in FP64
+  int fp64 = 0;
+  double *Md = nullptr, *Vd = nullptr, *USd = nullptr, *svdwd = nullptr, *rowd = nullptr, *lcd = nullptr;
+  size_t svdwd_elems = 0;
+  // warm start: the network, its inputs [cols][SPG_WS_FEATURES], outputs
+  // [cols][16 chi chi] and inference scratch
+  const spg_mlp* ws = nullptr;
+  float *wsX = nullptr, *wsY = nullptr, *wswork = nullptr;
+  // export of every row as it is finished (rows 1 ..): padded sites
+  // [rows-1][cols][16][chi][chi], sign gauge when exp_fix
+  T* exp_out = nullptr;
+  int exp_fix = 0;
 };
+
+// Boundary rows whose truncations run in FP64 in the mixed mode: rows 1 ..
+// fp64 (and row 0 when fp64 >= 1); none in the FP64 mode, where every row is.
+template <typename T>
+int fp64_rows_of(const spg_params* prm, const spg_problem* P) {
+  if (sizeof(T) == sizeof(double)) return 0;
+  if (prm->fp64_rows >= 0) return prm->fp64_rows;
+  return P->n <= SPG_FP64_ROWS_AUTO_SITES ? P->rows : 0;
+}
+
+bool fp64_row(int fp64, int r) { return fp64 >= 1 && r <= fp64; }
+
+// Whether a solve in SPG_MIXED runs the FP64 path instead: when the weight
+// factors of one site may multiply down to e^-SPG_FP32_WEIGHT_SPAN, states
+// that matter can get FP32 weights below the normal range (e^-87) and their
+// conditionals come out as zero.
+bool fp32_range_exceeded(const spg_problem* P, const spg_params* prm) {
+  return prm->precision == SPG_MIXED && prm->beta * std::ldexp(P->wspan, -P->shift) > SPG_FP32_WEIGHT_SPAN;
+}
 
 // Tensor-core workspace of a problem's largest zipper matrix (FP32 only).
 template <typename T>
@@ -497,7 +649,7 @@ size_t tc_work(const spg_problem* P, int chi) {
 }
 
 template <typename T>
-size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
+size_t boundary_bytes(const spg_problem* P, const Plan& pl, int fp64 = 0, const spg_mlp* ws = nullptr) {
   const int chi = pl.chi;
   const size_t sites = (size_t)(P->rows + 1) * P->cols;
   size_t b = 0;
@@ -523,12 +675,25 @@ size_t boundary_bytes(const spg_problem* P, const Plan& pl) {
   add(sizeof(T) * sweep_work_elems<T>(P->cols, chi, P->bmax));
   add(sizeof(double) * 4);
   add(sizeof(float) * tc_work<T>(P, chi));
+  if (fp64 > 0 && sizeof(T) == sizeof(float)) {
+    add(sizeof(double) * mmax * nmax);
+    add(sizeof(double) * nmax * chi);
+    add(sizeof(double) * mmax * chi);
+    add(sizeof(double) * truncated_svd_work((int)mmax, (int)nmax, chi));
+    add(sizeof(double) * P->cols * pl.stride);
+    add(sizeof(double) * (size_t)MAXP * chi * chi);
+  }
+  if (ws) {
+    add(sizeof(float) * P->cols * SPG_WS_FEATURES);
+    add(sizeof(float) * P->cols * (size_t)MAXP * chi * chi);
+    add(sizeof(float) * mlp_infer_elems(ws, P->cols));
+  }
   return b + 4096;
 }
 
 template <typename T>
 int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar, BoundaryBufs<T>& bb,
-                   bool init = true) {
+                   bool init = true, int fp64 = 0, const spg_mlp* ws = nullptr) {
   const int chi = pl.chi;
   const size_t sites = (size_t)(P->rows + 1) * P->cols;
   bb.mps.A = ar.get<T>(sites * pl.stride);
@@ -560,6 +725,24 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   bb.tcw_elems = tc_work<T>(P, chi);
   bb.tcw = bb.tcw_elems ? ar.get<float>(bb.tcw_elems) : nullptr;
   if (!bb.sdbl || (bb.tcw_elems && !bb.tcw)) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  bb.fp64 = sizeof(T) == sizeof(float) ? fp64 : 0;
+  if (bb.fp64 > 0) {
+    bb.Md = ar.get<double>(mmax * nmax);
+    bb.Vd = ar.get<double>(nmax * chi);
+    bb.USd = ar.get<double>(mmax * chi);
+    bb.svdwd_elems = truncated_svd_work((int)mmax, (int)nmax, chi);
+    bb.svdwd = ar.get<double>(bb.svdwd_elems);
+    bb.rowd = ar.get<double>((size_t)P->cols * pl.stride);
+    bb.lcd = ar.get<double>((size_t)MAXP * chi * chi);
+    if (!bb.lcd) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  }
+  bb.ws = ws;
+  if (ws) {
+    bb.wsX = ar.get<float>((size_t)P->cols * SPG_WS_FEATURES);
+    bb.wsY = ar.get<float>((size_t)P->cols * MAXP * chi * chi);
+    bb.wswork = ar.get<float>(mlp_infer_elems(ws, P->cols));
+    if (!bb.wswork) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  }
   if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * sites * 3, cudaMemcpyHostToDevice, st));
@@ -568,7 +751,83 @@ int carve_boundary(spg_ctx* ctx, const spg_problem* P, const Plan& pl, Arena& ar
   return SPG_OK;
 }
 
-// Boundary MPSs B_r for r = rows-1 .. down_to (S2-S3).
+// Row r of the boundary MPSs from B_{r+1} (S3): the left-canonical QR of
+// B_{r+1}, then either the zipper (MPO site by MPO site, right to left, with
+// the truncated SVD of each zipper matrix) or, with `warm`, the sites the
+// network predicts from the couplings near the row (the starting point of
+// the variational compression that follows).
+template <typename T>
+int build_row(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const Plan& pl, BoundaryBufs<T>& bb, int r,
+              bool warm) {
+  cudaStream_t st = ctx->stream;
+  const int cols = P->cols;
+  const bool f64 = bb.fp64 > 0 && fp64_row(bb.fp64, r);
+  if constexpr (std::is_same<T, float>::value) {
+    if (f64) {
+      // left-canonical QR of B_{r+1} in FP64 (the row seen as row 0 of a
+      // one-row MPS with the same dims and log-norm slot)
+      T* row = bb.mps.A + (size_t)(r + 1) * cols * pl.stride;
+      const size_t cnt = (size_t)cols * pl.stride;
+      DevMPS<double> md{bb.rowd, pl.stride, bb.dimA_dev + (size_t)(r + 1) * cols * 3, bb.mps.lognorm + r + 1};
+      CK((launch_convert<float, double>(row, bb.rowd, cnt, st)));
+      CK(launch_left_canonical<double>(md, 0, cols, nullptr, bb.lcd, st));
+      CK((launch_convert<double, float>(bb.rowd, row, cnt, st)));
+    }
+  }
+  if (!f64) CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, bb.T1, st));
+  CK(cudaMemcpyAsync(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (warm) {
+    std::vector<float> X((size_t)cols * SPG_WS_FEATURES);
+    ws_features(P, r, X.data());
+    CK(cudaMemcpyAsync(bb.wsX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, st));
+    CK(mlp_infer_bf16(bb.ws, bb.wsX, cols, bb.wswork, bb.wsY, st));
+    CK(launch_ws_scatter<T>(bb.wsY, pl.chi, cols, bb.mps, r, st));
+    CK(cudaStreamSynchronize(st));  // X is released on return
+    return SPG_OK;
+  }
+  CK(launch_set_strided<T>(bb.carry[0], 1, 1, T(1), st));
+  int K = 1, cur = 0;
+  for (int j = cols - 1; j >= 0; --j) {
+    const int s = r * cols + j;
+    const int* dm = &P->dims[(size_t)s * DIMW];
+    const int DL = dm[D_DL], DR = dm[D_DR], DU = dm[D_DU];
+    const int* din = &pl.dimA[((size_t)(r + 1) * cols + j) * 3];
+    const int p = din[0], chiL = din[1], chiR = din[2];
+    const T* Bsite = bb.mps.A + (size_t)((r + 1) * cols + j) * pl.stride;
+    T* out = bb.mps.A + (size_t)(r * cols + j) * pl.stride;
+    CK(launch_zip_matrix<T>(P->tb, bb.wt, Bsite, chiL, p, chiR, bb.carry[cur], DR, K, s, DL, DU, bb.T1, bb.M, st));
+    if (j == 0) {
+      CK(launch_zip_site0<T>(bb.M, DU, K, out, bb.mps.lognorm + r, st));
+    } else {
+      const int m = DL * chiL, n = DU * K;
+      const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
+      const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 2);
+      const uint64_t seed = prm->seed + (uint64_t)s * 7919u;
+      if constexpr (std::is_same<T, float>::value) {
+        if (f64) {
+          // the FP32 zipper matrix truncated in FP64, V and US rounded back
+          CK((launch_convert<float, double>(bb.M, bb.Md, (size_t)m * n, st)));
+          CK(truncated_svd<double>(bb.Md, m, n, keep, iters, seed, bb.Vd, bb.USd, bb.svdwd, bb.svdwd_elems, bb.s1,
+                                   bb.degc, st));
+          CK((launch_convert<double, float>(bb.Vd, bb.V, (size_t)n * keep, st)));
+          CK((launch_convert<double, float>(bb.USd, bb.US, (size_t)m * keep, st)));
+        }
+      }
+      if (!f64)
+        CK(truncated_svd<T>(bb.M, m, n, keep, iters, seed, bb.V, bb.US, bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st,
+                            bb.tcw, bb.tcw_elems));
+      CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1, bb.mps.lognorm + r,
+                             st));
+      cur ^= 1;
+      K = keep;
+    }
+  }
+  return SPG_OK;
+}
+
+// Boundary MPSs B_r for r = rows-1 .. down_to (S2-S4): weights, the trivial
+// B_L, then row by row the zipper (or the network's start when bb.ws is
+// set) and num_sweeps variational sweeps.
 template <typename T>
 int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const Plan& pl, BoundaryBufs<T>& bb,
                  int down_to) {
@@ -580,37 +839,15 @@ int run_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, cons
   // B_L: trivial sites (value 1)
   CK(launch_set_strided<T>(bb.mps.A + (size_t)P->rows * cols * pl.stride, pl.stride, cols, T(1), st));
   for (int r = P->rows - 1; r >= down_to; --r) {
-    CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, bb.T1, st));
-    CK(cudaMemcpyAsync(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(launch_set_strided<T>(bb.carry[0], 1, 1, T(1), st));
-    int K = 1, cur = 0;
-    for (int j = cols - 1; j >= 0; --j) {
-      const int s = r * cols + j;
-      const int* dm = &P->dims[(size_t)s * DIMW];
-      const int DL = dm[D_DL], DR = dm[D_DR], DU = dm[D_DU];
-      const int* din = &pl.dimA[((size_t)(r + 1) * cols + j) * 3];
-      const int p = din[0], chiL = din[1], chiR = din[2];
-      const T* Bsite = bb.mps.A + (size_t)((r + 1) * cols + j) * pl.stride;
-      T* out = bb.mps.A + (size_t)(r * cols + j) * pl.stride;
-      CK(launch_zip_matrix<T>(P->tb, bb.wt, Bsite, chiL, p, chiR, bb.carry[cur], DR, K, s, DL, DU, bb.T1, bb.M,
-                              st));
-      if (j == 0) {
-        CK(launch_zip_site0<T>(bb.M, DU, K, out, bb.mps.lognorm + r, st));
-      } else {
-        const int m = DL * chiL, n = DU * K;
-        const int keep = pl.dimA[((size_t)r * cols + j) * 3 + 1];
-        const int iters = prm->svd_iters >= 0 ? prm->svd_iters : (sizeof(T) == 8 ? 6 : 2);
-        CK(truncated_svd<T>(bb.M, m, n, keep, iters, prm->seed + (uint64_t)s * 7919u, bb.V, bb.US,
-                            bb.svdw, bb.svdw_elems, bb.s1, bb.degc, st, bb.tcw, bb.tcw_elems));
-        CK(launch_zip_write<T>(bb.V, bb.US, DL, chiL, DU, K, keep, out, bb.carry[cur ^ 1], bb.s1,
-                               bb.mps.lognorm + r, st));
-        cur ^= 1;
-        K = keep;
-      }
-    }
+    int rc = build_row<T>(ctx, P, prm, pl, bb, r, bb.ws != nullptr);
+    if (rc) return rc;
     if (prm->num_sweeps > 0)
       CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, r, cols, pl.dimA.data(), P->dims.data(), P->d.data(),
                                P->gD.data(), prm->num_sweeps, bb.swork, bb.sdbl, st));
+    // the row as finished, before the next row's left-canonical QR changes its gauge
+    if (bb.exp_out && r >= 1)
+      CK(launch_export_row<T>(bb.mps, r, cols, pl.chi, bb.exp_out + (size_t)(r - 1) * cols * MAXP * pl.chi * pl.chi,
+                              bb.dimA_dev + (size_t)r * cols * 3, bb.exp_fix, st));
   }
   return SPG_OK;
 }
@@ -712,8 +949,12 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (prm->num_sweeps < 0 || prm->num_sweeps > 16) return fail(ctx, SPG_EINVAL, "num_sweeps outside 0..16");
   if (prm->precision != SPG_FP64 && prm->precision != SPG_MIXED) return fail(ctx, SPG_EINVAL, "bad precision");
   if (prm->svd_iters < -1 || prm->svd_iters > 64) return fail(ctx, SPG_EINVAL, "svd_iters outside -1..64");
-  if (prm->warm_start != 0) return fail(ctx, SPG_EUNSUPPORTED, "warm start is not built in this version");
+  if (prm->warm_start != 0 && prm->warm_start != 1) return fail(ctx, SPG_EINVAL, "warm_start must be 0 or 1");
+  if (prm->warm_start && prm->num_sweeps < 1)
+    return fail(ctx, SPG_EINVAL, "warm_start needs num_sweeps >= 1 (the sweeps refine the network's start)");
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
+  if (prm->fp64_rows < -1) return fail(ctx, SPG_EINVAL, "fp64_rows must be >= -1");
+  if (prm->check_fp64 != 0 && prm->check_fp64 != 1) return fail(ctx, SPG_EINVAL, "check_fp64 must be 0 or 1");
   if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
   return SPG_OK;
 }
@@ -728,6 +969,7 @@ struct OutStage {
   int* diag;  // near_ties, err, degenerate cuts, Jacobi sweeps
   double* cand;  // candidates, log-norm of B_1
   unsigned long long* stamp;  // GPU timer at start, phase boundary, end
+  double* err;  // log-marginal error against FP64 (NaN unless checked)
 };
 
 size_t out_stage_bytes(const spg_problem* P, int cap) {
@@ -772,6 +1014,29 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
   return SPG_OK;
 }
 
+// Teacher-forced log-conditionals of the n (= *o.n) returned states along
+// their paths, site by site, written to out[b][site] (the per-result check
+// against FP64): the search's own right-environment, marginal and update
+// kernels with the selection replaced by each state's own next variable.
+template <typename T>
+int enqueue_forced(spg_ctx* ctx, const spg_problem* P, BoundaryBufs<T>& bb, SearchBufs<T>& sb, const OutStage& o,
+                   double* out) {
+  cudaStream_t st = ctx->stream;
+  DevSearch& ds = sb.ds;
+  const int cols = P->cols;
+  CK(launch_force_init(ds, o.n, 0, st));
+  int cur = 0;
+  for (int s = 0; s < P->n; ++s) {
+    const int i = s / cols, j = s % cols;
+    if (j == 0) CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, i, ds, sb.bt, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    CK(launch_force(s, ds, cur, o.states, out, st));
+    CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
+    cur ^= 1;
+  }
+  return SPG_OK;
+}
+
 // A solve is a fixed sequence of stream operations given the problem, the
 // parameters and the workspace (everything data-dependent lives on the
 // device), so it is captured into one CUDA graph on its second occurrence and
@@ -786,14 +1051,20 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   cudaStream_t st = ctx->stream;
   const int chi = prm->chi, cap = prm->beam;
   Plan pl = make_plan(P, chi, 1);
-  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi) + out_stage_bytes(P, cap);
+  const int f64 = fp64_rows_of<T>(prm, P);
+  const spg_mlp* ws = warm_of(ctx, P, prm);
+  const bool check = std::is_same<T, float>::value && prm->check_fp64 != 0;
+  const size_t lcn = (size_t)cap * P->n;  // one log-conditional per (state, site)
+  size_t need = boundary_bytes<T>(P, pl, f64, ws) + search_bytes<T>(P, cap, chi) + out_stage_bytes(P, cap);
+  if (check) need += boundary_bytes<double>(P, pl) + search_bytes<double>(P, cap, chi) + 2 * sizeof(double) * lcn + 4096;
   int rc = ensure_arena(ctx, need);
   if (rc) return rc;
   Arena ar{ctx->arena, 0, ctx->arena_bytes};
   BoundaryBufs<T> bb;
   SearchBufs<T> sb;
-  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false))) return rc;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false, f64, ws))) return rc;
   if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false))) return rc;
+  R->fp64_rows = std::min(f64, std::max(0, P->rows - 1));
   OutStage o;
   o.states = ar.get<uint16_t>((size_t)cap * P->n);
   o.E = ar.get<int64_t>(cap);
@@ -802,13 +1073,32 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   o.diag = ar.get<int>(4);
   o.cand = ar.get<double>(2);
   o.stamp = ar.get<unsigned long long>(4);
-  if (!o.stamp) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  o.err = ar.get<double>(1);
+  if (!o.err) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  // the plain FP64 boundary and search buffers of the check
+  BoundaryBufs<double> bb64;
+  SearchBufs<double> sb64;
+  double *lc_mixed = nullptr, *lc_fp64 = nullptr;
+  if (check) {
+    if ((rc = carve_boundary<double>(ctx, P, pl, ar, bb64, false))) return rc;
+    if ((rc = carve_search<double>(ctx, P, cap, chi, ar, sb64, false))) return rc;
+    bb64.wd = bb64.wt;
+    lc_mixed = ar.get<double>(lcn);
+    lc_fp64 = ar.get<double>(lcn);
+    if (!lc_fp64) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  }
   // plan dims: host data, uploaded outside any capture
   CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
+  if (check)
+    CK(cudaMemcpyAsync(bb64.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
 
   spg_ctx::Graph* g = nullptr;
-  for (auto& e : ctx->graphs)
+  // a warm-started solve uploads each row's network inputs from the host on
+  // the way, so it is never captured
+  const bool capturable = !prm->warm_start;
+  if (capturable)
+    for (auto& e : ctx->graphs)
     if (e.problem == P && e.tsize == (int)sizeof(T) && e.arena == ctx->arena && e.arena_bytes == ctx->arena_bytes &&
         std::memcmp(&e.prm, prm, sizeof(spg_params)) == 0)
       g = &e;
@@ -822,6 +1112,17 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     CK(launch_stamp(o.stamp + 1, st));
     if ((r2 = enqueue_search<T>(ctx, P, prm, bb, sb, o))) return r2;
     CK(launch_stamp(o.stamp + 2, st));
+    if (check) {
+      // the returned states' own conditionals: mixed (the boundary MPSs of
+      // this solve) against plain FP64 boundary MPSs
+      if ((r2 = enqueue_forced<T>(ctx, P, bb, sb, o, lc_mixed))) return r2;
+      if ((r2 = enqueue_boundary<double>(ctx, P, prm, pl, bb64))) return r2;
+      if ((r2 = enqueue_forced<double>(ctx, P, bb64, sb64, o, lc_fp64))) return r2;
+      CK(launch_logmarg_err(lc_mixed, lc_fp64, o.n, P->n, o.err, st));
+    } else {
+      // 0 in the FP64 mode; NaN (all bits set) when the mixed mode is unchecked
+      CK(cudaMemsetAsync(o.err, sizeof(T) == sizeof(double) ? 0 : 0xff, sizeof(double), st));
+    }
     if (profiling) profile_mark(st);  // closes the last kernel's interval
     return SPG_OK;
   };
@@ -840,7 +1141,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     if (e2 != cudaSuccess) return fail(ctx, SPG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
     return SPG_OK;
   };
-  if (profiling) {
+  if (profiling && capturable) {
     // captured with the profiler's per-kernel event records as graph nodes,
     // so that the times between them are device times without host gaps
     cudaGraphExec_t ex = nullptr;
@@ -857,6 +1158,9 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     g->launches = thread_launches() - l0;
     CK(cudaGraphLaunch(g->exec, st));
     R->launches = g->launches;
+  } else if (!capturable) {
+    if ((rc = enqueue_all())) return rc;
+    R->launches = thread_launches() - l0;
   } else {
     if ((rc = enqueue_all())) return rc;
     R->launches = thread_launches() - l0;
@@ -881,6 +1185,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   CK(cudaMemcpyAsync(R->d_diag, o.diag, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_cand, o.cand, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_stamp, o.stamp, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_err, o.err, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(R->ev[2], st));
   return SPG_OK;
 }
@@ -906,13 +1211,15 @@ int debug_marginals_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* p
   const int chi = prm->chi;
   const int cap = std::max(1, n_prefix);
   Plan pl = make_plan(P, chi, 1);
-  const size_t need = boundary_bytes<T>(P, pl) + search_bytes<T>(P, cap, chi);
+  const int f64 = fp64_rows_of<T>(prm, P);
+  const spg_mlp* ws = warm_of(ctx, P, prm);
+  const size_t need = boundary_bytes<T>(P, pl, f64, ws) + search_bytes<T>(P, cap, chi);
   int rc = ensure_arena(ctx, need);
   if (rc) return rc;
   Arena ar{ctx->arena, 0, ctx->arena_bytes};
   BoundaryBufs<T> bb;
   SearchBufs<T> sb;
-  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, ws))) return rc;
   if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb))) return rc;
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
   const int row = site / P->cols;
@@ -941,11 +1248,13 @@ template <typename T>
 int logz_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, double* log_z) {
   cudaStream_t st = ctx->stream;
   Plan pl = make_plan(P, prm->chi, 0);
-  int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl));
+  const int f64 = fp64_rows_of<T>(prm, P);
+  const spg_mlp* ws = warm_of(ctx, P, prm);
+  int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl, f64, ws));
   if (rc) return rc;
   Arena ar{ctx->arena, 0, ctx->arena_bytes};
   BoundaryBufs<T> bb;
-  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb))) return rc;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, ws))) return rc;
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
   if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, 0))) return rc;
   double* dv = reinterpret_cast<double*>(bb.s1) + 2;
@@ -957,6 +1266,107 @@ int logz_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, double*
   const double beta_u = prm->beta * std::ldexp(1.0, -P->shift);
   *log_z = h[0] + std::log(h[1]) - beta_u * P->min_sum;
   return SPG_OK;
+}
+
+template <typename T>
+int export_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int row, int fix, void* out,
+                int32_t* dims_host) {
+  cudaStream_t st = ctx->stream;
+  if (row == 0) {  // every row 1 .. rows-1 as it is finished
+    Plan pl = make_plan(P, prm->chi, 1);
+    const int f64 = fp64_rows_of<T>(prm, P);
+    const spg_mlp* ws = warm_of(ctx, P, prm);
+    int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl, f64, ws));
+    if (rc) return rc;
+    Arena ar{ctx->arena, 0, ctx->arena_bytes};
+    BoundaryBufs<T> bb;
+    if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, ws))) return rc;
+    if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+    bb.exp_out = static_cast<T*>(out);
+    bb.exp_fix = fix;
+    if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, 1))) return rc;
+    CK(cudaStreamSynchronize(st));
+    if (dims_host)
+      for (int r = 1; r < P->rows; ++r)
+        for (int j = 0; j < P->cols; ++j)
+          for (int q = 0; q < 3; ++q)
+            dims_host[((size_t)(r - 1) * P->cols + j) * 3 + q] = pl.dimA[((size_t)r * P->cols + j) * 3 + q];
+    return SPG_OK;
+  }
+  Plan pl = make_plan(P, prm->chi, row);
+  const int f64 = fp64_rows_of<T>(prm, P);
+  const spg_mlp* ws = warm_of(ctx, P, prm);
+  int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl, f64, ws));
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, ws))) return rc;
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, row))) return rc;
+  CK(launch_export_row<T>(bb.mps, row, P->cols, prm->chi, static_cast<T*>(out),
+                          bb.dimA_dev + (size_t)row * P->cols * 3, fix, st));
+  CK(cudaStreamSynchronize(st));
+  if (dims_host)
+    for (int j = 0; j < P->cols; ++j)
+      for (int q = 0; q < 3; ++q) dims_host[j * 3 + q] = pl.dimA[((size_t)row * P->cols + j) * 3 + q];
+  return SPG_OK;
+}
+
+template <typename T>
+int trace_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int row, int init, int n_sweeps,
+               double* out) {
+  cudaStream_t st = ctx->stream;
+  spg_params base = *prm;  // the rows below are built as a plain solve builds them
+  base.warm_start = 0;
+  spg_params net = *prm;
+  net.warm_start = 1;
+  const spg_mlp* ws = init >= 1 ? warm_of(ctx, P, &net) : nullptr;
+  if (init >= 1 && !ws) return fail(ctx, SPG_EINVAL, "no warm-start network for this problem and chi");
+  Plan pl = make_plan(P, prm->chi, row);
+  const int f64 = fp64_rows_of<T>(prm, P);
+  int rc = ensure_arena(ctx, boundary_bytes<T>(P, pl, f64, ws));
+  if (rc) return rc;
+  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  BoundaryBufs<T> bb;
+  if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, nullptr))) return rc;
+  if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  if ((rc = run_boundary<T>(ctx, P, &base, pl, bb, row + 1))) return rc;
+  if (ws) {
+    // the network's buffers, carved after the boundary's
+    bb.ws = ws;
+    bb.wsX = ar.get<float>((size_t)P->cols * SPG_WS_FEATURES);
+    bb.wsY = ar.get<float>((size_t)P->cols * MAXP * prm->chi * prm->chi);
+    bb.wswork = ar.get<float>(mlp_infer_elems(ws, P->cols));
+    if (!bb.wswork) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  }
+  // init 2: the zipper's trace, then the network's on the same B_{row+1}
+  // (its left-canonical QR again is a change of gauge only)
+  const int first = init == 2 ? 0 : init, last = init == 2 ? 1 : init;
+  for (int mode = first; mode <= last; ++mode) {
+    if ((rc = build_row<T>(ctx, P, prm, pl, bb, row, mode == 1))) return rc;
+    double* o = out + (size_t)(mode - first) * n_sweeps;
+    for (int k = 0; k < n_sweeps; ++k) {
+      CK(variational_sweeps<T>(P->tb, bb.wt, bb.mps, row, P->cols, pl.dimA.data(), P->dims.data(), P->d.data(),
+                               P->gD.data(), 1, bb.swork, bb.sdbl, st));
+      double ln[2];
+      CK(cudaMemcpyAsync(ln, bb.mps.lognorm + row, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      o[k] = ln[0] - ln[1];
+    }
+  }
+  return SPG_OK;
+}
+
+// out[b][s] = in[b][map[s]] for b < *n (the states of a transformed lattice
+// read back on the original sites)
+__global__ void k_permute_sites(const uint16_t* __restrict__ in, uint16_t* __restrict__ out, const int* n_dev,
+                                int N, const int* __restrict__ map) {
+  const size_t tot = (size_t)(*n_dev) * N;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / N;
+    const int s = (int)(e % N);
+    out[e] = in[b * N + map[s]];
+  }
 }
 
 }  // namespace
@@ -997,6 +1407,8 @@ int spg_params_default(spg_params* p) {
   p->cut_off_prob = 0.0;
   p->svd_iters = -1;
   p->merge = 1;
+  p->fp64_rows = -1;
+  p->check_fp64 = 0;
   return SPG_OK;
 }
 
@@ -1044,10 +1456,14 @@ void spg_destroy(spg_ctx* ctx) {
 
 const char* spg_last_error(const spg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei, const int32_t* ej,
-                      const double* J, const double* h, const int32_t* cluster_of_spin, int32_t grid_rows,
-                      int32_t grid_cols, const int32_t* cluster_row, const int32_t* cluster_col,
-                      int32_t energy_shift, int32_t node_type, spg_problem** out) {
+}  // extern "C"
+
+namespace {
+// The Ising form's tables (S1); upload = false builds the host tables only.
+int build_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei, const int32_t* ej,
+                const double* J, const double* h, const int32_t* cluster_of_spin, int32_t grid_rows,
+                int32_t grid_cols, const int32_t* cluster_row, const int32_t* cluster_col, int32_t energy_shift,
+                int32_t node_type, spg_problem** out, bool upload) {
   if (!ctx || !out) return SPG_EINVAL;
   *out = nullptr;
   if (n_spins <= 0 || n_edges < 0 || grid_rows <= 0 || grid_cols <= 0 || !cluster_of_spin || !cluster_row ||
@@ -1149,6 +1565,27 @@ int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int3
     }
     inter[{sa, sb}].push_back({pa, pb, Jv});
   }
+  // warm-start coupling blocks per site: couplings between the cluster's
+  // spin positions, fields, summed couplings to the cluster below and to the
+  // cluster on the right, by spin position (king's diagonals not included)
+  P->wsblk.assign((size_t)n * SPG_WS_PER_CLUSTER, 0.0);
+  if (h)
+    for (int i = 0; i < n_spins; ++i) P->wsblk[(size_t)site_of_spin[i] * SPG_WS_PER_CLUSTER + 28 + pos[i]] += h[i];
+  for (int e = 0; e < n_edges; ++e) {
+    const int a = ei[e], b = ej[e];
+    const int sa = site_of_spin[a], sb = site_of_spin[b];
+    const int ra = sa / grid_cols, ca = sa % grid_cols, rb = sb / grid_cols, cb = sb % grid_cols;
+    if (sa == sb) {
+      const int q1 = std::min(pos[a], pos[b]), q2 = std::max(pos[a], pos[b]);
+      P->wsblk[(size_t)sa * SPG_WS_PER_CLUSTER + ws_pair_slot(q1, q2)] += J[e];
+    } else if (ca == cb && std::abs(ra - rb) == 1) {
+      const int up = ra < rb ? a : b;
+      P->wsblk[(size_t)site_of_spin[up] * SPG_WS_PER_CLUSTER + 36 + pos[up]] += J[e];
+    } else if (ra == rb && std::abs(ca - cb) == 1) {
+      const int left = ca < cb ? a : b;
+      P->wsblk[(size_t)site_of_spin[left] * SPG_WS_PER_CLUSTER + 44 + pos[left]] += J[e];
+    }
+  }
   // pairwise tables over the spins that carry couplers, then projectors
   std::map<std::pair<int, int>, EdgeTab> edges;
   for (auto& kv : inter) {
@@ -1193,12 +1630,75 @@ int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int3
     for (int y = 0; y < P->d[nn]; ++y) e.Pn[y] = sube.Pn[sub(y, Sn)];
     edges[{m, nn}] = e;
   }
-  int rc = finish_problem(ctx, P, edges);
+  int rc = finish_problem(ctx, P, edges, upload);
   if (rc) {
     spg_problem_destroy(P);
     return rc;
   }
+  P->raw.n_spins = n_spins;
+  P->raw.ei.assign(ei, ei + n_edges);
+  P->raw.ej.assign(ej, ej + n_edges);
+  P->raw.J.assign(J, J + n_edges);
+  if (h) P->raw.h.assign(h, h + n_spins);
+  P->raw.cos.assign(cluster_of_spin, cluster_of_spin + n_spins);
+  P->raw.crow.assign(cluster_row, cluster_row + n);
+  P->raw.ccol.assign(cluster_col, cluster_col + n);
   *out = P;
+  return SPG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int spg_problem_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* ei, const int32_t* ej,
+                      const double* J, const double* h, const int32_t* cluster_of_spin, int32_t grid_rows,
+                      int32_t grid_cols, const int32_t* cluster_row, const int32_t* cluster_col,
+                      int32_t energy_shift, int32_t node_type, spg_problem** out) {
+  return build_ising(ctx, n_spins, n_edges, ei, ej, J, h, cluster_of_spin, grid_rows, grid_cols, cluster_row,
+                     cluster_col, energy_shift, node_type, out, true);
+}
+
+int spg_problem_update_ising(spg_problem* P, const double* J, const double* h) {
+  if (!P || !P->ctx) return SPG_EINVAL;
+  spg_ctx* ctx = P->ctx;
+  const auto& rw = P->raw;
+  if (rw.potts) return fail(ctx, SPG_EINVAL, "spg_problem_update_ising: not an Ising problem");
+  if (!J && !rw.ei.empty()) return fail(ctx, SPG_EINVAL, "spg_problem_update_ising: J is NULL");
+  spg_problem* Q = nullptr;
+  int rc = build_ising(ctx, rw.n_spins, (int32_t)rw.ei.size(), rw.ei.data(), rw.ej.data(), J, h, rw.cos.data(),
+                       P->rows, P->cols, rw.crow.data(), rw.ccol.data(), P->shift, P->node_type, &Q, false);
+  if (rc) return rc;
+  const bool same = Q->d == P->d && Q->dmax == P->dmax && Q->PL == P->PL && Q->PR == P->PR && Q->PU == P->PU &&
+                    Q->PD == P->PD && Q->PG == P->PG && Q->dims == P->dims && Q->gD == P->gD && Q->xsL == P->xsL &&
+                    Q->xoffL == P->xoffL && Q->keys == P->keys && Q->kbits == P->kbits && Q->bmax == P->bmax &&
+                    Q->lstride == P->lstride && Q->RL.size() == P->RL.size();
+  if (!same) {
+    spg_problem_destroy(Q);
+    return fail(ctx, SPG_EUNSUPPORTED,
+                "spg_problem_update_ising: the new couplings change the tables' structure; build a new problem");
+  }
+  // the solves that read the old tables finish first
+  if (cudaSetDevice(ctx->device) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    spg_problem_destroy(Q);
+    return fail(ctx, SPG_ECUDA, "spg_problem_update_ising: synchronisation failed");
+  }
+  for (spg_ctx* w : ctx->workers) cudaStreamSynchronize(w->stream);
+  P->E.swap(Q->E);
+  P->RL.swap(Q->RL);
+  P->RU.swap(Q->RU);
+  P->RA.swap(Q->RA);
+  P->min_sum = Q->min_sum;
+  P->wsblk.swap(Q->wsblk);
+  P->raw.J.swap(Q->raw.J);
+  P->raw.h.swap(Q->raw.h);
+  spg_problem_destroy(Q);
+  char* base = (char*)P->dev;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(base + P->o_E, P->E.data(), sizeof(int64_t) * P->E.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + P->o_RL, P->RL.data(), sizeof(int64_t) * P->RL.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + P->o_RU, P->RU.data(), sizeof(int64_t) * P->RU.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + P->o_RA, P->RA.data(), sizeof(int64_t) * P->RA.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   return SPG_OK;
 }
 
@@ -1278,6 +1778,15 @@ int spg_problem_potts(spg_ctx* ctx, int32_t grid_rows, int32_t grid_cols, const 
     spg_problem_destroy(P);
     return rc;
   }
+  P->raw.potts = true;
+  P->raw.d.assign(d, d + n);
+  size_t nloc = 0, npair = 0;
+  for (int s2 = 0; s2 < n; ++s2) nloc += (size_t)d[s2];
+  for (int k = 0; k < n_edges; ++k) npair += (size_t)d[em[k]] * d[en[k]];
+  P->raw.local.assign(local_E, local_E + nloc);
+  P->raw.em.assign(em, em + n_edges);
+  P->raw.en.assign(en, en + n_edges);
+  P->raw.pair.assign(pair_E, pair_E + npair);
   *out = P;
   return SPG_OK;
 }
@@ -1331,11 +1840,14 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
       cudaMallocAsync((void**)&R->d_n, sizeof(int) * 4, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_diag, sizeof(int) * 4, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_stamp, sizeof(unsigned long long) * 3, st) != cudaSuccess) {
+      cudaMallocAsync((void**)&R->d_stamp, sizeof(unsigned long long) * 3, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_err, sizeof(double), st) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
   }
-  rc = prm->precision == SPG_FP64 ? solve_impl<double>(ctx, P, prm, R) : solve_impl<float>(ctx, P, prm, R);
+  const bool use64 = prm->precision == SPG_FP64 || fp32_range_exceeded(P, prm);
+  R->precision_used = use64 ? SPG_FP64 : SPG_MIXED;
+  rc = use64 ? solve_impl<double>(ctx, P, prm, R) : solve_impl<float>(ctx, P, prm, R);
   if (rc) return cleanup(rc);
   *out = R;
   return SPG_OK;
@@ -1358,6 +1870,7 @@ int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, co
     if (rc) return fail(ctx, rc, "worker context creation failed");
     ctx->workers.push_back(w);
   }
+  for (spg_ctx* w : ctx->workers) w->warm = ctx->warm;
   // the batch starts after the work already on the context's stream
   cudaEvent_t start;
   CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
@@ -1407,7 +1920,7 @@ static int fetch(spg_result* R) {
 }
 
 int spg_result_get(spg_result* R, int32_t* n_states, int32_t* n_sites, uint16_t* states, int64_t* energies_fixed,
-                   double* energies, double* log_probs) {
+                   double* energies, double* log_probs, double* max_logmarg_err) {
   if (!R) return SPG_EINVAL;
   spg_ctx* ctx = R->ctx;
   int rc = fetch(R);
@@ -1424,6 +1937,8 @@ int spg_result_get(spg_result* R, int32_t* n_states, int32_t* n_sites, uint16_t*
   if (energies)
     for (int k = 0; k < R->n; ++k) energies[k] = (double)E[k];
   if (log_probs) CK(cudaMemcpy(log_probs, R->d_logp, sizeof(double) * R->n, cudaMemcpyDeviceToHost));
+  if (max_logmarg_err) CK(cudaMemcpy(max_logmarg_err, R->d_err, sizeof(double), cudaMemcpyDeviceToHost));
+  if (diag[1] & ERR_TIMEOUT) return fail(ctx, SPG_ETIMEOUT, "a bounded wait in a kernel gave up");
   if (diag[1] & ERR_ENERGY) return fail(ctx, SPG_ENUMERIC, "final energies disagree with the running energies");
   if (diag[1] & ERR_KEY) return fail(ctx, SPG_EUNSUPPORTED, "merge key overflow");
   return SPG_OK;
@@ -1449,6 +1964,9 @@ int spg_result_info(spg_result* R, spg_info* info) {
   info->boundary_lognorm = cand[1];
   info->kernel_launches = R->launches;
   info->jacobi_sweeps_max = diag[3];
+  info->fp64_rows = R->fp64_rows;
+  info->precision_used = R->precision_used;
+  CK(cudaMemcpy(&info->max_logmarg_err, R->d_err, sizeof(double), cudaMemcpyDeviceToHost));
   return SPG_OK;
 }
 
@@ -1465,6 +1983,7 @@ void spg_result_destroy(spg_result* R) {
   if (R->d_diag) cudaFreeAsync(R->d_diag, st);
   if (R->d_cand) cudaFreeAsync(R->d_cand, st);
   if (R->d_stamp) cudaFreeAsync(R->d_stamp, st);
+  if (R->d_err) cudaFreeAsync(R->d_err, st);
   for (int k = 0; k < 3; ++k)
     if (R->ev[k]) cudaEventDestroy(R->ev[k]);
   cudaGetLastError();
@@ -1482,7 +2001,7 @@ int spg_debug_marginals(spg_ctx* ctx, const spg_problem* P, const spg_params* pr
     for (int t = 0; t < site; ++t)
       if (prefixes[(size_t)k * site + t] >= P->d[t]) return fail(ctx, SPG_EINVAL, "prefix state out of range");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
-  return prm->precision == SPG_FP64
+  return (prm->precision == SPG_FP64 || fp32_range_exceeded(P, prm))
              ? debug_marginals_impl<double>(ctx, P, prm, site, n_prefix, prefixes, log_marg)
              : debug_marginals_impl<float>(ctx, P, prm, site, n_prefix, prefixes, log_marg);
 }
@@ -1492,7 +2011,8 @@ int spg_log_partition(spg_ctx* ctx, const spg_problem* P, const spg_params* prm,
   int rc = check_params(ctx, P, prm);
   if (rc) return rc;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
-  return prm->precision == SPG_FP64 ? logz_impl<double>(ctx, P, prm, log_z) : logz_impl<float>(ctx, P, prm, log_z);
+  return (prm->precision == SPG_FP64 || fp32_range_exceeded(P, prm)) ? logz_impl<double>(ctx, P, prm, log_z)
+                                                                       : logz_impl<float>(ctx, P, prm, log_z);
 }
 
 int spg_truncate(spg_ctx* ctx, const double* M, int32_t m, int32_t n, int32_t keep, int32_t iters, double* V,
@@ -1540,7 +2060,7 @@ int spg_tc_product(spg_ctx* ctx, const float* M, int32_t m, int32_t n, const flo
   int h = 0;
   CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (h) return fail(ctx, SPG_ECUDA, "spg_tc_product: a bounded wait in the kernel gave up");
+  if (h) return fail(ctx, SPG_ETIMEOUT, "spg_tc_product: a bounded wait in the kernel gave up");
   return SPG_OK;
 }
 
@@ -1596,6 +2116,204 @@ int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap) {
   p.streams.clear();
   p.flops.clear();
   p.used = 0;
+  return SPG_OK;
+}
+
+
+int spg_warm_features(const spg_problem* P, int32_t row, float* out) {
+  if (!P || !out || row < 0 || row >= P->rows) return SPG_EINVAL;
+  if (P->wsblk.empty()) return SPG_EUNSUPPORTED;
+  ws_features(P, row, out);
+  return SPG_OK;
+}
+
+int spg_boundary_export(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int32_t row, int32_t fix_signs,
+                        void* out, int32_t* dims) {
+  if (!ctx || !P || !out) return SPG_EINVAL;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (row < 0 || row >= P->rows || (row == 0 && P->rows < 2))
+    return fail(ctx, SPG_EINVAL, "spg_boundary_export: row outside 0 .. rows-1");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return prm->precision == SPG_FP64 ? export_impl<double>(ctx, P, prm, row, fix_signs != 0, out, dims)
+                                    : export_impl<float>(ctx, P, prm, row, fix_signs != 0, out, dims);
+}
+
+int spg_mlp_create(spg_ctx* ctx, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, spg_mlp** out) {
+  if (!ctx || !out) return SPG_EINVAL;
+  *out = nullptr;
+  if (n_in < 1 || n_in > 4096 || n_hidden < 1 || n_hidden > 1024 || n_out < 1 || n_out > 65536)
+    return fail(ctx, SPG_EUNSUPPORTED, "spg_mlp_create: sizes outside the limits");
+  CK(cudaSetDevice(ctx->device));
+  spg_mlp* m = new (std::nothrow) spg_mlp();
+  if (!m) return SPG_ENOMEM;
+  m->device = ctx->device;
+  m->stream = ctx->stream;
+  m->n_in = n_in;
+  m->n_hidden = n_hidden;
+  m->n_out = n_out;
+  int rc = mlp_setup(m);
+  if (!rc) rc = mlp_init_params(m, seed);
+  if (rc) {
+    spg_mlp_destroy(m);
+    return fail(ctx, rc, "spg_mlp_create: device allocation or initialisation failed");
+  }
+  *out = m;
+  return SPG_OK;
+}
+
+int spg_set_warm_start(spg_ctx* ctx, spg_mlp* mlp) {
+  if (!ctx) return SPG_EINVAL;
+  if (mlp && mlp->device != ctx->device) return fail(ctx, SPG_EINVAL, "network on another device");
+  ctx->warm = mlp;
+  for (spg_ctx* w : ctx->workers) w->warm = mlp;
+  return SPG_OK;
+}
+
+int spg_sweep_trace(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int32_t row, int32_t init,
+                    int32_t n_sweeps, double* log_overlap) {
+  if (!ctx || !P || !log_overlap) return SPG_EINVAL;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (row < 1 || row >= P->rows || init < 0 || init > 2 || n_sweeps < 1 || n_sweeps > 256)
+    return fail(ctx, SPG_EINVAL, "spg_sweep_trace: bad row, init or n_sweeps");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return prm->precision == SPG_FP64 ? trace_impl<double>(ctx, P, prm, row, init, n_sweeps, log_overlap)
+                                    : trace_impl<float>(ctx, P, prm, row, init, n_sweeps, log_overlap);
+}
+
+int spg_check_bounded_wait(spg_ctx* ctx, int64_t polls) {
+  if (!ctx || polls < 0 || polls > (int64_t)1 << 40) return SPG_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  int rc = ensure_arena(ctx, 4096);
+  if (rc) return rc;
+  int* flag = reinterpret_cast<int*>(ctx->arena);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  CK(launch_wait_check((long)polls, flag, st));
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h & ERR_TIMEOUT) return fail(ctx, SPG_ETIMEOUT, "bounded wait gave up (as it must: nothing completes it)");
+  return fail(ctx, SPG_ECUDA, "bounded wait check: the wait did not report its timeout");
+}
+
+int spg_inject_alloc_failure(int32_t after) {
+  alloc_failure_countdown().store(after < 0 ? -1 : after);
+  return SPG_OK;
+}
+
+int spg_solve_lattice8(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result** out,
+                       int32_t* best_k, int64_t* best_per_lattice) {
+  if (!ctx || !P || !prm || !out) return SPG_EINVAL;
+  *out = nullptr;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  const int rows = P->rows, cols = P->cols, n = P->n;
+  std::vector<spg_problem*> probs(8, nullptr);
+  std::vector<std::vector<int32_t>> maps(8, std::vector<int32_t>(n));
+  auto release = [&]() {
+    for (int k = 1; k < 8; ++k) spg_problem_destroy(probs[k]);
+  };
+  for (int k = 0; k < 8; ++k) {
+    int32_t R = 0, C = 0;
+    spg_lattice_site_map(rows, cols, k, maps[k].data(), &R, &C);
+    if (k == 0) {
+      probs[0] = const_cast<spg_problem*>(P);
+      continue;
+    }
+    if (C > SPG_MAX_COLS) {
+      release();
+      return fail(ctx, SPG_EUNSUPPORTED, "a transposed lattice is wider than the built limit");
+    }
+    const auto& rw = P->raw;
+    if (!rw.potts) {
+      std::vector<int32_t> crow(n), ccol(n);
+      for (int c = 0; c < n; ++c) {
+        const int t = maps[k][rw.crow[c] * cols + rw.ccol[c]];
+        crow[c] = t / C;
+        ccol[c] = t % C;
+      }
+      rc = spg_problem_ising(ctx, rw.n_spins, (int32_t)rw.ei.size(), rw.ei.data(), rw.ej.data(), rw.J.data(),
+                             rw.h.empty() ? nullptr : rw.h.data(), rw.cos.data(), R, C, crow.data(), ccol.data(),
+                             P->shift, P->node_type, &probs[k]);
+    } else {
+      // sites move with their local tables; edges keep their tables
+      std::vector<int32_t> d2(n), em2(rw.em.size()), en2(rw.en.size());
+      std::vector<size_t> off(n + 1, 0);
+      for (int s2 = 0; s2 < n; ++s2) off[s2 + 1] = off[s2] + (size_t)rw.d[s2];
+      std::vector<int32_t> old_of(n);
+      for (int s2 = 0; s2 < n; ++s2) old_of[maps[k][s2]] = s2;
+      std::vector<int64_t> local;
+      local.reserve(rw.local.size());
+      for (int t = 0; t < n; ++t) {
+        const int o = old_of[t];
+        d2[t] = rw.d[o];
+        local.insert(local.end(), rw.local.begin() + off[o], rw.local.begin() + off[o + 1]);
+      }
+      for (size_t e = 0; e < rw.em.size(); ++e) {
+        em2[e] = maps[k][rw.em[e]];
+        en2[e] = maps[k][rw.en[e]];
+      }
+      rc = spg_problem_potts(ctx, R, C, d2.data(), local.data(), (int32_t)em2.size(), em2.data(), en2.data(),
+                             rw.pair.data(), P->shift, P->node_type, &probs[k]);
+    }
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
+  std::vector<spg_params> prms(8, *prm);
+  std::vector<spg_result*> res(8, nullptr);
+  rc = spg_solve_batch(ctx, 8, probs.data(), prms.data(), res.data());
+  if (rc) {
+    release();
+    return rc;
+  }
+  // the first lowest best energy
+  int kb = -1;
+  int64_t bestE = 0;
+  for (int k = 0; k < 8 && !rc; ++k) {
+    int32_t ns = 0;
+    rc = spg_result_get(res[k], &ns, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    int64_t e0 = INT64_MAX;
+    if (!rc && ns > 0) rc = spg_result_get(res[k], nullptr, nullptr, nullptr, &e0, nullptr, nullptr, nullptr);
+    if (best_per_lattice) best_per_lattice[k] = e0;
+    if (!rc && (kb < 0 || e0 < bestE)) {
+      kb = k;
+      bestE = e0;
+    }
+  }
+  for (int k = 0; k < 8; ++k)
+    if (k != kb || rc) spg_result_destroy(res[k]);
+  if (rc) {
+    release();
+    return rc;
+  }
+  // the chosen lattice's states on the original sites
+  spg_result* R = res[kb];
+  spg_ctx* rctx = R->ctx;
+  cudaStream_t st = rctx->stream;
+  uint16_t* remapped = nullptr;
+  int* map_dev = nullptr;
+  if (cudaMallocAsync((void**)&remapped, sizeof(uint16_t) * (size_t)R->cap * R->N, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&map_dev, sizeof(int) * n, st) != cudaSuccess) {
+    cudaGetLastError();
+    spg_result_destroy(R);
+    release();
+    return fail(ctx, SPG_ENOMEM, "lattice remap: allocation failed");
+  }
+  CK(cudaMemcpyAsync(map_dev, maps[kb].data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  k_permute_sites<<<std::max(1, std::min(1024, (R->cap * R->N + 255) / 256)), 256, 0, st>>>(R->d_states, remapped,
+                                                                                             R->d_n, R->N, map_dev);
+  CK(cudaGetLastError());
+  cudaFreeAsync(R->d_states, st);
+  cudaFreeAsync(map_dev, st);
+  R->d_states = remapped;
+  CK(cudaStreamSynchronize(st));
+  release();
+  if (best_k) *best_k = kb;
+  *out = R;
   return SPG_OK;
 }
 

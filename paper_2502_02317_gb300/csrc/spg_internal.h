@@ -8,6 +8,25 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+// The warm-start network (include/spg.h spg_mlp_*): sizes, the flat FP32
+// parameters, their gradient and Adam moments (one allocation, 4 x
+// n_params), a BF16 copy of the parameters for inference, and scratch.
+struct spg_mlp {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_in = 0, n_hidden = 0, n_out = 0;
+  int64_t n_params = 0;
+  int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;  // offsets in the flat layout
+  float* p = nullptr;
+  float* g = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  void* pbf = nullptr;  // __nv_bfloat16[n_params]
+  int t = 0;            // Adam steps taken
+  float* scratch = nullptr;
+  size_t scratch_elems = 0;
+};
+
 namespace spg {
 
 // Kernels enqueued by this library since load (every launcher adds its own).
@@ -90,7 +109,7 @@ inline void profile_mark(cudaStream_t st) {
 constexpr int MAXS = 256;   // states of one cluster
 constexpr int MAXP = 16;    // projected (reduced-table) dimension
 constexpr int MAXCHI = 64;  // boundary-MPS bond
-constexpr int KEYW = 4;     // 64-bit words of a packed merge key
+constexpr int KEYW = 8;     // 64-bit words of a packed merge key
 constexpr int SMAX = 128;   // columns of the truncation's working block
 #define SPG_MAXFINAL 4096   // final states ordered by the last kernel
 
@@ -154,7 +173,7 @@ struct DevTables {
   const int* keys;   // [n][MAXKEY+1]: count, then sites of the reduced parent key
   const int* kshift; // bits per packed state
 };
-constexpr int MAXKEY = 40;
+constexpr int MAXKEY = 136;  // key sites: a row plus the sites around the current one
 constexpr int MAXBOND = MAXP * MAXP;
 
 // Boltzmann pieces (S2), each table shifted by its minimum so that every
@@ -229,6 +248,12 @@ class TcGemm {
   float *Mh_, *Ml_, *MTh_, *MTl_, *Bh_, *Bl_, *part_;
 };
 cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st);
+// One bounded mbarrier wait that nothing completes: ERR_TIMEOUT into *err
+// after `limit` polls (the failure path of the kernels' bounded waits).
+cudaError_t launch_wait_check(long limit, int* err, cudaStream_t st);
+// Test hook: the (n+1)-th device workspace allocation from now fails as if
+// the device were out of memory (n < 0: off).
+std::atomic<int>& alloc_failure_countdown();
 // Writes the GPU's global nanosecond timer into *slot when the stream reaches it.
 cudaError_t launch_stamp(unsigned long long* slot, cudaStream_t st);
 size_t truncated_svd_work(int m, int n, int keep);
@@ -273,6 +298,9 @@ cudaError_t gemm(bool transA, int m, int n, int k, const T* A, int lda, const T*
 template <typename T>
 cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb,
                   T* C, int ldc, cudaStream_t st);
+// dst[e] = (To) src[e] for e < count (a contiguous block changes precision).
+template <typename From, typename To>
+cudaError_t launch_convert(const From* src, To* dst, size_t count, cudaStream_t st);
 // base[e * stride] = v for e < count.
 template <typename T>
 cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st);
@@ -340,5 +368,36 @@ template <typename T>
 cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site,
                                     const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st);
+
+// ------------------------------------------------------------------ warm start
+// Offsets of the flat parameter layout and the device buffers (SPG_ENOMEM on
+// failure); initial parameters from a seed (synchronous).
+int mlp_setup(spg_mlp* m);
+int mlp_init_params(spg_mlp* m, uint64_t seed);
+// BF16 inference of n samples X [n][n_in] -> Y [n][n_out] (device), with
+// `work` holding mlp_infer_elems(m, n) floats.
+size_t mlp_infer_elems(const spg_mlp* m, int n);
+cudaError_t mlp_infer_bf16(const spg_mlp* m, const float* X, int n, float* work, float* Y, cudaStream_t st);
+// Row `row` of an MPS from padded network sites Y [cols][16][chi][chi]
+// (entries beyond each site's dims ignored).
+template <typename T>
+cudaError_t launch_ws_scatter(const float* Y, int chi, int cols, DevMPS<T> mps, int row, cudaStream_t st);
+// Row `row` of an MPS to padded sites out [cols][16][chi][chi] (zeros beyond
+// the dims); fix_signs applies the sign gauge (dims_dev: the row's [cols][3]).
+template <typename T>
+cudaError_t launch_export_row(DevMPS<T> mps, int row, int cols, int chi, T* out, const int* dims_dev, int fix_signs,
+                              cudaStream_t st);
+// Teacher forcing along the n (= *n_dev) full states `targets` ([n][N]):
+// launch_force_init fills beam buffer `cur` with n empty prefixes; per site,
+// after the right environments (row start) and the marginals, launch_force
+// makes each element's target state its only child and writes that state's
+// log-conditional to out[b][site]; launch_update then extends the prefixes.
+cudaError_t launch_force_init(const DevSearch& ds, const int* n_dev, int cur, cudaStream_t st);
+cudaError_t launch_force(int site, const DevSearch& ds, int cur, const uint16_t* targets, double* out,
+                         cudaStream_t st);
+// *out = max over the n x N entries of |a - r| / max(1, |r|) (inf when one
+// side is -inf and the other is not).
+cudaError_t launch_logmarg_err(const double* a, const double* r, const int* n_dev, int N, double* out,
+                               cudaStream_t st);
 
 }  // namespace spg

@@ -22,7 +22,8 @@
 // owns the tensor-memory allocation, and all four warps drain the
 // accumulator (warp w reads TMEM lanes 32w..32w+31 = rows of the tile).
 // Every wait on an mbarrier is bounded; on a timeout the kernel records
-// ERR_TIMEOUT, still releases its tensor memory and returns.
+// ERR_TIMEOUT, waits (bounded) for the loads it already issued, releases its
+// tensor memory and returns.
 #include <cuda.h>
 
 #include <cstring>
@@ -43,8 +44,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  for (long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, long limit = WAIT_LIMIT) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(128, 1)
   bool ok = true;
   if (warp == 0 && lane == 0) {
     // loader
+    int issued = 0;
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES;
       if (i >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((i / STAGES) - 1) & 1, err);
@@ -152,6 +154,15 @@ __global__ void __launch_bounds__(128, 1)
       tma_load_2d(st + A_BYTES, &tAl, kc, m0, fb);
       tma_load_2d(st + 2 * A_BYTES, &tBh, kc, 0, fb);
       tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tBl, kc, 0, fb);
+      issued = i + 1;
+    }
+    // every issued load lands in this CTA's shared memory before it exits,
+    // also when a wait here or in the MMA issuer gave up: wait (bounded) for
+    // the last load issued into each stage (at once true when it was consumed)
+    for (int s = 0; s < STAGES; ++s) {
+      int last = issued - 1;
+      while (last >= 0 && last % STAGES != s) --last;
+      if (last >= 0) mbar_wait(full0 + 8 * s, (last / STAGES) & 1, err);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: 4 K-steps of 8 per stage, three products each
@@ -200,6 +211,20 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+}
+
+// The bounded wait of the kernels above on an mbarrier that nothing arrives
+// on: it must give up after `limit` polls, record ERR_TIMEOUT and return
+// (the failure path of every bounded wait, exercised without any copy or
+// tensor memory in flight).
+__global__ void k_wait_check(long limit, int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, limit);
 }
 
 // hi = x rounded to TF32 (round to nearest, ties away), lo = x - hi (exact in
@@ -384,6 +409,12 @@ cudaError_t TcGemm::run(bool trans, const float* Bt, int s, float* out) {
     k_sum_splits<<<(int)std::min<size_t>((sstride + 255) / 256, 4096), 256, 0, st_>>>(part_, nsplit, sstride, s,
                                                                                       rowsA, rowsA, out);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_check(long limit, int* err, cudaStream_t st) {
+  count_launches("k_wait_check", st);
+  k_wait_check<<<1, 32, 0, st>>>(limit, err);
   return cudaGetLastError();
 }
 

@@ -123,7 +123,10 @@ def test_king_d8_chi64_log_partition(spg, ctx, king8, prec):
     inst, fg, p, bd = king8
     ref = log_z_of(p, bd)
     prob = spg.spg_problem_potts(ctx, inst)
-    prm = spg.params(beta=1.0, chi=64, precision=prec)
+    # fp64_rows = 0: FP32 truncations throughout, so that the tensor-core
+    # products run (the default truncates every row of a lattice this small
+    # in FP64)
+    prm = spg.params(beta=1.0, chi=64, precision=prec, fp64_rows=0)
     got, ran = kernels_run(spg, ctx, lambda: spg.spg_log_partition(ctx, prob, prm))
     assert abs(got - ref) <= TOL[prec] * max(1.0, abs(ref)), (got, ref)
     assert "k_tsqr_leaf" in ran
@@ -135,7 +138,7 @@ def test_king_d8_chi64_log_partition(spg, ctx, king8, prec):
 def test_king_d8_chi64_marginals(spg, ctx, king8, prec):
     inst, fg, p, bd = king8
     prob = spg.spg_problem_potts(ctx, inst)
-    prm = spg.params(beta=1.0, chi=64, precision=prec)
+    prm = spg.params(beta=1.0, chi=64, precision=prec, fp64_rows=0)
     rng = np.random.default_rng(19)
     for s in (0, 3, 5, 9, 14, 15):
         pre = np.array([[rng.integers(0, d) for d in fg.d[:s]] for _ in range(4)], dtype=np.int64).reshape(4, s)

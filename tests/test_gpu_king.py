@@ -3,7 +3,9 @@ against the FP64 oracle, element by element.
 
 Tolerances as in test_gpu_parity: returned states and int64 energies
 bit-exact; log Z, log-marginals and log-probabilities within 1e-6 relative in
-FP64 mode and 1e-3 in mixed mode (conditionals >= 1e-6).  The oracle's dense
+FP64 mode and 1e-3 in mixed mode (conditionals >= 1e-6).  The mixed mode
+runs with its default fp64_rows, which on these small lattices truncates
+every row in FP64.  The oracle's dense
 site tensors limit the parity cases to small cluster dimensions (bonds up to
 16 x 16); the 256-state bonds of 16-state Potts sites are covered by
 properties that hold at any size.
@@ -23,10 +25,10 @@ TOL = {0: 1e-6, 1: 1e-3}
 LOG_FLOOR = float(np.log(1e-6))
 
 FP32_KING = pytest.mark.xfail(strict=True, reason=(
-    "known limit of the mixed mode on these king's graphs: FP32 conditionals miss the FP64 oracle by "
-    "3e-3 to 2e-2 (5x5 4-state Potts at beta 1.2 chi 8, 4x4 king's Ising at chi 8, the 3x3 king's "
-    "Ising example at beta 2); the FP64 mode matches the oracle to 1e-10 on the same cases, and the "
-    "searches' best energies agree"))
+    "known limit of the mixed mode: on the paper's 3x3 king's Ising example at beta 2 the FP32 storage "
+    "of the boundary MPS alone (a normwise perturbation of 6e-8) moves small conditionals by up to "
+    "3.5e-2, so even with every truncation in FP64 the FP32 conditionals miss the oracle by 3.4e-3; the "
+    "FP64 mode matches the oracle to 1e-10 and the searches' best energies agree"))
 
 
 @pytest.fixture(scope="module")
@@ -85,7 +87,7 @@ def test_king_log_partition(spg, ctx, make, beta, chi, prec):
 def test_king_debug_marginals(spg, ctx, make, beta, chi, prec, request):
     """Teacher-forced conditionals at sites of every row, random prefixes."""
     inst = make()
-    if prec == 1 and getattr(inst, "name", "") in ("kingpotts5x5_d4_s3", "king4x4x2_s5", "king3x3x2_s4"):
+    if prec == 1 and getattr(inst, "name", "") == "king3x3x2_s4":
         request.applymarker(FP32_KING)
     fg = fg_of(inst)
     bd = boundary.boundary_mpses(peps.build(fg, beta), chi)
