@@ -396,3 +396,86 @@ def test_king_search_finds_brute_force_ground_state(seed):
     assert int(res.energies[0]) == int(E.min())
     assert [int(v) for v in res.states[0]] == [int(c[k]) for c in cs]
     assert tables.energy(fg, res.states[0]) == int(E.min())
+
+
+# ---------------------------------------------------------------- further pins of the zipper and the search
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_truncation_error_falls_with_chi(L):
+    """Width-3 Chimera against the exact spin-level transfer matrix: the
+    zipper's log Z error decreases at every doubling of chi (1 .. 64) and is
+    below 1e-5 at chi 64."""
+    inst = I.chimera(L, 7, couplings="gauss", h_sigma=0.1, cols=3)
+    ref = exact.chimera_strip(inst, 1.0)["logZ"]
+    p = peps.build(tables.from_ising(inst), 1.0)
+    errs = [abs(boundary.log_partition(p, chi) - ref) for chi in (1, 2, 4, 8, 16, 32, 64)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-5
+
+
+def test_untruncated_zipper_reproduces_the_mpo_mps_product():
+    """With chi at least the full bond, one zipper row is exactly W B: every
+    amplitude of the resulting MPS (times exp(log-norm)) equals the product
+    of the row MPO with the MPS below, contracted densely."""
+    inst = I.chimera(3, 2, couplings="gauss", h_sigma=0.2, cols=3)
+    p = peps.build(tables.from_ising(inst), 0.7)
+    Bs = boundary.boundary_mpses(p, 10 ** 6, 0, down_to=1)
+    Ws = peps.mpo_row(p, 1)
+    B2, B1 = Bs[2], Bs[1]
+
+    def dense(mps):
+        T = np.ones((1, 1))  # [configurations, right bond]
+        for A in mps.sites:
+            a, s, b = A.shape
+            T = np.einsum("ca,asb->csb", T, A).reshape(-1, b)
+        return T[:, 0] * np.exp(mps.lognorm)
+
+    # W B densely: contract each MPO site with the MPS site (bond pairs)
+    T = np.ones((1, 1, 1))  # [configurations u, MPO bond, MPS bond]
+    for W, A in zip(Ws, B2.sites):
+        t = np.einsum("clb,lrus,bsd->curd", T, W, A)
+        T = t.reshape(t.shape[0] * t.shape[1], t.shape[2], t.shape[3])
+    exact_amps = T[:, 0, 0] * np.exp(B2.lognorm)
+    np.testing.assert_allclose(dense(B1), exact_amps, rtol=1e-10, atol=1e-12 * np.max(np.abs(exact_amps)))
+
+
+def test_sign_fix_gauge():
+    """Every right singular vector comes out with its largest-magnitude entry
+    (first on ties) positive, U V^T unchanged; the zipper's sites obey it."""
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((7, 9))
+    U, S, Vt = np.linalg.svd(M, full_matrices=False)
+    U2, Vt2 = boundary.sign_fix(U.copy(), Vt.copy())
+    np.testing.assert_allclose((U2 * S) @ Vt2, M, atol=1e-12)
+    for row in Vt2:
+        assert row[np.argmax(np.abs(row))] > 0
+    Vt3 = np.array([[0.5, -0.5, 0.1]])  # a tie: the first maximum decides
+    _, Vt3 = boundary.sign_fix(np.ones((1, 1)), Vt3)
+    assert Vt3[0, 0] == 0.5
+    p = peps.build(tables.from_ising(I.chimera(3, 4, couplings="gauss", h_sigma=0.1)), 1.0)
+    B = boundary.boundary_mpses(p, 8, 0, down_to=1)[1]
+    for A in B.sites[1:]:
+        for row in A.reshape(A.shape[0], -1):
+            assert row[np.argmax(np.abs(row))] > 0
+
+
+def test_degenerate_cut_is_flagged():
+    """At beta = 0 every weight is 1, the zipper matrices have rank 1, and a
+    cut below their dimensions falls between equal (zero) singular values:
+    flagged; a generic instance at beta = 1 is not."""
+    fg = tables.from_ising(I.chimera(3, 4, couplings="gauss", h_sigma=0.1))
+    assert boundary.boundary_mpses(peps.build(fg, 0.0), 4)[1].degenerate
+    assert not boundary.boundary_mpses(peps.build(fg, 1.0), 4)[1].degenerate
+
+
+def test_near_tie_is_counted():
+    """A single-spin lattice with h = 0 is Z2-symmetric: the two states of the
+    first site are exactly equally probable, so a beam of 1 cuts between
+    them and the prune records a near tie; a field makes the cut clear."""
+    sym = I.square(2, 3, cols=2)
+    r = search.solve(tables.from_ising(sym), search.Params(beta=1.0, chi=4, beam=1, merge=False))
+    assert r.near_ties >= 1
+    asym = I.square(2, 3, cols=2, h_sigma=2.0)
+    r = search.solve(tables.from_ising(asym), search.Params(beta=1.0, chi=4, beam=1, merge=False))
+    assert r.near_ties == 0 and r.min_cut_gap > 1e-6
