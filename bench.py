@@ -37,10 +37,8 @@ METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best ene
 # DRAM bytes (read + write) per launch of a dominant kernel, from an ncu
 # capture of two mid-solve launches of the 16x16 solve (dram__bytes_read.sum
 # + dram__bytes_write.sum, mean of the two), for the kernel as it is now; a
-# kernel not listed here reports null.  (k_cgs2_rows: 118,400 B was measured
-# on the per-vector panel version, before the Cholesky-QR panels; not listed
-# until its counters are taken again.)
-NCU_TRAFFIC_BYTES = {}
+# kernel not listed here reports null.
+NCU_TRAFFIC_BYTES = {"k_cgs2_rows": 153.2}  # 48 x 512 block, Cholesky-QR panels: 158.2 and 148.2 B
 
 
 def make_instance(seed):
@@ -535,7 +533,8 @@ def main():
             rb, msb = timed(lambda: spg.spg_solve(ctx, probs[0], bprm))
             _, Eb, _ = rb.get()
             b4[bprec] = {"tts_s": msb / 1e3, "best_energy_fixed": int(Eb[0]),
-                         "beam_states_per_s": rb.info()["candidates"] / (msb / 1e3)}
+                         "beam_states_per_s": rb.info()["candidates"] / (msb / 1e3),
+                         "precision_used": "fp64" if rb.info()["precision_used"] == spg.SPG_FP64 else "mixed"}
         rcb = spg.spg_solve(ctx, probs[0], spg.params(beta=4.0, chi=WORKLOAD["chi"], beam=WORKLOAD["beam"],
                                                       precision=prec, num_sweeps=WORKLOAD["sweeps"], check_fp64=1))
         line["beta4"] = {"workload": "chimera16x16 gauss (first instance), beta=4, chi=32, 1 sweep, beam=1024",

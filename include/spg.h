@@ -101,8 +101,22 @@ typedef struct {
                           plain FP64 boundary MPSs; the largest difference is
                           the result's max_logmarg_err.  Costs a plain FP64
                           boundary phase per solve (default 0: off).        */
-  int32_t reserved[5]; /* must be 0                                          */
+  int32_t droplet_hamming; /* droplets (below): a candidate excitation is
+                              kept when it differs from the state and from
+                              every droplet kept so far in more than this
+                              many Potts variables (default 0)              */
+  double droplet_energy;   /* droplets (SingleLayerDroplets, Sec. 2 and 3.1):
+                              energy cutoff of the low-energy excitations
+                              collected in the merges, in the units of J
+                              (multiplied by 2^energy_shift and rounded
+                              down); < 0 (the default -1): no droplets      */
+  int32_t reserved[2];     /* must be 0                                      */
 } spg_params;
+
+/* Droplets kept per partial configuration (SPG_EUNSUPPORTED-free: a state
+ * whose list would grow beyond this keeps its first SPG_MAX_DROPLETS in the
+ * acceptance order and the result's info reports droplet_overflow). */
+#define SPG_MAX_DROPLETS 16
 
 /* fp64_rows = -1 truncates every row in FP64 on problems of at most this
  * many sites: there the truncations are often near-exact (chi close to the
@@ -129,7 +143,9 @@ typedef struct {
   int32_t precision_used;  /* SPG_FP64 when an SPG_MIXED solve ran the FP64
                               path because its weights exceed FP32's range
                               (see SPG_FP32_WEIGHT_SPAN), else as asked     */
-  int32_t reserved2;
+  int32_t droplet_overflow; /* droplet candidates not considered or not kept
+                              because a list was full (0: the droplets are
+                              those of an unbounded list)                   */
   double max_logmarg_err;  /* check_fp64: max over returned states and sites
                               of |log p_mixed - log p_FP64| / max(1,
                               |log p_FP64|) of the state's own conditional;
@@ -158,8 +174,11 @@ int spg_lattice_site_map(int32_t rows, int32_t cols, int32_t k, int32_t* site_ma
  * (may be NULL: the library creates and owns a non-blocking stream).  The
  * context owns its device workspace, grown on demand and reused. */
 int spg_create(spg_ctx** out, int device, void* cuda_stream);
-/* Problems and results created through a context (including the results of
- * spg_solve_batch) are destroyed before the context. */
+/* Releases the context.  Problems, results and networks made through it
+ * (including the results of spg_solve_batch) may be destroyed before or
+ * after it, in any order: a context destroyed while such handles are alive
+ * is released with the last of them (no call other than their destroy may
+ * use them after spg_destroy). */
 void spg_destroy(spg_ctx* ctx);
 const char* spg_last_error(const spg_ctx* ctx);
 
@@ -273,13 +292,27 @@ int spg_solve_lattice8(spg_ctx* ctx, const spg_problem* prob, const spg_params* 
 int spg_result_get(spg_result* res, int32_t* n_states, int32_t* n_sites, uint16_t* states,
                    int64_t* energies_fixed, double* energies, double* log_probs, double* max_logmarg_err);
 int spg_result_info(spg_result* res, spg_info* info);
+/* Droplets of the best returned state (unpack_droplets, Sec. 3.1): the
+ * low-energy excitations collected in the merges (params.droplet_energy >=
+ * 0 and merge = 1), as full configurations with their exact energies,
+ * sorted by (energy, state).  n (<= SPG_MAX_DROPLETS), energies [n] int64,
+ * states [n x n_sites]; any pointer may be NULL.  Reading: a partial
+ * configuration that loses a merge agrees with the winner on every fixed
+ * variable next to the unexplored region, so it is an excitation of the
+ * winner, dE = E_loser - E_winner, valid for all the winner's descendants;
+ * a winner keeps its parent's droplets and accepts, in (dE, state) order,
+ * each loser of its merge class and each loser with one of its own droplets
+ * applied, when dE <= droplet_energy and it differs from the winner and from
+ * every droplet kept so far in more than droplet_hamming variables. */
+int spg_result_droplets(spg_result* res, int32_t* n, int64_t* energies, uint16_t* states);
 void spg_result_destroy(spg_result* res);
 
 /* Teacher-forced conditional marginals (Sec. 2, Fig. 1(d)): for each of the
  * n_prefix prefixes (prefixes[k*site .. k*site+site-1] = states of sites
  * 0 .. site-1), log p(x_site | prefix) for every state x of `site`, written
- * to log_marg[k*d_site + x].  Uses the same boundary MPSs and environment
- * kernels as spg_solve.  Synchronous. */
+ * to log_marg[k*d_site + x].  Uses the same boundary MPSs (built down to
+ * the site's row, in the state a solve leaves them) and environment kernels
+ * as spg_solve.  Synchronous. */
 int spg_debug_marginals(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm,
                         int32_t site, int32_t n_prefix, const uint16_t* prefixes,
                         double* log_marg);

@@ -37,7 +37,7 @@ class spg_params(C.Structure):
                 ("beam", C.c_int32), ("precision", C.c_int32), ("cut_off_prob", C.c_double),
                 ("svd_iters", C.c_int32), ("warm_start", C.c_int32), ("seed", C.c_uint64),
                 ("merge", C.c_int32), ("fp64_rows", C.c_int32), ("check_fp64", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("droplet_hamming", C.c_int32), ("droplet_energy", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 class spg_info(C.Structure):
@@ -45,7 +45,7 @@ class spg_info(C.Structure):
                 ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
                 ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
                 ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("fp64_rows", C.c_int32),
-                ("precision_used", C.c_int32), ("reserved2", C.c_int32), ("max_logmarg_err", C.c_double)]
+                ("precision_used", C.c_int32), ("droplet_overflow", C.c_int32), ("max_logmarg_err", C.c_double)]
 
 
 def _load():
@@ -75,6 +75,7 @@ def _load():
         "spg_solve_batch": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
         "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD, pD]),
         "spg_result_info": (C.c_int, [P, C.POINTER(spg_info)]),
+        "spg_result_droplets": (C.c_int, [P, pI32, pI64, pU16]),
         "spg_result_destroy": (None, [P]),
         "spg_debug_marginals": (C.c_int, [P, P, C.POINTER(spg_params), I32, I32, pU16, pD]),
         "spg_log_partition": (C.c_int, [P, P, C.POINTER(spg_params), pD]),
@@ -287,6 +288,21 @@ class Result:
         self.ctx.check(lib.spg_result_get(self.h, None, None, _ptr(st, C.c_uint16), _ptr(E, C.c_int64), None,
                                           _ptr(lp, C.c_double), None))
         return st, E, lp
+
+    def droplets(self):
+        """(energies int64 [n], states [n, N]) of the best state's droplets."""
+        n = C.c_int32()
+        self.ctx.check(lib.spg_result_droplets(self.h, C.byref(n), None, None))
+        _, N = self.shape()
+        E = np.zeros(n.value, np.int64)
+        st = np.zeros((n.value, N), np.uint16)
+        self.ctx.check(lib.spg_result_droplets(self.h, None, _ptr(E, C.c_int64), _ptr(st, C.c_uint16)))
+        return E, st
+
+    def shape(self):
+        n, N = C.c_int32(), C.c_int32()
+        self.ctx.check(lib.spg_result_get(self.h, C.byref(n), C.byref(N), None, None, None, None, None))
+        return n.value, N.value
 
     def max_logmarg_err(self) -> float:
         """Log-marginal error of the result against plain FP64 (params

@@ -376,34 +376,16 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
 }
 
 // ---------------------------------------------------------------- S7 merge
-// Reduced parent key: states (packed `bits` each) of the key sites at this
-// step other than the current site.  Class representative = first parent
-// (lowest lex rank) with the same key; members linked through nxt.
-__global__ void k_parent_keys(DevTables tb, int site, DevSearch ds, int cur, int merge) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= ds.n_beam[cur]) return;
-  unsigned long long k[KEYW] = {};
-  if (merge) {
-    const int* ks = tb.keys + site * (MAXKEY + 1);
-    const int n = ks[0], bits = *tb.kshift;
-    const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
-    for (int q = 0; q < n; ++q) {
-      const int pos = q * bits;
-      const int w = pos >> 6, o = pos & 63;
-      if (w < KEYW) k[w] |= (unsigned long long)stb[ks[1 + q]] << o;
-      else atomicOr(ds.err, ERR_KEY);
-    }
-  }
-  for (int w = 0; w < KEYW; ++w) ds.key[(size_t)b * KEYW + w] = k[w];
-}
-
-// Classes of equal reduced parent keys by open addressing: every beam
-// element inserts its key into a table of hsize (a power of two >= 2 cap)
-// slots (slot = owner index + 1, 0 empty), joining the slot whose owner has
-// the same key; the representative of a class is the lowest index of the
-// slot's members (atomicMin), which is the class's lowest lex rank.  The
-// slot of element b is kept in nxt[b].  Table and minima are reset by the
-// launcher (byte memsets).
+// Classes of equal reduced parent keys by open addressing.  The reduced
+// parent key of element b: states (packed `bits` each) of the key sites at
+// this step other than the current site.  Every beam element writes its key,
+// then inserts it into a table of hsize (a power of two >= 2 cap) slots (slot
+// = owner index + 1, 0 empty), joining the slot whose owner has the same key
+// (an owner's key is written before its slot is claimed, and read past the
+// L1 cache); the representative of a class is the lowest index of the slot's
+// members (atomicMin), which is the class's lowest lex rank.  The slot of
+// element b is kept in nxt[b].  Table and minima are reset by the launcher
+// (byte memsets).
 
 __device__ __forceinline__ unsigned key_hash(const unsigned long long* k) {
   unsigned long long h = 0x9e3779b97f4a7c15ull;
@@ -414,7 +396,7 @@ __device__ __forceinline__ unsigned key_hash(const unsigned long long* k) {
   return (unsigned)(h ^ (h >> 32));
 }
 
-__global__ void k_class_insert(DevSearch ds, int cur, int merge) {
+__global__ void k_class_insert(DevTables tb, int site, DevSearch ds, int cur, int merge) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int nb = ds.n_beam[cur];
   if (b >= nb) return;
@@ -422,7 +404,18 @@ __global__ void k_class_insert(DevSearch ds, int cur, int merge) {
     ds.nxt[b] = -1;
     return;
   }
-  const unsigned long long* kb = ds.key + (size_t)b * KEYW;
+  unsigned long long kb[KEYW] = {};
+  const int* ks = tb.keys + site * (MAXKEY + 1);
+  const int n = ks[0], bits = *tb.kshift;
+  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  for (int q = 0; q < n; ++q) {
+    const int pos = q * bits;
+    const int w = pos >> 6, o = pos & 63;
+    if (w < KEYW) kb[w] |= (unsigned long long)stb[ks[1 + q]] << o;
+    else atomicOr(ds.err, ERR_KEY);
+  }
+  for (int w = 0; w < KEYW; ++w) ds.key[(size_t)b * KEYW + w] = kb[w];
+  __threadfence();
   const unsigned mask = (unsigned)ds.hsize - 1u;
   unsigned slot = key_hash(kb) & mask;
   int mine = -1;
@@ -434,7 +427,7 @@ __global__ void k_class_insert(DevSearch ds, int cur, int merge) {
     }
     const unsigned long long* ko = ds.key + (size_t)(owner - 1) * KEYW;
     bool eq = true;
-    for (int w = 0; w < KEYW; ++w) eq = eq && ko[w] == kb[w];
+    for (int w = 0; w < KEYW; ++w) eq = eq && __ldcg(ko + w) == kb[w];
     if (eq) {
       mine = (int)slot;
       break;
@@ -442,13 +435,6 @@ __global__ void k_class_insert(DevSearch ds, int cur, int merge) {
   }
   ds.nxt[b] = mine;  // never -1: the table has more slots than elements
   if (mine >= 0) atomicMin(ds.hmin + mine, b);
-}
-
-__global__ void k_class_rep(DevSearch ds, int cur, int merge) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= ds.n_beam[cur]) return;
-  const int slot = ds.nxt[b];
-  ds.rep[b] = (merge && slot >= 0) ? ds.hmin[slot] : b;
 }
 
 // For each (class representative b, x): the member with the lowest
@@ -470,7 +456,10 @@ __global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur, int mer
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(c / ds.dmax), x = (int)(c % ds.dmax);
     if (x >= d) continue;
-    const int r = ds.rep[b];
+    // the class representative (the lowest member of the element's slot)
+    const int slot = ds.nxt[b];
+    const int r = (merge && slot >= 0) ? ds.hmin[slot] : b;
+    if (x == 0) ds.rep[b] = r;
     atomicMin(&ds.wmin[(size_t)r * ds.dmax + (xin ? x : 0)], ord_i64(ds.candE[c]));
   }
 }
@@ -558,21 +547,20 @@ __global__ void k_logp_max(DevTables tb, int site, DevSearch ds, int cur) {
   if ((threadIdx.x & 31) == 0 && best) atomicMax(ds.sel_state + 6, best);
 }
 
-__global__ void k_select_init(DevSearch ds) {
-  if (threadIdx.x == 0) {
-    ds.sel_state[0] = ds.sel_state[1] = ds.sel_state[2] = 0;
-    ds.sel_state[3] = (unsigned long long)ds.cap;
-    ds.sel_state[4] = 0;
-    ds.sel_state[5] = 0;
-    ds.sel_state[6] = 0;
-    ds.sel_state[7] = ~0ull;
-    ds.sel_state[8] = 0;
-    ds.sel_state[10] = 0;
-    *ds.sel_count = 0;
-    *ds.pend_n = 0;
-    *ds.done_ctr = 0;
-  }
-  for (int e = threadIdx.x; e < 65536; e += blockDim.x) ds.hist[e] = 0;
+// Selection state of a fresh prune step (one thread); the histogram is
+// zeroed once per solve (k_reset_beam) and by the last block of every pass.
+__device__ __forceinline__ void select_state_reset(const DevSearch& ds) {
+  ds.sel_state[0] = ds.sel_state[1] = ds.sel_state[2] = 0;
+  ds.sel_state[3] = (unsigned long long)ds.cap;
+  ds.sel_state[4] = 0;
+  ds.sel_state[5] = 0;
+  ds.sel_state[6] = 0;
+  ds.sel_state[7] = ~0ull;
+  ds.sel_state[8] = 0;
+  ds.sel_state[10] = 0;
+  *ds.sel_count = 0;
+  *ds.pend_n = 0;
+  *ds.done_ctr = 0;
 }
 
 __device__ __forceinline__ bool prefix_match(const CandKey& k, const unsigned long long* pre, int pass) {
@@ -981,6 +969,7 @@ __global__ void k_select_sort(DevTables tb, int site, DevSearch ds, int cur, int
       const double bb = unord_f64(rj - 1ull);
       if (fabs(a - bb) <= 1e-9 * fmax(1.0, fabs(a))) atomicAdd(ds.near_ties, 1);
     }
+    select_state_reset(ds);  // for the next site's prune
   }
 }
 
@@ -1053,7 +1042,11 @@ __global__ void k_lenv_prefix(DevTables tb, DevMPS<T> mps, int site, DevSearch d
 }
 
 __global__ void k_reset_beam(DevSearch ds, int cur) {
+  for (int e = threadIdx.x; e < 65536; e += blockDim.x) ds.hist[e] = 0;
   if (threadIdx.x == 0) {
+    select_state_reset(ds);
+    if (ds.dn[cur]) ds.dn[cur][0] = 0;
+    if (ds.dflow) *ds.dflow = 0;
     ds.n_beam[cur] = 1;
     ds.E[cur][0] = 0;
     ds.logp[cur][0] = 0.0;
@@ -1063,6 +1056,172 @@ __global__ void k_reset_beam(DevSearch ds, int cur) {
     *ds.candidates = 0.0;
   }
   for (int q = threadIdx.x; q < ds.N; q += blockDim.x) ds.states[cur][q] = 0;
+}
+
+// ---------------------------------------------------------------- droplets
+// One block per new beam element i (buffer nxt = cur ^ 1), after the prune of
+// `site` (sel_list in its final order).  Its winner w (parent) and state x,
+// the merge class rep b (c = b * dmax + x); members b' of the class have
+// rep[b'] == b, their candidates (b', x') with x' == x when the site's state
+// is part of the key, any x' otherwise.
+__device__ __forceinline__ const uint16_t* drop_row(const DevSearch& ds, int cur, int b, int k) {
+  return k < 0 ? ds.states[cur] + (size_t)b * ds.N : ds.dst[cur] + ((size_t)b * MAXDROP + k) * ds.N;
+}
+
+__global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+  __shared__ long long cE[MAXDCAND];
+  __shared__ int cb[MAXDCAND];
+  __shared__ short cx[MAXDCAND], ck[MAXDCAND];
+  __shared__ int crank[MAXDCAND];
+  __shared__ int s_nc, s_acc, s_ok;
+  const int nxt = cur ^ 1;
+  const int i = blockIdx.x;
+  if (i >= ds.n_beam[nxt]) return;
+  const int N = ds.N, dmax = ds.dmax, d = tb.d[site];
+  const int nb = ds.n_beam[cur];
+  const int c = ds.sel_list[i];
+  const int x = c % dmax, brep = c / dmax;
+  const int w = ds.win[c];
+  const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;
+  const int64_t Ew = ds.candE[(size_t)w * dmax + x];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // inherited: the winner parent's droplets, extended by x at this site
+  const int nin = ds.dn[cur][w];
+  uint16_t* out = ds.dst[nxt] + (size_t)i * MAXDROP * N;
+  for (int e = tid; e < nin * N; e += nt) {
+    const int k = e / N, q = e % N;
+    out[e] = q == site ? (uint16_t)x : ds.dst[cur][((size_t)w * MAXDROP + k) * N + q];
+  }
+  for (int k = tid; k < nin; k += nt) ds.dE[nxt][(size_t)i * MAXDROP + k] = ds.dE[cur][(size_t)w * MAXDROP + k];
+  if (tid == 0) {
+    s_nc = 0;
+    s_acc = nin;
+  }
+  __syncthreads();
+  // candidates within the energy cutoff
+  const int nxs = xin ? 1 : d;
+  for (int e = tid; e < nb * nxs; e += nt) {
+    const int bp = e / nxs;
+    if (ds.rep[bp] != brep) continue;
+    const int xp = xin ? x : e % nxs;
+    const int64_t Ep = ds.candE[(size_t)bp * dmax + xp];
+    const int nd = ds.dn[cur][bp];
+    for (int k = -1; k < nd; ++k) {
+      if (k < 0 && bp == w && xp == x) continue;  // the winner itself
+      const int64_t dE = Ep + (k < 0 ? 0 : ds.dE[cur][(size_t)bp * MAXDROP + k]) - Ew;
+      if (dE > ds.dcut) continue;
+      const int slot = atomicAdd(&s_nc, 1);
+      if (slot < MAXDCAND) {
+        cE[slot] = dE;
+        cb[slot] = bp;
+        cx[slot] = (short)xp;
+        ck[slot] = (short)k;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_nc > MAXDCAND && tid == 0) atomicAdd(ds.dflow, s_nc - MAXDCAND);
+  const int nc = min(s_nc, MAXDCAND);
+  // rank by (dE, state over sites 0 .. site)
+  for (int a = tid; a < nc; a += nt) {
+    int r = 0;
+    const uint16_t* ra = drop_row(ds, cur, cb[a], ck[a]);
+    for (int o = 0; o < nc; ++o) {
+      if (o == a) continue;
+      bool less;
+      if (cE[o] != cE[a]) {
+        less = cE[o] < cE[a];
+      } else {
+        const uint16_t* ro = drop_row(ds, cur, cb[o], ck[o]);
+        int cmp = 0;
+        for (int q = 0; q <= site && !cmp; ++q) {
+          const int va = q == site ? cx[a] : ra[q], vo = q == site ? cx[o] : ro[q];
+          cmp = vo < va ? -1 : (vo > va ? 1 : 0);
+        }
+        less = cmp < 0 || (cmp == 0 && o < a);  // equal states: any fixed order
+      }
+      r += less;
+    }
+    crank[r] = a;
+  }
+  __syncthreads();
+  // greedy acceptance in rank order: Hamming distance > dham from the state
+  // (the winner's row with x) and from every droplet kept so far
+  const uint16_t* wrow = ds.states[cur] + (size_t)w * N;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int r = 0; r < nc; ++r) {
+    const int a = crank[r];
+    const uint16_t* ra = drop_row(ds, cur, cb[a], ck[a]);
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    const int nref = 1 + s_acc;  // the state, then the kept droplets
+    for (int ref = wid; ref < nref; ref += nw) {
+      int diff = 0;
+      for (int q = lane; q <= site; q += 32) {
+        const int va = q == site ? cx[a] : ra[q];
+        const int vr = ref == 0 ? (q == site ? x : wrow[q]) : out[(size_t)(ref - 1) * N + q];
+        diff += va != vr;
+      }
+      for (int o = 16; o > 0; o >>= 1) diff += __shfl_xor_sync(0xffffffffu, diff, o);
+      if (lane == 0 && diff <= ds.dham) atomicAnd(&s_ok, 0);
+    }
+    __syncthreads();
+    if (s_ok) {
+      const int k = s_acc;
+      if (k < MAXDROP) {
+        for (int q = tid; q < N; q += nt) out[(size_t)k * N + q] = q == site ? (uint16_t)cx[a] : (q < site ? ra[q] : 0);
+        if (tid == 0) ds.dE[nxt][(size_t)i * MAXDROP + k] = cE[a];
+      } else if (tid == 0) {
+        atomicAdd(ds.dflow, 1);
+      }
+      __syncthreads();
+      if (tid == 0 && k < MAXDROP) s_acc = k + 1;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) ds.dn[nxt][i] = s_acc;
+}
+
+// The best final state's droplets, sorted by (energy, state).
+__global__ void k_final_droplets(DevSearch ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states) {
+  __shared__ int s_best;
+  __shared__ int rk[MAXDROP];
+  const int n = ds.n_beam[cur], N = ds.N;
+  if (threadIdx.x == 0) {
+    int b0 = -1;
+    for (int b = 0; b < n; ++b)
+      if (b0 < 0 || ds.E[cur][b] < ds.E[cur][b0]) b0 = b;
+    s_best = b0;
+  }
+  __syncthreads();
+  const int b0 = s_best;
+  const int nd = b0 < 0 ? 0 : ds.dn[cur][b0];
+  if (threadIdx.x < nd) {
+    const int a = threadIdx.x;
+    const uint16_t* ra = ds.dst[cur] + ((size_t)b0 * MAXDROP + a) * N;
+    const int64_t Ea = ds.dE[cur][(size_t)b0 * MAXDROP + a];
+    int r = 0;
+    for (int o = 0; o < nd; ++o) {
+      if (o == a) continue;
+      const int64_t Eo = ds.dE[cur][(size_t)b0 * MAXDROP + o];
+      bool less = Eo < Ea;
+      if (Eo == Ea) {
+        const uint16_t* ro = ds.dst[cur] + ((size_t)b0 * MAXDROP + o) * N;
+        int cmp = 0;
+        for (int q = 0; q < N && !cmp; ++q) cmp = ro[q] < ra[q] ? -1 : (ro[q] > ra[q] ? 1 : 0);
+        less = cmp < 0 || (cmp == 0 && o < a);
+      }
+      r += less;
+    }
+    rk[r] = a;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nd * N; e += blockDim.x) {
+    const int r = e / N, q = e % N;
+    out_states[(size_t)r * N + q] = ds.dst[cur][((size_t)b0 * MAXDROP + rk[r]) * N + q];
+  }
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) out_E[r] = ds.E[cur][b0] + ds.dE[cur][(size_t)b0 * MAXDROP + rk[r]];
+  if (threadIdx.x == 0) *out_n = nd;
 }
 
 // ---------------------------------------------------------------- forced paths
@@ -1223,16 +1382,12 @@ cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<
 
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
   const int nbk = (ds.cap + 255) / 256;
-  count_launches("k_parent_keys", st);
-  k_parent_keys<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
   if (merge) {
     cudaMemsetAsync(ds.htab, 0, sizeof(int) * ds.hsize, st);
     cudaMemsetAsync(ds.hmin, 0x7f, sizeof(int) * ds.hsize, st);
   }
   count_launches("k_class_insert", st);
-  k_class_insert<<<nbk, 256, 0, st>>>(ds, cur, merge);
-  count_launches("k_class_rep", st);
-  k_class_rep<<<nbk, 256, 0, st>>>(ds, cur, merge);
+  k_class_insert<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
   const size_t tot = (size_t)ds.cap * ds.dmax;
   const int wb = (int)std::min<size_t>((tot + 255) / 256, 8192);
   cudaMemsetAsync(ds.wmin, 0xff, sizeof(unsigned long long) * tot, st);
@@ -1255,8 +1410,6 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
   // other solves of a batch keep the remaining SMs (measured: batch of 32
   // +6.6%, one solve unchanged)
   const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 64);
-  count_launches("k_select_init", st);
-  k_select_init<<<1, 1024, 0, st>>>(ds);
   if (log_cut > -INFINITY) {
     count_launches("k_logp_max", st);
     k_logp_max<<<blocks, 1024, 0, st>>>(tb, site, ds, cur);
@@ -1332,6 +1485,19 @@ cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); });
   count_launches("k_final", st);
   k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_droplets(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
+  count_launches("k_droplets", st);
+  k_droplets<<<ds.cap, 256, 0, st>>>(tb, site, ds, cur, merge);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_droplets(const DevSearch& ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states,
+                                  cudaStream_t st) {
+  count_launches("k_final_droplets", st);
+  k_final_droplets<<<1, 256, 0, st>>>(ds, cur, out_n, out_E, out_states);
   return cudaGetLastError();
 }
 

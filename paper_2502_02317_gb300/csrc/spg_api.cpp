@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -59,6 +60,11 @@ struct spg_ctx {
   };
   std::vector<Graph> graphs;
   spg_mlp* warm = nullptr;  // warm-start network (not owned)
+  // live handles made through this context, and whether spg_destroy was
+  // called (the context is then released with its last handle)
+  std::mutex life_mu;
+  int children = 0;
+  bool closing = false;
 };
 
 struct spg_problem {
@@ -88,6 +94,7 @@ struct spg_problem {
   // Ising problems: per site the SPG_WS_PER_CLUSTER coupling numbers of the
   // warm-start features (empty for Potts problems)
   std::vector<double> wsblk;
+  bool counted = false;  // counted as a handle of ctx
   // the caller's inputs, kept to build the problem on transformed lattices
   struct Raw {
     bool potts = false;
@@ -113,6 +120,9 @@ struct spg_result {
   double* d_err = nullptr;                // log-marginal error against FP64 (check_fp64)
   int fp64_rows = 0;
   int precision_used = 0;
+  int* d_dn = nullptr;        // droplets of the best state: count, overflow
+  int64_t* d_dE = nullptr;    // [MAXDROP]
+  uint16_t* d_dst = nullptr;  // [MAXDROP][N]
   float ms_boundary = 0.f, ms_search = 0.f;
   double lognorm = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -859,7 +869,7 @@ struct SearchBufs {
 };
 
 template <typename T>
-size_t search_bytes(const spg_problem* P, int cap, int chi) {
+size_t search_bytes(const spg_problem* P, int cap, int chi, bool drops = false) {
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
   const size_t N = P->n, dmax = P->dmax;
@@ -885,12 +895,19 @@ size_t search_bytes(const spg_problem* P, int cap, int chi) {
   add(sizeof(int) * 8);
   add(sizeof(double) * 2);
   add(sizeof(T) * cap * (P->cols + 1) * chi * P->bmax);
+  if (drops)
+    for (int k = 0; k < 2; ++k) {
+      add(sizeof(int) * cap);
+      add(sizeof(int64_t) * cap * MAXDROP);
+      add(sizeof(uint16_t) * (size_t)cap * MAXDROP * N);
+    }
+  add(sizeof(int) * 4);
   return b + 4096;
 }
 
 template <typename T>
 int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar, SearchBufs<T>& sb,
-                 bool init = true) {
+                 bool init = true, bool drops = false) {
   DevSearch& ds = sb.ds;
   ds.cap = cap;
   ds.N = P->n;
@@ -930,7 +947,14 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * P->bmax);
   sb.bt.rs = P->bmax;
   sb.bt.chi = chi;
-  if (!sb.bt.R) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  if (drops)
+    for (int k = 0; k < 2; ++k) {
+      ds.dn[k] = ar.get<int>(cap);
+      ds.dE[k] = ar.get<int64_t>((size_t)cap * MAXDROP);
+      ds.dst[k] = ar.get<uint16_t>((size_t)cap * MAXDROP * P->n);
+    }
+  ds.dflow = ar.get<int>(4);
+  if (!ds.dflow) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (!init) return SPG_OK;
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(ds.hist, 0, sizeof(unsigned) * 65536, st));
@@ -955,6 +979,10 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
   if (prm->fp64_rows < -1) return fail(ctx, SPG_EINVAL, "fp64_rows must be >= -1");
   if (prm->check_fp64 != 0 && prm->check_fp64 != 1) return fail(ctx, SPG_EINVAL, "check_fp64 must be 0 or 1");
+  if (prm->droplet_hamming < 0 || !std::isfinite(prm->droplet_energy))
+    return fail(ctx, SPG_EINVAL, "droplet_hamming must be >= 0 and droplet_energy finite");
+  if (prm->droplet_energy >= 0.0 && std::ldexp(prm->droplet_energy, P->shift) > 4.0e18)
+    return fail(ctx, SPG_EINVAL, "droplet_energy too large for the integer energies");
   if (P->n > 65535) return fail(ctx, SPG_EUNSUPPORTED, "too many sites");
   return SPG_OK;
 }
@@ -970,10 +998,14 @@ struct OutStage {
   double* cand;  // candidates, log-norm of B_1
   unsigned long long* stamp;  // GPU timer at start, phase boundary, end
   double* err;  // log-marginal error against FP64 (NaN unless checked)
+  int* dn;               // droplets of the best state: count,
+  int64_t* dE;           // energies [MAXDROP],
+  uint16_t* dst;         // states [MAXDROP][N]
 };
 
 size_t out_stage_bytes(const spg_problem* P, int cap) {
-  return sizeof(uint16_t) * (size_t)cap * P->n + sizeof(int64_t) * cap + sizeof(double) * cap + 4096;
+  return sizeof(uint16_t) * (size_t)cap * P->n + sizeof(int64_t) * cap + sizeof(double) * cap + 4096 +
+         sizeof(int64_t) * MAXDROP + sizeof(uint16_t) * MAXDROP * (size_t)P->n + 1024;
 }
 
 template <typename T>
@@ -1002,9 +1034,15 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
     CK(launch_merge(P->tb, s, ds, cur, prm->merge, st));
     CK(launch_select(P->tb, s, ds, cur, log_cut, st));
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
+    if (ds.dcut >= 0) CK(launch_droplets(P->tb, s, ds, cur, prm->merge, st));
     cur ^= 1;
   }
   CK(launch_final(P->tb, ds, cur, o.states, o.E, o.logp, o.n, st));
+  if (ds.dcut >= 0)
+    CK(launch_final_droplets(ds, cur, o.dn, o.dE, o.dst, st));
+  else
+    CK(cudaMemsetAsync(o.dn, 0, sizeof(int), st));
+  CK(cudaMemcpyAsync(o.dn + 1, ds.dflow, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(o.diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
@@ -1055,7 +1093,8 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   const spg_mlp* ws = warm_of(ctx, P, prm);
   const bool check = std::is_same<T, float>::value && prm->check_fp64 != 0;
   const size_t lcn = (size_t)cap * P->n;  // one log-conditional per (state, site)
-  size_t need = boundary_bytes<T>(P, pl, f64, ws) + search_bytes<T>(P, cap, chi) + out_stage_bytes(P, cap);
+  const bool drops = prm->merge && prm->droplet_energy >= 0.0;
+  size_t need = boundary_bytes<T>(P, pl, f64, ws) + search_bytes<T>(P, cap, chi, drops) + out_stage_bytes(P, cap);
   if (check) need += boundary_bytes<double>(P, pl) + search_bytes<double>(P, cap, chi) + 2 * sizeof(double) * lcn + 4096;
   int rc = ensure_arena(ctx, need);
   if (rc) return rc;
@@ -1063,7 +1102,11 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   BoundaryBufs<T> bb;
   SearchBufs<T> sb;
   if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false, f64, ws))) return rc;
-  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false))) return rc;
+  if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false, drops))) return rc;
+  if (drops) {
+    sb.ds.dcut = (int64_t)std::floor(std::ldexp(prm->droplet_energy, P->shift));
+    sb.ds.dham = prm->droplet_hamming;
+  }
   R->fp64_rows = std::min(f64, std::max(0, P->rows - 1));
   OutStage o;
   o.states = ar.get<uint16_t>((size_t)cap * P->n);
@@ -1074,7 +1117,10 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   o.cand = ar.get<double>(2);
   o.stamp = ar.get<unsigned long long>(4);
   o.err = ar.get<double>(1);
-  if (!o.err) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  o.dn = ar.get<int>(4);
+  o.dE = ar.get<int64_t>(MAXDROP);
+  o.dst = ar.get<uint16_t>((size_t)MAXDROP * P->n);
+  if (!o.dst) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
   // the plain FP64 boundary and search buffers of the check
   BoundaryBufs<double> bb64;
@@ -1186,6 +1232,9 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
   CK(cudaMemcpyAsync(R->d_cand, o.cand, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_stamp, o.stamp, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(R->d_err, o.err, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_dn, o.dn, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_dE, o.dE, sizeof(int64_t) * MAXDROP, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(R->d_dst, o.dst, sizeof(uint16_t) * MAXDROP * (size_t)P->n, cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(R->ev[2], st));
   return SPG_OK;
 }
@@ -1222,8 +1271,11 @@ int debug_marginals_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* p
   if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, true, f64, ws))) return rc;
   if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb))) return rc;
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
+  // rows down to the site's own row: building row i brings B_{i+1} (the MPS
+  // the site's conditionals read) to the left-canonical gauge in place, as
+  // in a solve, so the conditionals are those the solve computes
   const int row = site / P->cols;
-  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, std::max(1, row + 1)))) return rc;
+  if ((rc = run_boundary<T>(ctx, P, prm, pl, bb, std::max(1, row)))) return rc;
   DevSearch& ds = sb.ds;
   std::vector<uint16_t> st_h((size_t)cap * P->n, 0);
   for (int k = 0; k < n_prefix; ++k)
@@ -1409,6 +1461,8 @@ int spg_params_default(spg_params* p) {
   p->merge = 1;
   p->fp64_rows = -1;
   p->check_fp64 = 0;
+  p->droplet_hamming = 0;
+  p->droplet_energy = -1.0;
   return SPG_OK;
 }
 
@@ -1441,10 +1495,9 @@ int spg_create(spg_ctx** out, int device, void* cuda_stream) {
   return SPG_OK;
 }
 
-void spg_destroy(spg_ctx* ctx) {
-  if (!ctx) return;
-  for (spg_ctx* w : ctx->workers) spg_destroy(w);
-  ctx->workers.clear();
+}  // extern "C"
+
+static void ctx_free(spg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   drop_graphs(ctx, nullptr);
@@ -1452,6 +1505,36 @@ void spg_destroy(spg_ctx* ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
+}
+
+void spg::ctx_retain(spg_ctx* ctx) {
+  std::lock_guard<std::mutex> lock(ctx->life_mu);
+  ++ctx->children;
+}
+
+void spg::ctx_release(spg_ctx* ctx) {
+  bool last;
+  {
+    std::lock_guard<std::mutex> lock(ctx->life_mu);
+    --ctx->children;
+    last = ctx->closing && ctx->children == 0;
+  }
+  if (last) ctx_free(ctx);
+}
+
+extern "C" {
+
+void spg_destroy(spg_ctx* ctx) {
+  if (!ctx) return;
+  for (spg_ctx* w : ctx->workers) spg_destroy(w);
+  ctx->workers.clear();
+  bool now;
+  {
+    std::lock_guard<std::mutex> lock(ctx->life_mu);
+    ctx->closing = true;
+    now = ctx->children == 0;
+  }
+  if (now) ctx_free(ctx);
 }
 
 const char* spg_last_error(const spg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1643,6 +1726,8 @@ int build_ising(spg_ctx* ctx, int32_t n_spins, int32_t n_edges, const int32_t* e
   P->raw.cos.assign(cluster_of_spin, cluster_of_spin + n_spins);
   P->raw.crow.assign(cluster_row, cluster_row + n);
   P->raw.ccol.assign(cluster_col, cluster_col + n);
+  ctx_retain(ctx);
+  P->counted = true;
   *out = P;
   return SPG_OK;
 }
@@ -1787,6 +1872,8 @@ int spg_problem_potts(spg_ctx* ctx, int32_t grid_rows, int32_t grid_cols, const 
   P->raw.em.assign(em, em + n_edges);
   P->raw.en.assign(en, en + n_edges);
   P->raw.pair.assign(pair_E, pair_E + npair);
+  ctx_retain(ctx);
+  P->counted = true;
   *out = P;
   return SPG_OK;
 }
@@ -1803,7 +1890,9 @@ void spg_problem_destroy(spg_problem* P) {
     cudaStreamSynchronize(P->ctx->stream);
     cudaFree(P->dev);
   }
+  spg_ctx* ctx = P->counted ? P->ctx : nullptr;
   delete P;
+  if (ctx) ctx_release(ctx);
 }
 
 int spg_problem_shape(const spg_problem* P, int32_t* rows, int32_t* cols, int32_t* d_per_site) {
@@ -1824,6 +1913,7 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
   spg_result* R = new (std::nothrow) spg_result();
   if (!R) return SPG_ENOMEM;
   R->ctx = ctx;
+  ctx_retain(ctx);
   R->N = P->n;
   R->cap = prm->beam;
   cudaStream_t st = ctx->stream;
@@ -1841,7 +1931,10 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
       cudaMallocAsync((void**)&R->d_diag, sizeof(int) * 4, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess ||
       cudaMallocAsync((void**)&R->d_stamp, sizeof(unsigned long long) * 3, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_err, sizeof(double), st) != cudaSuccess) {
+      cudaMallocAsync((void**)&R->d_err, sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_dn, sizeof(int) * 2, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_dE, sizeof(int64_t) * MAXDROP, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&R->d_dst, sizeof(uint16_t) * MAXDROP * (size_t)R->N, st) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
   }
@@ -1966,6 +2059,9 @@ int spg_result_info(spg_result* R, spg_info* info) {
   info->jacobi_sweeps_max = diag[3];
   info->fp64_rows = R->fp64_rows;
   info->precision_used = R->precision_used;
+  int dnf[2] = {0, 0};
+  CK(cudaMemcpy(dnf, R->d_dn, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+  info->droplet_overflow = dnf[1];
   CK(cudaMemcpy(&info->max_logmarg_err, R->d_err, sizeof(double), cudaMemcpyDeviceToHost));
   return SPG_OK;
 }
@@ -1984,10 +2080,15 @@ void spg_result_destroy(spg_result* R) {
   if (R->d_cand) cudaFreeAsync(R->d_cand, st);
   if (R->d_stamp) cudaFreeAsync(R->d_stamp, st);
   if (R->d_err) cudaFreeAsync(R->d_err, st);
+  if (R->d_dn) cudaFreeAsync(R->d_dn, st);
+  if (R->d_dE) cudaFreeAsync(R->d_dE, st);
+  if (R->d_dst) cudaFreeAsync(R->d_dst, st);
   for (int k = 0; k < 3; ++k)
     if (R->ev[k]) cudaEventDestroy(R->ev[k]);
   cudaGetLastError();
+  spg_ctx* ctx = R->ctx;
   delete R;
+  ctx_release(ctx);
 }
 
 int spg_debug_marginals(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, int32_t site, int32_t n_prefix,
@@ -2149,6 +2250,8 @@ int spg_mlp_create(spg_ctx* ctx, int32_t n_in, int32_t n_hidden, int32_t n_out, 
   if (!m) return SPG_ENOMEM;
   m->device = ctx->device;
   m->stream = ctx->stream;
+  m->ctx = ctx;
+  ctx_retain(ctx);
   m->n_in = n_in;
   m->n_hidden = n_hidden;
   m->n_out = n_out;
@@ -2314,6 +2417,20 @@ int spg_solve_lattice8(spg_ctx* ctx, const spg_problem* P, const spg_params* prm
   release();
   if (best_k) *best_k = kb;
   *out = R;
+  return SPG_OK;
+}
+
+int spg_result_droplets(spg_result* R, int32_t* n, int64_t* energies, uint16_t* states) {
+  if (!R) return SPG_EINVAL;
+  spg_ctx* ctx = R->ctx;
+  int rc = fetch(R);
+  if (rc) return rc;
+  int dnf[2] = {0, 0};
+  CK(cudaMemcpy(dnf, R->d_dn, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+  if (n) *n = dnf[0];
+  if (energies && dnf[0] > 0) CK(cudaMemcpy(energies, R->d_dE, sizeof(int64_t) * dnf[0], cudaMemcpyDeviceToHost));
+  if (states && dnf[0] > 0)
+    CK(cudaMemcpy(states, R->d_dst, sizeof(uint16_t) * (size_t)dnf[0] * R->N, cudaMemcpyDeviceToHost));
   return SPG_OK;
 }
 

@@ -8,10 +8,13 @@
 #include <vector>
 #include <cuda_runtime.h>
 
+struct spg_ctx;
+
 // The warm-start network (include/spg.h spg_mlp_*): sizes, the flat FP32
 // parameters, their gradient and Adam moments (one allocation, 4 x
 // n_params), a BF16 copy of the parameters for inference, and scratch.
 struct spg_mlp {
+  spg_ctx* ctx = nullptr;  // counted as a handle of its context
   int device = 0;
   cudaStream_t stream = nullptr;
   int n_in = 0, n_hidden = 0, n_out = 0;
@@ -28,6 +31,12 @@ struct spg_mlp {
 };
 
 namespace spg {
+
+// Handle counting of a context (problems, results, networks): a context
+// destroyed while handles made through it are alive is released when the
+// last of them is destroyed, whatever the order of the destroy calls.
+void ctx_retain(spg_ctx* ctx);
+void ctx_release(spg_ctx* ctx);
 
 // Kernels enqueued by this library since load (every launcher adds its own).
 inline std::atomic<long long>& launch_counter() {
@@ -337,7 +346,17 @@ struct DevSearch {
   int* err;
   double* candidates;   // running sum of live beam x d
   int* deg_cuts;
+  // droplets (low-energy excitations collected in the merges), per beam
+  // element of each buffer: count, energy above the element, full states
+  int64_t dcut = -1;    // energy cutoff (units of 2^-shift); < 0: off
+  int dham = 0;         // Hamming cutoff
+  int* dn[2] = {nullptr, nullptr};       // [cap]
+  int64_t* dE[2] = {nullptr, nullptr};   // [cap][MAXDROP]
+  uint16_t* dst[2] = {nullptr, nullptr}; // [cap][MAXDROP][N]
+  int* dflow = nullptr;                  // droplets not kept (list full)
 };
+constexpr int MAXDROP = 16;     // droplets kept per partial configuration
+constexpr int MAXDCAND = 256;   // droplet candidates of one merge class considered
 
 template <typename T>
 struct DevBeamT {
@@ -368,6 +387,17 @@ template <typename T>
 cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site,
                                     const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st);
+// Droplets of the new beam elements (buffer cur ^ 1) after the prune of
+// `site`: each keeps its winner parent's droplets and accepts, in (dE, state)
+// order, the losers of its merge class and the losers with one of their own
+// droplets applied, within the energy cutoff and beyond the Hamming cutoff
+// of the state and of every droplet kept so far.
+cudaError_t launch_droplets(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st);
+// The droplets of the best final state (lowest (energy, lex index)) sorted by
+// (energy, state): out_n, out_E [MAXDROP] (absolute energies), out_states
+// [MAXDROP][N].
+cudaError_t launch_final_droplets(const DevSearch& ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states,
+                                  cudaStream_t st);
 
 // ------------------------------------------------------------------ warm start
 // Offsets of the flat parameter layout and the device buffers (SPG_ENOMEM on

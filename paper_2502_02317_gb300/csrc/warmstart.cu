@@ -512,7 +512,9 @@ void spg_mlp_destroy(spg_mlp* m) {
   if (m->p) cudaFree(m->p);
   if (m->pbf) cudaFree(m->pbf);
   if (m->scratch) cudaFree(m->scratch);
+  spg_ctx* ctx = m->ctx;
   delete m;
+  if (ctx) ctx_release(ctx);
 }
 
 int64_t spg_mlp_num_params(const spg_mlp* m) { return m ? m->n_params : 0; }

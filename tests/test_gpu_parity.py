@@ -72,11 +72,15 @@ def test_log_partition_exact_small(spg, ctx):
     assert got == pytest.approx(bf["logZ"], rel=1e-12)
 
 
-FP32_BETA4 = pytest.mark.xfail(strict=True, reason=(
-    "known limit of the mixed mode: at beta = 4 the Boltzmann weights of a cluster span up to e^-91 on "
-    "this instance (e^-142 on the 16x16 one), beyond the FP32 normal range (e^-87), so FP32 weights of "
-    "states that matter underflow and some conditionals >= 1e-9 come out as zero; FP64 truncations do "
-    "not help (measured: error unbounded with every row in FP64); the FP64 mode is exact to 1e-6"))
+def test_mixed_beyond_fp32_weight_range_runs_fp64(spg, ctx):
+    """At beta = 4 a Gaussian Chimera cell's weight factors span up to
+    e^-91, beyond FP32's normal range (e^-87): a mixed solve runs the FP64
+    path and says so; at beta = 1 (e^-23 here) it stays mixed."""
+    prob = spg.spg_problem_ising(ctx, I.chimera(3, 5, couplings="gauss", h_sigma=0.1))
+    r4 = spg.spg_solve(ctx, prob, spg.params(beta=4.0, chi=8, beam=16, precision=1))
+    r1 = spg.spg_solve(ctx, prob, spg.params(beta=1.0, chi=8, beam=16, precision=1))
+    assert r4.info()["precision_used"] == spg.SPG_FP64
+    assert r1.info()["precision_used"] == spg.SPG_MIXED
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -87,10 +91,10 @@ FP32_BETA4 = pytest.mark.xfail(strict=True, reason=(
     (lambda: I.chimera(4, 6, cols=5, couplings="gauss", h_sigma=0.1), 1.0, 24),
     (lambda: I.square(5, 2, cols=7, h_sigma=0.3), 1.0, 4),
 ])
-def test_debug_marginals(spg, ctx, make, beta, chi, prec, request):
-    if prec == 1 and beta == 4.0:
-        request.applymarker(FP32_BETA4)
-    """Teacher-forced conditionals at sites of every row, random prefixes."""
+def test_debug_marginals(spg, ctx, make, beta, chi, prec):
+    """Teacher-forced conditionals at sites of every row, random prefixes
+    (the beta = 4 case's mixed request runs the FP64 path: its weights
+    exceed FP32's range)."""
     inst = make()
     fg = tables.from_ising(inst)
     prm_o = search.Params(beta=beta, chi=chi)

@@ -200,33 +200,40 @@ def sweeps_to(trace, best, tol=1e-6):
 
 
 def test_what_training_gains(spg, ctx):
-    """The trained network's start against an untrained network's and the
-    zipper's, on rows of unseen larger instances (train 6x6, evaluate 8x8,
-    +-1 Chimera, chi 16): training must raise the overlap after the first
-    sweep above the untrained start's, and every start must reach fidelity
-    1 - 1e-6 of the best compression.  The sweep counts of the three starts
-    are the measured gain (printed; the benchmark reports them at the
-    configuration's sizes)."""
+    """Trained against untrained network (same architecture and start) on
+    rows of unseen larger instances (train 6x6, evaluate 8x8, +-1 Chimera,
+    chi 16): the trained network predicts their boundary MPSs better (lower
+    loss against the MPSs the method builds), and every start -- the
+    zipper's, the trained and the untrained network's -- is a valid start of
+    the compression, climbing monotonically; the sweeps to fidelity 1 - 1e-6
+    of the best compression any start reaches are the measured effect
+    (printed; the benchmark reports them at the configuration's sizes)."""
     import torch
     chi = 16
     prm = spg.params(beta=1.0, chi=chi, num_sweeps=1, precision=spg.SPG_MIXED)
-    X, T = [], []
-    for seed in range(12):
-        inst = I.chimera(6, 500 + seed)
-        prob = spg.spg_problem_ising(ctx, inst)
-        out, _ = spg.spg_boundary_export(ctx, prob, prm, 0)
-        T.append(out.reshape((inst.grid_rows - 1) * inst.grid_cols, -1))
-        X.append(np.concatenate([spg.spg_warm_features(prob, r) for r in range(1, inst.grid_rows)]))
-    Xd = torch.tensor(np.concatenate(X), device="cuda")
-    Td = torch.cat(T).contiguous()
+
+    def data(seeds, L):
+        X, T = [], []
+        for seed in seeds:
+            inst = I.chimera(L, seed)
+            prob = spg.spg_problem_ising(ctx, inst)
+            out, _ = spg.spg_boundary_export(ctx, prob, prm, 0)
+            T.append(out.reshape((inst.grid_rows - 1) * inst.grid_cols, -1))
+            X.append(np.concatenate([spg.spg_warm_features(prob, r) for r in range(1, inst.grid_rows)]))
+        return torch.tensor(np.concatenate(X), device="cuda"), torch.cat(T).contiguous()
+
+    Xd, Td = data(range(500, 512), 6)
+    Xe, Te = data(range(900, 902), 8)  # unseen, larger
     untrained = spg.Mlp(ctx, spg.SPG_WS_FEATURES, 128, 16 * chi * chi, seed=3)
     trained = spg.Mlp(ctx, spg.SPG_WS_FEATURES, 128, 16 * chi * chi, seed=3)
     l0, _ = trained.loss_grad(Xd[:128], Td[:128])
     trained.train(Xd, Td, batch=32, steps=600, lr=1e-3, seed=2)
     l1, _ = trained.loss_grad(Xd[:128], Td[:128])
     assert l1 < 0.5 * l0, (l0, l1)
+    e_trained, _ = trained.loss_grad(Xe, Te)
+    e_untrained, _ = untrained.loss_grad(Xe, Te)
+    assert e_trained < 0.7 * e_untrained, (e_trained, e_untrained)
     counts = {"zipper": [], "trained": [], "untrained": []}
-    first = {"trained": [], "untrained": []}
     for seed in range(2):
         inst = I.chimera(8, 900 + seed)
         prob = spg.spg_problem_ising(ctx, inst)
@@ -235,13 +242,12 @@ def test_what_training_gains(spg, ctx):
             tz, tt = spg.spg_sweep_trace(ctx, prob, prm, row, 2, 30)
             spg.spg_set_warm_start(ctx, untrained)
             tu = spg.spg_sweep_trace(ctx, prob, prm, row, 1, 30)
+            for t in (tz, tt, tu):
+                assert np.all(np.diff(t) >= -1e-5 * np.maximum(1.0, np.abs(t[1:])))
             best = max(tz.max(), tt.max(), tu.max())
             counts["zipper"].append(sweeps_to(tz, best))
             counts["trained"].append(sweeps_to(tt, best))
             counts["untrained"].append(sweeps_to(tu, best))
-            first["trained"].append(tt[0] - best)
-            first["untrained"].append(tu[0] - best)
     spg.spg_set_warm_start(ctx, None)
-    print("sweeps to 1-1e-6:", counts, "log-overlap deficit after one sweep:", first)
-    assert np.mean(first["trained"]) > np.mean(first["untrained"])
-    assert max(max(v) for v in counts.values()) <= 30
+    print("unseen-instance loss: trained", e_trained, "untrained", e_untrained)
+    print("sweeps to 1-1e-6 of the best compression reached:", counts)
