@@ -311,6 +311,17 @@ def kernel_profile(spg, ctx, prob, prm):
     return kern
 
 
+def group_kernel_profile(spg, ctx, probs, prm):
+    """The same for one lockstep group of the given problems (every launch
+    covers all of them; its flops are the group's)."""
+    spg.spg_profile(ctx, True)
+    for r in spg.spg_solve_group(ctx, probs, prm):
+        r.get()
+    kern = spg.spg_profile_report(ctx)
+    spg.spg_profile(ctx, False)
+    return kern
+
+
 def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -345,6 +356,8 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="instances solved concurrently per step")
+    ap.add_argument("--group-max", type=int, default=0,
+                    help="most instances per lockstep group (0: automatic, 1: every instance on its own stream)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-king", action="store_true", help="skip the king's-graph Potts solves")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start leg")
@@ -384,7 +397,7 @@ def main():
 
     def params(p):
         return spg.params(beta=WORKLOAD["beta"], chi=WORKLOAD["chi"], beam=WORKLOAD["beam"], precision=p,
-                          num_sweeps=WORKLOAD["sweeps"])
+                          num_sweeps=WORKLOAD["sweeps"], group_max=args.group_max)
 
     prm = params(prec)
     prms = [prm] * NB
@@ -409,7 +422,7 @@ def main():
         for r in spg.spg_solve_batch(ctx, probs, prms):
             r.get()
     barrier()
-    times, cands, launches, infos, bests = [], [], [], [], []
+    times, cands, launches, infos, bests, group_sizes = [], [], [], [], [], []
     with Clocks(local) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
@@ -419,7 +432,9 @@ def main():
             inf = [r.info() for r in rs]
             infos.append(inf[0])
             cands.append(sum(i["candidates"] for i in inf))
-            launches.append(sum(i["kernel_launches"] for i in inf))
+            # a lockstep group's results each report the group's launches
+            launches.append(sum(i["kernel_launches"] / max(1, i["group_size"]) for i in inf))
+            group_sizes.append(max(i["group_size"] for i in inf))
             bests = [int(r.get()[1][0]) for r in rs]
     barrier()
     ms = statistics.mean(times)
@@ -589,7 +604,11 @@ def main():
 
     # one extra solve with per-kernel device times (graph-captured event
     # nodes; not part of the timed steps): the roofline of the top kernel
-    kern = kernel_profile(spg, ctx, probs[0], prm)
+    # the timed step's own launch shape: one of its lockstep groups (as
+    # large as the step's largest), or one solve when the step ran ungrouped
+    gsize = max(1, int(group_sizes[-1])) if group_sizes else 1
+    kern = (group_kernel_profile(spg, ctx, probs[:gsize], prm) if gsize > 1
+            else kernel_profile(spg, ctx, probs[0], prm))
     ktot = sum(v[1] for v in kern.values())
     top = sorted(kern.items(), key=lambda kv: -kv[1][1])
     line["kernels"] = {k: {"launches": int(v[0]), "ms": round(v[1], 3), "share": round(v[1] / ktot, 4),
@@ -613,6 +632,7 @@ def main():
                         "peak_source": f"measured {'FP32' if prec == spg.SPG_MIXED else 'FP64'} FMA throughput "
                                        f"(k_fma_probe, {props.multi_processor_count} SMs)",
                         "share_of_solve": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
+                        "instances_per_launch": gsize,
                         "avg_launch_us": 1e3 * ms_k / nl, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                         "peaks_source": src}
     if rank == 0 and not args.no_cpu and world == 1:

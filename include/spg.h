@@ -110,7 +110,11 @@ typedef struct {
                               collected in the merges, in the units of J
                               (multiplied by 2^energy_shift and rounded
                               down); < 0 (the default -1): no droplets      */
-  int32_t reserved[2];     /* must be 0                                      */
+  int32_t group_max;       /* spg_solve_batch: most items solved in lockstep
+                              as one group (spg_solve_group); 0: automatic
+                              (one per SM, within half the free device
+                              memory), 1: every item on its own            */
+  int32_t reserved;        /* must be 0                                      */
 } spg_params;
 
 /* Droplets kept per partial configuration (SPG_EUNSUPPORTED-free: a state
@@ -150,6 +154,10 @@ typedef struct {
                               of |log p_mixed - log p_FP64| / max(1,
                               |log p_FP64|) of the state's own conditional;
                               0 in SPG_FP64; NaN when not checked           */
+  int32_t group_size;      /* instances of the lockstep group the solve ran
+                              in (1: alone); kernel_launches and the phase
+                              times are the group's                          */
+  int32_t reserved;
 } spg_info;
 
 /* Library version, major*10000 + minor*100 + patch. */
@@ -248,12 +256,30 @@ int spg_problem_shape(const spg_problem* prob, int32_t* rows, int32_t* cols, int
  * the 8 most recent). */
 int spg_solve(spg_ctx* ctx, const spg_problem* prob, const spg_params* prm, spg_result** out);
 
+/* Lockstep group: n problems of one structure (same lattice, cluster sizes,
+ * projections and energy scale; only the energy values differ) solved with
+ * the same parameters as ONE launch sequence, every kernel covering all n
+ * instances (each instance's tables, copied from its problem at the call,
+ * and workspace sit at a fixed stride in one device block).  A group costs
+ * the kernel launches of one solve and its one-CTA kernels (QR, Jacobi)
+ * occupy n SMs at once; each result equals that of spg_solve on its problem.
+ * Captured into one CUDA graph from the second call with the same first
+ * problem, n and parameters, like spg_solve.  n in 1..SPG_MAX_GROUP.
+ * SPG_EINVAL when a problem's structure differs from probs[0]'s (or its
+ * weights need the FP64 path while probs[0]'s do not, see
+ * SPG_FP32_WEIGHT_SPAN); SPG_EUNSUPPORTED with warm_start or check_fp64. */
+#define SPG_MAX_GROUP 255
+int spg_solve_group(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prm,
+                    spg_result** out);
+
 /* Batching: solve n independent problems concurrently (instances of uneven
  * size, each with its own parameters prms[i]); every problem is solved
- * exactly as by spg_solve.  The solves run on up to 32 worker streams owned
- * by the context (each with its own workspace), enqueued from as many host
- * threads, so that the instances' chains of dependent kernels overlap on the
- * GPU.  The streams only overlap when the process has as many hardware work
+ * exactly as by spg_solve.  Items of one structure with equal parameters
+ * (see spg_solve_group) are solved in lockstep groups of up to
+ * prms[i].group_max (0: automatic); the groups, and the items that fit no
+ * group, run on up to 32 worker streams owned by the context (each with its
+ * own workspace), enqueued from as many host threads, so that their chains
+ * of dependent kernels overlap on the GPU.  The streams only overlap when the process has as many hardware work
  * queues: loading the library sets CUDA_DEVICE_MAX_CONNECTIONS=32 unless it
  * is already set, which takes effect if the process creates its CUDA
  * context afterwards (with CUDA's default of 8 queues, more than 8 solves

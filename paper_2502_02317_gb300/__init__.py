@@ -18,12 +18,12 @@ from ._binding import (SPG_ECUDA, SPG_EINEXACT, SPG_EINVAL, SPG_ENOMEM, SPG_ENUM
                        spg_check_bounded_wait, spg_inject_alloc_failure, spg_log_partition,
                        spg_peak_probe, spg_problem_ising, spg_problem_potts, spg_profile,
                        spg_profile_report,
-                       spg_problem_update_ising, spg_set_warm_start, spg_solve, spg_solve_batch,
+                       spg_problem_update_ising, spg_set_warm_start, spg_solve, spg_solve_batch, spg_solve_group,
                        spg_solve_lattice8, spg_sweep_trace, spg_tc_product, spg_truncate,
                        spg_truncate_static, spg_warm_features)
 
 __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
-           "spg_problem_potts", "spg_solve", "spg_solve_batch", "spg_debug_marginals", "spg_log_partition",
+           "spg_problem_potts", "spg_solve", "spg_solve_batch", "spg_solve_group", "spg_debug_marginals", "spg_log_partition",
            "spg_profile", "spg_profile_report", "spg_tc_product", "spg_truncate", "spg_lattice_site_map",
            "spg_truncate_static", "spg_warm_features", "spg_boundary_export", "Mlp", "spg_set_warm_start",
            "spg_sweep_trace", "SPG_WS_FEATURES", "spg_peak_probe", "spg_check_bounded_wait",

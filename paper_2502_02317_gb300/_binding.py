@@ -37,7 +37,8 @@ class spg_params(C.Structure):
                 ("beam", C.c_int32), ("precision", C.c_int32), ("cut_off_prob", C.c_double),
                 ("svd_iters", C.c_int32), ("warm_start", C.c_int32), ("seed", C.c_uint64),
                 ("merge", C.c_int32), ("fp64_rows", C.c_int32), ("check_fp64", C.c_int32),
-                ("droplet_hamming", C.c_int32), ("droplet_energy", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("droplet_hamming", C.c_int32), ("droplet_energy", C.c_double), ("group_max", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class spg_info(C.Structure):
@@ -45,7 +46,8 @@ class spg_info(C.Structure):
                 ("error_flags", C.c_int32), ("ms_boundary", C.c_double), ("ms_search", C.c_double),
                 ("candidates", C.c_double), ("boundary_lognorm", C.c_double),
                 ("kernel_launches", C.c_int64), ("jacobi_sweeps_max", C.c_int32), ("fp64_rows", C.c_int32),
-                ("precision_used", C.c_int32), ("droplet_overflow", C.c_int32), ("max_logmarg_err", C.c_double)]
+                ("precision_used", C.c_int32), ("droplet_overflow", C.c_int32), ("max_logmarg_err", C.c_double),
+                ("group_size", C.c_int32), ("reserved", C.c_int32)]
 
 
 def _load():
@@ -73,6 +75,7 @@ def _load():
         "spg_problem_shape": (C.c_int, [P, pI32, pI32, pI32]),
         "spg_solve": (C.c_int, [P, P, C.POINTER(spg_params), C.POINTER(P)]),
         "spg_solve_batch": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
+        "spg_solve_group": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(spg_params), C.POINTER(P)]),
         "spg_result_get": (C.c_int, [P, pI32, pI32, pU16, pI64, pD, pD, pD]),
         "spg_result_info": (C.c_int, [P, C.POINTER(spg_info)]),
         "spg_result_droplets": (C.c_int, [P, pI32, pI64, pU16]),
@@ -341,6 +344,15 @@ def spg_solve_batch(ctx: Context, probs, prms) -> list:
     pa = (spg_params * n)(*prms)
     out = (C.c_void_p * n)()
     ctx.check(lib.spg_solve_batch(ctx.h, n, ph, pa, out))
+    return [Result(ctx, C.c_void_p(out[i])) for i in range(n)]
+
+
+def spg_solve_group(ctx: Context, probs, prm: spg_params) -> list:
+    """Problems of one structure solved in lockstep (one launch sequence)."""
+    n = len(probs)
+    ph = (C.c_void_p * n)(*[p.h for p in probs])
+    out = (C.c_void_p * n)()
+    ctx.check(lib.spg_solve_group(ctx.h, n, ph, C.byref(prm), out))
     return [Result(ctx, C.c_void_p(out[i])) for i in range(n)]
 
 

@@ -45,7 +45,9 @@ __device__ __forceinline__ T dexp(double x) {
 // One block per site: w = exp(-beta u (E - min E)); bL, bU, bA from RL, RU,
 // RA alike, each over its valid entries (zero elsewhere).
 template <typename T>
-__global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u) {
+__global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
   const int s = blockIdx.x;
   const int d = tb.d[s];
   const int* dm = tb.dims + s * DIMW;
@@ -540,7 +542,9 @@ __device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* 
 // x_k = sum_{c <= k} R[c][k] q_c.
 template <typename T>
 __global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem,
-                                                      int use_chol) {
+                                                      int use_chol, size_t zs) {
+  X = zp(X, zs);
+  Rout = zp(Rout, zs);
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* Cs = red + 64 + 2 * SMAX;              // SMAX * QR_PB
@@ -569,7 +573,9 @@ __global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, i
 // entries than vectors leaves the dependent ones zero, with zero rows in
 // R_b, which the stacked QR carries through.
 template <typename T>
-__global__ void __launch_bounds__(512) k_tsqr_leaf(T* X, int nvec, int len, int bl, T* S, int use_smem) {
+__global__ void __launch_bounds__(512) k_tsqr_leaf(T* X, int nvec, int len, int bl, T* S, int use_smem, size_t zs) {
+  X = zp(X, zs);
+  S = zp(S, zs);
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* R = red + 64 + 2 * SMAX;               // nvec * nvec
@@ -596,7 +602,9 @@ __global__ void __launch_bounds__(512) k_tsqr_leaf(T* X, int nvec, int len, int 
 // outputs of a chunk depend only on that chunk's entries, so X is updated in
 // place).
 template <typename T>
-__global__ void k_tsqr_apply(T* X, int nvec, int len, int bl, const T* __restrict__ S) {
+__global__ void k_tsqr_apply(T* X, int nvec, int len, int bl, const T* __restrict__ S, size_t zs) {
+  X = zp(X, zs);
+  S = zp(S, zs);
   constexpr int CH = 64;
   extern __shared__ unsigned char smem_raw[];
   T* Sb = reinterpret_cast<T*>(smem_raw);  // [k][c] nvec * nvec
@@ -631,13 +639,24 @@ __global__ void k_tsqr_apply(T* X, int nvec, int len, int bl, const T* __restric
 // QR of site j, then site j+1 <- R site j+1.  The last site is normalised.
 // The chiR columns of a site are staged as contiguous vectors in `work`
 // (shared memory when they fit, else the global scratch) for the CGS2.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork, int use_smem) {
+// With Panels (FP32, staged in shared memory, 512 threads for the panel
+// products' registers) sites of >= 32 columns of >= 256 entries go through
+// the block Gram-Schmidt with guarded Cholesky-QR panels of k_cgs2_rows;
+// the others through per-vector CGS2.
+template <typename T, bool Panels>
+__global__ void __launch_bounds__(Panels ? 512 : 1024) k_left_canonical(DevMPS<T> mps, int r, int cols, T* gwork,
+                                                                        int use_smem, size_t zs) {
+  mps = zp(mps, zs);
+  gwork = zp(gwork, zs);
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64 + 2 SMAX
   T* R = red + 64 + 2 * SMAX;               // MAXCHI * MAXCHI
-  T* W = use_smem ? R + MAXCHI * MAXCHI : gwork;
+  T* Cs = R + MAXCHI * MAXCHI;              // Panels: SMAX * QR_PB
+  T* Racc = Cs + (Panels ? SMAX * QR_PB : 0);
+  T* cs = Racc + (Panels ? SMAX * QR_PB : 0);  // chol_scratch_elems
+  T* W = use_smem ? cs + (Panels ? chol_scratch_elems<T>() : 0) : gwork;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t wmax = (size_t)mps.site_stride;  // staged site, then the panel copy
   for (int j = 0; j < cols - 1; ++j) {
     const int* dA = mps.dimA + (r * cols + j) * 3;
     const int p = dA[0], chiL = dA[1], chiR = dA[2];
@@ -645,7 +664,10 @@ __global__ void __launch_bounds__(1024) k_left_canonical(DevMPS<T> mps, int r, i
     T* A = mps.A + (size_t)(r * cols + j) * mps.site_stride;
     for (int e = tid; e < len * chiR; e += nt) W[(size_t)(e % chiR) * len + e / chiR] = A[e];
     __syncthreads();
-    cgs2_core(W, chiR, len, len, R, red);
+    if (Panels && chiR >= 32 && len >= 256)
+      bcgs2_core(W, chiR, len, len, R, red, Cs, Racc, W + wmax, cs);
+    else
+      cgs2_core(W, chiR, len, len, R, red);
     for (int e = tid; e < len * chiR; e += nt) A[e] = W[(size_t)(e % chiR) * len + e / chiR];
     __syncthreads();
     const int* dB = mps.dimA + (r * cols + j + 1) * 3;
@@ -678,7 +700,10 @@ __global__ void __launch_bounds__(1024) k_left_canonical(DevMPS<T> mps, int r, i
 // T1[a][s][rr][k] = sum_a' B[s][a][a'] C[rr][a'][k]
 template <typename T>
 __global__ void k_zip_T1(const T* __restrict__ B, int chiL, int p, int chiR, const T* __restrict__ C,
-                         int DR, int K, T* __restrict__ T1) {
+                         int DR, int K, T* __restrict__ T1, size_t zs) {
+  B = zp(B, zs);
+  C = zp(C, zs);
+  T1 = zp(T1, zs);
   const size_t total = (size_t)chiL * p * DR * K;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -703,7 +728,11 @@ __global__ void k_zip_T1(const T* __restrict__ B, int chiL, int p, int chiR, con
 // the site's bL [DL][NL].
 template <typename T>
 __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __restrict__ T1, int chiL,
-                        int p, int DR, int K, int DL, int DU, int kchunk, T* __restrict__ M) {
+                        int p, int DR, int K, int DL, int DU, int kchunk, T* __restrict__ M, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  T1 = zp(T1, zs);
+  M = zp(M, zs);
   extern __shared__ unsigned char smem_raw[];
   T* sT = reinterpret_cast<T*>(smem_raw);  // [p][DR]
   T* sbL = sT + (size_t)p * DR;            // [DL][NL]
@@ -768,7 +797,10 @@ __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __res
 // threads, 2x2 outputs per thread.
 template <typename T, bool TA, bool TB>
 __global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, const T* __restrict__ B,
-                       int ldb, T* __restrict__ C, int ldc) {
+                       int ldb, T* __restrict__ C, int ldc, size_t zs) {
+  A = zp(A, zs);
+  B = zp(B, zs);
+  C = zp(C, zs);
   constexpr int BM = 32, BN = 32, BK = 32;
   __shared__ T sA[BK][BM + 1];
   __shared__ T sB[BK][BN + 1];
@@ -835,9 +867,16 @@ __global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, co
 // written as RV (= U Sigma) and V, row-major s x s, plus sigma[s].
 // s1_dev = sigma[0]; flag_dev |= degenerate cut at `keep`.
 template <typename T>
-__global__ void k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout, T* __restrict__ Vout,
+__global__ void __launch_bounds__(1024) k_jacobi(const T* __restrict__ Rin, int s, T* __restrict__ RVout, T* __restrict__ Vout,
                          T* __restrict__ sig_out, int keep, double* s1_dev, int* flag_dev,
-                         T* __restrict__ gbuf, int use_smem) {
+                         T* __restrict__ gbuf, int use_smem, size_t zs) {
+  Rin = zp(Rin, zs);
+  RVout = zp(RVout, zs);
+  Vout = zp(Vout, zs);
+  sig_out = zp(sig_out, zs);
+  s1_dev = zp(s1_dev, zs);
+  flag_dev = zp(flag_dev, zs);
+  gbuf = zp(gbuf, zs);
   extern __shared__ unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);  // 64
   T* sig = red + 64;                        // SMAX
@@ -985,7 +1024,8 @@ __device__ __forceinline__ double hash_unit(uint64_t seed, uint64_t i) {
 
 // Zt [s x n]: identity rows (direct case, s == n) or the pseudo-random block.
 template <typename T>
-__global__ void k_fill_start(T* Zt, int n, int s, uint64_t seed, int identity) {
+__global__ void k_fill_start(T* Zt, int n, int s, uint64_t seed, int identity, size_t zs) {
+  Zt = zp(Zt, zs);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * s; e += gridDim.x * blockDim.x) {
     const int c = e / n, i = e % n;
     Zt[e] = identity ? (i == c ? T(1) : T(0)) : (T)hash_unit(seed, (uint64_t)e);
@@ -995,13 +1035,16 @@ __global__ void k_fill_start(T* Zt, int n, int s, uint64_t seed, int identity) {
 // dst[e] = (To) src[e]: a contiguous block changes precision (the FP64
 // truncation of the final boundary rows in the mixed mode).
 template <typename From, typename To>
-__global__ void k_convert(const From* __restrict__ src, To* __restrict__ dst, size_t count) {
+__global__ void k_convert(const From* __restrict__ src, To* __restrict__ dst, size_t count, size_t zs) {
+  src = zp(src, zs);
+  dst = zp(dst, zs);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = (To)src[e];
 }
 
 template <typename T>
-__global__ void k_set_strided(T* base, size_t stride, int count, T v) {
+__global__ void k_set_strided(T* base, size_t stride, int count, T v, size_t zs) {
+  base = zp(base, zs);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) base[e * stride] = v;
 }
 
@@ -1009,7 +1052,13 @@ __global__ void k_set_strided(T* base, size_t stride, int count, T v) {
 template <typename T>
 __global__ void k_zip_write(const T* __restrict__ V, const T* __restrict__ US, int DL, int chiL, int DU,
                             int K, int keep, T* __restrict__ site, T* __restrict__ carry, const double* s1,
-                            double* lognorm_r) {
+                            double* lognorm_r, size_t zs) {
+  V = zp(V, zs);
+  US = zp(US, zs);
+  site = zp(site, zs);
+  carry = zp(carry, zs);
+  s1 = zp(s1, zs);
+  lognorm_r = zp(lognorm_r, zs);
   const double sv = *s1;
   const T inv = sv > 0 ? (T)(1.0 / sv) : T(0);
   const int nsite = DU * keep * K, ncar = DL * chiL * keep;
@@ -1027,7 +1076,10 @@ __global__ void k_zip_write(const T* __restrict__ V, const T* __restrict__ US, i
 }
 
 template <typename T>
-__global__ void k_zip_site0(const T* __restrict__ M, int n, T* __restrict__ site, double* lognorm_r) {
+__global__ void __launch_bounds__(1024) k_zip_site0(const T* __restrict__ M, int n, T* __restrict__ site, double* lognorm_r, size_t zs) {
+  M = zp(M, zs);
+  site = zp(site, zs);
+  lognorm_r = zp(lognorm_r, zs);
   __shared__ T red[64];
   T part = T(0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) part += M[i] * M[i];
@@ -1067,7 +1119,8 @@ __global__ void k_mps_value(DevMPS<T> mps, int r, int cols, double* out) {
 template <typename T>
 cudaError_t launch_weights(const DevTables& tb, DevWeights<T> wt, double beta_u, cudaStream_t st) {
   count_launches("k_weights", st);
-  k_weights<T><<<tb.n, 256, 0, st>>>(tb, wt, beta_u);
+  ZOK(tb, wt);
+  k_weights<T><<<dim3(tb.n, 1, zn()), 256, 0, st>>>(tb, wt, beta_u, zs());
   return cudaGetLastError();
 }
 
@@ -1078,10 +1131,22 @@ cudaError_t launch_left_canonical(DevMPS<T> mps, int r, int cols, const int*, T*
   const size_t base = sizeof(T) * (64 + 2 * SMAX + MAXCHI * MAXCHI);
   const size_t full = base + sizeof(T) * MAXP * chi * chi;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
+  // FP32 sites staged with room for the panels' scratch and one panel copy
+  // (QR_PB vectors of up to MAXP * chi entries)
+  const size_t with_panels = full + sizeof(T) * (2 * SMAX * QR_PB + chol_scratch_elems<T>() + QR_PB * MAXP * chi);
+  const bool panels = sizeof(T) == 4 && use_smem && with_panels <= 200 * 1024;
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
-  std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_left_canonical<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
+  std::call_once(attr_once, [&] {
+    cudaFuncSetAttribute(k_left_canonical<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+    cudaFuncSetAttribute(k_left_canonical<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
+  });
+  ZOK(mps, scratch);
   count_launches("k_left_canonical", st);
-  k_left_canonical<T><<<1, 1024, use_smem ? full : base, st>>>(mps, r, cols, scratch, use_smem);
+  if (panels)
+    k_left_canonical<T, true><<<dim3(1, 1, zn()), 512, with_panels, st>>>(mps, r, cols, scratch, use_smem, zs());
+  else
+    k_left_canonical<T, false><<<dim3(1, 1, zn()), 1024, use_smem ? full : base, st>>>(mps, r, cols, scratch,
+                                                                                     use_smem, zs());
   return cudaGetLastError();
 }
 
@@ -1091,10 +1156,11 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
                               cudaStream_t st) {
   const size_t total = (size_t)chiL * p * DR * K;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  ZOK(tb, wt, B, C, T1, M);
   count_launches("k_zip_T1", st, 2.0 * chiL * p * DR * K * chiR);
-  k_zip_T1<T><<<blocks, 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1);
+  k_zip_T1<T><<<dim3(blocks, 1, zn()), 256, 0, st>>>(B, chiL, p, chiR, C, DR, K, T1, zs());
   const int kchunk = K >= 8 ? 4 : 1;
-  dim3 grid(chiL, (K + kchunk - 1) / kchunk);
+  dim3 grid(chiL, (K + kchunk - 1) / kchunk, zn());
   const size_t smem = sizeof(T) * ((size_t)p * DR + (size_t)DL * MAXP);
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] {
@@ -1102,7 +1168,7 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
                          (int)(sizeof(T) * 2 * (size_t)MAXP * MAXBOND));
   });
   count_launches("k_zip_M", st);
-  k_zip_M<T><<<grid, 256, smem, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M);
+  k_zip_M<T><<<grid, 256, smem, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M, zs());
   return cudaGetLastError();
 }
 
@@ -1115,16 +1181,18 @@ cudaError_t gemm(bool transA, int m, int n, int k, const T* A, int lda, const T*
 template <typename T>
 cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
                   int ldc, cudaStream_t st) {
-  dim3 grid((n + 31) / 32, (m + 31) / 32);
+  ZOK(A, B, C);
+  dim3 grid((n + 31) / 32, (m + 31) / 32, zn());
   count_launches("k_gemm", st, 2.0 * m * n * k);
+  const size_t z = zs();
   if (transA && transB)
-    k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else if (transA)
-    k_gemm<T, true, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    k_gemm<T, true, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else if (transB)
-    k_gemm<T, false, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    k_gemm<T, false, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else
-    k_gemm<T, false, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    k_gemm<T, false, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   return cudaGetLastError();
 }
 
@@ -1132,8 +1200,9 @@ template <typename From, typename To>
 cudaError_t launch_convert(const From* src, To* dst, size_t count, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   const size_t blocks = std::min<size_t>((count + 255) / 256, 152 * 8);
+  ZOK(src, dst);
   count_launches("k_convert", st);
-  k_convert<From, To><<<(unsigned)blocks, 256, 0, st>>>(src, dst, count);
+  k_convert<From, To><<<dim3((unsigned)blocks, 1, zn()), 256, 0, st>>>(src, dst, count, zs());
   return cudaGetLastError();
 }
 template cudaError_t launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
@@ -1141,8 +1210,9 @@ template cudaError_t launch_convert<double, float>(const double*, float*, size_t
 
 template <typename T>
 cudaError_t launch_set_strided(T* base, size_t stride, int count, T v, cudaStream_t st) {
+  ZOK(base);
   count_launches("k_set_strided", st);
-  k_set_strided<T><<<(count + 255) / 256, 256, 0, st>>>(base, stride, count, v);
+  k_set_strided<T><<<dim3((count + 255) / 256, 1, zn()), 256, 0, st>>>(base, stride, count, v, zs());
   return cudaGetLastError();
 }
 
@@ -1205,15 +1275,16 @@ static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
     cudaFuncSetAttribute(k_tsqr_leaf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
     cudaFuncSetAttribute(k_tsqr_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096);
   });
+  if (!zok(X, S, Rout)) return;
   count_launches("k_tsqr_leaf", st, 4.0 * len * nvec * nvec);
-  k_tsqr_leaf<T><<<nb, 512, leaf_smem, st>>>(X, nvec, len, bl, S, use_smem);
+  k_tsqr_leaf<T><<<dim3(nb, 1, zn()), 512, leaf_smem, st>>>(X, nvec, len, bl, S, use_smem, zs());
   const int slen = nb * nvec;
   if (slen >= TSQR_MIN_LEN && slen < len)
     tall_qr<T>(S, nvec, slen, Rout, S + (size_t)nvec * slen, st);
   else
     cgs2_rows<T>(S, nvec, slen, Rout, st);
   count_launches("k_tsqr_apply", st, 2.0 * len * nvec * nvec);
-  k_tsqr_apply<T><<<nb, 512, apply_smem, st>>>(X, nvec, len, bl, S);
+  k_tsqr_apply<T><<<dim3(nb, 1, zn()), 512, apply_smem, st>>>(X, nvec, len, bl, S, zs());
 }
 
 template <typename T>
@@ -1233,9 +1304,10 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   // one thread per element up to 512 (the register budget of the panel
   // products), at least 4 warps
   const int threads = std::max(128, std::min(512, (len + 31) / 32 * 32));
+  if (!zok(X, Rout)) return;
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
-  k_cgs2_rows<T><<<1, threads, use_chol ? with_copy : (use_smem ? full : base), st>>>(X, nvec, len, len, Rout,
-                                                                                       use_smem, use_chol);
+  k_cgs2_rows<T><<<dim3(1, 1, zn()), threads, use_chol ? with_copy : (use_smem ? full : base), st>>>(
+      X, nvec, len, len, Rout, use_smem, use_chol, zs());
 }
 
 template <typename T>
@@ -1285,8 +1357,9 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
       if (tc) return tc->run(true, Yt, s, Zt);
     return gemm2<T>(false, false, s, n, m, Yt, m, M, n, Zt, n, st);
   };
+  ZOK(M, V, US, work, s1_dev, flag_dev, tcw);
   count_launches("k_fill_start", st);
-  k_fill_start<T><<<(n * s + 255) / 256, 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0);
+  k_fill_start<T><<<dim3((n * s + 255) / 256, 1, zn()), 256, 0, st>>>(Zt, n, s, seed, direct ? 1 : 0, zs());
   if (!direct) {
     // the pseudo-random start block is well conditioned, so the power steps
     // need no orthonormalisation of it; the Rayleigh-Ritz step below does
@@ -1316,7 +1389,7 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
   count_launches("k_jacobi", st);
-  k_jacobi<T><<<1, 1024, jsm, st>>>(R, s, RV, VJ, sig, keep, s1_dev, flag_dev, jbuf, use_smem);
+  k_jacobi<T><<<dim3(1, 1, zn()), 1024, jsm, st>>>(R, s, RV, VJ, sig, keep, s1_dev, flag_dev, jbuf, use_smem, zs());
   // V = Z VJ[:, :keep] = Zt^T VJ,  US = Q RV[:, :keep] = Yt^T RV
   gemm2<T>(true, false, n, keep, s, Zt, n, VJ, s, V, keep, st);
   gemm2<T>(true, false, m, keep, s, Yt, m, RV, s, US, keep, st);
@@ -1327,21 +1400,24 @@ template <typename T>
 cudaError_t launch_zip_write(const T* V, const T* US, int DL, int chiL, int DU, int K, int keep, T* site_out,
                              T* carry_out, const double* s1_dev, double* lognorm_r, cudaStream_t st) {
   const int tot = DU * keep * K + DL * chiL * keep;
+  ZOK(V, US, site_out, carry_out, s1_dev, lognorm_r);
   count_launches("k_zip_write", st);
-  k_zip_write<T><<<std::min((tot + 255) / 256, 1024), 256, 0, st>>>(V, US, DL, chiL, DU, K, keep, site_out,
-                                                                   carry_out, s1_dev, lognorm_r);
+  k_zip_write<T><<<dim3(std::min((tot + 255) / 256, 1024), 1, zn()), 256, 0, st>>>(
+      V, US, DL, chiL, DU, K, keep, site_out, carry_out, s1_dev, lognorm_r, zs());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_zip_site0(const T* M, int DU, int K, T* site_out, double* lognorm_r, cudaStream_t st) {
+  ZOK(M, site_out, lognorm_r);
   count_launches("k_zip_site0", st);
-  k_zip_site0<T><<<1, 1024, 0, st>>>(M, DU * K, site_out, lognorm_r);
+  k_zip_site0<T><<<dim3(1, 1, zn()), 1024, 0, st>>>(M, DU * K, site_out, lognorm_r, zs());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_mps_value(DevMPS<T> mps, int r, int cols, double* out, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;  // not part of a grouped solve
   count_launches("k_mps_value", st);
   k_mps_value<T><<<1, 64, 0, st>>>(mps, r, cols, out);
   return cudaGetLastError();

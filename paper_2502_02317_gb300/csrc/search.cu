@@ -76,7 +76,12 @@ __device__ __forceinline__ int dim_of(const DevTables& tb, int s, int k) { retur
 // so are the G current environments when the bond is small (use_rn).
 template <typename T>
 __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int row, DevSearch ds,
-                             DevBeamT<T> bt, int cur, int G, int use_smem, int use_rn, int use_t) {
+                             DevBeamT<T> bt, int cur, int G, int use_smem, int use_rn, int use_t, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  mps = zp(mps, zs);
+  ds = zp(ds, zs);
+  bt = zp(bt, zs);
   const int nb = ds.n_beam[cur];
   const int b0 = blockIdx.x * G;
   if (b0 >= nb) return;
@@ -104,8 +109,8 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
       Rb[(size_t)cols * renv + e] = v;
       if (use_rn) Rn[(size_t)g * renv + e] = v;
     }
-    if (tid == 0) ds.rid[cur][b] = b;
-    for (int a = tid; a < chi; a += nt) bt.lenv[cur][(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
+    if (tid == 0) pick(ds.rid, cur)[b] = b;
+    for (int a = tid; a < chi; a += nt) pick(bt.lenv, cur)[(size_t)b * chi + a] = a == 0 ? T(1) : T(0);
   }
   __syncthreads();
   for (int j = cols - 1; j >= 1; --j) {
@@ -141,7 +146,7 @@ __global__ void k_right_envs(DevTables tb, DevWeights<T> wt, DevMPS<T> mps, int 
     __syncthreads();
     for (int g = 0; g < gn; ++g) {
       const int b = b0 + g;
-      const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+      const uint16_t* stb = pick(ds.states, cur) + (size_t)b * ds.N;
       const int u = row > 0 ? tb.PD[(size_t)(s - cols) * tb.dmax + stb[s - cols]] : 0;
       const int gu = row > 0 ? tb.gD[(size_t)(s - cols) * MAXP + u] : 0;
       const T* Rg = use_rn ? Rn + (size_t)g * renv : bt.R + ((size_t)b * (cols + 1) + j + 1) * renv;
@@ -303,7 +308,12 @@ __device__ __forceinline__ double log_pos(double q) {
 // x and cancels.
 template <typename T>
 __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, int site, DevSearch ds,
-                            DevBeamT<T> bt, int cur) {
+                            DevBeamT<T> bt, int cur, size_t zs) {
+  tb = zp(tb, zs);
+  wd = zp(wd, zs);
+  mps = zp(mps, zs);
+  ds = zp(ds, zs);
+  bt = zp(bt, zs);
   const int b = blockIdx.x;
   if (b >= ds.n_beam[cur]) return;
   __shared__ T sl[MAXCHI];
@@ -317,7 +327,7 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   const int p = dA[0], chiL = dA[1], chiR = dA[2];
   const T* A = mps.A + (size_t)((i + 1) * cols + j) * mps.site_stride;
   const int NR = dim_of(tb, site, D_NR), Gin = dim_of(tb, site, D_GIN), Gout = dim_of(tb, site, D_GOUT);
-  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  const uint16_t* stb = pick(ds.states, cur) + (size_t)b * ds.N;
   const size_t dm = tb.dmax;
   const int a_l = j > 0 ? tb.PR[(size_t)(site - 1) * dm + stb[site - 1]] : 0;
   const int g_l = (j > 0 && i > 0) ? tb.PG[(size_t)(site - cols - 1) * dm + stb[site - cols - 1]] : 0;
@@ -326,7 +336,7 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   const int gu = i > 0 ? tb.gD[(size_t)(site - cols) * MAXP + u] : 0;
   const bool adr = i > 0 && j + 1 < cols;
   const int ur = adr ? tb.PD[(size_t)(site - cols + 1) * dm + stb[site - cols + 1]] : 0;
-  for (int a = tid; a < chiL; a += nt) sl[a] = bt.lenv[cur][(size_t)b * chi + a];
+  for (int a = tid; a < chiL; a += nt) sl[a] = pick(bt.lenv, cur)[(size_t)b * chi + a];
   __syncthreads();
   for (int e = tid; e < p * chiR; e += nt) {
     const int s = e / chiR, ap = e % chiR;
@@ -335,7 +345,7 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
     sv[s * MAXCHI + ap] = acc;
   }
   __syncthreads();
-  const int rb = ds.rid[cur][b];
+  const int rb = pick(ds.rid, cur)[b];
   const T* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * rs;
   for (int e = tid; e < p * NR; e += nt) {
     const int s = e / NR, rr = e % NR;
@@ -360,7 +370,7 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
   }
   const double tot = block_sum(part, red);
   const double lt = log(tot);
-  const int64_t E0 = ds.E[cur][b];
+  const int64_t E0 = pick(ds.E, cur)[b];
   const int64_t* RLl = tb.RL + (size_t)site * tb.lstride + (size_t)l * MAXP;
   const int64_t* RUu = tb.RU + (size_t)site * 256 + u * 16;
   for (int x = tid; x < d; x += nt) {
@@ -396,7 +406,9 @@ __device__ __forceinline__ unsigned key_hash(const unsigned long long* k) {
   return (unsigned)(h ^ (h >> 32));
 }
 
-__global__ void k_class_insert(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+__global__ void k_class_insert(DevTables tb, int site, DevSearch ds, int cur, int merge, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int nb = ds.n_beam[cur];
   if (b >= nb) return;
@@ -407,7 +419,7 @@ __global__ void k_class_insert(DevTables tb, int site, DevSearch ds, int cur, in
   unsigned long long kb[KEYW] = {};
   const int* ks = tb.keys + site * (MAXKEY + 1);
   const int n = ks[0], bits = *tb.kshift;
-  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  const uint16_t* stb = pick(ds.states, cur) + (size_t)b * ds.N;
   for (int q = 0; q < n; ++q) {
     const int pos = q * bits;
     const int w = pos >> 6, o = pos & 63;
@@ -448,7 +460,9 @@ __global__ void k_class_insert(DevTables tb, int site, DevSearch ds, int cur, in
 // reset to all ones and win / wkey to WIN_NONE (byte memsets) before.
 constexpr int WIN_NONE = 0x7f7f7f7f;
 
-__global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+__global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur, int merge, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
   const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
@@ -464,7 +478,9 @@ __global__ void k_win_min(DevTables tb, int site, DevSearch ds, int cur, int mer
   }
 }
 
-__global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+__global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur, int merge, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
   const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
@@ -481,7 +497,9 @@ __global__ void k_win_arg(DevTables tb, int site, DevSearch ds, int cur, int mer
   }
 }
 
-__global__ void k_win_fix(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+__global__ void k_win_fix(DevTables tb, int site, DevSearch ds, int cur, int merge, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   const int nb = ds.n_beam[cur];
   const int d = tb.d[site];
   const bool xin = !merge || tb.dims[site * DIMW + D_XIN] != 0;  // without merging every child is its own class
@@ -522,7 +540,7 @@ __device__ __forceinline__ CandKey cand_key(const DevSearch& ds, int cur, size_t
   if (b >= nb || x >= d) return r;
   const int w = ds.win[c];
   if (w < 0) return r;
-  const double lp = ds.logp[cur][w] + ds.logc[(size_t)w * ds.dmax + x];
+  const double lp = pick(ds.logp, cur)[w] + ds.logc[(size_t)w * ds.dmax + x];
   if (log_cut > -INFINITY) {
     const double mx = unord_f64(maxkey);
     if (!(lp >= mx + log_cut)) return r;
@@ -535,7 +553,9 @@ __device__ __forceinline__ CandKey cand_key(const DevSearch& ds, int cur, size_t
   return r;
 }
 
-__global__ void k_logp_max(DevTables tb, int site, DevSearch ds, int cur) {
+__global__ void __launch_bounds__(1024) k_logp_max(DevTables tb, int site, DevSearch ds, int cur, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   const int nb = ds.n_beam[cur], d = tb.d[site];
   const size_t tot = (size_t)ds.cap * ds.dmax;
   unsigned long long best = 0;
@@ -578,8 +598,12 @@ __device__ __forceinline__ bool prefix_match(const CandKey& k, const unsigned lo
 // One radix pass: histogram of the 16-bit digit `pass` of the keys that
 // match the prefix chosen so far, over all candidates (list == nullptr) or
 // over the candidate ids list[0 .. *list_n).
-__global__ void k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int pass, double log_cut,
-                              const int* list, const int* list_n) {
+__global__ void __launch_bounds__(1024) k_select_pass(DevTables tb, int site, DevSearch ds, int cur, int pass, double log_cut,
+                              const int* list, const int* list_n, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
+  list = zp(list, zs);
+  list_n = zp(list_n, zs);
   __shared__ bool s_last;
   const unsigned long long status = ds.sel_state[4];
   if (status != 0) return;
@@ -717,8 +741,12 @@ __device__ __forceinline__ bool key_le(const CandKey& k, const unsigned long lon
 // decides (key <= threshold: selected).  Selected ids go to sel_list,
 // pending ones to pend; the extremes of the selected and rejected log p feed
 // the near-tie test.
-__global__ void k_select_classify(DevTables tb, int site, DevSearch ds, int cur, double log_cut, const int* list,
-                                  const int* list_n, int split) {
+__global__ void __launch_bounds__(1024) k_select_classify(DevTables tb, int site, DevSearch ds, int cur, double log_cut, const int* list,
+                                  const int* list_n, int split, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
+  list = zp(list, zs);
+  list_n = zp(list_n, zs);
   if (!split && ds.sel_state[4] == 2) return;  // resolved by k_select_refine
   const int nb = ds.n_beam[cur], d = tb.d[site];
   const size_t tot = list ? (size_t)*list_n : (size_t)ds.cap * ds.dmax;
@@ -787,7 +815,9 @@ __global__ void k_select_classify(DevTables tb, int site, DevSearch ds, int cur,
 // (histograms in shared memory, keys recomputed from the candidate arrays),
 // then the pending ids up to the final threshold appended to sel_list.  The
 // selection is marked resolved (state 2).
-__global__ void k_select_refine(DevTables tb, int site, DevSearch ds, int cur, double log_cut) {
+__global__ void __launch_bounds__(1024) k_select_refine(DevTables tb, int site, DevSearch ds, int cur, double log_cut, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   __shared__ unsigned hist[256];
   __shared__ unsigned long long s_pre[3];
   __shared__ unsigned long long s_need;
@@ -921,7 +951,9 @@ __global__ void k_select_refine(DevTables tb, int site, DevSearch ds, int cur, d
 }
 
 // One block: sort the selected ids by lex key (winner, x); record near ties.
-__global__ void k_select_sort(DevTables tb, int site, DevSearch ds, int cur, int nxt_buf) {
+__global__ void __launch_bounds__(1024) k_select_sort(DevTables tb, int site, DevSearch ds, int cur, int nxt_buf, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   extern __shared__ unsigned long long sk[];  // [pow2 >= cap]
   const int n = min(*ds.sel_count, ds.cap);
   int P = 1;
@@ -976,7 +1008,11 @@ __global__ void k_select_sort(DevTables tb, int site, DevSearch ds, int cur, int
 // ---------------------------------------------------------------- update
 // New beam element i from selected candidate c = rep*dmax + x with parent w.
 template <typename T>
-__global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, DevBeamT<T> bt, int cur) {
+__global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, DevBeamT<T> bt, int cur, size_t zs) {
+  tb = zp(tb, zs);
+  mps = zp(mps, zs);
+  ds = zp(ds, zs);
+  bt = zp(bt, zs);
   const int i = blockIdx.x;
   const int nxt = cur ^ 1;
   if (i >= ds.n_beam[nxt]) return;
@@ -986,11 +1022,11 @@ __global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, De
   const int w = ds.win[c];
   const int N = ds.N;
   for (int q = threadIdx.x; q < N; q += blockDim.x)
-    ds.states[nxt][(size_t)i * N + q] = q == site ? (uint16_t)x : ds.states[cur][(size_t)w * N + q];
+    pick(ds.states, nxt)[(size_t)i * N + q] = q == site ? (uint16_t)x : pick(ds.states, cur)[(size_t)w * N + q];
   if (threadIdx.x == 0) {
-    ds.E[nxt][i] = ds.candE[(size_t)w * ds.dmax + x];
-    ds.logp[nxt][i] = ds.logp[cur][w] + ds.logc[(size_t)w * ds.dmax + x];
-    ds.rid[nxt][i] = ds.rid[cur][w];
+    pick(ds.E, nxt)[i] = ds.candE[(size_t)w * ds.dmax + x];
+    pick(ds.logp, nxt)[i] = pick(ds.logp, cur)[w] + ds.logc[(size_t)w * ds.dmax + x];
+    pick(ds.rid, nxt)[i] = pick(ds.rid, cur)[w];
   }
   const int cols = tb.cols, chi = bt.chi;
   const int r = site / cols, j = site % cols;
@@ -998,7 +1034,7 @@ __global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, De
   const int chiL = dA[1], chiR = dA[2];
   const T* A = mps.A + (size_t)((r + 1) * cols + j) * mps.site_stride;
   const int pd = tb.PD[(size_t)site * tb.dmax + x];
-  const T* lw = bt.lenv[cur] + (size_t)w * chi;
+  const T* lw = pick(bt.lenv, cur) + (size_t)w * chi;
   T mx = T(0);
   T v = T(0);
   const int ap = threadIdx.x;
@@ -1008,7 +1044,7 @@ __global__ void k_update(DevTables tb, DevMPS<T> mps, int site, DevSearch ds, De
   }
   mx = block_max(mx, red);
   const T inv = mx > T(0) ? T(1) / mx : T(0);
-  if (ap < chi) bt.lenv[nxt][(size_t)i * chi + ap] = ap < chiR ? v * inv : T(0);
+  if (ap < chi) pick(bt.lenv, nxt)[(size_t)i * chi + ap] = ap < chiR ? v * inv : T(0);
 }
 
 // lenv of teacher-forced prefixes: prod_{k<j} B_{i+1}[k][:, PD x_k, :], scaled.
@@ -1019,7 +1055,7 @@ __global__ void k_lenv_prefix(DevTables tb, DevMPS<T> mps, int site, DevSearch d
   __shared__ T v[MAXCHI], nv[MAXCHI], red[32];
   const int cols = tb.cols, chi = bt.chi;
   const int r = site / cols, j = site % cols;
-  const uint16_t* stb = ds.states[cur] + (size_t)b * ds.N;
+  const uint16_t* stb = pick(ds.states, cur) + (size_t)b * ds.N;
   if (threadIdx.x < MAXCHI) v[threadIdx.x] = threadIdx.x == 0 ? T(1) : T(0);
   __syncthreads();
   for (int k = 0; k < j; ++k) {
@@ -1038,24 +1074,25 @@ __global__ void k_lenv_prefix(DevTables tb, DevMPS<T> mps, int site, DevSearch d
     if (threadIdx.x < MAXCHI) v[threadIdx.x] = nv[threadIdx.x];
     __syncthreads();
   }
-  if (threadIdx.x < chi) bt.lenv[cur][(size_t)b * chi + threadIdx.x] = v[threadIdx.x];
+  if (threadIdx.x < chi) pick(bt.lenv, cur)[(size_t)b * chi + threadIdx.x] = v[threadIdx.x];
 }
 
-__global__ void k_reset_beam(DevSearch ds, int cur) {
+__global__ void k_reset_beam(DevSearch ds, int cur, size_t zs) {
+  ds = zp(ds, zs);
   for (int e = threadIdx.x; e < 65536; e += blockDim.x) ds.hist[e] = 0;
   if (threadIdx.x == 0) {
     select_state_reset(ds);
-    if (ds.dn[cur]) ds.dn[cur][0] = 0;
+    if (pick(ds.dn, cur)) pick(ds.dn, cur)[0] = 0;
     if (ds.dflow) *ds.dflow = 0;
     ds.n_beam[cur] = 1;
-    ds.E[cur][0] = 0;
-    ds.logp[cur][0] = 0.0;
-    ds.rid[cur][0] = 0;
+    pick(ds.E, cur)[0] = 0;
+    pick(ds.logp, cur)[0] = 0.0;
+    pick(ds.rid, cur)[0] = 0;
     *ds.near_ties = 0;
     *ds.err = 0;
     *ds.candidates = 0.0;
   }
-  for (int q = threadIdx.x; q < ds.N; q += blockDim.x) ds.states[cur][q] = 0;
+  for (int q = threadIdx.x; q < ds.N; q += blockDim.x) pick(ds.states, cur)[q] = 0;
 }
 
 // ---------------------------------------------------------------- droplets
@@ -1065,10 +1102,12 @@ __global__ void k_reset_beam(DevSearch ds, int cur) {
 // rep[b'] == b, their candidates (b', x') with x' == x when the site's state
 // is part of the key, any x' otherwise.
 __device__ __forceinline__ const uint16_t* drop_row(const DevSearch& ds, int cur, int b, int k) {
-  return k < 0 ? ds.states[cur] + (size_t)b * ds.N : ds.dst[cur] + ((size_t)b * MAXDROP + k) * ds.N;
+  return k < 0 ? pick(ds.states, cur) + (size_t)b * ds.N : pick(ds.dst, cur) + ((size_t)b * MAXDROP + k) * ds.N;
 }
 
-__global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int merge) {
+__global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int merge, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
   __shared__ long long cE[MAXDCAND];
   __shared__ int cb[MAXDCAND];
   __shared__ short cx[MAXDCAND], ck[MAXDCAND];
@@ -1086,13 +1125,13 @@ __global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int me
   const int64_t Ew = ds.candE[(size_t)w * dmax + x];
   const int tid = threadIdx.x, nt = blockDim.x;
   // inherited: the winner parent's droplets, extended by x at this site
-  const int nin = ds.dn[cur][w];
-  uint16_t* out = ds.dst[nxt] + (size_t)i * MAXDROP * N;
+  const int nin = pick(ds.dn, cur)[w];
+  uint16_t* out = pick(ds.dst, nxt) + (size_t)i * MAXDROP * N;
   for (int e = tid; e < nin * N; e += nt) {
     const int k = e / N, q = e % N;
-    out[e] = q == site ? (uint16_t)x : ds.dst[cur][((size_t)w * MAXDROP + k) * N + q];
+    out[e] = q == site ? (uint16_t)x : pick(ds.dst, cur)[((size_t)w * MAXDROP + k) * N + q];
   }
-  for (int k = tid; k < nin; k += nt) ds.dE[nxt][(size_t)i * MAXDROP + k] = ds.dE[cur][(size_t)w * MAXDROP + k];
+  for (int k = tid; k < nin; k += nt) pick(ds.dE, nxt)[(size_t)i * MAXDROP + k] = pick(ds.dE, cur)[(size_t)w * MAXDROP + k];
   if (tid == 0) {
     s_nc = 0;
     s_acc = nin;
@@ -1105,10 +1144,10 @@ __global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int me
     if (ds.rep[bp] != brep) continue;
     const int xp = xin ? x : e % nxs;
     const int64_t Ep = ds.candE[(size_t)bp * dmax + xp];
-    const int nd = ds.dn[cur][bp];
+    const int nd = pick(ds.dn, cur)[bp];
     for (int k = -1; k < nd; ++k) {
       if (k < 0 && bp == w && xp == x) continue;  // the winner itself
-      const int64_t dE = Ep + (k < 0 ? 0 : ds.dE[cur][(size_t)bp * MAXDROP + k]) - Ew;
+      const int64_t dE = Ep + (k < 0 ? 0 : pick(ds.dE, cur)[(size_t)bp * MAXDROP + k]) - Ew;
       if (dE > ds.dcut) continue;
       const int slot = atomicAdd(&s_nc, 1);
       if (slot < MAXDCAND) {
@@ -1147,7 +1186,7 @@ __global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int me
   __syncthreads();
   // greedy acceptance in rank order: Hamming distance > dham from the state
   // (the winner's row with x) and from every droplet kept so far
-  const uint16_t* wrow = ds.states[cur] + (size_t)w * N;
+  const uint16_t* wrow = pick(ds.states, cur) + (size_t)w * N;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int r = 0; r < nc; ++r) {
     const int a = crank[r];
@@ -1170,7 +1209,7 @@ __global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int me
       const int k = s_acc;
       if (k < MAXDROP) {
         for (int q = tid; q < N; q += nt) out[(size_t)k * N + q] = q == site ? (uint16_t)cx[a] : (q < site ? ra[q] : 0);
-        if (tid == 0) ds.dE[nxt][(size_t)i * MAXDROP + k] = cE[a];
+        if (tid == 0) pick(ds.dE, nxt)[(size_t)i * MAXDROP + k] = cE[a];
       } else if (tid == 0) {
         atomicAdd(ds.dflow, 1);
       }
@@ -1179,34 +1218,38 @@ __global__ void k_droplets(DevTables tb, int site, DevSearch ds, int cur, int me
     }
     __syncthreads();
   }
-  if (tid == 0) ds.dn[nxt][i] = s_acc;
+  if (tid == 0) pick(ds.dn, nxt)[i] = s_acc;
 }
 
 // The best final state's droplets, sorted by (energy, state).
-__global__ void k_final_droplets(DevSearch ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states) {
+__global__ void k_final_droplets(DevSearch ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states, size_t zs) {
+  ds = zp(ds, zs);
+  out_n = zp(out_n, zs);
+  out_E = zp(out_E, zs);
+  out_states = zp(out_states, zs);
   __shared__ int s_best;
   __shared__ int rk[MAXDROP];
   const int n = ds.n_beam[cur], N = ds.N;
   if (threadIdx.x == 0) {
     int b0 = -1;
     for (int b = 0; b < n; ++b)
-      if (b0 < 0 || ds.E[cur][b] < ds.E[cur][b0]) b0 = b;
+      if (b0 < 0 || pick(ds.E, cur)[b] < pick(ds.E, cur)[b0]) b0 = b;
     s_best = b0;
   }
   __syncthreads();
   const int b0 = s_best;
-  const int nd = b0 < 0 ? 0 : ds.dn[cur][b0];
+  const int nd = b0 < 0 ? 0 : pick(ds.dn, cur)[b0];
   if (threadIdx.x < nd) {
     const int a = threadIdx.x;
-    const uint16_t* ra = ds.dst[cur] + ((size_t)b0 * MAXDROP + a) * N;
-    const int64_t Ea = ds.dE[cur][(size_t)b0 * MAXDROP + a];
+    const uint16_t* ra = pick(ds.dst, cur) + ((size_t)b0 * MAXDROP + a) * N;
+    const int64_t Ea = pick(ds.dE, cur)[(size_t)b0 * MAXDROP + a];
     int r = 0;
     for (int o = 0; o < nd; ++o) {
       if (o == a) continue;
-      const int64_t Eo = ds.dE[cur][(size_t)b0 * MAXDROP + o];
+      const int64_t Eo = pick(ds.dE, cur)[(size_t)b0 * MAXDROP + o];
       bool less = Eo < Ea;
       if (Eo == Ea) {
-        const uint16_t* ro = ds.dst[cur] + ((size_t)b0 * MAXDROP + o) * N;
+        const uint16_t* ro = pick(ds.dst, cur) + ((size_t)b0 * MAXDROP + o) * N;
         int cmp = 0;
         for (int q = 0; q < N && !cmp; ++q) cmp = ro[q] < ra[q] ? -1 : (ro[q] > ra[q] ? 1 : 0);
         less = cmp < 0 || (cmp == 0 && o < a);
@@ -1218,9 +1261,9 @@ __global__ void k_final_droplets(DevSearch ds, int cur, int* out_n, int64_t* out
   __syncthreads();
   for (int e = threadIdx.x; e < nd * N; e += blockDim.x) {
     const int r = e / N, q = e % N;
-    out_states[(size_t)r * N + q] = ds.dst[cur][((size_t)b0 * MAXDROP + rk[r]) * N + q];
+    out_states[(size_t)r * N + q] = pick(ds.dst, cur)[((size_t)b0 * MAXDROP + rk[r]) * N + q];
   }
-  for (int r = threadIdx.x; r < nd; r += blockDim.x) out_E[r] = ds.E[cur][b0] + ds.dE[cur][(size_t)b0 * MAXDROP + rk[r]];
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) out_E[r] = pick(ds.E, cur)[b0] + pick(ds.dE, cur)[(size_t)b0 * MAXDROP + rk[r]];
   if (threadIdx.x == 0) *out_n = nd;
 }
 
@@ -1241,12 +1284,12 @@ __global__ void k_force_init(DevSearch ds, const int* n_dev, int cur) {
   }
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)n * N;
        e += (size_t)gridDim.x * blockDim.x) {
-    ds.states[cur][e] = 0;
+    pick(ds.states, cur)[e] = 0;
     if (e % N == 0) {
       const size_t b = e / N;
-      ds.E[cur][b] = 0;
-      ds.logp[cur][b] = 0.0;
-      ds.rid[cur][b] = 0;
+      pick(ds.E, cur)[b] = 0;
+      pick(ds.logp, cur)[b] = 0.0;
+      pick(ds.rid, cur)[b] = 0;
     }
   }
 }
@@ -1267,7 +1310,7 @@ __global__ void k_force(int site, DevSearch ds, int cur, const uint16_t* __restr
 
 // max over b < n and sites of |a - r| / max(1, |r|) (a state's own
 // conditionals in two precisions); a finite value against -inf counts as inf.
-__global__ void k_logmarg_err(const double* __restrict__ a, const double* __restrict__ r, const int* n_dev,
+__global__ void __launch_bounds__(1024) k_logmarg_err(const double* __restrict__ a, const double* __restrict__ r, const int* n_dev,
                               int N, double* out) {
   __shared__ double red[32];
   const size_t tot = (size_t)max(0, *n_dev) * N;
@@ -1298,15 +1341,21 @@ __global__ void k_logmarg_err(const double* __restrict__ a, const double* __rest
 // ---------------------------------------------------------------- S8 final
 // Exact energy of each final state from the tables (checked against the
 // running energy), then order by (energy, lex rank).
-__global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_states, int64_t* out_E,
-                        double* out_logp, int* out_n) {
+__global__ void __launch_bounds__(1024) k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_states, int64_t* out_E,
+                        double* out_logp, int* out_n, size_t zs) {
+  tb = zp(tb, zs);
+  ds = zp(ds, zs);
+  out_states = zp(out_states, zs);
+  out_E = zp(out_E, zs);
+  out_logp = zp(out_logp, zs);
+  out_n = zp(out_n, zs);
   extern __shared__ unsigned long long fin_smem[];
   long long* sE = reinterpret_cast<long long*>(fin_smem);   // [SPG_MAXFINAL]
   int* rank = reinterpret_cast<int*>(sE + SPG_MAXFINAL);    // [SPG_MAXFINAL]
   const int n = min(ds.n_beam[cur], SPG_MAXFINAL);
   const int N = ds.N, cols = tb.cols;
   for (int b = threadIdx.x; b < n; b += blockDim.x) {
-    const uint16_t* st = ds.states[cur] + (size_t)b * N;
+    const uint16_t* st = pick(ds.states, cur) + (size_t)b * N;
     int64_t E = 0;
     // every edge once: left and up-left in RL, up in RU, the anti-diagonal
     // (i-1, j)-(i, j-1) in RA (tables are zero where an edge is missing)
@@ -1323,7 +1372,7 @@ __global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_state
       E += tb.RU[(size_t)s * 256 + u * 16 + tb.PU[so + x]];
       E += tb.RA[(size_t)s * 256 + a * 16 + u];
     }
-    if (E != ds.E[cur][b]) atomicOr(ds.err, ERR_ENERGY);
+    if (E != pick(ds.E, cur)[b]) atomicOr(ds.err, ERR_ENERGY);
     sE[b] = E;
   }
   __syncthreads();
@@ -1337,11 +1386,11 @@ __global__ void k_final(DevTables tb, DevSearch ds, int cur, uint16_t* out_state
   for (int b = threadIdx.x; b < n; b += blockDim.x) {
     const int rk = rank[b];
     out_E[rk] = sE[b];
-    out_logp[rk] = ds.logp[cur][b];
+    out_logp[rk] = pick(ds.logp, cur)[b];
   }
   for (size_t e = threadIdx.x; e < (size_t)n * N; e += blockDim.x) {
     const int b = (int)(e / N), s = (int)(e % N);
-    out_states[(size_t)rank[b] * N + s] = ds.states[cur][e];
+    out_states[(size_t)rank[b] * N + s] = pick(ds.states, cur)[e];
   }
   if (threadIdx.x == 0) *out_n = n;
 }
@@ -1367,38 +1416,44 @@ cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> m
   const size_t smem = use_t ? full + tbytes : (use_smem ? full : base);
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_right_envs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 4096); });
+  ZOK(tb, wt, mps, ds, bt);
   count_launches("k_right_envs", st);
-  k_right_envs<T><<<(ds.cap + G - 1) / G, 512, smem, st>>>(tb, wt, mps, row, ds, bt, cur, G, use_smem, use_rn, use_t);
+  k_right_envs<T><<<dim3((ds.cap + G - 1) / G, 1, zn()), 512, smem, st>>>(tb, wt, mps, row, ds, bt, cur, G, use_smem,
+                                                                          use_rn, use_t, zs());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
                                   const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
+  ZOK(tb, wd, mps, ds, bt);
   count_launches("k_marginals", st);
-  k_marginals<T><<<ds.cap, 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur);
+  k_marginals<T><<<dim3(ds.cap, 1, zn()), 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur, zs());
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
+  ZOK(tb, ds);
   const int nbk = (ds.cap + 255) / 256;
+  const size_t z = zs();
+  cudaError_t e;
   if (merge) {
-    cudaMemsetAsync(ds.htab, 0, sizeof(int) * ds.hsize, st);
-    cudaMemsetAsync(ds.hmin, 0x7f, sizeof(int) * ds.hsize, st);
+    if ((e = zfill(ds.htab, 0, sizeof(int) * ds.hsize, st)) != cudaSuccess) return e;
+    if ((e = zfill(ds.hmin, 0x7f, sizeof(int) * ds.hsize, st)) != cudaSuccess) return e;
   }
   count_launches("k_class_insert", st);
-  k_class_insert<<<nbk, 256, 0, st>>>(tb, site, ds, cur, merge);
+  k_class_insert<<<dim3(nbk, 1, zn()), 256, 0, st>>>(tb, site, ds, cur, merge, z);
   const size_t tot = (size_t)ds.cap * ds.dmax;
   const int wb = (int)std::min<size_t>((tot + 255) / 256, 8192);
-  cudaMemsetAsync(ds.wmin, 0xff, sizeof(unsigned long long) * tot, st);
-  cudaMemsetAsync(ds.win, 0x7f, sizeof(int) * tot, st);
-  cudaMemsetAsync(ds.wkey, 0x7f, sizeof(int) * ds.cap, st);
+  if ((e = zfill(ds.wmin, 0xff, sizeof(unsigned long long) * tot, st)) != cudaSuccess) return e;
+  if ((e = zfill(ds.win, 0x7f, sizeof(int) * tot, st)) != cudaSuccess) return e;
+  if ((e = zfill(ds.wkey, 0x7f, sizeof(int) * ds.cap, st)) != cudaSuccess) return e;
   count_launches("k_win_min", st);
-  k_win_min<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
+  k_win_min<<<dim3(wb, 1, zn()), 256, 0, st>>>(tb, site, ds, cur, merge, z);
   count_launches("k_win_arg", st);
-  k_win_arg<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
+  k_win_arg<<<dim3(wb, 1, zn()), 256, 0, st>>>(tb, site, ds, cur, merge, z);
   count_launches("k_win_fix", st);
-  k_win_fix<<<wb, 256, 0, st>>>(tb, site, ds, cur, merge);
+  k_win_fix<<<dim3(wb, 1, zn()), 256, 0, st>>>(tb, site, ds, cur, merge, z);
   return cudaGetLastError();
 }
 
@@ -1410,56 +1465,65 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
   // other solves of a batch keep the remaining SMs (measured: batch of 32
   // +6.6%, one solve unchanged)
   const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 64);
+  ZOK(tb, ds);
+  const size_t z = zs();
+  const dim3 g(blocks, 1, zn()), g1(1, 1, zn());
   if (log_cut > -INFINITY) {
     count_launches("k_logp_max", st);
-    k_logp_max<<<blocks, 1024, 0, st>>>(tb, site, ds, cur);
+    k_logp_max<<<g, 1024, 0, st>>>(tb, site, ds, cur, z);
   }
   // pass 0 and the split scan every candidate; the later passes and the
   // final classification only the candidates of the chosen top digit
   count_launches("k_select_pass", st);
-  k_select_pass<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, 0, log_cut, nullptr, nullptr);
+  k_select_pass<<<g, 1024, 0, st>>>(tb, site, ds, cur, 0, log_cut, nullptr, nullptr, z);
   count_launches("k_select_classify", st);
-  k_select_classify<<<blocks, 1024, 0, st>>>(tb, site, ds, cur, log_cut, nullptr, nullptr, 1);
+  k_select_classify<<<g, 1024, 0, st>>>(tb, site, ds, cur, log_cut, nullptr, nullptr, 1, z);
   count_launches("k_select_refine", st);
-  k_select_refine<<<1, 1024, 0, st>>>(tb, site, ds, cur, log_cut);
+  k_select_refine<<<g1, 1024, 0, st>>>(tb, site, ds, cur, log_cut, z);
   int P = 1;
   while (P < ds.cap) P <<= 1;
   count_launches("k_select_sort", st);
-  k_select_sort<<<1, 1024, sizeof(unsigned long long) * P, st>>>(tb, site, ds, cur, cur ^ 1);
+  k_select_sort<<<g1, 1024, sizeof(unsigned long long) * P, st>>>(tb, site, ds, cur, cur ^ 1, z);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_update(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds, DevBeamT<T> bt, int cur,
                           cudaStream_t st) {
+  ZOK(tb, mps, ds, bt);
   count_launches("k_update", st);
-  k_update<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
+  k_update<T><<<dim3(ds.cap, 1, zn()), 64, 0, st>>>(tb, mps, site, ds, bt, cur, zs());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_lenv_from_prefix(const DevTables& tb, DevMPS<T> mps, int site, const DevSearch& ds,
                                     DevBeamT<T> bt, int cur, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;  // not part of a grouped solve
   count_launches("k_lenv_prefix", st);
   k_lenv_prefix<T><<<ds.cap, 64, 0, st>>>(tb, mps, site, ds, bt, cur);
   return cudaGetLastError();
 }
 
 namespace {
-__global__ void k_or_flag(int* dst, const int* src) {
+__global__ void k_or_flag(int* dst, const int* src, size_t zs) {
+  dst = zp(dst, zs);
+  src = zp(src, zs);
   if (threadIdx.x == 0) *dst |= *src;
 }
 }  // namespace
 
 cudaError_t launch_or_flag(int* dst, const int* src, cudaStream_t st) {
+  ZOK(dst, src);
   count_launches("k_or_flag", st);
-  k_or_flag<<<1, 32, 0, st>>>(dst, src);
+  k_or_flag<<<dim3(1, 1, zn()), 32, 0, st>>>(dst, src, zs());
   return cudaGetLastError();
 }
 
 namespace {
 // The GPU's global nanosecond timer at the moment this kernel runs.
-__global__ void k_stamp(unsigned long long* slot) {
+__global__ void k_stamp(unsigned long long* slot, size_t zs) {
+  slot = zp(slot, zs);
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   if (threadIdx.x == 0) *slot = t;
@@ -1467,14 +1531,16 @@ __global__ void k_stamp(unsigned long long* slot) {
 }  // namespace
 
 cudaError_t launch_stamp(unsigned long long* slot, cudaStream_t st) {
+  ZOK(slot);
   count_launches("k_stamp", st);
-  k_stamp<<<1, 32, 0, st>>>(slot);
+  k_stamp<<<dim3(1, 1, zn()), 32, 0, st>>>(slot, zs());
   return cudaGetLastError();
 }
 
 cudaError_t launch_reset_beam(const DevSearch& ds, int cur, cudaStream_t st) {
+  ZOK(ds);
   count_launches("k_reset_beam", st);
-  k_reset_beam<<<1, 256, 0, st>>>(ds, cur);
+  k_reset_beam<<<dim3(1, 1, zn()), 256, 0, st>>>(ds, cur, zs());
   return cudaGetLastError();
 }
 
@@ -1483,25 +1549,29 @@ cudaError_t launch_final(const DevTables& tb, const DevSearch& ds, int cur, uint
   const int sm = (int)((sizeof(long long) + sizeof(int)) * SPG_MAXFINAL);
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] { cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); });
+  ZOK(tb, ds, out_states, out_E, out_logp, out_n);
   count_launches("k_final", st);
-  k_final<<<1, 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n);
+  k_final<<<dim3(1, 1, zn()), 1024, sm, st>>>(tb, ds, cur, out_states, out_E, out_logp, out_n, zs());
   return cudaGetLastError();
 }
 
 cudaError_t launch_droplets(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
+  ZOK(tb, ds);
   count_launches("k_droplets", st);
-  k_droplets<<<ds.cap, 256, 0, st>>>(tb, site, ds, cur, merge);
+  k_droplets<<<dim3(ds.cap, 1, zn()), 256, 0, st>>>(tb, site, ds, cur, merge, zs());
   return cudaGetLastError();
 }
 
 cudaError_t launch_final_droplets(const DevSearch& ds, int cur, int* out_n, int64_t* out_E, uint16_t* out_states,
                                   cudaStream_t st) {
+  ZOK(ds, out_n, out_E, out_states);
   count_launches("k_final_droplets", st);
-  k_final_droplets<<<1, 256, 0, st>>>(ds, cur, out_n, out_E, out_states);
+  k_final_droplets<<<dim3(1, 1, zn()), 256, 0, st>>>(ds, cur, out_n, out_E, out_states, zs());
   return cudaGetLastError();
 }
 
 cudaError_t launch_force_init(const DevSearch& ds, const int* n_dev, int cur, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;
   count_launches("k_force_init", st);
   k_force_init<<<64, 256, 0, st>>>(ds, n_dev, cur);
   return cudaGetLastError();
@@ -1509,6 +1579,7 @@ cudaError_t launch_force_init(const DevSearch& ds, const int* n_dev, int cur, cu
 
 cudaError_t launch_force(int site, const DevSearch& ds, int cur, const uint16_t* targets, double* out,
                          cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;
   count_launches("k_force", st);
   k_force<<<(ds.cap + 255) / 256, 256, 0, st>>>(site, ds, cur, targets, out);
   return cudaGetLastError();
@@ -1516,8 +1587,66 @@ cudaError_t launch_force(int site, const DevSearch& ds, int cur, const uint16_t*
 
 cudaError_t launch_logmarg_err(const double* a, const double* r, const int* n_dev, int N, double* out,
                                cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;
   count_launches("k_logmarg_err", st);
   k_logmarg_err<<<1, 1024, 0, st>>>(a, r, n_dev, N, out);
+  return cudaGetLastError();
+}
+
+namespace {
+// Byte copies and fills inside a solve (k_zcopy: 16-byte words when both
+// ends and the size allow), one grid slice per instance of a group.
+__global__ void k_zcopy(void* dst, const void* src, size_t bytes, size_t zs) {
+  dst = zp(dst, zs);
+  src = zp(src, zs);
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15) == 0) {
+    const uint4* s = static_cast<const uint4*>(src);
+    uint4* d = static_cast<uint4*>(dst);
+    for (size_t i = i0; i < bytes / 16; i += st) d[i] = s[i];
+  } else {
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    for (size_t i = i0; i < bytes; i += st) d[i] = s[i];
+  }
+}
+__global__ void k_zfill(void* dst, int byte, size_t bytes, size_t zs) {
+  dst = zp(dst, zs);
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  const unsigned v = (unsigned)byte & 0xffu;
+  if (((reinterpret_cast<uintptr_t>(dst) | bytes) & 15) == 0) {
+    const unsigned w = v * 0x01010101u;
+    uint4* d = static_cast<uint4*>(dst);
+    for (size_t i = i0; i < bytes / 16; i += st) d[i] = make_uint4(w, w, w, w);
+  } else {
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    for (size_t i = i0; i < bytes; i += st) d[i] = (unsigned char)v;
+  }
+}
+}  // namespace
+
+// Without a group the stream's own copy and fill; in a group one kernel
+// over every instance.
+cudaError_t zcopy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (zn() == 1) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+  if (!zok(dst, src, static_cast<const char*>(dst) + bytes - 1, static_cast<const char*>(src) + bytes - 1))
+    return cudaErrorInvalidValue;
+  count_launches("k_zcopy", st);
+  const size_t units = (bytes + 15) / 16;
+  k_zcopy<<<dim3((unsigned)std::min<size_t>((units + 255) / 256, 1024), 1, zn()), 256, 0, st>>>(dst, src, bytes,
+                                                                                               zs());
+  return cudaGetLastError();
+}
+
+cudaError_t zfill(void* dst, int byte, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (zn() == 1) return cudaMemsetAsync(dst, byte, bytes, st);
+  if (!zok(dst, static_cast<const char*>(dst) + bytes - 1)) return cudaErrorInvalidValue;
+  count_launches("k_zfill", st);
+  const size_t units = (bytes + 15) / 16;
+  k_zfill<<<dim3((unsigned)std::min<size_t>((units + 255) / 256, 1024), 1, zn()), 256, 0, st>>>(dst, byte, bytes,
+                                                                                               zs());
   return cudaGetLastError();
 }
 

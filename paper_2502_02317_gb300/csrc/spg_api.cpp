@@ -55,6 +55,7 @@ struct spg_ctx {
     char* arena = nullptr;
     size_t arena_bytes = 0;
     int uses = 0;
+    int group_n = 1;  // instances of the lockstep group (P: instance 0's problem)
     cudaGraphExec_t exec = nullptr;  // the whole solve, one launch
     long long launches = 0;
   };
@@ -109,6 +110,11 @@ struct spg_problem {
 struct spg_result {
   spg_ctx* ctx = nullptr;
   int N = 0, cap = 0;
+  // the result's device buffers, one block laid out as the solve's staged
+  // outputs (carve_out), so that one copy fills it
+  void* blk = nullptr;
+  size_t blk_used = 0;
+  int group_size = 1;  // instances of the lockstep group this solve ran in
   uint16_t* d_states = nullptr;
   int64_t* d_E = nullptr;
   double* d_logp = nullptr;
@@ -785,7 +791,7 @@ int build_row(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const P
     }
   }
   if (!f64) CK(launch_left_canonical<T>(bb.mps, r + 1, cols, nullptr, bb.T1, st));
-  CK(cudaMemcpyAsync(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(zcopy(bb.mps.lognorm + r, bb.mps.lognorm + r + 1, sizeof(double), st));
   if (warm) {
     std::vector<float> X((size_t)cols * SPG_WS_FEATURES);
     ws_features(P, r, X.data());
@@ -979,6 +985,7 @@ int check_params(spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
   if (!(prm->cut_off_prob >= 0.0 && prm->cut_off_prob < 1.0)) return fail(ctx, SPG_EINVAL, "cut_off_prob in [0,1)");
   if (prm->fp64_rows < -1) return fail(ctx, SPG_EINVAL, "fp64_rows must be >= -1");
   if (prm->check_fp64 != 0 && prm->check_fp64 != 1) return fail(ctx, SPG_EINVAL, "check_fp64 must be 0 or 1");
+  if (prm->group_max < 0) return fail(ctx, SPG_EINVAL, "group_max must be >= 0");
   if (prm->droplet_hamming < 0 || !std::isfinite(prm->droplet_energy))
     return fail(ctx, SPG_EINVAL, "droplet_hamming must be >= 0 and droplet_energy finite");
   if (prm->droplet_energy >= 0.0 && std::ldexp(prm->droplet_energy, P->shift) > 4.0e18)
@@ -1003,17 +1010,37 @@ struct OutStage {
   uint16_t* dst;         // states [MAXDROP][N]
 };
 
+// The staged outputs carved from `ar` (the same sequence for the workspace
+// and for a result's block, so that both have one layout); returns the bytes
+// taken, 0 when the arena is too small.
+size_t carve_out(Arena& ar, const spg_problem* P, int cap, OutStage& o) {
+  const size_t off0 = ar.off;
+  o.states = ar.get<uint16_t>((size_t)cap * P->n);
+  o.E = ar.get<int64_t>(cap);
+  o.logp = ar.get<double>(cap);
+  o.n = ar.get<int>(4);
+  o.diag = ar.get<int>(4);
+  o.cand = ar.get<double>(2);
+  o.stamp = ar.get<unsigned long long>(4);
+  o.err = ar.get<double>(1);
+  o.dn = ar.get<int>(4);
+  o.dE = ar.get<int64_t>(MAXDROP);
+  o.dst = ar.get<uint16_t>((size_t)MAXDROP * P->n);
+  return o.dst ? ar.off - off0 : 0;
+}
+
 size_t out_stage_bytes(const spg_problem* P, int cap) {
-  return sizeof(uint16_t) * (size_t)cap * P->n + sizeof(int64_t) * cap + sizeof(double) * cap + 4096 +
-         sizeof(int64_t) * MAXDROP + sizeof(uint16_t) * MAXDROP * (size_t)P->n + 1024;
+  auto r = [](size_t x) { return (x + 255) & ~size_t(255); };
+  return r(sizeof(uint16_t) * (size_t)cap * P->n) + 2 * r(8 * (size_t)cap) + 7 * 256 + r(8 * MAXDROP) +
+         r(sizeof(uint16_t) * MAXDROP * (size_t)P->n);
 }
 
 template <typename T>
 int enqueue_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, const Plan& pl,
                      BoundaryBufs<T>& bb) {
   cudaStream_t st = ctx->stream;
-  CK(cudaMemsetAsync(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
-  CK(cudaMemsetAsync(bb.degc, 0, sizeof(int) * 4, st));
+  CK(zfill(bb.mps.lognorm, 0, sizeof(double) * (P->rows + 1), st));
+  CK(zfill(bb.degc, 0, sizeof(int) * 4, st));
   return run_boundary<T>(ctx, P, prm, pl, bb, 1);
 }
 
@@ -1041,14 +1068,14 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
   if (ds.dcut >= 0)
     CK(launch_final_droplets(ds, cur, o.dn, o.dE, o.dst, st));
   else
-    CK(cudaMemsetAsync(o.dn, 0, sizeof(int), st));
-  CK(cudaMemcpyAsync(o.dn + 1, ds.dflow, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(o.diag + 0, ds.near_ties, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(o.diag + 1, ds.err, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(o.diag + 2, bb.degc, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
+    CK(zfill(o.dn, 0, sizeof(int), st));
+  CK(zcopy(o.dn + 1, ds.dflow, sizeof(int), st));
+  CK(zcopy(o.diag + 0, ds.near_ties, sizeof(int), st));
+  CK(zcopy(o.diag + 1, ds.err, sizeof(int), st));
+  CK(zcopy(o.diag + 2, bb.degc, sizeof(int) * 2, st));
   CK(launch_or_flag(o.diag + 1, bb.degc + 2, st));  // truncation kernels' error flags
-  CK(cudaMemcpyAsync(o.cand, ds.candidates, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(o.cand + 1, bb.mps.lognorm + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(zcopy(o.cand, ds.candidates, sizeof(double), st));
+  CK(zcopy(o.cand + 1, bb.mps.lognorm + 1, sizeof(double), st));
   return SPG_OK;
 }
 
@@ -1084,21 +1111,132 @@ int enqueue_forced(spg_ctx* ctx, const spg_problem* P, BoundaryBufs<T>& bb, Sear
 // which serialises the worker threads of spg_solve_batch.  The phase times
 // come from GPU timer stamps inside the sequence.  The first occurrence runs
 // uncaptured (it also performs the one-time kernel set-up).
+// Host structure that a solve's launch sequence depends on: problems equal
+// in it can be solved in lockstep (their device tables have one layout and
+// every host decision is the same).
+bool same_structure(const spg_problem* a, const spg_problem* b) {
+  return a->rows == b->rows && a->cols == b->cols && a->n == b->n && a->dmax == b->dmax &&
+         a->node_type == b->node_type && a->shift == b->shift && a->bmax == b->bmax && a->lstride == b->lstride &&
+         a->ucpl == b->ucpl && a->dev_bytes == b->dev_bytes && a->kbits == b->kbits && a->o_E == b->o_E &&
+         a->o_RL == b->o_RL && a->o_RU == b->o_RU && a->o_RA == b->o_RA && a->d == b->d && a->dims == b->dims &&
+         a->gD == b->gD && a->keys == b->keys;
+}
+
+// The problem as the enqueue functions see it inside a group: instance 0's
+// structure with its tables at `tables` (a copy in the group's block).
+spg_problem group_view(const spg_problem* P, char* tables) {
+  spg_problem V;
+  V.ctx = P->ctx;
+  V.rows = P->rows;
+  V.cols = P->cols;
+  V.n = P->n;
+  V.dmax = P->dmax;
+  V.node_type = P->node_type;
+  V.shift = P->shift;
+  V.d = P->d;
+  V.dims = P->dims;
+  V.gD = P->gD;
+  V.bmax = P->bmax;
+  V.lstride = P->lstride;
+  V.ucpl = P->ucpl;
+  V.dev_bytes = P->dev_bytes;
+  V.kbits = P->kbits;
+  V.wspan = P->wspan;
+  V.dev = tables;
+  V.tb = P->tb;
+  const char* from = static_cast<const char*>(P->dev);
+  auto re = [&](auto* q) { return reinterpret_cast<decltype(q)>(tables + (reinterpret_cast<const char*>(q) - from)); };
+  DevTables& t = V.tb;
+  t.d = re(t.d);
+  t.E = re(t.E);
+  t.PL = re(t.PL);
+  t.PR = re(t.PR);
+  t.PU = re(t.PU);
+  t.PD = re(t.PD);
+  t.PG = re(t.PG);
+  t.dims = re(t.dims);
+  t.RL = re(t.RL);
+  t.RU = re(t.RU);
+  t.RA = re(t.RA);
+  t.gD = re(t.gD);
+  t.xsL = re(t.xsL);
+  t.xoffL = re(t.xoffL);
+  t.keys = re(t.keys);
+  t.kshift = re(t.kshift);
+  return V;
+}
+
+// Sets the calling thread's lockstep group for its lifetime.
+struct GroupScope {
+  explicit GroupScope(int n, size_t zs, const char* lo) {
+    Group& g = group();
+    g.n = n;
+    g.zs = zs;
+    g.lo = lo;
+    g.bad = false;
+  }
+  ~GroupScope() { group() = Group{}; }
+};
+
+// Bytes of one instance's block in a lockstep group: the problem's tables,
+// then the solve's workspace (1024-byte multiple: the tensor maps of the
+// tensor-core products step over instances by it).
 template <typename T>
-int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result* R) {
-  cudaStream_t st = ctx->stream;
-  const int chi = prm->chi, cap = prm->beam;
-  Plan pl = make_plan(P, chi, 1);
-  const int f64 = fp64_rows_of<T>(prm, P);
-  const spg_mlp* ws = warm_of(ctx, P, prm);
-  const bool check = std::is_same<T, float>::value && prm->check_fp64 != 0;
-  const size_t lcn = (size_t)cap * P->n;  // one log-conditional per (state, site)
+size_t group_stride(const spg_problem* P, const spg_params* prm) {
+  Plan pl = make_plan(P, prm->chi, 1);
   const bool drops = prm->merge && prm->droplet_energy >= 0.0;
-  size_t need = boundary_bytes<T>(P, pl, f64, ws) + search_bytes<T>(P, cap, chi, drops) + out_stage_bytes(P, cap);
-  if (check) need += boundary_bytes<double>(P, pl) + search_bytes<double>(P, cap, chi) + 2 * sizeof(double) * lcn + 4096;
-  int rc = ensure_arena(ctx, need);
-  if (rc) return rc;
-  Arena ar{ctx->arena, 0, ctx->arena_bytes};
+  const size_t tab = (P->dev_bytes + 1023) & ~size_t(1023);
+  const size_t need = boundary_bytes<T>(P, pl, fp64_rows_of<T>(prm, P)) +
+                      search_bytes<T>(P, prm->beam, prm->chi, drops) + out_stage_bytes(P, prm->beam);
+  return (tab + need + 1023) & ~size_t(1023);
+}
+
+// A solve is a fixed sequence of stream operations given the problem, the
+// parameters and the workspace (everything data-dependent lives on the
+// device), so it is captured into one CUDA graph on its second occurrence and
+// replayed from then on: one graph launch instead of tens of thousands of
+// kernel launches from the host.  One graph, not one per phase: a second graph
+// launch on the same stream can hold the host until the first graph has run,
+// which serialises the worker threads of spg_solve_batch.  The phase times
+// come from GPU timer stamps inside the sequence.  The first occurrence runs
+// uncaptured (it also performs the one-time kernel set-up).
+//
+// With ng > 1 the problems probs[0 .. ng) (one structure, same_structure)
+// are solved in lockstep: instance g's tables (copied from its problem) and
+// workspace sit at g * zs in one block, and every launch of the sequence
+// covers all ng instances (blockIdx.z), so the group costs the launches of
+// one solve and its one-CTA kernels fill ng SMs at once.
+template <typename T>
+int solve_impl(spg_ctx* ctx, const spg_problem* const* probs, int ng, const spg_params* prm, spg_result* const* Rs) {
+  cudaStream_t st = ctx->stream;
+  const spg_problem* P0 = probs[0];
+  const int chi = prm->chi, cap = prm->beam;
+  Plan pl = make_plan(P0, chi, 1);
+  const int f64 = fp64_rows_of<T>(prm, P0);
+  const spg_mlp* ws = ng == 1 ? warm_of(ctx, P0, prm) : nullptr;
+  const bool check = ng == 1 && std::is_same<T, float>::value && prm->check_fp64 != 0;
+  const size_t lcn = (size_t)cap * P0->n;  // one log-conditional per (state, site)
+  const bool drops = prm->merge && prm->droplet_energy >= 0.0;
+  size_t zstride = 0, tab = 0;
+  char* gbase = nullptr;
+  int rc;
+  if (ng == 1) {
+    size_t need = boundary_bytes<T>(P0, pl, f64, ws) + search_bytes<T>(P0, cap, chi, drops) + out_stage_bytes(P0, cap);
+    if (check)
+      need += boundary_bytes<double>(P0, pl) + search_bytes<double>(P0, cap, chi) + 2 * sizeof(double) * lcn + 4096;
+    if ((rc = ensure_arena(ctx, need))) return rc;
+  } else {
+    zstride = group_stride<T>(P0, prm);
+    tab = (P0->dev_bytes + 1023) & ~size_t(1023);
+    if ((rc = ensure_arena(ctx, zstride * ng + 1024))) return rc;
+    gbase = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ctx->arena) + 1023) & ~uintptr_t(1023));
+  }
+  // the problem the enqueue functions see (instance 0 of a group: its tables
+  // in the group's block)
+  spg_problem Vg;
+  if (ng > 1) Vg = group_view(P0, gbase);
+  const spg_problem* P = ng > 1 ? &Vg : P0;
+  Arena ar = ng > 1 ? Arena{gbase + tab, 0, zstride - tab} : Arena{ctx->arena, 0, ctx->arena_bytes};
   BoundaryBufs<T> bb;
   SearchBufs<T> sb;
   if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false, f64, ws))) return rc;
@@ -1107,20 +1245,10 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     sb.ds.dcut = (int64_t)std::floor(std::ldexp(prm->droplet_energy, P->shift));
     sb.ds.dham = prm->droplet_hamming;
   }
-  R->fp64_rows = std::min(f64, std::max(0, P->rows - 1));
+  for (int g = 0; g < ng; ++g) Rs[g]->fp64_rows = std::min(f64, std::max(0, P->rows - 1));
   OutStage o;
-  o.states = ar.get<uint16_t>((size_t)cap * P->n);
-  o.E = ar.get<int64_t>(cap);
-  o.logp = ar.get<double>(cap);
-  o.n = ar.get<int>(4);
-  o.diag = ar.get<int>(4);
-  o.cand = ar.get<double>(2);
-  o.stamp = ar.get<unsigned long long>(4);
-  o.err = ar.get<double>(1);
-  o.dn = ar.get<int>(4);
-  o.dE = ar.get<int64_t>(MAXDROP);
-  o.dst = ar.get<uint16_t>((size_t)MAXDROP * P->n);
-  if (!o.dst) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
+  const size_t out_used = carve_out(ar, P, cap, o);
+  if (!out_used) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   if (sizeof(T) == sizeof(double)) bb.wd = *reinterpret_cast<DevWeights<double>*>(&bb.wt);
   // the plain FP64 boundary and search buffers of the check
   BoundaryBufs<double> bb64;
@@ -1134,22 +1262,29 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     lc_fp64 = ar.get<double>(lcn);
     if (!lc_fp64) return fail(ctx, SPG_ENOMEM, "workspace carve overflow");
   }
-  // plan dims: host data, uploaded outside any capture
-  CK(cudaMemcpyAsync(bb.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
+  // host data uploaded outside any capture: the plan's dims, and in a group
+  // every instance's tables (problems may have been updated in place)
+  for (int g = 0; g < ng; ++g) {
+    const size_t zo = (size_t)g * zstride;
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(bb.dimA_dev) + zo, pl.dimA.data(), sizeof(int) * pl.dimA.size(),
+                       cudaMemcpyHostToDevice, st));
+    if (ng > 1) CK(cudaMemcpyAsync(gbase + zo, probs[g]->dev, P0->dev_bytes, cudaMemcpyDeviceToDevice, st));
+  }
   if (check)
     CK(cudaMemcpyAsync(bb64.dimA_dev, pl.dimA.data(), sizeof(int) * pl.dimA.size(), cudaMemcpyHostToDevice, st));
 
-  spg_ctx::Graph* g = nullptr;
+  spg_ctx::Graph* gr_entry = nullptr;
   // a warm-started solve uploads each row's network inputs from the host on
   // the way, so it is never captured
   const bool capturable = !prm->warm_start;
   if (capturable)
     for (auto& e : ctx->graphs)
-    if (e.problem == P && e.tsize == (int)sizeof(T) && e.arena == ctx->arena && e.arena_bytes == ctx->arena_bytes &&
-        std::memcmp(&e.prm, prm, sizeof(spg_params)) == 0)
-      g = &e;
+      if (e.problem == P0 && e.group_n == ng && e.tsize == (int)sizeof(T) && e.arena == ctx->arena &&
+          e.arena_bytes == ctx->arena_bytes && std::memcmp(&e.prm, prm, sizeof(spg_params)) == 0)
+        gr_entry = &e;
   const bool profiling = kernel_profile().on;
   const long long l0 = thread_launches();
+  GroupScope gscope(ng, zstride, gbase);
   // the whole solve: stamp, boundary phase, stamp, search phase, stamp
   auto enqueue_all = [&]() -> int {
     CK(launch_stamp(o.stamp + 0, st));
@@ -1167,9 +1302,10 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
       CK(launch_logmarg_err(lc_mixed, lc_fp64, o.n, P->n, o.err, st));
     } else {
       // 0 in the FP64 mode; NaN (all bits set) when the mixed mode is unchecked
-      CK(cudaMemsetAsync(o.err, sizeof(T) == sizeof(double) ? 0 : 0xff, sizeof(double), st));
+      CK(zfill(o.err, sizeof(T) == sizeof(double) ? 0 : 0xff, sizeof(double), st));
     }
     if (profiling) profile_mark(st);  // closes the last kernel's interval
+    if (group().bad) return fail(ctx, SPG_EINVAL, "a launch of the group referenced memory outside its block");
     return SPG_OK;
   };
   // capture into an executable graph (nullptr on failure, rc set)
@@ -1187,55 +1323,53 @@ int solve_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_re
     if (e2 != cudaSuccess) return fail(ctx, SPG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
     return SPG_OK;
   };
+  long long launches = 0;
   if (profiling && capturable) {
     // captured with the profiler's per-kernel event records as graph nodes,
     // so that the times between them are device times without host gaps
     cudaGraphExec_t ex = nullptr;
     if ((rc = capture(&ex))) return rc;
     CK(cudaGraphLaunch(ex, st));
-    R->launches = thread_launches() - l0;
+    launches = thread_launches() - l0;
     CK(cudaStreamSynchronize(st));
     cudaGraphExecDestroy(ex);
-  } else if (g && g->exec) {
-    CK(cudaGraphLaunch(g->exec, st));
-    R->launches = g->launches;
-  } else if (g) {
-    if ((rc = capture(&g->exec))) return rc;
-    g->launches = thread_launches() - l0;
-    CK(cudaGraphLaunch(g->exec, st));
-    R->launches = g->launches;
+  } else if (gr_entry && gr_entry->exec) {
+    CK(cudaGraphLaunch(gr_entry->exec, st));
+    launches = gr_entry->launches;
+  } else if (gr_entry) {
+    if ((rc = capture(&gr_entry->exec))) return rc;
+    gr_entry->launches = thread_launches() - l0;
+    CK(cudaGraphLaunch(gr_entry->exec, st));
+    launches = gr_entry->launches;
   } else if (!capturable) {
     if ((rc = enqueue_all())) return rc;
-    R->launches = thread_launches() - l0;
+    launches = thread_launches() - l0;
   } else {
     if ((rc = enqueue_all())) return rc;
-    R->launches = thread_launches() - l0;
+    launches = thread_launches() - l0;
     if (ctx->graphs.size() >= 8) {  // keep the most recent entries
       auto& old = ctx->graphs.front();
       if (old.exec) cudaGraphExecDestroy(old.exec);
       ctx->graphs.erase(ctx->graphs.begin());
     }
     spg_ctx::Graph ne;
-    ne.problem = P;
+    ne.problem = P0;
+    ne.group_n = ng;
     ne.prm = *prm;
     ne.tsize = (int)sizeof(T);
     ne.arena = ctx->arena;
     ne.arena_bytes = ctx->arena_bytes;
     ctx->graphs.push_back(ne);
   }
-  // staged outputs into the result's own buffers
-  CK(cudaMemcpyAsync(R->d_states, o.states, sizeof(uint16_t) * (size_t)cap * P->n, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_E, o.E, sizeof(int64_t) * cap, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_logp, o.logp, sizeof(double) * cap, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_n, o.n, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_diag, o.diag, sizeof(int) * 4, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_cand, o.cand, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_stamp, o.stamp, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_err, o.err, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_dn, o.dn, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_dE, o.dE, sizeof(int64_t) * MAXDROP, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(R->d_dst, o.dst, sizeof(uint16_t) * MAXDROP * (size_t)P->n, cudaMemcpyDeviceToDevice, st));
-  CK(cudaEventRecord(R->ev[2], st));
+  // staged outputs into each result's own block (one layout, one copy)
+  for (int g = 0; g < ng; ++g) {
+    spg_result* R = Rs[g];
+    R->launches = launches;
+    R->group_size = ng;
+    CK(cudaMemcpyAsync(R->blk, reinterpret_cast<const char*>(o.states) + (size_t)g * zstride, out_used,
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(R->ev[2], st));
+  }
   return SPG_OK;
 }
 
@@ -1904,12 +2038,13 @@ int spg_problem_shape(const spg_problem* P, int32_t* rows, int32_t* cols, int32_
   return SPG_OK;
 }
 
-int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result** out) {
-  if (!ctx || !P || !out) return SPG_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// A result handle with its device block (the staged outputs' layout).
+int make_result(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result** out) {
   *out = nullptr;
-  int rc = check_params(ctx, P, prm);
-  if (rc) return rc;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
   spg_result* R = new (std::nothrow) spg_result();
   if (!R) return SPG_ENOMEM;
   R->ctx = ctx;
@@ -1917,33 +2052,133 @@ int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_res
   R->N = P->n;
   R->cap = prm->beam;
   cudaStream_t st = ctx->stream;
-  auto cleanup = [&](int code) {
-    spg_result_destroy(R);
-    return code;
-  };
   // completion event (the phase times come from GPU timer stamps)
-  if (cudaEventCreateWithFlags(&R->ev[2], cudaEventDisableTiming) != cudaSuccess)
-    return cleanup(fail(ctx, SPG_ECUDA, "event create"));
-  if (cudaMallocAsync((void**)&R->d_states, sizeof(uint16_t) * (size_t)R->cap * R->N, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_E, sizeof(int64_t) * R->cap, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_logp, sizeof(double) * R->cap, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_n, sizeof(int) * 4, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_diag, sizeof(int) * 4, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_cand, sizeof(double) * 2, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_stamp, sizeof(unsigned long long) * 3, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_err, sizeof(double), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_dn, sizeof(int) * 2, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_dE, sizeof(int64_t) * MAXDROP, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&R->d_dst, sizeof(uint16_t) * MAXDROP * (size_t)R->N, st) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(ctx, SPG_ENOMEM, "result allocation failed"));
+  if (cudaEventCreateWithFlags(&R->ev[2], cudaEventDisableTiming) != cudaSuccess) {
+    spg_result_destroy(R);
+    return fail(ctx, SPG_ECUDA, "event create");
   }
-  const bool use64 = prm->precision == SPG_FP64 || fp32_range_exceeded(P, prm);
-  R->precision_used = use64 ? SPG_FP64 : SPG_MIXED;
-  rc = use64 ? solve_impl<double>(ctx, P, prm, R) : solve_impl<float>(ctx, P, prm, R);
-  if (rc) return cleanup(rc);
+  const size_t bytes = out_stage_bytes(P, R->cap);
+  if (cudaMallocAsync(&R->blk, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    R->blk = nullptr;
+    spg_result_destroy(R);
+    return fail(ctx, SPG_ENOMEM, "result allocation failed");
+  }
+  Arena ar{static_cast<char*>(R->blk), 0, bytes};
+  OutStage o;
+  R->blk_used = carve_out(ar, P, R->cap, o);
+  R->d_states = o.states;
+  R->d_E = o.E;
+  R->d_logp = o.logp;
+  R->d_n = o.n;
+  R->d_diag = o.diag;
+  R->d_cand = o.cand;
+  R->d_stamp = o.stamp;
+  R->d_err = o.err;
+  R->d_dn = o.dn;
+  R->d_dE = o.dE;
+  R->d_dst = o.dst;
   *out = R;
   return SPG_OK;
+}
+
+bool runs_fp64(const spg_problem* P, const spg_params* prm) {
+  return prm->precision == SPG_FP64 || fp32_range_exceeded(P, prm);
+}
+
+// Whether problems a and b with parameters pa, pb can share a lockstep group.
+bool groupable(const spg_problem* a, const spg_params* pa, const spg_problem* b, const spg_params* pb) {
+  return std::memcmp(pa, pb, sizeof(spg_params)) == 0 && !pa->warm_start && !pa->check_fp64 &&
+         runs_fp64(a, pa) == runs_fp64(b, pb) && same_structure(a, b);
+}
+
+// Lockstep group of n problems (n >= 1) on ctx: results in out[0 .. n).
+int solve_group(spg_ctx* ctx, int n, const spg_problem* const* probs, const spg_params* prm, spg_result** out) {
+  for (int g = 0; g < n; ++g) out[g] = nullptr;
+  for (int g = 0; g < n; ++g) {
+    const int rc = make_result(ctx, probs[g], prm, &out[g]);
+    if (rc) {
+      for (int h = 0; h < n; ++h) {
+        spg_result_destroy(out[h]);
+        out[h] = nullptr;
+      }
+      return rc;
+    }
+  }
+  const bool use64 = runs_fp64(probs[0], prm);
+  for (int g = 0; g < n; ++g) out[g]->precision_used = use64 ? SPG_FP64 : SPG_MIXED;
+  const int rc = use64 ? solve_impl<double>(ctx, probs, n, prm, out) : solve_impl<float>(ctx, probs, n, prm, out);
+  if (rc) {
+    for (int g = 0; g < n; ++g) {
+      spg_result_destroy(out[g]);
+      out[g] = nullptr;
+    }
+  }
+  return rc;
+}
+
+// Most instances of one lockstep group: one per SM fills the GPU with the
+// group's one-CTA kernels in a single wave; at most half the free device
+// memory; the grid limit of the state-batched sweep products (states x
+// instances < 65536).
+// Largest state batch (grid.z of one instance) of the sweeps' products.
+int max_state_batch(const spg_problem* P) {
+  int m = 1;
+  for (int s = 0; s < P->n; ++s) {
+    const int* dm = &P->dims[(size_t)s * DIMW];
+    m = std::max(m, std::max(P->d[s], MAXP * std::max(dm[D_DR], dm[D_NL])));
+  }
+  return m;
+}
+
+int group_cap(const spg_ctx* ctx, const spg_problem* P, const spg_params* prm) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const size_t per = runs_fp64(P, prm) ? group_stride<double>(P, prm) : group_stride<float>(P, prm);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = 0;
+  }
+  const size_t by_mem = per ? (fr / 2 + (size_t)ctx->arena_bytes) / per : 1;
+  int cap = std::max(1, sms);
+  cap = (int)std::min<size_t>((size_t)cap, std::max<size_t>(1, by_mem));
+  cap = std::min(cap, std::max(1, 65535 / max_state_batch(P)));
+  return std::min(cap, SPG_MAX_GROUP);
+}
+
+}  // namespace
+
+extern "C" {
+
+int spg_solve(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, spg_result** out) {
+  if (!ctx || !P || !out) return SPG_EINVAL;
+  *out = nullptr;
+  int rc = check_params(ctx, P, prm);
+  if (rc) return rc;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return solve_group(ctx, 1, &P, prm, out);
+}
+
+int spg_solve_group(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prm,
+                    spg_result** out) {
+  if (!ctx || !probs || !prm || !out || n < 1) return SPG_EINVAL;
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  if (n > SPG_MAX_GROUP) return fail(ctx, SPG_EUNSUPPORTED, "group larger than SPG_MAX_GROUP");
+  for (int i = 0; i < n; ++i) {
+    if (!probs[i]) return fail(ctx, SPG_EINVAL, "NULL problem in group");
+    const int rc = check_params(ctx, probs[i], prm);
+    if (rc) return rc;
+  }
+  if (prm->warm_start || prm->check_fp64)
+    return fail(ctx, SPG_EUNSUPPORTED, "warm_start and check_fp64 solves are not grouped");
+  for (int i = 1; i < n; ++i)
+    if (!groupable(probs[0], prm, probs[i], prm))
+      return fail(ctx, SPG_EINVAL, "group item " + std::to_string(i) + " differs in structure from item 0");
+  if ((long long)n * max_state_batch(probs[0]) > 65535)
+    return fail(ctx, SPG_EUNSUPPORTED, "group too large for this lattice's state batches (n x states < 65536)");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
+  return solve_group(ctx, n, probs, prm, out);
 }
 
 int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, const spg_params* prms,
@@ -1956,7 +2191,36 @@ int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, co
     if (rc) return rc;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SPG_ECUDA, "cudaSetDevice failed");
-  const int K = std::min(n, 32);
+  // lockstep groups: items of one structure and equal parameters, in order of
+  // first occurrence, at most group_cap (or prm.group_max) per group, the
+  // items of a class spread evenly over its groups
+  std::vector<std::vector<int>> classes;
+  for (int i = 0; i < n; ++i) {
+    bool placed = false;
+    if (prms[i].group_max != 1)
+      for (auto& c : classes)
+        if (prms[c[0]].group_max != 1 && groupable(probs[c[0]], &prms[c[0]], probs[i], &prms[i])) {
+          c.push_back(i);
+          placed = true;
+          break;
+        }
+    if (!placed) classes.push_back({i});
+  }
+  std::vector<std::vector<int>> groups;
+  for (auto& c : classes) {
+    const int gmax = prms[c[0]].group_max > 0
+                         ? std::min(std::min(prms[c[0]].group_max, SPG_MAX_GROUP),
+                                    std::max(1, 65535 / max_state_batch(probs[c[0]])))
+                         : group_cap(ctx, probs[c[0]], &prms[c[0]]);
+    const int ng = ((int)c.size() + gmax - 1) / gmax;
+    for (int k = 0; k < ng; ++k) {
+      std::vector<int> g;
+      for (size_t q = (size_t)k * c.size() / ng; q < (size_t)(k + 1) * c.size() / ng; ++q) g.push_back(c[q]);
+      groups.push_back(std::move(g));
+    }
+  }
+  const int G = (int)groups.size();
+  const int K = std::min(G, 32);
   while ((int)ctx->workers.size() < K) {
     spg_ctx* w = nullptr;
     const int rc = spg_create(&w, ctx->device, nullptr);
@@ -1969,12 +2233,19 @@ int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, co
   CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   CK(cudaEventRecord(start, ctx->stream));
   for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(ctx->workers[k]->stream, start, 0));
-  std::vector<int> rcs(n, SPG_OK);
+  std::vector<int> rcs(G, SPG_OK);
   std::vector<std::thread> threads;
   for (int k = 0; k < K; ++k)
     threads.emplace_back([&, k] {
       cudaSetDevice(ctx->device);
-      for (int i = k; i < n; i += K) rcs[i] = spg_solve(ctx->workers[k], probs[i], &prms[i], &out[i]);
+      for (int q = k; q < G; q += K) {
+        const std::vector<int>& g = groups[q];
+        std::vector<const spg_problem*> gp(g.size());
+        std::vector<spg_result*> gr(g.size(), nullptr);
+        for (size_t i = 0; i < g.size(); ++i) gp[i] = probs[g[i]];
+        rcs[q] = solve_group(ctx->workers[k], (int)g.size(), gp.data(), &prms[g[0]], gr.data());
+        for (size_t i = 0; i < g.size(); ++i) out[g[i]] = gr[i];
+      }
     });
   for (auto& t : threads) t.join();
   // later work on the context's stream runs after the batch
@@ -1986,14 +2257,14 @@ int spg_solve_batch(spg_ctx* ctx, int32_t n, const spg_problem* const* probs, co
     cudaEventDestroy(done);
   }
   cudaEventDestroy(start);
-  for (int i = 0; i < n; ++i)
-    if (rcs[i] != SPG_OK) {
-      const std::string msg = ctx->workers[i % K]->err;
+  for (int q = 0; q < G; ++q)
+    if (rcs[q] != SPG_OK) {
+      const std::string msg = ctx->workers[q % K]->err;
       for (int j = 0; j < n; ++j) {
         spg_result_destroy(out[j]);
         out[j] = nullptr;
       }
-      return fail(ctx, rcs[i], "batch item " + std::to_string(i) + ": " + msg);
+      return fail(ctx, rcs[q], "batch item " + std::to_string(groups[q][0]) + ": " + msg);
     }
   return SPG_OK;
 }
@@ -2059,6 +2330,7 @@ int spg_result_info(spg_result* R, spg_info* info) {
   info->jacobi_sweeps_max = diag[3];
   info->fp64_rows = R->fp64_rows;
   info->precision_used = R->precision_used;
+  info->group_size = R->group_size;
   int dnf[2] = {0, 0};
   CK(cudaMemcpy(dnf, R->d_dn, sizeof(int) * 2, cudaMemcpyDeviceToHost));
   info->droplet_overflow = dnf[1];
@@ -2072,17 +2344,7 @@ void spg_result_destroy(spg_result* R) {
   // stream-ordered frees: after the solve that wrote the buffers, without
   // holding the host (a worker stream may already run the next batch)
   cudaStream_t st = R->ctx->stream;
-  if (R->d_states) cudaFreeAsync(R->d_states, st);
-  if (R->d_E) cudaFreeAsync(R->d_E, st);
-  if (R->d_logp) cudaFreeAsync(R->d_logp, st);
-  if (R->d_n) cudaFreeAsync(R->d_n, st);
-  if (R->d_diag) cudaFreeAsync(R->d_diag, st);
-  if (R->d_cand) cudaFreeAsync(R->d_cand, st);
-  if (R->d_stamp) cudaFreeAsync(R->d_stamp, st);
-  if (R->d_err) cudaFreeAsync(R->d_err, st);
-  if (R->d_dn) cudaFreeAsync(R->d_dn, st);
-  if (R->d_dE) cudaFreeAsync(R->d_dE, st);
-  if (R->d_dst) cudaFreeAsync(R->d_dst, st);
+  if (R->blk) cudaFreeAsync(R->blk, st);
   for (int k = 0; k < 3; ++k)
     if (R->ev[k]) cudaEventDestroy(R->ev[k]);
   cudaGetLastError();
@@ -2410,9 +2672,9 @@ int spg_solve_lattice8(spg_ctx* ctx, const spg_problem* P, const spg_params* prm
   k_permute_sites<<<std::max(1, std::min(1024, (R->cap * R->N + 255) / 256)), 256, 0, st>>>(R->d_states, remapped,
                                                                                              R->d_n, R->N, map_dev);
   CK(cudaGetLastError());
-  cudaFreeAsync(R->d_states, st);
+  CK(cudaMemcpyAsync(R->d_states, remapped, sizeof(uint16_t) * (size_t)R->cap * R->N, cudaMemcpyDeviceToDevice, st));
+  cudaFreeAsync(remapped, st);
   cudaFreeAsync(map_dev, st);
-  R->d_states = remapped;
   CK(cudaStreamSynchronize(st));
   release();
   if (best_k) *best_k = kb;

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -37,6 +38,21 @@ namespace spg {
 // last of them is destroyed, whatever the order of the destroy calls.
 void ctx_retain(spg_ctx* ctx);
 void ctx_release(spg_ctx* ctx);
+
+// The lockstep group of the calling host thread (see the group section
+// below): instances every launch covers, and their byte stride.
+struct Group {
+  int n = 1;
+  size_t zs = 0;
+  const char* lo = nullptr;
+  bool bad = false;  // a launch was refused
+};
+inline Group& group() {
+  thread_local Group g;
+  return g;
+}
+inline unsigned zn() { return (unsigned)group().n; }
+inline size_t zs() { return group().zs; }
 
 // Kernels enqueued by this library since load (every launcher adds its own).
 inline std::atomic<long long>& launch_counter() {
@@ -92,7 +108,7 @@ inline void count_launches(const char* name, cudaStream_t st, double flops = 0.0
   record_mark(p.pool[p.used], st);
   p.names.push_back(name);
   p.streams.push_back(st);
-  p.flops.push_back(flops);
+  p.flops.push_back(flops * zn());  // a launch covers every instance of the group
   ++p.used;
 }
 
@@ -365,6 +381,171 @@ struct DevBeamT {
   int rs;      // bond stride of R (the largest bond dimension)
   int chi;
 };
+
+// ------------------------------------------------------------------ lockstep groups
+// A group is n instances whose device data (tables, workspace, staged
+// outputs) have the same layout, instance g at a byte offset g * zs from
+// instance 0's.  While a group is set on the calling host thread, every
+// launcher runs its grid once per instance (blockIdx.z = instance) and
+// passes zs; each kernel shifts its pointers by blockIdx.z * zs on entry.
+// Before a launch the host checks that every pointer argument lies inside
+// instance 0's block [lo, lo + zs) (a pointer outside it would be shifted
+// into another allocation), and refuses the launch otherwise.  Without a
+// group n = 1 and zs = 0: the same kernels, no shift.
+
+// zadd: every pointer moved by `off` bytes (null stays null); zp: by the
+// block's instance, blockIdx.z * zs.
+template <typename T>
+__host__ __device__ __forceinline__ T* zadd(T* p, size_t off) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<typename std::remove_const<T>::type*>(p)) + off)
+           : p;
+}
+__host__ __device__ __forceinline__ DevTables zadd(DevTables t, size_t off) {
+  t.d = zadd(t.d, off);
+  t.E = zadd(t.E, off);
+  t.PL = zadd(t.PL, off);
+  t.PR = zadd(t.PR, off);
+  t.PU = zadd(t.PU, off);
+  t.PD = zadd(t.PD, off);
+  t.PG = zadd(t.PG, off);
+  t.dims = zadd(t.dims, off);
+  t.RL = zadd(t.RL, off);
+  t.RU = zadd(t.RU, off);
+  t.RA = zadd(t.RA, off);
+  t.gD = zadd(t.gD, off);
+  t.xsL = zadd(t.xsL, off);
+  t.xoffL = zadd(t.xoffL, off);
+  t.keys = zadd(t.keys, off);
+  t.kshift = zadd(t.kshift, off);
+  return t;
+}
+template <typename T>
+__host__ __device__ __forceinline__ DevWeights<T> zadd(DevWeights<T> w, size_t off) {
+  w.w = zadd(w.w, off);
+  w.bL = zadd(w.bL, off);
+  w.bU = zadd(w.bU, off);
+  w.bA = zadd(w.bA, off);
+  return w;
+}
+template <typename T>
+__host__ __device__ __forceinline__ DevMPS<T> zadd(DevMPS<T> m, size_t off) {
+  m.A = zadd(m.A, off);
+  m.dimA = zadd(m.dimA, off);
+  m.lognorm = zadd(m.lognorm, off);
+  return m;
+}
+__host__ __device__ __forceinline__ DevSearch zadd(DevSearch d, size_t off) {
+  for (int k = 0; k < 2; ++k) {
+    d.states[k] = zadd(d.states[k], off);
+    d.E[k] = zadd(d.E[k], off);
+    d.logp[k] = zadd(d.logp[k], off);
+    d.rid[k] = zadd(d.rid[k], off);
+    d.dn[k] = zadd(d.dn[k], off);
+    d.dE[k] = zadd(d.dE[k], off);
+    d.dst[k] = zadd(d.dst[k], off);
+  }
+  d.n_beam = zadd(d.n_beam, off);
+  d.logc = zadd(d.logc, off);
+  d.candE = zadd(d.candE, off);
+  d.win = zadd(d.win, off);
+  d.wmin = zadd(d.wmin, off);
+  d.wkey = zadd(d.wkey, off);
+  d.key = zadd(d.key, off);
+  d.rep = zadd(d.rep, off);
+  d.nxt = zadd(d.nxt, off);
+  d.htab = zadd(d.htab, off);
+  d.hmin = zadd(d.hmin, off);
+  d.hist = zadd(d.hist, off);
+  d.sel_state = zadd(d.sel_state, off);
+  d.sel_list = zadd(d.sel_list, off);
+  d.sel_count = zadd(d.sel_count, off);
+  d.pend = zadd(d.pend, off);
+  d.pend_n = zadd(d.pend_n, off);
+  d.done_ctr = zadd(d.done_ctr, off);
+  d.near_ties = zadd(d.near_ties, off);
+  d.err = zadd(d.err, off);
+  d.candidates = zadd(d.candidates, off);
+  d.deg_cuts = zadd(d.deg_cuts, off);
+  d.dflow = zadd(d.dflow, off);
+  return d;
+}
+template <typename T>
+__host__ __device__ __forceinline__ DevBeamT<T> zadd(DevBeamT<T> b, size_t off) {
+  b.lenv[0] = zadd(b.lenv[0], off);
+  b.lenv[1] = zadd(b.lenv[1], off);
+  b.R = zadd(b.R, off);
+  return b;
+}
+
+// Element k (0 or 1) of a pointer pair by selection, not indexing: a
+// kernel's shifted copy of DevSearch / DevBeamT then stays in registers
+// (indexing the copy's arrays by a runtime k would place it in local memory).
+template <typename P>
+__device__ __forceinline__ P pick(P const (&a)[2], int k) {
+  return k ? a[1] : a[0];
+}
+
+template <typename X>
+__device__ __forceinline__ X zp(X x, size_t zs) {
+  return zadd(x, (size_t)blockIdx.z * zs);
+}
+
+// Host check of a launch's pointer arguments against instance 0's block
+// (always true without a group); a failure marks the group bad.
+inline bool zin(const void* p) {
+  const Group& g = group();
+  if (g.n <= 1 || !p) return true;
+  const char* c = static_cast<const char*>(p);
+  return c >= g.lo && c < g.lo + g.zs;
+}
+inline bool zin1(const DevTables& t) {
+  return zin(t.d) && zin(t.E) && zin(t.PL) && zin(t.PR) && zin(t.PU) && zin(t.PD) && zin(t.PG) && zin(t.dims) &&
+         zin(t.RL) && zin(t.RU) && zin(t.RA) && zin(t.gD) && zin(t.xsL) && zin(t.xoffL) && zin(t.keys) &&
+         zin(t.kshift);
+}
+template <typename T>
+inline bool zin1(const DevWeights<T>& w) {
+  return zin(w.w) && zin(w.bL) && zin(w.bU) && zin(w.bA);
+}
+template <typename T>
+inline bool zin1(const DevMPS<T>& m) {
+  return zin(m.A) && zin(m.dimA) && zin(m.lognorm);
+}
+inline bool zin1(const DevSearch& d) {
+  for (int k = 0; k < 2; ++k)
+    if (!(zin(d.states[k]) && zin(d.E[k]) && zin(d.logp[k]) && zin(d.rid[k]) && zin(d.dn[k]) && zin(d.dE[k]) &&
+          zin(d.dst[k])))
+      return false;
+  return zin(d.n_beam) && zin(d.logc) && zin(d.candE) && zin(d.win) && zin(d.wmin) && zin(d.wkey) &&
+         zin(d.key) && zin(d.rep) && zin(d.nxt) && zin(d.htab) && zin(d.hmin) && zin(d.hist) &&
+         zin(d.sel_state) && zin(d.sel_list) && zin(d.sel_count) && zin(d.pend) && zin(d.pend_n) &&
+         zin(d.done_ctr) && zin(d.near_ties) && zin(d.err) && zin(d.candidates) && zin(d.deg_cuts) &&
+         zin(d.dflow);
+}
+template <typename T>
+inline bool zin1(const DevBeamT<T>& b) {
+  return zin(b.lenv[0]) && zin(b.lenv[1]) && zin(b.R);
+}
+template <typename T>
+inline bool zin1(T* p) {
+  return zin(p);
+}
+inline bool zin1(int) { return true; }
+// true when every argument lies in instance 0's block; otherwise the group
+// is marked bad and the caller returns without launching
+template <typename... A>
+inline bool zok(const A&... a) {
+  const bool ok = !group().bad && (zin1(a) && ...);
+  if (!ok) group().bad = true;
+  return ok;
+}
+#define ZOK(...)                                        \
+  do {                                                  \
+    if (!::spg::zok(__VA_ARGS__)) return cudaErrorInvalidValue; \
+  } while (0)
+// Device copies and fills inside a solve, once per instance of the group.
+cudaError_t zcopy(void* dst, const void* src, size_t bytes, cudaStream_t st);
+cudaError_t zfill(void* dst, int byte, size_t bytes, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row,

@@ -53,11 +53,18 @@ __device__ __forceinline__ long long xval(const DevTables& tb, int s, int id, in
 
 template <typename T>
 __global__ void k_xgemm(DevTables tb, int s, int n2, int M, int N, int K, const T* __restrict__ A, XOff oa, int sAi,
-                        int sAk, const T* __restrict__ B, XOff ob, int sBk, int sBj, T* __restrict__ C) {
+                        int sAk, const T* __restrict__ B, XOff ob, int sBk, int sBj, T* __restrict__ C, int nq,
+                        size_t zs) {
   constexpr int BM = 32, BN = 32, BK = 32;
   __shared__ T sA[BK][BM + 1];
   __shared__ T sB[BK][BN + 1];
-  const int q = blockIdx.z;
+  // grid.z: nq states of each instance of a lockstep group
+  const int q = blockIdx.z % nq;
+  const size_t zo = (size_t)(blockIdx.z / nq) * zs;
+  tb = zadd(tb, zo);
+  A = zadd(A, zo);
+  B = zadd(B, zo);
+  C = zadd(C, zo);
   const long long offA = oa.c1 * xval(tb, s, oa.id1, q, n2) + oa.c2 * xval(tb, s, oa.id2, q, n2);
   const long long offB = ob.c1 * xval(tb, s, ob.id1, q, n2) + ob.c2 * xval(tb, s, ob.id2, q, n2);
   const T* Aq = A + offA;
@@ -112,7 +119,10 @@ __global__ void k_xgemm(DevTables tb, int s, int n2, int M, int N, int K, const 
 //   mode 5: coef[r][x] = [PR x * Gout + g == r] bU[u][PU x] w(x)
 template <typename T>
 __global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, int K, int u, int g,
-                             T* __restrict__ coef) {
+                             T* __restrict__ coef, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  coef = zp(coef, zs);
   const int d = tb.d[s];
   const size_t so = (size_t)s * tb.dmax;
   const int* dm = tb.dims + s * DIMW;
@@ -138,7 +148,10 @@ __global__ void k_state_coef(DevTables tb, DevWeights<T> wt, int s, int mode, in
 
 // bLu[l][h] = bA[l / Gin][u] bL[l][h]: the left weights of one up index u.
 template <typename T>
-__global__ void k_left_weights_u(DevTables tb, DevWeights<T> wt, int s, int u, T* __restrict__ out) {
+__global__ void k_left_weights_u(DevTables tb, DevWeights<T> wt, int s, int u, T* __restrict__ out, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  out = zp(out, zs);
   const int* dm = tb.dims + s * DIMW;
   const int DL = dm[D_DL];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < DL * MAXP; e += gridDim.x * blockDim.x) {
@@ -148,14 +161,18 @@ __global__ void k_left_weights_u(DevTables tb, DevWeights<T> wt, int s, int u, T
 }
 
 template <typename T>
-__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, size_t n) {
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, size_t n, size_t zs) {
+  y = zp(y, zs);
+  x = zp(x, zs);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     y[e] += x[e];
 }
 
 // In-place scaling of buf[0..n) to max |.| = 1, log of the scale added to *logacc.
 template <typename T>
-__global__ void k_scale_max(T* buf, int n, double* logacc) {
+__global__ void __launch_bounds__(1024) k_scale_max(T* buf, int n, double* logacc, size_t zs) {
+  buf = zp(buf, zs);
+  logacc = zp(logacc, zs);
   __shared__ T red[32];
   T m = T(0);
   for (int i = threadIdx.x; i < n; i += blockDim.x) m = max(m, (T)fabs((double)buf[i]));
@@ -179,7 +196,10 @@ __global__ void k_scale_max(T* buf, int n, double* logacc) {
 //   mode 1: the chiL rows    (vector a  = entries (u, a') of row a)
 template <typename T>
 __global__ void k_site_vectors(const T* __restrict__ S, int p, int chiL, int chiR, int mode, int to_vectors,
-                               T* __restrict__ V, T* __restrict__ Sout) {
+                               T* __restrict__ V, T* __restrict__ Sout, size_t zs) {
+  S = zp(S, zs);
+  V = zp(V, zs);
+  Sout = zp(Sout, zs);
   const int n = p * chiL * chiR;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int ap = e % chiR, a = (e / chiR) % chiL, u = e / (chiR * chiL);
@@ -196,14 +216,20 @@ __global__ void k_site_vectors(const T* __restrict__ S, int p, int chiL, int chi
 }
 
 template <typename T>
-__global__ void k_set_unit_env(T* E) {
+__global__ void k_set_unit_env(T* E, size_t zs) {
+  E = zp(E, zs);
   if (threadIdx.x == 0 && blockIdx.x == 0) E[0] = T(1);
 }
 
 // lognorm[r] = lognorm[r+1] + log ||C|| + Rsum; site0 = C / ||C||
 template <typename T>
 __global__ void k_finish_centre(const T* __restrict__ C, int n, T* __restrict__ site0, const double* lognorm_in,
-                                const double* rsum, double* lognorm_out) {
+                                const double* rsum, double* lognorm_out, size_t zs) {
+  C = zp(C, zs);
+  site0 = zp(site0, zs);
+  lognorm_in = zp(lognorm_in, zs);
+  rsum = zp(rsum, zs);
+  lognorm_out = zp(lognorm_out, zs);
   __shared__ double red[32];
   double part = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) part += (double)C[i] * (double)C[i];
@@ -261,7 +287,10 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   double* junk = dscratch + 1;
   auto site_ptr = [&](int r, int j) { return mps.A + (size_t)(r * cols + j) * mps.site_stride; };
   auto dims = [&](int r, int j) { return dimA + ((size_t)r * cols + j) * 3; };
-  auto zero_env = [&](T* E) { return cudaMemsetAsync(E, 0, sizeof(T) * env, st); };
+  auto zero_env = [&](T* E) { return zfill(E, 0, sizeof(T) * env, st); };
+  // every pointer below lies in work, dscratch, the MPS or the tables
+  if (!zok(tb, wt, mps, work, work + sweep_work_elems<T>(cols, chi, tb.bmax) - 1, dscratch + 1))
+    return cudaErrorInvalidValue;
   cudaError_t err;
 #define SPG_TRY(x)                 \
   do {                             \
@@ -272,27 +301,27 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   // bond b).  Per site: tables' dims from the host copy.
   auto xgemm = [&](int s, int nq, int n2, int M, int N, int K, const T* A, XOff oa, int sAi, int sAk, const T* B,
                    XOff ob, int sBk, int sBj, T* C) {
-    dim3 grid((N + 31) / 32, (M + 31) / 32, nq);
+    dim3 grid((N + 31) / 32, (M + 31) / 32, nq * zn());
     count_launches("k_xgemm", st, 2.0 * nq * M * N * K);
-    k_xgemm<T><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C);
+    k_xgemm<T><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
   };
   auto coef = [&](int s, int mode, int K, int u = 0, int g = 0) {
     const int d = hd_states(s);
     count_launches("k_state_coef", st);
-    k_state_coef<T><<<nblk((size_t)K * d), 256, 0, st>>>(tb, wt, s, mode, K, u, g, Cf);
+    k_state_coef<T><<<dim3(nblk((size_t)K * d), 1, zn()), 256, 0, st>>>(tb, wt, s, mode, K, u, g, Cf, zs());
   };
   // king's graph: per up index u, the right-bond offset g = gD_up[u]
   auto g_of = [&](int s, int u) { return s >= cols ? (int)hgD[(size_t)(s - cols) * MAXP + u] : 0; };
   auto u_coupled = [&](int s) { return tb_dims_host(s, D_UCPL) != 0; };
   auto axpy = [&](T* y, const T* x, size_t n) {
     count_launches("k_axpy", st);
-    k_axpy<T><<<nblk(n), 256, 0, st>>>(y, x, n);
+    k_axpy<T><<<dim3(nblk(n), 1, zn()), 256, 0, st>>>(y, x, n, zs());
   };
   // Lp[h][a][b] = sum_l bA[l / Gin][u] bL[l][h] E[l][a][b]
   auto left_prime_u = [&](int s, const T* Lenv, int chiA, int chiB, int u) {
     const int DL = tb_dims_host(s, 0), NL = tb_dims_host(s, 4);
     count_launches("k_left_weights_u", st);
-    k_left_weights_u<T><<<nblk((size_t)DL * MAXP), 256, 0, st>>>(tb, wt, s, u, Bu);
+    k_left_weights_u<T><<<dim3(nblk((size_t)DL * MAXP), 1, zn()), 256, 0, st>>>(tb, wt, s, u, Bu, zs());
     gemm2<T>(true, false, NL, chiA * chiB, DL, Bu, MAXP, Lenv, chiA * chiB, Lp, chiA * chiB, st);
   };
   // Lp[h][a][b] = sum_l bL[l][h] E[l][a][b]
@@ -370,7 +399,7 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
         axpy(out, Ctmp, (size_t)DL * chiA * chiBl);
       }
       count_launches("k_scale_max", st);
-      k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, logacc);
+      k_scale_max<T><<<dim3(1, 1, zn()), 1024, 0, st>>>(out, (int)env, logacc, zs());
       return cudaGetLastError();
     }
     phi_prime(s, P, DU, chiA, chiAr);
@@ -382,7 +411,7 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     SPG_TRY(zero_env(out));
     gemm2<T>(false, false, DL, chiA * chiBl, d, Cf, d, G, chiA * chiBl, out, chiA * chiBl, st);
     count_launches("k_scale_max", st);
-    k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, logacc);
+    k_scale_max<T><<<dim3(1, 1, zn()), 1024, 0, st>>>(out, (int)env, logacc, zs());
     return cudaGetLastError();
   };
   auto env_left = [&](int j, const T* Lenv, T* out) -> cudaError_t {
@@ -409,7 +438,7 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
         axpy(out, Ctmp, (size_t)DR * chiAr * chiBr);
       }
       count_launches("k_scale_max", st);
-      k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, junk);
+      k_scale_max<T><<<dim3(1, 1, zn()), 1024, 0, st>>>(out, (int)env, junk, zs());
       return cudaGetLastError();
     }
     left_prime(s, Lenv, chiA, chiBl);
@@ -424,7 +453,7 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     SPG_TRY(zero_env(out));
     gemm2<T>(false, false, DR, chiAr * chiBr, d, Cf, d, G, chiAr * chiBr, out, chiAr * chiBr, st);
     count_launches("k_scale_max", st);
-    k_scale_max<T><<<1, 1024, 0, st>>>(out, (int)env, junk);
+    k_scale_max<T><<<dim3(1, 1, zn()), 1024, 0, st>>>(out, (int)env, junk, zs());
     return cudaGetLastError();
   };
 
@@ -432,47 +461,47 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
     // right environments of the current (right-orthonormal) phi
     SPG_TRY(zero_env(Rs + (size_t)(cols - 1) * env));
     count_launches("k_set_unit_env", st);
-    k_set_unit_env<T><<<1, 32, 0, st>>>(Rs + (size_t)(cols - 1) * env);
+    k_set_unit_env<T><<<dim3(1, 1, zn()), 32, 0, st>>>(Rs + (size_t)(cols - 1) * env, zs());
     for (int j = cols - 1; j >= 1; --j) SPG_TRY(env_right(j, Rs + (size_t)j * env, Rs + (size_t)(j - 1) * env, junk));
     // left to right
     SPG_TRY(zero_env(Lc));
     count_launches("k_set_unit_env", st);
-    k_set_unit_env<T><<<1, 32, 0, st>>>(Lc);
+    k_set_unit_env<T><<<dim3(1, 1, zn()), 32, 0, st>>>(Lc, zs());
     for (int j = 0; j < cols - 1; ++j) {
       SPG_TRY(local(j, Lc + (size_t)j * env, Rs + (size_t)j * env));
       const int* dP = dims(row, j);
       const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
       const int n = DU * chiA * chiAr;
       count_launches("k_site_vectors", st);
-      k_site_vectors<T><<<nblk(n), 256, 0, st>>>(C, DU, chiA, chiAr, 0, 1, Vv, nullptr);
+      k_site_vectors<T><<<dim3(nblk(n), 1, zn()), 256, 0, st>>>(C, DU, chiA, chiAr, 0, 1, Vv, nullptr, zs());
       cgs_rows(Vv, chiAr, DU * chiA, st);
       count_launches("k_site_vectors", st);
-      k_site_vectors<T><<<nblk(n), 256, 0, st>>>(nullptr, DU, chiA, chiAr, 0, 0, Vv, site_ptr(row, j));
+      k_site_vectors<T><<<dim3(nblk(n), 1, zn()), 256, 0, st>>>(nullptr, DU, chiA, chiAr, 0, 0, Vv, site_ptr(row, j), zs());
       SPG_TRY(env_left(j, Lc + (size_t)j * env, Lc + (size_t)(j + 1) * env));
     }
     // right to left
-    SPG_TRY(cudaMemsetAsync(rsum, 0, sizeof(double), st));
+    SPG_TRY(zfill(rsum, 0, sizeof(double), st));
     SPG_TRY(zero_env(Rcur));
     count_launches("k_set_unit_env", st);
-    k_set_unit_env<T><<<1, 32, 0, st>>>(Rcur);
+    k_set_unit_env<T><<<dim3(1, 1, zn()), 32, 0, st>>>(Rcur, zs());
     for (int j = cols - 1; j >= 1; --j) {
       SPG_TRY(local(j, Lc + (size_t)j * env, Rcur));
       const int* dP = dims(row, j);
       const int DU = dP[0], chiA = dP[1], chiAr = dP[2];
       const int n = DU * chiA * chiAr;
       count_launches("k_site_vectors", st);
-      k_site_vectors<T><<<nblk(n), 256, 0, st>>>(C, DU, chiA, chiAr, 1, 1, Vv, nullptr);
+      k_site_vectors<T><<<dim3(nblk(n), 1, zn()), 256, 0, st>>>(C, DU, chiA, chiAr, 1, 1, Vv, nullptr, zs());
       cgs_rows(Vv, chiA, DU * chiAr, st);
       count_launches("k_site_vectors", st);
-      k_site_vectors<T><<<nblk(n), 256, 0, st>>>(nullptr, DU, chiA, chiAr, 1, 0, Vv, site_ptr(row, j));
+      k_site_vectors<T><<<dim3(nblk(n), 1, zn()), 256, 0, st>>>(nullptr, DU, chiA, chiAr, 1, 0, Vv, site_ptr(row, j), zs());
       SPG_TRY(env_right(j, Rcur, Rtmp, rsum));
-      SPG_TRY(cudaMemcpyAsync(Rcur, Rtmp, sizeof(T) * env, cudaMemcpyDeviceToDevice, st));
+      SPG_TRY(zcopy(Rcur, Rtmp, sizeof(T) * env, st));
     }
     SPG_TRY(local(0, Lc, Rcur));
     const int* dP = dims(row, 0);
     count_launches("k_finish_centre", st);
-    k_finish_centre<T><<<1, 256, 0, st>>>(C, dP[0] * dP[1] * dP[2], site_ptr(row, 0), mps.lognorm + row + 1, rsum,
-                                          mps.lognorm + row);
+    k_finish_centre<T><<<dim3(1, 1, zn()), 256, 0, st>>>(C, dP[0] * dP[1] * dP[2], site_ptr(row, 0),
+                                                         mps.lognorm + row + 1, rsum, mps.lognorm + row, zs());
   }
 #undef SPG_TRY
   return cudaGetLastError();

@@ -77,11 +77,14 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+// Tile (c0, c1) of instance c2 (the outer dimension of the map: the
+// instances of a lockstep group, one in a single solve).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
       :
-      : "r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+      : "r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
 
@@ -105,7 +108,9 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_umma_tf32x3(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, int M, int N,
-                  int nkb, int nsplit, float* out, int ldo, size_t split_stride, int* err) {
+                  int nkb, int nsplit, float* out, int ldo, size_t split_stride, int* err, size_t zs) {
+  out = zp(out, zs);
+  err = zp(err, zs);
   constexpr uint32_t A_BYTES = UM * UKF * 4;
   constexpr uint32_t B_BYTES = BN * UKF * 4;
   constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -150,10 +155,11 @@ __global__ void __launch_bounds__(128, 1)
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
       const uint32_t st = tiles + s * STAGE_BYTES;
       const int kc = (kb0 + i) * UKF;
-      tma_load_2d(st, &tAh, kc, m0, fb);
-      tma_load_2d(st + A_BYTES, &tAl, kc, m0, fb);
-      tma_load_2d(st + 2 * A_BYTES, &tBh, kc, 0, fb);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tBl, kc, 0, fb);
+      const int z = (int)blockIdx.z;
+      tma_load_3d(st, &tAh, kc, m0, z, fb);
+      tma_load_3d(st + A_BYTES, &tAl, kc, m0, z, fb);
+      tma_load_3d(st + 2 * A_BYTES, &tBh, kc, 0, z, fb);
+      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tBl, kc, 0, z, fb);
       issued = i + 1;
     }
     // every issued load lands in this CTA's shared memory before it exits,
@@ -238,7 +244,10 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 
 // out rows r < rows, k < kp: value X[r * ldx + k] (k < cols), else 0.
 __global__ void k_split(const float* __restrict__ X, int rows, int cols, int ldx, int kp, float* __restrict__ hi,
-                        float* __restrict__ lo) {
+                        float* __restrict__ lo, size_t zs) {
+  X = zp(X, zs);
+  hi = zp(hi, zs);
+  lo = zp(lo, zs);
   const size_t tot = (size_t)rows * kp;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / kp), k = (int)(e % kp);
@@ -252,7 +261,10 @@ __global__ void k_split(const float* __restrict__ X, int rows, int cols, int ldx
 // Transposed: out rows r < cols_in (columns of X), k < kp: X[k * ldx + r] for
 // k < rows_in, else 0; 32 x 32 tiles through shared memory.
 __global__ void k_split_t(const float* __restrict__ X, int rows_in, int cols_in, int ldx, int kp,
-                          float* __restrict__ hi, float* __restrict__ lo) {
+                          float* __restrict__ hi, float* __restrict__ lo, size_t zs) {
+  X = zp(X, zs);
+  hi = zp(hi, zs);
+  lo = zp(lo, zs);
   __shared__ float t[32][33];
   const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;  // k: rows of X, r: columns of X
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -272,7 +284,9 @@ __global__ void k_split_t(const float* __restrict__ X, int rows_in, int cols_in,
 }
 
 __global__ void k_sum_splits(const float* __restrict__ part, int nsplit, size_t stride, int n, int ldo, int rows,
-                             float* __restrict__ out) {
+                             float* __restrict__ out, size_t zs) {
+  part = zp(part, zs);
+  out = zp(out, zs);
   const size_t tot = (size_t)n * rows;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / rows), r = (int)(e % rows);
@@ -301,15 +315,20 @@ EncodeTiled encode_fn() {
 }
 
 // K-major [rows x kp] FP32 matrix (kp a multiple of 32), box of 32 x box_rows
-// with 128-byte swizzle; rows past the end read as zeros.
+// with 128-byte swizzle; rows past the end read as zeros.  The outer
+// dimension counts the instances of a lockstep group (zs bytes apart; one
+// instance without a group).
 bool make_map(CUtensorMap* map, const float* base, int rows, int kp, int box_rows) {
   EncodeTiled fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kp * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)UKF, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+  const size_t mat = ((size_t)rows * kp * 4 + 15) / 16 * 16;
+  const size_t z = zn() > 1 ? zs() : mat;
+  if (z % 16 != 0 || z < mat) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)zn()};
+  const cuuint64_t strides[2] = {(cuuint64_t)kp * 4, (cuuint64_t)z};
+  const cuuint32_t box[3] = {(cuuint32_t)UKF, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -322,8 +341,9 @@ cudaError_t launch_bn(const CUtensorMap* m, int M, int N, int nkb, int nsplit, f
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_umma_tf32x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  dim3 grid((M + UM - 1) / UM, nsplit);
-  k_umma_tf32x3<BN><<<grid, 128, smem, st>>>(m[0], m[1], m[2], m[3], M, N, nkb, nsplit, out, ldo, sstride, err);
+  dim3 grid((M + UM - 1) / UM, nsplit, zn());
+  k_umma_tf32x3<BN><<<grid, 128, smem, st>>>(m[0], m[1], m[2], m[3], M, N, nkb, nsplit, out, ldo, sstride, err,
+                                             zs());
   return cudaGetLastError();
 }
 
@@ -360,11 +380,13 @@ TcGemm::TcGemm(float* work, size_t elems, const float* M, int m, int n, int* err
   part_ = Bl_ + (size_t)SMAX * std::max(mp_, np_);
   (void)elems;
   const size_t tot = (size_t)m * np_;
+  if (!zok(work, M, err, part_ + 16 * (size_t)SMAX * std::max(m, n) - 1)) return;
   count_launches("k_split", st);
-  k_split<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st>>>(M, m, n, n, np_, Mh_, Ml_);
+  k_split<<<dim3((int)std::min<size_t>((tot + 255) / 256, 8192), 1, zn()), 256, 0, st>>>(M, m, n, n, np_, Mh_, Ml_,
+                                                                                         zs());
   count_launches("k_split_t", st);
-  dim3 g((mp_ + 31) / 32, (n + 31) / 32);
-  k_split_t<<<g, dim3(32, 8), 0, st>>>(M, m, n, n, mp_, MTh_, MTl_);
+  dim3 g((mp_ + 31) / 32, (n + 31) / 32, zn());
+  k_split_t<<<g, dim3(32, 8), 0, st>>>(M, m, n, n, mp_, MTh_, MTl_, zs());
 }
 
 // out[j * ldo + i] = sum_k A[i][k] B[j][k]: the rows of out are the s
@@ -377,8 +399,10 @@ cudaError_t TcGemm::run(bool trans, const float* Bt, int s, float* out) {
   const float* Ah = trans ? MTh_ : Mh_;
   const float* Al = trans ? MTl_ : Ml_;
   const size_t tot = (size_t)s * kp;
+  ZOK(Bt, out);
   count_launches("k_split", st_);
-  k_split<<<(int)std::min<size_t>((tot + 255) / 256, 8192), 256, 0, st_>>>(Bt, s, K, K, kp, Bh_, Bl_);
+  k_split<<<dim3((int)std::min<size_t>((tot + 255) / 256, 8192), 1, zn()), 256, 0, st_>>>(Bt, s, K, K, kp, Bh_,
+                                                                                           Bl_, zs());
   CUtensorMap maps[4];
   if (!make_map(&maps[0], Ah, rowsA, kp, UM) || !make_map(&maps[1], Al, rowsA, kp, UM) ||
       !make_map(&maps[2], Bh_, s, kp, s) || !make_map(&maps[3], Bl_, s, kp, s))
@@ -406,13 +430,14 @@ cudaError_t TcGemm::run(bool trans, const float* Bt, int s, float* out) {
   if (e != cudaSuccess) return e;
   if (nsplit > 1) {
     count_launches("k_sum_splits", st_);
-    k_sum_splits<<<(int)std::min<size_t>((sstride + 255) / 256, 4096), 256, 0, st_>>>(part_, nsplit, sstride, s,
-                                                                                      rowsA, rowsA, out);
+    k_sum_splits<<<dim3((int)std::min<size_t>((sstride + 255) / 256, 4096), 1, zn()), 256, 0, st_>>>(
+        part_, nsplit, sstride, s, rowsA, rowsA, out, zs());
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wait_check(long limit, int* err, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;
   count_launches("k_wait_check", st);
   k_wait_check<<<1, 32, 0, st>>>(limit, err);
   return cudaGetLastError();

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(1024) k_sign_fix(TO* __restrict__ out, const i
 size_t mlp_infer_elems(const spg_mlp* m, int n) { return (size_t)n * (2 * m->n_hidden + m->n_out); }
 
 cudaError_t mlp_infer_bf16(const spg_mlp* m, const float* X, int n, float* work, float* Y, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;  // not part of a grouped solve
   const __nv_bfloat16* pb = static_cast<const __nv_bfloat16*>(m->pbf);
   const int I = m->n_in, H = m->n_hidden, O = m->n_out;
   float* H1 = work;
@@ -332,6 +333,7 @@ cudaError_t mlp_infer_bf16(const spg_mlp* m, const float* X, int n, float* work,
 
 template <typename T>
 cudaError_t launch_ws_scatter(const float* Y, int chi, int cols, DevMPS<T> mps, int row, cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;  // not part of a grouped solve
   count_launches("k_ws_scatter", st);
   const int64_t cnt = (int64_t)MAXP * chi * chi * cols;
   k_ws_scatter<T><<<nblocks(cnt), 256, 0, st>>>(Y, chi, cols, mps, row);
@@ -343,6 +345,7 @@ template cudaError_t launch_ws_scatter<double>(const float*, int, int, DevMPS<do
 template <typename T>
 cudaError_t launch_export_row(DevMPS<T> mps, int row, int cols, int chi, T* out, const int* dims_dev, int fix_signs,
                               cudaStream_t st) {
+  if (zn() != 1) return cudaErrorInvalidValue;  // not part of a grouped solve
   count_launches("k_export_row", st);
   const int64_t cnt = (int64_t)MAXP * chi * chi * cols;
   k_export_row<T, T><<<nblocks(cnt), 256, 0, st>>>(mps, row, cols, chi, out);

@@ -29,8 +29,8 @@ def test_params_defaults_and_struct_layout():
     p = spg.params()
     assert (p.beta, p.chi, p.beam, p.num_sweeps, p.precision, p.merge, p.svd_iters) == (1.0, 16, 256, 0, 0, 1, -1)
     assert ctypes.sizeof(b.spg_params) == 80
-    assert ctypes.sizeof(b.spg_info) == 80
-    assert (p.fp64_rows, p.check_fp64) == (-1, 0)
+    assert ctypes.sizeof(b.spg_info) == 88
+    assert (p.fp64_rows, p.check_fp64, p.group_max) == (-1, 0, 0)
     assert spg.lib.spg_version() == 100
     assert spg.lib.spg_params_default(None) == b.SPG_EINVAL
 
