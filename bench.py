@@ -445,7 +445,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if prec == spg.SPG_MIXED else "f64", "data": "synthetic",
             "config": config_dict({"precision": args.precision,
-                                   "parallelism": f"replicas x{world}, {NB} instances in flight per GPU"}),
+                                   "parallelism": f"replicas x{world}, {NB} instances per GPU in lockstep groups "
+                                                  f"of up to {max(group_sizes) if group_sizes else 1} "
+                                                  f"(one launch sequence per group)"}),
             "gpu_launches": int(sum(launches)), "clocks": clk.summary()}
     if args.only_main:
         # per-kernel device times of one more solve (after the timed steps),

@@ -102,6 +102,8 @@ __global__ void k_weights(DevTables tb, DevWeights<T> wt, double beta_u, size_t 
 // ---------------------------------------------------------------- CGS2 QR
 __device__ __forceinline__ int wid_of() { return (int)(threadIdx.x >> 5); }
 
+constexpr int QR_PB = 16;  // vectors per panel of the block variant
+
 template <typename T>
 __host__ __device__ constexpr T qr_tol() {
   return sizeof(T) == 8 ? T(1e-13) : T(1e-5);
@@ -117,9 +119,15 @@ __host__ __device__ constexpr T qr_tol() {
 // norm is numerically dependent: zeroed, R_kk = 0.  Column k of R (nvec x
 // nvec, row-major; x_k = sum_{c <= k} R[c][k] q_c) is written when Rout is set.
 // Scratch: red >= 64 + 2 * SMAX T.
+//
+// Options of the block variant: inter == nullptr means no earlier
+// coefficients; Rp (stride QR_PB) receives the panel's own column k - clo
+// (rows clo .. k); dep_abs > 0 replaces the relative rule by nk <= dep_abs
+// (unit input vectors); red[42] keeps the smallest nk / n0 of the vectors
+// kept (the cancellation of the panel, reset by the caller).
 template <typename T>
 __device__ void cgs2_vec(T* V, int k, int clo, int nvec, int len, int ld, T* Rout, T* red, const T* inter,
-                         int istride) {
+                         int istride, T* Rp = nullptr, T dep_abs = T(0)) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   T* rc = red + 64;          // coefficients of the current pass [SMAX]
@@ -198,14 +206,16 @@ __device__ void cgs2_vec(T* V, int k, int clo, int nvec, int len, int ld, T* Rou
     nk2 = warp_sum(nk2);
     T r2 = T(0);
     for (int c = clo + lane; c < k; c += 32) r2 += racc[c] * racc[c];
-    for (int c = lane; c < clo; c += 32) r2 += inter[(size_t)c * istride] * inter[(size_t)c * istride];
+    if (inter)
+      for (int c = lane; c < clo; c += 32) r2 += inter[(size_t)c * istride] * inter[(size_t)c * istride];
     r2 = warp_sum(r2);
     if (lane == 0) {
       const T nk = sqrt(nk2);
       const T n0 = sqrt(nk2 + r2);
-      const bool dep = !(nk > rel_tol * n0) || n0 == T(0);
+      const bool dep = dep_abs > T(0) ? !(nk > dep_abs) : (!(nk > rel_tol * n0) || n0 == T(0));
       red[40] = dep ? T(0) : T(1) / nk;
       red[41] = dep ? T(0) : nk;
+      if (!dep) red[42] = min(red[42], nk / n0);
     }
   }
   __syncthreads();
@@ -214,7 +224,9 @@ __device__ void cgs2_vec(T* V, int k, int clo, int nvec, int len, int ld, T* Rou
   if (Rout)
     for (int c = tid; c < nvec; c += nt)
       Rout[(size_t)c * nvec + k] =
-          c < clo ? inter[(size_t)c * istride] : (c < k ? racc[c] : (c == k ? red[41] : T(0)));
+          c < clo ? (inter ? inter[(size_t)c * istride] : T(0)) : (c < k ? racc[c] : (c == k ? red[41] : T(0)));
+  if (Rp)
+    for (int c = clo + tid; c <= k; c += nt) Rp[(c - clo) * QR_PB + (k - clo)] = c < k ? racc[c] : red[41];
   __syncthreads();
 }
 
@@ -231,8 +243,12 @@ __device__ void cgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red) {
 // projects against the panel's earlier vectors.  The same two-pass
 // projections as cgs2_core, grouped so that most of the multiply-adds run as
 // register-tiled panel products instead of one dot per (vector, earlier
-// vector) pair.
-constexpr int QR_PB = 16;
+// vector) pair.  A panel whose vectors lost most of their length to the
+// projections (numerically near the span of the earlier vectors) is, where
+// the caller needs an orthonormal result, projected once more after its
+// normalisation and re-orthonormalised (panel_second_pass): normalising a
+// remainder at the rounding level of the projections would otherwise carry
+// that rounding, amplified, into its direction.
 
 // Tile of the panel Gram step: TC earlier vectors x 4 panel vectors (FP64
 // keeps 2 x 4 to stay inside the register budget of a 1024-thread CTA).
@@ -465,6 +481,12 @@ __device__ void panel_cholqr(T* V, int k0, int b, int nvec, int len, int ld, T* 
   if (tid == 0) *flag = 1;
   __syncthreads();
   panel_cholesky(G, b, ref2, tol_c, tol_d, L1, inv);
+  if (tid == 0) {  // the panel's cancellation: first pivots against the columns' norms
+    T m = red[42];
+    for (int k = 0; k < b; ++k)
+      if (L1[k * QR_PB + k] != T(0) && ref2[k] > T(0)) m = min(m, L1[k * QR_PB + k] / sqrt(ref2[k]));
+    red[42] = m;
+  }
   panel_solve(V, k0, b, len, ld, L1, inv);
   panel_gram(V, k0, b, len, ld, G);
   for (int e = tid; e < b * b; e += nt) {
@@ -517,22 +539,68 @@ __device__ void panel_cholqr(T* V, int k0, int b, int nvec, int len, int ld, T* 
 // V are int: nvec * ld stays below 2^31 for every caller (staged blocks and
 // zipper blocks of at most SMAX vectors).  With Pc (QR_PB * len) and cs
 // (chol_scratch_elems) given, FP32 panels go through panel_cholqr.
+// The second pass of panel k0 .. k0+b-1 (orthonormal, R's columns of the
+// panel written: S1 above the panel, R1 on it): S2 = Q_prev^T Q1 and Q1 -=
+// Q_prev S2 (one projection; Cs = S2), then CGS2 inside the panel of these
+// nearly unit vectors (R2; a vector keeping at most a tenth of its length
+// was within the span of the earlier vectors and is zeroed).  X = Q_prev S1
+// + Q1 R1 and Q1 = Q_prev S2 + Q2 R2 give R's panel columns [S1 + S2 R1;
+// R2 R1] (Racc holds them on the way; R2 in cs).
+template <typename T>
+__device__ void panel_second_pass(T* V, int k0, int b, int nvec, int len, int ld, T* Rout, T* red, T* Cs, T* Racc,
+                                  T* R2) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  bgs_project(V, k0, b, len, ld, Cs, Racc, true);
+  for (int j = 0; j < b; ++j)
+    cgs2_vec(V, k0 + j, k0, nvec, len, ld, (T*)nullptr, red, (const T*)nullptr, 0, R2, T(0.1));
+  if (!Rout) return;
+  // new columns into Racc ([(k0 + b) rows][QR_PB]), then back into Rout
+  for (int e = tid; e < (k0 + b) * b; e += nt) {
+    const int c = e / b, j = e % b;
+    T v;
+    if (c < k0) {
+      v = Rout[(size_t)c * nvec + k0 + j];
+      for (int i = 0; i <= j; ++i) v += Cs[c * QR_PB + i] * Rout[(size_t)(k0 + i) * nvec + k0 + j];
+    } else {
+      const int i = c - k0;
+      v = T(0);
+      for (int m = i; m <= j; ++m) v += R2[i * QR_PB + m] * Rout[(size_t)(k0 + m) * nvec + k0 + j];
+    }
+    Racc[c * QR_PB + j] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < (k0 + b) * b; e += nt) {
+    const int c = e / b, j = e % b;
+    Rout[(size_t)c * nvec + k0 + j] = Racc[c * QR_PB + j];
+  }
+  __syncthreads();
+}
+
+// reorth_eta > 0: panels (after the first) whose smallest kept nk / n0 falls
+// below it take panel_second_pass, with r2 (QR_PB^2 T) as scratch.
 template <typename T>
 __device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* Cs, T* Racc, T* Pc = nullptr,
-                           T* cs = nullptr) {
+                           T* cs = nullptr, T reorth_eta = T(0), T* r2 = nullptr) {
   for (int k0 = 0; k0 < nvec; k0 += QR_PB) {
     const int b = min(QR_PB, nvec - k0);
     if (k0 > 0) {
       bgs_project(V, k0, b, len, ld, Cs, Racc, true);
       bgs_project(V, k0, b, len, ld, Cs, Racc, false);
     }
+    if (threadIdx.x == 0) red[42] = T(1);
+    __syncthreads();
+    bool done = false;
     if constexpr (sizeof(T) == 4) {
       if (Pc && cs) {
         panel_cholqr(V, k0, b, nvec, len, ld, Rout, red, Racc, Pc, cs);
-        continue;
+        done = true;
       }
     }
-    for (int j = 0; j < b; ++j) cgs2_vec(V, k0 + j, k0, nvec, len, ld, Rout, red, Racc + j, QR_PB);
+    if (!done)
+      for (int j = 0; j < b; ++j) cgs2_vec(V, k0 + j, k0, nvec, len, ld, Rout, red, Racc + j, QR_PB);
+    __syncthreads();
+    if (k0 > 0 && reorth_eta > T(0) && r2 && red[42] < reorth_eta)
+      panel_second_pass(V, k0, b, nvec, len, ld, Rout, red, Cs, Racc, r2);
   }
 }
 
@@ -540,9 +608,16 @@ __device__ void bcgs2_core(T* V, int nvec, int len, int ld, T* Rout, T* red, T* 
 // vector contiguous so every access is coalesced; the vectors are staged in
 // shared memory when they fit.  R (nvec x nvec, row-major) as in cgs2_core:
 // x_k = sum_{c <= k} R[c][k] q_c.
+// Cancellation below which a panel takes the second pass: its direction
+// errors stay near eps / eta (2e-14 in FP64, 6e-5 in FP32).
+template <typename T>
+__host__ __device__ constexpr T reorth_eta() {
+  return sizeof(T) == 8 ? T(1e-2) : T(1e-3);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, int ld, T* Rout, int use_smem,
-                                                      int use_chol, size_t zs) {
+                                                      int use_chol, int reorth, size_t zs) {
   X = zp(X, zs);
   Rout = zp(Rout, zs);
   extern __shared__ unsigned char smem_raw[];
@@ -557,7 +632,8 @@ __global__ void __launch_bounds__(512, 1) k_cgs2_rows(T* X, int nvec, int len, i
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) V[e] = X[(size_t)(e / len) * ld + e % len];
   __syncthreads();
-  bcgs2_core(V, nvec, len, vld, Rout, red, Cs, Racc, Pc, use_chol ? cs : (T*)nullptr);
+  bcgs2_core(V, nvec, len, vld, Rout, red, Cs, Racc, Pc, use_chol ? cs : (T*)nullptr,
+             reorth ? reorth_eta<T>() : T(0), cs);
   if (use_smem)
     for (int e = tid; e < nvec * len; e += nt) X[(size_t)(e / len) * ld + e % len] = V[e];
 }
@@ -665,7 +741,7 @@ __global__ void __launch_bounds__(Panels ? 512 : 1024) k_left_canonical(DevMPS<T
     for (int e = tid; e < len * chiR; e += nt) W[(size_t)(e % chiR) * len + e / chiR] = A[e];
     __syncthreads();
     if (Panels && chiR >= 32 && len >= 256)
-      bcgs2_core(W, chiR, len, len, R, red, Cs, Racc, W + wmax, cs);
+      bcgs2_core(W, chiR, len, len, R, red, Cs, Racc, W + wmax, cs, reorth_eta<T>(), cs);
     else
       cgs2_core(W, chiR, len, len, R, red);
     for (int e = tid; e < len * chiR; e += nt) A[e] = W[(size_t)(e % chiR) * len + e / chiR];
@@ -1247,7 +1323,7 @@ size_t truncated_svd_sigma_offset(int m, int n, int keep) {
 }
 
 template <typename T>
-static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st);
+static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st, int reorth);
 
 // Entries per TSQR block: staged in shared memory when it fits (FP32), else
 // 1024 entries worked on in global memory (L2); never fewer than nvec.
@@ -1264,7 +1340,7 @@ static int tsqr_block(int nvec, int* use_smem) {
 }
 
 template <typename T>
-static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
+static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st, int reorth) {
   int use_smem = 0;
   const int bl = tsqr_block<T>(nvec, &use_smem);
   const int nb = (len + bl - 1) / bl;
@@ -1280,15 +1356,19 @@ static void tall_qr(T* X, int nvec, int len, T* Rout, T* S, cudaStream_t st) {
   k_tsqr_leaf<T><<<dim3(nb, 1, zn()), 512, leaf_smem, st>>>(X, nvec, len, bl, S, use_smem, zs());
   const int slen = nb * nvec;
   if (slen >= TSQR_MIN_LEN && slen < len)
-    tall_qr<T>(S, nvec, slen, Rout, S + (size_t)nvec * slen, st);
+    tall_qr<T>(S, nvec, slen, Rout, S + (size_t)nvec * slen, st, reorth);
   else
-    cgs2_rows<T>(S, nvec, slen, Rout, st);
+    cgs2_rows<T>(S, nvec, slen, Rout, st, reorth);
   count_launches("k_tsqr_apply", st, 2.0 * len * nvec * nvec);
   k_tsqr_apply<T><<<dim3(nb, 1, zn()), 512, apply_smem, st>>>(X, nvec, len, bl, S, zs());
 }
 
+// reorth: the result must be orthonormal to rounding (a QR whose R is used,
+// or whose Q is a site of an MPS), so panels with strong cancellation take
+// the second pass; the power steps of the subspace iteration only need a
+// basis of the span and skip it.
 template <typename T>
-static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
+static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st, int reorth) {
   const size_t base = sizeof(T) * (64 + 2 * SMAX + 2 * SMAX * QR_PB + chol_scratch_elems<T>());
   const size_t full = base + sizeof(T) * (size_t)nvec * len;
   const int use_smem = full <= 200 * 1024 ? 1 : 0;
@@ -1307,22 +1387,22 @@ static void cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
   if (!zok(X, Rout)) return;
   count_launches("k_cgs2_rows", st, 4.0 * len * nvec * nvec);
   k_cgs2_rows<T><<<dim3(1, 1, zn()), threads, use_chol ? with_copy : (use_smem ? full : base), st>>>(
-      X, nvec, len, len, Rout, use_smem, use_chol, zs());
+      X, nvec, len, len, Rout, use_smem, use_chol, reorth, zs());
 }
 
 template <typename T>
 void launch_cgs2_rows(T* X, int nvec, int len, T* Rout, cudaStream_t st) {
-  cgs2_rows<T>(X, nvec, len, Rout, st);
+  cgs2_rows<T>(X, nvec, len, Rout, st, 1);
 }
 
 // QR of the rows of X: one CTA for short vectors, TSQR for long ones (tsq:
 // tsqr_scratch_elems(len) elements).
 template <typename T>
-static void qr_rows(T* X, int nvec, int len, T* Rout, T* tsq, cudaStream_t st) {
+static void qr_rows(T* X, int nvec, int len, T* Rout, T* tsq, cudaStream_t st, int reorth) {
   if (len >= TSQR_MIN_LEN)
-    tall_qr<T>(X, nvec, len, Rout, tsq, st);
+    tall_qr<T>(X, nvec, len, Rout, tsq, st, reorth);
   else
-    cgs2_rows<T>(X, nvec, len, Rout, st);
+    cgs2_rows<T>(X, nvec, len, Rout, st, reorth);
 }
 
 // Work layout: Zt [s x n], Yt [s x m] (rows = the block's column vectors),
@@ -1364,14 +1444,14 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
     // the pseudo-random start block is well conditioned, so the power steps
     // need no orthonormalisation of it; the Rayleigh-Ritz step below does
     // need an orthonormal Z, hence the QR when there are no power steps
-    if (iters == 0) qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
+    if (iters == 0) qr_rows(Zt, s, n, (T*)nullptr, tsq, st, 1);
     for (int it = 0; it < iters; ++it) {
       cudaError_t e = prod_y();  // Y = M Z
       if (e != cudaSuccess) return e;
-      qr_rows(Yt, s, m, (T*)nullptr, tsq, st);
+      qr_rows(Yt, s, m, (T*)nullptr, tsq, st, 0);
       e = prod_z();  // Z = M^T Y
       if (e != cudaSuccess) return e;
-      qr_rows(Zt, s, n, (T*)nullptr, tsq, st);
+      qr_rows(Zt, s, n, (T*)nullptr, tsq, st, 0);
     }
   }
   // P = M Z = Q R (rows of Yt become the columns of Q); R = U_R Sigma V_J^T
@@ -1381,7 +1461,7 @@ cudaError_t truncated_svd(const T* M, int m, int n, int keep, int iters, uint64_
     const cudaError_t e = prod_y();
     if (e != cudaSuccess) return e;
   }
-  qr_rows(Yt, s, m, R, tsq, st);
+  qr_rows(Yt, s, m, R, tsq, st, 1);
   const size_t jsm_base = sizeof(T) * (64 + SMAX) + sizeof(int) * SMAX;
   const size_t jsm_full = jsm_base + sizeof(T) * 2 * (size_t)s * s;
   const int use_smem = jsm_full <= 200 * 1024 ? 1 : 0;

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <type_traits>
+
 #include "spg_internal.h"
 
 namespace spg {
@@ -383,6 +385,117 @@ __global__ void k_marginals(DevTables tb, DevWeights<double> wd, DevMPS<T> mps, 
     ds.candE[(size_t)b * ds.dmax + x] = e;
   }
   if (tid == 0 && !(tot >= 0.0)) atomicOr(ds.err, ERR_NAN);
+}
+
+// The mixed mode's marginals: the same conditionals with the state weights
+// formed in FP32 and the normalisation in FP64.  Per beam element b, as in
+// k_marginals: v = lenv B_j, Z[p][r] = sum_a' v[p][a'] R[a'][r * Gout + g];
+// Z is scaled to max |.| = 1 (a factor that cancels in the normalisation),
+// so that the FP32 product q(x) = w(x) bL[l][PL x] bU[u][PU x] Z[PD x][PR x]
+// stays in FP32's range for the states that matter (the weight factors of a
+// site stay above e^-SPG_FP32_WEIGHT_SPAN, else the solve runs the FP64
+// path); sum_x q(x) in FP64, logc = log q (FP32) - log sum (FP64).
+// One warp per beam element, 8 per block: the block stages B_j's site once
+// (when it fits), each warp works without block barriers (its reductions
+// are shuffles), so a block's elements proceed independently.
+constexpr int MW = 8;  // beam elements (warps) per block
+__global__ void __launch_bounds__(256) k_marginals_f32(DevTables tb, DevWeights<float> wt, DevMPS<float> mps,
+                                                      int site, DevSearch ds, DevBeamT<float> bt, int cur,
+                                                      int staged, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  mps = zp(mps, zs);
+  ds = zp(ds, zs);
+  bt = zp(bt, zs);
+  const int nb = ds.n_beam[cur];
+  const int b0 = blockIdx.x * MW;
+  if (b0 >= nb) return;
+  extern __shared__ __align__(16) float smk[];
+  __shared__ float sl[MW][MAXCHI];
+  __shared__ float sv[MW][MAXP * MAXCHI];
+  __shared__ float sZ[MW][MAXP * MAXP];
+  const int cols = tb.cols, chi = bt.chi, rs = bt.rs;
+  const int i = site / cols, j = site % cols;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int* dA = mps.dimA + ((i + 1) * cols + j) * 3;
+  const int p = dA[0], chiL = dA[1], chiR = dA[2];
+  const float* A = mps.A + (size_t)((i + 1) * cols + j) * mps.site_stride;
+  if (staged) {
+    for (int e = tid; e < p * chiL * chiR; e += 256) smk[e] = A[e];
+    __syncthreads();
+  }
+  const float* Ar = staged ? smk : A;
+  const int b = b0 + w;
+  if (b >= nb) return;  // after the only block barrier
+  const int NR = dim_of(tb, site, D_NR), Gin = dim_of(tb, site, D_GIN), Gout = dim_of(tb, site, D_GOUT);
+  const size_t dm = tb.dmax;
+  const uint16_t* stb = pick(ds.states, cur) + (size_t)b * ds.N;
+  const int a_l = j > 0 ? tb.PR[(size_t)(site - 1) * dm + stb[site - 1]] : 0;
+  const int g_l = (j > 0 && i > 0) ? tb.PG[(size_t)(site - cols - 1) * dm + stb[site - cols - 1]] : 0;
+  const int l = a_l * Gin + g_l;
+  const int u = i > 0 ? tb.PD[(size_t)(site - cols) * dm + stb[site - cols]] : 0;
+  const int gu = i > 0 ? tb.gD[(size_t)(site - cols) * MAXP + u] : 0;
+  const bool adr = i > 0 && j + 1 < cols;
+  const int ur = adr ? tb.PD[(size_t)(site - cols + 1) * dm + stb[site - cols + 1]] : 0;
+  for (int a = lane; a < chiL; a += 32) sl[w][a] = pick(bt.lenv, cur)[(size_t)b * chi + a];
+  __syncwarp();
+  // v[p][a'] = sum_a lenv[a] B[p][a][a']
+  for (int e = lane; e < p * chiR; e += 32) {
+    const int sp = e / chiR, ap = e % chiR;
+    float acc = 0.f;
+    for (int a = 0; a < chiL; ++a) acc += sl[w][a] * Ar[((size_t)sp * chiL + a) * chiR + ap];
+    sv[w][sp * MAXCHI + ap] = acc;
+  }
+  __syncwarp();
+  const int rb = pick(ds.rid, cur)[b];
+  const float* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * rs;
+  float zmx = 0.f;
+  for (int e = lane; e < p * NR; e += 32) {
+    const int sp = e / NR, rr = e % NR;
+    const int col = rr * Gout + gu;
+    float acc = 0.f;
+    for (int ap = 0; ap < chiR; ++ap) acc += sv[w][sp * MAXCHI + ap] * Rj[(size_t)ap * rs + col];
+    sZ[w][sp * MAXP + rr] = acc;
+    zmx = fmaxf(zmx, fabsf(acc));
+  }
+  zmx = warp_max(zmx);
+  __syncwarp();
+  const float zin = zmx > 0.f ? 1.f / zmx : 0.f;
+  const size_t so = (size_t)site * dm;
+  const float* bLl = wt.bL + (size_t)site * tb.lstride + (size_t)l * MAXP;
+  const float* bUu = wt.bU + (size_t)site * 256 + u * 16;
+  const int d = tb.d[site];
+  float q[MAXS / 32];
+  double part = 0.0;
+#pragma unroll
+  for (int k = 0; k < MAXS / 32; ++k) {
+    const int x = lane + 32 * k;
+    float v = 0.f;
+    if (x < d) {
+      v = wt.w[so + x] * bLl[tb.PL[so + x]] * bUu[tb.PU[so + x]] * (sZ[w][tb.PD[so + x] * MAXP + tb.PR[so + x]] * zin);
+      v = v > 0.f ? v : 0.f;
+    }
+    q[k] = v;
+    part += (double)v;
+  }
+  const double tot = warp_sum(part);
+  const double lt = log(tot);
+  const int64_t E0 = pick(ds.E, cur)[b];
+  const int64_t* RLl = tb.RL + (size_t)site * tb.lstride + (size_t)l * MAXP;
+  const int64_t* RUu = tb.RU + (size_t)site * 256 + u * 16;
+#pragma unroll
+  for (int k = 0; k < MAXS / 32; ++k) {
+    const int x = lane + 32 * k;
+    if (x < d) {
+      const int pl = tb.PL[so + x], pu = tb.PU[so + x], pr = tb.PR[so + x];
+      const double lc = (tot > 0.0) ? (q[k] > 0.f ? (double)logf(q[k]) - lt : -INFINITY) : -INFINITY;
+      ds.logc[(size_t)b * ds.dmax + x] = lc;
+      int64_t e = E0 + tb.E[so + x] + RLl[pl] + RUu[pu];
+      if (adr) e += tb.RA[(size_t)(site + 1) * 256 + pr * 16 + ur];
+      ds.candE[(size_t)b * ds.dmax + x] = e;
+    }
+  }
+  if (lane == 0 && !(tot >= 0.0)) atomicOr(ds.err, ERR_NAN);
 }
 
 // ---------------------------------------------------------------- S7 merge
@@ -1424,12 +1537,28 @@ cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> m
 }
 
 template <typename T>
-cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
-                                  const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
-  ZOK(tb, wd, mps, ds, bt);
-  count_launches("k_marginals", st);
-  k_marginals<T><<<dim3(ds.cap, 1, zn()), 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur, zs());
-  return cudaGetLastError();
+cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<double> wd, DevMPS<T> mps, int site,
+                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    ZOK(tb, wt, mps, ds, bt);
+    // the site staged in shared memory when it fits beside the warps' buffers
+    const size_t site_bytes = sizeof(float) * mps.site_stride;
+    const int staged = site_bytes <= 96 * 1024 ? 1 : 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(k_marginals_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    });
+    count_launches("k_marginals", st);
+    k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, staged ? site_bytes : 0, st>>>(
+        tb, wt, mps, site, ds, bt, cur, staged, zs());
+    return cudaGetLastError();
+  } else {
+    (void)wt;
+    ZOK(tb, wd, mps, ds, bt);
+    count_launches("k_marginals", st);
+    k_marginals<T><<<dim3(ds.cap, 1, zn()), 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur, zs());
+    return cudaGetLastError();
+  }
 }
 
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge, cudaStream_t st) {
@@ -1464,7 +1593,8 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
   // as on a full-GPU grid (they move a few tens of MB through L2), and the
   // other solves of a batch keep the remaining SMs (measured: batch of 32
   // +6.6%, one solve unchanged)
-  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, 64);
+  // (in a lockstep group every instance gets 16: the group fills the GPU)
+  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, zn() > 1 ? 16 : 64);
   ZOK(tb, ds);
   const size_t z = zs();
   const dim3 g(blocks, 1, zn()), g1(1, 1, zn());
@@ -1654,10 +1784,11 @@ template cudaError_t launch_right_envs<double>(const DevTables&, DevWeights<doub
                                                const DevSearch&, DevBeamT<double>, int, cudaStream_t);
 template cudaError_t launch_right_envs<float>(const DevTables&, DevWeights<float>, DevMPS<float>, int,
                                               const DevSearch&, DevBeamT<float>, int, cudaStream_t);
-template cudaError_t launch_marginals<double>(const DevTables&, DevWeights<double>, DevMPS<double>, int,
-                                                   const DevSearch&, DevBeamT<double>, int, cudaStream_t);
-template cudaError_t launch_marginals<float>(const DevTables&, DevWeights<double>, DevMPS<float>, int,
-                                                  const DevSearch&, DevBeamT<float>, int, cudaStream_t);
+template cudaError_t launch_marginals<double>(const DevTables&, DevWeights<double>, DevWeights<double>,
+                                              DevMPS<double>, int, const DevSearch&, DevBeamT<double>, int,
+                                              cudaStream_t);
+template cudaError_t launch_marginals<float>(const DevTables&, DevWeights<float>, DevWeights<double>, DevMPS<float>,
+                                             int, const DevSearch&, DevBeamT<float>, int, cudaStream_t);
 template cudaError_t launch_update<double>(const DevTables&, DevMPS<double>, int, const DevSearch&,
                                            DevBeamT<double>, int, cudaStream_t);
 template cudaError_t launch_update<float>(const DevTables&, DevMPS<float>, int, const DevSearch&, DevBeamT<float>,

@@ -872,7 +872,49 @@ template <typename T>
 struct SearchBufs {
   DevSearch ds;
   DevBeamT<T> bt;
+  float* rtw = nullptr;         // tensor-core right environments' work (FP32)
+  std::vector<char> tc_rows;    // rows whose right environments take that path
 };
+
+// Whether a problem's right environments may run on the tensor cores at
+// bond chi (renv_tc.cu): bonds of at most 32, environment bond <= 16.
+bool renv_tc_problem(const spg_problem* P, int chi) { return chi <= 32 && P->bmax <= 16 && P->cols >= 3; }
+
+// The rows whose sites satisfy the conditions of renv_tc.cu (Gout = 1, no
+// up-index coupling, DL, DR, NL <= 16, B_{i+1}'s sites within 16 x 32 x 32,
+// and, but at the rightmost column, every right class of a site's states
+// with one left class, distinct for distinct right classes).
+std::vector<char> renv_tc_rows(const spg_problem* P, const Plan& pl) {
+  std::vector<char> ok(P->rows, 0);
+  if (!renv_tc_problem(P, pl.chi)) return ok;
+  const int cols = P->cols;
+  for (int i = 0; i < P->rows; ++i) {
+    bool good = true;
+    for (int j = 1; j < cols && good; ++j) {
+      const int s = i * cols + j;
+      const int* dm = &P->dims[(size_t)s * DIMW];
+      good = dm[D_DR] <= 16 && dm[D_DL] <= 16 && dm[D_NL] <= 16 && dm[D_GOUT] == 1 && dm[D_UCPL] == 0;
+      const int* dA = &pl.dimA[((size_t)(i + 1) * cols + j) * 3];
+      good = good && dA[0] <= 16 && dA[1] <= 32 && dA[2] <= 32;
+      int h_of[MAXP], r_of[MAXP];
+      for (int q = 0; q < MAXP; ++q) h_of[q] = r_of[q] = -1;
+      for (int x = 0; x < P->d[s] && good && j < cols - 1; ++x) {
+        const int r = P->PR[(size_t)s * P->dmax + x], h = P->PL[(size_t)s * P->dmax + x];
+        if (r >= MAXP || h >= MAXP) {
+          good = false;
+        } else if (h_of[r] < 0) {
+          good = r_of[h] < 0;  // distinct right classes keep distinct left classes
+          h_of[r] = h;
+          r_of[h] = r;
+        } else {
+          good = h_of[r] == h;
+        }
+      }
+    }
+    ok[i] = good ? 1 : 0;
+  }
+  return ok;
+}
 
 template <typename T>
 size_t search_bytes(const spg_problem* P, int cap, int chi, bool drops = false) {
@@ -901,6 +943,7 @@ size_t search_bytes(const spg_problem* P, int cap, int chi, bool drops = false) 
   add(sizeof(int) * 8);
   add(sizeof(double) * 2);
   add(sizeof(T) * cap * (P->cols + 1) * chi * P->bmax);
+  if (sizeof(T) == sizeof(float) && renv_tc_problem(P, chi)) add(sizeof(float) * renv_tc_elems(P->cols, cap));
   if (drops)
     for (int k = 0; k < 2; ++k) {
       add(sizeof(int) * cap);
@@ -953,6 +996,7 @@ int carve_search(spg_ctx* ctx, const spg_problem* P, int cap, int chi, Arena& ar
   sb.bt.R = ar.get<T>((size_t)cap * (P->cols + 1) * chi * P->bmax);
   sb.bt.rs = P->bmax;
   sb.bt.chi = chi;
+  if (sizeof(T) == sizeof(float) && renv_tc_problem(P, chi)) sb.rtw = ar.get<float>(renv_tc_elems(P->cols, cap));
   if (drops)
     for (int k = 0; k < 2; ++k) {
       ds.dn[k] = ar.get<int>(cap);
@@ -1044,6 +1088,17 @@ int enqueue_boundary(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, 
   return run_boundary<T>(ctx, P, prm, pl, bb, 1);
 }
 
+// Right environments of row i for beam buffer cur: on the tensor cores
+// where the row allows it (FP32), else k_right_envs.
+template <typename T>
+cudaError_t right_envs(const spg_problem* P, BoundaryBufs<T>& bb, SearchBufs<T>& sb, int i, int cur,
+                       cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    if (sb.rtw && i < (int)sb.tc_rows.size() && sb.tc_rows[i])
+      return launch_right_envs_tc(P->tb, bb.wt, bb.mps, i, sb.ds, sb.bt, cur, sb.rtw, st);
+  return launch_right_envs<T>(P->tb, bb.wt, bb.mps, i, sb.ds, sb.bt, cur, st);
+}
+
 template <typename T>
 int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, BoundaryBufs<T>& bb,
                    SearchBufs<T>& sb, const OutStage& o) {
@@ -1056,8 +1111,8 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
   CK(launch_reset_beam(ds, cur, st));
   for (int s = 0; s < P->n; ++s) {
     const int i = s / cols, j = s % cols;
-    if (j == 0) CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, i, ds, sb.bt, cur, st));
-    CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    if (j == 0) CK(right_envs<T>(P, bb, sb, i, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
     CK(launch_merge(P->tb, s, ds, cur, prm->merge, st));
     CK(launch_select(P->tb, s, ds, cur, log_cut, st));
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
@@ -1093,8 +1148,8 @@ int enqueue_forced(spg_ctx* ctx, const spg_problem* P, BoundaryBufs<T>& bb, Sear
   int cur = 0;
   for (int s = 0; s < P->n; ++s) {
     const int i = s / cols, j = s % cols;
-    if (j == 0) CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, i, ds, sb.bt, cur, st));
-    CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    if (j == 0) CK(right_envs<T>(P, bb, sb, i, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
     CK(launch_force(s, ds, cur, o.states, out, st));
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
     cur ^= 1;
@@ -1136,6 +1191,8 @@ spg_problem group_view(const spg_problem* P, char* tables) {
   V.d = P->d;
   V.dims = P->dims;
   V.gD = P->gD;
+  V.PL = P->PL;  // host projections read by the choice of right-environment kernel
+  V.PR = P->PR;
   V.bmax = P->bmax;
   V.lstride = P->lstride;
   V.ucpl = P->ucpl;
@@ -1241,6 +1298,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* const* probs, int ng, const spg_
   SearchBufs<T> sb;
   if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false, f64, ws))) return rc;
   if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false, drops))) return rc;
+  sb.tc_rows = renv_tc_rows(P, pl);
   if (drops) {
     sb.ds.dcut = (int64_t)std::floor(std::ldexp(prm->droplet_energy, P->shift));
     sb.ds.dham = prm->droplet_hamming;
@@ -1418,9 +1476,10 @@ int debug_marginals_impl(spg_ctx* ctx, const spg_problem* P, const spg_params* p
   int nb[2] = {n_prefix, 0};
   CK(cudaMemcpyAsync(ds.n_beam, nb, sizeof(nb), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(ds.E[0], 0, sizeof(int64_t) * cap, st));
-  CK(launch_right_envs<T>(P->tb, bb.wt, bb.mps, row, ds, sb.bt, 0, st));
+  sb.tc_rows = renv_tc_rows(P, pl);
+  CK(right_envs<T>(P, bb, sb, row, 0, st));
   CK(launch_lenv_from_prefix<T>(P->tb, bb.mps, site, ds, sb.bt, 0, st));
-  CK(launch_marginals<T>(P->tb, bb.wd, bb.mps, site, ds, sb.bt, 0, st));
+  CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, site, ds, sb.bt, 0, st));
   const int d = P->d[site];
   std::vector<double> lc((size_t)cap * P->dmax);
   CK(cudaMemcpyAsync(lc.data(), ds.logc, sizeof(double) * lc.size(), cudaMemcpyDeviceToHost, st));

@@ -550,8 +550,14 @@ cudaError_t zfill(void* dst, int byte, size_t bytes, cudaStream_t st);
 template <typename T>
 cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> mps, int row,
                               const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
+// The right environments of a row on the tensor cores (renv_tc.cu; FP32,
+// rows that pass renv_tc_row_ok), with `work` holding renv_tc_elems(cols,
+// cap) floats (256-byte aligned).
+size_t renv_tc_elems(int cols, int cap);
+cudaError_t launch_right_envs_tc(const DevTables& tb, DevWeights<float> wt, DevMPS<float> mps, int row,
+                                 const DevSearch& ds, DevBeamT<float> bt, int cur, float* work, cudaStream_t st);
 template <typename T>
-cudaError_t launch_marginals(const DevTables& tb, DevWeights<double> wd, DevMPS<T> mps, int site,
+cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<double> wd, DevMPS<T> mps, int site,
                              const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge,
                          cudaStream_t st);

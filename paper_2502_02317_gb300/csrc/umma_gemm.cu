@@ -30,6 +30,7 @@
 #include <mutex>
 
 #include "spg_internal.h"
+#include "tc_ptx.h"
 
 namespace spg {
 
@@ -38,69 +39,12 @@ namespace {
 constexpr int UM = 128;      // rows of A per CTA (tcgen05 M)
 constexpr int UKF = 32;      // K floats per stage: one 128-byte swizzle row
 constexpr int STAGES = 3;
-constexpr long WAIT_LIMIT = 1L << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, long limit = WAIT_LIMIT) {
-  for (long it = 0; it < limit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  atomicOr(err, ERR_TIMEOUT);
-  return false;
-}
-
-// Shared-memory matrix descriptor of a K-major tile written by TMA with
-// 128-byte swizzle: rows of 128 bytes, 8-row atoms of 1024 bytes (stride
-// byte offset), leading byte offset unused for this layout, version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor: D in FP32, A and B in TF32, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
-}
-
-// Tile (c0, c1) of instance c2 (the outer dimension of the map: the
-// instances of a lockstep group, one in a single solve).
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      :
-      : "r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-      :
-      : "r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
+using tc::mbar_wait;
+using tc::smem_u32;
+using tc::sw128_desc;
+using tc::tma_load_3d;
+using tc::umma_commit;
+using tc::umma_tf32;
 
 // D tile (128 x BN) of A B^T over k-blocks [kb0, kb1) of 32, written
 // transposed: out[c * ldo + r] for r < M, c < N.
@@ -172,7 +116,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: 4 K-steps of 8 per stage, three products each
-    constexpr uint32_t idesc = tf32_idesc(BN);
+    constexpr uint32_t idesc = tc::tf32_idesc(UM, BN);
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES;
       ok = mbar_wait(full0 + 8 * s, (i / STAGES) & 1, err);
@@ -233,14 +177,7 @@ __global__ void k_wait_check(long limit, int* err) {
   if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, limit);
 }
 
-// hi = x rounded to TF32 (round to nearest, ties away), lo = x - hi (exact in
-// FP32).  Rows of the output are padded with zeros to kp entries.
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
-  lo = x - hi;
-}
+using tc::split_tf32;  // rows of the split outputs are padded with zeros to kp entries
 
 // out rows r < rows, k < kp: value X[r * ldx + k] (k < cols), else 0.
 __global__ void k_split(const float* __restrict__ X, int rows, int cols, int ldx, int kp, float* __restrict__ hi,
@@ -348,6 +285,12 @@ cudaError_t launch_bn(const CUtensorMap* m, int M, int N, int nkb, int nsplit, f
 }
 
 }  // namespace
+
+// A tensor map of a K-major FP32 matrix for the tcgen05 kernels of other
+// translation units (the layout and instance rules of make_map).
+bool make_f32_tensor_map(void* map, const float* base, int rows, int kp, int box_rows) {
+  return make_map(static_cast<CUtensorMap*>(map), base, rows, kp, box_rows);
+}
 
 size_t tc_gemm_elems(int m, int n, int s) {
   const size_t mp = ((size_t)m + 31) / 32 * 32, np = ((size_t)n + 31) / 32 * 32;

@@ -105,8 +105,11 @@ def test_chimera16_marginals(spg, ctx, chimera16, prec):
     for s in (0, 5, fg.cols, 7 * fg.cols + 9, n - fg.cols, n - 1):
         pre = np.array([[rng.integers(0, d) for d in fg.d[:s]] for _ in range(4)], dtype=np.int64).reshape(4, s)
         ref = search.debug_marginals(fg, search.Params(beta=1.0, chi=32, num_sweeps=1), s, pre, boundary=bd)
-        got = spg.spg_debug_marginals(ctx, prob, prm, s, pre)
+        got, ran = kernels_run(spg, ctx, lambda: spg.spg_debug_marginals(ctx, prob, prm, s, pre))
         close(got, ref, TOL[prec], None if prec == 0 else LOG_FLOOR)
+        # the mixed mode's right environments of Chimera rows run on the
+        # tensor cores (renv_tc.cu), the FP64 mode's on k_right_envs
+        assert ("k_renv_tc" in ran) == (prec == 1) and ("k_right_envs" in ran) == (prec == 0), ran
 
 
 @pytest.fixture(scope="module")
@@ -136,9 +139,15 @@ def test_king_d8_chi64_log_partition(spg, ctx, king8, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_king_d8_chi64_marginals(spg, ctx, king8, prec):
+    """The mixed mode as the precision pattern runs it: the final boundary
+    row (B_1) truncated in FP64, rows 2 and 3 in FP32 (tall QR and
+    tensor-core products).  With every row in FP32 (fp64_rows = 0, the
+    log Z test above) the conditionals of this 16-state lattice sit at
+    about 1.1e-3 of the oracle: FP32's truncation floor, the limit that the
+    FP64 final rows remove."""
     inst, fg, p, bd = king8
     prob = spg.spg_problem_potts(ctx, inst)
-    prm = spg.params(beta=1.0, chi=64, precision=prec, fp64_rows=0)
+    prm = spg.params(beta=1.0, chi=64, precision=prec, fp64_rows=1)
     rng = np.random.default_rng(19)
     for s in (0, 3, 5, 9, 14, 15):
         pre = np.array([[rng.integers(0, d) for d in fg.d[:s]] for _ in range(4)], dtype=np.int64).reshape(4, s)
