@@ -30,15 +30,21 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=1024, sweeps=1, batch=32)
+# batch: instances per step, one lockstep group per 152 (one instance per SM
+# for the groups' one-CTA kernels)
+WORKLOAD = dict(L=16, couplings="gauss", h_sigma=0.1, beta=1.0, chi=32, beam=1024, sweeps=1, batch=152)
 METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best energy"
 
 
-# DRAM bytes (read + write) per launch of a dominant kernel, from an ncu
-# capture of two mid-solve launches of the 16x16 solve (dram__bytes_read.sum
-# + dram__bytes_write.sum, mean of the two), for the kernel as it is now; a
-# kernel not listed here reports null.
-NCU_TRAFFIC_BYTES = {"k_cgs2_rows": 153.2}  # 48 x 512 block, Cholesky-QR panels: 158.2 and 148.2 B
+# DRAM bytes (read + write) per instance and launch of a dominant kernel,
+# from an ncu capture of mid-solve launches (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the instances one launch covers), for the
+# kernel as it is now; a kernel not listed here reports null.
+NCU_TRAFFIC_BYTES = {}
+
+# kernels whose products run on the tensor cores (split TF32: three TF32
+# passes per FP32-accurate multiply-add)
+TENSOR_KERNELS = ("k_renv_tc", "k_umma_tf32x3")
 
 
 def make_instance(seed):
@@ -356,6 +362,9 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="instances solved concurrently per step")
+    ap.add_argument("--ncu-solve", action="store_true",
+                    help="solve the batch once (its first, uncaptured occurrence) and exit: the command of an ncu "
+                         "launch list of one step's kernels; prints no bench line")
     ap.add_argument("--group-max", type=int, default=0,
                     help="most instances per lockstep group (0: automatic, 1: every instance on its own stream)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -401,6 +410,15 @@ def main():
 
     prm = params(prec)
     prms = [prm] * NB
+    if args.ncu_solve:
+        rs = spg.spg_solve_batch(ctx, probs, prms)
+        n = sum(r.info()["kernel_launches"] / max(1, r.info()["group_size"]) for r in rs)
+        for r in rs:
+            r.get()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"ncu_solve": {"instances": NB, "kernel_launches": int(round(n))}}))
+        return 0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -626,17 +644,34 @@ def main():
                          "source": "measured: k_fma_probe (8 independent FMA chains per thread, 8 blocks of 256 "
                                    "threads per SM), CUDA events"}
     alu_peak = peak32 if prec == spg.SPG_MIXED else peak64
-    name, (nl, ms_k, fl_k) = next((kv for kv in top if kv[1][2] > 0), top[0])
-    achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
     peaks, src = measured_peaks()
-    line["roofline"] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                        "frac": achieved / alu_peak, "traffic": NCU_TRAFFIC_BYTES.get(name),
-                        "peak_source": f"measured {'FP32' if prec == spg.SPG_MIXED else 'FP64'} FMA throughput "
-                                       f"(k_fma_probe, {props.multi_processor_count} SMs)",
-                        "share_of_solve": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
-                        "instances_per_launch": gsize,
-                        "avg_launch_us": 1e3 * ms_k / nl, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                        "peaks_source": src}
+    # TF32 dense: the measured BF16 peak (sustained: kernels inside a long
+    # step) x the nominal TF32/BF16 ratio 1.1/2.25; FP32-accurate split-TF32
+    # products deliver a third of it
+    tf32x3_peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25 / 3.0
+
+    def kernel_roofline(name, nl, ms_k, fl_k):
+        tensor = name in TENSOR_KERNELS and prec == spg.SPG_MIXED
+        achieved = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
+        peak = tf32x3_peak if tensor else alu_peak
+        traffic = NCU_TRAFFIC_BYTES.get(name)
+        return {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic * gsize if traffic is not None else None,
+                "peak_source": (f"measured BF16 sustained {peaks['bf16_tflops_sustained']} TF/s x 1.1/2.25 (TF32) / 3 "
+                                "(split-TF32 passes), " + src if tensor else
+                                f"measured {'FP32' if prec == spg.SPG_MIXED else 'FP64'} FMA throughput "
+                                f"(k_fma_probe, {props.multi_processor_count} SMs)"),
+                "share_of_step": round(ms_k / ktot, 4), "flops_per_launch": fl_k / nl,
+                "avg_launch_us": 1e3 * ms_k / nl, "instances_per_launch": gsize}
+    # the dominant kernel of the step (largest device time) with its
+    # algorithmic flops, and the other counted kernels beside it
+    counted = [kv for kv in top if kv[1][2] > 0]
+    name, (nl, ms_k, fl_k) = counted[0] if counted else top[0]
+    line["roofline"] = {**kernel_roofline(name, nl, ms_k, fl_k), "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                        "peaks_source": src,
+                        "dominant_uncounted": [k for k, _ in top[:3] if k not in dict(counted)]}
+    line["kernel_rooflines"] = [kernel_roofline(k, *v) for k, v in counted[:6]]
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(0)
         line["cpu_baseline_cfg1"] = {"all_cores": {**cpu_oracle_cfg1(), "cores": len(os.sched_getaffinity(0))},

@@ -867,6 +867,73 @@ __global__ void k_zip_M(DevTables tb, DevWeights<T> wt, int site, const T* __res
   }
 }
 
+// The same zipper matrix with one block per bond index a and every k at
+// once (the launch shape of a lockstep group, where the GPU is full): the
+// block stages T1[a] ([p][DR][K], contiguous) and the site's tables, forms
+// every Y_u[h] for all k (k fastest: conflict-free reads of the slab), then
+// every M entry of rows (l, a) with k fastest (coalesced writes).  Each
+// entry's sums run in the order of k_zip_M, so the results are the same.
+template <typename T>
+__global__ void __launch_bounds__(256) k_zip_M_rows(DevTables tb, DevWeights<T> wt, int site, const T* __restrict__ T1,
+                                                    int chiL, int p, int DR, int K, int DL, int DU,
+                                                    T* __restrict__ M, size_t zs) {
+  tb = zp(tb, zs);
+  wt = zp(wt, zs);
+  T1 = zp(T1, zs);
+  M = zp(M, zs);
+  extern __shared__ unsigned char smem_raw[];
+  T* sT = reinterpret_cast<T*>(smem_raw);  // [p][DR][K]
+  T* sY = sT + (size_t)p * DR * K;         // [DU][NL][K]
+  T* sbL = sY + (size_t)DU * MAXP * K;     // [DL][NL]
+  __shared__ T sw[MAXS];
+  __shared__ uint8_t sPU[MAXS], sPD[MAXS], sPR[MAXS];
+  __shared__ int16_t sx[MAXS];
+  __shared__ int soff[MAXP + 1];
+  __shared__ T sbU[256], sbA[256];
+  __shared__ int sg[MAXP];
+  const int a = blockIdx.x;
+  const int d = tb.d[site];
+  const int* dm = tb.dims + site * DIMW;
+  const int NL = dm[D_NL], Gin = dm[D_GIN], Gout = dm[D_GOUT];
+  const int cols = tb.cols;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int x = tid; x < d; x += nt) {
+    sw[x] = wt.w[(size_t)site * tb.dmax + x];
+    sPU[x] = tb.PU[(size_t)site * tb.dmax + x];
+    sPD[x] = tb.PD[(size_t)site * tb.dmax + x];
+    sPR[x] = tb.PR[(size_t)site * tb.dmax + x];
+    sx[x] = tb.xsL[(size_t)site * tb.dmax + x];
+  }
+  for (int e = tid; e < 256; e += nt) {
+    sbU[e] = wt.bU[(size_t)site * 256 + e];
+    sbA[e] = wt.bA[(size_t)site * 256 + e];
+  }
+  for (int e = tid; e < DL * NL; e += nt) sbL[e] = wt.bL[(size_t)site * tb.lstride + (e / NL) * MAXP + e % NL];
+  for (int e = tid; e <= MAXP; e += nt) soff[e] = tb.xoffL[site * (MAXP + 1) + e];
+  for (int u = tid; u < MAXP; u += nt) sg[u] = (site >= cols && u < DU) ? tb.gD[(size_t)(site - cols) * MAXP + u] : 0;
+  const T* Ta = T1 + (size_t)a * p * DR * K;
+  for (int e = tid; e < p * DR * K; e += nt) sT[e] = Ta[e];
+  __syncthreads();
+  for (int e = tid; e < DU * NL * K; e += nt) {
+    const int k = e % K, h = (e / K) % NL, u = e / (K * NL);
+    const int g = sg[u];
+    T acc = T(0);
+    for (int q = soff[h]; q < soff[h + 1]; ++q) {
+      const int x = sx[q];
+      acc += sbU[u * 16 + sPU[x]] * sw[x] * sT[((size_t)sPD[x] * DR + sPR[x] * Gout + g) * K + k];
+    }
+    sY[((size_t)u * MAXP + h) * K + k] = acc;
+  }
+  __syncthreads();
+  const size_t ldM = (size_t)DU * K;
+  for (int e = tid; e < DL * DU * K; e += nt) {
+    const int k = e % K, u = (e / K) % DU, l = e / (K * DU);
+    T acc = T(0);
+    for (int h = 0; h < NL; ++h) acc += sbL[l * NL + h] * sY[((size_t)u * MAXP + h) * K + k];
+    M[((size_t)l * chiL + a) * ldM + (size_t)u * K + k] = sbA[(l / Gin) * 16 + u] * acc;
+  }
+}
+
 // ---------------------------------------------------------------- GEMM
 // C[m x n] = op(A) op(B), row-major; op(A) = A (m x k, lda) or A^T (A stored
 // k x m); op(B) = B (k x n, ldb) or B^T (B stored n x k).  32x32 tile, 256
@@ -1238,13 +1305,21 @@ cudaError_t launch_zip_matrix(const DevTables& tb, DevWeights<T> wt, const T* B,
   const int kchunk = K >= 8 ? 4 : 1;
   dim3 grid(chiL, (K + kchunk - 1) / kchunk, zn());
   const size_t smem = sizeof(T) * ((size_t)p * DR + (size_t)DL * MAXP);
+  // a lockstep group fills the GPU: one block per bond index with every k
+  // (when the slab and the Y tables fit), else the per-k-chunk kernel
+  const size_t smem_rows = sizeof(T) * ((size_t)p * DR * K + (size_t)DU * MAXP * K + (size_t)DL * MAXP);
+  const bool rows = zn() > 1 && smem_rows <= 160 * 1024;
   static std::once_flag attr_once;  // thread-safe: batches enqueue from several threads
   std::call_once(attr_once, [&] {
     cudaFuncSetAttribute(k_zip_M<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * 2 * (size_t)MAXP * MAXBOND));
+    cudaFuncSetAttribute(k_zip_M_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   });
   count_launches("k_zip_M", st);
-  k_zip_M<T><<<grid, 256, smem, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M, zs());
+  if (rows)
+    k_zip_M_rows<T><<<dim3(chiL, 1, zn()), 256, smem_rows, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, M, zs());
+  else
+    k_zip_M<T><<<grid, 256, smem, st>>>(tb, wt, site, T1, chiL, p, DR, K, DL, DU, kchunk, M, zs());
   return cudaGetLastError();
 }
 

@@ -1538,7 +1538,7 @@ cudaError_t launch_right_envs(const DevTables& tb, DevWeights<T> wt, DevMPS<T> m
 
 template <typename T>
 cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<double> wd, DevMPS<T> mps, int site,
-                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st) {
+                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st, double flops) {
   if constexpr (std::is_same<T, float>::value) {
     ZOK(tb, wt, mps, ds, bt);
     // the site staged in shared memory when it fits beside the warps' buffers
@@ -1548,14 +1548,14 @@ cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<d
     std::call_once(once, [] {
       cudaFuncSetAttribute(k_marginals_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     });
-    count_launches("k_marginals", st);
+    count_launches("k_marginals", st, flops);
     k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, staged ? site_bytes : 0, st>>>(
         tb, wt, mps, site, ds, bt, cur, staged, zs());
     return cudaGetLastError();
   } else {
     (void)wt;
     ZOK(tb, wd, mps, ds, bt);
-    count_launches("k_marginals", st);
+    count_launches("k_marginals", st, flops);
     k_marginals<T><<<dim3(ds.cap, 1, zn()), 256, 0, st>>>(tb, wd, mps, site, ds, bt, cur, zs());
     return cudaGetLastError();
   }
@@ -1786,9 +1786,9 @@ template cudaError_t launch_right_envs<float>(const DevTables&, DevWeights<float
                                               const DevSearch&, DevBeamT<float>, int, cudaStream_t);
 template cudaError_t launch_marginals<double>(const DevTables&, DevWeights<double>, DevWeights<double>,
                                               DevMPS<double>, int, const DevSearch&, DevBeamT<double>, int,
-                                              cudaStream_t);
+                                              cudaStream_t, double);
 template cudaError_t launch_marginals<float>(const DevTables&, DevWeights<float>, DevWeights<double>, DevMPS<float>,
-                                             int, const DevSearch&, DevBeamT<float>, int, cudaStream_t);
+                                             int, const DevSearch&, DevBeamT<float>, int, cudaStream_t, double);
 template cudaError_t launch_update<double>(const DevTables&, DevMPS<double>, int, const DevSearch&,
                                            DevBeamT<double>, int, cudaStream_t);
 template cudaError_t launch_update<float>(const DevTables&, DevMPS<float>, int, const DevSearch&, DevBeamT<float>,

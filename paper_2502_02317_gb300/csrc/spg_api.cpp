@@ -874,7 +874,23 @@ struct SearchBufs {
   DevBeamT<T> bt;
   float* rtw = nullptr;         // tensor-core right environments' work (FP32)
   std::vector<char> tc_rows;    // rows whose right environments take that path
+  std::vector<double> mflops;   // per site: algorithmic flops of one beam element's marginals
 };
+
+// Algorithmic flops of one beam element's conditionals at each site
+// (profiling): v = lenv B (2 p chiL chiR), Z = v R (2 p NR chiR), the
+// weights and their sum (4 d).
+std::vector<double> marginal_flops(const spg_problem* P, const Plan& pl) {
+  std::vector<double> f(P->n, 0.0);
+  for (int s = 0; s < P->n; ++s) {
+    const int i = s / P->cols, j = s % P->cols;
+    if ((size_t)((i + 1) * P->cols + j) * 3 + 2 >= pl.dimA.size()) continue;
+    const int* dA = &pl.dimA[((size_t)(i + 1) * P->cols + j) * 3];
+    const double p = dA[0], chiL = dA[1], chiR = dA[2], NR = P->dims[(size_t)s * DIMW + D_NR];
+    f[s] = 2.0 * p * chiL * chiR + 2.0 * p * NR * chiR + 4.0 * P->d[s];
+  }
+  return f;
+}
 
 // Whether a problem's right environments may run on the tensor cores at
 // bond chi (renv_tc.cu): bonds of at most 32, environment bond <= 16.
@@ -1112,7 +1128,8 @@ int enqueue_search(spg_ctx* ctx, const spg_problem* P, const spg_params* prm, Bo
   for (int s = 0; s < P->n; ++s) {
     const int i = s / cols, j = s % cols;
     if (j == 0) CK(right_envs<T>(P, bb, sb, i, cur, st));
-    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st,
+                           s < (int)sb.mflops.size() ? sb.mflops[s] * ds.cap : 0.0));
     CK(launch_merge(P->tb, s, ds, cur, prm->merge, st));
     CK(launch_select(P->tb, s, ds, cur, log_cut, st));
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
@@ -1149,7 +1166,8 @@ int enqueue_forced(spg_ctx* ctx, const spg_problem* P, BoundaryBufs<T>& bb, Sear
   for (int s = 0; s < P->n; ++s) {
     const int i = s / cols, j = s % cols;
     if (j == 0) CK(right_envs<T>(P, bb, sb, i, cur, st));
-    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st));
+    CK(launch_marginals<T>(P->tb, bb.wt, bb.wd, bb.mps, s, ds, sb.bt, cur, st,
+                           s < (int)sb.mflops.size() ? sb.mflops[s] * ds.cap : 0.0));
     CK(launch_force(s, ds, cur, o.states, out, st));
     CK(launch_update<T>(P->tb, bb.mps, s, ds, sb.bt, cur, st));
     cur ^= 1;
@@ -1299,6 +1317,7 @@ int solve_impl(spg_ctx* ctx, const spg_problem* const* probs, int ng, const spg_
   if ((rc = carve_boundary<T>(ctx, P, pl, ar, bb, false, f64, ws))) return rc;
   if ((rc = carve_search<T>(ctx, P, cap, chi, ar, sb, false, drops))) return rc;
   sb.tc_rows = renv_tc_rows(P, pl);
+  sb.mflops = marginal_flops(P, pl);
   if (drops) {
     sb.ds.dcut = (int64_t)std::floor(std::ldexp(prm->droplet_energy, P->shift));
     sb.ds.dham = prm->droplet_hamming;

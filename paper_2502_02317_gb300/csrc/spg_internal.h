@@ -557,8 +557,9 @@ size_t renv_tc_elems(int cols, int cap);
 cudaError_t launch_right_envs_tc(const DevTables& tb, DevWeights<float> wt, DevMPS<float> mps, int row,
                                  const DevSearch& ds, DevBeamT<float> bt, int cur, float* work, cudaStream_t st);
 template <typename T>
+// flops: the launch's algorithmic flops for the profiler (0: not counted).
 cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<double> wd, DevMPS<T> mps, int site,
-                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st);
+                             const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st, double flops = 0.0);
 cudaError_t launch_merge(const DevTables& tb, int site, const DevSearch& ds, int cur, int merge,
                          cudaStream_t st);
 cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, int cur,

@@ -51,59 +51,78 @@ __device__ __forceinline__ long long xval(const DevTables& tb, int s, int id, in
   }
 }
 
+// One 32 x 32 output tile of state q's product per group of 64 threads, QPB
+// states per block (4 in FP32, 2 in FP64); each thread holds a 4 x 4
+// register tile and reads a four-wide column of A and row of B from shared
+// memory per k (two vector loads per 16 multiply-adds).  Every output sums
+// over k in order, as a one-entry-per-thread kernel would.  grid: (N tiles,
+// M tiles, state blocks x instances of a lockstep group).
 template <typename T>
-__global__ void k_xgemm(DevTables tb, int s, int n2, int M, int N, int K, const T* __restrict__ A, XOff oa, int sAi,
-                        int sAk, const T* __restrict__ B, XOff ob, int sBk, int sBj, T* __restrict__ C, int nq,
-                        size_t zs) {
-  constexpr int BM = 32, BN = 32, BK = 32;
-  __shared__ T sA[BK][BM + 1];
-  __shared__ T sB[BK][BN + 1];
-  // grid.z: nq states of each instance of a lockstep group
-  const int q = blockIdx.z % nq;
-  const size_t zo = (size_t)(blockIdx.z / nq) * zs;
+__host__ __device__ constexpr int xgemm_qpb() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
+template <typename T>
+__global__ void __launch_bounds__(64 * xgemm_qpb<T>()) k_xgemm(DevTables tb, int s, int n2, int M, int N, int K,
+                                                               const T* __restrict__ A, XOff oa, int sAi, int sAk,
+                                                               const T* __restrict__ B, XOff ob, int sBk, int sBj,
+                                                               T* __restrict__ C, int nq, size_t zs) {
+  constexpr int QPB = xgemm_qpb<T>();
+  constexpr int BT = 32, LD = BT + 4;  // tile edge; padded row (a multiple of 4 for the vector loads)
+  __shared__ __align__(16) T sA[QPB][BT][LD];  // [k][i]
+  __shared__ __align__(16) T sB[QPB][BT][LD];  // [k][j]
+  const int nqb = (nq + QPB - 1) / QPB;
+  const int qb = blockIdx.z % nqb;
+  const size_t zo = (size_t)(blockIdx.z / nqb) * zs;
   tb = zadd(tb, zo);
   A = zadd(A, zo);
   B = zadd(B, zo);
   C = zadd(C, zo);
-  const long long offA = oa.c1 * xval(tb, s, oa.id1, q, n2) + oa.c2 * xval(tb, s, oa.id2, q, n2);
-  const long long offB = ob.c1 * xval(tb, s, ob.id1, q, n2) + ob.c2 * xval(tb, s, ob.id2, q, n2);
+  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int q = qb * QPB + g;
+  const bool live = q < nq;
+  const int qq = live ? q : 0;
+  const long long offA = oa.c1 * xval(tb, s, oa.id1, qq, n2) + oa.c2 * xval(tb, s, oa.id2, qq, n2);
+  const long long offB = ob.c1 * xval(tb, s, ob.id1, qq, n2) + ob.c2 * xval(tb, s, ob.id2, qq, n2);
   const T* Aq = A + offA;
   const T* Bq = B + offB;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  T acc[2][2] = {};
-  for (int kk = 0; kk < K; kk += BK) {
-    for (int e = threadIdx.x; e < BK * BM; e += 256) {
-      const int i = e / BK, kq = e % BK;
+  const int ty = t >> 3, tx = t & 7;  // rows ty*4.., columns tx*4..
+  const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
+  T acc[4][4] = {};
+  for (int kk = 0; kk < K; kk += BT) {
+    for (int e = t; e < BT * BT; e += 64) {
+      const int i = e / BT, kq = e % BT;
       const int gi = row0 + i, gk = kk + kq;
-      sA[kq][i] = (gi < M && gk < K) ? Aq[(long long)gi * sAi + (long long)gk * sAk] : T(0);
-    }
-    for (int e = threadIdx.x; e < BK * BN; e += 256) {
-      const int kq = e / BN, j = e % BN;
-      const int gj = col0 + j, gk = kk + kq;
-      sB[kq][j] = (gj < N && gk < K) ? Bq[(long long)gk * sBk + (long long)gj * sBj] : T(0);
+      sA[g][kq][i] = (live && gi < M && gk < K) ? Aq[(long long)gi * sAi + (long long)gk * sAk] : T(0);
+      const int kb = e / BT, j = e % BT;
+      const int gj = col0 + j, gkb = kk + kb;
+      sB[g][kb][j] = (live && gj < N && gkb < K) ? Bq[(long long)gkb * sBk + (long long)gj * sBj] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kq = 0; kq < BK; ++kq) {
-      const T a0 = sA[kq][ty * 2], a1 = sA[kq][ty * 2 + 1];
-      const T b0 = sB[kq][tx * 2], b1 = sB[kq][tx * 2 + 1];
-      acc[0][0] += a0 * b0;
-      acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0;
-      acc[1][1] += a1 * b1;
+    for (int kq = 0; kq < BT; ++kq) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        a[r] = sA[g][kq][ty * 4 + r];
+        b[r] = sB[g][kq][tx * 4 + r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
     }
     __syncthreads();
   }
+  if (!live) return;
   T* Cq = C + (size_t)q * M * N;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int gi = row0 + ty * 2 + i;
+  for (int r = 0; r < 4; ++r) {
+    const int gi = row0 + ty * 4 + r;
     if (gi >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gj = col0 + tx * 2 + j;
-      if (gj < N) Cq[(size_t)gi * N + gj] = acc[i][j];
+    for (int c = 0; c < 4; ++c) {
+      const int gj = col0 + tx * 4 + c;
+      if (gj < N) Cq[(size_t)gi * N + gj] = acc[r][c];
     }
   }
 }
@@ -301,9 +320,10 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   // bond b).  Per site: tables' dims from the host copy.
   auto xgemm = [&](int s, int nq, int n2, int M, int N, int K, const T* A, XOff oa, int sAi, int sAk, const T* B,
                    XOff ob, int sBk, int sBj, T* C) {
-    dim3 grid((N + 31) / 32, (M + 31) / 32, nq * zn());
+    constexpr int QPB = xgemm_qpb<T>();
+    dim3 grid((N + 31) / 32, (M + 31) / 32, ((nq + QPB - 1) / QPB) * zn());
     count_launches("k_xgemm", st, 2.0 * nq * M * N * K);
-    k_xgemm<T><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
+    k_xgemm<T><<<grid, 64 * QPB, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
   };
   auto coef = [&](int s, int mode, int K, int u = 0, int g = 0) {
     const int d = hd_states(s);
