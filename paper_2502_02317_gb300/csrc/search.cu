@@ -410,9 +410,10 @@ __global__ void __launch_bounds__(256) k_marginals_f32(DevTables tb, DevWeights<
   const int nb = ds.n_beam[cur];
   const int b0 = blockIdx.x * MW;
   if (b0 >= nb) return;
+  // dynamic shared memory: the staged site (staged: p chiL chiR floats),
+  // then per warp v [MAXP][chi] and the environment columns [chi][MAXP]
   extern __shared__ __align__(16) float smk[];
   __shared__ float sl[MW][MAXCHI];
-  __shared__ float sv[MW][MAXP * MAXCHI];
   __shared__ float sZ[MW][MAXP * MAXP];
   const int cols = tb.cols, chi = bt.chi, rs = bt.rs;
   const int i = site / cols, j = site % cols;
@@ -424,7 +425,11 @@ __global__ void __launch_bounds__(256) k_marginals_f32(DevTables tb, DevWeights<
     for (int e = tid; e < p * chiL * chiR; e += 256) smk[e] = A[e];
     __syncthreads();
   }
+  // `staged` is the site's slot in floats (0: read from global memory)
   const float* Ar = staged ? smk : A;
+  const size_t wbuf = (size_t)MAXP * bt.chi;  // floats of one warp's v (and of its environment columns)
+  float* svw = smk + (staged ? (size_t)staged : 0) + (size_t)w * 2 * wbuf;
+  float* srw = svw + wbuf;
   const int b = b0 + w;
   if (b >= nb) return;  // after the only block barrier
   const int NR = dim_of(tb, site, D_NR), Gin = dim_of(tb, site, D_GIN), Gout = dim_of(tb, site, D_GOUT);
@@ -439,24 +444,56 @@ __global__ void __launch_bounds__(256) k_marginals_f32(DevTables tb, DevWeights<
   const int ur = adr ? tb.PD[(size_t)(site - cols + 1) * dm + stb[site - cols + 1]] : 0;
   for (int a = lane; a < chiL; a += 32) sl[w][a] = pick(bt.lenv, cur)[(size_t)b * chi + a];
   __syncwarp();
-  // v[p][a'] = sum_a lenv[a] B[p][a][a']
-  for (int e = lane; e < p * chiR; e += 32) {
-    const int sp = e / chiR, ap = e % chiR;
-    float acc = 0.f;
-    for (int a = 0; a < chiL; ++a) acc += sl[w][a] * Ar[((size_t)sp * chiL + a) * chiR + ap];
-    sv[w][sp * MAXCHI + ap] = acc;
-  }
-  __syncwarp();
+  // the environment columns the element reads, R[a'][r * Gout + g] for
+  // r < NR, staged (coalesced over r) while v is formed
   const int rb = pick(ds.rid, cur)[b];
   const float* Rj = bt.R + ((size_t)rb * (cols + 1) + (j + 1)) * chi * rs;
+  for (int e = lane; e < chiR * NR; e += 32) srw[e] = Rj[(size_t)(e / NR) * rs + (e % NR) * Gout + gu];
+  // v[p][a'] = sum_a lenv[a] B[p][a][a'], four outputs per lane at a time
+  // (each sums over a in order)
+  const int nv = p * chiR;
+  for (int e0 = lane; e0 < nv; e0 += 128) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* ap4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = min(e0 + 32 * t, nv - 1);
+      ap4[t] = Ar + (size_t)(e / chiR) * chiL * chiR + e % chiR;
+    }
+    for (int a = 0; a < chiL; ++a) {
+      const float la = sl[w][a];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] += la * ap4[t][(size_t)a * chiR];
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = e0 + 32 * t;
+      if (e < nv) svw[(e / chiR) * chi + e % chiR] = acc[t];
+    }
+  }
+  __syncwarp();
   float zmx = 0.f;
-  for (int e = lane; e < p * NR; e += 32) {
-    const int sp = e / NR, rr = e % NR;
-    const int col = rr * Gout + gu;
-    float acc = 0.f;
-    for (int ap = 0; ap < chiR; ++ap) acc += sv[w][sp * MAXCHI + ap] * Rj[(size_t)ap * rs + col];
-    sZ[w][sp * MAXP + rr] = acc;
-    zmx = fmaxf(zmx, fabsf(acc));
+  const int nz = p * NR;
+  for (int e0 = lane; e0 < nz; e0 += 128) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int sp4[4], rr4[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = min(e0 + 32 * t, nz - 1);
+      sp4[t] = e / NR;
+      rr4[t] = e % NR;
+    }
+    for (int ap = 0; ap < chiR; ++ap)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] += svw[sp4[t] * chi + ap] * srw[ap * NR + rr4[t]];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = e0 + 32 * t;
+      if (e < nz) {
+        sZ[w][sp4[t] * MAXP + rr4[t]] = acc[t];
+        zmx = fmaxf(zmx, fabsf(acc[t]));
+      }
+    }
   }
   zmx = warp_max(zmx);
   __syncwarp();
@@ -1542,15 +1579,17 @@ cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<d
   if constexpr (std::is_same<T, float>::value) {
     ZOK(tb, wt, mps, ds, bt);
     // the site staged in shared memory when it fits beside the warps' buffers
-    const size_t site_bytes = sizeof(float) * mps.site_stride;
-    const int staged = site_bytes <= 96 * 1024 ? 1 : 0;
+    const size_t site_floats = mps.site_stride;
+    const size_t warp_floats = (size_t)MW * 2 * MAXP * bt.chi;
+    const int staged = sizeof(float) * (site_floats + warp_floats) <= 160 * 1024 ? (int)site_floats : 0;
+    const size_t smem = sizeof(float) * ((size_t)staged + warp_floats);
     static std::once_flag once;
     std::call_once(once, [] {
-      cudaFuncSetAttribute(k_marginals_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      cudaFuncSetAttribute(k_marginals_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     count_launches("k_marginals", st, flops);
-    k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, staged ? site_bytes : 0, st>>>(
-        tb, wt, mps, site, ds, bt, cur, staged, zs());
+    k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, smem, st>>>(tb, wt, mps, site, ds, bt, cur,
+                                                                                  staged, zs());
     return cudaGetLastError();
   } else {
     (void)wt;
