@@ -938,20 +938,21 @@ __global__ void __launch_bounds__(256) k_zip_M_rows(DevTables tb, DevWeights<T> 
 // C[m x n] = op(A) op(B), row-major; op(A) = A (m x k, lda) or A^T (A stored
 // k x m); op(B) = B (k x n, ldb) or B^T (B stored n x k).  32x32 tile, 256
 // threads, 2x2 outputs per thread.
-template <typename T, bool TA, bool TB>
-__global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, const T* __restrict__ B,
-                       int ldb, T* __restrict__ C, int ldc, size_t zs) {
+template <typename T, bool TA, bool TB, int MT>
+__global__ void __launch_bounds__((32 / MT) * (32 / MT)) k_gemm(int m, int n, int k, const T* __restrict__ A, int lda,
+                                                                const T* __restrict__ B, int ldb, T* __restrict__ C,
+                                                                int ldc, size_t zs) {
   A = zp(A, zs);
   B = zp(B, zs);
   C = zp(C, zs);
-  constexpr int BM = 32, BN = 32, BK = 32;
+  constexpr int BM = 32, BN = 32, BK = 32, TPR = 32 / MT, NT = TPR * TPR;
   __shared__ T sA[BK][BM + 1];
   __shared__ T sB[BK][BN + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % TPR, ty = threadIdx.x / TPR;
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  T acc[2][2] = {};
+  T acc[MT][MT] = {};
   for (int kk = 0; kk < k; kk += BK) {
-    for (int e = threadIdx.x; e < BK * BM; e += 256) {
+    for (int e = threadIdx.x; e < BK * BM; e += NT) {
       int kq, i;
       if (TA) {  // contiguous along m
         kq = e / BM;
@@ -965,7 +966,7 @@ __global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, co
       if (gi < m && gk < k) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
       sA[kq][i] = v;
     }
-    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+    for (int e = threadIdx.x; e < BK * BN; e += NT) {
       int kq, j;
       if (TB) {  // contiguous along k
         j = e / BK;
@@ -982,22 +983,26 @@ __global__ void k_gemm(int m, int n, int k, const T* __restrict__ A, int lda, co
     __syncthreads();
 #pragma unroll 8
     for (int kq = 0; kq < BK; ++kq) {
-      const T a0 = sA[kq][ty * 2], a1 = sA[kq][ty * 2 + 1];
-      const T b0 = sB[kq][tx * 2], b1 = sB[kq][tx * 2 + 1];
-      acc[0][0] += a0 * b0;
-      acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0;
-      acc[1][1] += a1 * b1;
+      T a[MT], b[MT];
+#pragma unroll
+      for (int r = 0; r < MT; ++r) {
+        a[r] = sA[kq][ty * MT + r];
+        b[r] = sB[kq][tx * MT + r];
+      }
+#pragma unroll
+      for (int r = 0; r < MT; ++r)
+#pragma unroll
+        for (int c = 0; c < MT; ++c) acc[r][c] += a[r] * b[c];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int gi = row0 + ty * 2 + i;
+  for (int i = 0; i < MT; ++i) {
+    const int gi = row0 + ty * MT + i;
     if (gi >= m) continue;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gj = col0 + tx * 2 + j;
+    for (int j = 0; j < MT; ++j) {
+      const int gj = col0 + tx * MT + j;
       if (gj < n) C[(size_t)gi * ldc + gj] = acc[i][j];
     }
   }
@@ -1336,14 +1341,27 @@ cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int
   dim3 grid((n + 31) / 32, (m + 31) / 32, zn());
   count_launches("k_gemm", st, 2.0 * m * n * k);
   const size_t z = zs();
-  if (transA && transB)
-    k_gemm<T, true, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+  // a lockstep group fills the GPU: 4 x 4 outputs per thread (64 threads per
+  // tile, more multiply-adds per shared-memory read); alone, 2 x 2 on 256
+  // threads (shorter chains for the small, latency-bound products).  Each
+  // output sums over k in the same order either way.
+  if (zn() > 1) {
+    if (transA && transB)
+      k_gemm<T, true, true, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    else if (transA)
+      k_gemm<T, true, false, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    else if (transB)
+      k_gemm<T, false, true, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    else
+      k_gemm<T, false, false, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+  } else if (transA && transB)
+    k_gemm<T, true, true, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else if (transA)
-    k_gemm<T, true, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    k_gemm<T, true, false, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else if (transB)
-    k_gemm<T, false, true><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    k_gemm<T, false, true, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   else
-    k_gemm<T, false, false><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+    k_gemm<T, false, false, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
   return cudaGetLastError();
 }
 

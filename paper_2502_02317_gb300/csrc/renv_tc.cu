@@ -38,6 +38,7 @@
 // tensor memory and returns.
 #include <cuda.h>
 
+#include "spg.h"
 #include "spg_internal.h"
 #include "tc_ptx.h"
 
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ float sbA[256];
   __shared__ int s_hr[16];
   __shared__ int s_abort;
+  __shared__ uint8_t s_up[RT_B][SPG_MAX_COLS];  // PD class of the cluster above column j, per element
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full = tc::smem_u32(&bars[0]), done = tc::smem_u32(&bars[1]);
   const int cols = tb.cols, chi = bt.chi, rs = bt.rs;
@@ -202,12 +204,20 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  // the PD class of the fixed cluster above column j for the block's element g
-  auto up_class = [&](int g, int j) -> int {
-    if (row == 0 || g >= gn) return 0;
-    const int s_up = (row - 1) * cols + j;
-    return tb.PD[(size_t)s_up * tb.dmax + pick(ds.states, cur)[(size_t)(b0 + g) * ds.N + s_up]];
-  };
+  // the PD class of the fixed cluster above column j for the block's
+  // element g, for every column at once (the state and table loads of all
+  // of them in flight together)
+  for (int e = tid; e < RT_B * cols; e += 128) {
+    const int g = e / cols, j = e % cols;
+    int u = 0;
+    if (row > 0 && g < gn) {
+      const int s_up = (row - 1) * cols + j;
+      u = tb.PD[(size_t)s_up * tb.dmax + pick(ds.states, cur)[(size_t)(b0 + g) * ds.N + s_up]];
+    }
+    s_up[g][j] = (uint8_t)u;
+  }
+  __syncthreads();
+  auto up_class = [&](int g, int j) -> int { return s_up[g < RT_B ? g : 0][j]; };
   // R_j[a][l] = bA[l / Gin][u] sum_h bL[l][h] Y[h][a] from Ys: thread (bl2,
   // a0) of 16 per beam element takes a = a0 and a0 + 16 for every l (Ys
   // read along a, bL broadcast); scaled to max |.| = 1; written to R and,
@@ -341,10 +351,17 @@ __global__ void __launch_bounds__(128, 1)
     float acc[RT_A];
 #pragma unroll
     for (int a = 0; a < RT_A; ++a) acc[a] = 0.f;
-    for (int pd = 0; pd < p; ++pd) {
+    // the coefficients first: the accumulator loads below are ordered
+    // against every memory access
+    float cv[RT_PD];
+#pragma unroll
+    for (int pd = 0; pd < RT_PD; ++pd) cv[pd] = (valid && pd < p) ? cu[pd * 16] : 0.f;
+#pragma unroll
+    for (int pd = 0; pd < RT_PD; ++pd) {
+      if (pd >= p) break;
       float v[RT_A];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pd * RT_A), v);
-      const float c = valid ? cu[pd * 16] : 0.f;
+      const float c = cv[pd];
 #pragma unroll
       for (int a = 0; a < RT_A; ++a) acc[a] += c * v[a];
     }

@@ -89,11 +89,13 @@ __global__ void __launch_bounds__(64 * xgemm_qpb<T>()) k_xgemm(DevTables tb, int
   const int row0 = blockIdx.y * BT, col0 = blockIdx.x * BT;
   T acc[4][4] = {};
   for (int kk = 0; kk < K; kk += BT) {
+    // consecutive threads along the operand's unit-stride index (coalesced)
+    const bool a_k = sAk == 1, b_j = sBj == 1 || sBk != 1;
     for (int e = t; e < BT * BT; e += 64) {
-      const int i = e / BT, kq = e % BT;
+      const int i = a_k ? e / BT : e % BT, kq = a_k ? e % BT : e / BT;
       const int gi = row0 + i, gk = kk + kq;
       sA[g][kq][i] = (live && gi < M && gk < K) ? Aq[(long long)gi * sAi + (long long)gk * sAk] : T(0);
-      const int kb = e / BT, j = e % BT;
+      const int kb = b_j ? e / BT : e % BT, j = b_j ? e % BT : e / BT;
       const int gj = col0 + j, gkb = kk + kb;
       sB[g][kb][j] = (live && gj < N && gkb < K) ? Bq[(long long)gkb * sBk + (long long)gj * sBj] : T(0);
     }
