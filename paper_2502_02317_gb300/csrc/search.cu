@@ -1632,8 +1632,8 @@ cudaError_t launch_select(const DevTables& tb, int site, const DevSearch& ds, in
   // as on a full-GPU grid (they move a few tens of MB through L2), and the
   // other solves of a batch keep the remaining SMs (measured: batch of 32
   // +6.6%, one solve unchanged)
-  // (in a lockstep group every instance gets 16: the group fills the GPU)
-  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, zn() > 1 ? 16 : 64);
+  // (in a lockstep group every instance gets 8: the group fills the GPU)
+  const int blocks = (int)std::min<size_t>((tot + 1023) / 1024, zn() > 1 ? 8 : 64);
   ZOK(tb, ds);
   const size_t z = zs();
   const dim3 g(blocks, 1, zn()), g1(1, 1, zn());
