@@ -28,11 +28,12 @@
 // environments <= 16, B_{i+1}'s sites of at most 16 x 32 x 32, and the class
 // condition above on every column but the rightmost.
 //
-// One CTA of 4 warps per tile of 8 beam elements of one instance (grid.z:
+// One CTA of 8 warps per tile of 8 beam elements of one instance (grid.z:
 // the instances of a lockstep group) runs the row's columns right to left:
 // TMA loads the column's split site (prepared per row by k_renv_prep) and
 // the tile's split R_{j+1} (written by the same CTA in the previous column),
-// thread 0 issues the MMAs, every warp reads its 32 accumulator lanes.
+// thread 0 issues the MMAs, warps w and w + 4 read accumulator lane quarter
+// w & 3 (half of the state classes each).
 // Every mbarrier wait is bounded: on a timeout ERR_TIMEOUT is recorded, the
 // CTA waits (bounded) for its copies and products in flight, frees its
 // tensor memory and returns.
@@ -60,6 +61,7 @@ constexpr uint32_t B_HALF = 256 * RT_K * 4;     // 32 KB: one TMA box of 256 row
 constexpr uint32_t B_BYTES = 2 * B_HALF;        // 64 KB per TF32 part
 constexpr uint32_t TX_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr size_t RT_SMEM = 2 * (size_t)B_BYTES + 2 * (size_t)A_BYTES + 1024;
+constexpr int RT_T = 256;    // threads: warps w and w + 4 share accumulator lane quarter w
 
 // Per row and column j (1 .. cols-2) of the row: the split site B_j as a
 // K-major [512][32] matrix (row pd * 32 + a, column a'; zeros beyond the
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(256) k_renv_prep(DevTables tb, DevWeights<floa
 // The row's right environments for beam tile blockIdx.x of instance
 // blockIdx.z.  Asp: the tiles' split R_{j+1} ([tiles][128][32] per part),
 // Bh/Bl/Cu/hr from k_renv_prep.
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(RT_T, 1)
     k_renv_tc(const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
               const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl, DevTables tb,
               DevWeights<float> wt, DevMPS<float> mps, int row, DevSearch ds, DevBeamT<float> bt, int cur,
@@ -195,11 +197,11 @@ __global__ void __launch_bounds__(128, 1)
   for (int g = 0; g < gn; ++g) {
     const int b = b0 + g;
     float* Rb = bt.R + ((size_t)b * (cols + 1) + cols) * renv;
-    for (int e = tid; e < (int)renv; e += 128) Rb[e] = e == 0 ? 1.f : 0.f;
+    for (int e = tid; e < (int)renv; e += RT_T) Rb[e] = e == 0 ? 1.f : 0.f;
     if (tid == 0) pick(ds.rid, cur)[b] = b;
-    for (int a = tid; a < chi; a += 128) pick(bt.lenv, cur)[(size_t)b * chi + a] = a == 0 ? 1.f : 0.f;
+    for (int a = tid; a < chi; a += RT_T) pick(bt.lenv, cur)[(size_t)b * chi + a] = a == 0 ? 1.f : 0.f;
   }
-  for (int e = tid; e < RT_B * 16 * (RT_A + 1); e += 128) (&Ys[0][0][0])[e] = 0.f;
+  for (int e = tid; e < RT_B * 16 * (RT_A + 1); e += RT_T) (&Ys[0][0][0])[e] = 0.f;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(128, 1)
   // the PD class of the fixed cluster above column j for the block's
   // element g, for every column at once (the state and table loads of all
   // of them in flight together)
-  for (int e = tid; e < RT_B * cols; e += 128) {
+  for (int e = tid; e < RT_B * cols; e += RT_T) {
     const int g = e / cols, j = e % cols;
     int u = 0;
     if (row > 0 && g < gn) {
@@ -219,63 +221,55 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   auto up_class = [&](int g, int j) -> int { return s_up[g < RT_B ? g : 0][j]; };
   // R_j[a][l] = bA[l / Gin][u] sum_h bL[l][h] Y[h][a] from Ys: thread (bl2,
-  // a0) of 16 per beam element takes a = a0 and a0 + 16 for every l (Ys
-  // read along a, bL broadcast); scaled to max |.| = 1; written to R and,
-  // split, as the next column's operand; Ys cleared for the next column
+  // a), a warp per beam element, every l (Ys read along a, bL broadcast);
+  // scaled to max |.| = 1; written to R and, split, as the next column's
+  // operand; Ys cleared for the next column
   auto finish_column = [&](int j) {
     const int s = row * cols + j;
     const int* dA = mps.dimA + ((row + 1) * cols + j) * 3;
     const int chiL = dA[1];
     const int* dm = tb.dims + s * DIMW;
     const int DL = dm[D_DL], NL = dm[D_NL], Gin = dm[D_GIN];
-    for (int e = tid; e < 16 * MAXP; e += 128) sbL[e] = (e / MAXP) < DL ? wt.bL[(size_t)s * tb.lstride + e] : 0.f;
-    for (int e = tid; e < 256; e += 128) sbA[e] = wt.bA[(size_t)s * 256 + e];
+    for (int e = tid; e < 16 * MAXP; e += RT_T) sbL[e] = (e / MAXP) < DL ? wt.bL[(size_t)s * tb.lstride + e] : 0.f;
+    for (int e = tid; e < 256; e += RT_T) sbA[e] = wt.bA[(size_t)s * 256 + e];
     __syncthreads();
-    const int bl2 = tid >> 4, a0 = tid & 15;
+    const int bl2 = tid >> 5, a = tid & 31;
     const int u2 = up_class(bl2, j);
     const bool bok = bl2 < gn;
-    float out[2][16];
+    float out[16];
     float mx = 0.f;
+    float y[16];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int a = a0 + 16 * q;
-      float y[16];
+    for (int hh = 0; hh < 16; ++hh) y[hh] = Ys[bl2][hh][a];
 #pragma unroll
-      for (int hh = 0; hh < 16; ++hh) y[hh] = Ys[bl2][hh][a];
+    for (int l = 0; l < 16; ++l) {
+      float t = 0.f;
+      if (bok && l < DL && a < chiL) {
 #pragma unroll
-      for (int l = 0; l < 16; ++l) {
-        float t = 0.f;
-        if (bok && l < DL && a < chiL) {
-#pragma unroll
-          for (int hh = 0; hh < 16; ++hh)
-            if (hh < NL) t += sbL[l * MAXP + hh] * y[hh];
-          t *= sbA[(l / Gin) * 16 + u2];
-        }
-        out[q][l] = t;
-        mx = fmaxf(mx, fabsf(t));
+        for (int hh = 0; hh < 16; ++hh)
+          if (hh < NL) t += sbL[l * MAXP + hh] * y[hh];
+        t *= sbA[(l / Gin) * 16 + u2];
       }
+      out[l] = t;
+      mx = fmaxf(mx, fabsf(t));
     }
-    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const float inv = mx > 0.f ? 1.f / mx : 0.f;
+    if (bok && a < chi) {
+      float* Rj = bt.R + ((size_t)(b0 + bl2) * (cols + 1) + j) * renv + (size_t)a * rs;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int a = a0 + 16 * q;
-      if (bok && a < chi) {
-        float* Rj = bt.R + ((size_t)(b0 + bl2) * (cols + 1) + j) * renv + (size_t)a * rs;
+      for (int l = 0; l < 16; ++l)
+        if (l < rs) Rj[l] = out[l] * inv;
+    }
 #pragma unroll
-        for (int l = 0; l < 16; ++l)
-          if (l < rs) Rj[l] = out[q][l] * inv;
-      }
-#pragma unroll
-      for (int l = 0; l < 16; ++l) {
-        float hi, lo;
-        tc::split_tf32(out[q][l] * inv, hi, lo);
-        Ath[(size_t)(bl2 * RT_R + l) * RT_K + a] = hi;
-        Atl[(size_t)(bl2 * RT_R + l) * RT_K + a] = lo;
-      }
+    for (int l = 0; l < 16; ++l) {
+      float hi, lo;
+      tc::split_tf32(out[l] * inv, hi, lo);
+      Ath[(size_t)(bl2 * RT_R + l) * RT_K + a] = hi;
+      Atl[(size_t)(bl2 * RT_R + l) * RT_K + a] = lo;
     }
     __syncthreads();
-    for (int e = tid; e < RT_B * 16 * (RT_A + 1); e += 128) (&Ys[0][0][0])[e] = 0.f;
+    for (int e = tid; e < RT_B * 16 * (RT_A + 1); e += RT_T) (&Ys[0][0][0])[e] = 0.f;
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
   };
@@ -287,7 +281,7 @@ __global__ void __launch_bounds__(128, 1)
     const int* dA = mps.dimA + ((row + 1) * cols + j) * 3;
     const int p = dA[0], chiL = dA[1], chiR = dA[2];
     const float* Bs = mps.A + (size_t)((row + 1) * cols + j) * mps.site_stride;
-    for (int e = tid; e < RT_B * 16 * RT_A; e += 128) {
+    for (int e = tid; e < RT_B * 16 * RT_A; e += RT_T) {
       const int g = e / (16 * RT_A), h = (e / RT_A) % 16, a = e % RT_A;
       if (g >= gn || a >= chiL) continue;
       const float* W = Cu + ((size_t)j * 16 + up_class(g, j)) * 256 + h * 16;
@@ -299,7 +293,10 @@ __global__ void __launch_bounds__(128, 1)
     finish_column(j);
   }
   // this thread's accumulator row: beam element bl, right-bond entry r
-  const int bl = 2 * warp + (lane >> 4), r = lane & 15;
+  // (warps w and w + 4 read lane quarter w & 3 and take the state classes
+  // pd < 8 and pd >= 8 respectively)
+  const int quarter = warp & 3, half = warp >> 2;
+  const int bl = 2 * quarter + (lane >> 4), r = lane & 15;
   int it = 0;
   for (int j = cols - 2; j >= 1; --j, ++it) {
     const int s = row * cols + j;
@@ -353,23 +350,30 @@ __global__ void __launch_bounds__(128, 1)
     for (int a = 0; a < RT_A; ++a) acc[a] = 0.f;
     // the coefficients first: the accumulator loads below are ordered
     // against every memory access
-    float cv[RT_PD];
+    constexpr int PH = RT_PD / 2;  // classes per half
+    const int pd0 = half * PH;
+    float cv[PH];
 #pragma unroll
-    for (int pd = 0; pd < RT_PD; ++pd) cv[pd] = (valid && pd < p) ? cu[pd * 16] : 0.f;
+    for (int q = 0; q < PH; ++q) cv[q] = (valid && pd0 + q < p) ? cu[(pd0 + q) * 16] : 0.f;
 #pragma unroll
-    for (int pd = 0; pd < RT_PD; ++pd) {
-      if (pd >= p) break;
+    for (int q = 0; q < PH; ++q) {
+      if (pd0 + q >= p) break;
       float v[RT_A];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pd * RT_A), v);
-      const float c = cv[pd];
+      tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((pd0 + q) * RT_A), v);
+      const float c = cv[q];
 #pragma unroll
       for (int a = 0; a < RT_A; ++a) acc[a] += c * v[a];
     }
+    // the lower half's partial sum, then the upper half's added to it
     const int h = valid ? s_hr[r] : -1;
-    if (h >= 0)
+    if (half == 0 && h >= 0)
 #pragma unroll
       for (int a = 0; a < RT_A; ++a) Ys[bl][h][a] = acc[a];
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (half == 1 && h >= 0)
+#pragma unroll
+      for (int a = 0; a < RT_A; ++a) Ys[bl][h][a] += acc[a];
     __syncthreads();
     finish_column(j);
   }
@@ -420,7 +424,7 @@ cudaError_t launch_right_envs_tc(const DevTables& tb, DevWeights<float> wt, DevM
   // algorithmic flops of the products (the three split-TF32 passes are the
   // way they are computed, not more work)
   count_launches("k_renv_tc", st, 2.0 * (double)tiles * RT_M * RT_N * RT_K * (cols - 2));
-  k_renv_tc<<<dim3(tiles, 1, zn()), 128, RT_SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], tb, wt, mps, row, ds, bt,
+  k_renv_tc<<<dim3(tiles, 1, zn()), RT_T, RT_SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], tb, wt, mps, row, ds, bt,
                                                         cur, Cu, hr, Ah, Al, zs());
   return cudaGetLastError();
 }
