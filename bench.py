@@ -374,6 +374,8 @@ def main():
                     help="grid side override (profiling of a smaller case of the same kernels)")
     ap.add_argument("--beam", type=int, default=None,
                     help="beam override (batches of small-beam solves; not the benchmark workload)")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="tile shapes timed at each shape's first uncaptured launch (on) or the built-in ones (off)")
     ap.add_argument("--only-main", action="store_true",
                     help="timed steps only (no end-to-end, FP64, uneven-batch or profile runs): the ncu "
                          "launch list")
@@ -391,6 +393,7 @@ def main():
     import paper_2502_02317_gb300 as spg
     import torch
 
+    spg.spg_autotune_set(spg.SPG_TUNE_ON if args.autotune == "on" else spg.SPG_TUNE_OFF)
     world, rank, local = dist_info()
     torch.cuda.set_device(local)
     if world > 1:
@@ -467,6 +470,15 @@ def main():
                                                   f"of up to {max(group_sizes) if group_sizes else 1} "
                                                   f"(one launch sequence per group)"}),
             "gpu_launches": int(sum(launches)), "clocks": clk.summary()}
+    # the autotuner's choices for the shapes of the timed step (timed during
+    # the warm-up's uncaptured solves; the timed steps replay graphs
+    # captured with them)
+    choices = {}
+    timed_shapes = spg.spg_autotune_report()
+    for kern, _dev, _grp, _shape, choice, _us in timed_shapes:
+        choices.setdefault(kern, {}).setdefault(str(choice), 0)
+        choices[kern][str(choice)] += 1
+    line["autotune"] = {"mode": args.autotune, "shapes_timed": len(timed_shapes), "variant_counts": choices}
     if args.only_main:
         # per-kernel device times of one more solve (after the timed steps),
         # to set beside an ncu launch list of the timed step

@@ -546,6 +546,51 @@ int spg_peak_probe_stream(void* cuda_stream, int32_t kind, double* tflops);
 int spg_profile(spg_ctx* ctx, int enable);
 int spg_profile_report(spg_ctx* ctx, char* json_out, size_t cap);
 
+/* Autotuner of tile shapes (the paper has no counterpart: its package leaves
+ * kernel tiling to its tensor libraries).  Three kernels come in variants
+ * that differ only in how outputs are spread over threads and blocks and
+ * compute every output by the same operations, so that results do not
+ * depend on the variant, bit for bit:
+ *   k_gemm      (SIMT products of the truncations and sweeps): 1, 2, 4 or 8
+ *               outputs per thread along each tile edge (variants 0..3);
+ *   k_xgemm     (the sweeps' per-state products): 1, 2 or 4 states per
+ *               block (variants 0..2; FP64 up to 2);
+ *   k_marginals (mixed mode): the boundary-MPS site staged in shared memory
+ *               (variant 0, when it fits) or read through the L1 cache
+ *               (variant 1, more warps per SM).
+ * Process-wide mode (all contexts and devices):
+ *   SPG_TUNE_OFF        the built-in choice everywhere;
+ *   SPG_TUNE_ON         (default) the first launch of a shape (kernel, sizes,
+ *                       strides, instances of the group, device) on a stream
+ *                       that is not being captured runs every valid variant
+ *                       three times on the real operands, timed with CUDA
+ *                       events on that stream (the host waits for the stream
+ *                       there), and keeps the fastest for that launch and all
+ *                       later ones of the shape, graph captures included; a
+ *                       shape first met inside a capture or while
+ *                       spg_profile records keeps the built-in choice until
+ *                       an uncaptured launch times it;
+ *   SPG_TUNE_FORCE + k  variant k of every tuned kernel (the last valid one
+ *                       at or below k), nothing timed: for tests.
+ * A solve's first, uncaptured run is where its shapes are timed, so a first
+ * solve takes longer with SPG_TUNE_ON.  Graphs already captured keep the
+ * variants they were captured with.
+ * spg_autotune_set: sets the mode (SPG_EINVAL outside 0 .. SPG_TUNE_FORCE+3),
+ *   returns the previous one in *previous (may be NULL).
+ * spg_autotune_clear: forgets every timed shape (SPG_EINVAL while another
+ *   host thread is timing one).
+ * spg_autotune_report: the number of timed shapes and, into text_out
+ *   (NUL-terminated, truncated to cap bytes; may be NULL), one line per shape:
+ *   "<kernel> dev <d> group <n> shape <sizes...> -> <variant> us <t0> <t1> ..."
+ *   (best time of each variant in microseconds, -1 for one that could not
+ *   run the shape).  Host only; never fails. */
+#define SPG_TUNE_OFF 0
+#define SPG_TUNE_ON 1
+#define SPG_TUNE_FORCE 2
+int spg_autotune_set(int32_t mode, int32_t* previous);
+int spg_autotune_clear(void);
+int spg_autotune_report(int32_t* n_shapes, char* text_out, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

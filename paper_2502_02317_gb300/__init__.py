@@ -13,13 +13,15 @@ import os as _os
 _os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from ._binding import (SPG_ECUDA, SPG_EINEXACT, SPG_EINVAL, SPG_ENOMEM, SPG_ENUMERIC, SPG_ETIMEOUT,
-                       SPG_EUNSUPPORTED, SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, SPG_WS_FEATURES, Context, Mlp, Problem, Result,
+                       SPG_EUNSUPPORTED, SPG_FP64, SPG_KING, SPG_MIXED, SPG_SQUARE, SPG_TUNE_FORCE, SPG_TUNE_OFF,
+                       SPG_TUNE_ON, SPG_WS_FEATURES, Context, Mlp, Problem, Result,
                        SpgError, lib, params, spg_boundary_export, spg_debug_marginals, spg_lattice_site_map,
                        spg_check_bounded_wait, spg_inject_alloc_failure, spg_log_partition,
                        spg_peak_probe, spg_problem_ising, spg_problem_potts, spg_profile,
                        spg_profile_report,
                        spg_problem_update_ising, spg_set_warm_start, spg_solve, spg_solve_batch, spg_solve_group,
-                       spg_solve_lattice8, spg_sweep_trace, spg_tc_product, spg_truncate,
+                       spg_solve_lattice8, spg_sweep_trace, spg_tc_product, spg_truncate, spg_autotune_clear,
+                       spg_autotune_report, spg_autotune_set,
                        spg_truncate_static, spg_warm_features)
 
 __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
@@ -28,5 +30,7 @@ __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_pro
            "spg_truncate_static", "spg_warm_features", "spg_boundary_export", "Mlp", "spg_set_warm_start",
            "spg_sweep_trace", "SPG_WS_FEATURES", "spg_peak_probe", "spg_check_bounded_wait",
            "spg_inject_alloc_failure", "spg_solve_lattice8", "spg_problem_update_ising",
+           "spg_autotune_set", "spg_autotune_clear", "spg_autotune_report", "SPG_TUNE_OFF", "SPG_TUNE_ON",
+           "SPG_TUNE_FORCE",
            "SPG_FP64", "SPG_MIXED", "SPG_SQUARE", "SPG_KING", "SPG_EINVAL", "SPG_EINEXACT", "SPG_ENOMEM",
            "SPG_ECUDA", "SPG_ETIMEOUT", "SPG_ENUMERIC", "SPG_EUNSUPPORTED"]

@@ -27,6 +27,9 @@ SPG_SQUARE = 0
 SPG_KING = 1
 SPG_FP64 = 0
 SPG_MIXED = 1
+SPG_TUNE_OFF = 0
+SPG_TUNE_ON = 1
+SPG_TUNE_FORCE = 2
 
 _ERRNAMES = {v: k for k, v in dict(SPG_EINVAL=-1, SPG_EINEXACT=-2, SPG_ENOMEM=-3, SPG_ECUDA=-4,
                                    SPG_ETIMEOUT=-5, SPG_ENUMERIC=-6, SPG_EUNSUPPORTED=-7).items()}
@@ -102,6 +105,9 @@ def _load():
         "spg_inject_alloc_failure": (C.c_int, [I32]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
+        "spg_autotune_set": (C.c_int, [I32, pI32]),
+        "spg_autotune_clear": (C.c_int, []),
+        "spg_autotune_report": (C.c_int, [pI32, C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -381,6 +387,39 @@ def spg_profile_report(ctx: Context) -> dict:
     buf = C.create_string_buffer(1 << 16)
     ctx.check(lib.spg_profile_report(ctx.h, buf, len(buf)))
     return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def spg_autotune_set(mode: int) -> int:
+    """Sets the process-wide autotuner mode (SPG_TUNE_OFF, SPG_TUNE_ON or
+    SPG_TUNE_FORCE + k); returns the previous mode."""
+    prev = C.c_int32(0)
+    rc = lib.spg_autotune_set(int(mode), C.byref(prev))
+    if rc != 0:
+        raise SpgError(rc, f"autotuner mode {mode} out of range")
+    return prev.value
+
+
+def spg_autotune_clear() -> None:
+    """Forgets every timed shape."""
+    rc = lib.spg_autotune_clear()
+    if rc != 0:
+        raise SpgError(rc, "a shape is being timed")
+
+
+def spg_autotune_report() -> list:
+    """[(kernel, device, group, shape tuple, chosen variant, [best us per
+    variant, -1: could not run])] of every timed shape."""
+    n = C.c_int32(0)
+    buf = C.create_string_buffer(1 << 20)
+    lib.spg_autotune_report(C.byref(n), buf, len(buf))
+    out = []
+    for line in buf.value.decode().splitlines():
+        head, tail = line.split(" -> ")
+        f = head.split()
+        choice, times = tail.split(" us")
+        out.append((f[0], int(f[2]), int(f[4]), tuple(int(x) for x in f[6:]), int(choice),
+                    [float(t) for t in times.split()]))
+    return out
 
 
 def spg_truncate(ctx: Context, M, keep: int, iters: int = 6):

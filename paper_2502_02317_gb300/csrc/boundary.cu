@@ -936,8 +936,9 @@ __global__ void __launch_bounds__(256) k_zip_M_rows(DevTables tb, DevWeights<T> 
 
 // ---------------------------------------------------------------- GEMM
 // C[m x n] = op(A) op(B), row-major; op(A) = A (m x k, lda) or A^T (A stored
-// k x m); op(B) = B (k x n, ldb) or B^T (B stored n x k).  32x32 tile, 256
-// threads, 2x2 outputs per thread.
+// k x m); op(B) = B (k x n, ldb) or B^T (B stored n x k).  32x32 tile,
+// MT x MT outputs per thread ((32 / MT)^2 threads); each output is one chain
+// of fused multiply-adds over k in order, whatever MT is.
 template <typename T, bool TA, bool TB, int MT>
 __global__ void __launch_bounds__((32 / MT) * (32 / MT)) k_gemm(int m, int n, int k, const T* __restrict__ A, int lda,
                                                                 const T* __restrict__ B, int ldb, T* __restrict__ C,
@@ -1334,34 +1335,44 @@ cudaError_t gemm(bool transA, int m, int n, int k, const T* A, int lda, const T*
   return gemm2<T>(transA, false, m, n, k, A, lda, B, ldb, C, ldc, st);
 }
 
+// One k_gemm variant: MT x MT outputs per thread (32 / MT threads along each
+// tile edge).
+template <typename T, bool TA, bool TB>
+void gemm_variant(int v, dim3 grid, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
+                  size_t z, cudaStream_t st) {
+  switch (v) {
+    case 0: k_gemm<T, TA, TB, 1><<<grid, 1024, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z); break;
+    case 1: k_gemm<T, TA, TB, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z); break;
+    case 2: k_gemm<T, TA, TB, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z); break;
+    default: k_gemm<T, TA, TB, 8><<<grid, 16, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z); break;
+  }
+}
+
 template <typename T>
 cudaError_t gemm2(bool transA, bool transB, int m, int n, int k, const T* A, int lda, const T* B, int ldb, T* C,
                   int ldc, cudaStream_t st) {
   ZOK(A, B, C);
   dim3 grid((n + 31) / 32, (m + 31) / 32, zn());
-  count_launches("k_gemm", st, 2.0 * m * n * k);
   const size_t z = zs();
-  // a lockstep group fills the GPU: 4 x 4 outputs per thread (64 threads per
-  // tile, more multiply-adds per shared-memory read); alone, 2 x 2 on 256
-  // threads (shorter chains for the small, latency-bound products).  Each
-  // output sums over k in the same order either way.
-  if (zn() > 1) {
+  auto run = [&](int v) {
     if (transA && transB)
-      k_gemm<T, true, true, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+      gemm_variant<T, true, true>(v, grid, m, n, k, A, lda, B, ldb, C, ldc, z, st);
     else if (transA)
-      k_gemm<T, true, false, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+      gemm_variant<T, true, false>(v, grid, m, n, k, A, lda, B, ldb, C, ldc, z, st);
     else if (transB)
-      k_gemm<T, false, true, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+      gemm_variant<T, false, true>(v, grid, m, n, k, A, lda, B, ldb, C, ldc, z, st);
     else
-      k_gemm<T, false, false, 4><<<grid, 64, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
-  } else if (transA && transB)
-    k_gemm<T, true, true, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
-  else if (transA)
-    k_gemm<T, true, false, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
-  else if (transB)
-    k_gemm<T, false, true, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
-  else
-    k_gemm<T, false, false, 2><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, z);
+      gemm_variant<T, false, false>(v, grid, m, n, k, A, lda, B, ldb, C, ldc, z, st);
+  };
+  // built-in choice: a lockstep group fills the GPU, 4 x 4 outputs per
+  // thread (64 threads per tile, more multiply-adds per shared-memory read);
+  // alone, 2 x 2 on 256 threads (shorter chains for the small, latency-bound
+  // products).  Every variant sums each output over k in the same order (the
+  // same fused multiply-adds), so the autotuner may pick any of them.
+  const long long shape[] = {(long long)sizeof(T), transA, transB, m, n, k, lda, ldb, ldc};
+  const int v = tune_pick("k_gemm", shape, 9, st, 4, 0xfu, zn() > 1 ? 2 : 1, run);
+  count_launches("k_gemm", st, 2.0 * m * n * k);
+  run(v);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // merging of partial configurations equal on the boundary of the explored
 // region), Sec. 3.1 (SearchParameters(max_states, cut_off_prob),
 // merge_branches, low_energy_spectrum), Fig. 1(d)-(e).
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -1578,18 +1579,30 @@ cudaError_t launch_marginals(const DevTables& tb, DevWeights<T> wt, DevWeights<d
                              const DevSearch& ds, DevBeamT<T> bt, int cur, cudaStream_t st, double flops) {
   if constexpr (std::is_same<T, float>::value) {
     ZOK(tb, wt, mps, ds, bt);
-    // the site staged in shared memory when it fits beside the warps' buffers
+    // variant 0: the site staged in shared memory (when it fits beside the
+    // warps' buffers); variant 1: the site read through the L1 cache, less
+    // shared memory per block and more blocks per SM.  Both compute the same
+    // values from the same data.
     const size_t site_floats = mps.site_stride;
     const size_t warp_floats = (size_t)MW * 2 * MAXP * bt.chi;
-    const int staged = sizeof(float) * (site_floats + warp_floats) <= 160 * 1024 ? (int)site_floats : 0;
-    const size_t smem = sizeof(float) * ((size_t)staged + warp_floats);
+    const bool fits = sizeof(float) * (site_floats + warp_floats) <= 160 * 1024;
     static std::once_flag once;
     std::call_once(once, [] {
       cudaFuncSetAttribute(k_marginals_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
+    auto run = [&](int v) {
+      const int staged = v == 0 ? (int)site_floats : 0;
+      const size_t smem = sizeof(float) * ((size_t)staged + warp_floats);
+      k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, smem, st>>>(tb, wt, mps, site, ds, bt, cur,
+                                                                                    staged, zs());
+    };
+    // the bonds of a site depend on its column and on whether its row is the
+    // first (the beam still filling) or the last (trivial environment below)
+    const int i = site / tb.cols, j = site % tb.cols;
+    const long long shape[] = {bt.chi, ds.cap, tb.dmax, (long long)site_floats, j, std::min(i, 1), i == tb.rows - 1};
+    const int v = tune_pick("k_marginals", shape, 7, st, 2, fits ? 3u : 2u, fits ? 0 : 1, run);
     count_launches("k_marginals", st, flops);
-    k_marginals_f32<<<dim3((ds.cap + MW - 1) / MW, 1, zn()), 32 * MW, smem, st>>>(tb, wt, mps, site, ds, bt, cur,
-                                                                                  staged, zs());
+    run(v);
     return cudaGetLastError();
   } else {
     (void)wt;

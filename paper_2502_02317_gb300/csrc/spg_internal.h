@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <functional>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -130,6 +131,15 @@ inline void profile_mark(cudaStream_t st) {
   p.flops.push_back(0.0);
   ++p.used;
 }
+
+// Autotuner (autotune.cpp): the variant of a kernel to launch for a shape.
+// `launch(v)` enqueues variant v on `st` (not counted as a library launch);
+// `valid` has bit v set for every variant that may run this shape; `dflt` is
+// the built-in choice.  The variants of one kernel must give bit-identical
+// results and must not read what they write (each may run several times).
+constexpr int TUNE_MAX_VARIANTS = 4;
+int tune_pick(const char* kernel, const long long* shape, int n_shape, cudaStream_t st, int n_var, unsigned valid,
+              int dflt, const std::function<void(int)>& launch);
 
 constexpr int MAXS = 256;   // states of one cluster
 constexpr int MAXP = 16;    // projected (reduced-table) dimension

@@ -52,21 +52,17 @@ __device__ __forceinline__ long long xval(const DevTables& tb, int s, int id, in
 }
 
 // One 32 x 32 output tile of state q's product per group of 64 threads, QPB
-// states per block (4 in FP32, 2 in FP64); each thread holds a 4 x 4
-// register tile and reads a four-wide column of A and row of B from shared
-// memory per k (two vector loads per 16 multiply-adds).  Every output sums
-// over k in order, as a one-entry-per-thread kernel would.  grid: (N tiles,
+// states per block (1, 2 or 4, the autotuner's choice); each thread holds a
+// 4 x 4 register tile and reads a four-wide column of A and row of B from
+// shared memory per k (two vector loads per 16 multiply-adds).  Every output
+// sums over k in order, as a one-entry-per-thread kernel would, whatever QPB
+// is.  grid: (N tiles,
 // M tiles, state blocks x instances of a lockstep group).
-template <typename T>
-__host__ __device__ constexpr int xgemm_qpb() {
-  return sizeof(T) == 4 ? 4 : 2;
-}
-template <typename T>
-__global__ void __launch_bounds__(64 * xgemm_qpb<T>()) k_xgemm(DevTables tb, int s, int n2, int M, int N, int K,
-                                                               const T* __restrict__ A, XOff oa, int sAi, int sAk,
-                                                               const T* __restrict__ B, XOff ob, int sBk, int sBj,
-                                                               T* __restrict__ C, int nq, size_t zs) {
-  constexpr int QPB = xgemm_qpb<T>();
+template <typename T, int QPB>
+__global__ void __launch_bounds__(64 * QPB) k_xgemm(DevTables tb, int s, int n2, int M, int N, int K,
+                                                    const T* __restrict__ A, XOff oa, int sAi, int sAk,
+                                                    const T* __restrict__ B, XOff ob, int sBk, int sBj,
+                                                    T* __restrict__ C, int nq, size_t zs) {
   constexpr int BT = 32, LD = BT + 4;  // tile edge; padded row (a multiple of 4 for the vector loads)
   __shared__ __align__(16) T sA[QPB][BT][LD];  // [k][i]
   __shared__ __align__(16) T sB[QPB][BT][LD];  // [k][j]
@@ -322,10 +318,30 @@ cudaError_t variational_sweeps(const DevTables& tb, DevWeights<T> wt, DevMPS<T> 
   // bond b).  Per site: tables' dims from the host copy.
   auto xgemm = [&](int s, int nq, int n2, int M, int N, int K, const T* A, XOff oa, int sAi, int sAk, const T* B,
                    XOff ob, int sBk, int sBj, T* C) {
-    constexpr int QPB = xgemm_qpb<T>();
-    dim3 grid((N + 31) / 32, (M + 31) / 32, ((nq + QPB - 1) / QPB) * zn());
+    // variant v: 2^v states per block (FP64 up to 2: the tiles of 4 states
+    // exceed the static shared memory); a variant whose grid would have
+    // more than 65535 blocks along z is not valid for the shape
+    auto grid_of = [&](int v) {
+      const int qpb = 1 << v;
+      return dim3((N + 31) / 32, (M + 31) / 32, (unsigned)(((nq + qpb - 1) / qpb) * zn()));
+    };
+    auto run = [&](int v) {
+      const dim3 grid = grid_of(v);
+      if (v == 0)
+        k_xgemm<T, 1><<<grid, 64, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
+      else if (v == 1)
+        k_xgemm<T, 2><<<grid, 128, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
+      else if constexpr (sizeof(T) == 4)
+        k_xgemm<T, 4><<<grid, 256, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
+    };
+    const int nvar = sizeof(T) == 4 ? 3 : 2;
+    unsigned valid = 0;
+    for (int v = 0; v < nvar; ++v)
+      if ((size_t)((nq + (1 << v) - 1) >> v) * zn() <= 65535) valid |= 1u << v;
+    const long long shape[] = {(long long)sizeof(T), M, N, K, nq, sAi, sAk, sBk, sBj};
+    const int v = tune_pick("k_xgemm", shape, 9, st, nvar, valid, nvar - 1, run);
     count_launches("k_xgemm", st, 2.0 * nq * M * N * K);
-    k_xgemm<T><<<grid, 64 * QPB, 0, st>>>(tb, s, n2, M, N, K, A, oa, sAi, sAk, B, ob, sBk, sBj, C, nq, zs());
+    run(v);
   };
   auto coef = [&](int s, int mode, int K, int u = 0, int g = 0) {
     const int d = hd_states(s);

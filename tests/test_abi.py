@@ -114,3 +114,27 @@ def test_binding_rejects_misread_tensors_before_any_launch():
     assert b._stream_handle(None) is None
     assert b._stream_handle(0) is None
     assert b._stream_handle(1234).value == 1234
+
+
+def test_autotuner_modes_on_the_host():
+    """The autotuner's process-wide mode: on by default, every documented
+    mode accepted, out-of-range ones refused; no shape is timed without a
+    launch, and the report and clear calls need no device."""
+    import paper_2502_02317_gb300 as spg
+    prev = spg.spg_autotune_set(spg.SPG_TUNE_OFF)
+    try:
+        assert prev == spg.SPG_TUNE_ON
+        last = spg.SPG_TUNE_OFF
+        for mode in [spg.SPG_TUNE_ON] + [spg.SPG_TUNE_FORCE + k for k in range(4)]:
+            assert spg.spg_autotune_set(mode) == last
+            last = mode
+        for bad in (-1, spg.SPG_TUNE_FORCE + 4):
+            with pytest.raises(spg.SpgError) as e:
+                spg.spg_autotune_set(bad)
+            assert e.value.code == spg.SPG_EINVAL
+        spg.spg_autotune_clear()
+        assert spg.spg_autotune_report() == []
+        n = ctypes.c_int32(-1)
+        assert spg.lib.spg_autotune_report(ctypes.byref(n), None, 0) == 0 and n.value == 0
+    finally:
+        spg.spg_autotune_set(spg.SPG_TUNE_ON)
