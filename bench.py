@@ -160,9 +160,10 @@ def cpu_oracle_sample(seed, max_sites=6):
         children = {}
         for b in beam:
             lc = search.log_conditional(p, B, i, j, b.lenv, b.R, b.states)
+            dEs = search.delta_energies(fg, s, b.states)
             for x in range(fg.d[s]):
                 st = b.states + (x,)
-                E = b.E + search.delta_energy(fg, s, x, b.states)
+                E = b.E + int(dEs[x])
                 key = tuple(st[t] for t in ks)
                 cand += 1
                 cur = children.get(key)

@@ -25,6 +25,14 @@ Workload shapes (paper Sec. 2 Eq. 1-2; Fig. 4 for the Chimera unit cell):
   clusters (the quasi-2D graph of the paper's Fig. 1(a)).
 * ``king_potts``: an L x L grid of Potts variables with d states, local tables
   and d x d pairwise tables on all 8-neighbour edges.
+* ``large_cells``: a rows x cols grid (king's-graph or square-lattice
+  adjacency) of clusters of k spins -- 16 is the size of a Zephyr unit cell,
+  24 of a Pegasus one (paper Sec. 3.1.1, Fig. 4: both map onto king's graphs
+  of clusters) -- with K_{k/2,k/2} couplers inside a cell (between its first
+  and second halves) and ``links`` couplers between every pair of
+  neighbouring cells, each between a spin drawn from each cell (distinct
+  pairs), J uniform in {-1,+1}, h = 0.  Only the sizes follow the vendors'
+  cells; the wiring is this generator's.
 * ``inpainting``: an L x L grid of d labels shaped like an inpainting problem
   (Sec. 3 example, Fig. 5: data on a circular boundary, the inside to be
   filled in): pixels on or outside a ring observe one of d labels in d equal
@@ -273,3 +281,49 @@ def batch_chimera(n_instances: int, L_lo: int, L_hi: int, base_seed: int,
     Ls = rng.integers(L_lo, L_hi + 1, size=n_instances)
     coins = rng.integers(0, len(chis), size=n_instances)
     return [(chimera(int(L), base_seed + 1 + i), int(chis[c])) for i, (L, c) in enumerate(zip(Ls, coins))]
+
+
+def large_cells(rows: int, cols: int, k: int, seed: int, links: int = 2, node_type: int = KING,
+                intra: str = "bipartite") -> IsingInstance:
+    """rows x cols grid of clusters of k spins (module header: ``large_cells``).
+    intra: "bipartite" (K_{k/2,k/2} inside a cell) or "ring" (spin t coupled
+    to spin t+1 mod k: fewer couplers, the same number of states)."""
+    if k % 2 or k < 4:
+        raise ValueError("k must be even and at least 4")
+    rng = _rng(seed)
+    ei, ej = [], []
+
+    def spins(i, j):
+        return [k * (i * cols + j) + t for t in range(k)]
+
+    nbrs = ((0, 1), (1, -1), (1, 0), (1, 1)) if node_type == KING else ((0, 1), (1, 0))
+    for i in range(rows):
+        for j in range(cols):
+            s = spins(i, j)
+            if intra == "ring":
+                for a in range(k):
+                    ei.append(s[a])
+                    ej.append(s[(a + 1) % k])
+            else:
+                for a in range(k // 2):
+                    for b in range(k // 2, k):
+                        ei.append(s[a])
+                        ej.append(s[b])
+            for di, dj in nbrs:
+                ii, jj = i + di, j + dj
+                if not (0 <= ii < rows and 0 <= jj < cols):
+                    continue
+                t = spins(ii, jj)
+                pairs = set()
+                while len(pairs) < links:
+                    pairs.add((int(rng.integers(k)), int(rng.integers(k))))
+                for a, b in sorted(pairs):
+                    ei.append(s[a])
+                    ej.append(t[b])
+    J = rng.choice(np.array([-1.0, 1.0]), size=len(ei))
+    n = rows * cols * k
+    return IsingInstance(n, np.array(ei, np.int32), np.array(ej, np.int32), J, np.zeros(n),
+                         np.repeat(np.arange(rows * cols, dtype=np.int32), k), rows, cols,
+                         (np.arange(rows * cols) // cols).astype(np.int32),
+                         (np.arange(rows * cols) % cols).astype(np.int32), 0, node_type,
+                         name=f"cells{rows}x{cols}x{k}_l{links}_s{seed}")

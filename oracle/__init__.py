@@ -12,9 +12,13 @@ no blocking, fusion or reordering beyond what each step states:
 * ``tables``   -- Eq. 1 / Eq. 2 and Sec. 2: spins grouped into clusters, the
   local energy table of every cluster over all its states ("full spectrum")
   and the pairwise table of every grid edge, reduced to its distinct rows and
-  columns with projectors (Sec. 3.1, "Sparsity").
+  columns with projectors (Sec. 3.1, "Sparsity"); for clusters of more than
+  8 spins (Sec. 3.1.1: Pegasus, Zephyr) the sparse form, whose pairwise
+  tables are over the coupled spins' configurations only.
 * ``peps``     -- Sec. 2, Fig. 1(c): Boltzmann weights at inverse temperature
-  beta and the row MPOs of the PEPS on the square and king's lattices.
+  beta and the row MPOs of the PEPS on the square and king's lattices
+  (sparse factor graphs: classes over a cluster's interface configurations,
+  site tensors by grouping the states' terms).
 * ``boundary`` -- Sec. 2, Fig. 1(d) and Sec. 3.1 (``MpsParameters``,
   ``SVDTruncate``): bottom-up boundary MPSs by MPO-MPS zipper application with
   SVD truncation to bond dimension chi, then variational sweeps.
@@ -27,8 +31,10 @@ no blocking, fusion or reordering beyond what each step states:
   each of the 8 rotations / reflections of the grid, states mapped back to
   the original sites, the best of 8 kept.
 * ``exact``    -- pins that do not use any of the above: brute force over all
-  spin configurations (<= 24 spins) and spin-level row transfer matrices for
-  width-3 Chimera strips (exact log Z and exact ground energy).
+  spin configurations (<= 24 spins), spin-level row transfer matrices for
+  width-3 Chimera strips (exact log Z and exact ground energy), and sums over
+  the interface spins of large clusters (exact log Z, ground energy and the
+  first cluster's marginal).
 
 Where the paper leaves a point open, the reading taken is stated in the
 docstring of the function that implements it.

@@ -8,6 +8,14 @@ Eq. 1, directly:
   ground energy and degeneracy, log Z = log sum exp(-beta E), and exact
   conditional marginals of cluster states given a prefix of cluster states;
 * ``potts_all_energies``: every configuration of a small Potts instance;
+* ``interface_sum``: clusters of many spins (up to 24 per cluster) whose
+  inter-cluster couplers touch few spins: every cluster's states are
+  enumerated for its own energy (fields and couplers inside it), grouped by
+  the configuration of its interface spins (those with a coupler to another
+  cluster), and every combination of interface configurations is summed
+  (log-sum-exp) or minimised with the couplers between clusters, giving the
+  exact log Z, ground energy and the exact marginal of the states of the
+  cluster on grid cell (0, 0);
 * ``chimera_strip``: row transfer matrices of a Chimera-like strip of width
   <= 3 cells over the 4w side-A spins of a row (the only spins with couplers
   to the next row), giving exact log Z (log-sum-exp) and the exact ground
@@ -210,3 +218,74 @@ def chimera_strip(inst, beta: float):
         m = w.max(axis=0)
         lv = lf + m + np.log(np.exp(w - m[None, :]).sum(axis=0))
     return {"logZ": logsumexp(lv), "ground": int(G.min())}
+
+
+def _bits(x, n):
+    """Spin values s = 2b - 1 of the n low bits of every x ([len(x), n])."""
+    x = np.asarray(x, dtype=np.int64)[:, None]
+    return 2 * ((x >> np.arange(n, dtype=np.int64)[None, :]) & 1) - 1
+
+
+def interface_sum(inst, beta: float, max_bits: int = 22):
+    """Exact log Z, ground energy and log-marginal of the states of the
+    cluster on cell (0, 0) (module header), from Eq. 2 on the instance's
+    arrays.  The sum runs over 2^(total interface spins) <= 2^max_bits
+    combinations."""
+    J = _grid_ints(inst.J, inst.energy_shift)
+    h = _grid_ints(inst.h, inst.energy_shift)
+    u = 2.0 ** (-inst.energy_shift)
+    cos = np.asarray(inst.cluster_of_spin)
+    n_cl = int(cos.max()) + 1
+    members = [np.sort(np.nonzero(cos == c)[0]) for c in range(n_cl)]
+    pos = {int(sp): (c, k) for c in range(n_cl) for k, sp in enumerate(members[c])}
+    ei, ej = np.asarray(inst.ei), np.asarray(inst.ej)
+    inter = [e for e in range(len(J)) if cos[ei[e]] != cos[ej[e]]]
+    iface = [sorted({pos[int(v)][1] for e in inter for v in (ei[e], ej[e]) if cos[v] == c}) for c in range(n_cl)]
+    off = np.concatenate([[0], np.cumsum([len(f) for f in iface])]).astype(np.int64)
+    T = int(off[-1])
+    if T > max_bits:
+        raise ValueError("too many interface spins")
+    F, M, E0, a0 = [], [], None, None
+    for c in range(n_cl):
+        k = len(members[c])
+        S = _bits(np.arange(2 ** k), k)
+        E = S @ h[members[c]]
+        for e in range(len(J)):
+            if cos[ei[e]] == c and cos[ej[e]] == c:
+                E = E + J[e] * S[:, pos[int(ei[e])][1]] * S[:, pos[int(ej[e])][1]]
+        a = np.zeros(2 ** k, dtype=np.int64)
+        for t, q in enumerate(iface[c]):
+            a |= ((np.arange(2 ** k, dtype=np.int64) >> q) & 1) << t
+        lw = -beta * u * E.astype(np.float64)
+        Fc = np.full(2 ** len(iface[c]), -np.inf)
+        np.logaddexp.at(Fc, a, lw)
+        Mc = np.full(2 ** len(iface[c]), np.iinfo(np.int64).max, dtype=np.int64)
+        np.minimum.at(Mc, a, E)
+        F.append(Fc)
+        M.append(Mc)
+        if members[c].size and int(inst.cluster_row[c]) == 0 and int(inst.cluster_col[c]) == 0:
+            E0, a0, c0 = E, a, c
+    # inter-cluster couplers as (bit offset of each end in the combination, J)
+    ends = [(off[cos[ei[e]]] + iface[cos[ei[e]]].index(pos[int(ei[e])][1]),
+             off[cos[ej[e]]] + iface[cos[ej[e]]].index(pos[int(ej[e])][1]), J[e]) for e in inter]
+    G0 = np.full(len(F[c0]), -np.inf)  # log-sum over the rest, per interface configuration of cell (0, 0)
+    ground = None
+    chunk = 1 << 18
+    for lo in range(0, 2 ** T, chunk):
+        g = np.arange(lo, min(2 ** T, lo + chunk), dtype=np.int64)
+        Ein = np.zeros(len(g), dtype=np.int64)
+        for bi, bj, Jv in ends:
+            Ein += Jv * (2 * ((g >> bi) & 1) - 1) * (2 * ((g >> bj) & 1) - 1)
+        lrest = -beta * u * Ein.astype(np.float64)
+        emin = Ein.copy()
+        for c in range(n_cl):
+            ac = (g >> off[c]) & ((1 << len(iface[c])) - 1)
+            emin += M[c][ac]
+            if c != c0:
+                lrest += F[c][ac]
+        g_min = int(emin.min())
+        ground = g_min if ground is None else min(ground, g_min)
+        np.logaddexp.at(G0, (g >> off[c0]) & ((1 << len(iface[c0])) - 1), lrest)
+    logZ = logsumexp(F[c0] + G0)
+    logp0 = -beta * u * E0.astype(np.float64) + G0[a0] - logZ
+    return {"logZ": logZ, "ground": ground, "logp_first": logp0}

@@ -43,6 +43,18 @@ Readings taken here (the paper gives no formula for the site tensors):
   classes), b_up the up edge's, b_ad the up-right edge's of the left
   neighbour, and P_G(u) the down-right class of the upper cluster's states
   in class u.  Row 0 has u of dimension 1, the last row s of dimension 1.
+
+``Sparsity = Sparse`` (Sec. 3.1; factor graphs with sparse edges, see
+``tables``): no pairwise table of the cluster is formed.  A projection of
+cluster s onto a set of edges is a function of the configuration of the
+union U of the spins those edges couple (its "interface"), so its classes
+are found over the 2^|U| interface configurations (first occurrence over
+them in ascending order is first occurrence over the states, as for a
+single edge) and read off for every state; and the site tensor W is formed
+as the sum of the states' terms grouped by their output indices (r, s),
+which never builds the one-hot state map of the dense construction.  Both
+constructions give the same classes, representatives and W (up to the
+summation order of the sums over states).
 """
 from __future__ import annotations
 
@@ -92,6 +104,7 @@ class SiteData:
     b_up: np.ndarray  # [DU, NU]
     b_ad: np.ndarray  # [NR(i, j-1), DU]
     g_of_u: np.ndarray  # [DU] P_G class of the upper cluster's P_D class u
+    sparse: bool = False  # W built by grouping the states' terms (module header)
 
 
 @dataclass
@@ -122,6 +135,8 @@ def _incident(fg: FactorGraph, s: int, t: int):
 
 
 def _class_of(fg: FactorGraph, s: int, nbrs: list):
+    if fg.sparse:
+        return _class_of_sparse(fg, s, nbrs)
     vecs = []
     for t in nbrs:
         if t is None:
@@ -130,6 +145,29 @@ def _class_of(fg: FactorGraph, s: int, nbrs: list):
         if T is not None:
             vecs.append(T)
     return classes(fg.d[s], vecs)
+
+
+def _class_of_sparse(fg: FactorGraph, s: int, nbrs: list):
+    """``_class_of`` over the interface configurations of cluster s (module
+    header): the key of configuration c is the tuple of the edges' rows
+    Esub[sub_e(c)]; P[x] = class of x's interface configuration."""
+    from .tables import sub_index
+    parts = []  # (positions in s of the edge's coupled spins, Esub with s's index first)
+    for t in nbrs:
+        if t is None:
+            continue
+        e = fg.edge(min(s, t), max(s, t))
+        if e is None:
+            continue
+        parts.append((e.pos_m, e.Esub) if s == e.m else (e.pos_n, e.Esub.T))
+    U = np.array(sorted({int(q) for pos, _ in parts for q in pos}), dtype=np.int64)
+    c = np.arange(2 ** len(U), dtype=np.int64)
+    x_of_c = np.zeros_like(c)  # the first state carrying configuration c
+    for k, q in enumerate(U):
+        x_of_c |= ((c >> k) & 1) << int(q)
+    keys = [Es[sub_index(x_of_c, pos)] for pos, Es in parts]
+    Pc, reps_c = classes(len(c), keys)
+    return Pc[sub_index(np.arange(fg.d[s]), U)], x_of_c[reps_c]
 
 
 def build(fg: FactorGraph, beta: float) -> PEPS:
@@ -155,11 +193,11 @@ def build(fg: FactorGraph, beta: float) -> PEPS:
         """Boltzmann factors of edge (s, t) between state lists rs of s and
         rt of t, shifted by the table's minimum ([len(rs), len(rt)]), or
         ones when there is no edge."""
-        T = _incident(fg, s, t) if (s is not None and t is not None) else None
-        if T is None:
+        e = fg.edge(min(s, t), max(s, t)) if (s is not None and t is not None) else None
+        if e is None:
             return np.ones((len(rs), len(rt)))
-        mn = float(T.min())
-        return np.exp(-beta * u * (T[np.ix_(rs, rt)] - mn).astype(np.float64))
+        mn = float(e.min())
+        return np.exp(-beta * u * (e.block(s, rs, rt) - mn).astype(np.float64))
 
     sites = []
     for s in range(fg.n_sites):
@@ -192,9 +230,10 @@ def build(fg: FactorGraph, beta: float) -> PEPS:
         NR = len(c["repR"])
         sites.append(SiteData(d, E, w, c["PL"], c["PU"], c["PR"], c["PD"], c["PG"], c["repR"], c["repD"],
                               len(c["repL"]), len(c["repU"]), NR, len(c["repD"]), len(c["repG"]),
-                              NRl * Gin, NR * Gout, len(repDu), Gin, Gout, b_left, b_up, b_ad, g_of_u))
+                              NRl * Gin, NR * Gout, len(repDu), Gin, Gout, b_left, b_up, b_ad, g_of_u,
+                              fg.sparse))
     for e in fg.edges.values():
-        log_offset += -beta * u * float(e.E.min())
+        log_offset += -beta * u * float(e.min())
     return PEPS(fg, beta, sites, log_offset)
 
 
@@ -211,6 +250,14 @@ def site_terms(st: SiteData, l: int, u: int):
 def mpo_site(st: SiteData) -> np.ndarray:
     """Dense W[l, r, u, s] of one site (definition in the module header)."""
     W = np.zeros((st.DL, st.DR, st.DU, st.ND))
+    if st.sparse:
+        # the states' terms summed by output index (r, s)
+        for u in range(st.DU):
+            for l in range(st.DL):
+                coef, r, s = site_terms(st, l, u)
+                W[l, :, u, :] = np.bincount(r * st.ND + s, weights=coef,
+                                            minlength=st.DR * st.ND).reshape(st.DR, st.ND)
+        return W
     for u in range(st.DU):
         terms = [site_terms(st, l, u) for l in range(st.DL)]
         C = np.stack([t[0] for t in terms])  # [DL, d]

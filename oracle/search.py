@@ -124,8 +124,16 @@ def right_envs(p: peps_mod.PEPS, B: bnd.MPS, i: int, upper_states) -> list:
         uj = 0 if i == 0 else int(p.site(i - 1, j).PD[upper_states[j]])
         A = B.sites[j]
         Rn = np.zeros((A.shape[0], st.DL))
+        if st.sparse:
+            # the sum over states grouped by their output pair (s, r)
+            _, r, s = peps_mod.site_terms(st, 0, uj)
+            pairs, inv = np.unique(s * st.DR + r, return_inverse=True)
+            Vp = np.einsum("axb,bx->ax", A[:, pairs // st.DR, :], R[j + 1][:, pairs % st.DR])
         for l in range(st.DL):
             coef, r, s = peps_mod.site_terms(st, l, uj)
+            if st.sparse:
+                Rn[:, l] = Vp @ np.bincount(inv, weights=coef, minlength=len(pairs))
+                continue
             V = np.einsum("axb,bx->ax", A[:, s, :], R[j + 1][:, r])  # [chi, d]
             Rn[:, l] = V @ coef
         R[j] = Rn / np.max(np.abs(Rn))
@@ -138,20 +146,24 @@ def log_conditional(p, B, i, j, lenv, R, prefix):
     st = p.site(i, j)
     coef, r, s = peps_mod.site_terms(st, _l(p, i, j, prefix), _u(p, i, j, prefix))
     A = B.sites[j]
-    q = np.empty(st.d)
-    for x in range(st.d):
-        q[x] = coef[x] * float(lenv @ A[:, s[x], :] @ R[j + 1][:, r[x]])
+    # q(x) = coef(x) (lenv A[:, s(x), :] R[:, r(x)]); the contraction depends
+    # on x only through (s(x), r(x)), so it is evaluated once per pair (the
+    # same expression for every state of the pair)
+    pairs, inv = np.unique(s * st.DR + r, return_inverse=True)
+    z = np.array([float(lenv @ A[:, int(k) // st.DR, :] @ R[j + 1][:, int(k) % st.DR]) for k in pairs])
+    q = coef * z[inv]
     q = np.maximum(q, 0.0)
     with np.errstate(divide="ignore"):
         return np.log(q) - np.log(np.sum(q))
 
 
-def delta_energy(fg: FactorGraph, s: int, x: int, prefix) -> int:
-    """E_s(x) plus the pairwise terms of x with the fixed clusters."""
-    dE = int(fg.E_loc[s][x])
+def delta_energies(fg: FactorGraph, s: int, prefix) -> np.ndarray:
+    """E_s(x) plus the pairwise terms of x with the fixed clusters, for every
+    state x of site s (int64 [d_s])."""
+    dE = np.array(fg.E_loc[s], dtype=np.int64)
     for (m, n), e in fg.edges.items():
         if n == s:
-            dE += int(e.E[prefix[m], x])
+            dE = dE + (e.E[prefix[m]] if e.E is not None else e.Esub[e.sub_m[prefix[m]], e.sub_n])
     return dE
 
 
@@ -229,9 +241,10 @@ def solve(fg: FactorGraph, prm: Params, boundary=None) -> Result:
         n_cand = 0
         for b in beam:
             lc = log_conditional(p, B, i, j, b.lenv, b.R, b.states)
+            dEs = delta_energies(fg, s, b.states)
             for x in range(fg.d[s]):
                 st = b.states + (x,)
-                E = b.E + delta_energy(fg, s, x, b.states)
+                E = b.E + int(dEs[x])
                 key = tuple(st[t] for t in ks) if prm.merge else st
                 n_cand += 1
                 if drop_on:

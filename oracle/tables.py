@@ -20,6 +20,20 @@ Readings taken here:
   distinct rows of E_e numbered in order of first occurrence (x ascending);
   P_col likewise for columns.  The reduced table R_e satisfies
   E_e[x, y] == R_e[P_row[x], P_col[y]] for all x, y.
+
+``Sparsity`` (Sec. 3.1, Sec. 3.1.1: clusters of O(10-20) spins, Pegasus'
+24 and Zephyr's 16, for which explicit tensors are infeasible): a sparse
+edge never forms the d_m x d_n table.  The couplers of the edge touch only
+some spins of each cluster (positions ``pos_m`` in m, ``pos_n`` in n); the
+table is a function of those spins' configurations,
+E_e[x, y] = Esub[sub_m[x], sub_n[y]], with sub_m[x] = sum_k b_{pos_m[k]}(x) 2^k.
+Every configuration of the coupled spins occurs, so two states have equal
+rows of E_e exactly when their rows of Esub are equal, and the first state
+carrying a given configuration a (only a's spins set) grows with a: the
+projectors and the reduced table computed over the configurations a of the
+coupled spins are those of the full table (first-occurrence order
+included).  ``from_ising`` builds sparse edges for clusters of more than 8
+spins, or on request.
 """
 from __future__ import annotations
 
@@ -39,10 +53,36 @@ class InexactEnergy(ValueError):
 class Edge:
     m: int  # row-major-first site
     n: int
-    E: np.ndarray  # int64 [d_m, d_n]  full table
+    E: np.ndarray  # int64 [d_m, d_n]  full table (None on a sparse edge)
     R: np.ndarray  # int64 [Dm, Dn]    reduced table
     Pm: np.ndarray  # int64 [d_m]      row projector of site m
     Pn: np.ndarray  # int64 [d_n]      column projector of site n
+    # sparse edge (module header): E[x, y] = Esub[sub_m[x], sub_n[y]]
+    Esub: np.ndarray = None  # int64 [2^len(pos_m), 2^len(pos_n)]
+    pos_m: np.ndarray = None  # positions of the coupled spins in cluster m (ascending)
+    pos_n: np.ndarray = None
+    sub_m: np.ndarray = None  # int64 [d_m]
+    sub_n: np.ndarray = None  # int64 [d_n]
+
+    def value(self, xm, xn) -> int:
+        """E[xm, xn]."""
+        if self.E is not None:
+            return int(self.E[xm, xn])
+        return int(self.Esub[self.sub_m[xm], self.sub_n[xn]])
+
+    def min(self) -> int:
+        """min over all (xm, xn) of E (every coupled configuration occurs)."""
+        return int(self.E.min()) if self.E is not None else int(self.Esub.min())
+
+    def block(self, row_site: int, rs, cs) -> np.ndarray:
+        """The table seen from row_site (m: E, n: E^T) at states rs x cs."""
+        rs, cs = np.asarray(rs), np.asarray(cs)
+        if self.E is not None:
+            T = self.E if row_site == self.m else self.E.T
+            return T[np.ix_(rs, cs)]
+        if row_site == self.m:
+            return self.Esub[np.ix_(self.sub_m[rs], self.sub_n[cs])]
+        return self.Esub.T[np.ix_(self.sub_n[rs], self.sub_m[cs])]
 
 
 @dataclass
@@ -55,6 +95,7 @@ class FactorGraph:
     shift: int
     node_type: int
     spins_of_site: list = field(default_factory=list)  # Ising form only
+    sparse: bool = False  # Sparsity = Sparse: sparse edges, sites built by projection classes
 
     @property
     def n_sites(self):
@@ -81,24 +122,48 @@ def spins_of_state(k):
     return 2 * b - 1
 
 
+def _dedupe(rows):
+    """First-occurrence class of every row of ``rows`` and the class count."""
+    index = {}
+    P = np.empty(rows.shape[0], dtype=np.int64)
+    for x in range(rows.shape[0]):
+        key = np.ascontiguousarray(rows[x]).tobytes()
+        if key not in index:
+            index[key] = len(index)
+        P[x] = index[key]
+    return P, len(index)
+
+
 def project(E):
     """Distinct rows/columns of E in first-occurrence order (reading above)."""
-    def dedupe(rows):
-        index = {}
-        P = np.empty(rows.shape[0], dtype=np.int64)
-        for x in range(rows.shape[0]):
-            key = rows[x].tobytes()
-            if key not in index:
-                index[key] = len(index)
-            P[x] = index[key]
-        return P, len(index)
-
-    Pm, Dm = dedupe(E)
-    Pn, Dn = dedupe(E.T.copy())
+    Pm, Dm = _dedupe(E)
+    Pn, Dn = _dedupe(E.T.copy())
     first_m = np.array([int(np.argmax(Pm == a)) for a in range(Dm)])
     first_n = np.array([int(np.argmax(Pn == b)) for b in range(Dn)])
     R = E[np.ix_(first_m, first_n)]
     return R, Pm, Pn
+
+
+def sub_index(x, pos):
+    """Configuration index of the spins at positions ``pos`` in states x:
+    sum_k bit pos[k] of x, times 2^k."""
+    x = np.asarray(x, dtype=np.int64)
+    out = np.zeros_like(x)
+    for k, q in enumerate(pos):
+        out |= ((x >> int(q)) & 1) << k
+    return out
+
+
+def project_sparse(Esub, sub_m, sub_n):
+    """``project`` of the full table Esub[sub_m[x], sub_n[y]] computed on the
+    coupled configurations (module header): classes of the rows (columns) of
+    Esub in order of a (b) ascending, which is their order of first
+    occurrence over x (y) ascending."""
+    cm, Dm = _dedupe(Esub)
+    cn, Dn = _dedupe(Esub.T.copy())
+    first_a = np.array([int(np.argmax(cm == c)) for c in range(Dm)])
+    first_b = np.array([int(np.argmax(cn == c)) for c in range(Dn)])
+    return Esub[np.ix_(first_a, first_b)], cm[sub_m], cn[sub_n]
 
 
 def adjacent(node_type, rm, cm, rn, cn):
@@ -108,8 +173,10 @@ def adjacent(node_type, rm, cm, rn, cn):
     return max(dr, dc) == 1
 
 
-def from_ising(inst) -> FactorGraph:
-    """Eq. 2 -> Eq. 1: clusters of spins become Potts variables."""
+def from_ising(inst, sparse=None) -> FactorGraph:
+    """Eq. 2 -> Eq. 1: clusters of spins become Potts variables.  sparse:
+    True / False, or None for sparse edges when a cluster has more than 8
+    spins (module header)."""
     rows, cols = inst.grid_rows, inst.grid_cols
     shift = inst.energy_shift
     n_sites = rows * cols
@@ -125,8 +192,12 @@ def from_ising(inst) -> FactorGraph:
     pos_in_site = np.empty(inst.n_spins, dtype=np.int64)
     for s in range(n_sites):
         pos_in_site[spins_of_site[s]] = np.arange(len(spins_of_site[s]))
-    S = [spins_of_state(len(sp)) for sp in spins_of_site]
     d = [2 ** len(sp) for sp in spins_of_site]
+    if sparse is None:
+        sparse = max(len(sp) for sp in spins_of_site) > 8
+    if sparse:
+        return _from_ising_sparse(inst, rows, cols, shift, J, h, site_of_spin, spins_of_site, pos_in_site, d)
+    S = [spins_of_state(len(sp)) for sp in spins_of_site]
 
     E_loc = [S[s] @ h[spins_of_site[s]] for s in range(n_sites)]
     pair = {}
@@ -149,6 +220,53 @@ def from_ising(inst) -> FactorGraph:
         edges[(m, n)] = Edge(m, n, E, R, Pm, Pn)
     return FactorGraph(rows, cols, d, [np.asarray(t, dtype=np.int64) for t in E_loc], edges,
                        shift, inst.node_type, spins_of_site)
+
+
+def _spin_column(n_states, pos):
+    """Spin s = 2b - 1 at position pos of every state 0 .. n_states-1."""
+    return 2 * ((np.arange(n_states, dtype=np.int64) >> int(pos)) & 1) - 1
+
+
+def _from_ising_sparse(inst, rows, cols, shift, J, h, site_of_spin, spins_of_site, pos_in_site, d):
+    """``from_ising`` with sparse edges: local tables over every state of a
+    cluster, pairwise tables over the configurations of the coupled spins."""
+    n_sites = rows * cols
+    E_loc = []
+    xs = [np.arange(d[s], dtype=np.int32) for s in range(n_sites)]  # states (clusters of <= 30 spins)
+    for s in range(n_sites):
+        E = np.zeros(d[s], dtype=np.int64)
+        for q, spin in enumerate(spins_of_site[s]):
+            if h[spin] != 0:
+                E += h[spin] * (2 * ((xs[s] >> q) & 1) - 1)
+        E_loc.append(E)
+    couplers = {}
+    for e in range(len(J)):
+        i, j = int(inst.ei[e]), int(inst.ej[e])
+        si, sj = int(site_of_spin[i]), int(site_of_spin[j])
+        if si == sj:
+            # s_i s_j = +1 when the two bits agree, -1 otherwise
+            p, q = int(pos_in_site[i]), int(pos_in_site[j])
+            E_loc[si] += J[e] * (1 - 2 * (((xs[si] >> p) ^ (xs[si] >> q)) & 1))
+            continue
+        if si > sj:
+            si, sj, i, j = sj, si, j, i
+        if not adjacent(inst.node_type, si // cols, si % cols, sj // cols, sj % cols):
+            raise ValueError(f"coupling between non-neighbouring clusters {si} {sj}")
+        couplers.setdefault((si, sj), []).append((int(pos_in_site[i]), int(pos_in_site[j]), int(J[e])))
+    edges = {}
+    for (m, n), cl in sorted(couplers.items()):
+        pos_m = np.array(sorted({a for a, _, _ in cl}), dtype=np.int64)
+        pos_n = np.array(sorted({b for _, b, _ in cl}), dtype=np.int64)
+        A, B = 2 ** len(pos_m), 2 ** len(pos_n)
+        Esub = np.zeros((A, B), dtype=np.int64)
+        for a, b, Jv in cl:
+            ka, kb = int(np.searchsorted(pos_m, a)), int(np.searchsorted(pos_n, b))
+            Esub += Jv * np.outer(_spin_column(A, ka), _spin_column(B, kb))
+        sub_m = sub_index(np.arange(d[m]), pos_m)
+        sub_n = sub_index(np.arange(d[n]), pos_n)
+        R, Pm, Pn = project_sparse(Esub, sub_m, sub_n)
+        edges[(m, n)] = Edge(m, n, None, R, Pm, Pn, Esub, pos_m, pos_n, sub_m, sub_n)
+    return FactorGraph(rows, cols, d, E_loc, edges, shift, inst.node_type, spins_of_site, sparse=True)
 
 
 def from_potts(inst) -> FactorGraph:
@@ -182,7 +300,7 @@ def energy(fg: FactorGraph, x) -> int:
     x = [int(v) for v in x]
     E = sum(int(fg.E_loc[s][x[s]]) for s in range(fg.n_sites))
     for (m, n), e in fg.edges.items():
-        E += int(e.E[x[m], x[n]])
+        E += e.value(x[m], x[n])
     return E
 
 
