@@ -40,7 +40,11 @@ METRIC = "beam states/sec & time-to-solution vs plain FP64 GPU at equal best ene
 # from an ncu capture of mid-solve launches (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the instances one launch covers), for the
 # kernel as it is now; a kernel not listed here reports null.
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {
+    # the 8-warp kernel in a group of 8 instances: 17.4 MB read + 248.3 MB
+    # written per launch (almost all of it the environments it writes)
+    "k_renv_tc": (17.4e6 + 248.3e6) / 8,
+}
 
 # kernels whose products run on the tensor cores (split TF32: three TF32
 # passes per FP32-accurate multiply-add)
