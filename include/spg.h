@@ -178,6 +178,48 @@ int spg_params_default(spg_params* p);
 int spg_lattice_site_map(int32_t rows, int32_t cols, int32_t k, int32_t* site_map, int32_t* new_rows,
                          int32_t* new_cols);
 
+/* Clustered Hamiltonian on the host: the paper's
+ * potts_hamiltonian(ising_graph(inst); spectrum = full_spectrum,
+ * cluster_assignment_rule) (Sec. 2, Eq. 1 and 2; Sec. 3.1 and 3.1.1:
+ * Sparsity, the large clusters of Pegasus and Zephyr).  Host only, no device
+ * and no context.  The spins of each grid cell form one Potts variable with
+ * 2^k states, k <= SPG_MAX_HAMILTONIAN_SPINS (more than the solver's
+ * SPG_MAX_STATES: spg_problem_ising takes clusters of up to 8 spins); state
+ * x = sum_q b_q 2^q over the cluster's spins in ascending index, s = 2b - 1.
+ *   local table   E_s[x]: fields and couplings inside cluster s (int64, units
+ *                 of 2^-energy_shift);
+ *   edge k        one per pair of neighbouring clusters (m < n, row-major;
+ *                 edges in ascending (m, n)) with a coupling between them:
+ *                 reduced table R[Dm][Dn] (row-major) and projectors Pm[x]
+ *                 (d_m states), Pn[y] (d_n states) with
+ *                 E_e[x, y] = R[Pm[x]][Pn[y]]; Pm numbers the distinct rows of
+ *                 E_e in order of first occurrence (x ascending), Pn the
+ *                 columns.  E_e is never formed: it is built over the
+ *                 configurations of the spins its couplers touch (at most
+ *                 SPG_MAX_HAMILTONIAN_COUPLED per side).
+ * Inputs as spg_problem_ising (copied; J, h on the 2^-energy_shift grid, h
+ * may be NULL).  Returns SPG_EINVAL (sizes, NULL arrays, clusters or
+ * couplings off the grid, couplings between non-neighbouring clusters),
+ * SPG_EINEXACT, SPG_EUNSUPPORTED (a cluster or an edge side beyond the
+ * limits), SPG_ENOMEM.  The accessors copy into caller arrays, which may be
+ * NULL to query sizes first. */
+#define SPG_MAX_HAMILTONIAN_SPINS 24
+#define SPG_MAX_HAMILTONIAN_COUPLED 12
+typedef struct spg_hamiltonian spg_hamiltonian;
+int spg_potts_hamiltonian(int32_t n_spins, int32_t n_edges, const int32_t* ei, const int32_t* ej, const double* J,
+                          const double* h, const int32_t* cluster_of_spin, int32_t grid_rows, int32_t grid_cols,
+                          const int32_t* cluster_row, const int32_t* cluster_col, int32_t energy_shift,
+                          int32_t node_type, spg_hamiltonian** out);
+/* Number of sites (grid cells) and of edges. */
+int spg_hamiltonian_size(const spg_hamiltonian* H, int32_t* n_sites, int32_t* n_edges);
+/* States of site s (2^k) and, if E is not NULL, its local table E[states]. */
+int spg_hamiltonian_local(const spg_hamiltonian* H, int32_t site, int64_t* n_states, int64_t* E);
+/* Edge k: its sites m < n, reduced sizes Dm, Dn and, where not NULL, R
+ * [Dm*Dn], Pm [states of m], Pn [states of n]. */
+int spg_hamiltonian_edge(const spg_hamiltonian* H, int32_t k, int32_t* m, int32_t* n, int32_t* Dm, int32_t* Dn,
+                         int64_t* R, int32_t* Pm, int32_t* Pn);
+void spg_hamiltonian_destroy(spg_hamiltonian* H);
+
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
  * (may be NULL: the library creates and owns a non-blocking stream).  The
  * context owns its device workspace, grown on demand and reused. */

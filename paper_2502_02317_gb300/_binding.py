@@ -105,6 +105,12 @@ def _load():
         "spg_inject_alloc_failure": (C.c_int, [I32]),
         "spg_profile": (C.c_int, [P, C.c_int]),
         "spg_profile_report": (C.c_int, [P, C.c_char_p, C.c_size_t]),
+        "spg_potts_hamiltonian": (C.c_int, [I32, I32, pI32, pI32, pD, pD, pI32, I32, I32, pI32, pI32, I32, I32,
+                                            C.POINTER(P)]),
+        "spg_hamiltonian_size": (C.c_int, [P, pI32, pI32]),
+        "spg_hamiltonian_local": (C.c_int, [P, I32, pI64, pI64]),
+        "spg_hamiltonian_edge": (C.c_int, [P, I32, pI32, pI32, pI32, pI32, pI64, pI32, pI32]),
+        "spg_hamiltonian_destroy": (None, [P]),
         "spg_autotune_set": (C.c_int, [I32, pI32]),
         "spg_autotune_clear": (C.c_int, []),
         "spg_autotune_report": (C.c_int, [pI32, C.c_char_p, C.c_size_t]),
@@ -267,6 +273,50 @@ def spg_problem_ising(ctx: Context, inst) -> Problem:
                                     inst.grid_rows, inst.grid_cols, _ptr(cr, C.c_int32), _ptr(cc, C.c_int32),
                                     inst.energy_shift, inst.node_type, C.byref(out)))
     return Problem(ctx, out)
+
+
+def spg_potts_hamiltonian(inst) -> dict:
+    """The clustered Hamiltonian of an Ising instance, built by the library
+    on the host (no device): {"E_loc": [int64 [d_s] per site], "edges":
+    {(m, n): (R int64 [Dm, Dn], Pm int32 [d_m], Pn int32 [d_n])}}."""
+    ei = np.ascontiguousarray(inst.ei, np.int32)
+    ej = np.ascontiguousarray(inst.ej, np.int32)
+    J = np.ascontiguousarray(inst.J, np.float64)
+    h = np.ascontiguousarray(inst.h, np.float64)
+    cos = np.ascontiguousarray(inst.cluster_of_spin, np.int32)
+    cr = np.ascontiguousarray(inst.cluster_row, np.int32)
+    cc = np.ascontiguousarray(inst.cluster_col, np.int32)
+    H = C.c_void_p()
+    rc = lib.spg_potts_hamiltonian(inst.n_spins, len(ei), _ptr(ei, C.c_int32), _ptr(ej, C.c_int32),
+                                   _ptr(J, C.c_double), _ptr(h, C.c_double), _ptr(cos, C.c_int32), inst.grid_rows,
+                                   inst.grid_cols, _ptr(cr, C.c_int32), _ptr(cc, C.c_int32), inst.energy_shift,
+                                   inst.node_type, C.byref(H))
+    if rc != 0:
+        raise SpgError(rc, "spg_potts_hamiltonian refused the instance")
+    try:
+        ns, ne = C.c_int32(), C.c_int32()
+        lib.spg_hamiltonian_size(H, C.byref(ns), C.byref(ne))
+        E_loc, d = [], []
+        for s in range(ns.value):
+            n = C.c_int64()
+            lib.spg_hamiltonian_local(H, s, C.byref(n), None)
+            E = np.empty(n.value, np.int64)
+            lib.spg_hamiltonian_local(H, s, None, _ptr(E, C.c_int64))
+            E_loc.append(E)
+            d.append(n.value)
+        edges = {}
+        for k in range(ne.value):
+            m, n, Dm, Dn = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+            lib.spg_hamiltonian_edge(H, k, C.byref(m), C.byref(n), C.byref(Dm), C.byref(Dn), None, None, None)
+            R = np.empty((Dm.value, Dn.value), np.int64)
+            Pm = np.empty(d[m.value], np.int32)
+            Pn = np.empty(d[n.value], np.int32)
+            lib.spg_hamiltonian_edge(H, k, None, None, None, None, _ptr(R, C.c_int64), _ptr(Pm, C.c_int32),
+                                     _ptr(Pn, C.c_int32))
+            edges[(m.value, n.value)] = (R, Pm, Pn)
+        return {"E_loc": E_loc, "edges": edges}
+    finally:
+        lib.spg_hamiltonian_destroy(H)
 
 
 def spg_problem_potts(ctx: Context, inst) -> Problem:

@@ -1,0 +1,72 @@
+"""The library's clustered Hamiltonian (spg_potts_hamiltonian, host only: the
+paper's potts_hamiltonian, Sec. 2 Eq. 1-2, Sec. 3.1 Sparsity, Sec. 3.1.1
+large clusters) against the oracle's tables, bit for bit, on the CPU: local
+tables, the set of edges, reduced tables and projectors, for Chimera cells
+(dense oracle tables) and for cells of 16 (Zephyr) and 24 (Pegasus) spins
+(sparse oracle tables); and the refusals of inputs outside its limits."""
+import numpy as np
+import pytest
+
+import instances as I
+from oracle import tables
+
+CASES = {
+    "chimera_pm1": lambda: I.chimera(3, 1),
+    "chimera_gauss": lambda: I.chimera(3, 2, couplings="gauss", h_sigma=0.1),
+    "king_ising": lambda: I.king_ising(3, 3, 2, 5),
+    "cells8_king": lambda: I.large_cells(2, 2, 8, 3),
+    "cells16_king": lambda: I.large_cells(2, 2, 16, 21, links=3),
+    "cells16_square": lambda: I.large_cells(2, 3, 16, 23, links=2, node_type=I.SQUARE),
+    "cells24_ring": lambda: I.large_cells(1, 2, 24, 22, links=3, intra="ring"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hamiltonian_equals_the_oracle_tables(name):
+    import paper_2502_02317_gb300 as spg
+    inst = CASES[name]()
+    H = spg.spg_potts_hamiltonian(inst)
+    fg = tables.from_ising(inst)
+    assert len(H["E_loc"]) == fg.n_sites
+    for s in range(fg.n_sites):
+        np.testing.assert_array_equal(H["E_loc"][s], fg.E_loc[s])
+    assert sorted(H["edges"]) == sorted(fg.edges)
+    for k, e in fg.edges.items():
+        R, Pm, Pn = H["edges"][k]
+        np.testing.assert_array_equal(R, e.R)
+        np.testing.assert_array_equal(Pm, e.Pm)
+        np.testing.assert_array_equal(Pn, e.Pn)
+
+
+def _row_of_cells(k, couplers, J=1.0, cols=2, col_of_cell=None):
+    """Cells of k spins on a 1 x cols grid (cell c on column col_of_cell[c]);
+    couplers (c, a, c', b) between spin a of cell c and spin b of cell c'."""
+    col_of_cell = list(range(cols)) if col_of_cell is None else col_of_cell
+    n = len(col_of_cell)
+    ei = np.array([c * k + a for c, a, _, _ in couplers], np.int32)
+    ej = np.array([c2 * k + b for _, _, c2, b in couplers], np.int32)
+    return I.IsingInstance(n * k, ei, ej, np.full(len(couplers), J), np.zeros(n * k),
+                           np.repeat(np.arange(n, dtype=np.int32), k), 1, cols, np.zeros(n, np.int32),
+                           np.array(col_of_cell, np.int32), 0, I.KING)
+
+
+def test_hamiltonian_refusals():
+    import paper_2502_02317_gb300 as spg
+
+    def code(inst):
+        with pytest.raises(spg.SpgError) as e:
+            spg.spg_potts_hamiltonian(inst)
+        return e.value.code
+
+    # 26 spins in one cluster: beyond SPG_MAX_HAMILTONIAN_SPINS (refused before allocating 2^26 states)
+    assert code(_row_of_cells(26, [(0, 0, 1, 0)])) == spg.SPG_EUNSUPPORTED
+    # 13 coupled spins on each side of one edge: beyond SPG_MAX_HAMILTONIAN_COUPLED
+    assert code(_row_of_cells(14, [(0, q, 1, q) for q in range(13)])) == spg.SPG_EUNSUPPORTED
+    # J off the 2^-shift grid
+    assert code(_row_of_cells(4, [(0, 0, 1, 0)], J=0.3)) == spg.SPG_EINEXACT
+    # cells on columns 0 and 2 are not grid neighbours
+    assert code(_row_of_cells(4, [(0, 0, 1, 0)], cols=3, col_of_cell=[0, 2, 1])) == spg.SPG_EINVAL
+    # two clusters on one grid cell
+    assert code(_row_of_cells(4, [(0, 0, 1, 0)], col_of_cell=[0, 0])) == spg.SPG_EINVAL
+    # within the limits the same shapes build
+    assert len(spg.spg_potts_hamiltonian(_row_of_cells(12, [(0, q, 1, q) for q in range(12)]))["edges"]) == 1
