@@ -218,6 +218,31 @@ int spg_hamiltonian_local(const spg_hamiltonian* H, int32_t site, int64_t* n_sta
  * [Dm*Dn], Pm [states of m], Pn [states of n]. */
 int spg_hamiltonian_edge(const spg_hamiltonian* H, int32_t k, int32_t* m, int32_t* n, int32_t* Dm, int32_t* Dn,
                          int64_t* R, int32_t* Pm, int32_t* Pn);
+/* Joint projections of site s = (i, j) for its PEPS tensor (Sec. 2, Fig. 1(c);
+ * Sec. 3.1 Sparsity): the classes of equal table rows of a state over a set
+ * of its edges, numbered in order of first occurrence (x ascending), one
+ * class when the set has no edge:
+ *   SPG_CLASS_L: edges to (i, j-1) and (i-1, j-1)   SPG_CLASS_U: (i-1, j)
+ *   SPG_CLASS_R: edges to (i, j+1) and (i-1, j+1)   SPG_CLASS_G: (i+1, j+1)
+ *   SPG_CLASS_D: edges to (i+1, j-1), (i+1, j) and (i+1, j+1).
+ * They are found over the configurations of the spins those edges couple
+ * (at most 20).  Writes the class count and, where not NULL, P[states of s]
+ * and reps[class count] (the first state of each class). */
+#define SPG_CLASS_L 0
+#define SPG_CLASS_U 1
+#define SPG_CLASS_R 2
+#define SPG_CLASS_D 3
+#define SPG_CLASS_G 4
+int spg_hamiltonian_classes(const spg_hamiltonian* H, int32_t site, int32_t which, int32_t* n_classes, int32_t* P,
+                            int32_t* reps);
+/* Class weights of site s at inverse temperature beta: C[h][v][r][d] = sum
+ * over the states x with (P_L, P_U, P_R, P_D)(x) = (h, v, r, d) of
+ * exp(-beta 2^-energy_shift (E_s[x] - min E_s)) (row-major, NL*NU*NR*ND
+ * doubles).  With the Boltzmann factors of the reduced tables this is the
+ * whole site tensor: W[l, r, u, d] = sum_{h, v} b_left[l][h] b_up[u][v]
+ * C[h][v][r][d] (times the anti-diagonal factor on king's graphs), so no
+ * tensor over the 2^k states is formed.  SPG_EINVAL for beta <= 0. */
+int spg_hamiltonian_class_weights(const spg_hamiltonian* H, int32_t site, double beta, double* C);
 void spg_hamiltonian_destroy(spg_hamiltonian* H);
 
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t

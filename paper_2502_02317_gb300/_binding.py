@@ -110,6 +110,8 @@ def _load():
         "spg_hamiltonian_size": (C.c_int, [P, pI32, pI32]),
         "spg_hamiltonian_local": (C.c_int, [P, I32, pI64, pI64]),
         "spg_hamiltonian_edge": (C.c_int, [P, I32, pI32, pI32, pI32, pI32, pI64, pI32, pI32]),
+        "spg_hamiltonian_classes": (C.c_int, [P, I32, I32, pI32, pI32, pI32]),
+        "spg_hamiltonian_class_weights": (C.c_int, [P, I32, D, pD]),
         "spg_hamiltonian_destroy": (None, [P]),
         "spg_autotune_set": (C.c_int, [I32, pI32]),
         "spg_autotune_clear": (C.c_int, []),
@@ -275,10 +277,73 @@ def spg_problem_ising(ctx: Context, inst) -> Problem:
     return Problem(ctx, out)
 
 
-def spg_potts_hamiltonian(inst) -> dict:
+class Hamiltonian:
     """The clustered Hamiltonian of an Ising instance, built by the library
-    on the host (no device): {"E_loc": [int64 [d_s] per site], "edges":
-    {(m, n): (R int64 [Dm, Dn], Pm int32 [d_m], Pn int32 [d_n])}}."""
+    on the host (spg_potts_hamiltonian; no device).  E_loc: int64 [d_s] per
+    site; edges: {(m, n): (R int64 [Dm, Dn], Pm int32 [d_m], Pn int32
+    [d_n])}; classes(s, which) and class_weights(s, beta) as in
+    include/spg.h."""
+
+    L, U, R, D, G = 0, 1, 2, 3, 4
+
+    def __init__(self, h):
+        self.h = h
+        ns, ne = C.c_int32(), C.c_int32()
+        lib.spg_hamiltonian_size(h, C.byref(ns), C.byref(ne))
+        self.E_loc = []
+        for s in range(ns.value):
+            n = C.c_int64()
+            lib.spg_hamiltonian_local(h, s, C.byref(n), None)
+            E = np.empty(n.value, np.int64)
+            lib.spg_hamiltonian_local(h, s, None, _ptr(E, C.c_int64))
+            self.E_loc.append(E)
+        self.edges = {}
+        for k in range(ne.value):
+            m, n, Dm, Dn = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+            lib.spg_hamiltonian_edge(h, k, C.byref(m), C.byref(n), C.byref(Dm), C.byref(Dn), None, None, None)
+            R = np.empty((Dm.value, Dn.value), np.int64)
+            Pm = np.empty(len(self.E_loc[m.value]), np.int32)
+            Pn = np.empty(len(self.E_loc[n.value]), np.int32)
+            lib.spg_hamiltonian_edge(h, k, None, None, None, None, _ptr(R, C.c_int64), _ptr(Pm, C.c_int32),
+                                     _ptr(Pn, C.c_int32))
+            self.edges[(m.value, n.value)] = (R, Pm, Pn)
+
+    def classes(self, site: int, which: int):
+        """(P int32 [d_site], reps int32 [n_classes]) of joint projection
+        `which` (Hamiltonian.L, U, R, D, G)."""
+        nc = C.c_int32()
+        rc = lib.spg_hamiltonian_classes(self.h, site, which, C.byref(nc), None, None)
+        if rc != 0:
+            raise SpgError(rc, "spg_hamiltonian_classes")
+        P = np.empty(len(self.E_loc[site]), np.int32)
+        reps = np.empty(nc.value, np.int32)
+        lib.spg_hamiltonian_classes(self.h, site, which, None, _ptr(P, C.c_int32), _ptr(reps, C.c_int32))
+        return P, reps
+
+    def class_weights(self, site: int, beta: float):
+        """C [NL, NU, NR, ND] (float64): the summed state weights per class
+        tuple."""
+        dims = [len(self.classes(site, w)[1]) for w in (self.L, self.U, self.R, self.D)]
+        Cw = np.empty(dims, np.float64)
+        rc = lib.spg_hamiltonian_class_weights(self.h, site, float(beta), _ptr(Cw, C.c_double))
+        if rc != 0:
+            raise SpgError(rc, "spg_hamiltonian_class_weights")
+        return Cw
+
+    def close(self):
+        if self.h:
+            lib.spg_hamiltonian_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spg_potts_hamiltonian(inst) -> Hamiltonian:
+    """spg_potts_hamiltonian of an Ising instance (host only)."""
     ei = np.ascontiguousarray(inst.ei, np.int32)
     ej = np.ascontiguousarray(inst.ej, np.int32)
     J = np.ascontiguousarray(inst.J, np.float64)
@@ -293,30 +358,7 @@ def spg_potts_hamiltonian(inst) -> dict:
                                    inst.node_type, C.byref(H))
     if rc != 0:
         raise SpgError(rc, "spg_potts_hamiltonian refused the instance")
-    try:
-        ns, ne = C.c_int32(), C.c_int32()
-        lib.spg_hamiltonian_size(H, C.byref(ns), C.byref(ne))
-        E_loc, d = [], []
-        for s in range(ns.value):
-            n = C.c_int64()
-            lib.spg_hamiltonian_local(H, s, C.byref(n), None)
-            E = np.empty(n.value, np.int64)
-            lib.spg_hamiltonian_local(H, s, None, _ptr(E, C.c_int64))
-            E_loc.append(E)
-            d.append(n.value)
-        edges = {}
-        for k in range(ne.value):
-            m, n, Dm, Dn = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-            lib.spg_hamiltonian_edge(H, k, C.byref(m), C.byref(n), C.byref(Dm), C.byref(Dn), None, None, None)
-            R = np.empty((Dm.value, Dn.value), np.int64)
-            Pm = np.empty(d[m.value], np.int32)
-            Pn = np.empty(d[n.value], np.int32)
-            lib.spg_hamiltonian_edge(H, k, None, None, None, None, _ptr(R, C.c_int64), _ptr(Pm, C.c_int32),
-                                     _ptr(Pn, C.c_int32))
-            edges[(m.value, n.value)] = (R, Pm, Pn)
-        return {"E_loc": E_loc, "edges": edges}
-    finally:
-        lib.spg_hamiltonian_destroy(H)
+    return Hamiltonian(H)
 
 
 def spg_problem_potts(ctx: Context, inst) -> Problem:

@@ -22,15 +22,18 @@
 #include "spg.h"
 
 struct spg_hamiltonian {
-  int rows = 0, cols = 0;
+  int rows = 0, cols = 0, shift = 0;
   std::vector<int> k;                      // spins per site
   std::vector<std::vector<int64_t>> E;     // local tables
   struct Edge {
     int m = 0, n = 0, Dm = 0, Dn = 0;
     std::vector<int64_t> R;
     std::vector<int32_t> Pm, Pn;
+    std::vector<int> Sm, Sn;               // positions of the coupled spins in m and n
+    std::vector<int64_t> T;                // energy over their configurations [2^|Sm|][2^|Sn|]
   };
   std::vector<Edge> edges;
+  std::map<std::pair<int, int>, int> edge_of;  // (m, n) -> index in edges
 };
 
 namespace {
@@ -111,6 +114,7 @@ extern "C" int spg_potts_hamiltonian(int32_t n_spins, int32_t n_edges, const int
     }
     H->rows = grid_rows;
     H->cols = grid_cols;
+    H->shift = energy_shift;
     H->k.resize(n);
     H->E.resize(n);
     for (int s = 0; s < n && rc == SPG_OK; ++s) {
@@ -203,6 +207,10 @@ extern "C" int spg_potts_hamiltonian(int32_t n_spins, int32_t n_edges, const int
       e.Pn.resize(H->E[e.n].size());
       for (int64_t x = 0; x < (int64_t)e.Pm.size(); ++x) e.Pm[x] = cm[sub_of(x, Sm)];
       for (int64_t y = 0; y < (int64_t)e.Pn.size(); ++y) e.Pn[y] = cn[sub_of(y, Sn)];
+      e.Sm = Sm;
+      e.Sn = Sn;
+      e.T.swap(T);
+      H->edge_of[{e.m, e.n}] = (int)H->edges.size();
       H->edges.push_back(std::move(e));
     }
   } catch (const std::bad_alloc&) {
@@ -246,3 +254,114 @@ extern "C" int spg_hamiltonian_edge(const spg_hamiltonian* H, int32_t k, int32_t
 }
 
 extern "C" void spg_hamiltonian_destroy(spg_hamiltonian* H) { delete H; }
+
+namespace {
+
+// Joint projection `which` of site s (include/spg.h spg_hamiltonian_classes):
+// the class of every state and the first state of every class.  The key of
+// an interface configuration c (the spins coupled by the projection's edges,
+// ascending) is the tuple of its rows of the edges' configuration tables;
+// classes in order of c ascending, which is the order of first occurrence
+// over the states (the first state carrying c grows with c).
+int site_classes(const spg_hamiltonian* H, int s, int which, std::vector<int32_t>& P, std::vector<int32_t>& reps) {
+  const int cols = H->cols, rows = H->rows, i = s / cols, j = s % cols;
+  auto at = [&](int ii, int jj) { return (ii >= 0 && ii < rows && jj >= 0 && jj < cols) ? ii * cols + jj : -1; };
+  std::vector<int> nb;
+  switch (which) {
+    case SPG_CLASS_L: nb = {at(i, j - 1), at(i - 1, j - 1)}; break;
+    case SPG_CLASS_U: nb = {at(i - 1, j)}; break;
+    case SPG_CLASS_R: nb = {at(i, j + 1), at(i - 1, j + 1)}; break;
+    case SPG_CLASS_D: nb = {at(i + 1, j - 1), at(i + 1, j), at(i + 1, j + 1)}; break;
+    case SPG_CLASS_G: nb = {at(i + 1, j + 1)}; break;
+    default: return SPG_EINVAL;
+  }
+  struct Part {
+    const spg_hamiltonian::Edge* e;
+    bool row;  // s is the edge's row variable (m)
+  };
+  std::vector<Part> parts;
+  std::vector<int> U;
+  for (int t : nb) {
+    if (t < 0) continue;
+    auto it = H->edge_of.find({std::min(s, t), std::max(s, t)});
+    if (it == H->edge_of.end()) continue;
+    const spg_hamiltonian::Edge& e = H->edges[it->second];
+    parts.push_back({&e, s == e.m});
+    const std::vector<int>& S = s == e.m ? e.Sm : e.Sn;
+    U.insert(U.end(), S.begin(), S.end());
+  }
+  std::sort(U.begin(), U.end());
+  U.erase(std::unique(U.begin(), U.end()), U.end());
+  if (U.size() > 20) return SPG_EUNSUPPORTED;
+  const int64_t nc = (int64_t)1 << U.size();
+  std::vector<int32_t> cls((size_t)nc);
+  std::vector<int64_t> first;
+  std::map<std::vector<int64_t>, int32_t> index;
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t x = 0;  // the first state carrying configuration c
+    for (size_t q = 0; q < U.size(); ++q) x |= ((c >> q) & 1) << U[q];
+    std::vector<int64_t> key;
+    for (const Part& p : parts) {
+      const spg_hamiltonian::Edge& e = *p.e;
+      const int64_t na = (int64_t)1 << e.Sm.size(), nbb = (int64_t)1 << e.Sn.size();
+      if (p.row) {
+        const int64_t a = sub_of(x, e.Sm);
+        key.insert(key.end(), e.T.begin() + a * nbb, e.T.begin() + (a + 1) * nbb);
+      } else {
+        const int64_t b = sub_of(x, e.Sn);
+        for (int64_t a = 0; a < na; ++a) key.push_back(e.T[a * nbb + b]);
+      }
+    }
+    auto it = index.find(key);
+    if (it == index.end()) {
+      it = index.emplace(std::move(key), (int32_t)first.size()).first;
+      first.push_back(x);
+    }
+    cls[(size_t)c] = it->second;
+  }
+  const int64_t d = (int64_t)H->E[s].size();
+  P.resize((size_t)d);
+  for (int64_t x = 0; x < d; ++x) P[(size_t)x] = cls[(size_t)sub_of(x, U)];
+  reps.assign(first.begin(), first.end());
+  return SPG_OK;
+}
+
+}  // namespace
+
+extern "C" int spg_hamiltonian_classes(const spg_hamiltonian* H, int32_t site, int32_t which, int32_t* n_classes,
+                                       int32_t* P, int32_t* reps) {
+  if (!H || site < 0 || site >= (int32_t)H->E.size()) return SPG_EINVAL;
+  std::vector<int32_t> Pv, rv;
+  try {
+    const int rc = site_classes(H, site, which, Pv, rv);
+    if (rc != SPG_OK) return rc;
+  } catch (const std::bad_alloc&) {
+    return SPG_ENOMEM;
+  }
+  if (n_classes) *n_classes = (int32_t)rv.size();
+  if (P) std::memcpy(P, Pv.data(), sizeof(int32_t) * Pv.size());
+  if (reps) std::memcpy(reps, rv.data(), sizeof(int32_t) * rv.size());
+  return SPG_OK;
+}
+
+extern "C" int spg_hamiltonian_class_weights(const spg_hamiltonian* H, int32_t site, double beta, double* C) {
+  if (!H || site < 0 || site >= (int32_t)H->E.size() || !C || !(beta > 0.0)) return SPG_EINVAL;
+  try {
+    std::vector<int32_t> P[4], reps;
+    for (int w = 0; w < 4; ++w) {
+      const int rc = site_classes(H, site, w, P[w], reps);
+      if (rc != SPG_OK) return rc;
+    }
+    int64_t N[4];
+    for (int w = 0; w < 4; ++w) N[w] = 1 + *std::max_element(P[w].begin(), P[w].end());
+    const std::vector<int64_t>& E = H->E[site];
+    const int64_t mn = *std::min_element(E.begin(), E.end());
+    const double bu = beta * std::ldexp(1.0, -H->shift);
+    std::fill(C, C + N[0] * N[1] * N[2] * N[3], 0.0);
+    for (size_t x = 0; x < E.size(); ++x)
+      C[((P[0][x] * N[1] + P[1][x]) * N[2] + P[2][x]) * N[3] + P[3][x]] += std::exp(-bu * (double)(E[x] - mn));
+  } catch (const std::bad_alloc&) {
+    return SPG_ENOMEM;
+  }
+  return SPG_OK;
+}

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import instances as I
-from oracle import tables
+from oracle import peps, tables
 
 CASES = {
     "chimera_pm1": lambda: I.chimera(3, 1),
@@ -27,15 +27,45 @@ def test_hamiltonian_equals_the_oracle_tables(name):
     inst = CASES[name]()
     H = spg.spg_potts_hamiltonian(inst)
     fg = tables.from_ising(inst)
-    assert len(H["E_loc"]) == fg.n_sites
+    assert len(H.E_loc) == fg.n_sites
     for s in range(fg.n_sites):
-        np.testing.assert_array_equal(H["E_loc"][s], fg.E_loc[s])
-    assert sorted(H["edges"]) == sorted(fg.edges)
+        np.testing.assert_array_equal(H.E_loc[s], fg.E_loc[s])
+    assert sorted(H.edges) == sorted(fg.edges)
     for k, e in fg.edges.items():
-        R, Pm, Pn = H["edges"][k]
+        R, Pm, Pn = H.edges[k]
         np.testing.assert_array_equal(R, e.R)
         np.testing.assert_array_equal(Pm, e.Pm)
         np.testing.assert_array_equal(Pn, e.Pn)
+
+
+@pytest.mark.parametrize("name", [n for n in CASES if n != "cells24_ring"])
+def test_site_classes_and_class_weights_give_the_oracle_site_tensors(name):
+    """The joint projections of every site equal the oracle's PEPS site data
+    (classes and representatives), and the site tensor rebuilt from the
+    library's class weights, W[l, (a', g'), u, d] = b_ad[a, u] [g' = P_G(u)]
+    sum_{h, v} b_left[l, h] b_up[u, v] C[h, v, a', d] with the oracle's
+    Boltzmann factors, equals the oracle's W."""
+    import paper_2502_02317_gb300 as spg
+    inst = CASES[name]()
+    beta = 0.8
+    H = spg.spg_potts_hamiltonian(inst)
+    p = peps.build(tables.from_ising(inst), beta)
+    for s, st in enumerate(p.sites):
+        for which, field in ((H.L, "PL"), (H.U, "PU"), (H.R, "PR"), (H.D, "PD"), (H.G, "PG")):
+            P, reps = H.classes(s, which)
+            np.testing.assert_array_equal(P, getattr(st, field))
+            assert len(reps) == int(P.max()) + 1 and np.array_equal(P[reps], np.arange(len(reps)))
+            if field in ("PR", "PD"):
+                np.testing.assert_array_equal(reps, st.repR if field == "PR" else st.repD)
+        Cw = H.class_weights(s, beta)
+        T = np.einsum("lh,uv,hvrd->lurd", st.b_left, st.b_up, Cw)
+        W = np.zeros((st.DL, st.DR, st.DU, st.ND))
+        a = np.arange(st.DL) // st.Gin
+        for u in range(st.DU):
+            cols = np.arange(st.NR) * st.Gout + int(st.g_of_u[u])
+            W[:, cols, u, :] = st.b_ad[a, u][:, None, None] * T[:, u, :, :]
+        ref = peps.mpo_site(st)
+        np.testing.assert_allclose(W, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
 
 
 def _row_of_cells(k, couplers, J=1.0, cols=2, col_of_cell=None):
@@ -69,4 +99,4 @@ def test_hamiltonian_refusals():
     # two clusters on one grid cell
     assert code(_row_of_cells(4, [(0, 0, 1, 0)], col_of_cell=[0, 0])) == spg.SPG_EINVAL
     # within the limits the same shapes build
-    assert len(spg.spg_potts_hamiltonian(_row_of_cells(12, [(0, q, 1, q) for q in range(12)]))["edges"]) == 1
+    assert len(spg.spg_potts_hamiltonian(_row_of_cells(12, [(0, q, 1, q) for q in range(12)])).edges) == 1
