@@ -398,6 +398,23 @@ int spg_result_info(spg_result* res, spg_info* info);
  * applied, when dE <= droplet_energy and it differs from the winner and from
  * every droplet kept so far in more than droplet_hamming variables. */
 int spg_result_droplets(spg_result* res, int32_t* n, int64_t* energies, uint16_t* states);
+
+/* Diversity of a set of solutions (Fig. 3 (c), (f)): how many solutions lie
+ * within approximation ratio a_r of the best energy and differ pairwise in
+ * more than N/2 variables.  Host only.  vars [n x N] (row-major int32: the
+ * spins of each solution, or its Potts states; the caller decodes cluster
+ * states into spins for a count over spins), energies [n] (int64), e_best:
+ * the best energy considered (not necessarily in the set).  Readings: the
+ * printed ratio E - E_best < a_r 2 E_best, which no negative E_best meets,
+ * is taken as E - E_best < 2 a_r |E_best| (strict); the pairwise condition
+ * by first fit: the solutions within the ratio in ascending (energy,
+ * lexicographic vars, index) order, each counted when it differs in more than N/2
+ * variables (2 d > N) from every one counted before it (the rule of the
+ * droplets' Hamming cutoff).  Writes the count and, where not NULL, the
+ * counted solutions' indices in counting order (chosen [n]).  SPG_EINVAL for
+ * n < 0, N < 1, a_r < 0 or NULL arrays with n > 0. */
+int spg_diversity(int32_t n, int32_t N, const int32_t* vars, const int64_t* energies, int64_t e_best, double a_r,
+                  int32_t* count, int32_t* chosen);
 void spg_result_destroy(spg_result* res);
 
 /* Teacher-forced conditional marginals (Sec. 2, Fig. 1(d)): for each of the

@@ -30,6 +30,9 @@ no blocking, fusion or reordering beyond what each step states:
 * ``lattice``  -- Sec. 3.1 (lattice transformations): the instance solved on
   each of the 8 rotations / reflections of the grid, states mapped back to
   the original sites, the best of 8 kept.
+* ``metrics``  -- Fig. 3 (c), (f): the diversity of a set of solutions
+  (within an approximation ratio of the best energy, pairwise more than N/2
+  variables apart).
 * ``exact``    -- pins that do not use any of the above: brute force over all
   spin configurations (<= 24 spins), spin-level row transfer matrices for
   width-3 Chimera strips (exact log Z and exact ground energy), and sums over

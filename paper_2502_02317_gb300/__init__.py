@@ -22,6 +22,7 @@ from ._binding import (SPG_ECUDA, SPG_EINEXACT, SPG_EINVAL, SPG_ENOMEM, SPG_ENUM
                        spg_problem_update_ising, spg_set_warm_start, spg_solve, spg_solve_batch, spg_solve_group,
                        spg_solve_lattice8, spg_sweep_trace, spg_tc_product, spg_truncate, spg_autotune_clear,
                        spg_autotune_report, spg_autotune_set, spg_potts_hamiltonian, Hamiltonian,
+                       spg_diversity,
                        spg_truncate_static, spg_warm_features)
 
 __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_problem_ising",
@@ -31,6 +32,6 @@ __all__ = ["Context", "Problem", "Result", "SpgError", "lib", "params", "spg_pro
            "spg_sweep_trace", "SPG_WS_FEATURES", "spg_peak_probe", "spg_check_bounded_wait",
            "spg_inject_alloc_failure", "spg_solve_lattice8", "spg_problem_update_ising",
            "spg_autotune_set", "spg_autotune_clear", "spg_autotune_report", "SPG_TUNE_OFF", "SPG_TUNE_ON",
-           "SPG_TUNE_FORCE", "spg_potts_hamiltonian", "Hamiltonian",
+           "SPG_TUNE_FORCE", "spg_potts_hamiltonian", "Hamiltonian", "spg_diversity",
            "SPG_FP64", "SPG_MIXED", "SPG_SQUARE", "SPG_KING", "SPG_EINVAL", "SPG_EINEXACT", "SPG_ENOMEM",
            "SPG_ECUDA", "SPG_ETIMEOUT", "SPG_ENUMERIC", "SPG_EUNSUPPORTED"]

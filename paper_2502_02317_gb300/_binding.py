@@ -113,6 +113,7 @@ def _load():
         "spg_hamiltonian_classes": (C.c_int, [P, I32, I32, pI32, pI32, pI32]),
         "spg_hamiltonian_class_weights": (C.c_int, [P, I32, D, pD]),
         "spg_hamiltonian_destroy": (None, [P]),
+        "spg_diversity": (C.c_int, [I32, I32, pI32, pI64, C.c_int64, D, pI32, pI32]),
         "spg_autotune_set": (C.c_int, [I32, pI32]),
         "spg_autotune_clear": (C.c_int, []),
         "spg_autotune_report": (C.c_int, [pI32, C.c_char_p, C.c_size_t]),
@@ -479,6 +480,21 @@ def spg_profile_report(ctx: Context) -> dict:
     buf = C.create_string_buffer(1 << 16)
     ctx.check(lib.spg_profile_report(ctx.h, buf, len(buf)))
     return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def spg_diversity(solutions, energies, e_best: int, a_r: float = 0.01):
+    """(count, indices in counting order) of spg_diversity: solutions [n, N]
+    (spins or Potts states), energies [n] int64."""
+    X = np.ascontiguousarray(np.asarray(solutions).reshape(len(energies), -1), np.int32)
+    E = np.ascontiguousarray(energies, np.int64)
+    n, N = X.shape
+    cnt = C.c_int32()
+    chosen = np.empty(max(n, 1), np.int32)
+    rc = lib.spg_diversity(n, N, _ptr(X, C.c_int32), _ptr(E, C.c_int64), int(e_best), float(a_r), C.byref(cnt),
+                           _ptr(chosen, C.c_int32))
+    if rc != 0:
+        raise SpgError(rc, "spg_diversity: bad arguments")
+    return cnt.value, [int(v) for v in chosen[:cnt.value]]
 
 
 def spg_autotune_set(mode: int) -> int:

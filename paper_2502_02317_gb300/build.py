@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libspg.so")
 SOURCES = ["boundary.cu", "search.cu", "spg_api.cpp", "truncate_static.cu", "sweep.cu", "umma_gemm.cu", "renv_tc.cu",
-           "warmstart.cu", "probe.cu", "autotune.cpp", "hamiltonian.cpp"]
+           "warmstart.cu", "probe.cu", "autotune.cpp", "hamiltonian.cpp", "metrics.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-cudart", "shared"]
 
