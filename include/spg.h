@@ -243,6 +243,25 @@ int spg_hamiltonian_classes(const spg_hamiltonian* H, int32_t site, int32_t whic
  * C[h][v][r][d] (times the anti-diagonal factor on king's graphs), so no
  * tensor over the 2^k states is formed.  SPG_EINVAL for beta <= 0. */
 int spg_hamiltonian_class_weights(const spg_hamiltonian* H, int32_t site, double beta, double* C);
+/* The PEPS site tensor of site s = (i, j) at inverse temperature beta (Sec. 2,
+ * Fig. 1(b)-(c); the row MPO of the boundary-MPS contraction), assembled from
+ * the class weights C and the Boltzmann factors of the reduced tables
+ * between class representatives (first states), never from a tensor over the
+ * states:
+ *   W[(a, g)][(a', g')][u][d] = b_ad[a][u] [g' = P_G(u)]
+ *       sum_{h, v} b_left[(a, g)][h] b_up[u][v] C[h][v][a'][d]
+ * with a the P_R class of (i, j-1), g the P_G class of (i-1, j-1) (left bond
+ * a * G_in + g), a' this site's P_R class and g' the P_G class of (i-1, j)
+ * (right bond a' * G_out + g'), u the P_D class of (i-1, j), d this site's
+ * P_D class; b_left the factors of the edges to (i, j-1) and (i-1, j-1),
+ * b_up of the edge to (i-1, j), b_ad of the edge (i-1, j)-(i, j-1), and
+ * P_G(u) the P_G class of the states of class u.  Every weight is shifted by
+ * its table's minimum (exp(-beta 2^-shift (E - min E))), so log Z = log of
+ * the contracted network - beta 2^-shift (sum of the local tables' and the
+ * edges' minima).  A missing neighbour or edge contributes dimension 1 and
+ * factors 1.  Writes dims = {DL, DR, DU, ND} and, where not NULL, W
+ * (row-major [DL][DR][DU][ND] doubles).  SPG_EINVAL for beta <= 0. */
+int spg_hamiltonian_site_tensor(const spg_hamiltonian* H, int32_t site, double beta, int32_t* dims, double* W);
 void spg_hamiltonian_destroy(spg_hamiltonian* H);
 
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t

@@ -112,6 +112,7 @@ def _load():
         "spg_hamiltonian_edge": (C.c_int, [P, I32, pI32, pI32, pI32, pI32, pI64, pI32, pI32]),
         "spg_hamiltonian_classes": (C.c_int, [P, I32, I32, pI32, pI32, pI32]),
         "spg_hamiltonian_class_weights": (C.c_int, [P, I32, D, pD]),
+        "spg_hamiltonian_site_tensor": (C.c_int, [P, I32, D, pI32, pD]),
         "spg_hamiltonian_destroy": (None, [P]),
         "spg_diversity": (C.c_int, [I32, I32, pI32, pI64, C.c_int64, D, pI32, pI32]),
         "spg_autotune_set": (C.c_int, [I32, pI32]),
@@ -330,6 +331,16 @@ class Hamiltonian:
         if rc != 0:
             raise SpgError(rc, "spg_hamiltonian_class_weights")
         return Cw
+
+    def site_tensor(self, site: int, beta: float):
+        """W [DL, DR, DU, ND] (float64): the site's PEPS tensor."""
+        dims = np.zeros(4, np.int32)
+        rc = lib.spg_hamiltonian_site_tensor(self.h, site, float(beta), _ptr(dims, C.c_int32), None)
+        if rc != 0:
+            raise SpgError(rc, "spg_hamiltonian_site_tensor")
+        W = np.empty(tuple(int(v) for v in dims), np.float64)
+        lib.spg_hamiltonian_site_tensor(self.h, site, float(beta), _ptr(dims, C.c_int32), _ptr(W, C.c_double))
+        return W
 
     def close(self):
         if self.h:

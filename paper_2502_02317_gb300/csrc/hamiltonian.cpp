@@ -365,3 +365,88 @@ extern "C" int spg_hamiltonian_class_weights(const spg_hamiltonian* H, int32_t s
   }
   return SPG_OK;
 }
+
+namespace {
+
+const spg_hamiltonian::Edge* edge_between(const spg_hamiltonian* H, int s, int t) {
+  if (s < 0 || t < 0) return nullptr;
+  auto it = H->edge_of.find({std::min(s, t), std::max(s, t)});
+  return it == H->edge_of.end() ? nullptr : &H->edges[it->second];
+}
+
+// Boltzmann factors exp(-bu (E_e[xs][xt] - min E_e)) of the edge between s
+// and t (seen from s) at the states rs x rt; ones without an edge.
+std::vector<double> boltz(const spg_hamiltonian* H, int s, int t, const std::vector<int32_t>& rs,
+                          const std::vector<int32_t>& rt, double bu) {
+  std::vector<double> out(rs.size() * rt.size(), 1.0);
+  const spg_hamiltonian::Edge* e = edge_between(H, s, t);
+  if (!e) return out;
+  const int64_t nb = (int64_t)1 << e->Sn.size();
+  const int64_t mn = *std::min_element(e->T.begin(), e->T.end());
+  for (size_t a = 0; a < rs.size(); ++a)
+    for (size_t b = 0; b < rt.size(); ++b) {
+      const int64_t xm = s == e->m ? rs[a] : rt[b], xn = s == e->m ? rt[b] : rs[a];
+      const int64_t v = e->T[sub_of(xm, e->Sm) * nb + sub_of(xn, e->Sn)];
+      out[a * rt.size() + b] = std::exp(-bu * (double)(v - mn));
+    }
+  return out;
+}
+
+}  // namespace
+
+extern "C" int spg_hamiltonian_site_tensor(const spg_hamiltonian* H, int32_t site, double beta, int32_t* dims,
+                                           double* W) {
+  if (!H || site < 0 || site >= (int32_t)H->E.size() || !(beta > 0.0)) return SPG_EINVAL;
+  try {
+    const int cols = H->cols, rows = H->rows, i = site / cols, j = site % cols;
+    auto at = [&](int ii, int jj) { return (ii >= 0 && ii < rows && jj >= 0 && jj < cols) ? ii * cols + jj : -1; };
+    const int left = at(i, j - 1), upleft = at(i - 1, j - 1), up = at(i - 1, j);
+    const double bu = beta * std::ldexp(1.0, -H->shift);
+    std::vector<int32_t> P[4], rep[4], tmp, repRl{0}, repGul{0}, repDu{0}, PGu, repGu{0};
+    for (int w = 0; w < 4; ++w) {
+      const int rc = site_classes(H, site, w, P[w], rep[w]);
+      if (rc != SPG_OK) return rc;
+    }
+    int rc = SPG_OK;
+    if (left >= 0 && (rc = site_classes(H, left, SPG_CLASS_R, tmp, repRl)) != SPG_OK) return rc;
+    if (upleft >= 0 && (rc = site_classes(H, upleft, SPG_CLASS_G, tmp, repGul)) != SPG_OK) return rc;
+    if (up >= 0 && (rc = site_classes(H, up, SPG_CLASS_D, tmp, repDu)) != SPG_OK) return rc;
+    if (up >= 0 && (rc = site_classes(H, up, SPG_CLASS_G, PGu, repGu)) != SPG_OK) return rc;
+    const int NL = (int)rep[0].size(), NU = (int)rep[1].size(), NR = (int)rep[2].size(), ND = (int)rep[3].size();
+    const int NRl = (int)repRl.size(), Gin = (int)repGul.size(), DU = (int)repDu.size(), Gout = (int)repGu.size();
+    const int DL = NRl * Gin, DR = NR * Gout;
+    if (dims) {
+      dims[0] = DL;
+      dims[1] = DR;
+      dims[2] = DU;
+      dims[3] = ND;
+    }
+    if (!W) return SPG_OK;
+    const std::vector<double> bh = boltz(H, left, site, repRl, rep[0], bu);     // [NRl][NL]
+    const std::vector<double> bd = boltz(H, upleft, site, repGul, rep[0], bu);  // [Gin][NL]
+    const std::vector<double> bup = boltz(H, up, site, repDu, rep[1], bu);      // [DU][NU]
+    const std::vector<double> bad = boltz(H, up, left, repDu, repRl, bu);       // [DU][NRl]
+    std::vector<double> C((size_t)NL * NU * NR * ND);
+    if ((rc = spg_hamiltonian_class_weights(H, site, beta, C.data())) != SPG_OK) return rc;
+    std::fill(W, W + (size_t)DL * DR * DU * ND, 0.0);
+    for (int l = 0; l < DL; ++l) {
+      const int a = l / Gin, g = l % Gin;
+      for (int u = 0; u < DU; ++u) {
+        const int gu = up >= 0 ? PGu[repDu[u]] : 0;
+        const double f = bad[(size_t)u * NRl + a];
+        for (int ap = 0; ap < NR; ++ap)
+          for (int d = 0; d < ND; ++d) {
+            double acc = 0.0;
+            for (int h = 0; h < NL; ++h)
+              for (int v = 0; v < NU; ++v)
+                acc += bh[(size_t)a * NL + h] * bd[(size_t)g * NL + h] * bup[(size_t)u * NU + v] *
+                       C[(((size_t)h * NU + v) * NR + ap) * ND + d];
+            W[(((size_t)l * DR + ap * Gout + gu) * DU + u) * ND + d] = f * acc;
+          }
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    return SPG_ENOMEM;
+  }
+  return SPG_OK;
+}

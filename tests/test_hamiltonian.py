@@ -100,3 +100,44 @@ def test_hamiltonian_refusals():
     assert code(_row_of_cells(4, [(0, 0, 1, 0)], col_of_cell=[0, 0])) == spg.SPG_EINVAL
     # within the limits the same shapes build
     assert len(spg.spg_potts_hamiltonian(_row_of_cells(12, [(0, q, 1, q) for q in range(12)])).edges) == 1
+
+
+@pytest.mark.parametrize("name", ["chimera_pm1", "king_ising", "cells8_king", "cells16_king", "cells16_square"])
+def test_site_tensors_equal_the_oracle_site_tensors(name):
+    import paper_2502_02317_gb300 as spg
+    inst = CASES[name]()
+    H = spg.spg_potts_hamiltonian(inst)
+    p = peps.build(tables.from_ising(inst), 0.8)
+    for s, st in enumerate(p.sites):
+        ref = peps.mpo_site(st)
+        W = H.site_tensor(s, 0.8)
+        assert W.shape == ref.shape == (st.DL, st.DR, st.DU, st.ND)
+        np.testing.assert_allclose(W, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+
+
+def _contract(Ws, rows, cols):
+    """Z of the network of site tensors W[l][r][u][d] (plain einsum over every
+    shared bond; the boundary bonds have dimension 1)."""
+    letters = iter("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ")
+    hb = {(i, j): next(letters) for i in range(rows) for j in range(cols + 1)}
+    vb = {(i, j): next(letters) for i in range(rows + 1) for j in range(cols)}
+    terms = [f"{hb[i, j]}{hb[i, j + 1]}{vb[i, j]}{vb[i + 1, j]}" for i in range(rows) for j in range(cols)]
+    return float(np.einsum(",".join(terms) + "->", *Ws))
+
+
+@pytest.mark.parametrize("rows,cols,links,node", [(1, 3, 2, I.KING), (2, 2, 1, I.KING), (2, 2, 2, I.SQUARE)])
+def test_site_tensors_of_zephyr_size_cells_give_the_exact_log_z(rows, cols, links, node):
+    """16-spin cells: the network of the library's site tensors, contracted
+    exactly, with the tables' minima added back, gives the log Z of
+    exact.interface_sum (a sum over the interface spins' configurations
+    written from Eq. 2; no oracle tables, tensors or MPSs)."""
+    import paper_2502_02317_gb300 as spg
+    from oracle import exact
+    inst = I.large_cells(rows, cols, 16, 60 + rows * 10 + links, links=links, node_type=node)
+    beta = 0.5
+    H = spg.spg_potts_hamiltonian(inst)
+    Ws = [H.site_tensor(s, beta) for s in range(rows * cols)]
+    shift = sum(int(E.min()) for E in H.E_loc) + sum(int(R.min()) for R, _, _ in H.edges.values())
+    log_z = np.log(_contract(Ws, rows, cols)) - beta * shift
+    ref = exact.interface_sum(inst, beta)["logZ"]
+    assert abs(log_z - ref) <= 1e-10 * abs(ref)
