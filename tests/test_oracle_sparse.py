@@ -125,3 +125,13 @@ def test_zephyr_size_cells_against_the_interface_sum(rows, cols, links, node):
     for x, E in zip(res.states, res.energies):
         assert E >= ref["ground"]
         assert E == tables.ising_energy(inst, tables.spins_from_states(fg, x, inst.n_spins))
+
+
+def test_the_eight_lattice_transformations_keep_log_z_of_large_cells():
+    """Sec. 3.1 (all_lattice_transformations): the 8 rotations / reflections of
+    a 2 x 3 king's grid of 16-spin cells give the same untruncated log Z."""
+    from oracle import lattice
+    inst = I.large_cells(2, 3, 16, 77, links=1)
+    vals = [log_z(tables.from_ising(lattice.transform(inst, k)), 0.4, 64) for k in range(8)]
+    assert max(vals) - min(vals) <= 1e-9 * abs(vals[0])
+    assert abs(vals[0] - exact.interface_sum(inst, 0.4)["logZ"]) <= 1e-9 * abs(vals[0])
