@@ -226,8 +226,10 @@ int spg_hamiltonian_edge(const spg_hamiltonian* H, int32_t k, int32_t* m, int32_
  *   SPG_CLASS_R: edges to (i, j+1) and (i-1, j+1)   SPG_CLASS_G: (i+1, j+1)
  *   SPG_CLASS_D: edges to (i+1, j-1), (i+1, j) and (i+1, j+1).
  * They are found over the configurations of the spins those edges couple
- * (at most 20).  Writes the class count and, where not NULL, P[states of s]
- * and reps[class count] (the first state of each class). */
+ * (at most 20, and at most 2^24 key entries: configurations x the edges'
+ * row lengths; SPG_EUNSUPPORTED beyond).  Writes the class count and, where
+ * not NULL, P[states of s] and reps[class count] (the first state of each
+ * class). */
 #define SPG_CLASS_L 0
 #define SPG_CLASS_U 1
 #define SPG_CLASS_R 2
@@ -260,7 +262,9 @@ int spg_hamiltonian_class_weights(const spg_hamiltonian* H, int32_t site, double
  * the contracted network - beta 2^-shift (sum of the local tables' and the
  * edges' minima).  A missing neighbour or edge contributes dimension 1 and
  * factors 1.  Writes dims = {DL, DR, DU, ND} and, where not NULL, W
- * (row-major [DL][DR][DU][ND] doubles).  SPG_EINVAL for beta <= 0. */
+ * (row-major [DL][DR][DU][ND] doubles).  SPG_EINVAL for beta <= 0;
+ * SPG_EUNSUPPORTED when the sums exceed 4e9 multiply-adds
+ * (DL DU NR ND NL NU). */
 int spg_hamiltonian_site_tensor(const spg_hamiltonian* H, int32_t site, double beta, int32_t* dims, double* W);
 void spg_hamiltonian_destroy(spg_hamiltonian* H);
 

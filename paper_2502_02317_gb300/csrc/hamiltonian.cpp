@@ -294,6 +294,9 @@ int site_classes(const spg_hamiltonian* H, int s, int which, std::vector<int32_t
   U.erase(std::unique(U.begin(), U.end()), U.end());
   if (U.size() > 20) return SPG_EUNSUPPORTED;
   const int64_t nc = (int64_t)1 << U.size();
+  int64_t key_len = 0;  // entries of one configuration's key
+  for (const Part& p : parts) key_len += (int64_t)1 << (p.row ? p.e->Sn.size() : p.e->Sm.size());
+  if (nc * std::max<int64_t>(key_len, 1) > ((int64_t)1 << 24)) return SPG_EUNSUPPORTED;  // keys beyond 128 MB
   std::vector<int32_t> cls((size_t)nc);
   std::vector<int64_t> first;
   std::map<std::vector<int64_t>, int32_t> index;
@@ -415,6 +418,8 @@ extern "C" int spg_hamiltonian_site_tensor(const spg_hamiltonian* H, int32_t sit
     const int NL = (int)rep[0].size(), NU = (int)rep[1].size(), NR = (int)rep[2].size(), ND = (int)rep[3].size();
     const int NRl = (int)repRl.size(), Gin = (int)repGul.size(), DU = (int)repDu.size(), Gout = (int)repGu.size();
     const int DL = NRl * Gin, DR = NR * Gout;
+    // the sums cost DL DU NR ND NL NU multiply-adds
+    if ((double)DL * DU * NR * ND * NL * NU > 4e9) return SPG_EUNSUPPORTED;
     if (dims) {
       dims[0] = DL;
       dims[1] = DR;

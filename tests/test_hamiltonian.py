@@ -141,3 +141,28 @@ def test_site_tensors_of_zephyr_size_cells_give_the_exact_log_z(rows, cols, link
     log_z = np.log(_contract(Ws, rows, cols)) - beta * shift
     ref = exact.interface_sum(inst, beta)["logZ"]
     assert abs(log_z - ref) <= 1e-10 * abs(ref)
+
+
+def test_projection_over_too_many_interface_spins_is_refused():
+    """Site (0, 1) of a 2 x 3 king's grid of 22-spin cells couples 7 of its
+    spins to each cell below: its P_D spans 21 interface spins (beyond 20)."""
+    import paper_2502_02317_gb300 as spg
+    k = 22
+    ei, ej = [], []
+    for t, col in enumerate((0, 1, 2)):
+        for q in range(7):
+            ei.append(k * 1 + 7 * t + q)        # cell (0, 1)
+            ej.append(k * (3 + col))            # spin 0 of cell (1, col)
+    n = 6 * k
+    inst = I.IsingInstance(n, np.array(ei, np.int32), np.array(ej, np.int32), np.ones(len(ei)), np.zeros(n),
+                           np.repeat(np.arange(6, dtype=np.int32), k), 2, 3,
+                           np.array([0, 0, 0, 1, 1, 1], np.int32), np.array([0, 1, 2, 0, 1, 2], np.int32), 0,
+                           I.KING)
+    H = spg.spg_potts_hamiltonian(inst)
+    assert len(H.edges) == 3
+    with pytest.raises(spg.SpgError) as e:
+        H.classes(1, H.D)
+    assert e.value.code == spg.SPG_EUNSUPPORTED
+    P, reps = H.classes(1, H.L)  # no edge on the left: one class
+    assert len(reps) == 1 and not P.any()
+
