@@ -234,8 +234,9 @@ def sweeps_to_fidelity(trace, best, tol=1e-6):
 
 def warm_start_leg(spg, ctx, torch, n_train=16, n_eval=2, eval_rows=(2, 9), n_sweeps=12, steps=1500, chi=64,
                    hidden=256):
-    """The learned warm start (BASELINE config 5, scaled down to bench
-    minutes): an MLP from the couplings near a boundary row to that row's MPS
+    """The learned warm start (trained on 12x12 +-1 Chimera instances,
+    judged on unseen 16x16 ones at chi 64, scaled down to bench minutes): an
+    MLP from the couplings near a boundary row to that row's MPS
     sites, trained by the library's own kernels on every row the method
     builds for n_train 12x12 +-1 Chimera instances at chi 64, then judged on
     unseen 16x16 instances by the plain contraction: sweeps until the
