@@ -197,7 +197,7 @@ def cpu_oracle_sample(seed, max_sites=6):
             "sampled_rate": cand / dt, "boundary_s": t_boundary, "projected_solve_s": proj_t}
 
 
-def cpu_oracle_cfg1(seeds=(0, 1)):
+def cpu_oracle_chimera3x3(seeds=(0, 1)):
     """Full oracle solves of the plain FP64 workload (3x3 Chimera, +-1, beta
     1, chi 16, beam 256): beam states per second, no sampling."""
     import instances as I
@@ -212,12 +212,12 @@ def cpu_oracle_cfg1(seeds=(0, 1)):
     return {"value": cand / t, "unit": "beam states/s", "seeds": len(seeds), "s": t}
 
 
-def cpu_oracle_cfg1_one_thread():
-    """cpu_oracle_cfg1 in a child process with every BLAS pool at 1 thread
-    (the variables are read when NumPy loads)."""
+def cpu_oracle_chimera3x3_one_thread():
+    """cpu_oracle_chimera3x3 in a child process with every BLAS pool at 1
+    thread (the variables are read when NumPy loads)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                BLIS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    code = "import bench, json; print(json.dumps(bench.cpu_oracle_cfg1()))"
+    code = "import bench, json; print(json.dumps(bench.cpu_oracle_chimera3x3()))"
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     if r.returncode != 0:
         return {"error": r.stderr[-300:]}
@@ -692,10 +692,11 @@ def main():
     line["kernel_rooflines"] = [kernel_roofline(k, *v) for k, v in counted[:6]]
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(0)
-        line["cpu_baseline_cfg1"] = {"all_cores": {**cpu_oracle_cfg1(), "cores": len(os.sched_getaffinity(0))},
-                                     "one_thread": {**cpu_oracle_cfg1_one_thread(), "cores": 1},
-                                     "workload": "full oracle solves of 3x3 Chimera +-1, beta 1, chi 16, beam 256 "
-                                                 "(seeds 0, 1)"}
+        line["cpu_baseline_chimera3x3"] = {"all_cores": {**cpu_oracle_chimera3x3(),
+                                                         "cores": len(os.sched_getaffinity(0))},
+                                           "one_thread": {**cpu_oracle_chimera3x3_one_thread(), "cores": 1},
+                                           "workload": "full oracle solves of 3x3 Chimera +-1, beta 1, chi 16, "
+                                                       "beam 256 (seeds 0, 1)"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
