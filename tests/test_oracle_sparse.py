@@ -135,3 +135,28 @@ def test_the_eight_lattice_transformations_keep_log_z_of_large_cells():
     vals = [log_z(tables.from_ising(lattice.transform(inst, k)), 0.4, 64) for k in range(8)]
     assert max(vals) - min(vals) <= 1e-9 * abs(vals[0])
     assert abs(vals[0] - exact.interface_sum(inst, 0.4)["logZ"]) <= 1e-9 * abs(vals[0])
+
+
+@pytest.mark.parametrize("make", [lambda: I.large_cells(1, 2, 10, 4), lambda: I.large_cells(2, 2, 4, 9, links=2),
+                                  lambda: I.chimera(2, 3, couplings="gauss", h_sigma=0.1, cols=1)])
+def test_interface_sum_equals_brute_force(make):
+    """exact.interface_sum (used above for cells too large for brute force)
+    against exact.brute_force on instances of at most 20 spins: log Z, the
+    ground energy and the exact marginal of the first cell's states."""
+    inst = make()
+    beta = 0.7
+    bf = exact.brute_force(inst, beta)
+    it = exact.interface_sum(inst, beta)
+    assert abs(it["logZ"] - bf["logZ"]) <= 1e-12 * abs(bf["logZ"])
+    assert it["ground"] == bf["ground"]
+    cos = np.asarray(inst.cluster_of_spin)
+    c0 = int(np.nonzero((np.asarray(inst.cluster_row) == 0) & (np.asarray(inst.cluster_col) == 0))[0][0])
+    members = np.sort(np.nonzero(cos == c0)[0])
+    idx = np.arange(2 ** inst.n_spins, dtype=np.int64)
+    x0 = np.zeros_like(idx)
+    for k, sp in enumerate(members):
+        x0 |= ((idx >> int(sp)) & 1) << k
+    u = 2.0 ** -inst.energy_shift
+    m = np.full(2 ** len(members), -np.inf)
+    np.logaddexp.at(m, x0, -beta * u * bf["E"].astype(np.float64))
+    np.testing.assert_allclose(it["logp_first"], m - bf["logZ"], rtol=0, atol=1e-10)
