@@ -37,7 +37,8 @@ no blocking, fusion or reordering beyond what each step states:
   spin configurations (<= 24 spins), spin-level row transfer matrices for
   width-3 Chimera strips (exact log Z and exact ground energy), and sums over
   the interface spins of large clusters (exact log Z, ground energy and the
-  first cluster's marginal).
+  first cluster's marginal); ``bruteforce.c`` (loaded by ``native``) is the
+  same brute force in C with OpenMP, for up to 30 spins.
 
 Where the paper leaves a point open, the reading taken is stated in the
 docstring of the function that implements it.

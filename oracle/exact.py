@@ -16,6 +16,8 @@ Eq. 1, directly:
   (log-sum-exp) or minimised with the couplers between clusters, giving the
   exact log Z, ground energy and the exact marginal of the states of the
   cluster on grid cell (0, 0);
+* ``brute_force_c``: the same ground energy, degeneracy and log Z from a C
+  enumerator parallel over the host's cores (``bruteforce.c``);
 * ``chimera_strip``: row transfer matrices of a Chimera-like strip of width
   <= 3 cells over the 4w side-A spins of a row (the only spins with couplers
   to the next row), giving exact log Z (log-sum-exp) and the exact ground
@@ -289,3 +291,25 @@ def interface_sum(inst, beta: float, max_bits: int = 22):
     logZ = logsumexp(F[c0] + G0)
     logp0 = -beta * u * E0.astype(np.float64) + G0[a0] - logZ
     return {"logZ": logZ, "ground": ground, "logp_first": logp0}
+
+
+def brute_force_c(inst, beta: float):
+    """``brute_force``'s ground energy, degeneracy and log Z from the C
+    enumerator (bruteforce.c, OpenMP over the host's cores; up to 30 spins):
+    {"ground", "degeneracy", "logZ"}."""
+    import ctypes
+
+    from . import native
+    J = np.ascontiguousarray(_grid_ints(inst.J, inst.energy_shift), np.int64)
+    h = np.ascontiguousarray(_grid_ints(inst.h, inst.energy_shift), np.int64)
+    ei = np.ascontiguousarray(inst.ei, np.int32)
+    ej = np.ascontiguousarray(inst.ej, np.int32)
+    emin, deg, lz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    p32, p64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    rc = native.lib().oracle_brute_force(inst.n_spins, len(J), ei.ctypes.data_as(p32), ej.ctypes.data_as(p32),
+                                         J.ctypes.data_as(p64), h.ctypes.data_as(p64),
+                                         beta * 2.0 ** (-inst.energy_shift), ctypes.byref(emin), ctypes.byref(deg),
+                                         ctypes.byref(lz))
+    if rc != 0:
+        raise ValueError("the C brute force takes 1..30 spins")
+    return {"ground": emin.value, "degeneracy": deg.value, "logZ": lz.value}

@@ -160,3 +160,14 @@ def test_interface_sum_equals_brute_force(make):
     m = np.full(2 ** len(members), -np.inf)
     np.logaddexp.at(m, x0, -beta * u * bf["E"].astype(np.float64))
     np.testing.assert_allclose(it["logp_first"], m - bf["logZ"], rtol=0, atol=1e-10)
+
+
+def test_28_spins_in_two_cells_against_the_c_brute_force():
+    """Two 14-spin cells (28 spins, beyond the NumPy enumeration): log Z at an
+    untruncated bond dimension equals the C enumerator's (2^28 configurations
+    on the host's cores)."""
+    inst = I.large_cells(1, 2, 14, 33, links=3)
+    fg = tables.from_ising(inst)
+    assert fg.sparse
+    ref = exact.brute_force_c(inst, 0.6)
+    assert abs(log_z(fg, 0.6, 64) - ref["logZ"]) <= 1e-9 * abs(ref["logZ"])
