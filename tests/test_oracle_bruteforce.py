@@ -2,6 +2,7 @@
 enumeration of exact.brute_force: the same ground energy and degeneracy
 (exact integers) and log Z, on Chimera (Gaussian J and fields), square,
 king's and large-cell instances of 16 to 20 spins."""
+import numpy as np
 import pytest
 
 import instances as I
@@ -27,3 +28,17 @@ def test_c_brute_force_refuses_too_many_spins():
     inst = I.large_cells(1, 2, 16, 1)  # 32 spins
     with pytest.raises(ValueError):
         exact.brute_force_c(inst, 1.0)
+
+
+def test_king_graph_log_z_beyond_the_numpy_enumeration():
+    """27 spins (3 x 3 king's graph, 3 spins per cluster, every spin of a
+    cluster coupled to every spin of its 8 neighbours): the oracle's log Z
+    at an untruncated bond dimension equals the C brute force."""
+    from oracle import boundary, peps, tables
+    inst = I.king_ising(3, 3, 3, 12)
+    beta = 0.6
+    p = peps.build(tables.from_ising(inst), beta)
+    B0 = boundary.boundary_mpses(p, 4096, 0, down_to=0)[0]
+    log_z = B0.lognorm + float(np.log(boundary.contract_value(B0))) + p.log_offset
+    ref = exact.brute_force_c(inst, beta)["logZ"]
+    assert abs(log_z - ref) <= 1e-9 * abs(ref)
