@@ -30,15 +30,20 @@ def test_c_brute_force_refuses_too_many_spins():
         exact.brute_force_c(inst, 1.0)
 
 
-def test_king_graph_log_z_beyond_the_numpy_enumeration():
+def test_king_graph_beyond_the_numpy_enumeration():
     """27 spins (3 x 3 king's graph, 3 spins per cluster, every spin of a
     cluster coupled to every spin of its 8 neighbours): the oracle's log Z
-    at an untruncated bond dimension equals the C brute force."""
-    from oracle import boundary, peps, tables
+    at an untruncated bond dimension, and the ground energy of its search in
+    the exact limit (merging, beam >= boundary keys x states = 8^4 x 8),
+    equal the C brute force."""
+    from oracle import boundary, peps, search, tables
     inst = I.king_ising(3, 3, 3, 12)
     beta = 0.6
-    p = peps.build(tables.from_ising(inst), beta)
+    fg = tables.from_ising(inst)
+    p = peps.build(fg, beta)
     B0 = boundary.boundary_mpses(p, 4096, 0, down_to=0)[0]
     log_z = B0.lognorm + float(np.log(boundary.contract_value(B0))) + p.log_offset
-    ref = exact.brute_force_c(inst, beta)["logZ"]
-    assert abs(log_z - ref) <= 1e-9 * abs(ref)
+    ref = exact.brute_force_c(inst, beta)
+    assert abs(log_z - ref["logZ"]) <= 1e-9 * abs(ref["logZ"])
+    res = search.solve(fg, search.Params(beta=beta, chi=4096, beam=8 ** 4 * 8))
+    assert int(res.energies[0]) == ref["ground"]
