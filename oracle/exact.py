@@ -14,8 +14,8 @@ Eq. 1, directly:
   the configuration of its interface spins (those with a coupler to another
   cluster), and every combination of interface configurations is summed
   (log-sum-exp) or minimised with the couplers between clusters, giving the
-  exact log Z, ground energy and the exact marginal of the states of the
-  cluster on grid cell (0, 0);
+  exact log Z, ground energy and the exact marginal of one cluster's states,
+  also given the states of other clusters (conditionals);
 * ``brute_force_c``: the same ground energy, degeneracy and log Z from a C
   enumerator parallel over the host's cores (``bruteforce.c``);
 * ``chimera_strip``: row transfer matrices of a Chimera-like strip of width
@@ -228,11 +228,15 @@ def _bits(x, n):
     return 2 * ((x >> np.arange(n, dtype=np.int64)[None, :]) & 1) - 1
 
 
-def interface_sum(inst, beta: float, max_bits: int = 22):
-    """Exact log Z, ground energy and log-marginal of the states of the
-    cluster on cell (0, 0) (module header), from Eq. 2 on the instance's
-    arrays.  The sum runs over 2^(total interface spins) <= 2^max_bits
-    combinations."""
+def interface_sum(inst, beta: float, max_bits: int = 22, fixed=None, target: int = 0):
+    """Exact log Z, ground energy and the log-marginal of the states of the
+    cluster on site `target` (row-major cell index; module header), from
+    Eq. 2 on the instance's arrays, with the clusters of the sites in
+    `fixed` ({site: state}) held at those states: then log Z and the ground
+    energy are those of the configurations that agree with them, and the
+    marginal is the conditional given them.  The sum runs over
+    2^(total interface spins) <= 2^max_bits combinations."""
+    fixed = fixed or {}
     J = _grid_ints(inst.J, inst.energy_shift)
     h = _grid_ints(inst.h, inst.energy_shift)
     u = 2.0 ** (-inst.energy_shift)
@@ -259,13 +263,18 @@ def interface_sum(inst, beta: float, max_bits: int = 22):
         for t, q in enumerate(iface[c]):
             a |= ((np.arange(2 ** k, dtype=np.int64) >> q) & 1) << t
         lw = -beta * u * E.astype(np.float64)
+        site = int(inst.cluster_row[c]) * inst.grid_cols + int(inst.cluster_col[c])
+        keep = np.ones(2 ** k, dtype=bool)
+        if site in fixed:  # only the held state contributes
+            keep[:] = False
+            keep[int(fixed[site])] = True
         Fc = np.full(2 ** len(iface[c]), -np.inf)
-        np.logaddexp.at(Fc, a, lw)
+        np.logaddexp.at(Fc, a[keep], lw[keep])
         Mc = np.full(2 ** len(iface[c]), np.iinfo(np.int64).max, dtype=np.int64)
-        np.minimum.at(Mc, a, E)
+        np.minimum.at(Mc, a[keep], E[keep])
         F.append(Fc)
         M.append(Mc)
-        if members[c].size and int(inst.cluster_row[c]) == 0 and int(inst.cluster_col[c]) == 0:
+        if site == target:
             E0, a0, c0 = E, a, c
     # inter-cluster couplers as (bit offset of each end in the combination, J)
     ends = [(off[cos[ei[e]]] + iface[cos[ei[e]]].index(pos[int(ei[e])][1]),
@@ -280,17 +289,22 @@ def interface_sum(inst, beta: float, max_bits: int = 22):
             Ein += Jv * (2 * ((g >> bi) & 1) - 1) * (2 * ((g >> bj) & 1) - 1)
         lrest = -beta * u * Ein.astype(np.float64)
         emin = Ein.copy()
+        ok = np.ones(len(g), dtype=bool)
         for c in range(n_cl):
             ac = (g >> off[c]) & ((1 << len(iface[c])) - 1)
-            emin += M[c][ac]
+            ok &= M[c][ac] != np.iinfo(np.int64).max  # combinations a held cluster cannot take
+            emin += np.where(M[c][ac] != np.iinfo(np.int64).max, M[c][ac], 0)
             if c != c0:
                 lrest += F[c][ac]
-        g_min = int(emin.min())
-        ground = g_min if ground is None else min(ground, g_min)
+        if ok.any():
+            g_min = int(emin[ok].min())
+            ground = g_min if ground is None else min(ground, g_min)
         np.logaddexp.at(G0, (g >> off[c0]) & ((1 << len(iface[c0])) - 1), lrest)
     logZ = logsumexp(F[c0] + G0)
-    logp0 = -beta * u * E0.astype(np.float64) + G0[a0] - logZ
-    return {"logZ": logZ, "ground": ground, "logp_first": logp0}
+    logp = -beta * u * E0.astype(np.float64) + G0[a0] - logZ
+    if target in fixed:
+        logp = np.where(np.arange(len(logp)) == int(fixed[target]), 0.0, -np.inf)
+    return {"logZ": logZ, "ground": ground, "logp": logp}
 
 
 def brute_force_c(inst, beta: float):

@@ -110,8 +110,8 @@ def test_24_spins_in_two_cells_against_brute_force():
 @pytest.mark.parametrize("rows,cols,links,node", [(1, 3, 2, I.KING), (2, 2, 1, I.KING), (2, 2, 2, I.SQUARE)])
 def test_zephyr_size_cells_against_the_interface_sum(rows, cols, links, node):
     """Cells of 16 spins (65,536 states): log Z at an untruncated bond
-    dimension and the conditional of the first cell equal
-    ``exact.interface_sum``; every state the search returns carries its Eq. 2
+    dimension, the marginal of the first cell and the teacher-forced
+    conditionals of the later cells equal ``exact.interface_sum``; every state the search returns carries its Eq. 2
     energy, none below the exact ground energy."""
     inst = I.large_cells(rows, cols, 16, 40 + rows * 10 + links, links=links, node_type=node)
     fg = tables.from_ising(inst)
@@ -120,7 +120,16 @@ def test_zephyr_size_cells_against_the_interface_sum(rows, cols, links, node):
     assert abs(log_z(fg, beta, 64) - ref["logZ"]) <= 1e-9 * abs(ref["logZ"])
     prm = search.Params(beta=beta, chi=64, beam=2)
     got0 = search.debug_marginals(fg, prm, 0, [[]])[0]
-    np.testing.assert_allclose(got0, ref["logp_first"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(got0, ref["logp"], rtol=1e-9, atol=1e-9)
+    # teacher-forced conditionals of the later sites given random prefixes
+    rng = np.random.default_rng(5)
+    for site in range(1, fg.n_sites):
+        pre = [int(rng.integers(fg.d[t])) for t in range(site)]
+        got = search.debug_marginals(fg, prm, site, [pre])[0]
+        exact_c = exact.interface_sum(inst, beta, fixed=dict(enumerate(pre)), target=site)["logp"]
+        fin = np.isfinite(exact_c)
+        assert np.array_equal(np.isfinite(got), fin)
+        np.testing.assert_allclose(got[fin], exact_c[fin], rtol=1e-9, atol=1e-8)
     res = search.solve(fg, prm)
     for x, E in zip(res.states, res.energies):
         assert E >= ref["ground"]
@@ -159,7 +168,16 @@ def test_interface_sum_equals_brute_force(make):
     u = 2.0 ** -inst.energy_shift
     m = np.full(2 ** len(members), -np.inf)
     np.logaddexp.at(m, x0, -beta * u * bf["E"].astype(np.float64))
-    np.testing.assert_allclose(it["logp_first"], m - bf["logZ"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(it["logp"], m - bf["logZ"], rtol=0, atol=1e-10)
+    # conditionals given the first sites' states, against brute force
+    fg = tables.from_ising(inst)
+    cs = exact.cluster_states(inst.n_spins, fg.spins_of_site)
+    rng = np.random.default_rng(2)
+    for site in range(1, fg.n_sites):
+        pre = [int(rng.integers(fg.d[t])) for t in range(site)]
+        got = exact.interface_sum(inst, beta, fixed=dict(enumerate(pre)), target=site)["logp"]
+        ref = exact.exact_conditional(bf["E"], beta, inst.energy_shift, cs, site, pre, fg.d[site])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10)
 
 
 def test_28_spins_in_two_cells_against_the_c_brute_force():
